@@ -1,0 +1,195 @@
+"""Plain FP64 CPU oracle for the rank-one SVD update (Gandhi & Rajgor, arXiv 1707.08369).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke()``
+and by the ``cpu_baseline`` leg of ``bench.py``; never by the library.  It
+shares no code with the CUDA path.  The arithmetic lives in ``svdup_oracle.c``
+(plain C, OpenMP over independent roots and output columns); this module only
+builds/loads it and marshals numpy arrays.
+
+Functions and the passages they follow:
+  schur2            Alg. 6.1 STEP 2/3 (and App. A): [[g,1],[1,0]] = Q diag(r1,r2) Q^T
+  gemv_t            RankOneUpdate STEP 1 (Sec. 6.2): X^T a
+  secular_roots     Sec. 3.1, zeros of the secular function, by bisection
+  rank_one_eig      RankOneUpdate STEPs 2-5 (Sec. 6.2) with deflation (Sec. 3.1)
+  rank_one_compact  the same, returned as (k, idx, poles, org, tau, zhat, 1/||c_j||)
+  rank_one_update   RankOneUpdate STEPs 1-7 with a dense product (Sec. 6.2)
+  svd_update        Alg. 6.1 STEPs 1-8, descending order, paired signs
+  jacobi_svd        independent one-sided Jacobi SVD (Hestenes)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "svdup_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+OK, EINVAL, ENOMEM, ENOCONV = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile svdup_oracle.c into oracle/liboracle.so with gcc (-fopenmp)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        lib.oracle_schur2.argtypes = [D, P]
+        lib.oracle_gemv_t.argtypes = [I, I, P, I, P, P]
+        lib.oracle_secular_roots.argtypes = [I, P, P, D, P, P]
+        lib.oracle_rank_one_eig.argtypes = [I, P, P, D, P, P]
+        lib.oracle_rank_one_compact.argtypes = [I, P, P, D, P, P, P, P, P, P, P, P]
+        lib.oracle_rank_one_update_z.argtypes = [I, I, P, I, P, P, D, P, P, I, I, P]
+        lib.oracle_rank_one_update.argtypes = [I, I, P, I, P, P, D, P, P, I]
+        lib.oracle_svd_update.argtypes = [I, I, P, I, P, P, I, P, P, P, P, P]
+        lib.oracle_jacobi_svd.argtypes = [I, I, P, I, P, P, P]
+        lib.oracle_num_threads.restype = I
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _vec(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel())
+
+
+def _mat(a):
+    """Column-major float64 copy of a 2-D array."""
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def schur2(g: float):
+    """Returns (r1, r2, Q) with [[g,1],[1,0]] = Q diag(r1, r2) Q^T."""
+    out = np.zeros(6)
+    _load().oracle_schur2(float(g), _p(out))
+    Q = np.array([[out[2], out[4]], [out[3], out[5]]])
+    return out[0], out[1], Q
+
+
+def gemv_t(A, x):
+    A = _mat(A)
+    x = _vec(x)
+    y = np.zeros(A.shape[1])
+    _load().oracle_gemv_t(A.shape[0], A.shape[1], _p(A), A.shape[0], _p(x), _p(y))
+    return y
+
+
+def secular_roots(d, z, rho):
+    """Roots of 1 + rho sum z_i^2/(d_i - mu) for strictly ascending d and nonzero z.
+    Returns (org, tau): mu_j = d[org[j]] + tau[j], ascending."""
+    d = _vec(d); z = _vec(z)
+    k = d.size
+    org = np.zeros(k, dtype=np.int32)
+    tau = np.zeros(k)
+    st = _load().oracle_secular_roots(k, _p(d), _p(z), float(rho), _p(org), _p(tau))
+    if st not in (OK, ENOCONV):
+        raise RuntimeError("oracle_secular_roots failed: %d" % st)
+    return org, tau
+
+
+def rank_one_eig(d, z, rho, vectors=True):
+    """diag(d) + rho z z^T = Q diag(lam) Q^T, lam ascending."""
+    d = _vec(d); z = _vec(z)
+    N = d.size
+    lam = np.zeros(N)
+    Q = np.zeros((N, N), order="F") if vectors else None
+    st = _load().oracle_rank_one_eig(N, _p(d), _p(z), float(rho), _p(lam),
+                                      _p(Q) if vectors else None)
+    if st not in (OK, ENOCONV):
+        raise RuntimeError("oracle_rank_one_eig failed: %d" % st)
+    return (lam, Q) if vectors else lam
+
+
+def rank_one_compact(d, z, rho):
+    """Compact eigen-system: dict(k, idx, dk, org, tau, zhat, inv_norm, lam)."""
+    d = _vec(d); z = _vec(z)
+    N = d.size
+    k = ctypes.c_int(0)
+    idx = np.zeros(N, dtype=np.int32); org = np.zeros(N, dtype=np.int32)
+    dk = np.zeros(N); tau = np.zeros(N); zhat = np.zeros(N); inv = np.zeros(N); lam = np.zeros(N)
+    st = _load().oracle_rank_one_compact(N, _p(d), _p(z), float(rho), ctypes.byref(k), _p(idx), _p(dk),
+                                          _p(org), _p(tau), _p(zhat), _p(inv), _p(lam))
+    if st not in (OK, ENOCONV):
+        raise RuntimeError("oracle_rank_one_compact failed: %d" % st)
+    k = k.value
+    return dict(k=k, idx=idx[:k], dk=dk[:k], org=org[:k], tau=tau[:k], zhat=zhat[:k],
+                inv_norm=inv[:k], lam=lam)
+
+
+def rank_one_update_z(X, d, z, rho, cols=None):
+    """Y = (X Q)[:, cols] for diag(d) + rho z z^T = Q diag(lam) Q^T.  Returns (lam, Y)."""
+    X = _mat(X)
+    d = _vec(d); z = _vec(z)
+    rows, N = X.shape
+    lam = np.zeros(N)
+    if cols is None:
+        Y = np.zeros((rows, N), order="F")
+        st = _load().oracle_rank_one_update_z(rows, N, _p(X), max(rows, 1), _p(d), _p(z), float(rho),
+                                               _p(lam), _p(Y), max(rows, 1), N, None)
+    else:
+        cols = np.ascontiguousarray(np.asarray(cols, dtype=np.int32))
+        Y = np.zeros((rows, cols.size), order="F")
+        st = _load().oracle_rank_one_update_z(rows, N, _p(X), max(rows, 1), _p(d), _p(z), float(rho),
+                                               _p(lam), _p(Y), max(rows, 1), cols.size, _p(cols))
+    if st not in (OK, ENOCONV):
+        raise RuntimeError("oracle_rank_one_update_z failed: %d" % st)
+    return lam, Y
+
+
+def rank_one_update(X, d, a1, rho):
+    """RankOneUpdate(X, a1, D, rho) of Sec. 6.2 (dense product).  Returns (lam, X Q)."""
+    X = _mat(X)
+    d = _vec(d); a1 = _vec(a1)
+    rows, N = X.shape
+    lam = np.zeros(N)
+    Y = np.zeros((rows, N), order="F")
+    st = _load().oracle_rank_one_update(rows, N, _p(X), rows, _p(d), _p(a1), float(rho), _p(lam), _p(Y), rows)
+    if st not in (OK, ENOCONV):
+        raise RuntimeError("oracle_rank_one_update failed: %d" % st)
+    return lam, Y
+
+
+def svd_update(U, S, V, a, b):
+    """Alg. 6.1: SVD of U diag(S) V^T + a b^T.  Returns (Un, Sn, Vn), Sn descending."""
+    U = _mat(U); V = _mat(V)
+    S = _vec(S); a = _vec(a); b = _vec(b)
+    m, n = U.shape[0], V.shape[0]
+    Un = np.zeros((m, m), order="F"); Sn = np.zeros(m); Vn = np.zeros((n, n), order="F")
+    st = _load().oracle_svd_update(m, n, _p(U), m, _p(S), _p(V), n, _p(a), _p(b), _p(Un), _p(Sn), _p(Vn))
+    if st not in (OK, ENOCONV):
+        raise RuntimeError("oracle_svd_update failed: %d" % st)
+    return Un, Sn, Vn
+
+
+def jacobi_svd(A):
+    """One-sided Jacobi SVD of A (m x n, m <= n): A = U diag(S) Vt^T with Vt n x m."""
+    A = _mat(A)
+    m, n = A.shape
+    U = np.zeros((m, m), order="F"); S = np.zeros(m); Vt = np.zeros((n, m), order="F")
+    st = _load().oracle_jacobi_svd(m, n, _p(A), m, _p(U), _p(S), _p(Vt))
+    if st not in (OK, ENOCONV):
+        raise RuntimeError("oracle_jacobi_svd failed: %d" % st)
+    return U, S, Vt
