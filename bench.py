@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark: rank-one SVD updates per second on one GB300, square n = 8192.
+
+Workload: A = U diag(sigma) V^T with Haar U, V (8192 x 8192) and sigma log-uniform in
+[1e-4, 1]; each step applies one rank-one update a b^T (a, b ~ N(0,1)) to the previous
+result (chained updates, Alg. 6.1), inputs resident in HBM.  U and V are 512 MiB
+each, larger than L2, so no flush is needed between steps.
+
+One JSON line on stdout (rank 0).  `value` is whole-job updates/s (device-timed with
+CUDA events on the library's stream); `e2e` is the same metric through the host-buffer
+entry point (copies inside the timed region); `roofline` is for the dominant kernel
+(timed live with the library's stage timers); `cpu_baseline` is the CPU oracle on a
+bounded, extrapolated sample of the same update.
+
+--impl reference times the CPU oracle (the reference arm of this comparison) instead.
+Under torchrun every rank runs an independent replica (no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MODES = {"fp64": 0, "bf16x3": 1, "fp16x2": 2}
+FP64_PEAK_TFLOPS = 1.0  # measured DFMA throughput on this GB300 pool
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--mode", default="fp64", choices=list(MODES))
+    ap.add_argument("--eps", type=float, default=1e-12)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-cols", type=int, default=64)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(U, S, V, a, b, ncols):
+    """The oracle's update on a bounded sample: the four eigen-updates (STEPs 4-7) with
+    all roots, z vectors and norms, and `ncols` sampled output columns of each product;
+    the full update time is extrapolated linearly in columns.  Returns (seconds_full,
+    seconds_spent, description)."""
+    import oracle
+    m, n = U.shape[0], V.shape[0]
+    t_spent0 = time.perf_counter()
+    t0 = time.perf_counter()
+    p = oracle.gemv_t(U, a)
+    q = oracle.gemv_t(V, b)
+    t_gemv = time.perf_counter() - t0
+    alpha, beta = float(a @ a), float(b @ b)
+    r1, r2, Qu = oracle.schur2(beta)
+    r3, r4, Qv = oracle.schur2(alpha)
+    sq = S * q[:m]
+    z1 = Qu[0, 0] * p + Qu[1, 0] * sq
+    z2p = Qu[0, 1] * p + Qu[1, 1] * sq
+    sp = np.concatenate([S * p, np.zeros(n - m)])
+    z3 = Qv[0, 0] * q + Qv[1, 0] * sp
+    z4p = Qv[0, 1] * q + Qv[1, 1] * sp
+    Dv = np.concatenate([S ** 2, np.zeros(n - m)])
+    total = t_gemv
+    plan = [(U, S ** 2, z1, r1, z2p, m), (None, None, None, r2, None, m),
+            (V, Dv, z3, r3, z4p, n), (None, None, None, r4, None, n)]
+    carry = None
+    for i, (X, d, z, rho, znext, N) in enumerate(plan):
+        if X is None:  # second solve of the side: poles and z from the first
+            d, z = carry
+            X = np.asfortranarray(np.random.default_rng(i).standard_normal((N, N)))
+        t0 = time.perf_counter()
+        if znext is not None:
+            lam, zrow = oracle.rank_one_update_z(znext[None, :], d, z, rho)
+            carry = (lam, zrow[0])
+        else:
+            lam = oracle.rank_one_eig(d, z, rho, vectors=False)
+        t_solve = time.perf_counter() - t0
+        cols = np.linspace(0, N - 1, ncols).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.rank_one_update_z(X, d, z, rho, cols=cols)
+        t_sample = time.perf_counter() - t0
+        per_col = max(t_sample - t_solve, 0.0) / ncols
+        total += t_solve + per_col * N
+    spent = time.perf_counter() - t_spent0
+    desc = ("oracle (bisection roots, dense product): all roots, z and norms of the 4 "
+            "eigen-updates plus %d sampled output columns per product, extrapolated "
+            "linearly to all columns (extrapolated)" % ncols)
+    return total, spent, desc
+
+
+def make_inputs(n, seed, device, steps):
+    from paper_1707_08369_gb300 import workloads as wl
+    U, S, V, a0, b0 = wl.loguniform_sq(n, seed=seed, device=device)
+    g = wl.rng(seed + 7)
+    ab = [(g.standard_normal(n), g.standard_normal(n)) for _ in range(steps)]
+    return U, S, V, ab
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n = args.n
+    U, S, V, ab = make_inputs(n, 170708369 + 2, None, 1)
+    a, b = ab[0]
+    ncols = 16
+    times = []
+    for i in range(args.warmup + args.steps):
+        full, spent, desc = oracle_sample(U, S, V, a, b, ncols)
+        if i >= args.warmup:
+            times.append(full)
+    t = float(np.mean(times))
+    value = 1.0 / t
+    line = {"impl": "reference", "metric": "rank-1 SVD updates/s at n=8192", "value": value,
+            "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "square n=%d, Haar U/V, sigma log-uniform [1e-4,1], chained "
+                                   "N(0,1) rank-one updates" % n, "n": n, "mode": "oracle"},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": desc.replace("%d" % ncols, str(ncols))},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    import paper_1707_08369_gb300 as sv
+    from paper_1707_08369_gb300 import build as svbuild
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    svbuild.build()
+    sv.load()
+    n = args.n
+    mode = MODES[args.mode]
+    dev = torch.device("cuda", local)
+    steps_total = args.warmup + args.steps
+    U, S, V, ab = make_inputs(n, 170708369 + 2 + 1000 * rank, dev, steps_total)
+    # cpu baseline needs host copies of the step-0 inputs
+    U_h, S_h, V_h = (U, S, V) if (rank == 0 and not args.no_cpu) else (None, None, None)
+    tU = torch.from_numpy(np.asfortranarray(U).T.copy()).to(dev).t()
+    tV = torch.from_numpy(np.asfortranarray(V).T.copy()).to(dev).t()
+    tS = torch.from_numpy(S.copy()).to(dev)
+    ta = [torch.from_numpy(a).to(dev) for a, _ in ab]
+    tb = [torch.from_numpy(b).to(dev) for _, b in ab]
+    stream = torch.cuda.Stream(device=dev)
+    h = sv.Handle(local, stream=stream)
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            h.update(tU, tS, tV, ta[i], tb[i], eps=args.eps, mode=mode, check=False)
+        rc = h.sync()
+        if rc != 0:
+            raise SystemExit("warm-up update failed: %s" % sv.error_string(rc))
+        h.timing(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        launches0 = h.launch_count()
+        clocks = ClockSampler(local)
+        clocks.start()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for i in range(args.steps):
+            j = args.warmup + i
+            h.update(tU, tS, tV, ta[j], tb[j], eps=args.eps, mode=mode, check=False)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+        launches = h.launch_count() - launches0
+        rc = h.sync()
+        if rc != 0:
+            raise SystemExit("timed update failed: %s" % sv.error_string(rc))
+        stages = h.timing_read()
+        h.timing(False)
+    lat = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)])
+    total_ms = float(ev[0].elapsed_time(ev[-1]))
+    # timing stage records add a little launch overhead; they are inside the timed region
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * args.steps / (total_ms / 1e3)
+
+    # dominant product stage -> roofline
+    prod = {k: v for k, v in stages.items() if k in ("p2m", "m2l", "out")}
+    dom = max(prod, key=lambda k: prod[k][0])
+    dom_ms, dom_cnt, dom_fl = prod[dom]
+    achieved = (dom_fl / max(dom_cnt, 1)) / ((dom_ms / max(dom_cnt, 1)) / 1e3) / 1e12
+    roofline = {"kernel": "k_gemm_f64<%s>" % dom.upper(), "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": None,
+                "peak_source": "measured DFMA throughput (FP64 pipe), not in MEASURED_PEAKS.json"}
+    stage_ms = {k: round(v[0] / args.steps, 3) for k, v in stages.items()}
+
+    # end-to-end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        pU = torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
+        pV = torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
+        pS = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        pa = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        pb = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        # column-major views of the pinned buffers
+        pUf = pU.T
+        pVf = pV.T
+        pUf[...] = tU.cpu().numpy()
+        pVf[...] = tV.cpu().numpy()
+        pS[...] = tS.cpu().numpy()
+        times = []
+        for i in range(args.e2e_steps):
+            pa[...] = ab[i][0]
+            pb[...] = ab[i][1]
+            t0 = time.perf_counter()
+            h.update_host(pUf, pS, pVf, pa, pb, eps=args.eps, mode=mode)
+            times.append(time.perf_counter() - t0)
+        h2d = 8 * (2 * n * n + 3 * n)
+        d2h = 8 * (2 * n * n + n)
+        e2e = {"value": ws / float(np.mean(times)), "unit": "updates/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        full, spent, desc = oracle_sample(U_h, S_h, V_h, ab[0][0], ab[0][1], args.cpu_cols)
+        cpu = {"value": 1.0 / full, "unit": "updates/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": desc + "; %.1f s of CPU time spent" % spent}
+
+    if rank == 0:
+        line = {"metric": "rank-1 SVD updates/s at n=8192", "value": value, "unit": "updates/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if mode == 0 else args.mode, "data": "synthetic",
+                "config": {"workload": "square n=%d, Haar U/V, sigma log-uniform [1e-4,1], chained "
+                                       "N(0,1) rank-one updates" % n,
+                           "n": n, "mode": args.mode, "eps": args.eps,
+                           "l2": "inputs larger than L2 (U, V 512 MiB each)",
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "stage_ms_per_update": stage_ms,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

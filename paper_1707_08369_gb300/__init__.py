@@ -1,0 +1,215 @@
+"""GB300 rank-one SVD update (Gandhi & Rajgor, arXiv 1707.08369, Alg. 6.1).
+
+Thin Python binding over the C ABI in include/svdup.h (libsvdup.so): it only
+marshals arguments.  Every step of the update runs in the library's CUDA
+kernels; PyTorch is used for device memory and streams.  There is no CPU
+fallback: if the shared library is missing or fails to load, every call raises.
+
+Names follow the C ABI: create / destroy / sync / update / update_host /
+rank_one_eig / secular / cauchy_product / error_string / launch_count.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsvdup.so")
+
+OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE, ECUDA, EORDER = 0, 1, 2, 3, 4, 5, 6
+FP64, MIXED_BF16X3, MIXED_FP16X2 = 0, 1, 2
+DENSE, REFINE = 0x100, 0x200
+
+_lib = None
+
+
+class SvdupError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (code %d)" % (where, error_string(code) if _lib else "?", code))
+
+
+def load(path: str = LIB_PATH):
+    """Load libsvdup.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libsvdup.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.svdup_create.argtypes = [ctypes.POINTER(P), I, P, ctypes.c_uint]
+    lib.svdup_destroy.argtypes = [P]
+    lib.svdup_sync.argtypes = [P]
+    lib.svdup_error_string.argtypes = [I]
+    lib.svdup_error_string.restype = ctypes.c_char_p
+    lib.svdup_launch_count.argtypes = [P]
+    lib.svdup_launch_count.restype = ctypes.c_longlong
+    lib.svdup_timing.argtypes = [P, I]
+    lib.svdup_timing_read.argtypes = [P, P, P, P, I]
+    lib.svdup_update.argtypes = [P, I, I, P, I, P, P, I, P, P, D, I]
+    lib.svdup_update_host.argtypes = [P, I, I, P, I, P, P, I, P, P, D, I]
+    lib.svdup_rank_one_eig.argtypes = [P, I, P, P, D, P, P, P, P, P, P, P, P]
+    lib.svdup_secular.argtypes = [P, I, P, P, D, P, P]
+    lib.svdup_cauchy_product.argtypes = [P, I, I, P, I, P, P, D, P, I, P, D, I]
+    _lib = lib
+    return lib
+
+
+def error_string(code: int) -> str:
+    return load().svdup_error_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise SvdupError(code, where)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_f64(t, name, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("%s must be a float64 CUDA tensor" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements" % (name, numel))
+    return t
+
+
+def _colmajor_ld(t, rows, cols, name):
+    """Leading dimension of a column-major (Fortran-ordered) 2-D tensor."""
+    if t.dim() != 2 or t.shape[0] != rows or t.shape[1] != cols:
+        raise ValueError("%s must be %d x %d" % (name, rows, cols))
+    if t.stride(0) != 1:
+        raise ValueError("%s must be column-major (stride(0) == 1)" % name)
+    return max(t.stride(1), rows)
+
+
+class Handle:
+    """A library handle bound to a device and a CUDA stream (torch's current stream
+    by default)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib.svdup_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream.cuda_stream), 0),
+               "svdup_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            load().svdup_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self) -> int:
+        return int(load().svdup_sync(self._h))
+
+    def launch_count(self) -> int:
+        return int(load().svdup_launch_count(self._h))
+
+    STAGES = ("gemv", "solve", "sign", "gather", "setup", "p2m", "m2l", "out")
+
+    def timing(self, enable: bool = True):
+        _check(load().svdup_timing(self._h, 1 if enable else 0), "svdup_timing")
+
+    def timing_read(self):
+        """{stage: (ms, intervals, flops)} since timing was enabled."""
+        n = len(self.STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        fl = (ctypes.c_double * n)()
+        _check(load().svdup_timing_read(self._h, ms, cnt, fl, n), "svdup_timing_read")
+        return {s: (ms[i], cnt[i], fl[i]) for i, s in enumerate(self.STAGES)}
+
+    def update(self, U, S, V, a, b, eps: float = 1e-12, mode: int = FP64, check: bool = True):
+        """In-place Alg. 6.1 on device tensors: U (m x m) and V (n x n) column-major
+        float64, S (m, descending), a (m), b (n).  Queues the work; with check=True
+        waits and raises on a device error."""
+        m, n = S.numel(), b.numel()
+        for t, nm in ((U, "U"), (S, "S"), (V, "V"), (a, "a"), (b, "b")):
+            _dev_f64(t, nm)
+        ldu = _colmajor_ld(U, m, m, "U")
+        ldv = _colmajor_ld(V, n, n, "V")
+        _check(load().svdup_update(self._h, m, n, _ptr(U), ldu, _ptr(S), _ptr(V), ldv, _ptr(a),
+                                   _ptr(b), float(eps), int(mode)), "svdup_update")
+        if check:
+            _check(self.sync(), "svdup_update (device)")
+
+    def update_host(self, U, S, V, a, b, eps: float = 1e-12, mode: int = FP64):
+        """The same update on host numpy arrays (copied in and out inside the call)."""
+        import numpy as np
+        for t, nm in ((U, "U"), (S, "S"), (V, "V"), (a, "a"), (b, "b")):
+            if not isinstance(t, np.ndarray) or t.dtype != np.float64:
+                raise TypeError("%s must be a float64 numpy array" % nm)
+        if not (U.flags.f_contiguous and V.flags.f_contiguous):
+            raise ValueError("U and V must be column-major (Fortran order)")
+        m, n = S.size, b.size
+        p = lambda x: ctypes.c_void_p(x.ctypes.data)
+        _check(load().svdup_update_host(self._h, m, n, p(U), m, p(S), p(V), n, p(a), p(b),
+                                        float(eps), int(mode)), "svdup_update_host")
+
+    def rank_one_eig(self, d, z, rho: float):
+        """Compact eigen-system of diag(d) + rho z z^T (device tensors).  Returns a dict
+        with k, idx, dk, org, tau, zhat, inv_norm (first k valid) and lam (all N)."""
+        import torch
+        N = d.numel()
+        _dev_f64(d, "d"); _dev_f64(z, "z", N)
+        dev = d.device
+        out = dict(k=torch.zeros(1, dtype=torch.int32, device=dev),
+                   idx=torch.zeros(N, dtype=torch.int32, device=dev),
+                   dk=torch.zeros(N, dtype=torch.float64, device=dev),
+                   org=torch.zeros(N, dtype=torch.int32, device=dev),
+                   tau=torch.zeros(N, dtype=torch.float64, device=dev),
+                   zhat=torch.zeros(N, dtype=torch.float64, device=dev),
+                   inv_norm=torch.zeros(N, dtype=torch.float64, device=dev),
+                   lam=torch.zeros(N, dtype=torch.float64, device=dev))
+        _check(load().svdup_rank_one_eig(self._h, N, _ptr(d), _ptr(z), float(rho), _ptr(out["k"]),
+                                         _ptr(out["idx"]), _ptr(out["dk"]), _ptr(out["org"]),
+                                         _ptr(out["tau"]), _ptr(out["zhat"]), _ptr(out["inv_norm"]),
+                                         _ptr(out["lam"])), "svdup_rank_one_eig")
+        _check(self.sync(), "svdup_rank_one_eig (device)")
+        return out
+
+    def secular(self, d, z, rho: float):
+        """Roots of the secular equation for strictly ascending d and nonzero z."""
+        import torch
+        k = d.numel()
+        _dev_f64(d, "d"); _dev_f64(z, "z", k)
+        org = torch.zeros(k, dtype=torch.int32, device=d.device)
+        tau = torch.zeros(k, dtype=torch.float64, device=d.device)
+        _check(load().svdup_secular(self._h, k, _ptr(d), _ptr(z), float(rho), _ptr(org), _ptr(tau)),
+               "svdup_secular")
+        _check(self.sync(), "svdup_secular (device)")
+        return org, tau
+
+    def cauchy_product(self, X, d, z, rho: float, eps: float = 1e-12, mode: int = FP64):
+        """Y = X Q for diag(d) + rho z z^T = Q diag(lam) Q^T; returns (lam, Y)."""
+        import torch
+        rows, N = X.shape
+        _dev_f64(X, "X"); _dev_f64(d, "d", N); _dev_f64(z, "z", N)
+        ldx = _colmajor_ld(X, rows, N, "X")
+        Y = torch.zeros((N, rows), dtype=torch.float64, device=X.device).t()
+        lam = torch.zeros(N, dtype=torch.float64, device=X.device)
+        _check(load().svdup_cauchy_product(self._h, rows, N, _ptr(X), ldx, _ptr(d), _ptr(z),
+                                           float(rho), _ptr(Y), rows, _ptr(lam), float(eps),
+                                           int(mode)), "svdup_cauchy_product")
+        _check(self.sync(), "svdup_cauchy_product (device)")
+        return lam, Y
+
+
+def colmajor(t):
+    """A column-major copy of a 2-D tensor (what the library expects for matrices)."""
+    return t.t().contiguous().t()

@@ -1,0 +1,622 @@
+// svdup_api.cu -- host side of libsvdup.so: handles, workspace, and the order in which
+// the stages of Alg. 6.1 are queued on the handle's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "svdup_internal.cuh"
+
+namespace svdup {
+
+long long g_launch_count = 0;
+
+}  // namespace svdup
+
+using namespace svdup;
+
+struct TimerRec {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+struct svdup_ctx {
+  int device;
+  cudaStream_t stream;
+  int* status;  // device word
+  char* ws;
+  size_t ws_size;
+  int maxit;
+  // stage timers
+  int timing;
+  TimerRec* recs;
+  int nrec, caprec;
+  TimerRec* pool;  // recycled event pairs
+  int npool, cappool;
+  double ms[SVDUP_NSTAGE];
+  long long cnt[SVDUP_NSTAGE];
+  int open_stage;
+  cudaEvent_t open_ev;
+  double* flops_dev;  // 3 accumulators (P2M, M2L, OUT), device
+};
+
+namespace {
+
+// Bump allocator over the workspace; `base == nullptr` only measures.
+struct Arena {
+  char* base;
+  size_t off;
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+Eig make_eig(Arena& ar, int N) {
+  Eig e;
+  memset(&e, 0, sizeof(e));
+  e.N = N;
+  size_t n = (size_t)(N > 0 ? N : 1);
+  e.rhop = ar.take<double>(1);
+  e.ds = ar.take<double>(n);
+  e.zs = ar.take<double>(n);
+  e.perm = ar.take<int>(n);
+  e.defl = ar.take<int>(n);
+  e.nrot = ar.take<int>(1);
+  e.rj = ar.take<int>(n);
+  e.ri = ar.take<int>(n);
+  e.rc = ar.take<double>(n);
+  e.rs = ar.take<double>(n);
+  e.kp = ar.take<int>(1);
+  e.idx = ar.take<int>(n);
+  e.didx = ar.take<int>(n);
+  e.dk = ar.take<double>(n);
+  e.zk = ar.take<double>(n);
+  e.dc = ar.take<double>(n);
+  e.z2c = ar.take<double>(n);
+  e.org = ar.take<int>(n);
+  e.tau = ar.take<double>(n);
+  e.dorg = ar.take<double>(n);
+  e.orgc = ar.take<int>(n);
+  e.tauc = ar.take<double>(n);
+  e.zhat = ar.take<double>(n);
+  e.inv = ar.take<double>(n);
+  e.lam = ar.take<double>(n);
+  e.rank_root = ar.take<int>(n);
+  e.rank_defl = ar.take<int>(n);
+  e.tol = ar.take<double>(1);
+  return e;
+}
+
+// Expansion order from the accuracy (App. D STEP 1: p = log5(1/eps)), and the leaf
+// size: about 2p points per leaf in the paper (STEP 2); here leaves are wider so the
+// near field stays a few leaves across on graded spectra (relative leaf widths shrink
+// with more leaves) while the far field is a handful of large contractions.
+int expansion_order(double eps) {
+  int p = (int)ceil(log(1.0 / eps) / log(5.0));
+  if (p < 4) p = 4;
+  if (p > 32) p = 32;
+  return p;
+}
+
+int leaf_size(int N) {
+  if (N <= 2048) return 64;
+  return 128;
+}
+
+bool use_dense(int N, int mode) {
+  if (mode & SVDUP_DENSE) return true;
+  return N <= 512;
+}
+
+FmmPlan make_plan(Arena& ar, int N, int rows, double eps) {
+  FmmPlan f;
+  memset(&f, 0, sizeof(f));
+  f.p = expansion_order(eps);
+  f.s = leaf_size(N);
+  f.Lmax = (N + f.s - 1) / f.s;
+  if (f.Lmax < 1) f.Lmax = 1;
+  size_t L = (size_t)f.Lmax;
+  f.L = ar.take<int>(2);
+  f.sbox_c = ar.take<double>(L);
+  f.sbox_r = ar.take<double>(L);
+  f.tbox_c = ar.take<double>(L + 1);
+  f.tbox_r = ar.take<double>(L + 1);
+  f.tj0 = ar.take<int>(L + 1);
+  f.tj1 = ar.take<int>(L + 1);
+  f.nnear = ar.take<int>(L + 1);
+  f.near = ar.take<int>((L + 1) * L);
+  f.S = ar.take<double>(L * f.s * f.p);
+  f.T = ar.take<double>(L * f.p * (L + 1) * f.p);
+  f.Lop = ar.take<double>((L + 1) * f.s * f.p);
+  f.ldphi = rows > 0 ? rows : 1;
+  f.Phi = ar.take<double>((size_t)f.ldphi * L * f.p);
+  f.Psi = ar.take<double>((size_t)f.ldphi * (L + 1) * f.p);
+  return f;
+}
+
+int ensure_ws(svdup_ctx* h, size_t bytes) {
+  if (bytes <= h->ws_size) return SVDUP_OK;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_size = 0;
+  void* p = nullptr;
+  size_t want = bytes + bytes / 8;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    return SVDUP_ENOMEM;
+  }
+  h->ws = (char*)p;
+  h->ws_size = want;
+  return SVDUP_OK;
+}
+
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SVDUP_OK : SVDUP_ECUDA;
+}
+
+int set_device(svdup_ctx* h) {
+  return cudaSetDevice(h->device) == cudaSuccess ? SVDUP_OK : SVDUP_ECUDA;
+}
+
+// The per-update workspace.
+struct UpdateWs {
+  double *p, *q, *ab, *z2p, *z4p, *ysort, *zsec2, *zsec4, *ones, *g1, *g, *yv, *h1, *h, *sign,
+      *work;
+  Eig E1, E2, E3, E4;
+  double *Xs, *W;
+  FmmPlan F;
+};
+
+UpdateWs layout_update(Arena& ar, int m, int n, double eps) {
+  UpdateWs u;
+  u.p = ar.take<double>(m);
+  u.q = ar.take<double>(n);
+  u.ab = ar.take<double>(2);
+  u.z2p = ar.take<double>(m);
+  u.z4p = ar.take<double>(n);
+  u.ysort = ar.take<double>(n);
+  u.zsec2 = ar.take<double>(m);
+  u.zsec4 = ar.take<double>(n);
+  u.ones = ar.take<double>(m);
+  u.g1 = ar.take<double>(m);
+  u.g = ar.take<double>(m);
+  u.yv = ar.take<double>(n);
+  u.h1 = ar.take<double>(n);
+  u.h = ar.take<double>(n);
+  u.sign = ar.take<double>(n);
+  u.work = ar.take<double>(n);
+  u.E1 = make_eig(ar, m);
+  u.E2 = make_eig(ar, m);
+  u.E3 = make_eig(ar, n);
+  u.E4 = make_eig(ar, n);
+  u.Xs = ar.take<double>((size_t)n * n);
+  u.W = ar.take<double>((size_t)n * n);
+  u.F = make_plan(ar, n, n, eps);
+  return u;
+}
+
+// Stage timers: an event pair per timed interval, resolved at svdup_timing_read.
+cudaEvent_t take_event(svdup_ctx* h) {
+  cudaEvent_t e = nullptr;
+  if (h->npool > 0) {
+    TimerRec& r = h->pool[--h->npool];
+    e = r.a;
+    if (r.b) {  // split pairs back into single events
+      if (h->npool + 1 > h->cappool) {
+        h->cappool = h->cappool ? 2 * h->cappool : 64;
+        h->pool = (TimerRec*)realloc(h->pool, h->cappool * sizeof(TimerRec));
+      }
+      h->pool[h->npool++] = TimerRec{-1, r.b, nullptr};
+    }
+    return e;
+  }
+  cudaEventCreate(&e);
+  return e;
+}
+
+void stage_begin(svdup_ctx* h, int stage) {
+  if (!h->timing) return;
+  h->open_stage = stage;
+  h->open_ev = take_event(h);
+  cudaEventRecord(h->open_ev, h->stream);
+}
+
+void stage_end(svdup_ctx* h) {
+  if (!h->timing || h->open_stage < 0) return;
+  cudaEvent_t b = take_event(h);
+  cudaEventRecord(b, h->stream);
+  if (h->nrec + 1 > h->caprec) {
+    h->caprec = h->caprec ? 2 * h->caprec : 256;
+    h->recs = (TimerRec*)realloc(h->recs, h->caprec * sizeof(TimerRec));
+  }
+  h->recs[h->nrec++] = TimerRec{h->open_stage, h->open_ev, b};
+  h->open_stage = -1;
+}
+
+// One solve: deflation, roots, final ordering, zhat; the column norms follow separately
+// (fused with a transposed product when the next solve needs its z).
+void queue_solve(svdup_ctx* h, Eig e) {
+  launch_deflate(h->stream, e, nullptr, h->status);
+  launch_secular(h->stream, e, h->status, h->maxit);
+  launch_merge(h->stream, e);
+  launch_loewner(h->stream, e);
+}
+
+// Y[:, out(q)] = (X Q)[:, q] for the solve e (X rows x N, modified in place by the
+// deflation rotations).  Xs is a rows x N scratch.
+void queue_product(svdup_ctx* h, Eig e, FmmPlan f, int rows, double* X, long long ldx,
+                   double* Xs, OutMap om, int mode) {
+  int dense = use_dense(e.N, mode) ? 1 : 0;
+  stage_begin(h, SVDUP_STAGE_GATHER);
+  launch_rotate_columns(h->stream, e, X, ldx, rows);
+  launch_gather_columns(h->stream, e, X, ldx, rows, Xs, rows, om);
+  stage_end(h);
+  stage_begin(h, SVDUP_STAGE_SETUP);
+  launch_fmm_setup(h->stream, e, f, dense);
+  stage_end(h);
+  if (!dense) {
+    stage_begin(h, SVDUP_STAGE_P2M);
+    launch_product_f64_stage(h->stream, 0, e, f, rows, Xs, rows, om, dense);
+    stage_end(h);
+    stage_begin(h, SVDUP_STAGE_M2L);
+    launch_product_f64_stage(h->stream, 1, e, f, rows, Xs, rows, om, dense);
+    stage_end(h);
+  }
+  stage_begin(h, SVDUP_STAGE_OUT);
+  launch_product_f64_stage(h->stream, 2, e, f, rows, Xs, rows, om, dense);
+  stage_end(h);
+  if (h->timing) launch_flop_count(h->stream, e, f, rows, dense, h->flops_dev);
+}
+
+}  // namespace
+
+extern "C" {
+
+int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
+  (void)flags;
+  if (!out) return SVDUP_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return SVDUP_ECUDA;
+  svdup_ctx* h = (svdup_ctx*)calloc(1, sizeof(svdup_ctx));
+  if (!h) return SVDUP_ENOMEM;
+  h->device = device;
+  h->stream = (cudaStream_t)stream;
+  h->maxit = 64;
+  h->open_stage = -1;
+  const char* mi = getenv("SVDUP_SECULAR_MAXIT");
+  if (mi) h->maxit = atoi(mi);
+  if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess) {
+    free(h);
+    return SVDUP_ENOMEM;
+  }
+  if (cudaMalloc(&h->flops_dev, 3 * sizeof(double)) != cudaSuccess ||
+      cudaMemsetAsync(h->flops_dev, 0, 3 * sizeof(double), h->stream) != cudaSuccess) {
+    cudaFree(h->status);
+    free(h);
+    return SVDUP_ENOMEM;
+  }
+  if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess) {
+    cudaFree(h->status);
+    free(h);
+    return SVDUP_ECUDA;
+  }
+  *out = h;
+  return SVDUP_OK;
+}
+
+int svdup_destroy(svdup_t h) {
+  if (!h) return SVDUP_EINVAL;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->ws) cudaFree(h->ws);
+  cudaFree(h->status);
+  cudaFree(h->flops_dev);
+  for (int i = 0; i < h->nrec; i++) { cudaEventDestroy(h->recs[i].a); cudaEventDestroy(h->recs[i].b); }
+  for (int i = 0; i < h->npool; i++) {
+    cudaEventDestroy(h->pool[i].a);
+    if (h->pool[i].b) cudaEventDestroy(h->pool[i].b);
+  }
+  free(h->recs);
+  free(h->pool);
+  free(h);
+  return SVDUP_OK;
+}
+
+int svdup_timing(svdup_t h, int enable) {
+  if (!h) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
+  // recycle outstanding records
+  for (int i = 0; i < h->nrec; i++) {
+    if (h->npool + 1 > h->cappool) {
+      h->cappool = h->cappool ? 2 * h->cappool : 64;
+      h->pool = (TimerRec*)realloc(h->pool, h->cappool * sizeof(TimerRec));
+    }
+    h->pool[h->npool++] = h->recs[i];
+  }
+  h->nrec = 0;
+  for (int s = 0; s < SVDUP_NSTAGE; s++) { h->ms[s] = 0.0; h->cnt[s] = 0; }
+  h->timing = enable ? 1 : 0;
+  h->open_stage = -1;
+  if (cudaMemsetAsync(h->flops_dev, 0, 3 * sizeof(double), h->stream) != cudaSuccess)
+    return SVDUP_ECUDA;
+  return SVDUP_OK;
+}
+
+int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, int nstage) {
+  if (!h || nstage < 0 || nstage > SVDUP_NSTAGE) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  double fl[3] = {0, 0, 0};
+  if (cudaMemcpyAsync(fl, h->flops_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
+      cudaSuccess)
+    return SVDUP_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
+  for (int i = 0; i < h->nrec; i++) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, h->recs[i].a, h->recs[i].b) != cudaSuccess) return SVDUP_ECUDA;
+    h->ms[h->recs[i].stage] += t;
+    h->cnt[h->recs[i].stage] += 1;
+    if (h->npool + 1 > h->cappool) {
+      h->cappool = h->cappool ? 2 * h->cappool : 64;
+      h->pool = (TimerRec*)realloc(h->pool, h->cappool * sizeof(TimerRec));
+    }
+    h->pool[h->npool++] = h->recs[i];
+  }
+  h->nrec = 0;
+  for (int s = 0; s < nstage; s++) {
+    if (ms) ms[s] = h->ms[s];
+    if (count) count[s] = h->cnt[s];
+    if (flops) {
+      flops[s] = 0.0;
+      if (s == SVDUP_STAGE_P2M) flops[s] = fl[0];
+      if (s == SVDUP_STAGE_M2L) flops[s] = fl[1];
+      if (s == SVDUP_STAGE_OUT) flops[s] = fl[2];
+    }
+  }
+  return SVDUP_OK;
+}
+
+int svdup_sync(svdup_t h) {
+  if (!h) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  int st = 0;
+  if (cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
+      cudaSuccess)
+    return SVDUP_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
+  if (st != 0) {
+    if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess) return SVDUP_ECUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
+  }
+  return st;
+}
+
+const char* svdup_error_string(int code) {
+  switch (code) {
+    case SVDUP_OK: return "ok";
+    case SVDUP_EINVAL: return "invalid argument";
+    case SVDUP_ENOMEM: return "out of device memory for the workspace";
+    case SVDUP_ENOCONV: return "secular root did not converge within the iteration cap";
+    case SVDUP_ENONFINITE: return "non-finite value in the inputs or an intermediate";
+    case SVDUP_ECUDA: return "CUDA runtime error";
+    case SVDUP_EORDER: return "singular values are not in descending order";
+    default: return "unknown error";
+  }
+}
+
+long long svdup_launch_count(svdup_t h) {
+  (void)h;
+  return g_launch_count;
+}
+
+int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double* V, int ldv,
+                 const double* a, const double* b, double eps, int mode) {
+  if (!h || !U || !S || !V || !a || !b) return SVDUP_EINVAL;
+  if (m < 1 || n < m || ldu < m || ldv < n) return SVDUP_EINVAL;
+  if (!(eps > 0.0 && eps < 1.0)) return SVDUP_EINVAL;
+  int prec = mode & SVDUP_MODE_MASK;
+  if (prec != SVDUP_FP64) return SVDUP_EINVAL;  // mixed forms: not in this build yet
+  if (set_device(h)) return SVDUP_ECUDA;
+  Arena meas = {nullptr, 0};
+  layout_update(meas, m, n, eps);
+  int rc = ensure_ws(h, meas.off);
+  if (rc) return rc;
+  Arena ar = {h->ws, 0};
+  UpdateWs u = layout_update(ar, m, n, eps);
+  cudaStream_t st = h->stream;
+
+  // STEP 1 (rewritten): p = U^T a, q = V^T b, alpha, beta
+  stage_begin(h, SVDUP_STAGE_GEMV);
+  launch_gemv_pq(st, m, n, U, ldu, V, ldv, a, b, u.p, u.q, u.ab);
+  stage_end(h);
+  stage_begin(h, SVDUP_STAGE_SOLVE);
+  // STEPs 2, 4: first left solve; its transposed product gives the second left z
+  launch_fill_left(st, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
+  queue_solve(h, u.E1);
+  launch_apply_qt(st, u.E1, u.z2p, u.ysort, u.zsec2);
+  // STEP 5: second left solve
+  launch_fill_second(st, u.E2, u.E1.lam, u.zsec2);
+  queue_solve(h, u.E2);
+  launch_norms(st, u.E2, nullptr, nullptr);
+  // STEPs 3, 6: first right solve
+  launch_fill_right(st, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
+  queue_solve(h, u.E3);
+  launch_apply_qt(st, u.E3, u.z4p, u.ysort, u.zsec4);
+  // STEP 7: second right solve
+  launch_fill_second(st, u.E4, u.E3.lam, u.zsec4);
+  queue_solve(h, u.E4);
+  launch_norms(st, u.E4, nullptr, nullptr);
+  stage_end(h);
+  // sign pairing of right vectors with left vectors (before S is overwritten)
+  stage_begin(h, SVDUP_STAGE_SIGN);
+  launch_fill_ones(st, m, u.ones);
+  launch_apply_q(st, u.E2, u.ones, u.work, u.g1);
+  launch_apply_q(st, u.E1, u.g1, u.work, u.g);
+  launch_sign_combine(st, m, n, S, u.p, u.q, u.g, u.yv);
+  launch_apply_qt(st, u.E3, u.yv, u.ysort, u.h1);
+  launch_apply_qt(st, u.E4, u.h1, u.ysort, u.h);
+  launch_sign_finish(st, m, n, u.h, u.sign);
+  stage_end(h);
+  // products: U -> W -> U (descending), V -> W -> V (descending, signed)
+  OutMap om1 = {u.W, (long long)m, m, 0, nullptr};
+  queue_product(h, u.E1, u.F, m, U, ldu, u.Xs, om1, mode);
+  OutMap om2 = {U, (long long)ldu, m, 1, nullptr};
+  queue_product(h, u.E2, u.F, m, u.W, m, u.Xs, om2, mode);
+  OutMap om3 = {u.W, (long long)n, n, 0, nullptr};
+  queue_product(h, u.E3, u.F, n, V, ldv, u.Xs, om3, mode);
+  OutMap om4 = {V, (long long)ldv, n, 1, u.sign};
+  queue_product(h, u.E4, u.F, n, u.W, n, u.Xs, om4, mode);
+  // STEP 8
+  launch_sqrt_desc(st, m, u.E2.lam, S, h->status);
+  return check_launch();
+}
+
+int svdup_update_host(svdup_t h, int m, int n, double* U, int ldu, double* S, double* V, int ldv,
+                      const double* a, const double* b, double eps, int mode) {
+  if (!h || !U || !S || !V || !a || !b) return SVDUP_EINVAL;
+  if (m < 1 || n < m || ldu < m || ldv < n) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  double *dU = nullptr, *dS = nullptr, *dV = nullptr, *da = nullptr, *db = nullptr;
+  size_t bu = (size_t)m * m * sizeof(double), bv = (size_t)n * n * sizeof(double);
+  int rc = SVDUP_OK;
+  if (cudaMalloc(&dU, bu) != cudaSuccess || cudaMalloc(&dS, m * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dV, bv) != cudaSuccess || cudaMalloc(&da, m * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&db, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    rc = SVDUP_ENOMEM;
+    goto out;
+  }
+  if (cudaMemcpy2DAsync(dU, m * sizeof(double), U, (size_t)ldu * sizeof(double),
+                        m * sizeof(double), m, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(dS, S, m * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess ||
+      cudaMemcpy2DAsync(dV, n * sizeof(double), V, (size_t)ldv * sizeof(double),
+                        n * sizeof(double), n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(da, a, m * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(db, b, n * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess) {
+    rc = SVDUP_ECUDA;
+    goto out;
+  }
+  rc = svdup_update(h, m, n, dU, m, dS, dV, n, da, db, eps, mode);
+  if (rc) goto out;
+  if (cudaMemcpy2DAsync(U, (size_t)ldu * sizeof(double), dU, m * sizeof(double),
+                        m * sizeof(double), m, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(S, dS, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaMemcpy2DAsync(V, (size_t)ldv * sizeof(double), dV, n * sizeof(double),
+                        n * sizeof(double), n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) {
+    rc = SVDUP_ECUDA;
+    goto out;
+  }
+  rc = svdup_sync(h);
+out:
+  cudaStreamSynchronize(h->stream);
+  if (dU) cudaFree(dU);
+  if (dS) cudaFree(dS);
+  if (dV) cudaFree(dV);
+  if (da) cudaFree(da);
+  if (db) cudaFree(db);
+  return rc;
+}
+
+int svdup_rank_one_eig(svdup_t h, int N, const double* d, const double* z, double rho, int* k,
+                       int* idx, double* dk, int* org, double* tau, double* zhat, double* inv_norm,
+                       double* lam) {
+  if (!h || N < 1 || !d || !z || !k || !idx || !dk || !org || !tau || !zhat || !inv_norm || !lam)
+    return SVDUP_EINVAL;
+  if (!(rho != 0.0) || !isfinite(rho)) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  Arena meas = {nullptr, 0};
+  make_eig(meas, N);
+  meas.take<double>(1);
+  int rc = ensure_ws(h, meas.off);
+  if (rc) return rc;
+  Arena ar = {h->ws, 0};
+  Eig e = make_eig(ar, N);
+  double* rhod = ar.take<double>(1);
+  cudaStream_t st = h->stream;
+  if (cudaMemcpyAsync(rhod, &rho, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SVDUP_ECUDA;
+  launch_fill_generic(st, e, d, z, rhod, h->status);
+  queue_solve(h, e);
+  launch_norms(st, e, nullptr, nullptr);
+  cudaMemcpyAsync(k, e.kp, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(idx, e.idx, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(dk, e.dk, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(org, e.org, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(tau, e.tau, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(zhat, e.zhat, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(inv_norm, e.inv, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(lam, e.lam, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return check_launch();
+}
+
+int svdup_secular(svdup_t h, int k, const double* d, const double* z, double rho, int* org,
+                  double* tau) {
+  if (!h || k < 1 || !d || !z || !org || !tau) return SVDUP_EINVAL;
+  if (!(rho != 0.0) || !isfinite(rho)) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  Arena meas = {nullptr, 0};
+  make_eig(meas, k);
+  int rc = ensure_ws(h, meas.off);
+  if (rc) return rc;
+  Arena ar = {h->ws, 0};
+  Eig e = make_eig(ar, k);
+  cudaStream_t st = h->stream;
+  if (cudaMemcpyAsync(e.rhop, &rho, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SVDUP_ECUDA;
+  launch_secular_direct(st, e, k, d, z, h->status, h->maxit);
+  cudaMemcpyAsync(org, e.org, k * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(tau, e.tau, k * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return check_launch();
+}
+
+int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, const double* d,
+                         const double* z, double rho, double* Y, int ldy, double* lam, double eps,
+                         int mode) {
+  if (!h || rows < 1 || N < 1 || !X || !d || !z || !Y || !lam) return SVDUP_EINVAL;
+  if (ldx < rows || ldy < rows || !(eps > 0.0 && eps < 1.0)) return SVDUP_EINVAL;
+  if (!(rho != 0.0) || !isfinite(rho)) return SVDUP_EINVAL;
+  if ((mode & SVDUP_MODE_MASK) != SVDUP_FP64) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  auto lay = [&](Arena& ar, Eig* e, double** Xw, double** Xs, FmmPlan* f, double** rhod) {
+    *e = make_eig(ar, N);
+    *rhod = ar.take<double>(1);
+    *Xw = ar.take<double>((size_t)rows * N);
+    *Xs = ar.take<double>((size_t)rows * N);
+    *f = make_plan(ar, N, rows, eps);
+  };
+  Eig e;
+  double *Xw, *Xs, *rhod;
+  FmmPlan f;
+  Arena meas = {nullptr, 0};
+  lay(meas, &e, &Xw, &Xs, &f, &rhod);
+  int rc = ensure_ws(h, meas.off);
+  if (rc) return rc;
+  Arena ar = {h->ws, 0};
+  lay(ar, &e, &Xw, &Xs, &f, &rhod);
+  cudaStream_t st = h->stream;
+  if (cudaMemcpyAsync(rhod, &rho, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SVDUP_ECUDA;
+  if (cudaMemcpy2DAsync(Xw, (size_t)rows * sizeof(double), X, (size_t)ldx * sizeof(double),
+                        (size_t)rows * sizeof(double), N, cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return SVDUP_ECUDA;
+  launch_fill_generic(st, e, d, z, rhod, h->status);
+  queue_solve(h, e);
+  launch_norms(st, e, nullptr, nullptr);
+  OutMap om = {Y, (long long)ldy, N, 0, nullptr};
+  queue_product(h, e, f, rows, Xw, rows, Xs, om, mode);
+  cudaMemcpyAsync(lam, e.lam, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return check_launch();
+}
+
+}  // extern "C"

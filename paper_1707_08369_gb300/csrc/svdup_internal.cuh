@@ -1,0 +1,165 @@
+// svdup_internal.cuh -- device-side structures and helpers shared by the CUDA
+// sources of libsvdup.so (not part of the public interface).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/svdup.h"
+
+namespace svdup {
+
+// ---------------------------------------------------------------------------
+// Device status word: the first error wins (atomicCAS from 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void latch(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+constexpr double kU = 1.1102230246251565e-16;  // 2^-53, unit roundoff of IEEE double
+
+// 1/x for IEEE double by Newton-Raphson on the reciprocal: an FP32 seed from the
+// hardware reciprocal (__frcp_rn) refined by two FP64 Newton steps r <- r + r(1 - x r),
+// each doubling the number of correct bits (2^-23 -> 2^-46 -> below 2^-53).  Outside
+// the FP32 normal range the seed is unusable and CUDA's division is used instead.
+__device__ __forceinline__ double rcp64(double x) {
+  double ax = fabs(x);
+  if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_prod(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// One symmetric rank-one eigen-problem diag(d) + rho z z^T (RankOneUpdate, Sec. 6.2)
+// in device memory.  N is known on the host; k (the non-deflated count) lives on the
+// device so that nothing waits on the host between stages.
+// ---------------------------------------------------------------------------
+struct Eig {
+  int N;
+  double* rhop;  // rho (1 value, device: it depends on device-computed norms)
+  // sorted (ascending) poles and their z, after deflation rotations
+  double* ds;
+  double* zs;
+  int* perm;  // sorted position -> physical column of the basis X
+  int* defl;  // sorted position -> 1 if deflated
+  // deflation rotations, in application order: positions (rj, ri), cos rc, sin rs
+  int* nrot;
+  int* rj;
+  int* ri;
+  double* rc;
+  double* rs;
+  // non-deflated set
+  int* kp;     // k
+  int* idx;    // k sorted positions
+  int* didx;   // N - k deflated sorted positions
+  double* dk;  // k poles
+  double* zk;  // k z values
+  // the same in the rho > 0 orientation used by the solver: dc ascending, z2c = z^2
+  double* dc;
+  double* z2c;
+  // roots: mu_j = dk[org[j]] + tau[j]; dorg[j] = dk[org[j]]
+  int* org;
+  double* tau;
+  double* dorg;
+  int* orgc;     // roots in the rho > 0 orientation (solver and Loewner step)
+  double* tauc;
+  double* zhat;
+  double* inv;  // 1 / ||c_j||
+  // all N eigenvalues ascending, and where each came from
+  double* lam;
+  int* rank_root;  // root j -> final index
+  int* rank_defl;  // sorted position s (deflated) -> final index, else -1
+  double* tol;     // deflation tolerance (1 value)
+};
+
+// Column mapping of a product's output: physical column of final index q is
+//   out_rev ? (out_n - 1 - q) : q, and the column is scaled by colscale[q] if set.
+struct OutMap {
+  double* Y;
+  long long ldy;
+  int out_n;
+  int out_rev;
+  const double* colscale;  // indexed by final index q, may be null
+};
+
+// FMM (flat Chebyshev far field + direct near field) plan for one product.
+// Source leaf a holds poles [a s, a s + s).  Target leaf b < Ls holds the roots of the
+// same index range except the extreme root (the largest for rho > 0, the smallest for
+// rho < 0, which can lie far outside the poles); target leaf Ls holds that root alone.
+struct FmmPlan {
+  int p;     // expansion order
+  int s;     // leaf size
+  int Lmax;  // upper bound on the number of source leaves (ceil(N / s)); targets Lmax + 1
+  int* L;    // device: [0] source leaves Ls, [1] target leaves Lt
+  double* sbox_c;
+  double* sbox_r;
+  double* tbox_c;
+  double* tbox_r;
+  int* tj0;  // per target leaf: first root
+  int* tj1;  // per target leaf: one past the last root
+  int* nnear;  // per target leaf: number of near source leaves
+  int* near;   // per target leaf b: near source leaves, ascending, at near[b * Lmax + i]
+  double* S;      // P2M operators, [leaf][alpha][t] (s x p col-major): zhat_t u_alpha(x_t)
+  double* T;      // M2L operator, (Lmax p) x ((Lmax+1) p) col-major, zero where not admissible
+  double* Lop;    // L2P operators, [leaf][jl][beta] (p x s col-major): u_beta(y_j) inv_j
+  double* Phi;    // rows x (Lmax p) far-field expansions
+  double* Psi;    // rows x ((Lmax+1) p) local expansions
+  long long ldphi;
+};
+
+// Host-side launchers (defined in svdup_solve.cu / svdup_product.cu).  Each queues
+// its kernels on `st` and adds to the launch counter.
+void launch_gemv_pq(cudaStream_t st, int m, int n, const double* U, long long ldu, const double* V,
+                    long long ldv, const double* a, const double* b, double* p, double* q,
+                    double* ab);
+void launch_fill_left(cudaStream_t st, Eig e, int m, const double* S, const double* p,
+                      const double* q, const double* ab, double* z2p, double* rho2, int* status);
+void launch_fill_right(cudaStream_t st, Eig e, int m, int n, const double* S, const double* p,
+                       const double* q, const double* ab, double* z4p, double* rho4, int* status);
+void launch_fill_second(cudaStream_t st, Eig e, const double* lam_prev, const double* zsec);
+void launch_fill_generic(cudaStream_t st, Eig e, const double* d, const double* z,
+                         const double* rho, int* status);
+void launch_deflate(cudaStream_t st, Eig e, double* yvec, int* status);
+void launch_secular(cudaStream_t st, Eig e, int* status, int maxit);
+void launch_secular_direct(cudaStream_t st, Eig e, int k, const double* d, const double* z,
+                           int* status, int maxit);
+void launch_merge(cudaStream_t st, Eig e);
+void launch_loewner(cudaStream_t st, Eig e);
+void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final);
+void launch_apply_qt(cudaStream_t st, Eig e, const double* xphys, double* work, double* out_final);
+void launch_apply_q(cudaStream_t st, Eig e, const double* xfinal, double* work, double* yphys);
+void launch_sign_combine(cudaStream_t st, int m, int n, const double* S, const double* p,
+                         const double* q, const double* g, double* y);
+void launch_sign_finish(cudaStream_t st, int m, int n, const double* h, double* sign);
+void launch_fill_ones(cudaStream_t st, int n, double* w);
+void launch_sqrt_desc(cudaStream_t st, int m, const double* lam, double* S, int* status);
+
+void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows);
+void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
+                           double* Xs, long long ldxs, OutMap om);
+void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense);
+// adds the useful flops of one product's P2M, M2L and output stages to acc[0..2]
+void launch_flop_count(cudaStream_t st, Eig e, FmmPlan f, int rows, int dense, double* acc);
+// stage 0 = P2M, 1 = M2L, 2 = L2P + near field (dense: the whole product)
+void launch_product_f64_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, int rows,
+                              const double* Xs, long long ldxs, OutMap om, int dense);
+
+}  // namespace svdup

@@ -1,0 +1,455 @@
+// svdup_product.cu -- the product X * Ctilde (RankOneUpdate STEPs 3-7, Sec. 6.2;
+// Eq. U1CTrummers / UCTildeProduct) in FP64:
+//   Ctilde_tj = zhat_t / (d_t - mu_j) * (1 / ||c_j||)
+// evaluated for all rows of X at once by a Chebyshev far-field / direct near-field
+// split of the Cauchy matrix (Sec. 5 and App. D, Dutt-Gu-Rokhlin), or densely.
+//
+// Far field (App. D, read with a flat, single-level partition): the k sorted poles are
+// cut into leaves of s consecutive poles, and target leaf b holds roots [b s, b s + s)
+// (roots interlace the poles).  For a source leaf a and target leaf b that are well
+// separated, 1/(x - y) is interpolated in both variables on p Chebyshev nodes
+// t_alpha = cos((2 alpha - 1) pi / (2p)) (App. D STEP 3) with the Lagrange basis
+// u_alpha (STEP 4):
+//     1/(x - y) ~= sum_alpha sum_beta u_alpha(x^) [1 / (xbar_alpha - ybar_beta)] u_beta(y^),
+// which turns the product into three GEMMs over all rows:
+//     Phi = X_leaf * S_leaf           (P2M, far-field expansions, STEP 5)
+//     Psi = Phi * T                   (M2L, expansions translated to targets, STEP 8)
+//     Y   = Psi_leaf * L_leaf + X_near * C_near    (L2P, STEP 9, and P2P, STEP 10)
+// The near-field block C_near is generated on the fly from the offsets (never stored).
+// Separation: leaves a, b are admissible when |a - b| >= 2 and the gap between their
+// intervals is at least max(r_a, r_b); the near range of b is the smallest run of
+// source leaves containing b-1..b+1 and every non-admissible leaf.
+#include <cuda_runtime.h>
+
+#include "svdup_internal.cuh"
+
+namespace svdup {
+
+extern long long g_launch_count;
+#define SVDUP_COUNT_LAUNCH() (++g_launch_count)
+
+// ---------------------------------------------------------------------------
+// Deflation rotations applied to the columns of X (in place): X <- X G_1^T ... G_r^T,
+// i.e. each row of X transforms like z^T.  One thread per row.
+// ---------------------------------------------------------------------------
+__global__ void k_rotate_columns(Eig e, double* X, long long ldx, int rows) {
+  const int nr = e.nrot[0];
+  if (nr == 0) return;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  for (int i = 0; i < nr; i++) {
+    long long ca = e.perm[e.rj[i]], cb = e.perm[e.ri[i]];
+    double c = e.rc[i], sn = e.rs[i];
+    double xa = X[r + ca * ldx], xb = X[r + cb * ldx];
+    X[r + ca * ldx] = c * xa - sn * xb;
+    X[r + cb * ldx] = sn * xa + c * xb;
+  }
+}
+
+void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows) {
+  k_rotate_columns<<<(rows + 63) / 64, 64, 0, st>>>(e, X, ldx, rows);
+  SVDUP_COUNT_LAUNCH();
+}
+
+__device__ __forceinline__ long long out_col(const OutMap& om, int q) {
+  return om.out_rev ? (long long)(om.out_n - 1 - q) : (long long)q;
+}
+
+// Non-deflated columns gathered into sorted order (Xs[:, t] = X[:, perm[idx[t]]]);
+// deflated columns are eigenvectors already and go straight to their output column.
+// One block per column.
+__global__ void k_gather_columns(Eig e, const double* __restrict__ X, long long ldx, int rows,
+                                 double* Xs, long long ldxs, OutMap om) {
+  const int k = e.kp[0];
+  const int c = blockIdx.x;
+  if (c < k) {
+    const double* src = X + (long long)e.perm[e.idx[c]] * ldx;
+    double* dst = Xs + (long long)c * ldxs;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = src[r];
+  } else if (c < e.N) {
+    int s = e.didx[c - k];
+    int q = e.rank_defl[s];
+    double sc = om.colscale ? om.colscale[q] : 1.0;
+    const double* src = X + (long long)e.perm[s] * ldx;
+    double* dst = om.Y + out_col(om, q) * om.ldy;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = sc * src[r];
+  }
+}
+
+void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
+                           double* Xs, long long ldxs, OutMap om) {
+  k_gather_columns<<<e.N, 256, 0, st>>>(e, X, ldx, rows, Xs, ldxs, om);
+  SVDUP_COUNT_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// FMM set-up: leaves, boxes, near ranges, and the operator matrices.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cheb_node(int alpha, int p) {
+  return cospi((2.0 * alpha + 1.0) / (2.0 * p));  // alpha = 0..p-1  (App. D Eq. Define_ti)
+}
+
+// Lagrange basis u_alpha(x) on the p Chebyshev nodes (App. D Eq. Define_uj).
+__device__ double lagrange(int alpha, int p, double x) {
+  double ta = cheb_node(alpha, p);
+  double v = 1.0;
+  for (int b = 0; b < p; b++) {
+    if (b == alpha) continue;
+    double tb = cheb_node(b, p);
+    v *= (x - tb) / (ta - tb);
+  }
+  return v;
+}
+
+// Half-width of a box [lo, hi]; a (near-)single-point box gets a small positive width
+// relative to its position so that points map to finite coordinates near 0.
+__device__ __forceinline__ double box_radius(double lo, double hi) {
+  double r = 0.5 * (hi - lo);
+  double floor_r = 1e-6 * fmax(fabs(lo), fabs(hi));
+  return fmax(fmax(r, floor_r), 1e-300);
+}
+
+// Box coordinate in [-1, 1] (clamped: rounding can put a point a few ulps outside).
+__device__ __forceinline__ double box_coord(double off, double r) {
+  return fmin(1.0, fmax(-1.0, off / r));
+}
+
+// Leaves and boxes.  Sources: leaf a = poles [a s, a s + s).  Targets: see FmmPlan.
+// Dense mode: one source leaf with every pole, one target leaf with every root.
+__global__ void k_fmm_boxes(Eig e, FmmPlan f, int dense) {
+  const int k = e.kp[0];
+  const double rho = e.rhop[0];
+  int Ls, Lt;
+  if (k == 0) { Ls = 0; Lt = 0; }
+  else if (dense) { Ls = 1; Lt = 1; }
+  else { Ls = (k + f.s - 1) / f.s; Lt = Ls + 1; }
+  if (blockIdx.x == 0 && threadIdx.x == 0) { f.L[0] = Ls; f.L[1] = Lt; }
+  const int s = dense ? max(k, 1) : f.s;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < Lt; a += gridDim.x * blockDim.x) {
+    if (a < Ls) {
+      int t0 = a * s, t1 = min(k, t0 + s) - 1;
+      double lo = e.dk[t0], hi = e.dk[t1];
+      f.sbox_c[a] = 0.5 * (lo + hi);
+      f.sbox_r[a] = box_radius(lo, hi);
+    }
+    int j0, j1;
+    if (dense) { j0 = 0; j1 = k; }
+    else if (a < Ls) {
+      int lo = rho > 0.0 ? 0 : 1, hi = rho > 0.0 ? k - 1 : k;
+      j0 = max(a * s, lo);
+      j1 = min(a * s + s, hi);
+      if (j1 < j0) j1 = j0;
+    } else {
+      j0 = rho > 0.0 ? k - 1 : 0;
+      j1 = j0 + 1;
+    }
+    f.tj0[a] = j0;
+    f.tj1[a] = j1;
+    if (j1 > j0) {
+      double lo = e.dorg[j0] + e.tau[j0], hi = e.dorg[j1 - 1] + e.tau[j1 - 1];
+      f.tbox_c[a] = 0.5 * (lo + hi);
+      f.tbox_r[a] = box_radius(lo, hi);
+    } else {
+      f.tbox_c[a] = 0.0;
+      f.tbox_r[a] = 1.0;
+    }
+  }
+}
+
+// Near list of target leaf b: the source leaves b-1..b+1 (for b < Ls) and every source
+// leaf a not admissible with b, i.e. with |c_a - c_b| - r_a - r_b < max(r_a, r_b).
+// Everything else is far field.
+__global__ void k_fmm_near(Eig e, FmmPlan f, int dense) {
+  const int Ls = f.L[0], Lt = f.L[1];
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < Lt; b += gridDim.x * blockDim.x) {
+    int* lst = f.near + (long long)b * f.Lmax;
+    if (dense) { lst[0] = 0; f.nnear[b] = 1; continue; }
+    int cnt = 0;
+    const bool has = f.tj1[b] > f.tj0[b];
+    const double cb = f.tbox_c[b], rb = f.tbox_r[b];
+    for (int a = 0; a < Ls; a++) {
+      bool nr = (b < Ls && a >= b - 1 && a <= b + 1);
+      if (!nr && has) {
+        double ca = f.sbox_c[a], ra = f.sbox_r[a];
+        double gap = fabs(ca - cb) - ra - rb;
+        nr = !(gap >= fmax(ra, rb));
+      }
+      if (nr) lst[cnt++] = a;
+    }
+    f.nnear[b] = cnt;
+  }
+}
+
+__device__ __forceinline__ bool is_near(const FmmPlan& f, int b, int a) {
+  const int* lst = f.near + (long long)b * f.Lmax;
+  const int n = f.nnear[b];
+  for (int i = 0; i < n; i++) {
+    if (lst[i] == a) return true;
+    if (lst[i] > a) return false;
+  }
+  return false;
+}
+
+// P2M operator of source leaf a: S[a][alpha][tl] = zhat_t u_alpha((d_t - c_a) / r_a)
+// (App. D STEP 5 with the far-field variable mapped to [-1, 1]).
+__global__ void k_fmm_S(Eig e, FmmPlan f) {
+  const int k = e.kp[0], L = f.L[0], p = f.p, s = f.s;
+  long long total = (long long)L * s * p;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    int a = (int)(x / ((long long)s * p));
+    int rem = (int)(x - (long long)a * s * p);
+    int alpha = rem / s, tl = rem - alpha * s;
+    int t = a * s + tl;
+    double v = 0.0;
+    if (t < k) v = e.zhat[t] * lagrange(alpha, p, box_coord(e.dk[t] - f.sbox_c[a], f.sbox_r[a]));
+    f.S[x] = v;
+  }
+}
+
+// M2L operator: T[(a, alpha), (b, beta)] = 1 / (xbar_{a,alpha} - ybar_{b,beta}) for
+// admissible pairs, 0 otherwise (App. D STEP 8, with the kernel evaluated at the two
+// boxes' Chebyshev nodes).  Col-major with leading dimension Lmax p.
+__global__ void k_fmm_T(FmmPlan f) {
+  const int Ls = f.L[0], Lt = f.L[1], p = f.p;
+  const long long ldT = (long long)f.Lmax * p;
+  const long long nr = (long long)Ls * p, nc = (long long)Lt * p;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nr * nc;
+       x += (long long)gridDim.x * blockDim.x) {
+    int col = (int)(x / nr), row = (int)(x - (long long)col * nr);
+    int a = row / p, alpha = row - a * p;
+    int b = col / p, beta = col - b * p;
+    double v = 0.0;
+    if (!is_near(f, b, a)) {
+      double xa = (f.sbox_c[a] - f.tbox_c[b]) + f.sbox_r[a] * cheb_node(alpha, p) -
+                  f.tbox_r[b] * cheb_node(beta, p);
+      v = 1.0 / xa;
+    }
+    f.T[row + col * ldT] = v;
+  }
+}
+
+// L2P operator of target leaf b: Lop[b][jl][beta] = u_beta((mu_j - c_b) / r_b) inv_j
+// (App. D STEP 9), j = tj0[b] + jl.
+__global__ void k_fmm_L(Eig e, FmmPlan f) {
+  const int Lt = f.L[1], p = f.p, s = f.s;
+  long long total = (long long)Lt * s * p;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(x / ((long long)s * p));
+    int rem = (int)(x - (long long)b * s * p);
+    int jl = rem / p, beta = rem - jl * p;
+    int j = f.tj0[b] + jl;
+    double v = 0.0;
+    if (j < f.tj1[b]) {
+      double y = box_coord((e.dorg[j] - f.tbox_c[b]) + e.tau[j], f.tbox_r[b]);
+      v = lagrange(beta, p, y) * e.inv[j];
+    }
+    f.Lop[x] = v;
+  }
+}
+
+void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense) {
+  k_fmm_boxes<<<(f.Lmax + 128) / 128, 128, 0, st>>>(e, f, dense);
+  SVDUP_COUNT_LAUNCH();
+  k_fmm_near<<<(f.Lmax + 128) / 128, 128, 0, st>>>(e, f, dense);
+  SVDUP_COUNT_LAUNCH();
+  if (dense) return;
+  long long sp = (long long)(f.Lmax + 1) * f.s * f.p;
+  int blocks = (int)((sp + 255) / 256);
+  k_fmm_S<<<blocks, 256, 0, st>>>(e, f);
+  SVDUP_COUNT_LAUNCH();
+  k_fmm_L<<<blocks, 256, 0, st>>>(e, f);
+  SVDUP_COUNT_LAUNCH();
+  long long nt = (long long)f.Lmax * f.p * (long long)(f.Lmax + 1) * f.p;
+  int tb = (int)((nt + 255) / 256);
+  k_fmm_T<<<tb, 256, 0, st>>>(f);
+  SVDUP_COUNT_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GEMM tiles for the three stages.  Tile 64 rows x 32 columns, K in steps of 16,
+// 128 threads, 4 x 4 outputs per thread.  (FP64 on this part issues roughly two DFMA
+// per SM per clock, so the tile only has to keep the FP64 pipe fed.)
+// ---------------------------------------------------------------------------
+constexpr int BM = 64, BN = 32, BK = 16;
+
+enum { ST_P2M = 0, ST_M2L = 1, ST_OUT = 2 };
+
+template <int STAGE>
+__global__ void __launch_bounds__(128) k_gemm_f64(Eig e, FmmPlan f, int rows,
+                                                  const double* __restrict__ Xs, long long ldxs,
+                                                  OutMap om, int dense) {
+  __shared__ double As[BK][BM];
+  __shared__ double Bs[BK][BN + 1];
+  const int k = e.kp[0];
+  const int Ls = f.L[0], Lt = f.L[1];
+  const int p = f.p;
+  const int s = dense ? max(k, 1) : f.s;
+  const int leaf = blockIdx.y;
+  if (leaf >= (STAGE == ST_P2M ? Ls : Lt)) return;
+  const int r0 = blockIdx.x * BM;
+  const int c0 = blockIdx.z * BN;  // column chunk within the block's output range
+  int ncols, j0 = 0;
+  if (STAGE == ST_P2M || STAGE == ST_M2L) ncols = p;
+  else { j0 = f.tj0[leaf]; ncols = f.tj1[leaf] - j0; }
+  if (c0 >= ncols) return;
+  const int tid = threadIdx.x;
+  const int tx = tid & 7, ty = tid >> 3;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+  // K segments.  P2M: the leaf's poles.  M2L: every source expansion (T is zero on
+  // near pairs).  Output: the leaf's local expansion (L2P), then each near source leaf.
+  int nseg;
+  if (STAGE == ST_P2M || STAGE == ST_M2L) nseg = 1;
+  else nseg = dense ? 2 : 1 + f.nnear[leaf];
+  for (int sg = 0; sg < nseg; sg++) {
+    int g0, g1;
+    if (STAGE == ST_P2M) { g0 = leaf * f.s; g1 = min(k, g0 + f.s); }
+    else if (STAGE == ST_M2L) { g0 = 0; g1 = Ls * p; }
+    else if (dense) { g0 = 0; g1 = (sg == 0) ? 0 : k; }
+    else if (sg == 0) { g0 = 0; g1 = p; }
+    else {
+      int a = f.near[(long long)leaf * f.Lmax + sg - 1];
+      g0 = a * f.s;
+      g1 = min(k, g0 + f.s);
+    }
+    for (int kb = g0; kb < g1; kb += BK) {
+      // A tile: BK columns x BM rows
+      for (int x = tid; x < BK * BM; x += 128) {
+        int kk = x / BM, r = x - kk * BM;
+        int g = kb + kk;
+        double v = 0.0;
+        if (g < g1 && r0 + r < rows) {
+          const double* col;
+          if (STAGE == ST_P2M) col = Xs + (long long)g * ldxs;
+          else if (STAGE == ST_M2L) col = f.Phi + (long long)g * f.ldphi;
+          else col = (sg == 0) ? f.Psi + (long long)(leaf * p + g) * f.ldphi
+                               : Xs + (long long)g * ldxs;
+          v = col[r0 + r];
+        }
+        As[kk][r] = v;
+      }
+      // B tile: BK x BN
+      for (int x = tid; x < BK * BN; x += 128) {
+        int kk = x / BN, c = x - kk * BN;
+        int g = kb + kk;
+        int cc = c0 + c;
+        double v = 0.0;
+        if (g < g1 && cc < ncols) {
+          if (STAGE == ST_P2M) {
+            v = f.S[(long long)leaf * f.s * p + (long long)cc * f.s + (g - leaf * f.s)];
+          } else if (STAGE == ST_M2L) {
+            v = f.T[(long long)g + (long long)(leaf * p + cc) * ((long long)f.Lmax * p)];
+          } else if (sg == 0) {
+            v = f.Lop[(long long)leaf * f.s * p + (long long)cc * p + g];
+          } else {
+            int j = j0 + cc;
+            double del = (e.dk[g] - e.dorg[j]) - e.tau[j];
+            v = e.zhat[g] * e.inv[j] * rcp64(del);
+          }
+        }
+        Bs[kk][c] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; kk++) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+          for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  // epilogue
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    int cc = c0 + tx * 4 + j;
+    if (cc >= ncols) continue;
+    double* col;
+    double sc = 1.0;
+    if (STAGE == ST_P2M) col = f.Phi + (long long)(leaf * p + cc) * f.ldphi;
+    else if (STAGE == ST_M2L) col = f.Psi + (long long)(leaf * p + cc) * f.ldphi;
+    else {
+      int jj = j0 + cc;
+      int q = e.rank_root[jj];
+      if (om.colscale) sc = om.colscale[q];
+      col = om.Y + out_col(om, q) * om.ldy;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      int r = r0 + ty * 4 + i;
+      if (r < rows) col[r] = sc * acc[i][j];
+    }
+  }
+}
+
+// Useful flops of the three product stages (2 per multiply-add), from the device-side
+// plan: P2M 2 rows k p; M2L 2 rows p^2 per admissible leaf pair; output 2 rows s_b
+// (p + near sources of b) per target leaf (dense: 2 rows k^2).
+__global__ void k_flop_count(Eig e, FmmPlan f, int rows, int dense, double* acc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = e.kp[0];
+  const double R = (double)rows;
+  if (dense) {
+    acc[2] += 2.0 * R * (double)k * (double)k;
+    return;
+  }
+  const int Ls = f.L[0], Lt = f.L[1], p = f.p, s = f.s;
+  double p2m = 2.0 * R * (double)k * p, m2l = 0.0, out = 0.0;
+  for (int b = 0; b < Lt; b++) {
+    int nb = f.tj1[b] - f.tj0[b];
+    if (nb <= 0) continue;
+    int near_src = 0;
+    for (int i = 0; i < f.nnear[b]; i++) {
+      int a = f.near[(long long)b * f.Lmax + i];
+      near_src += min(k, a * s + s) - a * s;
+    }
+    m2l += 2.0 * R * (double)p * p * (double)(Ls - f.nnear[b]);
+    out += 2.0 * R * (double)nb * (double)(p + near_src);
+  }
+  acc[0] += p2m;
+  acc[1] += m2l;
+  acc[2] += out;
+}
+
+void launch_flop_count(cudaStream_t st, Eig e, FmmPlan f, int rows, int dense, double* acc) {
+  k_flop_count<<<1, 32, 0, st>>>(e, f, rows, dense, acc);
+  SVDUP_COUNT_LAUNCH();
+}
+
+void launch_product_f64_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, int rows,
+                              const double* Xs, long long ldxs, OutMap om, int dense) {
+  int rt = (rows + BM - 1) / BM;
+  if (dense) {
+    if (stage != 2) return;
+    dim3 g3(rt, 1, (e.N + BN - 1) / BN);
+    k_gemm_f64<ST_OUT><<<g3, 128, 0, st>>>(e, f, rows, Xs, ldxs, om, dense);
+    SVDUP_COUNT_LAUNCH();
+    return;
+  }
+  int pc = (f.p + BN - 1) / BN;
+  if (stage == 0) {
+    dim3 g1(rt, f.Lmax, pc);
+    k_gemm_f64<ST_P2M><<<g1, 128, 0, st>>>(e, f, rows, Xs, ldxs, om, dense);
+  } else if (stage == 1) {
+    dim3 g1(rt, f.Lmax + 1, pc);
+    k_gemm_f64<ST_M2L><<<g1, 128, 0, st>>>(e, f, rows, Xs, ldxs, om, dense);
+  } else {
+    dim3 g3(rt, f.Lmax + 1, (f.s + BN - 1) / BN);
+    k_gemm_f64<ST_OUT><<<g3, 128, 0, st>>>(e, f, rows, Xs, ldxs, om, dense);
+  }
+  SVDUP_COUNT_LAUNCH();
+}
+
+}  // namespace svdup

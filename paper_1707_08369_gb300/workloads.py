@@ -36,19 +36,27 @@ def haar(n: int, g: np.random.Generator, device=None) -> np.ndarray:
     torch CUDA device) the QR runs there; the Gaussian is always drawn by numpy."""
     G = g.standard_normal((n, n))
     if device is None:
-        Q, R = np.linalg.qr(G)
-        s = np.sign(np.diag(R))
-        s[s == 0] = 1.0
-        return np.asfortranarray(Q * s)
+        return haar_from_gaussian(G)
     import torch
     Gt = torch.from_numpy(G).to(device)
-    Q, R = torch.linalg.qr(Gt)
+    try:
+        Q, R = torch.linalg.qr(Gt)
+    except RuntimeError:  # no device linear-algebra library in this torch build
+        del Gt
+        return haar_from_gaussian(G)
     s = torch.sign(torch.diagonal(R))
     s[s == 0] = 1.0
     Q = Q * s
     out = Q.cpu().numpy()
     del Gt, Q, R
     return np.asfortranarray(out)
+
+
+def haar_from_gaussian(G: np.ndarray) -> np.ndarray:
+    Q, R = np.linalg.qr(G)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return np.asfortranarray(Q * s)
 
 
 def small_gaussian(m: int = 64, n: int = 64, seed: int = BASE_SEED + 0):

@@ -1,0 +1,270 @@
+"""Parity of the CUDA FP64 path with the CPU oracle, through the C ABI.
+
+Tolerances (FP64 path at eps = 1e-12): singular values max|dS|/S_1 <= 1e-12,
+||Ahat Vhat - Uhat Shat|| / ||Ahat|| <= 1e-10, ||Uhat^T Uhat - I||_max <= 1e-10,
+elementwise vectors against the oracle <= 1e-9 where the spectrum is separated.
+Integer outputs (deflation index sets) are compared exactly."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1707_08369_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U53 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import paper_1707_08369_gb300 as sv
+    from paper_1707_08369_gb300 import build
+    build.build()
+    sv.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return sv
+
+
+@pytest.fixture(scope="module")
+def hnd(sv):
+    return sv.Handle(0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def devF(x):
+    """column-major device copy"""
+    return torch.from_numpy(np.asfortranarray(x).T.copy()).cuda().t()
+
+
+# ------------------------------------------------------------------ secular roots
+@pytest.mark.parametrize("k,sgn,spread,seed", [(1, 1, "u", 0), (2, -1, "u", 1), (37, 1, "u", 2),
+                                               (300, -1, "g", 3), (1000, 1, "g", 4), (4099, 1, "u", 5)])
+def test_secular_vs_oracle(sv, hnd, orc, k, sgn, spread, seed):
+    g = np.random.default_rng(seed)
+    d = np.sort(g.uniform(0, 1, k)) if spread == "u" else np.sort(10 ** (-8 * g.uniform(0, 1, k)))
+    z = g.standard_normal(k)
+    rho = sgn * g.uniform(0.3, 3.0)
+    org_o, tau_o = orc.secular_roots(d, z, rho)
+    org_g, tau_g = hnd.secular(dev(d), dev(z), rho)
+    org_g = org_g.cpu().numpy(); tau_g = tau_g.cpu().numpy()
+    # the same root expressed from possibly different origins: compare mu - d[org_o]
+    diff = (d[org_g] - d[org_o]) + (tau_g - tau_o)
+    # attainable accuracy of each root (Sec. 3.1): the rounding error of evaluating w
+    # (at most about k u (1 + |rho| sum|z_i^2 / delta_i|)) divided by the slope
+    # |rho| sum z_i^2 / delta_i^2; both the oracle's bisection and the GPU iteration
+    # stop inside that interval, so they may differ by twice its width.
+    R = abs(rho)
+    bound = np.empty(k)
+    for j in range(k):
+        delta = (d - d[org_o[j]]) - tau_o[j]
+        t = z * z / delta
+        bound[j] = k * U53 * (1.0 + R * np.abs(t).sum()) / (R * np.sum(t / delta))
+    assert np.all(np.abs(diff) <= 2.0 * bound + 8 * U53 * np.abs(tau_o))
+
+
+# ------------------------------------------------------------------ compact eigen-system
+@pytest.mark.parametrize("N,sgn,case,seed", [(5, 1, "plain", 0), (64, -1, "plain", 1),
+                                             (300, 1, "graded", 2), (700, -1, "defl", 3),
+                                             (2500, 1, "plain", 4)])
+def test_rank_one_eig_vs_oracle(sv, hnd, orc, N, sgn, case, seed):
+    g = np.random.default_rng(seed)
+    if case == "graded":
+        d = 10 ** (-8 * g.uniform(0, 1, N))
+    else:
+        d = g.uniform(0, 1, N)
+    z = g.standard_normal(N)
+    if case == "defl":  # zero components, exact duplicates and near-equal poles
+        z[::17] = 0.0
+        d[5::23] = d[4::23][: len(d[5::23])]
+        d[9::31] = d[8::31][: len(d[9::31])] + 1e-17
+    rho = sgn * g.uniform(0.3, 3.0)
+    ref = orc.rank_one_compact(d, z, rho)
+    out = hnd.rank_one_eig(dev(d), dev(z), rho)
+    k = int(out["k"].item())
+    assert k == ref["k"]
+    assert np.array_equal(out["idx"].cpu().numpy()[:k], ref["idx"])
+    dk = out["dk"].cpu().numpy()[:k]
+    assert np.all(np.abs(dk - ref["dk"]) <= 16 * U53 * np.abs(ref["dk"]))
+    lam_g = out["lam"].cpu().numpy()
+    assert np.abs(lam_g - ref["lam"]).max() <= 1e-13 * np.abs(ref["lam"]).max()
+    zh = out["zhat"].cpu().numpy()[:k]
+    assert np.abs(zh - ref["zhat"]).max() <= 1e-11 * np.abs(ref["zhat"]).max()
+    inv = out["inv_norm"].cpu().numpy()[:k]
+    assert np.all(np.abs(inv - ref["inv_norm"]) <= 1e-10 * np.abs(ref["inv_norm"]))
+
+
+# ------------------------------------------------------------------ Cauchy product
+@pytest.mark.parametrize("rows,N,mode_dense,seed,spread", [(7, 33, True, 0, "u"), (130, 200, True, 1, "u"),
+                                                           (96, 700, False, 2, "u"), (257, 1500, False, 3, "g"),
+                                                           (64, 1500, True, 4, "g")])
+def test_cauchy_product_vs_oracle(sv, hnd, orc, rows, N, mode_dense, seed, spread):
+    g = np.random.default_rng(seed)
+    d = g.uniform(0, 1, N) if spread == "u" else 10 ** (-6 * g.uniform(0, 1, N))
+    z = g.standard_normal(N)
+    rho = g.uniform(0.5, 2.0) * (1 if seed % 2 == 0 else -1)
+    X = wl.haar(max(rows, N), g)[:rows, :N]
+    lam_o, Y_o = orc.rank_one_update_z(X, d, z, rho)
+    mode = sv.FP64 | (sv.DENSE if mode_dense else 0)
+    lam_g, Y_g = hnd.cauchy_product(devF(X), dev(d), dev(z), rho, eps=1e-12, mode=mode)
+    Y_g = Y_g.cpu().numpy()
+    assert np.abs(lam_g.cpu().numpy() - lam_o).max() <= 1e-13 * np.abs(lam_o).max()
+    assert np.abs(Y_g - Y_o).max() <= 1e-10
+
+
+# ------------------------------------------------------------------ full update
+def _run_update(sv, hnd, U, S, V, a, b, eps=1e-12, mode=0):
+    tU, tS, tV = devF(U), dev(S), devF(V)
+    hnd.update(tU, tS, tV, dev(a), dev(b), eps=eps, mode=mode)
+    return tU.cpu().numpy(), tS.cpu().numpy(), tV.cpu().numpy()
+
+
+def _invariants(U, S, V, a, b, Un, Sn, Vn):
+    m, n = U.shape[0], V.shape[0]
+    Ah = U @ np.diag(S) @ V[:, :m].T + np.outer(a, b)
+    nrm = np.linalg.norm(Ah, 2)
+    recon = np.linalg.norm(Ah @ Vn[:, :m] - Un * Sn) / nrm
+    orthU = np.abs(Un.T @ Un - np.eye(m)).max()
+    orthV = np.abs(Vn.T @ Vn - np.eye(n)).max()
+    return Ah, nrm, recon, orthU, orthV
+
+
+def test_update_small_gaussian(sv, hnd, orc):
+    """64 x 64 N(0,1) workload; input SVD from the oracle's Jacobi SVD; exact roots and
+    dense product on both sides: every output element against the oracle."""
+    A, a, b = wl.small_gaussian()
+    U, S, Vt = orc.jacobi_svd(A)
+    Uo, So, Vo = orc.svd_update(U, S, Vt, a, b)
+    Un, Sn, Vn = _run_update(sv, hnd, U, S, Vt, a, b)
+    assert np.abs(Sn - So).max() <= 1e-12 * So[0]
+    assert np.abs(Un - Uo).max() <= 1e-10
+    assert np.abs(Vn - Vo).max() <= 1e-10
+    Ah, nrm, recon, orthU, orthV = _invariants(U, S, Vt, a, b, Un, Sn, Vn)
+    assert recon <= 1e-10 and orthU <= 1e-10 and orthV <= 1e-10
+
+
+@pytest.mark.parametrize("m,n,seed", [(1, 1, 0), (2, 2, 1), (3, 8, 2), (48, 80, 3), (100, 100, 4), (513, 600, 5)])
+def test_update_shapes(sv, hnd, orc, m, n, seed):
+    g = wl.rng(seed + 50)
+    A = g.standard_normal((m, n))
+    a = g.standard_normal(m); b = g.standard_normal(n)
+    U, S, Vh = np.linalg.svd(A)
+    Uo, So, Vo = orc.svd_update(U, S, Vh.T, a, b)
+    Un, Sn, Vn = _run_update(sv, hnd, U, S, Vh.T, a, b)
+    assert np.abs(Sn - So).max() <= 1e-12 * So[0]
+    assert np.abs(Un - Uo).max() <= 1e-9
+    assert np.abs(Vn[:, :m] - Vo[:, :m]).max() <= 1e-9
+    Ah, nrm, recon, orthU, orthV = _invariants(U, S, Vh.T, a, b, Un, Sn, Vn)
+    assert recon <= 1e-10 and orthU <= 1e-10 and orthV <= 1e-10
+    if n > m:  # null space as a subspace
+        assert np.linalg.norm(Ah @ Vn[:, m:]) <= 1e-10 * nrm
+
+
+def test_update_fmm_path(sv, hnd, orc):
+    """Square n = 1536 with the log-uniform spectrum: the far-field (FMM) product runs
+    (N > 512).  Values against the oracle; vectors elementwise where the squared
+    singular values are separated by far more than u ||Ahat||^2 (the accuracy of the
+    Gram formulation, App. A); the reconstruction at the oracle's own level."""
+    U, S, V, a, b = wl.loguniform_sq(1536, seed=wl.BASE_SEED + 77)
+    Uo, So, Vo = orc.svd_update(U, S, V, a, b)
+    Un, Sn, Vn = _run_update(sv, hnd, U, S, V, a, b, eps=1e-12)
+    assert np.abs(Sn - So).max() <= 1e-12 * So[0]
+    Ah, nrm, recon, orthU, orthV = _invariants(U, S, V, a, b, Un, Sn, Vn)
+    assert orthU <= 1e-10 and orthV <= 1e-10
+    recon_o = np.linalg.norm(Ah @ Vo - Uo * So) / nrm
+    assert recon <= max(1e-10, 4.0 * recon_o)
+    sq = So ** 2
+    gaps = np.minimum(np.abs(np.diff(sq, prepend=np.inf)), np.abs(np.diff(sq, append=-np.inf)))
+    sep = gaps > 1e8 * U53 * nrm ** 2
+    assert sep.sum() >= 1
+    assert np.abs(Un[:, sep] - Uo[:, sep]).max() <= 1e-7
+    assert np.abs(Vn[:, sep] - Vo[:, sep]).max() <= 1e-7
+
+
+def test_update_graded_rect_small(sv, hnd, orc):
+    """The graded spectrum with near-equal pairs, rectangular, at a reduced size."""
+    U, S, V, a, b = wl.graded_rect(256, 512, seed=wl.BASE_SEED + 11)
+    Uo, So, Vo = orc.svd_update(U, S, V, a, b)
+    Un, Sn, Vn = _run_update(sv, hnd, U, S, V, a, b)
+    nrm = So[0]
+    # values: squared-value accuracy of the Gram formulation (App. A)
+    assert np.abs(Sn ** 2 - So ** 2).max() <= 64 * 256 * U53 * nrm ** 2
+    assert np.abs(Sn - So).max() <= 1e-12 * nrm
+    Ah, nrm2, recon, orthU, orthV = _invariants(U, S, V, a, b, Un, Sn, Vn)
+    assert orthU <= 1e-10 and orthV <= 1e-10
+    assert recon <= 1e-6
+
+
+def test_update_host_matches_device(sv, hnd, orc):
+    A, a, b = wl.small_gaussian(40, 56, seed=3)
+    U, S, Vh = np.linalg.svd(A)
+    V = np.asfortranarray(Vh.T)
+    Un, Sn, Vn = _run_update(sv, hnd, U, S, V, a, b)
+    Uh, Sh, Vhh = np.asfortranarray(U.copy()), S.copy(), np.asfortranarray(V.copy())
+    hnd.update_host(Uh, Sh, Vhh, a.copy(), b.copy())
+    assert np.array_equal(Sh, Sn) and np.array_equal(Uh, Un) and np.array_equal(Vhh, Vn)
+
+
+def test_chained_updates(sv, hnd, orc):
+    """Updates chained on the device (each applies to the previous result) track the
+    oracle chained the same way."""
+    g = wl.rng(9)
+    m = n = 96
+    U, S, V, a, b = wl.loguniform_sq(n, seed=wl.BASE_SEED + 9)
+    tU, tS, tV = devF(U), dev(S), devF(V)
+    Uo, So, Vo = U, S, V
+    for it in range(3):
+        a = g.standard_normal(m); b = g.standard_normal(n)
+        hnd.update(tU, tS, tV, dev(a), dev(b))
+        Uo, So, Vo = orc.svd_update(Uo, So, Vo, a, b)
+    assert np.abs(tS.cpu().numpy() - So).max() <= 1e-11 * So[0]
+
+
+# ------------------------------------------------------------------ errors, no fault
+def test_invalid_arguments(sv, hnd):
+    U = devF(np.eye(4)); S = dev(np.ones(4)); V = devF(np.eye(4)); a = dev(np.ones(4))
+    with pytest.raises(sv.SvdupError) as ei:
+        hnd.update(U, S, V, a, dev(np.ones(4)), eps=0.0)
+    assert ei.value.code == sv.EINVAL
+    lib = sv.load()
+    assert lib.svdup_update(hnd._h, 5, 4, 1, 5, 1, 1, 4, 1, 1, 1e-12, 0) == sv.EINVAL
+
+
+def test_nonfinite_input_reports_status(sv, hnd):
+    A, a, b = wl.small_gaussian(16, 16, seed=1)
+    U, S, Vh = np.linalg.svd(A)
+    a[3] = np.nan
+    with pytest.raises(sv.SvdupError) as ei:
+        _run_update(sv, hnd, U, S, Vh.T, a, b)
+    assert ei.value.code == sv.ENONFINITE
+    # the handle stays usable
+    a[3] = 0.5
+    _run_update(sv, hnd, U, S, Vh.T, a, b)
+
+
+def test_unsorted_singular_values(sv, hnd):
+    A, a, b = wl.small_gaussian(8, 8, seed=2)
+    U, S, Vh = np.linalg.svd(A)
+    S = S[::-1].copy()
+    with pytest.raises(sv.SvdupError) as ei:
+        _run_update(sv, hnd, U, S, Vh.T, a, b)
+    assert ei.value.code == sv.EORDER
+
+
+def test_iteration_cap_reports_noconv(sv):
+    """A secular iteration cap of 1 returns SVDUP_ENOCONV through the status word."""
+    os.environ["SVDUP_SECULAR_MAXIT"] = "1"
+    try:
+        h = sv.Handle(0)
+    finally:
+        del os.environ["SVDUP_SECULAR_MAXIT"]
+    A, a, b = wl.small_gaussian(32, 32, seed=4)
+    U, S, Vh = np.linalg.svd(A)
+    with pytest.raises(sv.SvdupError) as ei:
+        _run_update(sv, h, U, S, Vh.T, a, b)
+    assert ei.value.code == sv.ENOCONV
+    h.close()
