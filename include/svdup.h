@@ -148,6 +148,32 @@ int svdup_secular(svdup_t h, int k, const double* d, const double* z, double rho
                   double* tau);
 
 /*
+ * Secular roots with no device allocation (the paper has no counterpart: this is an
+ * interface variant of svdup_secular).  For callers that cannot allocate device
+ * memory -- a host application whose memory pool already holds the device memory it
+ * may use, a plug-in that must not call the CUDA allocator, a latency-critical loop in
+ * which cudaMalloc/cudaFree would synchronise the device -- and so cannot create a
+ * handle.  Same operation and output as svdup_secular: device pointers d (k, strictly
+ * ascending), z (k, nonzero), rho != 0 -> org (k ints), tau (k), root j =
+ * d[org[j]] + tau[j], ascending.
+ *   stream  a cudaStream_t of the calling thread's current device (NULL: the legacy
+ *           default stream); the work is queued there and the call returns without
+ *           waiting.
+ *   info    device int owned by the caller: set to 0, then to the first device error
+ *           (SVDUP_ENOCONV, SVDUP_ENONFINITE) once the stream reaches that point.
+ * Scratch lives in one fixed array in the library's device memory, about
+ * 48 * SVDUP_SECULAR_STATIC_MAX_K bytes, held by every GPU that loads the library until
+ * the process exits; k > SVDUP_SECULAR_STATIC_MAX_K returns SVDUP_EINVAL.  Nothing is
+ * allocated or freed.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it.  Every call on a device uses the same array:
+ * calls whose work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.
+ */
+#define SVDUP_SECULAR_STATIC_MAX_K 16384
+int svdup_secular_static(void* stream, int k, const double* d, const double* z, double rho,
+                         int* org, double* tau, int* info);
+
+/*
  * Cauchy product Y = X * Ctilde for the eigen-system of diag(d) + rho z z^T
  * (RankOneUpdate STEPs 3-7, Sec. 6.2; Eq. UCTildeProduct), device pointers:
  *   X rows x N (ldx), columns in the order of d; Y rows x N (ldy), column q is the

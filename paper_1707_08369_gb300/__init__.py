@@ -6,7 +6,8 @@ kernels; PyTorch is used for device memory and streams.  There is no CPU
 fallback: if the shared library is missing or fails to load, every call raises.
 
 Names follow the C ABI: create / destroy / sync / update / update_host /
-rank_one_eig / secular / cauchy_product / error_string / launch_count.
+rank_one_eig / secular / secular_static / cauchy_product / error_string /
+launch_count.
 """
 from __future__ import annotations
 
@@ -52,6 +53,7 @@ def load(path: str = LIB_PATH):
     lib.svdup_rank_one_eig.argtypes = [P, I, P, P, D, P, P, P, P, P, P, P, P]
     lib.svdup_secular.argtypes = [P, I, P, P, D, P, P]
     lib.svdup_cauchy_product.argtypes = [P, I, I, P, I, P, P, D, P, I, P, D, I]
+    lib.svdup_secular_static.argtypes = [P, I, P, P, D, P, P, P]
     _lib = lib
     return lib
 
@@ -208,6 +210,30 @@ class Handle:
                                            int(mode)), "svdup_cauchy_product")
         _check(self.sync(), "svdup_cauchy_product (device)")
         return lam, Y
+
+
+SECULAR_STATIC_MAX_K = 16384
+
+
+def secular_static(d, z, rho: float, stream=None):
+    """Secular roots through svdup_secular_static, the entry point that allocates no
+    device memory (its scratch is a fixed array inside the library; at most
+    SECULAR_STATIC_MAX_K roots).  Queued on `stream` (torch's current stream by
+    default) of d's device; returns (org, tau, info) device tensors without waiting,
+    info holding the device status once the stream has run."""
+    import torch
+    k = d.numel()
+    _dev_f64(d, "d"); _dev_f64(z, "z", k)
+    if stream is None:
+        stream = torch.cuda.current_stream(d.device)
+    org = torch.empty(k, dtype=torch.int32, device=d.device)
+    tau = torch.empty(k, dtype=torch.float64, device=d.device)
+    info = torch.empty(1, dtype=torch.int32, device=d.device)
+    with torch.cuda.device(d.device):
+        _check(load().svdup_secular_static(ctypes.c_void_p(stream.cuda_stream), k, _ptr(d), _ptr(z),
+                                           float(rho), _ptr(org), _ptr(tau), _ptr(info)),
+               "svdup_secular_static")
+    return org, tau, info
 
 
 def colmajor(t):
