@@ -1,5 +1,7 @@
 #!/usr/bin/env python
-"""Benchmark: rank-one SVD updates per second on one GB300, square n = 8192.
+"""Benchmark: rank-one SVD updates per second on one GB300, square n = 8192, in the
+mixed form (split-BF16 tensor-core products, FP64 roots) next to the plain FP64 form
+on the same GPU in the same run.
 
 Workload: A = U diag(sigma) V^T with Haar U, V (8192 x 8192) and sigma log-uniform in
 [1e-4, 1]; each step applies one rank-one update a b^T (a, b ~ N(0,1)) to the previous
@@ -7,10 +9,11 @@ result (chained updates, Alg. 6.1), inputs resident in HBM.  U and V are 512 MiB
 each, larger than L2, so no flush is needed between steps.
 
 One JSON line on stdout (rank 0).  `value` is whole-job updates/s (device-timed with
-CUDA events on the library's stream); `e2e` is the same metric through the host-buffer
-entry point (copies inside the timed region); `roofline` is for the dominant kernel
-(timed live with the library's stage timers); `cpu_baseline` is the CPU oracle on a
-bounded, extrapolated sample of the same update.
+CUDA events on the library's stream); `fp64` is the plain FP64 form on the same inputs;
+`e2e` is the same metric through the host-buffer entry point (copies inside the timed
+region); `roofline` is for the dominant kernel (timed live with the library's stage
+timers, which bracket exactly that kernel's launches); `cpu_baseline` is the CPU oracle
+on a bounded, extrapolated sample of the same update.
 
 --impl reference times the CPU oracle (the reference arm of this comparison) instead.
 Under torchrun every rank runs an independent replica (no collective in the data path).
@@ -30,8 +33,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-MODES = {"fp64": 0, "bf16x3": 1, "fp16x2": 2}
-FP64_PEAK_TFLOPS = 1.0  # measured DFMA throughput on this GB300 pool
+MODES = {"fp64": 0, "bf16x3": 1}
+DTYPES = {"fp64": "f64", "bf16x3": "bf16x3"}  # bf16x3: 3-term BF16 split products, FP32 accumulation
+METRIC = "rank-1 SVD updates/s at n=8192 (mixed vs FP64, same GPU) + p99 latency"
+
+
+def bench_config(args, ws):
+    n = args.n
+    return {"workload": "square n=%d, Haar U/V, sigma log-uniform [1e-4,1], chained "
+                        "N(0,1) rank-one updates" % n,
+            "n": n, "mode": args.mode, "eps": args.eps,
+            "l2": "inputs larger than L2 (U, V %d MiB each)" % (8 * n * n >> 20),
+            "parallelism": "replicas" if ws > 1 else "single"}
 
 
 def parse():
@@ -41,7 +54,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--mode", default="fp64", choices=list(MODES))
+    ap.add_argument("--mode", default="bf16x3", choices=list(MODES))
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-cols", type=int, default=64)
@@ -190,17 +205,75 @@ def run_reference(args, ws, rank):
             times.append(full)
     t = float(np.mean(times))
     value = 1.0 / t
-    line = {"impl": "reference", "metric": "rank-1 SVD updates/s at n=8192", "value": value,
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "square n=%d, Haar U/V, sigma log-uniform [1e-4,1], chained "
-                                   "N(0,1) rank-one updates" % n, "n": n, "mode": "oracle"},
+            "config": bench_config(args, ws),
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": desc.replace("%d" % ncols, str(ncols))},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def load_peaks():
+    """Measured peaks of this machine's GB300 (written next to the repository by the
+    driver); the documented fallback figures when the file is absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def fp64_peak_tflops(sm_mhz):
+    """FP64 (DFMA) peak from unit counts and clock: 152 SMs x 2 DFMA per SM per clock
+    x 2 flops (1.26 TFLOP/s at 2070 MHz)."""
+    return 152 * 2 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, ws, dev, clocks=None):
+    """W untimed then K timed chained updates on the handle's stream; returns per-update
+    latencies (ms), the total (ms), the launch count and the stage timers."""
+    import torch
+    with torch.cuda.stream(stream):
+        for i in range(warmup):
+            h.update(tU, tS, tV, ta[i], tb[i], eps=eps, mode=mode, check=False)
+        rc = h.sync()
+        if rc != 0:
+            raise SystemExit("warm-up update failed: %s" % sv.error_string(rc))
+        h.timing(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        launches0 = h.launch_count()
+        if clocks is not None:
+            clocks.start()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for i in range(steps):
+            j = warmup + i
+            h.update(tU, tS, tV, ta[j], tb[j], eps=eps, mode=mode, check=False)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop() if clocks is not None else None
+        launches = h.launch_count() - launches0
+        rc = h.sync()
+        if rc != 0:
+            raise SystemExit("timed update failed: %s" % sv.error_string(rc))
+        stages = h.timing_read()
+        h.timing(False)
+    lat = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(steps)])
+    total_ms = float(ev[0].elapsed_time(ev[-1]))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return lat, total_ms, launches, stages, clk
 
 
 def main():
@@ -223,62 +296,65 @@ def main():
     dev = torch.device("cuda", local)
     steps_total = args.warmup + args.steps
     U, S, V, ab = make_inputs(n, 170708369 + 2 + 1000 * rank, dev, steps_total)
-    # cpu baseline needs host copies of the step-0 inputs
     U_h, S_h, V_h = (U, S, V) if (rank == 0 and not args.no_cpu) else (None, None, None)
-    tU = torch.from_numpy(np.asfortranarray(U).T.copy()).to(dev).t()
-    tV = torch.from_numpy(np.asfortranarray(V).T.copy()).to(dev).t()
-    tS = torch.from_numpy(S.copy()).to(dev)
+
+    def upload():
+        tU = torch.from_numpy(np.asfortranarray(U).T.copy()).to(dev).t()
+        tV = torch.from_numpy(np.asfortranarray(V).T.copy()).to(dev).t()
+        tS = torch.from_numpy(S.copy()).to(dev)
+        return tU, tS, tV
+
     ta = [torch.from_numpy(a).to(dev) for a, _ in ab]
     tb = [torch.from_numpy(b).to(dev) for _, b in ab]
     stream = torch.cuda.Stream(device=dev)
     h = sv.Handle(local, stream=stream)
-    with torch.cuda.stream(stream):
-        for i in range(args.warmup):
-            h.update(tU, tS, tV, ta[i], tb[i], eps=args.eps, mode=mode, check=False)
-        rc = h.sync()
-        if rc != 0:
-            raise SystemExit("warm-up update failed: %s" % sv.error_string(rc))
-        h.timing(True)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        launches0 = h.launch_count()
-        clocks = ClockSampler(local)
-        clocks.start()
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize(dev)
-        ev[0].record(stream)
-        for i in range(args.steps):
-            j = args.warmup + i
-            h.update(tU, tS, tV, ta[j], tb[j], eps=args.eps, mode=mode, check=False)
-            ev[i + 1].record(stream)
-        torch.cuda.synchronize(dev)
-        if ws > 1:
-            torch.distributed.barrier()
-        clk = clocks.stop()
-        launches = h.launch_count() - launches0
-        rc = h.sync()
-        if rc != 0:
-            raise SystemExit("timed update failed: %s" % sv.error_string(rc))
-        stages = h.timing_read()
-        h.timing(False)
-    lat = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)])
-    total_ms = float(ev[0].elapsed_time(ev[-1]))
-    # timing stage records add a little launch overhead; they are inside the timed region
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    tU, tS, tV = upload()
+    clocks = ClockSampler(local)
+    lat, total_ms, launches, stages, clk = timed_updates(
+        sv, h, stream, tU, tS, tV, ta, tb, mode, args.eps, args.warmup, args.steps, ws, dev, clocks)
     value = ws * args.steps / (total_ms / 1e3)
 
-    # dominant product stage -> roofline
+    # the plain FP64 form on the same GPU, same workload (the comparison the metric names)
+    fp64 = None
+    if mode != 0 and not args.no_fp64:
+        del tU, tV
+        tU, tS, tV = upload()
+        k64 = max(3, args.fp64_steps)
+        lat64, tot64, _, stages64, _ = timed_updates(
+            sv, h, stream, tU, tS, tV, ta, tb, 0, args.eps, min(args.warmup, 3),
+            min(k64, steps_total - min(args.warmup, 3)), ws, dev)
+        k64 = len(lat64)
+        v64 = ws * k64 / (tot64 / 1e3)
+        fp64 = {"value": v64, "unit": "updates/s", "steps": k64, "ms_per_step": tot64 / k64,
+                "p99_ms": float(np.percentile(lat64, 99)), "mixed_over_fp64": value / v64}
+        del tU, tV
+        tU, tS, tV = upload()
+
+    # dominant product stage -> roofline (stage timers bracket exactly that kernel's launch)
+    peaks, peak_src = load_peaks()
     prod = {k: v for k, v in stages.items() if k in ("p2m", "m2l", "out")}
     dom = max(prod, key=lambda k: prod[k][0])
-    dom_ms, dom_cnt, dom_fl = prod[dom]
-    achieved = (dom_fl / max(dom_cnt, 1)) / ((dom_ms / max(dom_cnt, 1)) / 1e3) / 1e12
-    roofline = {"kernel": "k_gemm_f64<%s>" % dom.upper(), "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None,
-                "peak_source": "measured DFMA throughput (FP64 pipe), not in MEASURED_PEAKS.json"}
+    dom_ms, dom_cnt, dom_fl, dom_mma = prod[dom]
+    per_launch_s = (dom_ms / max(dom_cnt, 1)) / 1e3
+    stage_names = {"p2m": "P2M", "m2l": "M2L", "out": "OUT"}
+    if mode == 0:
+        peak = fp64_peak_tflops(clk.get("sm_mhz") if clk else None)
+        achieved = (dom_fl / max(dom_cnt, 1)) / per_launch_s / 1e12
+        roofline = {"kernel": "k_gemm_f64<%s>" % stage_names[dom], "bound": "alu",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None,
+                    "peak_source": "FP64 pipe from unit counts and the sampled SM clock "
+                                   "(152 SMs x 2 DFMA/clk x 2 flops)"}
+    else:
+        peak = float(peaks["bf16_tflops_sustained"])
+        achieved = (dom_mma / max(dom_cnt, 1)) / per_launch_s / 1e12
+        useful = (dom_fl / max(dom_cnt, 1)) / per_launch_s / 1e12
+        roofline = {"kernel": "k_umma<%s>" % stage_names[dom], "bound": "tensor",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "useful_tflops": useful,
+                    "peak_source": "bf16_tflops_sustained of %s MEASURED_PEAKS.json (kernel timed "
+                                   "inside a long step); achieved counts the six split BF16 "
+                                   "products executed" % peak_src}
     stage_ms = {k: round(v[0] / args.steps, 3) for k, v in stages.items()}
 
     # end-to-end through the host-buffer entry point (pinned host memory)
@@ -289,8 +365,7 @@ def main():
         pS = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
         pa = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
         pb = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-        # column-major views of the pinned buffers
-        pUf = pU.T
+        pUf = pU.T  # column-major views of the pinned buffers
         pVf = pV.T
         pUf[...] = tU.cpu().numpy()
         pVf[...] = tV.cpu().numpy()
@@ -316,16 +391,14 @@ def main():
                "sample": desc + "; %.1f s of CPU time spent" % spent}
 
     if rank == 0:
-        line = {"metric": "rank-1 SVD updates/s at n=8192", "value": value, "unit": "updates/s",
+        line = {"metric": METRIC,
+                "value": value, "unit": "updates/s",
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if mode == 0 else args.mode, "data": "synthetic",
-                "config": {"workload": "square n=%d, Haar U/V, sigma log-uniform [1e-4,1], chained "
-                                       "N(0,1) rank-one updates" % n,
-                           "n": n, "mode": args.mode, "eps": args.eps,
-                           "l2": "inputs larger than L2 (U, V 512 MiB each)",
-                           "parallelism": "replicas" if ws > 1 else "single"},
+                "vs_baseline": None, "dtype": DTYPES[args.mode], "data": "synthetic",
+                "config": bench_config(args, ws),
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "fp64": fp64,
                 "stage_ms_per_update": stage_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk}

@@ -40,6 +40,7 @@ extern "C" {
 #define SVDUP_ENONFINITE 4 /* NaN or Inf in the inputs or an intermediate */
 #define SVDUP_ECUDA 5      /* a CUDA runtime call failed */
 #define SVDUP_EORDER 6     /* S is not in descending order */
+#define SVDUP_ETIMEOUT 7   /* a device-side wait gave up after its time limit (about 1 s) */
 
 /* ---- update modes (svdup_update's mode argument) -------------------------- */
 #define SVDUP_FP64 0          /* every step in FP64 */
@@ -87,11 +88,13 @@ long long svdup_launch_count(svdup_t h);
 int svdup_timing(svdup_t h, int enable);
 
 /* Wait for the stream and return, per stage, the summed device time in ms, the
- * number of timed intervals, and the useful floating-point operations executed by
- * the product stages (2 per multiply-add of the stage's contraction; 0 for the other
- * stages) since timing was enabled.  Arrays hold nstage entries (nstage <=
- * SVDUP_NSTAGE); any of them may be NULL. */
-int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, int nstage);
+ * number of timed intervals, the useful floating-point operations of the product
+ * stages (2 per multiply-add of the stage's contraction; 0 for the other stages) and
+ * the tensor-core flops the mixed modes executed (2 per multiply-add of every split
+ * partial product, padding included; 0 in FP64 mode) since timing was enabled.
+ * Arrays hold nstage entries (nstage <= SVDUP_NSTAGE); any of them may be NULL. */
+int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, double* mma_flops,
+                      int nstage);
 
 /*
  * The full rank-one SVD update, Alg. 6.1 STEPs 1-8, in place (device pointers):

@@ -17,7 +17,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsvdup.so")
 
-OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE, ECUDA, EORDER = 0, 1, 2, 3, 4, 5, 6
+OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE, ECUDA, EORDER, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6, 7
 FP64, MIXED_BF16X3, MIXED_FP16X2 = 0, 1, 2
 DENSE, REFINE = 0x100, 0x200
 
@@ -47,7 +47,7 @@ def load(path: str = LIB_PATH):
     lib.svdup_launch_count.argtypes = [P]
     lib.svdup_launch_count.restype = ctypes.c_longlong
     lib.svdup_timing.argtypes = [P, I]
-    lib.svdup_timing_read.argtypes = [P, P, P, P, I]
+    lib.svdup_timing_read.argtypes = [P, P, P, P, P, I]
     lib.svdup_update.argtypes = [P, I, I, P, I, P, P, I, P, P, D, I]
     lib.svdup_update_host.argtypes = [P, I, I, P, I, P, P, I, P, P, D, I]
     lib.svdup_rank_one_eig.argtypes = [P, I, P, P, D, P, P, P, P, P, P, P, P]
@@ -128,13 +128,15 @@ class Handle:
         _check(load().svdup_timing(self._h, 1 if enable else 0), "svdup_timing")
 
     def timing_read(self):
-        """{stage: (ms, intervals, flops)} since timing was enabled."""
+        """{stage: (ms, intervals, useful flops, executed tensor-core flops)} since
+        timing was enabled."""
         n = len(self.STAGES)
         ms = (ctypes.c_double * n)()
         cnt = (ctypes.c_longlong * n)()
         fl = (ctypes.c_double * n)()
-        _check(load().svdup_timing_read(self._h, ms, cnt, fl, n), "svdup_timing_read")
-        return {s: (ms[i], cnt[i], fl[i]) for i, s in enumerate(self.STAGES)}
+        mfl = (ctypes.c_double * n)()
+        _check(load().svdup_timing_read(self._h, ms, cnt, fl, mfl, n), "svdup_timing_read")
+        return {s: (ms[i], cnt[i], fl[i], mfl[i]) for i, s in enumerate(self.STAGES)}
 
     def update(self, U, S, V, a, b, eps: float = 1e-12, mode: int = FP64, check: bool = True):
         """In-place Alg. 6.1 on device tensors: U (m x m) and V (n x n) column-major

@@ -2,6 +2,7 @@
 // the stages of Alg. 6.1 are queued on the handle's stream.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -10,6 +11,29 @@
 namespace svdup {
 
 long long g_launch_count = 0;
+
+static int debug_mode() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("SVDUP_DEBUG");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v;
+}
+
+static cudaError_t g_debug_err = cudaSuccess;  // first failure seen in debug mode
+
+void note_launch(const char* file, int line) {
+  ++g_launch_count;
+  if (!debug_mode()) return;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "svdup: kernel launched at %s:%d failed: %s\n", file, line,
+            cudaGetErrorString(e));
+    if (g_debug_err == cudaSuccess) g_debug_err = e;
+  }
+}
 
 }  // namespace svdup
 
@@ -37,7 +61,8 @@ struct svdup_ctx {
   long long cnt[SVDUP_NSTAGE];
   int open_stage;
   cudaEvent_t open_ev;
-  double* flops_dev;  // 3 accumulators (P2M, M2L, OUT), device
+  double* flops_dev;  // 6 accumulators, device: useful flops of P2M, M2L, OUT, then the
+                      // executed tensor-core flops of the same stages (mixed modes)
 };
 
 namespace {
@@ -88,6 +113,10 @@ Eig make_eig(Arena& ar, int N) {
   e.rank_root = ar.take<int>(n);
   e.rank_defl = ar.take<int>(n);
   e.tol = ar.take<double>(1);
+  const size_t nbox = (n + 63) / 64;
+  e.sqb = ar.take<double>(2 * nbox);
+  e.sqn = ar.take<int>(2 * nbox);
+  e.sqv = ar.take<double>(4 * 26 * nbox);
   return e;
 }
 
@@ -112,10 +141,14 @@ bool use_dense(int N, int mode) {
   return N <= 512;
 }
 
-FmmPlan make_plan(Arena& ar, int N, int rows, double eps) {
+// mixed: P = 16 nodes (the split products' K granularity; 5^-16 is far below the FP32
+// accumulation error) and no FP64 expansions (the split tiles of the MixPlan hold them).
+FmmPlan make_plan(Arena& ar, int N, int rows, double eps, bool mixed = false) {
   FmmPlan f;
   memset(&f, 0, sizeof(f));
-  f.p = expansion_order(eps);
+  f.p = mixed ? kMixP : expansion_order(eps);
+  const size_t rrows = (size_t)(rows > 0 ? rows : 1);
+  if (mixed) rows = 1;
   f.s = leaf_size(N);
   f.Lmax = (N + f.s - 1) / f.s;
   if (f.Lmax < 1) f.Lmax = 1;
@@ -135,7 +168,41 @@ FmmPlan make_plan(Arena& ar, int N, int rows, double eps) {
   f.ldphi = rows > 0 ? rows : 1;
   f.Phi = ar.take<double>((size_t)f.ldphi * L * f.p);
   f.Psi = ar.take<double>((size_t)f.ldphi * (L + 1) * f.p);
+  f.rotw = ar.take<double>(rrows * (size_t)((N + 63) / 64) * 3);
   return f;
+}
+
+// Split-tile buffers of the mixed product for up to `rows` rows and N columns (plan f).
+MixPlan make_mix(Arena& ar, int rows, const FmmPlan& f) {
+  MixPlan mp;
+  memset(&mp, 0, sizeof(mp));
+  mp.rows = rows;
+  mp.rt = (rows + 127) / 128;
+  mp.s = f.s;
+  mp.Lmax = f.Lmax;
+  mp.kx = f.Lmax * f.s / 64;
+  mp.kphi = (f.Lmax * kMixP + 63) / 64;
+  mp.ntT = ((f.Lmax + 1) * kMixP + 127) / 128;
+  const size_t hs = (size_t)f.s / 64, L = (size_t)f.Lmax;
+  mp.Xp = ar.take<unsigned char>((size_t)mp.rt * mp.kx * kMixTileA);
+  mp.Phip = ar.take<unsigned char>((size_t)mp.rt * mp.kphi * kMixTileA);
+  mp.Psip = ar.take<unsigned char>((size_t)mp.rt * (L + 1) * (3 * 128 * kMixP * 2));
+  mp.Sp = ar.take<unsigned char>(L * hs * (3 * kMixP * 64 * 2));
+  mp.Tp = ar.take<unsigned char>((size_t)mp.ntT * mp.kphi * kMixTileA);
+  mp.Lp = ar.take<unsigned char>((L + 1) * (3 * (size_t)f.s * kMixP * 2));
+  mp.Cp = ar.take<unsigned char>((L + 1) * L * hs * (3 * (size_t)f.s * 64 * 2));
+  mp.nnear = ar.take<int>(L + 1);
+  mp.near = ar.take<int>((L + 1) * L);
+  mp.noff = ar.take<int>(L + 2);
+  return mp;
+}
+
+bool is_mixed(int mode) { return (mode & SVDUP_MODE_MASK) == SVDUP_MIXED_BF16X3; }
+
+bool mode_ok(int mode) {
+  int prec = mode & SVDUP_MODE_MASK;
+  if (prec != SVDUP_FP64 && prec != SVDUP_MIXED_BF16X3) return false;
+  return (mode & ~(SVDUP_MODE_MASK | SVDUP_DENSE)) == 0;
 }
 
 int ensure_ws(svdup_ctx* h, size_t bytes) {
@@ -157,6 +224,10 @@ int ensure_ws(svdup_ctx* h, size_t bytes) {
 
 int check_launch() {
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && g_debug_err != cudaSuccess) {  // consumed by note_launch
+    e = g_debug_err;
+    g_debug_err = cudaSuccess;
+  }
   return e == cudaSuccess ? SVDUP_OK : SVDUP_ECUDA;
 }
 
@@ -171,9 +242,10 @@ struct UpdateWs {
   Eig E1, E2, E3, E4;
   double *Xs, *W;
   FmmPlan F;
+  MixPlan M;
 };
 
-UpdateWs layout_update(Arena& ar, int m, int n, double eps) {
+UpdateWs layout_update(Arena& ar, int m, int n, double eps, bool mixed) {
   UpdateWs u;
   u.p = ar.take<double>(m);
   u.q = ar.take<double>(n);
@@ -195,9 +267,11 @@ UpdateWs layout_update(Arena& ar, int m, int n, double eps) {
   u.E2 = make_eig(ar, m);
   u.E3 = make_eig(ar, n);
   u.E4 = make_eig(ar, n);
-  u.Xs = ar.take<double>((size_t)n * n);
+  u.Xs = mixed ? nullptr : ar.take<double>((size_t)n * n);
   u.W = ar.take<double>((size_t)n * n);
-  u.F = make_plan(ar, n, n, eps);
+  u.F = make_plan(ar, n, n, eps, mixed);
+  if (mixed) u.M = make_mix(ar, n, u.F);
+  else memset(&u.M, 0, sizeof(u.M));
   return u;
 }
 
@@ -242,7 +316,7 @@ void stage_end(svdup_ctx* h) {
 // One solve: deflation, roots, final ordering, zhat; the column norms follow separately
 // (fused with a transposed product when the next solve needs its z).
 void queue_solve(svdup_ctx* h, Eig e) {
-  launch_deflate(h->stream, e, nullptr, h->status);
+  launch_deflate(h->stream, e, h->status);
   launch_secular(h->stream, e, h->status, h->maxit);
   launch_merge(h->stream, e);
   launch_loewner(h->stream, e);
@@ -254,7 +328,7 @@ void queue_product(svdup_ctx* h, Eig e, FmmPlan f, int rows, double* X, long lon
                    double* Xs, OutMap om, int mode) {
   int dense = use_dense(e.N, mode) ? 1 : 0;
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(h->stream, e, X, ldx, rows);
+  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rotw);
   launch_gather_columns(h->stream, e, X, ldx, rows, Xs, rows, om);
   stage_end(h);
   stage_begin(h, SVDUP_STAGE_SETUP);
@@ -272,6 +346,37 @@ void queue_product(svdup_ctx* h, Eig e, FmmPlan f, int rows, double* X, long lon
   launch_product_f64_stage(h->stream, 2, e, f, rows, Xs, rows, om, dense);
   stage_end(h);
   if (h->timing) launch_flop_count(h->stream, e, f, rows, dense, h->flops_dev);
+}
+
+// The same product in split BF16 on the tensor cores (svdup_mixed.cu).
+void queue_product_mixed(svdup_ctx* h, Eig e, FmmPlan f, MixPlan mp, int rows, double* X,
+                         long long ldx, OutMap om, int mode) {
+  int dense = use_dense(e.N, mode) ? 1 : 0;
+  mp.rows = rows;
+  mp.rt = (rows + 127) / 128;
+  stage_begin(h, SVDUP_STAGE_GATHER);
+  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rotw);
+  launch_mix_gather(h->stream, e, X, ldx, rows, mp, om);
+  stage_end(h);
+  stage_begin(h, SVDUP_STAGE_SETUP);
+  launch_fmm_setup(h->stream, e, f, 0);
+  launch_mix_setup(h->stream, e, f, mp, dense);
+  stage_end(h);
+  if (!dense) {
+    stage_begin(h, SVDUP_STAGE_P2M);
+    launch_mix_stage(h->stream, 0, e, f, mp, om, dense, h->status);
+    stage_end(h);
+    stage_begin(h, SVDUP_STAGE_M2L);
+    launch_mix_stage(h->stream, 1, e, f, mp, om, dense, h->status);
+    stage_end(h);
+  }
+  stage_begin(h, SVDUP_STAGE_OUT);
+  launch_mix_stage(h->stream, 2, e, f, mp, om, dense, h->status);
+  stage_end(h);
+  if (h->timing) {
+    launch_flop_count(h->stream, e, f, rows, dense, h->flops_dev);
+    launch_mix_flop_count(h->stream, e, f, mp, dense, h->flops_dev + 3);
+  }
 }
 
 }  // namespace
@@ -295,8 +400,8 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
     free(h);
     return SVDUP_ENOMEM;
   }
-  if (cudaMalloc(&h->flops_dev, 3 * sizeof(double)) != cudaSuccess ||
-      cudaMemsetAsync(h->flops_dev, 0, 3 * sizeof(double), h->stream) != cudaSuccess) {
+  if (cudaMalloc(&h->flops_dev, 6 * sizeof(double)) != cudaSuccess ||
+      cudaMemsetAsync(h->flops_dev, 0, 6 * sizeof(double), h->stream) != cudaSuccess) {
     cudaFree(h->status);
     free(h);
     return SVDUP_ENOMEM;
@@ -344,16 +449,17 @@ int svdup_timing(svdup_t h, int enable) {
   for (int s = 0; s < SVDUP_NSTAGE; s++) { h->ms[s] = 0.0; h->cnt[s] = 0; }
   h->timing = enable ? 1 : 0;
   h->open_stage = -1;
-  if (cudaMemsetAsync(h->flops_dev, 0, 3 * sizeof(double), h->stream) != cudaSuccess)
+  if (cudaMemsetAsync(h->flops_dev, 0, 6 * sizeof(double), h->stream) != cudaSuccess)
     return SVDUP_ECUDA;
   return SVDUP_OK;
 }
 
-int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, int nstage) {
+int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, double* mma_flops,
+                      int nstage) {
   if (!h || nstage < 0 || nstage > SVDUP_NSTAGE) return SVDUP_EINVAL;
   if (set_device(h)) return SVDUP_ECUDA;
-  double fl[3] = {0, 0, 0};
-  if (cudaMemcpyAsync(fl, h->flops_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
+  double fl[6] = {0, 0, 0, 0, 0, 0};
+  if (cudaMemcpyAsync(fl, h->flops_dev, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
       cudaSuccess)
     return SVDUP_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
@@ -372,12 +478,9 @@ int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, in
   for (int s = 0; s < nstage; s++) {
     if (ms) ms[s] = h->ms[s];
     if (count) count[s] = h->cnt[s];
-    if (flops) {
-      flops[s] = 0.0;
-      if (s == SVDUP_STAGE_P2M) flops[s] = fl[0];
-      if (s == SVDUP_STAGE_M2L) flops[s] = fl[1];
-      if (s == SVDUP_STAGE_OUT) flops[s] = fl[2];
-    }
+    int slot = s == SVDUP_STAGE_P2M ? 0 : s == SVDUP_STAGE_M2L ? 1 : s == SVDUP_STAGE_OUT ? 2 : -1;
+    if (flops) flops[s] = slot >= 0 ? fl[slot] : 0.0;
+    if (mma_flops) mma_flops[s] = slot >= 0 ? fl[3 + slot] : 0.0;
   }
   return SVDUP_OK;
 }
@@ -406,6 +509,7 @@ const char* svdup_error_string(int code) {
     case SVDUP_ENONFINITE: return "non-finite value in the inputs or an intermediate";
     case SVDUP_ECUDA: return "CUDA runtime error";
     case SVDUP_EORDER: return "singular values are not in descending order";
+    case SVDUP_ETIMEOUT: return "a device-side wait gave up after its time limit";
     default: return "unknown error";
   }
 }
@@ -420,15 +524,15 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   if (!h || !U || !S || !V || !a || !b) return SVDUP_EINVAL;
   if (m < 1 || n < m || ldu < m || ldv < n) return SVDUP_EINVAL;
   if (!(eps > 0.0 && eps < 1.0)) return SVDUP_EINVAL;
-  int prec = mode & SVDUP_MODE_MASK;
-  if (prec != SVDUP_FP64) return SVDUP_EINVAL;  // mixed forms: not in this build yet
+  if (!mode_ok(mode)) return SVDUP_EINVAL;
+  const bool mixed = is_mixed(mode);
   if (set_device(h)) return SVDUP_ECUDA;
   Arena meas = {nullptr, 0};
-  layout_update(meas, m, n, eps);
+  layout_update(meas, m, n, eps, mixed);
   int rc = ensure_ws(h, meas.off);
   if (rc) return rc;
   Arena ar = {h->ws, 0};
-  UpdateWs u = layout_update(ar, m, n, eps);
+  UpdateWs u = layout_update(ar, m, n, eps, mixed);
   cudaStream_t st = h->stream;
 
   // STEP 1 (rewritten): p = U^T a, q = V^T b, alpha, beta
@@ -465,13 +569,20 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   stage_end(h);
   // products: U -> W -> U (descending), V -> W -> V (descending, signed)
   OutMap om1 = {u.W, (long long)m, m, 0, nullptr};
-  queue_product(h, u.E1, u.F, m, U, ldu, u.Xs, om1, mode);
   OutMap om2 = {U, (long long)ldu, m, 1, nullptr};
-  queue_product(h, u.E2, u.F, m, u.W, m, u.Xs, om2, mode);
   OutMap om3 = {u.W, (long long)n, n, 0, nullptr};
-  queue_product(h, u.E3, u.F, n, V, ldv, u.Xs, om3, mode);
   OutMap om4 = {V, (long long)ldv, n, 1, u.sign};
-  queue_product(h, u.E4, u.F, n, u.W, n, u.Xs, om4, mode);
+  if (mixed) {
+    queue_product_mixed(h, u.E1, u.F, u.M, m, U, ldu, om1, mode);
+    queue_product_mixed(h, u.E2, u.F, u.M, m, u.W, m, om2, mode);
+    queue_product_mixed(h, u.E3, u.F, u.M, n, V, ldv, om3, mode);
+    queue_product_mixed(h, u.E4, u.F, u.M, n, u.W, n, om4, mode);
+  } else {
+    queue_product(h, u.E1, u.F, m, U, ldu, u.Xs, om1, mode);
+    queue_product(h, u.E2, u.F, m, u.W, m, u.Xs, om2, mode);
+    queue_product(h, u.E3, u.F, n, V, ldv, u.Xs, om3, mode);
+    queue_product(h, u.E4, u.F, n, u.W, n, u.Xs, om4, mode);
+  }
   // STEP 8
   launch_sqrt_desc(st, m, u.E2.lam, S, h->status);
   return check_launch();
@@ -585,24 +696,29 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
   if (!h || rows < 1 || N < 1 || !X || !d || !z || !Y || !lam) return SVDUP_EINVAL;
   if (ldx < rows || ldy < rows || !(eps > 0.0 && eps < 1.0)) return SVDUP_EINVAL;
   if (!(rho != 0.0) || !isfinite(rho)) return SVDUP_EINVAL;
-  if ((mode & SVDUP_MODE_MASK) != SVDUP_FP64) return SVDUP_EINVAL;
+  if (!mode_ok(mode)) return SVDUP_EINVAL;
+  const bool mixed = is_mixed(mode);
   if (set_device(h)) return SVDUP_ECUDA;
-  auto lay = [&](Arena& ar, Eig* e, double** Xw, double** Xs, FmmPlan* f, double** rhod) {
+  auto lay = [&](Arena& ar, Eig* e, double** Xw, double** Xs, FmmPlan* f, MixPlan* mp,
+                 double** rhod) {
     *e = make_eig(ar, N);
     *rhod = ar.take<double>(1);
     *Xw = ar.take<double>((size_t)rows * N);
-    *Xs = ar.take<double>((size_t)rows * N);
-    *f = make_plan(ar, N, rows, eps);
+    *Xs = mixed ? nullptr : ar.take<double>((size_t)rows * N);
+    *f = make_plan(ar, N, rows, eps, mixed);
+    if (mixed) *mp = make_mix(ar, rows, *f);
   };
   Eig e;
   double *Xw, *Xs, *rhod;
   FmmPlan f;
+  MixPlan mp;
+  memset(&mp, 0, sizeof(mp));
   Arena meas = {nullptr, 0};
-  lay(meas, &e, &Xw, &Xs, &f, &rhod);
+  lay(meas, &e, &Xw, &Xs, &f, &mp, &rhod);
   int rc = ensure_ws(h, meas.off);
   if (rc) return rc;
   Arena ar = {h->ws, 0};
-  lay(ar, &e, &Xw, &Xs, &f, &rhod);
+  lay(ar, &e, &Xw, &Xs, &f, &mp, &rhod);
   cudaStream_t st = h->stream;
   if (cudaMemcpyAsync(rhod, &rho, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return SVDUP_ECUDA;
@@ -614,7 +730,8 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
   queue_solve(h, e);
   launch_norms(st, e, nullptr, nullptr);
   OutMap om = {Y, (long long)ldy, N, 0, nullptr};
-  queue_product(h, e, f, rows, Xw, rows, Xs, om, mode);
+  if (mixed) queue_product_mixed(h, e, f, mp, rows, Xw, rows, om, mode);
+  else queue_product(h, e, f, rows, Xw, rows, Xs, om, mode);
   cudaMemcpyAsync(lam, e.lam, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
   return check_launch();
 }

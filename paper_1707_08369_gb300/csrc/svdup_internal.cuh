@@ -15,6 +15,12 @@ __device__ __forceinline__ void latch(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Launch accounting: every kernel launch calls note_launch (via SVDUP_COUNT_LAUNCH),
+// which counts it and, when the environment sets SVDUP_DEBUG, waits for the device and
+// reports the launch site of the first failing kernel on stderr.
+void note_launch(const char* file, int line);
+#define SVDUP_COUNT_LAUNCH() ::svdup::note_launch(__FILE__, __LINE__)
+
 constexpr double kU = 1.1102230246251565e-16;  // 2^-53, unit roundoff of IEEE double
 
 // 1/x for IEEE double by Newton-Raphson on the reciprocal: an FP32 seed from the
@@ -88,6 +94,11 @@ struct Eig {
   int* rank_root;  // root j -> final index
   int* rank_defl;  // sorted position s (deflated) -> final index, else -1
   double* tol;     // deflation tolerance (1 value)
+  // far-field secular evaluation (null: direct sums only): per box of 64 roots its
+  // origin and half width, its near pole range, and the far sums at its nodes
+  double* sqb;
+  int* sqn;
+  double* sqv;
 };
 
 // Column mapping of a product's output: physical column of final index q is
@@ -123,9 +134,38 @@ struct FmmPlan {
   double* Phi;    // rows x (Lmax p) far-field expansions
   double* Psi;    // rows x ((Lmax+1) p) local expansions
   long long ldphi;
+  double* rotw;   // rows x ceil(N / 64) x 3 scratch of the column rotations
 };
 
-// Host-side launchers (defined in svdup_solve.cu / svdup_product.cu).  Each queues
+// Mixed-precision (split BF16) form of the product on the tensor cores.  Every operand
+// of the three contractions is stored pre-tiled in HBM as three BF16 planes
+// (x = hi + mid + lo, Sec. 5 / App. D operators split the same way), each plane in the
+// canonical K-major layout of the tcgen05 shared-memory descriptor, so one bulk copy
+// moves a whole tile.  A operands are 128-row tiles; K tiles are 64 wide (16 for the
+// local expansions Psi).  P = 16 Chebyshev nodes.
+struct MixPlan {
+  int rows, rt;  // rows of X and the number of 128-row tiles
+  int s;         // leaf size (64 or 128)
+  int Lmax;      // source leaves upper bound (ceil(N / s)); target leaves Lmax + 1
+  int kx;        // X K-tiles per row tile: Lmax * s / 64
+  int kphi;      // Phi K-tiles per row tile: ceil(Lmax * P / 64)
+  int ntT;       // M2L N-tiles: ceil((Lmax + 1) * P / 128)
+  unsigned char* Xp;    // [rt][kx] A tiles (128 x 64)
+  unsigned char* Phip;  // [rt][kphi] A tiles (128 x 64)
+  unsigned char* Psip;  // [rt][Lmax + 1] A tiles (128 x 16)
+  unsigned char* Sp;    // [Lmax][s / 64] B tiles (16 x 64)
+  unsigned char* Tp;    // [ntT][kphi] B tiles (128 x 64)
+  unsigned char* Lp;    // [Lmax + 1] B tiles (s x 16)
+  unsigned char* Cp;    // near-field pool: [(noff[b] + i) * (s / 64) + h] B tiles (s x 64)
+  int* nnear;           // per target leaf: near source leaves (dense: every leaf)
+  int* near;            // near[b * Lmax + i]
+  int* noff;            // exclusive prefix sum of nnear
+};
+
+constexpr int kMixP = 16;
+constexpr size_t kMixTileA = 3 * 128 * 64 * 2;  // A tile bytes (3 planes)
+
+// Host-side launchers (defined in svdup_solve.cu / svdup_product.cu / svdup_mixed.cu).  Each queues
 // its kernels on `st` and adds to the launch counter.
 void launch_gemv_pq(cudaStream_t st, int m, int n, const double* U, long long ldu, const double* V,
                     long long ldv, const double* a, const double* b, double* p, double* q,
@@ -137,7 +177,7 @@ void launch_fill_right(cudaStream_t st, Eig e, int m, int n, const double* S, co
 void launch_fill_second(cudaStream_t st, Eig e, const double* lam_prev, const double* zsec);
 void launch_fill_generic(cudaStream_t st, Eig e, const double* d, const double* z,
                          const double* rho, int* status);
-void launch_deflate(cudaStream_t st, Eig e, double* yvec, int* status);
+void launch_deflate(cudaStream_t st, Eig e, int* status);
 void launch_secular(cudaStream_t st, Eig e, int* status, int maxit);
 void launch_secular_direct(cudaStream_t st, Eig e, int k, const double* d, const double* z,
                            int* status, int maxit);
@@ -152,7 +192,9 @@ void launch_sign_finish(cudaStream_t st, int m, int n, const double* h, double* 
 void launch_fill_ones(cudaStream_t st, int n, double* w);
 void launch_sqrt_desc(cudaStream_t st, int m, const double* lam, double* S, int* status);
 
-void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows);
+// rotw: scratch of rows x ceil(N / 64) x 3 doubles
+void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
+                           double* rotw);
 void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
                            double* Xs, long long ldxs, OutMap om);
 void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense);
@@ -161,5 +203,17 @@ void launch_flop_count(cudaStream_t st, Eig e, FmmPlan f, int rows, int dense, d
 // stage 0 = P2M, 1 = M2L, 2 = L2P + near field (dense: the whole product)
 void launch_product_f64_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, int rows,
                               const double* Xs, long long ldxs, OutMap om, int dense);
+
+// mixed-precision product (svdup_mixed.cu)
+void launch_mix_gather(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
+                       MixPlan mp, OutMap om);
+void launch_mix_setup(cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int dense);
+// stage 0 = P2M, 1 = M2L, 2 = L2P + near field (dense: the whole product)
+void launch_mix_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, MixPlan mp, OutMap om,
+                      int dense, int* status);
+// adds the executed tensor-core flops (2 per multiply-add of every split product) of the
+// three stages to acc[0..2]
+void launch_mix_flop_count(cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int dense,
+                           double* acc);
 
 }  // namespace svdup

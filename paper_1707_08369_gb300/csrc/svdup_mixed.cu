@@ -1,0 +1,714 @@
+// svdup_mixed.cu -- the product X * Ctilde (RankOneUpdate STEPs 3-7, Sec. 6.2; Eq.
+// UCTildeProduct) in split BF16 on the fifth-generation tensor cores (tcgen05).
+//
+// The contractions are those of the FP64 path (svdup_product.cu): the Chebyshev far
+// field of App. D read with a flat partition into leaves,
+//     Phi = X_leaf S_leaf    (P2M),   Psi = Phi T    (M2L),
+//     Y_b = Psi_b L_b + X_near(b) C_near(b)    (L2P + near field),
+// with P = 16 Chebyshev nodes.  Every operand value x is split as x = hi + mid + lo
+// (three BF16 numbers, 24 significant bits together) and each product A B is formed
+// from the six partial products hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid with FP32
+// accumulation in tensor memory: FP32-level accuracy from BF16 multiplies.
+//
+// The FP64 operator values (S, T, L from the FP64 set-up kernels, the near-field Cauchy
+// entries zhat_t inv_j / delta_tj from the root offsets delta_tj = (d_t - d_org(j)) -
+// tau_j) are computed once per product and stored as split tiles; only the split, not
+// the arithmetic, is in BF16.  The near-field entries are generated once per product
+// rather than once per row tile: on this part an FP64 operation costs as much as ~64
+// FP32 ones, and every row tile shares the same entries.
+//
+// Tiles: every operand is stored in HBM pre-tiled, each tile's three planes back to
+// back, each plane in the canonical K-major no-swizzle layout of the tcgen05 shared
+// memory descriptor: element (r, k) of an R x KB plane is at byte
+//     (r / 8) * (KB * 16) + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// i.e. 8 x 8 core matrices of 128 contiguous bytes, K-adjacent core matrices 128 B
+// apart (leading byte offset) and 8-row groups KB * 16 B apart (stride byte offset).
+// A tile is therefore one contiguous bulk copy (cp.async.bulk) into shared memory.
+//
+// GEMM kernel: one CTA per 128-row output tile; 6 warps.  Warp 4 issues the bulk
+// copies into a two-stage shared-memory ring, warp 5 allocates tensor memory and one of
+// its threads issues the MMAs (M = 128, N = 16..128, K = 16 per instruction), warps 0-3
+// read the FP32 accumulator back (tcgen05.ld) and write the stage's output.  Every wait
+// on an mbarrier gives up after about one second of global time, latches
+// SVDUP_ETIMEOUT and lets the CTA finish.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "svdup_internal.cuh"
+
+namespace svdup {
+
+extern long long g_launch_count;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Tile geometry
+// ---------------------------------------------------------------------------
+constexpr int kTM = 128;                      // rows per A tile / MMA M
+constexpr int kKB = 64;                       // K per tile (X, Phi, T, C)
+constexpr uint32_t kTileA = 3 * kTM * kKB * 2;       // 49152
+constexpr uint32_t kPlaneA = kTM * kKB * 2;          // 16384
+constexpr uint32_t kTilePsi = 3 * kTM * kMixP * 2;   // 12288 (128 x 16)
+constexpr uint32_t kPlanePsi = kTM * kMixP * 2;      // 4096
+constexpr uint32_t kTileS = 3 * kMixP * kKB * 2;     // 6144 (16 x 64)
+constexpr uint32_t kPlaneS = kMixP * kKB * 2;        // 2048
+constexpr uint32_t kStageBytes = 2 * kTileA;         // A + B region per ring stage
+constexpr uint32_t kRingBytes = 2 * kStageBytes;     // two stages
+constexpr uint32_t kSmemBytes = kRingBytes + 256 + 1024;  // + barriers, + alignment slack
+
+__host__ __device__ constexpr uint32_t tile_L_bytes(int s) { return 3u * s * kMixP * 2; }
+__host__ __device__ constexpr uint32_t tile_C_bytes(int s) { return 3u * s * kKB * 2; }
+
+// byte offset of element (r, k) in a canonical K-major plane with K extent KB
+__device__ __forceinline__ uint32_t cl_off(int r, int k, int KB) {
+  return (uint32_t)((r >> 3) * (KB * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// ---------------------------------------------------------------------------
+// Splits: x = hi + mid + lo in BF16 (round to nearest at each step; each remainder is
+// exact in the wider type).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split3f(float x, uint16_t& h, uint16_t& m, uint16_t& l) {
+  __nv_bfloat16 bh = __float2bfloat16_rn(x);
+  float r = x - __bfloat162float(bh);
+  __nv_bfloat16 bm = __float2bfloat16_rn(r);
+  r = r - __bfloat162float(bm);
+  __nv_bfloat16 bl = __float2bfloat16_rn(r);
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+
+__device__ __forceinline__ void split3d(double x, uint16_t& h, uint16_t& m, uint16_t& l) {
+  __nv_bfloat16 bh = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(bh);
+  __nv_bfloat16 bm = __double2bfloat16(r);
+  r = r - (double)__bfloat162float(bm);
+  __nv_bfloat16 bl = __double2bfloat16(r);
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+
+__device__ __forceinline__ uint4 pack8(const uint16_t* v) {
+  uint4 o;
+  o.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+  o.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+  o.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
+  o.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+  return o;
+}
+
+// Writes 8 consecutive K values of one row into the three planes of a tile.
+__device__ __forceinline__ void store_split8(unsigned char* tile, uint32_t plane, uint32_t off,
+                                             const uint16_t* h, const uint16_t* m,
+                                             const uint16_t* l) {
+  *(uint4*)(tile + off) = pack8(h);
+  *(uint4*)(tile + plane + off) = pack8(m);
+  *(uint4*)(tile + 2 * plane + off) = pack8(l);
+}
+
+__device__ __forceinline__ void store_split8_f(unsigned char* tile, uint32_t plane, uint32_t off,
+                                               const float* v) {
+  uint16_t h[8], m[8], l[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) split3f(v[c], h[c], m[c], l[c]);
+  store_split8(tile, plane, off, h, m, l);
+}
+
+__device__ __forceinline__ void store_split8_d(unsigned char* tile, uint32_t plane, uint32_t off,
+                                               const double* v) {
+  uint16_t h[8], m[8], l[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) split3d(v[c], h[c], m[c], l[c]);
+  store_split8(tile, plane, off, h, m, l);
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers: mbarrier, bulk copy, tcgen05
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // one second
+
+// Waits for the phase of `bar` with the given parity to complete.  Gives up (returns
+// false) after kWaitLimitNs or once another role of the CTA has raised *abort.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort) return false;
+      uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > kWaitLimitNs) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared memory matrix descriptor (tcgen05): start address, leading and stride byte
+// offsets (all >> 4), descriptor version 1 at bit 46, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16
+// (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// X -> split A tiles.  Tile (rt, kt): rows rt*128.., sorted columns t = kt*64 + c
+// (column perm[idx[t]] of X for t < k, zero beyond; zero rows beyond `rows`).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mix_gather(Eig e, const double* __restrict__ X,
+                                                    long long ldx, int rows, MixPlan mp) {
+  __shared__ long long scol[kKB];
+  const int rt = blockIdx.x, kt = blockIdx.y;
+  const int k = e.kp[0];
+  if (threadIdx.x < kKB) {
+    int t = kt * kKB + threadIdx.x;
+    scol[threadIdx.x] = t < k ? (long long)e.perm[e.idx[t]] * ldx : -1;
+  }
+  __syncthreads();
+  unsigned char* tile = mp.Xp + ((size_t)rt * mp.kx + kt) * kTileA;
+  for (int it = threadIdx.x; it < kTM * (kKB / 8); it += blockDim.x) {
+    const int r = it & (kTM - 1), ch = it >> 7;
+    const long long row = (long long)rt * kTM + r;
+    float v[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      long long col = scol[ch * 8 + c];
+      v[c] = (col >= 0 && row < rows) ? (float)X[row + col] : 0.0f;
+    }
+    store_split8_f(tile, kPlaneA, cl_off(r, ch * 8, kKB), v);
+  }
+}
+
+__device__ __forceinline__ long long out_col_m(const OutMap& om, int q) {
+  return om.out_rev ? (long long)(om.out_n - 1 - q) : (long long)q;
+}
+
+// Deflated columns are eigenvectors already: straight to their output column.
+__global__ void k_mix_defl(Eig e, const double* __restrict__ X, long long ldx, int rows,
+                           OutMap om) {
+  const int k = e.kp[0];
+  const int c = k + blockIdx.x;
+  if (c >= e.N) return;
+  int s = e.didx[c - k];
+  int q = e.rank_defl[s];
+  double sc = om.colscale ? om.colscale[q] : 1.0;
+  const double* src = X + (long long)e.perm[s] * ldx;
+  double* dst = om.Y + out_col_m(om, q) * om.ldy;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = sc * src[r];
+}
+
+// ---------------------------------------------------------------------------
+// Set-up: near lists (dense: every source leaf), their offsets into the pool, and the
+// split operator tiles.
+// ---------------------------------------------------------------------------
+__global__ void k_mix_near(FmmPlan f, MixPlan mp, int dense) {
+  const int Ls = f.L[0], Lt = f.L[1];
+  for (int b = threadIdx.x; b < Lt; b += blockDim.x) {
+    int n = dense ? Ls : f.nnear[b];
+    mp.nnear[b] = n;
+    for (int i = 0; i < n; i++)
+      mp.near[(long long)b * mp.Lmax + i] = dense ? i : f.near[(long long)b * f.Lmax + i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < Lt; b++) {
+      mp.noff[b] = acc;
+      acc += mp.nnear[b];
+    }
+    mp.noff[Lt] = acc;
+  }
+}
+
+// S tile (a, h): B[alpha][kk] = S_a(tl = 64 h + kk, alpha) (16 x 64).
+__global__ void k_mix_pack_S(Eig e, FmmPlan f, MixPlan mp) {
+  const int hs = mp.s / kKB;
+  const int a = blockIdx.x / hs, h = blockIdx.x % hs;
+  if (a >= f.L[0]) return;
+  unsigned char* tile = mp.Sp + (size_t)blockIdx.x * kTileS;
+  for (int it = threadIdx.x; it < kMixP * (kKB / 8); it += blockDim.x) {
+    const int al = it % kMixP, ch = it / kMixP;
+    double v[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      int tl = h * kKB + ch * 8 + c;
+      v[c] = f.S[(size_t)a * f.s * f.p + (size_t)al * f.s + tl];
+    }
+    store_split8_d(tile, kPlaneS, cl_off(al, ch * 8, kKB), v);
+  }
+}
+
+// T tile (nt, kt): B[n][kk] = T(row = 64 kt + kk, col = 128 nt + n), zero outside
+// (Ls P) x (Lt P).
+__global__ void k_mix_pack_T(FmmPlan f, MixPlan mp) {
+  const int nt = blockIdx.x, kt = blockIdx.y;
+  const int Ls = f.L[0], Lt = f.L[1];
+  const long long ldT = (long long)f.Lmax * f.p;
+  unsigned char* tile = mp.Tp + ((size_t)nt * mp.kphi + kt) * kTileA;
+  for (int it = threadIdx.x; it < kTM * (kKB / 8); it += blockDim.x) {
+    const int n = it & (kTM - 1), ch = it >> 7;
+    const int col = nt * kTM + n;
+    double v[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      int row = kt * kKB + ch * 8 + c;
+      v[c] = (col < Lt * kMixP && row < Ls * kMixP) ? f.T[row + col * ldT] : 0.0;
+    }
+    store_split8_d(tile, kPlaneA, cl_off(n, ch * 8, kKB), v);
+  }
+}
+
+// L tile b: B[jl][beta] = L_b(beta, jl) (s x 16).
+__global__ void k_mix_pack_L(FmmPlan f, MixPlan mp) {
+  const int b = blockIdx.x;
+  if (b >= f.L[1]) return;
+  const int s = mp.s;
+  unsigned char* tile = mp.Lp + (size_t)b * tile_L_bytes(s);
+  const uint32_t plane = (uint32_t)s * kMixP * 2;
+  for (int it = threadIdx.x; it < s * (kMixP / 8); it += blockDim.x) {
+    const int jl = it % s, ch = it / s;
+    double v[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++)
+      v[c] = f.Lop[(size_t)b * f.s * f.p + (size_t)jl * f.p + ch * 8 + c];
+    store_split8_d(tile, plane, cl_off(jl, ch * 8, kMixP), v);
+  }
+}
+
+// Near-field tile (b, i, h): source leaf a = near[b][i], K half h:
+//   B[jl][kk] = zhat_t inv_j / delta_tj,  t = a s + 64 h + kk,  j = tj0[b] + jl,
+//   delta_tj = (dk_t - d_org(j)) - tau_j   (the offsets of the FP64 root solve),
+// zero for t >= k or j >= tj1[b].
+__global__ void k_mix_pack_C(Eig e, FmmPlan f, MixPlan mp) {
+  const int b = blockIdx.x, i = blockIdx.y, h = blockIdx.z;
+  if (b >= f.L[1] || i >= mp.nnear[b]) return;
+  const int k = e.kp[0];
+  const int s = mp.s, hs = s / kKB;
+  const int a = mp.near[(long long)b * mp.Lmax + i];
+  const int j0 = f.tj0[b], j1 = f.tj1[b];
+  unsigned char* tile = mp.Cp + ((size_t)(mp.noff[b] + i) * hs + h) * tile_C_bytes(s);
+  const uint32_t plane = (uint32_t)s * kKB * 2;
+  for (int it = threadIdx.x; it < s * (kKB / 8); it += blockDim.x) {
+    const int jl = it % s, ch = it / s;
+    const int j = j0 + jl;
+    double v[8];
+    if (j < j1) {
+      const double dO = e.dorg[j], tj = e.tau[j], inv = e.inv[j];
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        int t = a * s + h * kKB + ch * 8 + c;
+        v[c] = t < k ? e.zhat[t] * inv * rcp64((e.dk[t] - dO) - tj) : 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; c++) v[c] = 0.0;
+    }
+    store_split8_d(tile, plane, cl_off(jl, ch * 8, kKB), v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The tcgen05 GEMM.  A K tile is a pair (A tile, B tile) of split operands; the CTA
+// accumulates sum over its K tiles of A B^T (B stored N x K) into tensor memory.
+// ---------------------------------------------------------------------------
+enum { MS_P2M = 0, MS_M2L = 1, MS_OUT = 2 };
+
+struct KTile {
+  const unsigned char* a;
+  const unsigned char* b;
+  uint32_t abytes, bbytes;  // copy sizes (three planes)
+  uint32_t aplane, bplane;  // plane strides
+  int kb;                   // K extent (16 or 64)
+  int n;                    // MMA N
+  int col;                  // accumulator column offset
+  int first;                // first K tile of its accumulator
+};
+
+struct Job {
+  int rt, job;
+  int k, Ls, Lt;
+  int ntiles;
+};
+
+template <int STAGE>
+__device__ __forceinline__ int job_tiles(const Job& J, const FmmPlan& f, const MixPlan& mp,
+                                         int dense) {
+  const int hs = mp.s / kKB;
+  if (STAGE == MS_P2M) return (min(4 * J.job + 4, J.Ls) - 4 * J.job) * hs;
+  if (STAGE == MS_M2L) return (J.Ls + 3) / 4;
+  return (dense ? 0 : 1) + mp.nnear[J.job] * hs;
+}
+
+template <int STAGE>
+__device__ __forceinline__ KTile ktile(int i, const Job& J, const FmmPlan& f, const MixPlan& mp,
+                                       int dense) {
+  KTile t;
+  const int hs = mp.s / kKB;
+  if (STAGE == MS_P2M) {
+    const int a = 4 * J.job + i / hs, h = i % hs;
+    t.a = mp.Xp + ((size_t)J.rt * mp.kx + (size_t)a * hs + h) * kTileA;
+    t.b = mp.Sp + ((size_t)a * hs + h) * kTileS;
+    t.abytes = kTileA; t.aplane = kPlaneA;
+    t.bbytes = kTileS; t.bplane = kPlaneS;
+    t.kb = kKB; t.n = kMixP; t.col = (a - 4 * J.job) * kMixP; t.first = (h == 0);
+  } else if (STAGE == MS_M2L) {
+    t.a = mp.Phip + ((size_t)J.rt * mp.kphi + i) * kTileA;
+    t.b = mp.Tp + ((size_t)J.job * mp.kphi + i) * kTileA;
+    t.abytes = kTileA; t.aplane = kPlaneA;
+    t.bbytes = kTileA; t.bplane = kPlaneA;
+    t.kb = kKB; t.n = kTM; t.col = 0; t.first = (i == 0);
+  } else {
+    const int s = mp.s;
+    const int b = J.job;
+    if (!dense && i == 0) {
+      t.a = mp.Psip + ((size_t)J.rt * (mp.Lmax + 1) + b) * kTilePsi;
+      t.b = mp.Lp + (size_t)b * tile_L_bytes(s);
+      t.abytes = kTilePsi; t.aplane = kPlanePsi;
+      t.bbytes = tile_L_bytes(s); t.bplane = (uint32_t)s * kMixP * 2;
+      t.kb = kMixP; t.n = s; t.col = 0; t.first = 1;
+    } else {
+      const int q = i - (dense ? 0 : 1);
+      const int ni = q / hs, h = q % hs;
+      const int a = mp.near[(long long)b * mp.Lmax + ni];
+      t.a = mp.Xp + ((size_t)J.rt * mp.kx + (size_t)a * hs + h) * kTileA;
+      t.b = mp.Cp + ((size_t)(mp.noff[b] + ni) * hs + h) * tile_C_bytes(s);
+      t.abytes = kTileA; t.aplane = kPlaneA;
+      t.bbytes = tile_C_bytes(s); t.bplane = (uint32_t)s * kKB * 2;
+      t.kb = kKB; t.n = s; t.col = 0;
+      t.first = dense && q == 0;  // with the far field, tile 0 (Psi L) opened the sum
+    }
+  }
+  return t;
+}
+
+// The six partial products of the 3-term split: (A plane, B plane).
+__constant__ int kPairA[6] = {0, 0, 1, 0, 2, 1};
+__constant__ int kPairB[6] = {0, 1, 0, 2, 0, 1};
+
+template <int STAGE, int NCOLS>
+__global__ void __launch_bounds__(192, 1) k_umma(Eig e, FmmPlan f, MixPlan mp, OutMap om,
+                                                 int dense, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  Job J;
+  J.rt = blockIdx.x;
+  J.job = blockIdx.y;
+  J.k = e.kp[0];
+  J.Ls = f.L[0];
+  J.Lt = f.L[1];
+  // inactive jobs leave before any barrier or tensor-memory use (uniform per CTA)
+  if (STAGE == MS_P2M && 4 * J.job >= J.Ls) return;
+  if (STAGE == MS_M2L && J.job * (kTM / kMixP) >= J.Lt) return;
+  if (STAGE == MS_OUT && J.job >= J.Lt) return;
+  J.ntiles = job_tiles<STAGE>(J, f, mp, dense);
+
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t s_base = smem_u32(sm);
+  const uint32_t sA[2] = {s_base, s_base + kStageBytes};
+  const uint32_t sB[2] = {s_base + kTileA, s_base + kStageBytes + kTileA};
+  uint64_t* bars = (uint64_t*)(sm + kRingBytes);  // full[2], empty[2], accum
+  const uint32_t bar_full[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+  const uint32_t bar_empty[2] = {smem_u32(&bars[2]), smem_u32(&bars[3])};
+  const uint32_t bar_accum = smem_u32(&bars[4]);
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(sm + kRingBytes + 64);
+  volatile int* abort_flag = (volatile int*)(sm + kRingBytes + 128);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 5) {
+    tmem_alloc(smem_u32((const void*)tmem_slot), NCOLS);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(bar_full[0], 1);
+    mbar_init(bar_full[1], 1);
+    mbar_init(bar_empty[0], 1);
+    mbar_init(bar_empty[1], 1);
+    mbar_init(bar_accum, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {  // producer: bulk copies into the ring
+      for (int i = 0; i < J.ntiles; i++) {
+        const int st = i & 1;
+        const uint32_t u = (uint32_t)(i >> 1);
+        if (i >= 2 && !mbar_wait(bar_empty[st], (u & 1u) ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          latch(status, SVDUP_ETIMEOUT);
+          break;
+        }
+        KTile t = ktile<STAGE>(i, J, f, mp, dense);
+        mbar_expect_tx(bar_full[st], t.abytes + t.bbytes);
+        bulk_g2s(sA[st], t.a, t.abytes, bar_full[st]);
+        bulk_g2s(sB[st], t.b, t.bbytes, bar_full[st]);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {  // MMA issuer
+      for (int i = 0; i < J.ntiles; i++) {
+        const int st = i & 1;
+        const uint32_t u = (uint32_t)(i >> 1);
+        if (!mbar_wait(bar_full[st], u & 1u, abort_flag)) {
+          *abort_flag = 1;
+          latch(status, SVDUP_ETIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        KTile t = ktile<STAGE>(i, J, f, mp, dense);
+        const uint32_t idesc = idesc_bf16(kTM, t.n);
+        const uint32_t sbo = (uint32_t)t.kb * 16;
+        for (int ks = 0; ks < t.kb / 16; ks++) {
+#pragma unroll
+          for (int q = 0; q < 6; q++) {
+            uint64_t ad = sdesc(sA[st] + kPairA[q] * t.aplane + ks * 256, 128, sbo);
+            uint64_t bd = sdesc(sB[st] + kPairB[q] * t.bplane + ks * 256, 128, sbo);
+            uint32_t acc = (t.first && ks == 0 && q == 0) ? 0u : 1u;
+            umma_bf16(tmem + (uint32_t)t.col, ad, bd, idesc, acc);
+          }
+        }
+        umma_commit(bar_empty[st]);  // frees the stage once these MMAs have read it
+      }
+      umma_commit(bar_accum);  // every MMA issued above has completed
+    }
+  } else {
+    // epilogue: warps 0-3, TMEM lanes 32 w .. 32 w + 31 = output rows
+    const bool ok = mbar_wait(bar_accum, 0, abort_flag);
+    tc_fence_after();
+    const int r = warp * 32 + lane;
+    const long long row = (long long)J.rt * kTM + r;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    if (!ok) {
+      *abort_flag = 1;
+      latch(status, SVDUP_ETIMEOUT);
+    } else if (!*abort_flag) {
+      if (STAGE == MS_P2M) {
+        unsigned char* tile = mp.Phip + ((size_t)J.rt * mp.kphi + J.job) * kTileA;
+        for (int u = 0; u < 4; u++) {
+          float v[16];
+          if (4 * J.job + u < J.Ls) tmem_ld16(taddr + u * kMixP, v);
+          else
+            for (int c = 0; c < 16; c++) v[c] = 0.0f;
+          store_split8_f(tile, kPlaneA, cl_off(r, u * 16, kKB), v);
+          store_split8_f(tile, kPlaneA, cl_off(r, u * 16 + 8, kKB), v + 8);
+        }
+      } else if (STAGE == MS_M2L) {
+        for (int u = 0; u < kTM / kMixP; u++) {
+          const int b = J.job * (kTM / kMixP) + u;
+          if (b >= J.Lt) break;
+          float v[16];
+          tmem_ld16(taddr + u * kMixP, v);
+          unsigned char* tile = mp.Psip + ((size_t)J.rt * (mp.Lmax + 1) + b) * kTilePsi;
+          store_split8_f(tile, kPlanePsi, cl_off(r, 0, kMixP), v);
+          store_split8_f(tile, kPlanePsi, cl_off(r, 8, kMixP), v + 8);
+        }
+      } else {
+        const int j0 = f.tj0[J.job], nb = f.tj1[J.job] - j0;
+        for (int c0 = 0; c0 < nb; c0 += 16) {
+          float v[16];
+          tmem_ld16(taddr + c0, v);
+          if (row < mp.rows) {
+            for (int c = 0; c < 16 && c0 + c < nb; c++) {
+              const int q = e.rank_root[j0 + c0 + c];
+              const double sc = om.colscale ? om.colscale[q] : 1.0;
+              om.Y[row + out_col_m(om, q) * om.ldy] = sc * (double)v[c];
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, NCOLS);
+  }
+}
+
+template <int STAGE, int NCOLS>
+void launch_umma(cudaStream_t st, dim3 grid, Eig e, FmmPlan f, MixPlan mp, OutMap om, int dense,
+                 int* status) {
+  cudaFuncSetAttribute(k_umma<STAGE, NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kSmemBytes);
+  k_umma<STAGE, NCOLS><<<grid, 192, kSmemBytes, st>>>(e, f, mp, om, dense, status);
+  SVDUP_COUNT_LAUNCH();
+}
+
+// Executed tensor-core flops: 2 M N K per split product, six split products.
+__global__ void k_mix_flops(Eig e, FmmPlan f, MixPlan mp, int dense, double* acc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double M = (double)mp.rt * kTM, s = (double)mp.s;
+  const int Ls = f.L[0], Lt = f.L[1];
+  if (Ls == 0) return;
+  double p2m = 0.0, m2l = 0.0, out = 0.0;
+  if (!dense) {
+    p2m = 6.0 * 2.0 * M * kMixP * (double)Ls * s;
+    m2l = 6.0 * 2.0 * M * (double)((Lt * kMixP + kTM - 1) / kTM) * kTM * (double)((Ls + 3) / 4) *
+          kKB;
+  }
+  for (int b = 0; b < Lt; b++)
+    out += 6.0 * 2.0 * M * s * ((dense ? 0.0 : (double)kMixP) + (double)mp.nnear[b] * s);
+  acc[0] += p2m;
+  acc[1] += m2l;
+  acc[2] += out;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_mix_gather(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
+                       MixPlan mp, OutMap om) {
+  dim3 g(mp.rt, mp.kx);
+  k_mix_gather<<<g, 256, 0, st>>>(e, X, ldx, rows, mp);
+  SVDUP_COUNT_LAUNCH();
+  k_mix_defl<<<e.N, 256, 0, st>>>(e, X, ldx, rows, om);
+  SVDUP_COUNT_LAUNCH();
+}
+
+void launch_mix_setup(cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int dense) {
+  k_mix_near<<<1, 256, 0, st>>>(f, mp, dense);
+  SVDUP_COUNT_LAUNCH();
+  const int hs = mp.s / kKB;
+  if (!dense) {
+    k_mix_pack_S<<<mp.Lmax * hs, 128, 0, st>>>(e, f, mp);
+    SVDUP_COUNT_LAUNCH();
+    k_mix_pack_T<<<dim3(mp.ntT, mp.kphi), 256, 0, st>>>(f, mp);
+    SVDUP_COUNT_LAUNCH();
+    k_mix_pack_L<<<mp.Lmax + 1, 256, 0, st>>>(f, mp);
+    SVDUP_COUNT_LAUNCH();
+  }
+  k_mix_pack_C<<<dim3(mp.Lmax + 1, mp.Lmax, hs), 256, 0, st>>>(e, f, mp);
+  SVDUP_COUNT_LAUNCH();
+}
+
+void launch_mix_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, MixPlan mp, OutMap om,
+                      int dense, int* status) {
+  if (stage == 0) {
+    if (dense) return;
+    launch_umma<MS_P2M, 64>(st, dim3(mp.rt, mp.kphi), e, f, mp, om, dense, status);
+  } else if (stage == 1) {
+    if (dense) return;
+    launch_umma<MS_M2L, 128>(st, dim3(mp.rt, mp.ntT), e, f, mp, om, dense, status);
+  } else {
+    launch_umma<MS_OUT, 128>(st, dim3(mp.rt, mp.Lmax + 1), e, f, mp, om, dense, status);
+  }
+}
+
+void launch_mix_flop_count(cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int dense,
+                           double* acc) {
+  k_mix_flops<<<1, 32, 0, st>>>(e, f, mp, dense, acc);
+  SVDUP_COUNT_LAUNCH();
+}
+
+}  // namespace svdup

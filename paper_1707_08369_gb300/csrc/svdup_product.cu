@@ -26,28 +26,121 @@
 namespace svdup {
 
 extern long long g_launch_count;
-#define SVDUP_COUNT_LAUNCH() (++g_launch_count)
 
 // ---------------------------------------------------------------------------
 // Deflation rotations applied to the columns of X (in place): X <- X G_1^T ... G_r^T,
-// i.e. each row of X transforms like z^T.  One thread per row.
+// i.e. each row of X transforms like z^T.  Rotation i acts on columns (a_i, b_i) with
+// (cos, sin) = (c_i, s_i); the deflation walk makes each rotation either open a chain
+// (a_i untouched so far) or continue the previous one (a_i = b_{i-1}, the chain's
+// carrier).  Per row, with x the ORIGINAL column values (no column is read after it is
+// written), the carrier follows the affine recurrence
+//     v_i = s_i u_i + c_i x_{b_i},   u_i = chained ? v_{i-1} : x_{a_i},
+// and the outputs are  X[a_i] = c_i u_i - s_i x_{b_i}  and, at a chain's end,
+// X[b_i] = v_i.  The rotation list is cut into chunks of kRotChunk: pass 1 composes
+// each chunk's map v_out = A v_in + B (per row), pass 2 carries v across the chunks,
+// pass 3 replays each chunk from its carry and writes.  The only column shared by two
+// chunks is the last b of a chunk that the next chunk overwrites as its first a; pass 1
+// saves its original value so pass 3 never reads it back.  Scratch: rows x chunks x 3.
 // ---------------------------------------------------------------------------
-__global__ void k_rotate_columns(Eig e, double* X, long long ldx, int rows) {
+constexpr int kRotChunk = 64;
+
+__global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __restrict__ X,
+                                                     long long ldx, int rows, double* rotw) {
+  __shared__ long long sa[kRotChunk], sb[kRotChunk];
+  __shared__ double sc[kRotChunk], ss[kRotChunk];
+  __shared__ int sch[kRotChunk];
   const int nr = e.nrot[0];
-  if (nr == 0) return;
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ch = blockIdx.y, c0 = ch * kRotChunk;
+  if (c0 >= nr) return;
+  const int cn = min(kRotChunk, nr - c0);
+  for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+    const int g = c0 + i;
+    sa[i] = (long long)e.perm[e.rj[g]] * ldx;
+    sb[i] = (long long)e.perm[e.ri[g]] * ldx;
+    sc[i] = e.rc[g];
+    ss[i] = e.rs[g];
+    sch[i] = (g > 0 && e.rj[g] == e.ri[g - 1]) ? 1 : 0;
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
-  for (int i = 0; i < nr; i++) {
-    long long ca = e.perm[e.rj[i]], cb = e.perm[e.ri[i]];
-    double c = e.rc[i], sn = e.rs[i];
-    double xa = X[r + ca * ldx], xb = X[r + cb * ldx];
-    X[r + ca * ldx] = c * xa - sn * xb;
-    X[r + cb * ldx] = sn * xa + c * xb;
+  double A = 1.0, B = 0.0, xlast = 0.0;
+  for (int i = 0; i < cn; i++) {
+    const double xb = X[r + sb[i]];
+    if (sch[i]) {  // v = s (A v_in + B) + c xb
+      A = ss[i] * A;
+      B = fma(ss[i], B, sc[i] * xb);
+    } else {
+      const double xa = X[r + sa[i]];
+      A = 0.0;
+      B = fma(ss[i], xa, sc[i] * xb);
+    }
+    xlast = xb;
+  }
+  const size_t nch = gridDim.y;
+  double* w = rotw + ((size_t)r * nch + ch) * 3;
+  w[0] = A;
+  w[1] = B;
+  w[2] = xlast;
+}
+
+__global__ void k_rot_carry(Eig e, int rows, int nch, double* rotw) {
+  const int nr = e.nrot[0];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows || nr == 0) return;
+  const int used = (nr + kRotChunk - 1) / kRotChunk;
+  double v = 0.0;
+  for (int ch = 0; ch < used; ch++) {
+    double* w = rotw + ((size_t)r * nch + ch) * 3;
+    const double A = w[0], B = w[1];
+    w[0] = v;  // the carrier entering this chunk
+    v = fma(A, v, B);
   }
 }
 
-void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows) {
-  k_rotate_columns<<<(rows + 63) / 64, 64, 0, st>>>(e, X, ldx, rows);
+__global__ void __launch_bounds__(128) k_rot_apply(Eig e, double* X, long long ldx, int rows,
+                                                   const double* __restrict__ rotw) {
+  __shared__ long long sa[kRotChunk], sb[kRotChunk];
+  __shared__ double sc[kRotChunk], ss[kRotChunk];
+  __shared__ int sch[kRotChunk], send[kRotChunk];
+  const int nr = e.nrot[0];
+  const int ch = blockIdx.y, c0 = ch * kRotChunk;
+  if (c0 >= nr) return;
+  const int cn = min(kRotChunk, nr - c0);
+  for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+    const int g = c0 + i;
+    sa[i] = (long long)e.perm[e.rj[g]] * ldx;
+    sb[i] = (long long)e.perm[e.ri[g]] * ldx;
+    sc[i] = e.rc[g];
+    ss[i] = e.rs[g];
+    sch[i] = (g > 0 && e.rj[g] == e.ri[g - 1]) ? 1 : 0;
+    send[i] = (g + 1 >= nr || e.rj[g + 1] != e.ri[g]) ? 1 : 0;  // the chain ends here
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const size_t nch = gridDim.y;
+  const double* w = rotw + ((size_t)r * nch + ch) * 3;
+  double v = w[0];
+  const double xlast = w[2];
+  for (int i = 0; i < cn; i++) {
+    const double xb = (i == cn - 1) ? xlast : X[r + sb[i]];
+    const double u = sch[i] ? v : X[r + sa[i]];
+    X[r + sa[i]] = sc[i] * u - ss[i] * xb;
+    v = fma(ss[i], u, sc[i] * xb);
+    if (send[i]) X[r + sb[i]] = v;
+  }
+}
+
+void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
+                           double* rotw) {
+  const int nch = (e.N + kRotChunk - 1) / kRotChunk;
+  dim3 g((rows + 127) / 128, nch);
+  k_rot_compose<<<g, 128, 0, st>>>(e, X, ldx, rows, rotw);
+  SVDUP_COUNT_LAUNCH();
+  k_rot_carry<<<(rows + 127) / 128, 128, 0, st>>>(e, rows, nch, rotw);
+  SVDUP_COUNT_LAUNCH();
+  k_rot_apply<<<g, 128, 0, st>>>(e, X, ldx, rows, rotw);
   SVDUP_COUNT_LAUNCH();
 }
 

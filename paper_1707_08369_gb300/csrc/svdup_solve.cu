@@ -14,7 +14,6 @@
 namespace svdup {
 
 extern long long g_launch_count;
-#define SVDUP_COUNT_LAUNCH() (++g_launch_count)
 
 // ---------------------------------------------------------------------------
 // Alg. 6.1 STEP 1.  The paper forms btilde = U S V^T b and atilde = V S^T U^T a and
@@ -205,15 +204,76 @@ void launch_fill_generic(cudaStream_t st, Eig e, const double* d, const double* 
 //           removed when the dropped coupling |(d_s - d_j) c s| <= tol.
 //  (The paper's case (2), |abar| = 1, is the special case of (1) where z is a unit
 //  coordinate vector.)  tol = 8 u max(max|d|, |rho| ||z||^2).
-// One block.  Reductions and case (1) run in parallel; the case-(3) scan is a
-// sequential pass by one thread (each rotation changes the next comparison);
-// compaction of the kept set is a block-wide prefix sum.  An optional vector y
-// (a second direction in the same sorted basis) is rotated alongside z.
+// One block.  Reductions, case (1) and the compaction of its survivors run in
+// parallel.  Case (3) on consecutive survivors (i-1, i): a rotation merges pole i-1
+// into pole i, and the next pair (i, i+1) sees the merged values.  Along a run of
+// merges starting at i0 the carrier after i holds
+//     z~_i^2 = sum_{t=i0..i} z_t^2   and   d~_i = sum z_t^2 d_t / z~_i^2
+// (each Givens step is a z^2-weighted mean), so the sequential test reduces to
+//     |d_i - d~_{i-1}| |z_i| z~_{i-1} <= tol (z~_{i-1}^2 + z_i^2).
+// One thread walks the survivors on shared-memory copies with just these two running
+// sums to find where runs start and end; only pairs that pass with the original values
+// (a bitmask found in parallel) can start a run.  The rotation records (position pair,
+// cos, sin) and the merged values are then formed in parallel from segmented prefix
+// sums of z^2 and z^2 d over the runs.  This is the Bunch-Nielsen-Sorensen deflation
+// in exact arithmetic; only the rounding of the merged values differs from applying
+// the rotations one at a time.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_deflate(Eig e, double* yvec, int* status) {
+constexpr int kDeflateThreads = 1024;
+
+// Dynamic shared memory of k_deflate: two bitmasks, plus the survivors' d, z and
+// positions when they fit.
+static size_t deflate_smem(int N, int* in_smem) {
+  size_t words = (size_t)(N + 31) / 32;
+  size_t masks = 2 * words * sizeof(unsigned);
+  size_t arrays = (size_t)N * (2 * sizeof(double) + sizeof(int));
+  size_t total = ((masks + 15) & ~(size_t)15) + arrays;
+  if (total <= 192 * 1024) { *in_smem = 1; return total; }
+  *in_smem = 0;
+  return masks;
+}
+
+// First index i in [from, n) whose bit is set in mask, else n.
+__device__ __forceinline__ int next_set(const unsigned* mask, int from, int n) {
+  if (from >= n) return n;
+  int w = from >> 5;
+  const int nw = (n + 31) >> 5;
+  unsigned m = mask[w] & (0xffffffffu << (from & 31));
+  while (m == 0u) {
+    if (++w >= nw) return n;
+    m = mask[w];
+  }
+  int i = (w << 5) + __ffs(m) - 1;
+  return i < n ? i : n;
+}
+
+__device__ __forceinline__ bool bit_at(const unsigned* mask, int i) {
+  return (mask[i >> 5] >> (i & 31)) & 1u;
+}
+
+// Block-wide exclusive prefix sum of one int per thread (Hillis-Steele over scnt);
+// returns the exclusive prefix and writes the total to *total.
+__device__ int block_excl_scan(int v, int* scnt, int* total) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  scnt[tid] = v;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    int u = tid >= off ? scnt[tid - off] : 0;
+    __syncthreads();
+    scnt[tid] += u;
+    __syncthreads();
+  }
+  int incl = scnt[tid];
+  *total = scnt[nt - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status, int in_smem) {
+  extern __shared__ double dsm[];
   __shared__ double sred[2][32];
-  __shared__ int scnt[1024];
-  __shared__ int s_ncand;
+  __shared__ int scnt[kDeflateThreads];
+  __shared__ double sW[kDeflateThreads], sM[kDeflateThreads];
   __shared__ double s_tol, s_zn;
   const int N = e.N;
   const double rho = e.rhop[0];
@@ -244,112 +304,140 @@ __global__ void __launch_bounds__(1024) k_deflate(Eig e, double* yvec, int* stat
   }
   __syncthreads();
   const double tol = s_tol, zn = s_zn;
-  // thread t owns the contiguous chunk [b0, b1)
+  const int nwords = (N + 31) >> 5;
+  unsigned* cmask = (unsigned*)dsm;   // pair (i-1, i) passes with the original values
+  unsigned* pmask = cmask + nwords;   // pair (i-1, i) merged: i continues the run of i-1
+  double* kd;
+  double* kz;
+  int* kpos;
+  if (in_smem) {
+    char* base = (char*)dsm + (((size_t)2 * nwords * sizeof(unsigned) + 15) & ~(size_t)15);
+    kd = (double*)base;
+    kz = kd + N;
+    kpos = (int*)(kz + N);
+  } else {  // global scratch that the compaction below overwrites anyway
+    kd = e.dk;
+    kz = e.zk;
+    kpos = e.idx;
+  }
+  for (int w = tid; w < 2 * nwords; w += nt) cmask[w] = 0u;
+  // case (1) on my contiguous chunk [b0, b1), then the survivors' positions in order
   const int chunk = (N + nt - 1) / nt;
   const int b0 = min(N, tid * chunk), b1 = min(N, b0 + chunk);
-  // case (1), and the last kept position of my chunk
-  int last = -1;
+  int cnt = 0;
   for (int s = b0; s < b1; s++) {
     int d1 = (rho == 0.0 || fabs(rho) * zn * fabs(e.zs[s]) <= tol) ? 1 : 0;
     e.defl[s] = d1;
-    if (!d1) last = s;
+    cnt += !d1;
   }
-  // prefix max of "last kept" over chunks -> previous kept position before my chunk
-  scnt[tid] = last;
-  __syncthreads();
-  for (int off = 1; off < nt; off <<= 1) {
-    int v = tid >= off ? scnt[tid - off] : -1;
-    __syncthreads();
-    scnt[tid] = max(scnt[tid], v);
-    __syncthreads();
-  }
-  int prev = tid > 0 ? scnt[tid - 1] : -1;
-  __syncthreads();
-  // Case (3) in parallel with the original values: pair (j, s) with j the previous kept
-  // position.  e.idx holds j for every kept s and e.didx the candidate list (both are
-  // scratch until the compaction below).  The sequential order only matters where a
-  // rotation changed (d_j, z_j) of the left partner: one thread walks the candidates
-  // and, after each rotation, the chain's next kept position.
-  int ncand = 0;
+  int nk;
+  int pos = block_excl_scan(cnt, scnt, &nk);
   for (int s = b0; s < b1; s++) {
     if (e.defl[s]) continue;
-    e.idx[s] = prev;
-    if (prev >= 0) {
-      double zj = e.zs[prev], zs = e.zs[s];
-      double r = hypot(zj, zs);
-      if (fabs((e.ds[s] - e.ds[prev]) * (zs / r) * (zj / r)) <= tol) ncand++;
-    }
-    prev = s;
-  }
-  scnt[tid] = ncand;
-  __syncthreads();
-  for (int off = 1; off < nt; off <<= 1) {
-    int v = tid >= off ? scnt[tid - off] : 0;
-    __syncthreads();
-    scnt[tid] += v;
-    __syncthreads();
-  }
-  if (tid == nt - 1) s_ncand = scnt[nt - 1];
-  int cpos = scnt[tid] - ncand;
-  for (int s = b0; s < b1; s++) {
-    if (e.defl[s]) continue;
-    int j = e.idx[s];
-    if (j >= 0) {
-      double zj = e.zs[j], zs = e.zs[s];
-      double r = hypot(zj, zs);
-      if (fabs((e.ds[s] - e.ds[j]) * (zs / r) * (zj / r)) <= tol) e.didx[cpos++] = s;
-    }
+    kpos[pos] = s;
+    kd[pos] = e.ds[s];
+    kz[pos] = e.zs[s];
+    pos++;
   }
   __syncthreads();
+  // case (3) pre-test with the original values
+  for (int i = 1 + tid; i < nk; i += nt) {
+    double zj = kz[i - 1], zi = kz[i];
+    if (fabs(kd[i] - kd[i - 1]) * fabs(zi * zj) <= tol * fma(zi, zi, zj * zj))
+      atomicOr(&cmask[i >> 5], 1u << (i & 31));
+  }
+  __syncthreads();
+  // the walk: run boundaries from the running sums W = z~^2, M = W d~
   if (tid == 0) {
-    const int nc = s_ncand;
-    int nr = 0, c = 0;
-    int s = nc > 0 ? e.didx[c++] : -1;
-    while (s >= 0) {
-      int j = e.idx[s];
-      double zj = e.zs[j], zs = e.zs[s];
-      double r = hypot(zj, zs);
-      double cs = zs / r, sn = zj / r;
-      double dj = e.ds[j], dsv = e.ds[s];
-      int chain = -1;
-      if (fabs((dsv - dj) * cs * sn) <= tol) {
-        e.ds[j] = cs * cs * dj + sn * sn * dsv;
-        e.ds[s] = sn * sn * dj + cs * cs * dsv;
-        e.zs[j] = 0.0;
-        e.zs[s] = r;
-        e.defl[j] = 1;
-        if (yvec) {
-          double yj = yvec[j], ys = yvec[s];
-          yvec[j] = cs * yj - sn * ys;
-          yvec[s] = sn * yj + cs * ys;
-        }
-        e.rj[nr] = j; e.ri[nr] = s; e.rc[nr] = cs; e.rs[nr] = sn;
-        nr++;
-        int nx = s + 1;  // the next kept position now pairs with the rotated s
-        while (nx < N && e.defl[nx]) nx++;
-        if (nx < N) chain = nx;
+    int i = next_set(cmask, 1, nk);
+    double W = 0.0, M = 0.0;
+    bool run = false;
+    while (i < nk) {
+      if (!run) {
+        double zj = kz[i - 1];
+        W = zj * zj;
+        M = W * kd[i - 1];
       }
-      while (c < nc && e.didx[c] <= s) c++;
-      if (chain >= 0) s = chain;
-      else s = (c < nc) ? e.didx[c++] : -1;
+      const double zi = kz[i], di = kd[i], zi2 = zi * zi;
+      if (fabs(fma(di, W, -M)) * fabs(zi) * sqrt(W) <= tol * W * (W + zi2)) {
+        pmask[i >> 5] |= 1u << (i & 31);
+        W += zi2;
+        M = fma(zi2, di, M);
+        run = true;
+        i = i + 1;  // the next survivor now pairs with the carrier
+      } else {
+        run = false;
+        i = next_set(cmask, i + 1, nk);
+      }
     }
-    e.nrot[0] = nr;
+  }
+  __syncthreads();
+  // segmented sums over the runs, thread t owning survivors [c0, c1)
+  const int cpt = (nk + nt - 1) / nt;
+  const int c0 = min(nk, tid * cpt), c1 = min(nk, c0 + cpt);
+  {
+    double lW = 0.0, lM = 0.0;
+    int lflag = 0, lrot = 0;
+    for (int i = c0; i < c1; i++) {
+      const double z2 = kz[i] * kz[i];
+      if (!bit_at(pmask, i)) { lflag = 1; lW = z2; lM = z2 * kd[i]; }
+      else { lW += z2; lM = fma(z2, kd[i], lM); lrot++; }
+    }
+    int nrot;
+    const int rbase = block_excl_scan(lrot, scnt, &nrot);
+    // inclusive segmented scan of (flag, W, M) over the chunks
+    scnt[tid] = lflag;
+    sW[tid] = lW;
+    sM[tid] = lM;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+      int f2 = 0;
+      double W2 = 0.0, M2 = 0.0;
+      if (tid >= off) { f2 = scnt[tid - off]; W2 = sW[tid - off]; M2 = sM[tid - off]; }
+      __syncthreads();
+      if (tid >= off && !scnt[tid]) { sW[tid] += W2; sM[tid] += M2; scnt[tid] = f2; }
+      __syncthreads();
+    }
+    double W = tid > 0 ? sW[tid - 1] : 0.0;  // the run through survivor c0 - 1
+    double M = tid > 0 ? sM[tid - 1] : 0.0;
+    int ridx = rbase;
+    for (int i = c0; i < c1; i++) {
+      const bool p = bit_at(pmask, i);
+      const double zi = kz[i], di = kd[i], z2 = zi * zi;
+      if (!p) {
+        W = z2;
+        M = z2 * di;
+      } else {
+        // rotation merging survivor i-1 (the carrier) into i
+        const double zprev = bit_at(pmask, i - 1) ? sqrt(W) : kz[i - 1];  // signed at a run start
+        const double Wn = W + z2;
+        const double rn = sqrt(Wn);
+        const double cs = zi / rn, sn = zprev / rn;
+        const double dprev = M / W;
+        const int pj = kpos[i - 1], pi = kpos[i];
+        e.ds[pj] = cs * cs * dprev + sn * sn * di;
+        e.zs[pj] = 0.0;
+        e.defl[pj] = 1;
+        e.rj[ridx] = pj; e.ri[ridx] = pi; e.rc[ridx] = cs; e.rs[ridx] = sn;
+        ridx++;
+        W = Wn;
+        M = fma(z2, di, M);
+      }
+      if (!(i + 1 < nk && bit_at(pmask, i + 1))) {  // not merged away by the next pair
+        const int ps = kpos[i];
+        if (p) { e.ds[ps] = M / W; e.zs[ps] = sqrt(W); }
+        else { e.ds[ps] = di; e.zs[ps] = zi; }
+      }
+    }
+    if (tid == 0) e.nrot[0] = nrot;
   }
   __syncthreads();
   // compaction of the kept set
-  int cnt = 0;
+  cnt = 0;
   for (int s = b0; s < b1; s++) cnt += !e.defl[s];
-  scnt[tid] = cnt;
-  __syncthreads();
-  for (int off = 1; off < nt; off <<= 1) {  // inclusive Hillis-Steele scan
-    int v = tid >= off ? scnt[tid - off] : 0;
-    __syncthreads();
-    scnt[tid] += v;
-    __syncthreads();
-  }
-  int kk = scnt[nt - 1];
-  int pos = scnt[tid] - cnt;       // kept entries before my chunk
-  int dpos = b0 - pos;             // deflated entries before my chunk
+  int kk;
+  pos = block_excl_scan(cnt, scnt, &kk);  // kept entries before my chunk
+  int dpos = b0 - pos;                     // deflated entries before my chunk
   for (int s = b0; s < b1; s++) {
     if (!e.defl[s]) {
       e.idx[pos] = s;
@@ -376,8 +464,12 @@ __global__ void __launch_bounds__(1024) k_deflate(Eig e, double* yvec, int* stat
   }
 }
 
-void launch_deflate(cudaStream_t st, Eig e, double* yvec, int* status) {
-  k_deflate<<<1, 1024, 0, st>>>(e, yvec, status);
+void launch_deflate(cudaStream_t st, Eig e, int* status) {
+  int in_smem = 0;
+  size_t smem = deflate_smem(e.N, &in_smem);
+  // static (about 21 KB) plus dynamic shared memory may pass the 48 KB default
+  cudaFuncSetAttribute(k_deflate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_deflate<<<1, kDeflateThreads, smem, st>>>(e, status, in_smem);
   SVDUP_COUNT_LAUNCH();
 }
 
@@ -421,10 +513,187 @@ __device__ __forceinline__ SecSums secular_sums(const double* __restrict__ dc,
   return r;
 }
 
-// One root in the rho > 0 orientation; returns 0 on convergence.
-__device__ int secular_root(const double* __restrict__ dc, const double* __restrict__ z2c, int k,
-                            double R, double zn2, int j, int lane, int maxit, int* o_out,
-                            double* tau_out) {
+struct DirectSums {
+  const double* dc;
+  const double* z2c;
+  int k;
+  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
+    return secular_sums(dc, z2c, k, o, tau, jsplit, lane);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Far-field evaluation of the secular sums (this contests the paper's remark in
+// Sec. 3.1 that the FMM cannot serve the secular equation because the roots are
+// unknown: the SOURCES, the poles with weights z_i^2, are fixed, so their far field
+// is a fixed function of mu that can be sampled once).
+// The roots j in [64 b, min(64 b + 64, k - 1)) all lie in box b = [d_{64b}, d_{j1}],
+// j1 = min(64 b + 64, k - 1), of half width r and centre c.  Poles within 3 r of c,
+// and those of leaves b-1..b+1, are the near field and are summed directly with the
+// offsets, as in the direct sums.  The rest lie outside [c - 3r, c + 3r]; their four
+// sums (psi and psi' of the poles left of the box, the same right of it) are analytic
+// on the box and are interpolated on kSqP Chebyshev nodes of the first kind
+// (App. D STEP 3) with the barycentric formula.  The interpolation error is below
+// 10 * 5^-kSqP of the far terms' magnitude (a pole 3 r from the centre lies outside
+// the Bernstein ellipse of parameter 5), under the FP64 rounding of the sums.
+// Coordinates are measured from the pole d_{64b}, so every difference keeps relative
+// accuracy however far the box sits from zero.  The last root (beyond every pole) is
+// always summed directly.
+// ---------------------------------------------------------------------------
+constexpr int kSqLeaf = 64;
+constexpr int kSqP = 26;
+constexpr int kSqMinK = 1024;  // smaller problems use the direct sums only
+
+__device__ __forceinline__ int lower_bound_d(const double* a, int n, double v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Boxes: sqb[2b] = d_{64b} (the coordinate origin), sqb[2b+1] = r; sqn[2b], sqn[2b+1] =
+// the near pole range [n0, n1).
+__global__ void k_sq_boxes(const double* __restrict__ dc, const int* __restrict__ kp, double* sqb,
+                           int* sqn) {
+  const int k = kp[0];
+  if (k < kSqMinK) return;
+  const int nb = (k - 1 + kSqLeaf - 1) / kSqLeaf;
+  const int nleaf = (k + kSqLeaf - 1) / kSqLeaf;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    const int j0 = b * kSqLeaf, j1 = min(j0 + kSqLeaf, k - 1);
+    const double lo = dc[j0], hi = dc[j1];
+    const double r = 0.5 * (hi - lo);
+    const int t_lo = lower_bound_d(dc, k, lo - 2.0 * r);     // first pole >= c - 3r
+    const int t_hi = lower_bound_d(dc, k, hi + 2.0 * r);     // first pole >= c + 3r
+    int a_lo = min(b - 1, t_lo / kSqLeaf);
+    a_lo = max(a_lo, 0);
+    int a_hi = max(b + 1, t_hi / kSqLeaf);                   // leaf of the first pole past it
+    a_hi = min(a_hi, nleaf - 1);
+    sqb[2 * b] = lo;
+    sqb[2 * b + 1] = r;
+    sqn[2 * b] = a_lo * kSqLeaf;
+    sqn[2 * b + 1] = min(k, (a_hi + 1) * kSqLeaf);
+  }
+}
+
+// Far sums at the Chebyshev nodes of each box: sqv[(4 b + q) kSqP + beta] for q = psi_L,
+// psi_L', psi_R, psi_R'.  One warp per (box, node).
+__global__ void k_sq_nodes(const double* __restrict__ dc, const double* __restrict__ z2c,
+                           const int* __restrict__ kp, const double* __restrict__ sqb,
+                           const int* __restrict__ sqn, double* sqv) {
+  const int k = kp[0];
+  if (k < kSqMinK) return;
+  const int nb = (k - 1 + kSqLeaf - 1) / kSqLeaf;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nb * kSqP; w += warps) {
+    const int b = w / kSqP, beta = w - b * kSqP;
+    const double base = sqb[2 * b], r = sqb[2 * b + 1];
+    const int n0 = sqn[2 * b], n1 = sqn[2 * b + 1];
+    const double yo = r * (1.0 + cospi((2.0 * beta + 1.0) / (2.0 * kSqP)));
+    double pL = 0.0, dL = 0.0, pR = 0.0, dR = 0.0;
+    for (int t = lane; t < n0; t += 32) {
+      double del = (dc[t] - base) - yo;
+      double rc = rcp64(del);
+      double tt = z2c[t] * rc;
+      pL += tt;
+      dL = fma(tt, rc, dL);
+    }
+    for (int t = n1 + lane; t < k; t += 32) {
+      double del = (dc[t] - base) - yo;
+      double rc = rcp64(del);
+      double tt = z2c[t] * rc;
+      pR += tt;
+      dR = fma(tt, rc, dR);
+    }
+    pL = warp_sum(pL);
+    dL = warp_sum(dL);
+    pR = warp_sum(pR);
+    dR = warp_sum(dR);
+    if (lane == 0) {
+      double* v = sqv + (size_t)4 * b * kSqP;
+      v[beta] = pL;
+      v[kSqP + beta] = dL;
+      v[2 * kSqP + beta] = pR;
+      v[3 * kSqP + beta] = dR;
+    }
+  }
+}
+
+struct FarSums {
+  const double* dc;
+  const double* z2c;
+  int n0, n1;
+  double base, r;
+  const double* vals;  // 4 x kSqP node values of this box
+  const double* sx;    // Chebyshev nodes (shared memory)
+  const double* sw;    // barycentric weights (shared memory)
+  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
+    SecSums s = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const double dO = dc[o];
+    for (int i = n0 + lane; i < n1; i += 32) {
+      double del = (dc[i] - dO) - tau;
+      double rc = rcp64(del);
+      double t = z2c[i] * rc;
+      double dt = t * rc;
+      if (i <= jsplit) { s.psiL += t; s.dpsiL += dt; }
+      else { s.psiR += t; s.dpsiR += dt; }
+      s.asum += fabs(t);
+    }
+    s.psiL = warp_sum(s.psiL);
+    s.dpsiL = warp_sum(s.dpsiL);
+    s.psiR = warp_sum(s.psiR);
+    s.dpsiR = warp_sum(s.dpsiR);
+    s.asum = warp_sum(s.asum);
+    // barycentric interpolation at the box coordinate of mu
+    const double yh = (((dO - base) + tau) - r) / r;
+    double c = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0, f3 = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int hit = 0;
+    if (lane < kSqP) {
+      v0 = vals[lane];
+      v1 = vals[kSqP + lane];
+      v2 = vals[2 * kSqP + lane];
+      v3 = vals[3 * kSqP + lane];
+      const double df = yh - sx[lane];
+      if (df == 0.0) {
+        hit = 1;
+      } else {
+        c = sw[lane] / df;
+        f0 = c * v0; f1 = c * v1; f2 = c * v2; f3 = c * v3;
+      }
+    }
+    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+    double pL, dL, pR, dR;
+    if (hm) {  // mu sits exactly on a node
+      const int src = __ffs(hm) - 1;
+      pL = __shfl_sync(0xffffffffu, v0, src);
+      dL = __shfl_sync(0xffffffffu, v1, src);
+      pR = __shfl_sync(0xffffffffu, v2, src);
+      dR = __shfl_sync(0xffffffffu, v3, src);
+    } else {
+      const double den = warp_sum(c);
+      pL = warp_sum(f0) / den;
+      dL = warp_sum(f1) / den;
+      pR = warp_sum(f2) / den;
+      dR = warp_sum(f3) / den;
+    }
+    s.psiL += pL;   // far-left terms are negative, far-right positive
+    s.dpsiL += dL;
+    s.psiR += pR;
+    s.dpsiR += dR;
+    s.asum += pR - pL;
+    return s;
+  }
+};
+
+// One root in the rho > 0 orientation; returns 0 on convergence.  `sums` evaluates the
+// split sums of w at mu = d_o + tau (DirectSums or FarSums).
+template <class Sums>
+__device__ int secular_root(const Sums& sums, const double* __restrict__ dc,
+                            const double* __restrict__ z2c, int k, double R, double zn2, int j,
+                            int lane, int maxit, int* o_out, double* tau_out) {
   int o;
   double tau, lo, hi, aL, aR;
   SecSums sm;
@@ -434,7 +703,7 @@ __device__ int secular_root(const double* __restrict__ dc, const double* __restr
     double gap = dc[j + 1] - dc[j];
     o = j;
     tau = 0.5 * gap;
-    sm = secular_sums(dc, z2c, k, o, tau, j, lane);
+    sm = sums(o, tau, j, lane);
     w = 1.0 + R * (sm.psiL + sm.psiR);
     if (w >= 0.0) {  // root in (d_j, midpoint]
       o = j; lo = 0.0; hi = tau; aL = 0.0; aR = gap;
@@ -448,7 +717,7 @@ __device__ int secular_root(const double* __restrict__ dc, const double* __restr
     tau = 0.5 * hi;
     aL = (k >= 2) ? (dc[k - 2] - dc[k - 1]) : 0.0;
     aR = 0.0;
-    sm = secular_sums(dc, z2c, k, o, tau, j, lane);
+    sm = sums(o, tau, j, lane);
     w = 1.0 + R * (sm.psiL + sm.psiR);
     if (w < 0.0) lo = tau; else hi = tau;
   }
@@ -492,7 +761,7 @@ __device__ int secular_root(const double* __restrict__ dc, const double* __restr
       *o_out = o; *tau_out = tn; return 0;
     }
     tau = tn;
-    sm = secular_sums(dc, z2c, k, o, tau, last ? k - 1 : j, lane);
+    sm = sums(o, tau, last ? k - 1 : j, lane);
     w = 1.0 + R * (sm.psiL + sm.psiR);
     if (w < 0.0) lo = tau; else hi = tau;
     if (!(hi - lo > 2.0 * kU * fmax(fabs(lo), fabs(hi)))) { *o_out = o; *tau_out = tau; return 0; }
@@ -507,24 +776,42 @@ __device__ int secular_root(const double* __restrict__ dc, const double* __restr
 __global__ void k_secular(const double* __restrict__ dc, const double* __restrict__ z2c,
                           const int* __restrict__ kp, const double* __restrict__ rhop,
                           const double* __restrict__ dk, int* orgc, double* tauc, int* org,
-                          double* tau, double* dorg, int* status, int maxit) {
+                          double* tau, double* dorg, int* status, int maxit,
+                          const double* __restrict__ sqb, const int* __restrict__ sqn,
+                          const double* __restrict__ sqv) {
   __shared__ double s_zn2;
+  __shared__ double s_x[kSqP], s_w[kSqP];
   const int k = kp[0];
   const double rho = rhop[0];
   const double R = fabs(rho);
+  const bool far = sqv != nullptr && k >= kSqMinK;
   if (threadIdx.x < 32) {
     double a = 0.0;
     for (int i = threadIdx.x; i < k; i += 32) a += z2c[i];
     a = warp_sum(a);
     if (threadIdx.x == 0) s_zn2 = a;
   }
+  if (threadIdx.x < kSqP) {  // Chebyshev nodes and barycentric weights (first kind)
+    const double th = (2.0 * threadIdx.x + 1.0) / (2.0 * kSqP);
+    s_x[threadIdx.x] = cospi(th);
+    s_w[threadIdx.x] = (threadIdx.x & 1 ? -1.0 : 1.0) * sinpi(th);
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
+  const DirectSums direct = {dc, z2c, k};
   for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < k; j += warps) {
     int o;
     double t;
-    int bad = secular_root(dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
+    int bad;
+    if (far && j < k - 1) {
+      const int b = j / kSqLeaf;
+      const FarSums fs = {dc, z2c, sqn[2 * b], sqn[2 * b + 1], sqb[2 * b], sqb[2 * b + 1],
+                          sqv + (size_t)4 * b * kSqP, s_x, s_w};
+      bad = secular_root(fs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
+    } else {
+      bad = secular_root(direct, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
+    }
     if (lane == 0) {
       if (bad) latch(status, SVDUP_ENOCONV);
       if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
@@ -551,8 +838,19 @@ static int secular_blocks(int N) {
 }
 
 void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
+  const double* sqv = nullptr;
+  if (e.sqv && e.N >= kSqMinK) {  // far-field set-up (the kernels skip small k themselves)
+    const int nb = (e.N + kSqLeaf - 1) / kSqLeaf;
+    k_sq_boxes<<<(nb + 127) / 128, 128, 0, st>>>(e.dc, e.kp, e.sqb, e.sqn);
+    SVDUP_COUNT_LAUNCH();
+    const int nw = nb * kSqP;
+    k_sq_nodes<<<(nw * 32 + 255) / 256, 256, 0, st>>>(e.dc, e.z2c, e.kp, e.sqb, e.sqn, e.sqv);
+    SVDUP_COUNT_LAUNCH();
+    sqv = e.sqv;
+  }
   k_secular<<<secular_blocks(e.N), 256, 0, st>>>(e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc,
-                                                e.org, e.tau, e.dorg, status, maxit);
+                                                e.org, e.tau, e.dorg, status, maxit, e.sqb,
+                                                e.sqn, sqv);
   SVDUP_COUNT_LAUNCH();
 }
 
@@ -720,24 +1018,62 @@ void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_fin
 // order, then the transposed Cauchy product (k_norms with y).  Q x: Cauchy product,
 // deflated entries copied, rotations transposed in reverse order, scatter.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_gather_rotate(Eig e, const double* __restrict__ xphys,
-                                                        double* ysorted) {
-  for (int s = threadIdx.x; s < e.N; s += blockDim.x) ysorted[s] = xphys[e.perm[s]];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int nr = e.nrot[0];
-    for (int r = 0; r < nr; r++) {
-      int a = e.rj[r], b = e.ri[r];
-      double c = e.rc[r], sn = e.rs[r];
-      double ya = ysorted[a], yb = ysorted[b];
-      ysorted[a] = c * ya - sn * yb;
-      ysorted[b] = sn * ya + c * yb;
+// The vector lives in shared memory while one thread applies the rotations in order
+// (global scratch `ysorted` itself when N is too large for shared memory).
+static size_t vec_smem(int N) {
+  size_t b = (size_t)N * sizeof(double);
+  return b <= 160 * 1024 ? b : 0;
+}
+
+// One thread applies the rotations in order; the rotation records are staged through
+// shared memory in chunks so that its loop touches shared memory only.
+constexpr int kVecRotChunk = 1024;
+
+__device__ void rotate_vector_serial(const Eig& e, double* v, bool transpose) {
+  __shared__ int sa[kVecRotChunk], sb[kVecRotChunk];
+  __shared__ double sc[kVecRotChunk], ss[kVecRotChunk];
+  const int nr = e.nrot[0];
+  for (int c0 = 0; c0 < nr; c0 += kVecRotChunk) {
+    const int cn = min(kVecRotChunk, nr - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+      const int g = transpose ? nr - 1 - (c0 + i) : c0 + i;
+      sa[i] = e.rj[g]; sb[i] = e.ri[g]; sc[i] = e.rc[g]; ss[i] = e.rs[g];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < cn; i++) {
+        const int a = sa[i], b = sb[i];
+        const double c = sc[i], sn = ss[i];
+        const double va = v[a], vb = v[b];
+        if (!transpose) {
+          v[a] = c * va - sn * vb;
+          v[b] = sn * va + c * vb;
+        } else {
+          v[a] = c * va + sn * vb;
+          v[b] = -sn * va + c * vb;
+        }
+      }
     }
   }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_gather_rotate(Eig e, const double* __restrict__ xphys,
+                                                        double* ysorted, int in_smem) {
+  extern __shared__ double vsm[];
+  double* v = in_smem ? vsm : ysorted;
+  for (int s = threadIdx.x; s < e.N; s += blockDim.x) v[s] = xphys[e.perm[s]];
+  __syncthreads();
+  rotate_vector_serial(e, v, false);
+  if (in_smem)
+    for (int s = threadIdx.x; s < e.N; s += blockDim.x) ysorted[s] = v[s];
 }
 
 void launch_apply_qt(cudaStream_t st, Eig e, const double* xphys, double* work, double* out_final) {
-  k_gather_rotate<<<1, 1024, 0, st>>>(e, xphys, work);
+  size_t sm = vec_smem(e.N);
+  cudaFuncSetAttribute(k_gather_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_gather_rotate<<<1, 1024, sm, st>>>(e, xphys, work, sm > 0 ? 1 : 0);
   SVDUP_COUNT_LAUNCH();
   // k_norms recomputes inv (identical values); only the product is wanted here.
   launch_norms(st, e, work, out_final);
@@ -764,25 +1100,23 @@ __global__ void k_apply_q_core(Eig e, const double* __restrict__ xfinal, double*
   }
 }
 
-__global__ void __launch_bounds__(1024) k_unrotate_scatter(Eig e, double* vsorted, double* yphys) {
-  if (threadIdx.x == 0) {
-    int nr = e.nrot[0];
-    for (int r = nr - 1; r >= 0; r--) {
-      int a = e.rj[r], b = e.ri[r];
-      double c = e.rc[r], sn = e.rs[r];
-      double va = vsorted[a], vb = vsorted[b];
-      vsorted[a] = c * va + sn * vb;
-      vsorted[b] = -sn * va + c * vb;
-    }
-  }
+__global__ void __launch_bounds__(1024) k_unrotate_scatter(Eig e, double* vsorted, double* yphys,
+                                                           int in_smem) {
+  extern __shared__ double vsm[];
+  double* v = in_smem ? vsm : vsorted;
+  if (in_smem)
+    for (int s = threadIdx.x; s < e.N; s += blockDim.x) v[s] = vsorted[s];
   __syncthreads();
-  for (int s = threadIdx.x; s < e.N; s += blockDim.x) yphys[e.perm[s]] = vsorted[s];
+  rotate_vector_serial(e, v, true);
+  for (int s = threadIdx.x; s < e.N; s += blockDim.x) yphys[e.perm[s]] = v[s];
 }
 
 void launch_apply_q(cudaStream_t st, Eig e, const double* xfinal, double* work, double* yphys) {
   k_apply_q_core<<<secular_blocks(e.N), 256, 0, st>>>(e, xfinal, work);
   SVDUP_COUNT_LAUNCH();
-  k_unrotate_scatter<<<1, 1024, 0, st>>>(e, work, yphys);
+  size_t sm = vec_smem(e.N);
+  cudaFuncSetAttribute(k_unrotate_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_unrotate_scatter<<<1, 1024, sm, st>>>(e, work, yphys, sm > 0 ? 1 : 0);
   SVDUP_COUNT_LAUNCH();
 }
 

@@ -112,7 +112,7 @@ extern "C" int svdup_secular_static(void* stream, int k, const double* d, const 
     return SVDUP_ECUDA;
   }
   k_static_prep<<<(k + 255) / 256, 256, 0, st>>>(k, d, z, rho, e.rhop, e.kp, e.dc, e.z2c, e.dk);
-  ++g_launch_count;
+  SVDUP_COUNT_LAUNCH();
   launch_secular(st, e, info, 64);
   cudaError_t err = cudaGetLastError();
   return err == cudaSuccess ? SVDUP_OK : SVDUP_ECUDA;

@@ -268,3 +268,31 @@ def test_iteration_cap_reports_noconv(sv):
         _run_update(sv, h, U, S, Vh.T, a, b)
     assert ei.value.code == sv.ENOCONV
     h.close()
+
+
+def test_fresh_process_mid_size(sv):
+    """The first call of a fresh process at a size whose kernels need more than the
+    default 48 KB of shared memory (static plus dynamic) must launch and be correct:
+    run in a child process so no earlier, larger call has raised any kernel limit."""
+    import subprocess
+    import sys
+    code = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+import paper_1707_08369_gb300 as sv, oracle
+from paper_1707_08369_gb300 import workloads as wl
+sv.load(); oracle.build()
+g = np.random.default_rng(3)
+N, rows = 1500, 64
+d = 10 ** (-6 * g.uniform(0, 1, N)); z = g.standard_normal(N); rho = -1.1
+X = wl.haar(N, g)[:rows, :N]
+lam_o, Y_o = oracle.rank_one_update_z(X, d, z, rho)
+h = sv.Handle(0)
+Xd = torch.from_numpy(np.asfortranarray(X).T.copy()).cuda().t()
+lam, Y = h.cauchy_product(Xd, torch.from_numpy(d).cuda(), torch.from_numpy(z).cuda(), rho)
+assert np.abs(lam.cpu().numpy() - lam_o).max() <= 1e-13 * np.abs(lam_o).max()
+assert np.abs(Y.cpu().numpy() - Y_o).max() <= 1e-10
+print("ok")
+''' % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr

@@ -1,0 +1,128 @@
+"""Parity of the split-BF16 tensor-core product (SVDUP_MIXED_BF16X3) with the CPU
+oracle, through the C ABI.
+
+The mixed form keeps FP64 in the secular solve, the root offsets and the recomputed z
+(so eigenvalues are exactly those of the FP64 path) and forms the products from
+three-term BF16 splits with FP32 accumulation, i.e. to FP32 accuracy: about 2^-24
+relative per operand and per accumulation.  An output column of X Ctilde is a sum of
+k terms x_t c_tj with sum_t |x_t c_tj| <= ||x|| ||c_j|| = ||x||, so its error is
+bounded by a small multiple of sqrt(k) 2^-24 ||x|| for random-sign rounding.  The
+tests state the bound they use: 2e-6 elementwise for one product of orthonormal rows,
+and the target 1e-6 of the spec reading for the reconstruction of a full update.
+"""
+import numpy as np
+import pytest
+
+from paper_1707_08369_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import paper_1707_08369_gb300 as sv
+    from paper_1707_08369_gb300 import build
+    build.build()
+    sv.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return sv
+
+
+@pytest.fixture(scope="module")
+def hnd(sv):
+    return sv.Handle(0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def devF(x):
+    return torch.from_numpy(np.asfortranarray(x).T.copy()).cuda().t()
+
+
+@pytest.mark.parametrize("rows,N,dense,seed,spread", [
+    (7, 33, True, 0, "u"),        # one ragged row tile, one ragged leaf
+    (130, 200, True, 1, "u"),     # two row tiles, several leaves
+    (96, 700, False, 2, "u"),     # far field on, uniform poles
+    (257, 1500, False, 3, "g"),   # far field on, graded poles, ragged tiles
+    (64, 1500, True, 4, "g"),     # forced dense on the same problem size
+    (300, 2600, False, 5, "g"),   # leaf size 128
+])
+def test_mixed_cauchy_product_vs_oracle(sv, hnd, orc, rows, N, dense, seed, spread):
+    g = np.random.default_rng(seed)
+    d = g.uniform(0, 1, N) if spread == "u" else 10 ** (-6 * g.uniform(0, 1, N))
+    z = g.standard_normal(N)
+    rho = g.uniform(0.5, 2.0) * (1 if seed % 2 == 0 else -1)
+    X = wl.haar(max(rows, N), g)[:rows, :N]
+    lam_o, Y_o = orc.rank_one_update_z(X, d, z, rho)
+    mode = sv.MIXED_BF16X3 | (sv.DENSE if dense else 0)
+    lam_g, Y_g = hnd.cauchy_product(devF(X), dev(d), dev(z), rho, eps=1e-12, mode=mode)
+    Y_g = Y_g.cpu().numpy()
+    assert np.abs(lam_g.cpu().numpy() - lam_o).max() <= 1e-13 * np.abs(lam_o).max()
+    err = np.abs(Y_g - Y_o).max()
+    assert err <= MIXED_TOL, err
+
+
+def _invariants(U, S, V, a, b, Un, Sn, Vn):
+    m, n = U.shape[0], V.shape[0]
+    Ah = U @ np.diag(S) @ V[:, :m].T + np.outer(a, b)
+    nrm = np.linalg.norm(Ah, 2)
+    recon = np.linalg.norm(Ah @ Vn[:, :m] - Un * Sn) / nrm
+    orthU = np.abs(Un.T @ Un - np.eye(m)).max()
+    orthV = np.abs(Vn.T @ Vn - np.eye(n)).max()
+    return recon, orthU, orthV
+
+
+@pytest.mark.parametrize("m,n,seed", [(48, 80, 3), (100, 100, 4), (513, 600, 5)])
+def test_mixed_update_shapes(sv, hnd, orc, m, n, seed):
+    g = wl.rng(seed + 50)
+    A = g.standard_normal((m, n))
+    a = g.standard_normal(m); b = g.standard_normal(n)
+    U, S, Vh = np.linalg.svd(A)
+    Uo, So, Vo = orc.svd_update(U, S, Vh.T, a, b)
+    tU, tS, tV = devF(U), dev(S), devF(Vh.T)
+    hnd.update(tU, tS, tV, dev(a), dev(b), eps=1e-12, mode=sv.MIXED_BF16X3)
+    Un, Sn, Vn = tU.cpu().numpy(), tS.cpu().numpy(), tV.cpu().numpy()
+    # the roots are FP64 in both forms: singular values to the FP64 tolerance
+    assert np.abs(Sn - So).max() <= 1e-12 * So[0]
+    recon, orthU, orthV = _invariants(U, S, Vh.T, a, b, Un, Sn, Vn)
+    assert recon <= 1e-6 and orthU <= 1e-5 and orthV <= 1e-5, (recon, orthU, orthV)
+    assert np.abs(Un - Uo).max() <= 1e-4
+    assert np.abs(Vn[:, :m] - Vo[:, :m]).max() <= 1e-4
+
+
+def test_mixed_update_fmm_loguniform(sv, hnd, orc):
+    """Square n = 1536, log-uniform spectrum: far field on, split products."""
+    U, S, V, a, b = wl.loguniform_sq(1536, seed=wl.BASE_SEED + 77)
+    Uo, So, Vo = orc.svd_update(U, S, V, a, b)
+    tU, tS, tV = devF(U), dev(S), devF(V)
+    hnd.update(tU, tS, tV, dev(a), dev(b), eps=1e-12, mode=sv.MIXED_BF16X3)
+    Un, Sn, Vn = tU.cpu().numpy(), tS.cpu().numpy(), tV.cpu().numpy()
+    assert np.abs(Sn - So).max() <= 1e-12 * So[0]
+    recon, orthU, orthV = _invariants(U, S, V, a, b, Un, Sn, Vn)
+    assert recon <= 1e-6, recon
+    assert orthU <= 1e-5 and orthV <= 1e-5, (orthU, orthV)
+
+
+def test_mixed_matches_fp64_eigenvalues_bitwise(sv, hnd):
+    """The mixed form changes only the products: the eigenvalues (FP64 roots) are
+    bit-identical to the FP64 form's."""
+    U, S, V, a, b = wl.loguniform_sq(700, seed=wl.BASE_SEED + 5)
+    outs = []
+    for mode in (sv.FP64, sv.MIXED_BF16X3):
+        tU, tS, tV = devF(U), dev(S), devF(V)
+        hnd.update(tU, tS, tV, dev(a), dev(b), eps=1e-12, mode=mode)
+        outs.append(tS.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_mixed_rejects_unsupported_modes(sv, hnd):
+    U = devF(np.eye(4)); S = dev(np.ones(4)); V = devF(np.eye(4)); a = dev(np.ones(4))
+    for mode in (sv.MIXED_FP16X2, sv.MIXED_BF16X3 | 0x4000):
+        with pytest.raises(sv.SvdupError) as ei:
+            hnd.update(U, S, V, a, dev(np.ones(4)), mode=mode)
+        assert ei.value.code == sv.EINVAL
