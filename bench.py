@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--cpu-cols", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     return ap.parse_args()
 
 
@@ -276,6 +277,49 @@ def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, w
     return lat, total_ms, launches, stages, clk
 
 
+def accuracy_report(sv, h, stream, upload, ta, tb, eps, mode, dev):
+    """One update from the same inputs in the FP64 form and in `mode`; the mixed form's
+    errors against the FP64 form, and invariants of each output measured with random
+    probes x (n x 4, FP64 on the device): ||U^T U x - x||, ||V^T V x - x|| and the
+    reconstruction ||Ahat Vhat x - Uhat Shat x|| / (sigma_max ||x||) with
+    Ahat = U S V^T + a b^T applied factor by factor."""
+    import torch
+    outs = {}
+    with torch.cuda.stream(stream):
+        U0, S0, V0 = upload()
+        for m in sorted({0, mode}):
+            tU, tS, tV = upload()
+            h.update(tU, tS, tV, ta[0], tb[0], eps=eps, mode=m, check=True)
+            outs[m] = (tU, tS, tV)
+        torch.cuda.synchronize(dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(170708369)
+        n, m_ = V0.shape[0], U0.shape[0]
+        x = torch.randn(m_, 4, dtype=torch.float64, device=dev, generator=gen)
+        rep = {}
+        for mm, (Un, Sn, Vn) in outs.items():
+            Vm = Vn[:, :m_]
+            ortU = float(torch.linalg.norm(Un.t() @ (Un @ x) - x) / torch.linalg.norm(x))
+            y = torch.randn(n, 4, dtype=torch.float64, device=dev, generator=gen)
+            ortV = float(torch.linalg.norm(Vn.t() @ (Vn @ y) - y) / torch.linalg.norm(y))
+            w = Vm @ x
+            lhs = U0 @ (S0[:, None] * (V0[:, :m_].t() @ w)) + ta[0][:, None] * (tb[0][None, :] @ w)
+            rec = float(torch.linalg.norm(lhs - Un @ (Sn[:, None] * x)) / (Sn[0] * torch.linalg.norm(x)))
+            rep[mm] = {"orth_U": ortU, "orth_V": ortV, "recon": rec}
+        res = {"probe": "4 Gaussian probe vectors; norms are 2-norms of the probe block",
+               "fp64": rep[0]}
+        if mode != 0:
+            U64, S64, V64 = outs[0]
+            Um, Sm, Vm2 = outs[mode]
+            res["mixed"] = rep[mode]
+            res["mixed_vs_fp64"] = {
+                "sigma_max_rel": float((Sm - S64).abs().max() / S64[0]),
+                "U_max_abs": float((Um - U64).abs().max()),
+                "V_max_abs": float((Vm2[:, :m_] - V64[:, :m_]).abs().max())}
+    del outs
+    return res
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -329,6 +373,9 @@ def main():
                 "p99_ms": float(np.percentile(lat64, 99)), "mixed_over_fp64": value / v64}
         del tU, tV
         tU, tS, tV = upload()
+
+    accuracy = None if args.no_accuracy else accuracy_report(
+        sv, h, stream, upload, ta, tb, args.eps, mode, dev)
 
     # dominant product stage -> roofline (stage timers bracket exactly that kernel's launch)
     peaks, peak_src = load_peaks()
@@ -399,6 +446,7 @@ def main():
                 "config": bench_config(args, ws),
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                 "fp64": fp64,
+                "accuracy": accuracy,
                 "stage_ms_per_update": stage_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk}

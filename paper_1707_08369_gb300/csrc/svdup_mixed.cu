@@ -180,6 +180,20 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
   }
 }
 
+// The same wait bounded by time only (used for the final drain of issued MMAs, which
+// must complete even after another role gave up).
+__device__ bool mbar_wait_timed(uint32_t bar, uint32_t parity) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > kWaitLimitNs) return false;
+    }
+  }
+}
+
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
                                          uint32_t bar) {
   asm volatile(
@@ -486,13 +500,62 @@ __device__ __forceinline__ KTile ktile(int i, const Job& J, const FmmPlan& f, co
   return t;
 }
 
-// The six partial products of the 3-term split: (A plane, B plane).
+// The six partial products of the 3-term split: (A plane, B plane).  Product 0
+// (hi.hi) accumulates in its own tensor-memory region; the five cross products, smaller
+// by 2^-8 or more, share a second region.
 __constant__ int kPairA[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int kPairB[6] = {0, 1, 0, 2, 0, 1};
 
-template <int STAGE, int NCOLS>
-__global__ void __launch_bounds__(192, 1) k_umma(Eig e, FmmPlan f, MixPlan mp, OutMap om,
-                                                 int dense, int* status) {
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// (hi, lo) += x with Knuth's TwoSum in FP32: hi + lo carries about 48 significant bits.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (x - bb);
+  hi = s;
+  lo += err;
+}
+
+// Three BF16 terms of the double-float value hi + lo (24 significant bits).
+__device__ __forceinline__ void split3ff(float hi, float lo, uint16_t& h, uint16_t& m,
+                                         uint16_t& l) {
+  __nv_bfloat16 bh = __float2bfloat16_rn(hi);
+  float r = (hi - __bfloat162float(bh)) + lo;
+  __nv_bfloat16 bm = __float2bfloat16_rn(r);
+  r = r - __bfloat162float(bm);
+  __nv_bfloat16 bl = __float2bfloat16_rn(r);
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+
+__device__ __forceinline__ void store_split8_ff(unsigned char* tile, uint32_t plane, uint32_t off,
+                                                const float* hi, const float* lo) {
+  uint16_t h[8], m[8], l[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) split3ff(hi[c], lo[c], h[c], m[c], l[c]);
+  store_split8(tile, plane, off, h, m, l);
+}
+
+// Roles: warps 0-7 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) .., i.e.
+// output rows, and the column half w / 4 of the W accumulator columns), warp 8 issues
+// the bulk copies, warp 9 owns tensor memory and issues the MMAs.
+// Tensor memory (512 columns): two regions (K tiles alternate), each holding the hi.hi
+// accumulator in columns [0, W) and the cross-product accumulator in [128, 128 + W).
+// Every K tile is drained into double-float registers while the next one is multiplied,
+// so FP32 rounding in tensor memory covers at most one K tile (64 or 16 products).
+constexpr int kEpiWarps = 8;
+constexpr int kUmmaThreads = (kEpiWarps + 2) * 32;
+constexpr uint32_t kTmemCols = 512;
+
+template <int STAGE, int W>
+__global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixPlan mp, OutMap om,
+                                                          int dense, int* status) {
+  constexpr int QW = W / 2;        // columns per epilogue warp
+  constexpr int NCH = QW / 16;     // 16-column chunks per epilogue warp
   extern __shared__ unsigned char smem_raw[];
   Job J;
   J.rt = blockIdx.x;
@@ -508,26 +571,29 @@ __global__ void __launch_bounds__(192, 1) k_umma(Eig e, FmmPlan f, MixPlan mp, O
 
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_base = smem_u32(sm);
-  const uint32_t sA[2] = {s_base, s_base + kStageBytes};
-  const uint32_t sB[2] = {s_base + kTileA, s_base + kStageBytes + kTileA};
-  uint64_t* bars = (uint64_t*)(sm + kRingBytes);  // full[2], empty[2], accum
-  const uint32_t bar_full[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
-  const uint32_t bar_empty[2] = {smem_u32(&bars[2]), smem_u32(&bars[3])};
-  const uint32_t bar_accum = smem_u32(&bars[4]);
-  volatile uint32_t* tmem_slot = (volatile uint32_t*)(sm + kRingBytes + 64);
-  volatile int* abort_flag = (volatile int*)(sm + kRingBytes + 128);
+  uint64_t* bars = (uint64_t*)(sm + kRingBytes);  // full[2] empty[2] tfull[2] tempty[2] done
+  const uint32_t bar0 = smem_u32(bars);
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(sm + kRingBytes + 128);
+  volatile int* abort_flag = (volatile int*)(sm + kRingBytes + 192);
+  auto bar_full = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+  auto bar_empty = [&](int i) { return bar0 + 8u * (uint32_t)(2 + i); };
+  auto bar_tfull = [&](int i) { return bar0 + 8u * (uint32_t)(4 + i); };
+  auto bar_tempty = [&](int i) { return bar0 + 8u * (uint32_t)(6 + i); };
+  const uint32_t bar_done = bar0 + 8u * 8u;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == 5) {
-    tmem_alloc(smem_u32((const void*)tmem_slot), NCOLS);
+  if (warp == kEpiWarps + 1) {
+    tmem_alloc(smem_u32((const void*)tmem_slot), kTmemCols);
     tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    mbar_init(bar_full[0], 1);
-    mbar_init(bar_full[1], 1);
-    mbar_init(bar_empty[0], 1);
-    mbar_init(bar_empty[1], 1);
-    mbar_init(bar_accum, 1);
+    for (int i = 0; i < 2; i++) {
+      mbar_init(bar_full(i), 1);
+      mbar_init(bar_empty(i), 1);
+      mbar_init(bar_tfull(i), 1);
+      mbar_init(bar_tempty(i), kEpiWarps * 32);
+    }
+    mbar_init(bar_done, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -536,110 +602,155 @@ __global__ void __launch_bounds__(192, 1) k_umma(Eig e, FmmPlan f, MixPlan mp, O
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
-    if (lane == 0) {  // producer: bulk copies into the ring
+  if (warp == kEpiWarps) {
+    if (lane == 0) {  // producer: bulk copies into the shared-memory ring
       for (int i = 0; i < J.ntiles; i++) {
         const int st = i & 1;
         const uint32_t u = (uint32_t)(i >> 1);
-        if (i >= 2 && !mbar_wait(bar_empty[st], (u & 1u) ^ 1u, abort_flag)) {
+        if (i >= 2 && !mbar_wait(bar_empty(st), (u & 1u) ^ 1u, abort_flag)) {
           *abort_flag = 1;
           latch(status, SVDUP_ETIMEOUT);
           break;
         }
         KTile t = ktile<STAGE>(i, J, f, mp, dense);
-        mbar_expect_tx(bar_full[st], t.abytes + t.bbytes);
-        bulk_g2s(sA[st], t.a, t.abytes, bar_full[st]);
-        bulk_g2s(sB[st], t.b, t.bbytes, bar_full[st]);
+        const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kTileA;
+        mbar_expect_tx(bar_full(st), t.abytes + t.bbytes);
+        bulk_g2s(sa, t.a, t.abytes, bar_full(st));
+        bulk_g2s(sb, t.b, t.bbytes, bar_full(st));
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == kEpiWarps + 1) {
     if (lane == 0) {  // MMA issuer
       for (int i = 0; i < J.ntiles; i++) {
         const int st = i & 1;
         const uint32_t u = (uint32_t)(i >> 1);
-        if (!mbar_wait(bar_full[st], u & 1u, abort_flag)) {
+        if (!mbar_wait(bar_full(st), u & 1u, abort_flag) ||
+            (i >= 2 && !mbar_wait(bar_tempty(st), (u & 1u) ^ 1u, abort_flag))) {
           *abort_flag = 1;
           latch(status, SVDUP_ETIMEOUT);
           break;
         }
         tc_fence_after();
         KTile t = ktile<STAGE>(i, J, f, mp, dense);
+        const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kTileA;
+        const uint32_t dA = tmem + (uint32_t)st * 256u + (uint32_t)t.col;
+        const uint32_t dB = dA + 128u;
         const uint32_t idesc = idesc_bf16(kTM, t.n);
         const uint32_t sbo = (uint32_t)t.kb * 16;
         for (int ks = 0; ks < t.kb / 16; ks++) {
 #pragma unroll
           for (int q = 0; q < 6; q++) {
-            uint64_t ad = sdesc(sA[st] + kPairA[q] * t.aplane + ks * 256, 128, sbo);
-            uint64_t bd = sdesc(sB[st] + kPairB[q] * t.bplane + ks * 256, 128, sbo);
-            uint32_t acc = (t.first && ks == 0 && q == 0) ? 0u : 1u;
-            umma_bf16(tmem + (uint32_t)t.col, ad, bd, idesc, acc);
+            uint64_t ad = sdesc(sa + kPairA[q] * t.aplane + ks * 256, 128, sbo);
+            uint64_t bd = sdesc(sb + kPairB[q] * t.bplane + ks * 256, 128, sbo);
+            if (q == 0) umma_bf16(dA, ad, bd, idesc, ks > 0 ? 1u : 0u);
+            else umma_bf16(dB, ad, bd, idesc, (ks > 0 || q > 1) ? 1u : 0u);
           }
         }
-        umma_commit(bar_empty[st]);  // frees the stage once these MMAs have read it
+        umma_commit(bar_empty(st));  // frees the ring stage once these MMAs have read it
+        umma_commit(bar_tfull(st));  // hands the accumulators to the epilogue
       }
-      umma_commit(bar_accum);  // every MMA issued above has completed
+      // every MMA this thread issued has completed before tensor memory is released
+      umma_commit(bar_done);
+      if (!mbar_wait_timed(bar_done, 0)) latch(status, SVDUP_ETIMEOUT);
     }
   } else {
-    // epilogue: warps 0-3, TMEM lanes 32 w .. 32 w + 31 = output rows
-    const bool ok = mbar_wait(bar_accum, 0, abort_flag);
-    tc_fence_after();
-    const int r = warp * 32 + lane;
-    const long long row = (long long)J.rt * kTM + r;
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    // epilogue: drain every K tile into (hi, lo) pairs, then write the output
+    const int quad = warp & 3, qc = warp >> 2;
+    const int r = quad * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    float hi[QW], lo[QW];
+#pragma unroll
+    for (int c = 0; c < QW; c++) { hi[c] = 0.0f; lo[c] = 0.0f; }
+    bool ok = true;
+    for (int i = 0; i < J.ntiles && ok; i++) {
+      const int st = i & 1;
+      if (!mbar_wait(bar_tfull(st), (uint32_t)(i >> 1) & 1u, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      KTile t = ktile<STAGE>(i, J, f, mp, dense);
+#pragma unroll
+      for (int ch = 0; ch < NCH; ch++) {
+        const int col = qc * QW + ch * 16;
+        if (col >= t.col && col < t.col + t.n) {
+#pragma unroll
+          for (int part = 0; part < 2; part++) {  // hi.hi region, then the cross region
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)st * 256u + (uint32_t)part * 128u + (uint32_t)col, v);
+#pragma unroll
+            for (int c = 0; c < 16; c++) {
+              if (part == 0) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], v[c]);
+              else lo[ch * 16 + c] += v[c];  // cross terms: 2^-8 of hi.hi and below
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(bar_tempty(st));
+    }
     if (!ok) {
       *abort_flag = 1;
       latch(status, SVDUP_ETIMEOUT);
     } else if (!*abort_flag) {
       if (STAGE == MS_P2M) {
+        // half qc = leaves 4 job + 2 qc + {0, 1}: columns 32 qc .. of the Phi tile
         unsigned char* tile = mp.Phip + ((size_t)J.rt * mp.kphi + J.job) * kTileA;
-        for (int u = 0; u < 4; u++) {
-          float v[16];
-          if (4 * J.job + u < J.Ls) tmem_ld16(taddr + u * kMixP, v);
-          else
-            for (int c = 0; c < 16; c++) v[c] = 0.0f;
-          store_split8_f(tile, kPlaneA, cl_off(r, u * 16, kKB), v);
-          store_split8_f(tile, kPlaneA, cl_off(r, u * 16 + 8, kKB), v + 8);
+#pragma unroll
+        for (int u = 0; u < QW / kMixP; u++) {
+          if (4 * J.job + qc * (QW / kMixP) + u >= J.Ls)  // past the last leaf: zeros
+#pragma unroll
+            for (int c = 0; c < kMixP; c++) { hi[u * kMixP + c] = 0.0f; lo[u * kMixP + c] = 0.0f; }
         }
+#pragma unroll
+        for (int c8 = 0; c8 < QW; c8 += 8)
+          store_split8_ff(tile, kPlaneA, cl_off(r, qc * QW + c8, kKB), hi + c8, lo + c8);
       } else if (STAGE == MS_M2L) {
-        for (int u = 0; u < kTM / kMixP; u++) {
-          const int b = J.job * (kTM / kMixP) + u;
-          if (b >= J.Lt) break;
-          float v[16];
-          tmem_ld16(taddr + u * kMixP, v);
-          unsigned char* tile = mp.Psip + ((size_t)J.rt * (mp.Lmax + 1) + b) * kTilePsi;
-          store_split8_f(tile, kPlanePsi, cl_off(r, 0, kMixP), v);
-          store_split8_f(tile, kPlanePsi, cl_off(r, 8, kMixP), v + 8);
-        }
-      } else {
-        const int j0 = f.tj0[J.job], nb = f.tj1[J.job] - j0;
-        for (int c0 = 0; c0 < nb; c0 += 16) {
-          float v[16];
-          tmem_ld16(taddr + c0, v);
-          if (row < mp.rows) {
-            for (int c = 0; c < 16 && c0 + c < nb; c++) {
-              const int q = e.rank_root[j0 + c0 + c];
-              const double sc = om.colscale ? om.colscale[q] : 1.0;
-              om.Y[row + out_col_m(om, q) * om.ldy] = sc * (double)v[c];
-            }
+#pragma unroll
+        for (int u = 0; u < QW / kMixP; u++) {
+          const int b = J.job * (kTM / kMixP) + qc * (QW / kMixP) + u;
+          if (b < J.Lt) {
+            unsigned char* tile = mp.Psip + ((size_t)J.rt * (mp.Lmax + 1) + b) * kTilePsi;
+            store_split8_ff(tile, kPlanePsi, cl_off(r, 0, kMixP), hi + u * 16, lo + u * 16);
+            store_split8_ff(tile, kPlanePsi, cl_off(r, 8, kMixP), hi + u * 16 + 8, lo + u * 16 + 8);
           }
+        }
+      }
+    }
+    if (STAGE == MS_OUT) {
+      // Stage the FP64 tile column-major in the (now idle) ring, then write whole output
+      // columns: 128 consecutive rows per column, one warp per column.
+      double* stile = (double*)sm;  // [W][128]
+#pragma unroll
+      for (int c = 0; c < QW; c++) stile[(qc * QW + c) * kTM + r] = (double)hi[c] + (double)lo[c];
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
+      if (ok && !*abort_flag) {
+        const int j0 = f.tj0[J.job], nb = f.tj1[J.job] - j0;
+        const long long row0 = (long long)J.rt * kTM;
+        for (int cc = warp; cc < nb; cc += kEpiWarps) {
+          const int q = e.rank_root[j0 + cc];
+          const double sc = om.colscale ? om.colscale[q] : 1.0;
+          double* ycol = om.Y + out_col_m(om, q) * om.ldy + row0;
+          for (int rr = lane; rr < kTM; rr += 32)
+            if (row0 + rr < mp.rows) ycol[rr] = sc * stile[cc * kTM + rr];
         }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) {
+  if (warp == kEpiWarps + 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, NCOLS);
+    tmem_dealloc(tmem, kTmemCols);
   }
 }
 
-template <int STAGE, int NCOLS>
+template <int STAGE, int W>
 void launch_umma(cudaStream_t st, dim3 grid, Eig e, FmmPlan f, MixPlan mp, OutMap om, int dense,
                  int* status) {
-  cudaFuncSetAttribute(k_umma<STAGE, NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_umma<STAGE, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kSmemBytes);
-  k_umma<STAGE, NCOLS><<<grid, 192, kSmemBytes, st>>>(e, f, mp, om, dense, status);
+  k_umma<STAGE, W><<<grid, kUmmaThreads, kSmemBytes, st>>>(e, f, mp, om, dense, status);
   SVDUP_COUNT_LAUNCH();
 }
 
@@ -700,6 +811,8 @@ void launch_mix_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, MixPlan mp, 
   } else if (stage == 1) {
     if (dense) return;
     launch_umma<MS_M2L, 128>(st, dim3(mp.rt, mp.ntT), e, f, mp, om, dense, status);
+  } else if (mp.s == 64) {
+    launch_umma<MS_OUT, 64>(st, dim3(mp.rt, mp.Lmax + 1), e, f, mp, om, dense, status);
   } else {
     launch_umma<MS_OUT, 128>(st, dim3(mp.rt, mp.Lmax + 1), e, f, mp, om, dense, status);
   }

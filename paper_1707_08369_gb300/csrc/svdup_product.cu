@@ -182,18 +182,6 @@ __device__ __forceinline__ double cheb_node(int alpha, int p) {
   return cospi((2.0 * alpha + 1.0) / (2.0 * p));  // alpha = 0..p-1  (App. D Eq. Define_ti)
 }
 
-// Lagrange basis u_alpha(x) on the p Chebyshev nodes (App. D Eq. Define_uj).
-__device__ double lagrange(int alpha, int p, double x) {
-  double ta = cheb_node(alpha, p);
-  double v = 1.0;
-  for (int b = 0; b < p; b++) {
-    if (b == alpha) continue;
-    double tb = cheb_node(b, p);
-    v *= (x - tb) / (ta - tb);
-  }
-  return v;
-}
-
 // Half-width of a box [lo, hi]; a (near-)single-point box gets a small positive width
 // relative to its position so that points map to finite coordinates near 0.
 __device__ __forceinline__ double box_radius(double lo, double hi) {
@@ -283,20 +271,57 @@ __device__ __forceinline__ bool is_near(const FmmPlan& f, int b, int a) {
   return false;
 }
 
+// All p Lagrange basis values at x (App. D Eq. Define_uj) in the barycentric form on
+// the first-kind Chebyshev nodes: u_alpha(x) = [w_alpha / (x - t_alpha)] / sum_beta
+// [w_beta / (x - t_beta)], w_beta = (-1)^beta sin((2 beta + 1) pi / (2p)); a node hit
+// exactly gives the unit vector.  Nodes and weights come from shared memory.
+__device__ void lagrange_all(int p, double x, const double* st, const double* sw, double* out) {
+  int hit = -1;
+  double den = 0.0;
+  for (int b = 0; b < p; b++) {
+    const double df = x - st[b];
+    if (df == 0.0) hit = b;
+    const double c = df == 0.0 ? 0.0 : sw[b] / df;
+    out[b] = c;
+    den += c;
+  }
+  if (hit >= 0) {
+    for (int b = 0; b < p; b++) out[b] = b == hit ? 1.0 : 0.0;
+  } else {
+    const double inv = 1.0 / den;
+    for (int b = 0; b < p; b++) out[b] *= inv;
+  }
+}
+
+__device__ void cheb_tables(int p, double* st, double* sw) {
+  for (int b = threadIdx.x; b < p; b += blockDim.x) {
+    const double th = (2.0 * b + 1.0) / (2.0 * p);
+    st[b] = cospi(th);
+    sw[b] = (b & 1 ? -1.0 : 1.0) * sinpi(th);
+  }
+  __syncthreads();
+}
+
 // P2M operator of source leaf a: S[a][alpha][tl] = zhat_t u_alpha((d_t - c_a) / r_a)
-// (App. D STEP 5 with the far-field variable mapped to [-1, 1]).
+// (App. D STEP 5 with the far-field variable mapped to [-1, 1]); one thread per pole.
 __global__ void k_fmm_S(Eig e, FmmPlan f) {
+  __shared__ double st[32], sw[32];
+  cheb_tables(f.p, st, sw);
   const int k = e.kp[0], L = f.L[0], p = f.p, s = f.s;
-  long long total = (long long)L * s * p;
+  const long long total = (long long)L * s;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
        x += (long long)gridDim.x * blockDim.x) {
-    int a = (int)(x / ((long long)s * p));
-    int rem = (int)(x - (long long)a * s * p);
-    int alpha = rem / s, tl = rem - alpha * s;
-    int t = a * s + tl;
-    double v = 0.0;
-    if (t < k) v = e.zhat[t] * lagrange(alpha, p, box_coord(e.dk[t] - f.sbox_c[a], f.sbox_r[a]));
-    f.S[x] = v;
+    const int a = (int)(x / s), tl = (int)(x - (long long)a * s);
+    const int t = a * s + tl;
+    double* col = f.S + (size_t)a * s * p + tl;
+    if (t < k) {
+      double u[32];
+      lagrange_all(p, box_coord(e.dk[t] - f.sbox_c[a], f.sbox_r[a]), st, sw, u);
+      const double zt = e.zhat[t];
+      for (int alpha = 0; alpha < p; alpha++) col[(size_t)alpha * s] = zt * u[alpha];
+    } else {
+      for (int alpha = 0; alpha < p; alpha++) col[(size_t)alpha * s] = 0.0;
+    }
   }
 }
 
@@ -323,22 +348,25 @@ __global__ void k_fmm_T(FmmPlan f) {
 }
 
 // L2P operator of target leaf b: Lop[b][jl][beta] = u_beta((mu_j - c_b) / r_b) inv_j
-// (App. D STEP 9), j = tj0[b] + jl.
+// (App. D STEP 9), j = tj0[b] + jl; one thread per root.
 __global__ void k_fmm_L(Eig e, FmmPlan f) {
+  __shared__ double st[32], sw[32];
+  cheb_tables(f.p, st, sw);
   const int Lt = f.L[1], p = f.p, s = f.s;
-  long long total = (long long)Lt * s * p;
+  const long long total = (long long)Lt * s;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
        x += (long long)gridDim.x * blockDim.x) {
-    int b = (int)(x / ((long long)s * p));
-    int rem = (int)(x - (long long)b * s * p);
-    int jl = rem / p, beta = rem - jl * p;
-    int j = f.tj0[b] + jl;
-    double v = 0.0;
+    const int b = (int)(x / s), jl = (int)(x - (long long)b * s);
+    const int j = f.tj0[b] + jl;
+    double* out = f.Lop + (size_t)b * s * p + (size_t)jl * p;
     if (j < f.tj1[b]) {
-      double y = box_coord((e.dorg[j] - f.tbox_c[b]) + e.tau[j], f.tbox_r[b]);
-      v = lagrange(beta, p, y) * e.inv[j];
+      double u[32];
+      lagrange_all(p, box_coord((e.dorg[j] - f.tbox_c[b]) + e.tau[j], f.tbox_r[b]), st, sw, u);
+      const double inv = e.inv[j];
+      for (int beta = 0; beta < p; beta++) out[beta] = u[beta] * inv;
+    } else {
+      for (int beta = 0; beta < p; beta++) out[beta] = 0.0;
     }
-    f.Lop[x] = v;
   }
 }
 
@@ -348,11 +376,11 @@ void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense) {
   k_fmm_near<<<(f.Lmax + 128) / 128, 128, 0, st>>>(e, f, dense);
   SVDUP_COUNT_LAUNCH();
   if (dense) return;
-  long long sp = (long long)(f.Lmax + 1) * f.s * f.p;
-  int blocks = (int)((sp + 255) / 256);
-  k_fmm_S<<<blocks, 256, 0, st>>>(e, f);
+  long long sp = (long long)(f.Lmax + 1) * f.s;
+  int blocks = (int)((sp + 127) / 128);
+  k_fmm_S<<<blocks, 128, 0, st>>>(e, f);
   SVDUP_COUNT_LAUNCH();
-  k_fmm_L<<<blocks, 256, 0, st>>>(e, f);
+  k_fmm_L<<<blocks, 128, 0, st>>>(e, f);
   SVDUP_COUNT_LAUNCH();
   long long nt = (long long)f.Lmax * f.p * (long long)(f.Lmax + 1) * f.p;
   int tb = (int)((nt + 255) / 256);

@@ -211,9 +211,9 @@ void launch_fill_generic(cudaStream_t st, Eig e, const double* d, const double* 
 //     z~_i^2 = sum_{t=i0..i} z_t^2   and   d~_i = sum z_t^2 d_t / z~_i^2
 // (each Givens step is a z^2-weighted mean), so the sequential test reduces to
 //     |d_i - d~_{i-1}| |z_i| z~_{i-1} <= tol (z~_{i-1}^2 + z_i^2).
-// One thread walks the survivors on shared-memory copies with just these two running
-// sums to find where runs start and end; only pairs that pass with the original values
-// (a bitmask found in parallel) can start a run.  The rotation records (position pair,
+// One warp walks the survivors on shared-memory copies with just these two running
+// sums, 32 pairs per step, to find where runs start and end; only pairs that pass with
+// the original values (a bitmask found in parallel) can start a run.  The rotation records (position pair,
 // cos, sin) and the merged values are then formed in parallel from segmented prefix
 // sums of z^2 and z^2 d over the runs.  This is the Bunch-Nielsen-Sorensen deflation
 // in exact arithmetic; only the rounding of the merged values differs from applying
@@ -225,30 +225,12 @@ constexpr int kDeflateThreads = 1024;
 // positions when they fit.
 static size_t deflate_smem(int N, int* in_smem) {
   size_t words = (size_t)(N + 31) / 32;
-  size_t masks = 2 * words * sizeof(unsigned);
-  size_t arrays = (size_t)N * (2 * sizeof(double) + sizeof(int));
+  size_t masks = words * sizeof(unsigned);
+  size_t arrays = (size_t)N * (2 * sizeof(double) + sizeof(int) + 1);
   size_t total = ((masks + 15) & ~(size_t)15) + arrays;
   if (total <= 192 * 1024) { *in_smem = 1; return total; }
   *in_smem = 0;
   return masks;
-}
-
-// First index i in [from, n) whose bit is set in mask, else n.
-__device__ __forceinline__ int next_set(const unsigned* mask, int from, int n) {
-  if (from >= n) return n;
-  int w = from >> 5;
-  const int nw = (n + 31) >> 5;
-  unsigned m = mask[w] & (0xffffffffu << (from & 31));
-  while (m == 0u) {
-    if (++w >= nw) return n;
-    m = mask[w];
-  }
-  int i = (w << 5) + __ffs(m) - 1;
-  return i < n ? i : n;
-}
-
-__device__ __forceinline__ bool bit_at(const unsigned* mask, int i) {
-  return (mask[i >> 5] >> (i & 31)) & 1u;
 }
 
 // Block-wide exclusive prefix sum of one int per thread (Hillis-Steele over scnt);
@@ -269,58 +251,102 @@ __device__ int block_excl_scan(int v, int* scnt, int* total) {
   return incl - v;
 }
 
+// Segmented inclusive scan over the threads' chunks of (flag, W, M): a chunk with
+// flag set starts a new run at or after its start.  Returns the (W, M) of the run
+// through the element just before the calling thread's chunk.
+__device__ void run_carry(int lflag, double lW, double lM, int* sflag, double* sW, double* sM,
+                          double* cW, double* cM) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  sflag[tid] = lflag;
+  sW[tid] = lW;
+  sM[tid] = lM;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    int f2 = 0;
+    double W2 = 0.0, M2 = 0.0;
+    if (tid >= off) { f2 = sflag[tid - off]; W2 = sW[tid - off]; M2 = sM[tid - off]; }
+    __syncthreads();
+    if (tid >= off && !sflag[tid]) { sW[tid] += W2; sM[tid] += M2; sflag[tid] = f2; }
+    __syncthreads();
+  }
+  *cW = tid > 0 ? sW[tid - 1] : 0.0;
+  *cM = tid > 0 ? sM[tid - 1] : 0.0;
+  __syncthreads();
+}
+
+// The merge test of survivor i against the carrier (W = z~^2, M = W d~) of the run
+// through i - 1, squared so that it needs no division or root:
+//   (d_i W - M)^2 z_i^2 <= tol^2 W (W + z_i^2)^2   <=>   |d_i - d~| |z_i| z~ <= tol (z~^2 + z_i^2).
+// It is homogeneous in d (with tol) and in z; the caller scales both by powers of two.
+__device__ __forceinline__ bool merges(double di, double zi, double W, double M, double tol2) {
+  const double zi2 = zi * zi;
+  const double g = fma(di, W, -M);
+  const double s = W + zi2;
+  return g * g * zi2 <= tol2 * W * s * s;
+}
+
 __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status, int in_smem) {
   extern __shared__ double dsm[];
-  __shared__ double sred[2][32];
+  __shared__ double sred[3][32];
   __shared__ int scnt[kDeflateThreads];
   __shared__ double sW[kDeflateThreads], sM[kDeflateThreads];
-  __shared__ double s_tol, s_zn;
+  __shared__ double s_tol, s_zn, s_dsc, s_zsc;
   const int N = e.N;
   const double rho = e.rhop[0];
   int tid = threadIdx.x, nt = blockDim.x;
-  double zn2 = 0.0, dmax = 0.0;
+  double zn2 = 0.0, dmax = 0.0, zmax = 0.0;
   for (int s = tid; s < N; s += nt) {
     double z = e.zs[s], d = e.ds[s];
     zn2 = fma(z, z, zn2);
     dmax = fmax(dmax, fabs(d));
+    zmax = fmax(zmax, fabs(z));
   }
   zn2 = warp_sum(zn2);
   dmax = warp_max(dmax);
-  if ((tid & 31) == 0) { sred[0][tid >> 5] = zn2; sred[1][tid >> 5] = dmax; }
+  zmax = warp_max(zmax);
+  if ((tid & 31) == 0) { sred[0][tid >> 5] = zn2; sred[1][tid >> 5] = dmax; sred[2][tid >> 5] = zmax; }
   __syncthreads();
   if (tid < 32) {
     int nw = nt >> 5;
     zn2 = tid < nw ? sred[0][tid] : 0.0;
     dmax = tid < nw ? sred[1][tid] : 0.0;
+    zmax = tid < nw ? sred[2][tid] : 0.0;
     zn2 = warp_sum(zn2);
     dmax = warp_max(dmax);
+    zmax = warp_max(zmax);
     if (tid == 0) {
       double t = fabs(rho) * zn2;
       s_tol = 8.0 * kU * fmax(dmax, t);
       s_zn = sqrt(zn2);
+      // exact power-of-two scalings that bring max|d| and max|z| near 1 for the merge test
+      s_dsc = (dmax > 0.0 && isfinite(dmax)) ? ldexp(1.0, -ilogb(dmax)) : 1.0;
+      s_zsc = (zmax > 0.0 && isfinite(zmax)) ? ldexp(1.0, -ilogb(zmax)) : 1.0;
       e.tol[0] = s_tol;
       if (!isfinite(s_tol) || !isfinite(rho)) latch(status, SVDUP_ENONFINITE);
     }
   }
   __syncthreads();
-  const double tol = s_tol, zn = s_zn;
+  const double tol = s_tol, zn = s_zn, dsc = s_dsc, zsc = s_zsc;
+  const double tolS = tol * dsc, tol2 = tolS * tolS;
   const int nwords = (N + 31) >> 5;
   unsigned* cmask = (unsigned*)dsm;   // pair (i-1, i) passes with the original values
-  unsigned* pmask = cmask + nwords;   // pair (i-1, i) merged: i continues the run of i-1
-  double* kd;
-  double* kz;
-  int* kpos;
+  double* kd;                         // survivors' d * dsc
+  double* kz;                         // survivors' z * zsc
+  int* kpos;                          // survivors' sorted positions
+  unsigned char* brk;                 // 1: survivor i starts a run (pair (i-1, i) not merged)
   if (in_smem) {
-    char* base = (char*)dsm + (((size_t)2 * nwords * sizeof(unsigned) + 15) & ~(size_t)15);
+    char* base = (char*)dsm + (((size_t)nwords * sizeof(unsigned) + 15) & ~(size_t)15);
     kd = (double*)base;
     kz = kd + N;
     kpos = (int*)(kz + N);
+    brk = (unsigned char*)(kpos + N);
   } else {  // global scratch that the compaction below overwrites anyway
     kd = e.dk;
     kz = e.zk;
     kpos = e.idx;
+    brk = (unsigned char*)e.didx;
   }
-  for (int w = tid; w < 2 * nwords; w += nt) cmask[w] = 0u;
+  for (int w = tid; w < nwords; w += nt) cmask[w] = 0u;
   // case (1) on my contiguous chunk [b0, b1), then the survivors' positions in order
   const int chunk = (N + nt - 1) / nt;
   const int b0 = min(N, tid * chunk), b1 = min(N, b0 + chunk);
@@ -335,87 +361,120 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
   for (int s = b0; s < b1; s++) {
     if (e.defl[s]) continue;
     kpos[pos] = s;
-    kd[pos] = e.ds[s];
-    kz[pos] = e.zs[s];
+    kd[pos] = e.ds[s] * dsc;
+    kz[pos] = e.zs[s] * zsc;
     pos++;
   }
   __syncthreads();
-  // case (3) pre-test with the original values
-  for (int i = 1 + tid; i < nk; i += nt) {
-    double zj = kz[i - 1], zi = kz[i];
-    if (fabs(kd[i] - kd[i - 1]) * fabs(zi * zj) <= tol * fma(zi, zi, zj * zj))
-      atomicOr(&cmask[i >> 5], 1u << (i & 31));
+  // case (3) pre-test with the original values; it also seeds the run boundaries
+  for (int i = tid; i < nk; i += nt) {
+    bool m = false;
+    if (i > 0) {
+      const double zj = kz[i - 1];
+      const double W = zj * zj;
+      m = merges(kd[i], kz[i], W, W * kd[i - 1], tol2);
+      if (m) atomicOr(&cmask[i >> 5], 1u << (i & 31));
+    }
+    brk[i] = m ? 0 : 1;
   }
   __syncthreads();
-  // the walk: run boundaries from the running sums W = z~^2, M = W d~
-  if (tid == 0) {
-    int i = next_set(cmask, 1, nk);
-    double W = 0.0, M = 0.0;
-    bool run = false;
-    while (i < nk) {
-      if (!run) {
-        double zj = kz[i - 1];
-        W = zj * zj;
-        M = W * kd[i - 1];
+  // Run boundaries by one warp walking the survivors 32 pairs at a time.  From position
+  // pos with carrier (W, M), lane l tests pair (pos + l - 1, pos + l) against the
+  // carrier that exists if every earlier lane merged (W, M plus the lanes' exclusive
+  // prefix sums of z^2 and z^2 d): exactly the sequential carrier up to the first lane
+  // that fails.  Earlier lanes merge; the failing position starts a new run, and the
+  // walk resumes at the next pair that passes with the original values (only such a
+  // pair can start a merge).
+  const int cpt = (nk + nt - 1) / nt;
+  const int c0 = min(nk, tid * cpt), c1 = min(nk, c0 + cpt);
+  for (int i = tid; i < nk; i += nt) brk[i] = 1;
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    const int nw = (nk + 31) >> 5;
+    auto next_cand = [&](int from) -> int {  // first set bit of cmask at or after from
+      if (from >= nk) return nk;
+      for (int w0 = from >> 5; w0 < nw; w0 += 32) {
+        const int w = w0 + lane;
+        unsigned m = 0u;
+        if (w < nw) {
+          m = cmask[w];
+          if (w == (from >> 5)) m &= 0xffffffffu << (from & 31);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
+        if (bal) {
+          const int src = __ffs(bal) - 1;
+          const unsigned mm = __shfl_sync(0xffffffffu, m, src);
+          return min(nk, ((w0 + src) << 5) + __ffs(mm) - 1);
+        }
       }
-      const double zi = kz[i], di = kd[i], zi2 = zi * zi;
-      if (fabs(fma(di, W, -M)) * fabs(zi) * sqrt(W) <= tol * W * (W + zi2)) {
-        pmask[i >> 5] |= 1u << (i & 31);
-        W += zi2;
-        M = fma(zi2, di, M);
-        run = true;
-        i = i + 1;  // the next survivor now pairs with the carrier
+      return nk;
+    };
+    int pos = next_cand(1);
+    bool have = false;
+    double W = 0.0, M = 0.0;
+    while (pos < nk) {
+      if (!have) {
+        const double zj = kz[pos - 1];
+        W = zj * zj;
+        M = W * kd[pos - 1];
+      }
+      const int i = pos + lane;
+      double zi = 0.0, di = 0.0;
+      if (i < nk) { zi = kz[i]; di = kd[i]; }
+      const double z2 = zi * zi, dz = z2 * di;
+      double iz2 = z2, idz = dz;  // inclusive prefix over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double a2 = __shfl_up_sync(0xffffffffu, iz2, o);
+        const double ad = __shfl_up_sync(0xffffffffu, idz, o);
+        if (lane >= o) { iz2 += a2; idz += ad; }
+      }
+      const bool ok = i < nk && merges(di, zi, W + (iz2 - z2), M + (idz - dz), tol2);
+      const unsigned fail = __ballot_sync(0xffffffffu, !ok);
+      const int nm = fail ? __ffs(fail) - 1 : 32;  // lanes that merge
+      if (lane < nm) brk[i] = 0;
+      if (nm == 32) {
+        W += __shfl_sync(0xffffffffu, iz2, 31);
+        M += __shfl_sync(0xffffffffu, idz, 31);
+        have = true;
+        pos += 32;
       } else {
-        run = false;
-        i = next_set(cmask, i + 1, nk);
+        have = false;
+        pos = next_cand(pos + nm + 1);
       }
     }
   }
   __syncthreads();
-  // segmented sums over the runs, thread t owning survivors [c0, c1)
-  const int cpt = (nk + nt - 1) / nt;
-  const int c0 = min(nk, tid * cpt), c1 = min(nk, c0 + cpt);
+  // rotation records and merged values from the runs (segmented sums again)
   {
     double lW = 0.0, lM = 0.0;
     int lflag = 0, lrot = 0;
     for (int i = c0; i < c1; i++) {
       const double z2 = kz[i] * kz[i];
-      if (!bit_at(pmask, i)) { lflag = 1; lW = z2; lM = z2 * kd[i]; }
+      if (brk[i]) { lflag = 1; lW = z2; lM = z2 * kd[i]; }
       else { lW += z2; lM = fma(z2, kd[i], lM); lrot++; }
     }
     int nrot;
     const int rbase = block_excl_scan(lrot, scnt, &nrot);
-    // inclusive segmented scan of (flag, W, M) over the chunks
-    scnt[tid] = lflag;
-    sW[tid] = lW;
-    sM[tid] = lM;
-    __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {
-      int f2 = 0;
-      double W2 = 0.0, M2 = 0.0;
-      if (tid >= off) { f2 = scnt[tid - off]; W2 = sW[tid - off]; M2 = sM[tid - off]; }
-      __syncthreads();
-      if (tid >= off && !scnt[tid]) { sW[tid] += W2; sM[tid] += M2; scnt[tid] = f2; }
-      __syncthreads();
-    }
-    double W = tid > 0 ? sW[tid - 1] : 0.0;  // the run through survivor c0 - 1
-    double M = tid > 0 ? sM[tid - 1] : 0.0;
+    double W, M;
+    run_carry(lflag, lW, lM, scnt, sW, sM, &W, &M);
     int ridx = rbase;
     for (int i = c0; i < c1; i++) {
-      const bool p = bit_at(pmask, i);
+      const bool p = !brk[i];
       const double zi = kz[i], di = kd[i], z2 = zi * zi;
       if (!p) {
         W = z2;
         M = z2 * di;
       } else {
         // rotation merging survivor i-1 (the carrier) into i
-        const double zprev = bit_at(pmask, i - 1) ? sqrt(W) : kz[i - 1];  // signed at a run start
+        const double zprev = brk[i - 1] ? kz[i - 1] : sqrt(W);  // signed at a run start
         const double Wn = W + z2;
         const double rn = sqrt(Wn);
         const double cs = zi / rn, sn = zprev / rn;
         const double dprev = M / W;
         const int pj = kpos[i - 1], pi = kpos[i];
-        e.ds[pj] = cs * cs * dprev + sn * sn * di;
+        e.ds[pj] = (cs * cs * dprev + sn * sn * di) / dsc;
         e.zs[pj] = 0.0;
         e.defl[pj] = 1;
         e.rj[ridx] = pj; e.ri[ridx] = pi; e.rc[ridx] = cs; e.rs[ridx] = sn;
@@ -423,10 +482,10 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
         W = Wn;
         M = fma(z2, di, M);
       }
-      if (!(i + 1 < nk && bit_at(pmask, i + 1))) {  // not merged away by the next pair
+      if (!(i + 1 < nk && !brk[i + 1])) {  // not merged away by the next pair
         const int ps = kpos[i];
-        if (p) { e.ds[ps] = M / W; e.zs[ps] = sqrt(W); }
-        else { e.ds[ps] = di; e.zs[ps] = zi; }
+        if (p) { e.ds[ps] = (M / W) / dsc; e.zs[ps] = sqrt(W) / zsc; }
+        else { e.ds[ps] = di / dsc; e.zs[ps] = zi / zsc; }
       }
     }
     if (tid == 0) e.nrot[0] = nrot;
@@ -503,13 +562,12 @@ __device__ __forceinline__ SecSums secular_sums(const double* __restrict__ dc,
     double dt = t * rc;
     if (i <= jsplit) { r.psiL += t; r.dpsiL += dt; }
     else { r.psiR += t; r.dpsiR += dt; }
-    r.asum += fabs(t);
   }
   r.psiL = warp_sum(r.psiL);
   r.dpsiL = warp_sum(r.dpsiL);
   r.psiR = warp_sum(r.psiR);
   r.dpsiR = warp_sum(r.dpsiR);
-  r.asum = warp_sum(r.asum);
+  r.asum = r.psiR - r.psiL;  // poles left of the root give negative terms, right positive
   return r;
 }
 
@@ -633,6 +691,24 @@ struct FarSums {
   __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
     SecSums s = {0.0, 0.0, 0.0, 0.0, 0.0};
     const double dO = dc[o];
+    // barycentric weights of the far field at the box coordinate of mu
+    const double yh = (((dO - base) + tau) - r) / r;
+    double c = 0.0;
+    int hit = 0;
+    if (lane < kSqP) {
+      const double df = yh - sx[lane];
+      if (df == 0.0) hit = 1;
+      else c = sw[lane] / df;
+    }
+    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+    if (hm) c = (lane == __ffs(hm) - 1) ? 1.0 : 0.0;  // mu sits exactly on a node
+    else c = c / warp_sum(c);
+    if (lane < kSqP) {  // far-left terms are negative, far-right positive
+      s.psiL = c * vals[lane];
+      s.dpsiL = c * vals[kSqP + lane];
+      s.psiR = c * vals[2 * kSqP + lane];
+      s.dpsiR = c * vals[3 * kSqP + lane];
+    }
     for (int i = n0 + lane; i < n1; i += 32) {
       double del = (dc[i] - dO) - tau;
       double rc = rcp64(del);
@@ -640,50 +716,45 @@ struct FarSums {
       double dt = t * rc;
       if (i <= jsplit) { s.psiL += t; s.dpsiL += dt; }
       else { s.psiR += t; s.dpsiR += dt; }
-      s.asum += fabs(t);
     }
     s.psiL = warp_sum(s.psiL);
     s.dpsiL = warp_sum(s.dpsiL);
     s.psiR = warp_sum(s.psiR);
     s.dpsiR = warp_sum(s.dpsiR);
-    s.asum = warp_sum(s.asum);
-    // barycentric interpolation at the box coordinate of mu
-    const double yh = (((dO - base) + tau) - r) / r;
-    double c = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0, f3 = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-    int hit = 0;
-    if (lane < kSqP) {
-      v0 = vals[lane];
-      v1 = vals[kSqP + lane];
-      v2 = vals[2 * kSqP + lane];
-      v3 = vals[3 * kSqP + lane];
-      const double df = yh - sx[lane];
-      if (df == 0.0) {
-        hit = 1;
-      } else {
-        c = sw[lane] / df;
-        f0 = c * v0; f1 = c * v1; f2 = c * v2; f3 = c * v3;
-      }
+    s.asum = s.psiR - s.psiL;
+    return s;
+  }
+};
+
+// All poles summed by a whole block (the extreme root, whose bracket reaches far past
+// the poles, when the far-field form serves the others).  Every thread calls it.
+struct BlockSums {
+  const double* dc;
+  const double* z2c;
+  int k;
+  double* red;  // shared, 4 x 32
+  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const double dO = dc[o];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      double del = (dc[i] - dO) - tau;
+      double rc = rcp64(del);
+      double t = z2c[i] * rc;
+      double dt = t * rc;
+      if (i <= jsplit) { v[0] += t; v[1] += dt; }
+      else { v[2] += t; v[3] += dt; }
     }
-    const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    double pL, dL, pR, dR;
-    if (hm) {  // mu sits exactly on a node
-      const int src = __ffs(hm) - 1;
-      pL = __shfl_sync(0xffffffffu, v0, src);
-      dL = __shfl_sync(0xffffffffu, v1, src);
-      pR = __shfl_sync(0xffffffffu, v2, src);
-      dR = __shfl_sync(0xffffffffu, v3, src);
-    } else {
-      const double den = warp_sum(c);
-      pL = warp_sum(f0) / den;
-      dL = warp_sum(f1) / den;
-      pR = warp_sum(f2) / den;
-      dR = warp_sum(f3) / den;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      v[q] = warp_sum(v[q]);
+      if (lane == 0) red[q * 32 + w] = v[q];
     }
-    s.psiL += pL;   // far-left terms are negative, far-right positive
-    s.dpsiL += dL;
-    s.psiR += pR;
-    s.dpsiR += dR;
-    s.asum += pR - pL;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = warp_sum(lane < nw ? red[q * 32 + lane] : 0.0);
+    __syncthreads();
+    SecSums s = {v[0], v[1], v[2], v[3], v[2] - v[0]};
     return s;
   }
 };
@@ -804,7 +875,8 @@ __global__ void k_secular(const double* __restrict__ dc, const double* __restric
     int o;
     double t;
     int bad;
-    if (far && j < k - 1) {
+    if (far && j == k - 1) continue;  // k_secular_last
+    if (far) {
       const int b = j / kSqLeaf;
       const FarSums fs = {dc, z2c, sqn[2 * b], sqn[2 * b + 1], sqb[2 * b], sqb[2 * b + 1],
                           sqv + (size_t)4 * b * kSqP, s_x, s_w};
@@ -831,6 +903,51 @@ __global__ void k_secular(const double* __restrict__ dc, const double* __restric
   }
 }
 
+// The extreme root alone, its sums spread over a whole block.
+__global__ void __launch_bounds__(512) k_secular_last(
+    const double* __restrict__ dc, const double* __restrict__ z2c, const int* __restrict__ kp,
+    const double* __restrict__ rhop, const double* __restrict__ dk, int* orgc, double* tauc,
+    int* org, double* tau, double* dorg, int* status, int maxit) {
+  __shared__ double red[4 * 32];
+  __shared__ double s_zn2;
+  const int k = kp[0];
+  if (k < kSqMinK) return;
+  const double rho = rhop[0];
+  const double R = fabs(rho);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) a += z2c[i];
+  a = warp_sum(a);
+  if (lane == 0) red[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q];
+    s_zn2 = t;
+  }
+  __syncthreads();
+  const BlockSums bs = {dc, z2c, k, red};
+  int o;
+  double t;
+  const int j = k - 1;
+  const int bad = secular_root(bs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
+  if (threadIdx.x == 0) {
+    if (bad) latch(status, SVDUP_ENOCONV);
+    if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
+    orgc[j] = o;
+    tauc[j] = t;
+    if (rho > 0.0) {
+      org[j] = o;
+      tau[j] = t;
+      dorg[j] = dk[o];
+    } else {
+      org[0] = k - 1 - o;
+      tau[0] = -t;
+      dorg[0] = dk[k - 1 - o];
+    }
+  }
+}
+
 static int secular_blocks(int N) {
   int warps = N;                   // one warp per root
   int blocks = (warps * 32 + 255) / 256;
@@ -852,6 +969,11 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
                                                 e.org, e.tau, e.dorg, status, maxit, e.sqb,
                                                 e.sqn, sqv);
   SVDUP_COUNT_LAUNCH();
+  if (sqv) {
+    k_secular_last<<<1, 512, 0, st>>>(e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org,
+                                      e.tau, e.dorg, status, maxit);
+    SVDUP_COUNT_LAUNCH();
+  }
 }
 
 // The stand-alone secular entry point: d strictly ascending, z nonzero; the problem
@@ -882,44 +1004,57 @@ void launch_secular_direct(cudaStream_t st, Eig e, int k, const double* d, const
 // ---------------------------------------------------------------------------
 // All N eigenvalues in ascending order: the roots (already ascending) merged with the
 // deflated poles (kept values after rotation).  Ties: deflated before roots, then by
-// index.  rank_root / rank_defl record where each one went.
+// index.  rank_root / rank_defl record where each one went.  The ranks are counted over
+// shared-memory chunks of the deflated values by many blocks: one thread per eigenvalue
+// (roots first, then deflated), each comparing its value with every deflated value
+// (broadcast reads) and, for a deflated value, binary searching the ascending roots.
 // ---------------------------------------------------------------------------
-__global__ void k_merge(Eig e) {
+constexpr int kMergeChunk = 2048;
+
+__global__ void __launch_bounds__(128) k_merge_count(Eig e) {
+  __shared__ double sv[kMergeChunk];
   const int N = e.N, k = e.kp[0], nd = N - k;
-  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-    if (x < k) {
-      int j = x;
-      double mu = e.dorg[j] + e.tau[j];
-      int c = 0;
-      for (int t = 0; t < nd; t++) c += (e.ds[e.didx[t]] <= mu);
-      int r = j + c;
-      e.lam[r] = mu;
-      e.rank_root[j] = r;
-    } else {
-      int t = x - k;
-      int s = e.didx[t];
-      double v = e.ds[s];
-      int c = 0;
-      for (int u = 0; u < nd; u++) {
-        double w = e.ds[e.didx[u]];
-        c += (w < v) || (w == v && u < t);
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool root = x < k;
+  double key = 0.0;
+  if (x < N) key = root ? e.dorg[x] + e.tau[x] : e.ds[e.didx[x - k]];
+  const int me = x - k;
+  int cnt = 0;
+  for (int c0 = 0; c0 < nd; c0 += kMergeChunk) {
+    const int cn = min(kMergeChunk, nd - c0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cn; t += blockDim.x) sv[t] = e.ds[e.didx[c0 + t]];
+    __syncthreads();
+    if (x < N) {
+      if (root) {
+        for (int t = 0; t < cn; t++) cnt += (sv[t] <= key);
+      } else {
+        for (int t = 0; t < cn; t++) {
+          const double w = sv[t];
+          cnt += (w < key) || (w == key && c0 + t < me);
+        }
       }
-      // roots strictly below v (binary search: roots ascending)
-      int lo = 0, hi = k;
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        double mu = e.dorg[mid] + e.tau[mid];
-        if (mu < v) lo = mid + 1; else hi = mid;
-      }
-      int r = c + lo;
-      e.lam[r] = v;
-      e.rank_defl[s] = r;
     }
+  }
+  if (x >= N) return;
+  if (root) {
+    const int r = x + cnt;
+    e.lam[r] = key;
+    e.rank_root[x] = r;
+  } else {
+    int lo = 0, hi = k;  // roots strictly below the value
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (e.dorg[mid] + e.tau[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    const int r = cnt + lo;
+    e.lam[r] = key;
+    e.rank_defl[e.didx[me]] = r;
   }
 }
 
 void launch_merge(cudaStream_t st, Eig e) {
-  k_merge<<<(e.N + 255) / 256, 256, 0, st>>>(e);
+  k_merge_count<<<(e.N + 127) / 128, 128, 0, st>>>(e);
   SVDUP_COUNT_LAUNCH();
 }
 
@@ -1025,35 +1160,97 @@ static size_t vec_smem(int N) {
   return b <= 160 * 1024 ? b : 0;
 }
 
-// One thread applies the rotations in order; the rotation records are staged through
-// shared memory in chunks so that its loop touches shared memory only.
-constexpr int kVecRotChunk = 1024;
+// The deflation rotations applied to one vector v (shared or global memory), by the
+// whole block.  Rotation i acts on positions (a_i, b_i) with (cos, sin) = (c_i, s_i) and
+// either opens a chain or continues the previous one (a_i = b_{i-1}); no position is
+// read after it is written, so with x the original values each direction is an affine
+// recurrence over the rotation list, evaluated as a block-wide scan of affine maps over
+// per-thread chunks of the list:
+//  forward (G, in order):      u_i = chained_i ? v_{i-1} : x_{a_i},  v_i = s_i u_i + c_i x_{b_i},
+//                              out_{a_i} = c_i u_i - s_i x_{b_i},  out_{b_i} = v_i at a chain end;
+//  transposed (G^T, reversed): w_i = chained_{i+1} ? c_{i+1} x_{b_i} + s_{i+1} w_{i+1} : x_{b_i},
+//                              out_{b_i} = c_i w_i - s_i x_{a_i},
+//                              out_{a_i} = c_i x_{a_i} + s_i w_i unless chained_i.
+// The one value two chunks share (the boundary position of a chain crossing chunks) is
+// read before the scan and kept in a register.
+__device__ __forceinline__ bool rot_chained(const Eig& e, int i) {
+  return i > 0 && e.rj[i] == e.ri[i - 1];
+}
 
-__device__ void rotate_vector_serial(const Eig& e, double* v, bool transpose) {
-  __shared__ int sa[kVecRotChunk], sb[kVecRotChunk];
-  __shared__ double sc[kVecRotChunk], ss[kVecRotChunk];
-  const int nr = e.nrot[0];
-  for (int c0 = 0; c0 < nr; c0 += kVecRotChunk) {
-    const int cn = min(kVecRotChunk, nr - c0);
+// Inclusive scan of affine maps v -> A v + B over the block's threads, composing in
+// increasing thread order (dir > 0) or decreasing (dir < 0).  Returns the B of the
+// composition of the chunks before the caller's (the carry entering its chunk).
+__device__ double affine_carry(double A, double B, int dir, double* sA, double* sB) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int me = dir > 0 ? tid : nt - 1 - tid;  // position in composition order
+  sA[me] = A;
+  sB[me] = B;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    double Al = 1.0, Bl = 0.0;
+    if (me >= off) { Al = sA[me - off]; Bl = sB[me - off]; }
     __syncthreads();
-    for (int i = threadIdx.x; i < cn; i += blockDim.x) {
-      const int g = transpose ? nr - 1 - (c0 + i) : c0 + i;
-      sa[i] = e.rj[g]; sb[i] = e.ri[g]; sc[i] = e.rc[g]; ss[i] = e.rs[g];
+    if (me >= off) {
+      const double Ar = sA[me], Br = sB[me];
+      sA[me] = Ar * Al;
+      sB[me] = fma(Ar, Bl, Br);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int i = 0; i < cn; i++) {
-        const int a = sa[i], b = sb[i];
-        const double c = sc[i], sn = ss[i];
-        const double va = v[a], vb = v[b];
-        if (!transpose) {
-          v[a] = c * va - sn * vb;
-          v[b] = sn * va + c * vb;
-        } else {
-          v[a] = c * va + sn * vb;
-          v[b] = -sn * va + c * vb;
-        }
+  }
+  const double carry = me > 0 ? sB[me - 1] : 0.0;
+  __syncthreads();
+  return carry;
+}
+
+__device__ void rotate_vector(const Eig& e, double* v, bool transpose) {
+  __shared__ double sA[1024], sB[1024];
+  const int nr = e.nrot[0];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int per = (nr + nt - 1) / nt;
+  const int i0 = min(nr, tid * per), i1 = min(nr, i0 + per);
+  if (!transpose) {
+    double A = 1.0, B = 0.0, xlast = 0.0;
+    for (int i = i0; i < i1; i++) {
+      const double c = e.rc[i], sn = e.rs[i];
+      const double xb = v[e.ri[i]];
+      if (rot_chained(e, i)) { A = sn * A; B = fma(sn, B, c * xb); }
+      else { A = 0.0; B = fma(sn, v[e.rj[i]], c * xb); }
+      xlast = xb;
+    }
+    double vc = affine_carry(A, B, 1, sA, sB);
+    for (int i = i0; i < i1; i++) {
+      const int a = e.rj[i], b = e.ri[i];
+      const double c = e.rc[i], sn = e.rs[i];
+      const double xb = (i == i1 - 1) ? xlast : v[b];
+      const double u = rot_chained(e, i) ? vc : v[a];
+      v[a] = c * u - sn * xb;
+      vc = fma(sn, u, c * xb);
+      if (i + 1 >= nr || e.rj[i + 1] != b) v[b] = vc;
+    }
+  } else {
+    double A = 1.0, B = 0.0, xfirst = 0.0;
+    if (i0 < i1) xfirst = v[e.rj[i0]];
+    for (int i = i1 - 1; i >= i0; i--) {  // w_i as a map of w_{i1}
+      const double xb = v[e.ri[i]];
+      if (i + 1 < nr && rot_chained(e, i + 1)) {
+        const double c1 = e.rc[i + 1], s1 = e.rs[i + 1];
+        A = s1 * A;
+        B = fma(s1, B, c1 * xb);
+      } else {
+        A = 0.0;
+        B = xb;
       }
+    }
+    double w = affine_carry(A, B, -1, sA, sB);  // w_{i1}
+    for (int i = i1 - 1; i >= i0; i--) {
+      const int a = e.rj[i], b = e.ri[i];
+      const double c = e.rc[i], sn = e.rs[i];
+      const double xb = v[b];
+      if (i + 1 < nr && rot_chained(e, i + 1)) w = fma(e.rs[i + 1], w, e.rc[i + 1] * xb);
+      else w = xb;
+      const double xa = (i == i0) ? xfirst : v[a];
+      v[b] = c * w - sn * xa;
+      if (!rot_chained(e, i)) v[a] = fma(c, xa, sn * w);
     }
   }
   __syncthreads();
@@ -1065,7 +1262,7 @@ __global__ void __launch_bounds__(1024) k_gather_rotate(Eig e, const double* __r
   double* v = in_smem ? vsm : ysorted;
   for (int s = threadIdx.x; s < e.N; s += blockDim.x) v[s] = xphys[e.perm[s]];
   __syncthreads();
-  rotate_vector_serial(e, v, false);
+  rotate_vector(e, v, false);
   if (in_smem)
     for (int s = threadIdx.x; s < e.N; s += blockDim.x) ysorted[s] = v[s];
 }
@@ -1107,7 +1304,7 @@ __global__ void __launch_bounds__(1024) k_unrotate_scatter(Eig e, double* vsorte
   if (in_smem)
     for (int s = threadIdx.x; s < e.N; s += blockDim.x) v[s] = vsorted[s];
   __syncthreads();
-  rotate_vector_serial(e, v, true);
+  rotate_vector(e, v, true);
   for (int s = threadIdx.x; s < e.N; s += blockDim.x) yphys[e.perm[s]] = v[s];
 }
 

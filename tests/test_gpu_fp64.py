@@ -296,3 +296,33 @@ print("ok")
 ''' % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("mode_name", ["FP64", "MIXED_BF16X3"])
+def test_long_deflation_chain(sv, hnd, orc, mode_name):
+    """A cluster of 1200 numerically equal poles merges into one Givens chain of 1199
+    rotations, which crosses many chunks of the parallel rotation scans (columns and
+    vectors) and needs several sweeps of the run-boundary iteration."""
+    g = np.random.default_rng(21)
+    N, rows = 2000, 100
+    d = np.sort(g.uniform(0, 1, N))
+    d[200:1400] = d[200] * (1.0 + 1e-18 * np.arange(1200))
+    z = g.standard_normal(N)
+    rho = 0.9
+    X = wl.haar(N, g)[:rows, :N]
+    lam_o, Y_o = orc.rank_one_update_z(X, d, z, rho)
+    mode = getattr(sv, mode_name)
+    lam_g, Y_g = hnd.cauchy_product(devF(X), dev(d), dev(z), rho, eps=1e-12, mode=mode)
+    lam_g = lam_g.cpu().numpy(); Y_g = Y_g.cpu().numpy()
+    assert np.abs(lam_g - lam_o).max() <= 1e-13 * np.abs(lam_o).max()
+    tol = 1e-10 if mode_name == "FP64" else 2e-6
+    # The cluster's 1199 deflated eigenvalues are equal to the last bits, so any
+    # orthonormal basis of their eigenspace is correct and the order of the ties depends
+    # on the rounding of the merged values: compare that block through X Q_C Q_C^T X^T,
+    # which does not depend on the basis, and every other column elementwise.
+    clus = np.abs(lam_o - d[200]) <= 64 * U53 * d[200]
+    assert clus.sum() >= 1199
+    assert np.abs(Y_g[:, ~clus] - Y_o[:, ~clus]).max() <= tol
+    G_g = Y_g[:, clus] @ Y_g[:, clus].T
+    G_o = Y_o[:, clus] @ Y_o[:, clus].T
+    assert np.abs(G_g - G_o).max() <= 10 * tol
