@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=0.25)
     return ap.parse_args()
 
 
@@ -271,10 +275,23 @@ def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, w
     lat = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(steps)])
     total_ms = float(ev[0].elapsed_time(ev[-1]))
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dev)
     return lat, total_ms, launches, stages, clk
+
+
+def max_over_ranks(ms, device):
+    """The slowest rank's time (every rank runs an independent replica; the whole-job
+    rate is the units of all ranks over this time).  Works on any process-group backend
+    (NCCL on the GPU, gloo on the CPU)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, ms, ws):
+    """Whole-job units per second: every rank did units_per_rank units in at most ms."""
+    return ws * units_per_rank / (ms / 1e3)
 
 
 def accuracy_report(sv, h, stream, upload, ta, tb, eps, mode, dev):
@@ -320,6 +337,128 @@ def accuracy_report(sv, h, stream, upload, ta, tb, eps, mode, dev):
     return res
 
 
+def batched_form(sv, dev, mode, eps, count, steps, warmup, lanes):
+    """The batching form: `count` independent square updates, n log-uniform in
+    [32, 1024], each A Gaussian (its SVD taken on the device with torch.linalg.svd,
+    input preparation only), a, b Gaussian.  The product path is autotuned first; the
+    batch is recorded once into a CUDA graph and launched steps times (chained updates
+    of all problems per launch); the same batch without a graph is timed once."""
+    import torch
+    from paper_1707_08369_gb300 import workloads as wl
+    ns = wl.uneven_sizes(count, 32, 1024, seed=wl.BASE_SEED + 3)
+    g = torch.Generator(device=dev)
+    g.manual_seed(wl.BASE_SEED + 3)
+    items = []
+    for n in ns:
+        n = int(n)
+        A = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+        U, S, Vh = torch.linalg.svd(A)
+        a = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+        b = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+        # column-major U and V = Vh^T (a transposed row-major tensor is column-major)
+        items.append((U.t().contiguous().t(), S.contiguous(), Vh.contiguous().t(), a, b))
+    torch.cuda.synchronize(dev)
+    h = sv.Handle(dev.index)
+    t0 = time.perf_counter()
+    tuned = h.autotune(mode, nmax=1024)
+    t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bt = h.batch_plan(items, eps=eps, mode=mode, lanes=lanes)
+    t_plan = time.perf_counter() - t0
+    for _ in range(warmup):
+        bt.launch(check=False)
+    rc = h.sync()
+    if rc:
+        raise SystemExit("batched warm-up failed: %s" % sv.error_string(rc))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(h.stream)
+    for _ in range(steps):
+        bt.launch(check=False)
+    e1.record(h.stream)
+    torch.cuda.synchronize(dev)
+    rc = h.sync()
+    if rc:
+        raise SystemExit("batched run failed: %s" % sv.error_string(rc))
+    ms = e0.elapsed_time(e1) / steps
+    kernels = bt.kernels()
+    bt.close()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    h.update_batched(items, eps=eps, mode=mode, lanes=lanes)
+    t_nograph = time.perf_counter() - t0
+    h.close()
+    return {"workload": "%d independent square updates, n log-uniform in [32, 1024], Gaussian A "
+                        "(SVD by torch.linalg.svd on the device as input), N(0,1) a, b" % count,
+            "value": count / (ms / 1e3), "unit": "updates/s", "ms_per_batch": ms, "steps": steps,
+            "lanes": lanes, "graph_kernels": kernels, "plan_s": t_plan,
+            "autotune": {"dense_max": tuned[0], "leaf128_min": tuned[1], "seconds": t_tune},
+            "no_graph_ms_per_batch": t_nograph * 1e3}
+
+
+def serving_form(sv, dev, mode, eps, seconds, rate, nmats, lanes, seed):
+    """The serving form: `nmats` resident SVDs of m x 2m matrices, m log-uniform in
+    [1024, 4096], spectrum log-uniform in [1e-4, 1] with Haar U, V (QR of Gaussians on the
+    device, input preparation only); rank-one updates with N(0,1) a, b arrive as a
+    Poisson stream at `rate` per second for `seconds`, each for a uniformly chosen
+    matrix, and are submitted to the serving engine as they arrive.  Reports the
+    sustained updates/s (completed / time from the first arrival to the last
+    completion) and the latency percentiles (submission to completion, queueing
+    included)."""
+    import torch
+    from paper_1707_08369_gb300 import workloads as wl
+    g = np.random.default_rng(seed)
+    ms = np.rint(1024 * 4.0 ** g.uniform(0, 1, nmats)).astype(int)
+    tg = torch.Generator(device=dev)
+    tg.manual_seed(seed)
+    srv = sv.Server(dev.index, lanes=lanes, eps=eps, mode=mode)
+    live, shapes = [], []
+    for m in ms:
+        m = int(m)
+        n = 2 * m
+        U, _ = torch.linalg.qr(torch.randn(m, m, dtype=torch.float64, device=dev, generator=tg))
+        V, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=tg))
+        S = torch.from_numpy(np.sort(10.0 ** (-4.0 * g.uniform(0, 1, m)))[::-1].copy()).to(dev)
+        U, V = U.t().contiguous().t(), V.t().contiguous().t()
+        live.append((U, S, V))
+        shapes.append((m, n))
+    torch.cuda.synchronize(dev)
+    ids = [srv.register(U, S, V) for U, S, V in live]
+    # warm the lanes' workspaces with one update per matrix (not timed)
+    for i, (m, n) in enumerate(shapes):
+        srv.wait(srv.submit(ids[i], g.standard_normal(m), g.standard_normal(n)))
+    nreq = max(1, int(rate * seconds))
+    gaps = g.exponential(1.0 / rate, nreq)
+    which = g.integers(0, nmats, nreq)
+    vecs = [(g.standard_normal(shapes[i][0]), g.standard_normal(shapes[i][1])) for i in which]
+    base = srv.stats()["completed"]
+    t0 = time.perf_counter()
+    arrive = t0 + np.cumsum(gaps)
+    tickets = []
+    for k in range(nreq):
+        while time.perf_counter() < arrive[k]:
+            pass
+        tickets.append(srv.submit(ids[int(which[k])], *vecs[k]))
+    lats = []
+    for t in tickets:
+        st, lat = srv.wait(t)
+        if st:
+            raise SystemExit("serving update failed: %s" % sv.error_string(st))
+        lats.append(lat)
+    t_end = time.perf_counter()
+    stats = srv.stats()
+    srv.close()
+    lats = np.array(lats)
+    return {"workload": "%d resident SVDs m x 2m, m log-uniform in [1024, 4096], sigma log-uniform "
+                        "[1e-4, 1]; Poisson arrivals of N(0,1) rank-one updates at %g/s for %g s"
+                        % (nmats, rate, seconds),
+            "value": nreq / (t_end - t0), "unit": "updates/s (sustained)", "requests": nreq,
+            "offered_per_s": rate, "lanes": lanes,
+            "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99))},
+            "max_in_flight": stats["max_in_flight"], "max_workspace_bytes": stats["max_ws_bytes"],
+            "completed_total": stats["completed"] - base}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -356,7 +495,7 @@ def main():
     clocks = ClockSampler(local)
     lat, total_ms, launches, stages, clk = timed_updates(
         sv, h, stream, tU, tS, tV, ta, tb, mode, args.eps, args.warmup, args.steps, ws, dev, clocks)
-    value = ws * args.steps / (total_ms / 1e3)
+    value = replica_rate(args.steps, total_ms, ws)
 
     # the plain FP64 form on the same GPU, same workload (the comparison the metric names)
     fp64 = None
@@ -376,6 +515,13 @@ def main():
 
     accuracy = None if args.no_accuracy else accuracy_report(
         sv, h, stream, upload, ta, tb, args.eps, mode, dev)
+    batched = None
+    if not args.no_batched and ws == 1:
+        batched = batched_form(sv, dev, mode, args.eps, args.batch_count, 5, 2, 16)
+    serving = None
+    if not args.no_serving and ws == 1:
+        serving = serving_form(sv, dev, mode, args.eps, args.serve_seconds, 2000.0, 16, 8,
+                               170708369 + 4)
 
     # dominant product stage -> roofline (stage timers bracket exactly that kernel's launch)
     peaks, peak_src = load_peaks()
@@ -447,6 +593,8 @@ def main():
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                 "fp64": fp64,
                 "accuracy": accuracy,
+                "batched": batched,
+                "serving": serving,
                 "stage_ms_per_update": stage_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk}

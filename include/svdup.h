@@ -187,6 +187,99 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
                          const double* z, double rho, double* Y, int ldy, double* lam, double eps,
                          int mode);
 
+/* ---- batches of independent updates ------------------------------------- */
+/* One problem of a batch: the arguments of svdup_update (device pointers). */
+typedef struct svdup_problem {
+  int m, n;
+  double* U;
+  int ldu;
+  double* S;
+  double* V;
+  int ldv;
+  const double* a;
+  const double* b;
+} svdup_problem;
+
+typedef struct svdup_batch* svdup_batch_t;
+
+/*
+ * Plan a batch of independent updates (no counterpart in the paper: a way to run
+ * many Alg. 6.1 updates at once).  The problems are spread over `lanes` streams
+ * forked from the handle's stream (largest first, each to the least-loaded lane);
+ * every lane gets its own workspace, sized here for its largest problem, and shares
+ * the handle's status word.  The whole batch is recorded once into a CUDA graph, so a
+ * launch is a single graph launch on the handle's stream.  The graph is bound to the
+ * given pointers and sizes: launching it again updates the same buffers in place
+ * (chained updates).  lanes: 1..64 (0 picks 16).  The problem array is copied.
+ */
+int svdup_batch_create(svdup_t h, int count, const svdup_problem* probs, double eps, int mode,
+                       int lanes, svdup_batch_t* out);
+/* Queue the planned batch on the handle's stream (asynchronous; svdup_sync on the
+ * handle waits and returns the first device error of any problem). */
+int svdup_batch_launch(svdup_batch_t b);
+/* Number of kernel launches one svdup_batch_launch replays (graph nodes). */
+long long svdup_batch_kernels(svdup_batch_t b);
+int svdup_batch_destroy(svdup_batch_t b);
+/* The same batch without a graph: plans, queues, waits, releases.  Returns the first
+ * error of the whole call. */
+int svdup_update_batched(svdup_t h, int count, const svdup_problem* probs, double eps, int mode,
+                         int lanes);
+
+/*
+ * Autotuning of the product path for `mode` (no counterpart in the paper).  For
+ * N = 256, 512, ... up to nmax it times the Cauchy product (rows = N, synthetic poles
+ * and vectors generated on the device) with the dense tile product, the far field with
+ * leaves of 64 poles, and with leaves of 128, and keeps on the handle the largest N at
+ * which the dense product was fastest (dense_max) and the smallest N at which leaves
+ * of 128 beat 64 (leaf128_min).  svdup_tuning_get / svdup_tuning_set read and restore
+ * these two numbers (to cache them between processes).
+ */
+int svdup_autotune(svdup_t h, int mode, int nmax);
+int svdup_tuning_get(svdup_t h, int mode, int* dense_max, int* leaf128_min);
+int svdup_tuning_set(svdup_t h, int mode, int dense_max, int leaf128_min);
+
+/* Bytes of workspace svdup_update needs on this handle for an m x n problem in `mode`
+ * (the handle keeps the largest such workspace it has needed). */
+int svdup_update_workspace(svdup_t h, int m, int n, double eps, int mode, size_t* bytes);
+
+/* ---- serving: resident SVDs and a continuous stream of updates ------------- */
+/*
+ * A serving engine on one device (no counterpart in the paper, whose motivation in
+ * Sec. 1 is streaming data).  Callers register SVDs that stay resident in their own
+ * device buffers and then submit rank-one updates of them at any time.  One scheduler
+ * thread admits requests continuously: the oldest pending request whose matrix has no
+ * update in flight goes to a free lane (a stream with its own workspace) as soon as one
+ * is free and the free-HBM ledger (the workspace bytes of the updates in flight, capped
+ * by hbm_budget) has room for it.  Updates of different matrices run concurrently on
+ * the device; updates of one matrix apply in submission order.  Latency is measured on
+ * the host from submission to the completion of the update's last kernel.
+ *   lanes       1..64 concurrent updates (0 picks 8)
+ *   hbm_budget  bytes of workspace the engine may hold at once (0: 3/4 of free memory)
+ */
+typedef struct svdup_server* svdup_server_t;
+int svdup_server_create(int device, int lanes, size_t hbm_budget, double eps, int mode,
+                        svdup_server_t* out);
+/* Register a resident SVD (device pointers, as in svdup_update; the caller keeps them
+ * alive and leaves them alone while the engine runs).  *id receives its handle. */
+int svdup_server_register(svdup_server_t s, int m, int n, double* U, int ldu, double* S,
+                          double* V, int ldv, int* id);
+/* Submit an update of matrix id with HOST vectors a (m) and b (n), copied before the
+ * call returns.  *ticket identifies the request.  Never blocks on the device. */
+int svdup_server_submit(svdup_server_t s, int id, const double* a, const double* b,
+                        long long* ticket);
+/* Wait for a request; returns its status (SVDUP_OK or the device error of its update)
+ * and its latency in ms (may be NULL).  timeout_ms < 0 waits without limit; a request
+ * still running at the limit returns SVDUP_ETIMEOUT. */
+int svdup_server_wait(svdup_server_t s, long long ticket, double timeout_ms, double* latency_ms);
+/* Wait for every submitted request. */
+int svdup_server_drain(svdup_server_t s);
+/* Totals since create: completed updates, latency percentiles (ms), the largest number
+ * of updates in flight at once, and the largest workspace bytes held at once. */
+int svdup_server_stats(svdup_server_t s, long long* completed, double* p50_ms, double* p99_ms,
+                       int* max_in_flight, size_t* max_ws_bytes);
+/* Stop the scheduler (after draining) and release everything the engine allocated. */
+int svdup_server_destroy(svdup_server_t s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,8 +6,8 @@ kernels; PyTorch is used for device memory and streams.  There is no CPU
 fallback: if the shared library is missing or fails to load, every call raises.
 
 Names follow the C ABI: create / destroy / sync / update / update_host /
-rank_one_eig / secular / secular_static / cauchy_product / error_string /
-launch_count.
+rank_one_eig / secular / secular_static / cauchy_product / batch_create (batch_plan) /
+batch_launch / update_batched / autotune / tuning / error_string / launch_count.
 """
 from __future__ import annotations
 
@@ -54,8 +54,46 @@ def load(path: str = LIB_PATH):
     lib.svdup_secular.argtypes = [P, I, P, P, D, P, P]
     lib.svdup_cauchy_product.argtypes = [P, I, I, P, I, P, P, D, P, I, P, D, I]
     lib.svdup_secular_static.argtypes = [P, I, P, P, D, P, P, P]
+    lib.svdup_batch_create.argtypes = [P, I, P, D, I, I, ctypes.POINTER(P)]
+    lib.svdup_batch_launch.argtypes = [P]
+    lib.svdup_batch_kernels.argtypes = [P]
+    lib.svdup_batch_kernels.restype = ctypes.c_longlong
+    lib.svdup_batch_destroy.argtypes = [P]
+    lib.svdup_update_batched.argtypes = [P, I, P, D, I, I]
+    lib.svdup_autotune.argtypes = [P, I, I]
+    lib.svdup_tuning_get.argtypes = [P, I, P, P]
+    lib.svdup_tuning_set.argtypes = [P, I, I, I]
+    S_T = ctypes.c_size_t
+    lib.svdup_update_workspace.argtypes = [P, I, I, D, I, ctypes.POINTER(S_T)]
+    lib.svdup_server_create.argtypes = [I, I, S_T, D, I, ctypes.POINTER(P)]
+    lib.svdup_server_register.argtypes = [P, I, I, P, I, P, P, I, ctypes.POINTER(I)]
+    lib.svdup_server_submit.argtypes = [P, I, P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.svdup_server_wait.argtypes = [P, ctypes.c_longlong, D, ctypes.POINTER(D)]
+    lib.svdup_server_drain.argtypes = [P]
+    lib.svdup_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
+                                       ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(S_T)]
+    lib.svdup_server_destroy.argtypes = [P]
     _lib = lib
     return lib
+
+
+class Problem(ctypes.Structure):
+    """svdup_problem: the arguments of svdup_update for one member of a batch."""
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("U", ctypes.c_void_p),
+                ("ldu", ctypes.c_int), ("S", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("ldv", ctypes.c_int), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p)]
+
+
+def _problems(items):
+    """ctypes array of Problem from (U, S, V, a, b) device-tensor tuples."""
+    arr = (Problem * len(items))()
+    for i, (U, S, V, a, b) in enumerate(items):
+        m, n = S.numel(), b.numel()
+        for t, nm in ((U, "U"), (S, "S"), (V, "V"), (a, "a"), (b, "b")):
+            _dev_f64(t, nm)
+        arr[i] = Problem(m, n, U.data_ptr(), _colmajor_ld(U, m, m, "U"), S.data_ptr(), V.data_ptr(),
+                         _colmajor_ld(V, n, n, "V"), a.data_ptr(), b.data_ptr())
+    return arr
 
 
 def error_string(code: int) -> str:
@@ -165,6 +203,43 @@ class Handle:
         _check(load().svdup_update_host(self._h, m, n, p(U), m, p(S), p(V), n, p(a), p(b),
                                         float(eps), int(mode)), "svdup_update_host")
 
+    def batch_plan(self, items, eps: float = 1e-12, mode: int = FP64, lanes: int = 0):
+        """Record a batch of independent updates (a list of (U, S, V, a, b) device
+        tensors, as in update) into a CUDA graph; returns a Batch to launch."""
+        arr = _problems(items)
+        out = ctypes.c_void_p()
+        _check(load().svdup_batch_create(self._h, len(items), arr, float(eps), int(mode), int(lanes),
+                                         ctypes.byref(out)), "svdup_batch_create")
+        return Batch(self, out, items)
+
+    def update_batched(self, items, eps: float = 1e-12, mode: int = FP64, lanes: int = 0):
+        """The same batch without a graph; waits and raises on any error."""
+        arr = _problems(items)
+        _check(load().svdup_update_batched(self._h, len(items), arr, float(eps), int(mode), int(lanes)),
+               "svdup_update_batched")
+
+    def update_workspace(self, m: int, n: int, eps: float = 1e-12, mode: int = FP64) -> int:
+        """Workspace bytes svdup_update needs for an m x n problem."""
+        v = ctypes.c_size_t()
+        _check(load().svdup_update_workspace(self._h, int(m), int(n), float(eps), int(mode),
+                                             ctypes.byref(v)), "svdup_update_workspace")
+        return v.value
+
+    def autotune(self, mode: int = FP64, nmax: int = 4096):
+        """Measure the product-path choices for `mode`; returns (dense_max, leaf128_min)."""
+        _check(load().svdup_autotune(self._h, int(mode), int(nmax)), "svdup_autotune")
+        return self.tuning(mode)
+
+    def tuning(self, mode: int = FP64):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().svdup_tuning_get(self._h, int(mode), ctypes.byref(a), ctypes.byref(b)),
+               "svdup_tuning_get")
+        return a.value, b.value
+
+    def set_tuning(self, mode: int, dense_max: int, leaf128_min: int):
+        _check(load().svdup_tuning_set(self._h, int(mode), int(dense_max), int(leaf128_min)),
+               "svdup_tuning_set")
+
     def rank_one_eig(self, d, z, rho: float):
         """Compact eigen-system of diag(d) + rho z z^T (device tensors).  Returns a dict
         with k, idx, dk, org, tau, zhat, inv_norm (first k valid) and lam (all N)."""
@@ -212,6 +287,98 @@ class Handle:
                                            int(mode)), "svdup_cauchy_product")
         _check(self.sync(), "svdup_cauchy_product (device)")
         return lam, Y
+
+
+class Batch:
+    """A planned batch (svdup_batch_t): launch() queues one graph launch on the
+    handle's stream; the problems' tensors must stay alive while it exists."""
+
+    def __init__(self, handle, ptr, items):
+        self.handle = handle
+        self._b = ptr
+        self._items = items
+
+    def launch(self, check: bool = True):
+        _check(load().svdup_batch_launch(self._b), "svdup_batch_launch")
+        if check:
+            _check(self.handle.sync(), "svdup_batch_launch (device)")
+
+    def kernels(self) -> int:
+        return int(load().svdup_batch_kernels(self._b))
+
+    def close(self):
+        if self._b:
+            load().svdup_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving engine (svdup_server_*): register resident SVDs (device tensors as
+    in Handle.update, kept alive by this object), submit updates with host vectors,
+    wait for tickets, read latency statistics."""
+
+    def __init__(self, device: int = 0, lanes: int = 8, hbm_budget: int = 0, eps: float = 1e-12,
+                 mode: int = FP64):
+        out = ctypes.c_void_p()
+        _check(load().svdup_server_create(int(device), int(lanes), int(hbm_budget), float(eps),
+                                          int(mode), ctypes.byref(out)), "svdup_server_create")
+        self._s = out
+        self._mats = []
+
+    def register(self, U, S, V) -> int:
+        m, n = S.numel(), V.shape[0]
+        for t, nm in ((U, "U"), (S, "S"), (V, "V")):
+            _dev_f64(t, nm)
+        mid = ctypes.c_int()
+        _check(load().svdup_server_register(self._s, m, n, _ptr(U), _colmajor_ld(U, m, m, "U"),
+                                            _ptr(S), _ptr(V), _colmajor_ld(V, n, n, "V"),
+                                            ctypes.byref(mid)), "svdup_server_register")
+        self._mats.append((U, S, V))
+        return mid.value
+
+    def submit(self, mid: int, a, b) -> int:
+        import numpy as np
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        t = ctypes.c_longlong()
+        _check(load().svdup_server_submit(self._s, int(mid), ctypes.c_void_p(a.ctypes.data),
+                                          ctypes.c_void_p(b.ctypes.data), ctypes.byref(t)),
+               "svdup_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        """(status, latency_ms) of a request."""
+        lat = ctypes.c_double()
+        st = load().svdup_server_wait(self._s, int(ticket), float(timeout_ms), ctypes.byref(lat))
+        return int(st), lat.value
+
+    def drain(self):
+        _check(load().svdup_server_drain(self._s), "svdup_server_drain")
+
+    def stats(self):
+        c, p50, p99 = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        mif, mws = ctypes.c_int(), ctypes.c_size_t()
+        _check(load().svdup_server_stats(self._s, ctypes.byref(c), ctypes.byref(p50), ctypes.byref(p99),
+                                         ctypes.byref(mif), ctypes.byref(mws)), "svdup_server_stats")
+        return {"completed": c.value, "p50_ms": p50.value, "p99_ms": p99.value,
+                "max_in_flight": mif.value, "max_ws_bytes": mws.value}
+
+    def close(self):
+        if self._s:
+            load().svdup_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 SECULAR_STATIC_MAX_K = 16384

@@ -63,6 +63,9 @@ struct svdup_ctx {
   cudaEvent_t open_ev;
   double* flops_dev;  // 6 accumulators, device: useful flops of P2M, M2L, OUT, then the
                       // executed tensor-core flops of the same stages (mixed modes)
+  // product-path choices (set by svdup_autotune; defaults below): index 0 FP64, 1 mixed
+  int dense_max[2];   // N <= dense_max: dense Cauchy product (no far field)
+  int leaf128_min[2]; // N >= leaf128_min: leaves of 128 poles, else 64
 };
 
 namespace {
@@ -131,25 +134,30 @@ int expansion_order(double eps) {
   return p;
 }
 
-int leaf_size(int N) {
-  if (N <= 2048) return 64;
-  return 128;
+// Defaults of the product-path choices (svdup_autotune measures and replaces them).
+constexpr int kDefaultDenseMax = 512;
+constexpr int kDefaultLeaf128Min = 2049;
+
+int mode_index(int mode) { return (mode & SVDUP_MODE_MASK) == SVDUP_FP64 ? 0 : 1; }
+
+int leaf_size(const svdup_ctx* h, int N, int mode) {
+  return N >= h->leaf128_min[mode_index(mode)] ? 128 : 64;
 }
 
-bool use_dense(int N, int mode) {
+bool use_dense(const svdup_ctx* h, int N, int mode) {
   if (mode & SVDUP_DENSE) return true;
-  return N <= 512;
+  return N <= h->dense_max[mode_index(mode)];
 }
 
 // mixed: P = 16 nodes (the split products' K granularity; 5^-16 is far below the FP32
 // accumulation error) and no FP64 expansions (the split tiles of the MixPlan hold them).
-FmmPlan make_plan(Arena& ar, int N, int rows, double eps, bool mixed = false) {
+FmmPlan make_plan(Arena& ar, int N, int rows, double eps, int leaf, bool mixed) {
   FmmPlan f;
   memset(&f, 0, sizeof(f));
   f.p = mixed ? kMixP : expansion_order(eps);
   const size_t rrows = (size_t)(rows > 0 ? rows : 1);
   if (mixed) rows = 1;
-  f.s = leaf_size(N);
+  f.s = leaf;
   f.Lmax = (N + f.s - 1) / f.s;
   if (f.Lmax < 1) f.Lmax = 1;
   size_t L = (size_t)f.Lmax;
@@ -245,7 +253,7 @@ struct UpdateWs {
   MixPlan M;
 };
 
-UpdateWs layout_update(Arena& ar, int m, int n, double eps, bool mixed) {
+UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed) {
   UpdateWs u;
   u.p = ar.take<double>(m);
   u.q = ar.take<double>(n);
@@ -269,7 +277,7 @@ UpdateWs layout_update(Arena& ar, int m, int n, double eps, bool mixed) {
   u.E4 = make_eig(ar, n);
   u.Xs = mixed ? nullptr : ar.take<double>((size_t)n * n);
   u.W = ar.take<double>((size_t)n * n);
-  u.F = make_plan(ar, n, n, eps, mixed);
+  u.F = make_plan(ar, n, n, eps, leaf, mixed);
   if (mixed) u.M = make_mix(ar, n, u.F);
   else memset(&u.M, 0, sizeof(u.M));
   return u;
@@ -326,7 +334,7 @@ void queue_solve(svdup_ctx* h, Eig e) {
 // deflation rotations).  Xs is a rows x N scratch.
 void queue_product(svdup_ctx* h, Eig e, FmmPlan f, int rows, double* X, long long ldx,
                    double* Xs, OutMap om, int mode) {
-  int dense = use_dense(e.N, mode) ? 1 : 0;
+  int dense = use_dense(h, e.N, mode) ? 1 : 0;
   stage_begin(h, SVDUP_STAGE_GATHER);
   launch_rotate_columns(h->stream, e, X, ldx, rows, f.rotw);
   launch_gather_columns(h->stream, e, X, ldx, rows, Xs, rows, om);
@@ -351,7 +359,7 @@ void queue_product(svdup_ctx* h, Eig e, FmmPlan f, int rows, double* X, long lon
 // The same product in split BF16 on the tensor cores (svdup_mixed.cu).
 void queue_product_mixed(svdup_ctx* h, Eig e, FmmPlan f, MixPlan mp, int rows, double* X,
                          long long ldx, OutMap om, int mode) {
-  int dense = use_dense(e.N, mode) ? 1 : 0;
+  int dense = use_dense(h, e.N, mode) ? 1 : 0;
   mp.rows = rows;
   mp.rt = (rows + 127) / 128;
   stage_begin(h, SVDUP_STAGE_GATHER);
@@ -379,6 +387,188 @@ void queue_product_mixed(svdup_ctx* h, Eig e, FmmPlan f, MixPlan mp, int rows, d
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batches: lane contexts share the parent's status word and counters but own a
+// stream and a workspace.
+// ---------------------------------------------------------------------------
+svdup_ctx* lane_create(const svdup_ctx* parent) {
+  svdup_ctx* l = (svdup_ctx*)calloc(1, sizeof(svdup_ctx));
+  if (!l) return nullptr;
+  l->device = parent->device;
+  if (cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    free(l);
+    return nullptr;
+  }
+  l->status = parent->status;
+  l->flops_dev = parent->flops_dev;
+  l->maxit = parent->maxit;
+  l->open_stage = -1;
+  for (int i = 0; i < 2; i++) {
+    l->dense_max[i] = parent->dense_max[i];
+    l->leaf128_min[i] = parent->leaf128_min[i];
+  }
+  return l;
+}
+
+void lane_destroy(svdup_ctx* l) {
+  if (!l) return;
+  cudaStreamSynchronize(l->stream);
+  if (l->ws) cudaFree(l->ws);
+  cudaStreamDestroy(l->stream);
+  free(l->recs);
+  free(l->pool);
+  free(l);
+}
+
+size_t update_ws_bytes(const svdup_ctx* h, int m, int n, double eps, int mode) {
+  Arena meas = {nullptr, 0};
+  layout_update(meas, m, n, eps, leaf_size(h, n, mode), is_mixed(mode));
+  return meas.off;
+}
+
+bool problem_ok(const svdup_problem& p) {
+  return p.U && p.S && p.V && p.a && p.b && p.m >= 1 && p.n >= p.m && p.ldu >= p.m &&
+         p.ldv >= p.n;
+}
+
+}  // namespace
+
+struct svdup_batch {
+  svdup_ctx* parent;
+  int count, lanes;
+  svdup_problem* probs;
+  int* lane_of;  // problem -> lane, problems queued in index order within a lane
+  svdup_ctx** lane;
+  cudaStream_t origin;
+  cudaEvent_t fork;
+  cudaEvent_t* join;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  double eps;
+  int mode;
+  long long kernels;  // launches recorded into the graph
+};
+
+namespace {
+
+void batch_free(svdup_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->lane)
+    for (int l = 0; l < b->lanes; l++) lane_destroy(b->lane[l]);
+  if (b->join)
+    for (int l = 0; l < b->lanes; l++)
+      if (b->join[l]) cudaEventDestroy(b->join[l]);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  free(b->lane);
+  free(b->join);
+  free(b->probs);
+  free(b->lane_of);
+  free(b);
+}
+
+// Largest first to the least-loaded lane; cost ~ n^2 (m + n) (solves and products).
+void assign_lanes(svdup_batch* b) {
+  int* order = (int*)malloc(sizeof(int) * b->count);
+  double* cost = (double*)malloc(sizeof(double) * b->count);
+  double* load = (double*)calloc(b->lanes, sizeof(double));
+  for (int i = 0; i < b->count; i++) {
+    order[i] = i;
+    const double m = b->probs[i].m, n = b->probs[i].n;
+    cost[i] = n * n * (m + n);
+  }
+  // insertion sort by cost, descending (counts are modest)
+  for (int i = 1; i < b->count; i++) {
+    int v = order[i], j = i - 1;
+    while (j >= 0 && cost[order[j]] < cost[v]) { order[j + 1] = order[j]; j--; }
+    order[j + 1] = v;
+  }
+  for (int q = 0; q < b->count; q++) {
+    int best = 0;
+    for (int l = 1; l < b->lanes; l++)
+      if (load[l] < load[best]) best = l;
+    b->lane_of[order[q]] = best;
+    load[best] += cost[order[q]];
+  }
+  free(order);
+  free(cost);
+  free(load);
+}
+
+// Queue every problem on its lane, between a fork on `origin` and a join back to it.
+int batch_queue(svdup_batch* b) {
+  if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) return SVDUP_ECUDA;
+  for (int l = 0; l < b->lanes; l++)
+    if (cudaStreamWaitEvent(b->lane[l]->stream, b->fork, 0) != cudaSuccess) return SVDUP_ECUDA;
+  for (int i = 0; i < b->count; i++) {
+    const svdup_problem& p = b->probs[i];
+    int rc = svdup_update(b->lane[b->lane_of[i]], p.m, p.n, p.U, p.ldu, p.S, p.V, p.ldv, p.a, p.b,
+                          b->eps, b->mode);
+    if (rc) return rc;
+  }
+  for (int l = 0; l < b->lanes; l++) {
+    if (cudaEventRecord(b->join[l], b->lane[l]->stream) != cudaSuccess) return SVDUP_ECUDA;
+    if (cudaStreamWaitEvent(b->origin, b->join[l], 0) != cudaSuccess) return SVDUP_ECUDA;
+  }
+  return SVDUP_OK;
+}
+
+int batch_plan(svdup_t h, int count, const svdup_problem* probs, double eps, int mode, int lanes,
+               svdup_batch** out) {
+  *out = nullptr;
+  if (!h || count < 1 || !probs || !(eps > 0.0 && eps < 1.0) || !mode_ok(mode)) return SVDUP_EINVAL;
+  if (lanes == 0) lanes = 16;
+  if (lanes < 1 || lanes > 64) return SVDUP_EINVAL;
+  if (lanes > count) lanes = count;
+  for (int i = 0; i < count; i++)
+    if (!problem_ok(probs[i])) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  svdup_batch* b = (svdup_batch*)calloc(1, sizeof(svdup_batch));
+  if (!b) return SVDUP_ENOMEM;
+  b->parent = h;
+  b->count = count;
+  b->lanes = lanes;
+  b->eps = eps;
+  b->mode = mode;
+  b->probs = (svdup_problem*)malloc(sizeof(svdup_problem) * count);
+  b->lane_of = (int*)malloc(sizeof(int) * count);
+  b->lane = (svdup_ctx**)calloc(lanes, sizeof(svdup_ctx*));
+  b->join = (cudaEvent_t*)calloc(lanes, sizeof(cudaEvent_t));
+  if (!b->probs || !b->lane_of || !b->lane || !b->join) { batch_free(b); return SVDUP_ENOMEM; }
+  memcpy(b->probs, probs, sizeof(svdup_problem) * count);
+  assign_lanes(b);
+  if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    return SVDUP_ECUDA;
+  }
+  for (int l = 0; l < lanes; l++) {
+    b->lane[l] = lane_create(h);
+    if (!b->lane[l] || cudaEventCreateWithFlags(&b->join[l], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      batch_free(b);
+      return SVDUP_ECUDA;
+    }
+  }
+  // workspaces sized for each lane's largest problem now (nothing allocates later)
+  for (int l = 0; l < lanes; l++) {
+    size_t need = 0;
+    for (int i = 0; i < count; i++)
+      if (b->lane_of[i] == l) {
+        size_t w = update_ws_bytes(h, probs[i].m, probs[i].n, eps, mode);
+        if (w > need) need = w;
+      }
+    int rc = ensure_ws(b->lane[l], need);
+    if (rc) { batch_free(b); return rc; }
+  }
+  *out = b;
+  return SVDUP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -394,6 +584,10 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
   h->stream = (cudaStream_t)stream;
   h->maxit = 64;
   h->open_stage = -1;
+  for (int i = 0; i < 2; i++) {
+    h->dense_max[i] = kDefaultDenseMax;
+    h->leaf128_min[i] = kDefaultLeaf128Min;
+  }
   const char* mi = getenv("SVDUP_SECULAR_MAXIT");
   if (mi) h->maxit = atoi(mi);
   if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess) {
@@ -528,11 +722,12 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   const bool mixed = is_mixed(mode);
   if (set_device(h)) return SVDUP_ECUDA;
   Arena meas = {nullptr, 0};
-  layout_update(meas, m, n, eps, mixed);
+  const int leaf = leaf_size(h, n, mode);
+  layout_update(meas, m, n, eps, leaf, mixed);
   int rc = ensure_ws(h, meas.off);
   if (rc) return rc;
   Arena ar = {h->ws, 0};
-  UpdateWs u = layout_update(ar, m, n, eps, mixed);
+  UpdateWs u = layout_update(ar, m, n, eps, leaf, mixed);
   cudaStream_t st = h->stream;
 
   // STEP 1 (rewritten): p = U^T a, q = V^T b, alpha, beta
@@ -705,7 +900,7 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
     *rhod = ar.take<double>(1);
     *Xw = ar.take<double>((size_t)rows * N);
     *Xs = mixed ? nullptr : ar.take<double>((size_t)rows * N);
-    *f = make_plan(ar, N, rows, eps, mixed);
+    *f = make_plan(ar, N, rows, eps, leaf_size(h, N, mode), mixed);
     if (mixed) *mp = make_mix(ar, rows, *f);
   };
   Eig e;
@@ -734,6 +929,185 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
   else queue_product(h, e, f, rows, Xw, rows, Xs, om, mode);
   cudaMemcpyAsync(lam, e.lam, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
   return check_launch();
+}
+
+int svdup_batch_create(svdup_t h, int count, const svdup_problem* probs, double eps, int mode,
+                       int lanes, svdup_batch_t* out) {
+  if (!out) return SVDUP_EINVAL;
+  svdup_batch* b = nullptr;
+  int rc = batch_plan(h, count, probs, eps, mode, lanes, &b);
+  if (rc) return rc;
+  // Record the batch into a graph: capture on the batch's own origin stream (the
+  // handle's stream may be the legacy default stream, which cannot be captured).
+  const long long k0 = g_launch_count;
+  if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    return SVDUP_ECUDA;
+  }
+  rc = batch_queue(b);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(b->origin, &g);
+  b->graph = g;
+  if (rc == SVDUP_OK && ce != cudaSuccess) rc = SVDUP_ECUDA;
+  if (rc == SVDUP_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = SVDUP_ECUDA;
+  g_launch_count = k0;  // recorded, not launched
+  b->kernels = 0;
+  if (rc == SVDUP_OK) {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(b->graph, nullptr, &nn) == cudaSuccess) {
+      cudaGraphNode_t* nodes = (cudaGraphNode_t*)malloc(sizeof(cudaGraphNode_t) * (nn ? nn : 1));
+      if (nodes && cudaGraphGetNodes(b->graph, nodes, &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; i++) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+            b->kernels++;
+        }
+      free(nodes);
+    }
+  }
+  if (rc) {
+    cudaGetLastError();
+    batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return SVDUP_OK;
+}
+
+int svdup_batch_launch(svdup_batch_t b) {
+  if (!b || !b->exec) return SVDUP_EINVAL;
+  if (set_device(b->parent)) return SVDUP_ECUDA;
+  if (cudaGraphLaunch(b->exec, b->parent->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SVDUP_ECUDA;
+  }
+  g_launch_count += b->kernels;
+  return SVDUP_OK;
+}
+
+long long svdup_batch_kernels(svdup_batch_t b) { return b ? b->kernels : -1; }
+
+int svdup_batch_destroy(svdup_batch_t b) {
+  if (!b) return SVDUP_EINVAL;
+  cudaSetDevice(b->parent->device);
+  cudaStreamSynchronize(b->parent->stream);
+  batch_free(b);
+  return SVDUP_OK;
+}
+
+int svdup_update_batched(svdup_t h, int count, const svdup_problem* probs, double eps, int mode,
+                         int lanes) {
+  svdup_batch* b = nullptr;
+  int rc = batch_plan(h, count, probs, eps, mode, lanes, &b);
+  if (rc) return rc;
+  // the handle's stream -> origin -> lanes -> origin -> the handle's stream
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(e0, h->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(b->origin, e0, 0) != cudaSuccess) {
+    rc = SVDUP_ECUDA;
+  }
+  if (!rc) rc = batch_queue(b);
+  if (!rc && (cudaEventRecord(e1, b->origin) != cudaSuccess ||
+              cudaStreamWaitEvent(h->stream, e1, 0) != cudaSuccess))
+    rc = SVDUP_ECUDA;
+  int st = svdup_sync(h);
+  if (!rc) rc = st;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  batch_free(b);
+  cudaGetLastError();
+  return rc;
+}
+
+int svdup_tuning_get(svdup_t h, int mode, int* dense_max, int* leaf128_min) {
+  if (!h || !mode_ok(mode & SVDUP_MODE_MASK)) return SVDUP_EINVAL;
+  const int i = mode_index(mode);
+  if (dense_max) *dense_max = h->dense_max[i];
+  if (leaf128_min) *leaf128_min = h->leaf128_min[i];
+  return SVDUP_OK;
+}
+
+int svdup_tuning_set(svdup_t h, int mode, int dense_max, int leaf128_min) {
+  if (!h || !mode_ok(mode & SVDUP_MODE_MASK) || dense_max < 0 || leaf128_min < 1) return SVDUP_EINVAL;
+  const int i = mode_index(mode);
+  h->dense_max[i] = dense_max;
+  h->leaf128_min[i] = leaf128_min;
+  return SVDUP_OK;
+}
+
+int svdup_autotune(svdup_t h, int mode, int nmax) {
+  if (!h || !mode_ok(mode & SVDUP_MODE_MASK) || nmax < 256) return SVDUP_EINVAL;
+  mode &= SVDUP_MODE_MASK;
+  if (set_device(h)) return SVDUP_ECUDA;
+  const int i = mode_index(mode);
+  const int keep_dense = h->dense_max[i], keep_leaf = h->leaf128_min[i];
+  int nlim = 256;
+  while (nlim * 2 <= nmax) nlim *= 2;
+  const size_t maxN = (size_t)nlim;
+  double *X = nullptr, *Y = nullptr, *d = nullptr, *z = nullptr, *lam = nullptr;
+  int rc = SVDUP_OK;
+  if (cudaMalloc(&X, maxN * maxN * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&Y, maxN * maxN * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&d, maxN * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&z, maxN * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&lam, maxN * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    rc = SVDUP_ENOMEM;
+  }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (!rc && (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess))
+    rc = SVDUP_ECUDA;
+  int dense_max = 0, leaf128_min = 1 << 30;
+  bool dense_lost = false;
+  for (int N = 256; !rc && N <= nlim; N *= 2) {
+    launch_fill_random(h->stream, N, N, X, d, z, 0x5eedULL + (unsigned long long)N);
+    // candidates: 0 dense, 1 far field with 64-pole leaves, 2 with 128-pole leaves
+    float best = 1e30f;
+    int best_c = 0;
+    float tc[3] = {0, 0, 0};
+    for (int c = 0; c < 3 && !rc; c++) {
+      h->dense_max[i] = (c == 0) ? N : 0;
+      h->leaf128_min[i] = (c == 2) ? 1 : (1 << 30);
+      const int m = mode | (c == 0 ? SVDUP_DENSE : 0);
+      float best_t = 1e30f;
+      for (int rep = 0; rep < 3 && !rc; rep++) {  // first run warms the workspace
+        cudaEventRecord(t0, h->stream);
+        rc = svdup_cauchy_product(h, N, N, X, N, d, z, 1.0, Y, N, lam, 1e-12, m);
+        cudaEventRecord(t1, h->stream);
+        if (!rc) rc = svdup_sync(h);
+        float ms = 0.f;
+        if (!rc && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && rep > 0 && ms < best_t)
+          best_t = ms;
+      }
+      tc[c] = best_t;
+      if (best_t < best) { best = best_t; best_c = c; }
+    }
+    if (rc) break;
+    if (best_c == 0 && !dense_lost) dense_max = N;
+    else dense_lost = true;
+    if (tc[2] < tc[1] && N < leaf128_min) leaf128_min = N;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(X); cudaFree(Y); cudaFree(d); cudaFree(z); cudaFree(lam);
+  if (rc) {
+    h->dense_max[i] = keep_dense;
+    h->leaf128_min[i] = keep_leaf;
+    return rc;
+  }
+  h->dense_max[i] = dense_max;
+  h->leaf128_min[i] = leaf128_min;
+  return SVDUP_OK;
+}
+
+int svdup_update_workspace(svdup_t h, int m, int n, double eps, int mode, size_t* bytes) {
+  if (!h || !bytes || m < 1 || n < m || !(eps > 0.0 && eps < 1.0) || !mode_ok(mode))
+    return SVDUP_EINVAL;
+  *bytes = update_ws_bytes(h, m, n, eps, mode);
+  return SVDUP_OK;
 }
 
 }  // extern "C"

@@ -191,6 +191,9 @@ void launch_sign_combine(cudaStream_t st, int m, int n, const double* S, const d
 void launch_sign_finish(cudaStream_t st, int m, int n, const double* h, double* sign);
 void launch_fill_ones(cudaStream_t st, int n, double* w);
 void launch_sqrt_desc(cudaStream_t st, int m, const double* lam, double* S, int* status);
+// synthetic inputs for the autotuner
+void launch_fill_random(cudaStream_t st, int rows, int N, double* X, double* d, double* z,
+                        unsigned long long seed);
 
 // rotw: scratch of rows x ceil(N / 64) x 3 doubles
 void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,

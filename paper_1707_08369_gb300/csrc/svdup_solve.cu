@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
   }
   __syncthreads();
   const double tol = s_tol, zn = s_zn, dsc = s_dsc, zsc = s_zsc;
+  const double idsc = 1.0 / dsc, izsc = 1.0 / zsc;  // exact: powers of two
   const double tolS = tol * dsc, tol2 = tolS * tolS;
   const int nwords = (N + 31) >> 5;
   unsigned* cmask = (unsigned*)dsm;   // pair (i-1, i) passes with the original values
@@ -470,11 +471,11 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
         // rotation merging survivor i-1 (the carrier) into i
         const double zprev = brk[i - 1] ? kz[i - 1] : sqrt(W);  // signed at a run start
         const double Wn = W + z2;
-        const double rn = sqrt(Wn);
-        const double cs = zi / rn, sn = zprev / rn;
+        const double irn = 1.0 / sqrt(Wn);
+        const double cs = zi * irn, sn = zprev * irn;
         const double dprev = M / W;
         const int pj = kpos[i - 1], pi = kpos[i];
-        e.ds[pj] = (cs * cs * dprev + sn * sn * di) / dsc;
+        e.ds[pj] = (cs * cs * dprev + sn * sn * di) * idsc;
         e.zs[pj] = 0.0;
         e.defl[pj] = 1;
         e.rj[ridx] = pj; e.ri[ridx] = pi; e.rc[ridx] = cs; e.rs[ridx] = sn;
@@ -484,8 +485,8 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
       }
       if (!(i + 1 < nk && !brk[i + 1])) {  // not merged away by the next pair
         const int ps = kpos[i];
-        if (p) { e.ds[ps] = (M / W) / dsc; e.zs[ps] = sqrt(W) / zsc; }
-        else { e.ds[ps] = di / dsc; e.zs[ps] = zi / zsc; }
+        if (p) { e.ds[ps] = (M / W) * idsc; e.zs[ps] = sqrt(W) * izsc; }
+        else { e.ds[ps] = di * idsc; e.zs[ps] = zi * izsc; }
       }
     }
     if (tid == 0) e.nrot[0] = nrot;
@@ -1011,27 +1012,36 @@ void launch_secular_direct(cudaStream_t st, Eig e, int k, const double* d, const
 // ---------------------------------------------------------------------------
 constexpr int kMergeChunk = 2048;
 
-__global__ void __launch_bounds__(128) k_merge_count(Eig e) {
-  __shared__ double sv[kMergeChunk];
+// IEEE doubles ordered as signed 64-bit integers (ties and signs preserved), so the
+// comparisons run on the integer pipes rather than the FP64 unit.
+__device__ __forceinline__ long long ordered_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+__global__ void __launch_bounds__(64) k_merge_count(Eig e) {
+  __shared__ long long sv[kMergeChunk];
   const int N = e.N, k = e.kp[0], nd = N - k;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool root = x < k;
-  double key = 0.0;
-  if (x < N) key = root ? e.dorg[x] + e.tau[x] : e.ds[e.didx[x - k]];
+  double val = 0.0;
+  if (x < N) val = root ? e.dorg[x] + e.tau[x] : e.ds[e.didx[x - k]];
+  const long long key = ordered_key(val);
   const int me = x - k;
   int cnt = 0;
   for (int c0 = 0; c0 < nd; c0 += kMergeChunk) {
     const int cn = min(kMergeChunk, nd - c0);
     __syncthreads();
-    for (int t = threadIdx.x; t < cn; t += blockDim.x) sv[t] = e.ds[e.didx[c0 + t]];
+    for (int t = threadIdx.x; t < cn; t += blockDim.x) sv[t] = ordered_key(e.ds[e.didx[c0 + t]]);
     __syncthreads();
     if (x < N) {
       if (root) {
         for (int t = 0; t < cn; t++) cnt += (sv[t] <= key);
       } else {
+        const int lim = me - c0;  // equal values rank by position in didx
         for (int t = 0; t < cn; t++) {
-          const double w = sv[t];
-          cnt += (w < key) || (w == key && c0 + t < me);
+          const long long w = sv[t];
+          cnt += (w < key) || (w == key && t < lim);
         }
       }
     }
@@ -1039,22 +1049,22 @@ __global__ void __launch_bounds__(128) k_merge_count(Eig e) {
   if (x >= N) return;
   if (root) {
     const int r = x + cnt;
-    e.lam[r] = key;
+    e.lam[r] = val;
     e.rank_root[x] = r;
   } else {
-    int lo = 0, hi = k;  // roots strictly below the value
+    int lo = 0, hi = k;  // roots strictly below the value, in the same integer order
     while (lo < hi) {
       int mid = (lo + hi) >> 1;
-      if (e.dorg[mid] + e.tau[mid] < key) lo = mid + 1; else hi = mid;
+      if (ordered_key(e.dorg[mid] + e.tau[mid]) < key) lo = mid + 1; else hi = mid;
     }
     const int r = cnt + lo;
-    e.lam[r] = key;
+    e.lam[r] = val;
     e.rank_defl[e.didx[me]] = r;
   }
 }
 
 void launch_merge(cudaStream_t st, Eig e) {
-  k_merge_count<<<(e.N + 127) / 128, 128, 0, st>>>(e);
+  k_merge_count<<<(e.N + 63) / 64, 64, 0, st>>>(e);
   SVDUP_COUNT_LAUNCH();
 }
 
@@ -1386,6 +1396,40 @@ __global__ void k_sqrt_desc(int m, const double* __restrict__ lam, double* S, in
 
 void launch_sqrt_desc(cudaStream_t st, int m, const double* lam, double* S, int* status) {
   k_sqrt_desc<<<(m + 255) / 256, 256, 0, st>>>(m, lam, S, status);
+  SVDUP_COUNT_LAUNCH();
+}
+
+
+// ---------------------------------------------------------------------------
+// Synthetic inputs for the autotuner (not part of the method): X (rows x N, entries
+// uniform in [-1, 1) / sqrt(N)), poles d uniform in [0, 1), z uniform in [-1, 1), from
+// the SplitMix64 generator (Steele, Lea and Flood 2014) applied to a counter.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double splitmix_unit(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (1.0 / 9007199254740992.0);  // [0, 1) with 53 bits
+}
+
+__global__ void k_fill_random(int rows, int N, double* X, double* d, double* z,
+                              unsigned long long seed) {
+  const long long total = (long long)rows * N;
+  const double sc = 1.0 / sqrt((double)N);
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    X[x] = (2.0 * splitmix_unit(seed * 0x100000001B3ULL + (unsigned long long)x) - 1.0) * sc;
+    if (x < N) {
+      d[x] = splitmix_unit((seed ^ 0xD1B54A32D192ED03ULL) + (unsigned long long)x);
+      z[x] = 2.0 * splitmix_unit((seed ^ 0x8CB92BA72F3D8DD7ULL) + (unsigned long long)x) - 1.0;
+    }
+  }
+}
+
+void launch_fill_random(cudaStream_t st, int rows, int N, double* X, double* d, double* z,
+                        unsigned long long seed) {
+  k_fill_random<<<1024, 256, 0, st>>>(rows, N, X, d, z, seed);
   SVDUP_COUNT_LAUNCH();
 }
 
