@@ -120,6 +120,11 @@ Eig make_eig(Arena& ar, int N) {
   e.sqb = ar.take<double>(2 * nbox);
   e.sqn = ar.take<int>(2 * nbox);
   e.sqv = ar.take<double>(4 * 26 * nbox);
+  e.fsc = ar.take<int>(4);
+  e.tf = ar.take<float2>(n);
+  e.zf = ar.take<float2>(n);
+  e.yf = ar.take<float2>(n);
+  e.wf = ar.take<float2>(n);
   return e;
 }
 
@@ -176,7 +181,7 @@ FmmPlan make_plan(Arena& ar, int N, int rows, double eps, int leaf, bool mixed) 
   f.ldphi = rows > 0 ? rows : 1;
   f.Phi = ar.take<double>((size_t)f.ldphi * L * f.p);
   f.Psi = ar.take<double>((size_t)f.ldphi * (L + 1) * f.p);
-  f.rotw = ar.take<double>(rrows * (size_t)((N + 63) / 64) * 3);
+  f.rot = ar.take<unsigned char>(rotate_scratch_bytes(N, (int)rrows));
   return f;
 }
 
@@ -323,11 +328,14 @@ void stage_end(svdup_ctx* h) {
 
 // One solve: deflation, roots, final ordering, zhat; the column norms follow separately
 // (fused with a transposed product when the next solve needs its z).
-void queue_solve(svdup_ctx* h, Eig e) {
+// pairs: Loewner's zhat in double-float arithmetic (svdup_dfsum.cu), for solves whose
+// zhat feeds vectors only (never the z of another solve) in the mixed mode
+void queue_solve(svdup_ctx* h, Eig e, bool pairs = false) {
   launch_deflate(h->stream, e, h->status);
   launch_secular(h->stream, e, h->status, h->maxit);
   launch_merge(h->stream, e);
-  launch_loewner(h->stream, e);
+  if (pairs) launch_loewner_df(h->stream, e);
+  else launch_loewner(h->stream, e);
 }
 
 // Y[:, out(q)] = (X Q)[:, q] for the solve e (X rows x N, modified in place by the
@@ -336,7 +344,7 @@ void queue_product(svdup_ctx* h, Eig e, FmmPlan f, int rows, double* X, long lon
                    double* Xs, OutMap om, int mode) {
   int dense = use_dense(h, e.N, mode) ? 1 : 0;
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rotw);
+  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rot, false);
   launch_gather_columns(h->stream, e, X, ldx, rows, Xs, rows, om);
   stage_end(h);
   stage_begin(h, SVDUP_STAGE_SETUP);
@@ -363,7 +371,7 @@ void queue_product_mixed(svdup_ctx* h, Eig e, FmmPlan f, MixPlan mp, int rows, d
   mp.rows = rows;
   mp.rt = (rows + 127) / 128;
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rotw);
+  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rot, true);
   launch_mix_gather(h->stream, e, X, ldx, rows, mp, om);
   stage_end(h);
   stage_begin(h, SVDUP_STAGE_SETUP);
@@ -741,25 +749,26 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   launch_apply_qt(st, u.E1, u.z2p, u.ysort, u.zsec2);
   // STEP 5: second left solve
   launch_fill_second(st, u.E2, u.E1.lam, u.zsec2);
-  queue_solve(h, u.E2);
-  launch_norms(st, u.E2, nullptr, nullptr);
+  queue_solve(h, u.E2, mixed);
+  launch_norms(st, u.E2, nullptr, nullptr, mixed);
   // STEPs 3, 6: first right solve
   launch_fill_right(st, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
   queue_solve(h, u.E3);
   launch_apply_qt(st, u.E3, u.z4p, u.ysort, u.zsec4);
   // STEP 7: second right solve
   launch_fill_second(st, u.E4, u.E3.lam, u.zsec4);
-  queue_solve(h, u.E4);
-  launch_norms(st, u.E4, nullptr, nullptr);
+  queue_solve(h, u.E4, mixed);
+  launch_norms(st, u.E4, nullptr, nullptr, mixed);
   stage_end(h);
   // sign pairing of right vectors with left vectors (before S is overwritten)
   stage_begin(h, SVDUP_STAGE_SIGN);
   launch_fill_ones(st, m, u.ones);
-  launch_apply_q(st, u.E2, u.ones, u.work, u.g1);
-  launch_apply_q(st, u.E1, u.g1, u.work, u.g);
+  // in the mixed mode the sign sums run on FP32 pairs (only the signs are used)
+  launch_apply_q(st, u.E2, u.ones, u.work, u.g1, mixed);
+  launch_apply_q(st, u.E1, u.g1, u.work, u.g, mixed);
   launch_sign_combine(st, m, n, S, u.p, u.q, u.g, u.yv);
-  launch_apply_qt(st, u.E3, u.yv, u.ysort, u.h1);
-  launch_apply_qt(st, u.E4, u.h1, u.ysort, u.h);
+  launch_apply_qt(st, u.E3, u.yv, u.ysort, u.h1, mixed);
+  launch_apply_qt(st, u.E4, u.h1, u.ysort, u.h, mixed);
   launch_sign_finish(st, m, n, u.h, u.sign);
   stage_end(h);
   // products: U -> W -> U (descending), V -> W -> V (descending, signed)
@@ -922,8 +931,8 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
       cudaSuccess)
     return SVDUP_ECUDA;
   launch_fill_generic(st, e, d, z, rhod, h->status);
-  queue_solve(h, e);
-  launch_norms(st, e, nullptr, nullptr);
+  queue_solve(h, e, mixed);
+  launch_norms(st, e, nullptr, nullptr, mixed);
   OutMap om = {Y, (long long)ldy, N, 0, nullptr};
   if (mixed) queue_product_mixed(h, e, f, mp, rows, Xw, rows, om, mode);
   else queue_product(h, e, f, rows, Xw, rows, Xs, om, mode);

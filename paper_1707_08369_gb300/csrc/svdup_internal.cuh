@@ -99,6 +99,13 @@ struct Eig {
   double* sqb;
   int* sqn;
   double* sqv;
+  // double-float copies for the pair-arithmetic sums (svdup_dfsum.cu): scales fsc[4]
+  // (exponents), tau, zhat, y and root weights as (hi, lo) FP32 pairs
+  int* fsc;
+  float2* tf;
+  float2* zf;
+  float2* yf;
+  float2* wf;
 };
 
 // Column mapping of a product's output: physical column of final index q is
@@ -108,7 +115,7 @@ struct OutMap {
   long long ldy;
   int out_n;
   int out_rev;
-  const double* colscale;  // indexed by final index q, may be null
+  const double* colscale;  // +-1 signs indexed by final index q, may be null
 };
 
 // FMM (flat Chebyshev far field + direct near field) plan for one product.
@@ -134,7 +141,7 @@ struct FmmPlan {
   double* Phi;    // rows x (Lmax p) far-field expansions
   double* Psi;    // rows x ((Lmax+1) p) local expansions
   long long ldphi;
-  double* rotw;   // rows x ceil(N / 64) x 3 scratch of the column rotations
+  void* rot;      // scratch of the deflation rotations (rotate_scratch_bytes(N, rows))
 };
 
 // Mixed-precision (split BF16) form of the product on the tensor cores.  Every operand
@@ -183,9 +190,18 @@ void launch_secular_direct(cudaStream_t st, Eig e, int k, const double* d, const
                            int* status, int maxit);
 void launch_merge(cudaStream_t st, Eig e);
 void launch_loewner(cudaStream_t st, Eig e);
-void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final);
-void launch_apply_qt(cudaStream_t st, Eig e, const double* xphys, double* work, double* out_final);
-void launch_apply_q(cudaStream_t st, Eig e, const double* xfinal, double* work, double* yphys);
+void launch_loewner_df(cudaStream_t st, Eig e);
+// pairs = true: the sums in double-float arithmetic (svdup_dfsum.cu), for outputs that
+// need FP32 accuracy only (the mixed mode's vectors and signs)
+void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final,
+                  bool pairs = false);
+void launch_apply_qt(cudaStream_t st, Eig e, const double* xphys, double* work, double* out_final,
+                     bool pairs = false);
+void launch_apply_q(cudaStream_t st, Eig e, const double* xfinal, double* work, double* yphys,
+                    bool pairs = false);
+void launch_norms_df(cudaStream_t st, Eig e, const double* ysorted, double* out_final, int blocks);
+void launch_apply_q_core_df(cudaStream_t st, Eig e, const double* xfinal, double* vsorted,
+                            int blocks);
 void launch_sign_combine(cudaStream_t st, int m, int n, const double* S, const double* p,
                          const double* q, const double* g, double* y);
 void launch_sign_finish(cudaStream_t st, int m, int n, const double* h, double* sign);
@@ -195,9 +211,11 @@ void launch_sqrt_desc(cudaStream_t st, int m, const double* lam, double* S, int*
 void launch_fill_random(cudaStream_t st, int rows, int N, double* X, double* d, double* z,
                         unsigned long long seed);
 
-// rotw: scratch of rows x ceil(N / 64) x 3 doubles
+// scratch: rotate_scratch_bytes(N, rows) bytes, 16-byte aligned; mixed: FP32-accurate
+// arithmetic (see svdup_product.cu)
+size_t rotate_scratch_bytes(int N, int rows);
 void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
-                           double* rotw);
+                           void* scratch, bool mixed);
 void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
                            double* Xs, long long ldxs, OutMap om);
 void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense);

@@ -519,6 +519,21 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += err;
 }
 
+// Exact FP32 -> FP64 widening through the IEEE-754 bit fields: the exponent is re-biased
+// (1023 - 127 = 896) and the 23 fraction bits move up by 29.  FP32 subnormals (below
+// 1.2e-38) become signed zeros; Inf and NaN keep their class.  Integer work only, so the
+// conversion of an output tile stays off the FP64 pipe.
+__device__ __forceinline__ double widen_f32(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t mag = u & 0x7fffffffu;
+  unsigned long long d = (unsigned long long)(u & 0x80000000u) << 32;
+  if (mag >= 0x7f800000u)
+    d |= 0x7ff0000000000000ull | ((unsigned long long)(mag & 0x007fffffu) << 29);
+  else if (mag >= 0x00800000u)
+    d |= ((unsigned long long)mag << 29) + (896ull << 52);
+  return __longlong_as_double((long long)d);
+}
+
 // Three BF16 terms of the double-float value hi + lo (24 significant bits).
 __device__ __forceinline__ void split3ff(float hi, float lo, uint16_t& h, uint16_t& m,
                                          uint16_t& l) {
@@ -718,21 +733,26 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
       }
     }
     if (STAGE == MS_OUT) {
-      // Stage the FP64 tile column-major in the (now idle) ring, then write whole output
+      // The operands carry 24 significant bits, so the output is rounded to FP32 (hi + lo)
+      // and widened exactly; the column scale is a sign (+-1), applied as one.  The tile
+      // is staged column-major in the (now idle) ring, then written as whole output
       // columns: 128 consecutive rows per column, one warp per column.
-      double* stile = (double*)sm;  // [W][128]
+      float* stile = (float*)sm;  // [W][128]
 #pragma unroll
-      for (int c = 0; c < QW; c++) stile[(qc * QW + c) * kTM + r] = (double)hi[c] + (double)lo[c];
+      for (int c = 0; c < QW; c++) stile[(qc * QW + c) * kTM + r] = hi[c] + lo[c];
       asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
       if (ok && !*abort_flag) {
         const int j0 = f.tj0[J.job], nb = f.tj1[J.job] - j0;
         const long long row0 = (long long)J.rt * kTM;
         for (int cc = warp; cc < nb; cc += kEpiWarps) {
           const int q = e.rank_root[j0 + cc];
-          const double sc = om.colscale ? om.colscale[q] : 1.0;
+          const bool flip = om.colscale && om.colscale[q] < 0.0;
           double* ycol = om.Y + out_col_m(om, q) * om.ldy + row0;
           for (int rr = lane; rr < kTM; rr += 32)
-            if (row0 + rr < mp.rows) ycol[rr] = sc * stile[cc * kTM + rr];
+            if (row0 + rr < mp.rows) {
+              const float v = stile[cc * kTM + rr];
+              ycol[rr] = widen_f32(flip ? -v : v);
+            }
         }
       }
     }

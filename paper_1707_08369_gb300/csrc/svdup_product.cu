@@ -21,6 +21,7 @@
 // source leaves containing b-1..b+1 and every non-admissible leaf.
 #include <cuda_runtime.h>
 
+#include "svdup_df.cuh"
 #include "svdup_internal.cuh"
 
 namespace svdup {
@@ -30,117 +31,233 @@ extern long long g_launch_count;
 // ---------------------------------------------------------------------------
 // Deflation rotations applied to the columns of X (in place): X <- X G_1^T ... G_r^T,
 // i.e. each row of X transforms like z^T.  Rotation i acts on columns (a_i, b_i) with
-// (cos, sin) = (c_i, s_i); the deflation walk makes each rotation either open a chain
-// (a_i untouched so far) or continue the previous one (a_i = b_{i-1}, the chain's
-// carrier).  Per row, with x the ORIGINAL column values (no column is read after it is
-// written), the carrier follows the affine recurrence
+// (cos, sin) = (c_i, s_i); the deflation walk makes each rotation either open a run
+// (a_i untouched so far) or continue the previous one (a_i = b_{i-1}, the run's
+// carrier), and different runs touch disjoint columns.  Per row, with x the ORIGINAL
+// column values, the carrier follows the affine recurrence
 //     v_i = s_i u_i + c_i x_{b_i},   u_i = chained ? v_{i-1} : x_{a_i},
-// and the outputs are  X[a_i] = c_i u_i - s_i x_{b_i}  and, at a chain's end,
-// X[b_i] = v_i.  The rotation list is cut into chunks of kRotChunk: pass 1 composes
-// each chunk's map v_out = A v_in + B (per row), pass 2 carries v across the chunks,
-// pass 3 replays each chunk from its carry and writes.  The only column shared by two
-// chunks is the last b of a chunk that the next chunk overwrites as its first a; pass 1
-// saves its original value so pass 3 never reads it back.  Scratch: rows x chunks x 3.
+// and the outputs are  X[a_i] = c_i u_i - s_i x_{b_i}  and, at a run's end, X[b_i] = v_i.
+// One run can hold thousands of rotations (a graded spectrum merges most of its small
+// poles), so the list is cut into chunks of kRotChunk and scanned:
+//   prep     per chunk, the row-independent factor A = prod s_i of the map
+//            v_out = A v_in + B (A = 0 when a run starts inside the chunk);
+//   compose  per (row, chunk), the offset B, and the chunk's last original x_b;
+//   carry    per row, the carrier entering every chunk (B is overwritten with it);
+//   apply    per (row, chunk), the replay from that carrier, writing X.
+// The only column two chunks share is the last b of a chunk that the next chunk
+// overwrites as its first a; compose saves its original value, so apply never reads it
+// back.  Scratch is chunk-major ([chunk][row]), so the row threads of a block read and
+// write it coalesced.  FP64 form: 6 FP64 operations per row and rotation.  The mixed
+// form rounds every loaded value once to FP32 and carries unevaluated pairs of FP32
+// numbers (about 48 bits), so errors do not grow along long runs; its outputs are
+// FP32-accurate, as the split operands that follow.
 // ---------------------------------------------------------------------------
 constexpr int kRotChunk = 64;
+constexpr int kRotBatch = 8;
 
-__global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __restrict__ X,
-                                                     long long ldx, int rows, double* rotw) {
-  __shared__ long long sa[kRotChunk], sb[kRotChunk];
-  __shared__ double sc[kRotChunk], ss[kRotChunk];
-  __shared__ int sch[kRotChunk];
+struct RotScratch {  // carved from the plan's rotation scratch (see launch_rotate_columns)
+  double* A;         // [nch] chunk factors
+  float4* rotf;      // [N] (c_hi, c_lo, s_hi, s_lo)
+  double* Bw;        // [nch][rows] offsets, then carries (the mixed form stores a float2)
+  double* Xw;        // [nch][rows] the chunk's last original x_b
+};
+
+__global__ void __launch_bounds__(1024) k_rot_prep(Eig e, RotScratch w) {
   const int nr = e.nrot[0];
-  const int ch = blockIdx.y, c0 = ch * kRotChunk;
-  if (c0 >= nr) return;
+  const int nch = (nr + kRotChunk - 1) / kRotChunk;
+  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+    const int c0 = ch * kRotChunk, c1 = min(nr, c0 + kRotChunk);
+    double A = 1.0;
+    for (int g = c0; g < c1; g++) {
+      const bool chained = g > 0 && e.rj[g] == e.ri[g - 1];
+      A = chained ? A * e.rs[g] : 0.0;
+    }
+    w.A[ch] = A;
+  }
+  for (int g = threadIdx.x; g < nr; g += blockDim.x) {
+    const double c = e.rc[g], sn = e.rs[g];
+    const float ch = (float)c, sh = (float)sn;
+    w.rotf[g] = make_float4(ch, (float)(c - (double)ch), sh, (float)(sn - (double)sh));
+  }
+}
+
+// The chunk's rotations, staged once per block.
+struct RotChunkSm {
+  long long a[kRotChunk], b[kRotChunk];
+  float4 cs[kRotChunk];
+  double c[kRotChunk], s[kRotChunk];
+  unsigned char chained[kRotChunk], ends[kRotChunk];
+};
+
+__device__ __forceinline__ int stage_chunk(Eig e, long long ldx, const float4* rotf, int c0,
+                                           int nr, RotChunkSm& sm) {
   const int cn = min(kRotChunk, nr - c0);
   for (int i = threadIdx.x; i < cn; i += blockDim.x) {
     const int g = c0 + i;
-    sa[i] = (long long)e.perm[e.rj[g]] * ldx;
-    sb[i] = (long long)e.perm[e.ri[g]] * ldx;
-    sc[i] = e.rc[g];
-    ss[i] = e.rs[g];
-    sch[i] = (g > 0 && e.rj[g] == e.ri[g - 1]) ? 1 : 0;
+    sm.a[i] = (long long)e.perm[e.rj[g]] * ldx;
+    sm.b[i] = (long long)e.perm[e.ri[g]] * ldx;
+    sm.c[i] = e.rc[g];
+    sm.s[i] = e.rs[g];
+    sm.cs[i] = rotf[g];
+    sm.chained[i] = (g > 0 && e.rj[g] == e.ri[g - 1]) ? 1 : 0;
+    sm.ends[i] = (g + 1 >= nr || e.rj[g + 1] != e.ri[g]) ? 1 : 0;
   }
   __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  double A = 1.0, B = 0.0, xlast = 0.0;
-  for (int i = 0; i < cn; i++) {
-    const double xb = X[r + sb[i]];
-    if (sch[i]) {  // v = s (A v_in + B) + c xb
-      A = ss[i] * A;
-      B = fma(ss[i], B, sc[i] * xb);
-    } else {
-      const double xa = X[r + sa[i]];
-      A = 0.0;
-      B = fma(ss[i], xa, sc[i] * xb);
-    }
-    xlast = xb;
-  }
-  const size_t nch = gridDim.y;
-  double* w = rotw + ((size_t)r * nch + ch) * 3;
-  w[0] = A;
-  w[1] = B;
-  w[2] = xlast;
+  return cn;
 }
 
-__global__ void k_rot_carry(Eig e, int rows, int nch, double* rotw) {
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __restrict__ X,
+                                                     long long ldx, int rows, RotScratch w) {
+  __shared__ RotChunkSm sm;
+  const int nr = e.nrot[0];
+  const int ch = blockIdx.y, c0 = ch * kRotChunk;
+  if (c0 >= nr) return;
+  const int cn = stage_chunk(e, ldx, w.rotf, c0, nr, sm);
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  double B = 0.0, xlast = 0.0;
+  Df Bf = {0.f, 0.f};
+  for (int i0 = 0; i0 < cn; i0 += kRotBatch) {
+    double xb[kRotBatch], xa[kRotBatch];
+#pragma unroll
+    for (int u = 0; u < kRotBatch; u++) {  // a batch of independent loads in flight
+      const int i = i0 + u;
+      xb[u] = i < cn ? X[r + sm.b[i]] : 0.0;
+      xa[u] = (i < cn && !sm.chained[i]) ? X[r + sm.a[i]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kRotBatch; u++) {
+      const int i = i0 + u;
+      if (i < cn) {
+        if (!MIXED) {
+          B = fma(sm.s[i], sm.chained[i] ? B : xa[u], sm.c[i] * xb[u]);
+        } else {
+          const float4 q = sm.cs[i];
+          const Df uu = sm.chained[i] ? Bf : Df{(float)xa[u], 0.f};
+          Bf = df_add(df_mul(Df{q.z, q.w}, uu), df_mul(Df{q.x, q.y}, Df{(float)xb[u], 0.f}));
+        }
+        xlast = xb[u];
+      }
+    }
+  }
+  const size_t o = (size_t)ch * rows + r;
+  if (MIXED) {
+    float2 t = make_float2(Bf.hi, Bf.lo);
+    w.Bw[o] = *reinterpret_cast<double*>(&t);
+  } else {
+    w.Bw[o] = B;
+  }
+  w.Xw[o] = xlast;
+}
+
+template <bool MIXED>
+__global__ void k_rot_carry(Eig e, int rows, RotScratch w) {
   const int nr = e.nrot[0];
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows || nr == 0) return;
-  const int used = (nr + kRotChunk - 1) / kRotChunk;
+  const int nch = (nr + kRotChunk - 1) / kRotChunk;
   double v = 0.0;
-  for (int ch = 0; ch < used; ch++) {
-    double* w = rotw + ((size_t)r * nch + ch) * 3;
-    const double A = w[0], B = w[1];
-    w[0] = v;  // the carrier entering this chunk
-    v = fma(A, v, B);
+  Df vf = {0.f, 0.f};
+  for (int ch = 0; ch < nch; ch++) {
+    const size_t o = (size_t)ch * rows + r;
+    const double B = w.Bw[o], A = w.A[ch];
+    if (!MIXED) {
+      w.Bw[o] = v;  // the carrier entering this chunk
+      v = fma(A, v, B);
+    } else {
+      float2 t;
+      *reinterpret_cast<double*>(&t) = B;
+      float2 cur = make_float2(vf.hi, vf.lo);
+      w.Bw[o] = *reinterpret_cast<double*>(&cur);
+      vf = df_add(df_mul(df_from_f64(A, 0), vf), Df{t.x, t.y});
+    }
   }
 }
 
+template <bool MIXED>
 __global__ void __launch_bounds__(128) k_rot_apply(Eig e, double* X, long long ldx, int rows,
-                                                   const double* __restrict__ rotw) {
-  __shared__ long long sa[kRotChunk], sb[kRotChunk];
-  __shared__ double sc[kRotChunk], ss[kRotChunk];
-  __shared__ int sch[kRotChunk], send[kRotChunk];
+                                                   RotScratch w) {
+  __shared__ RotChunkSm sm;
   const int nr = e.nrot[0];
   const int ch = blockIdx.y, c0 = ch * kRotChunk;
   if (c0 >= nr) return;
-  const int cn = min(kRotChunk, nr - c0);
-  for (int i = threadIdx.x; i < cn; i += blockDim.x) {
-    const int g = c0 + i;
-    sa[i] = (long long)e.perm[e.rj[g]] * ldx;
-    sb[i] = (long long)e.perm[e.ri[g]] * ldx;
-    sc[i] = e.rc[g];
-    ss[i] = e.rs[g];
-    sch[i] = (g > 0 && e.rj[g] == e.ri[g - 1]) ? 1 : 0;
-    send[i] = (g + 1 >= nr || e.rj[g + 1] != e.ri[g]) ? 1 : 0;  // the chain ends here
-  }
-  __syncthreads();
+  const int cn = stage_chunk(e, ldx, w.rotf, c0, nr, sm);
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
-  const size_t nch = gridDim.y;
-  const double* w = rotw + ((size_t)r * nch + ch) * 3;
-  double v = w[0];
-  const double xlast = w[2];
-  for (int i = 0; i < cn; i++) {
-    const double xb = (i == cn - 1) ? xlast : X[r + sb[i]];
-    const double u = sch[i] ? v : X[r + sa[i]];
-    X[r + sa[i]] = sc[i] * u - ss[i] * xb;
-    v = fma(ss[i], u, sc[i] * xb);
-    if (send[i]) X[r + sb[i]] = v;
+  const size_t o = (size_t)ch * rows + r;
+  const double xlast = w.Xw[o];
+  double v = w.Bw[o];
+  Df vf;
+  if (MIXED) {
+    float2 t;
+    *reinterpret_cast<double*>(&t) = v;
+    vf = Df{t.x, t.y};
+  }
+  for (int i0 = 0; i0 < cn; i0 += kRotBatch) {
+    // Loads of a batch first: within a chunk, column b_i is written only at rotation i
+    // (a run's end) or i + 1 (as the next a), and a run-start column a_i by rotation i
+    // alone, so no value loaded here has been written yet.
+    double xb[kRotBatch], xa[kRotBatch];
+#pragma unroll
+    for (int u = 0; u < kRotBatch; u++) {
+      const int i = i0 + u;
+      xb[u] = i < cn ? ((i == cn - 1) ? xlast : X[r + sm.b[i]]) : 0.0;
+      xa[u] = (i < cn && !sm.chained[i]) ? X[r + sm.a[i]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kRotBatch; u++) {
+      const int i = i0 + u;
+      if (i < cn) {
+        if (!MIXED) {
+          const double uu = sm.chained[i] ? v : xa[u];
+          X[r + sm.a[i]] = fma(sm.c[i], uu, -sm.s[i] * xb[u]);
+          v = fma(sm.s[i], uu, sm.c[i] * xb[u]);
+          if (sm.ends[i]) X[r + sm.b[i]] = v;
+        } else {
+          const float4 q = sm.cs[i];
+          const Df cc = {q.x, q.y}, ss = {q.z, q.w}, xx = {(float)xb[u], 0.f};
+          const Df uu = sm.chained[i] ? vf : Df{(float)xa[u], 0.f};
+          const Df out = df_add(df_mul(cc, uu), df_mul(Df{-ss.hi, -ss.lo}, xx));
+          X[r + sm.a[i]] = (double)(out.hi + out.lo);
+          vf = df_add(df_mul(ss, uu), df_mul(cc, xx));
+          if (sm.ends[i]) X[r + sm.b[i]] = (double)(vf.hi + vf.lo);
+        }
+      }
+    }
   }
 }
 
+size_t rotate_scratch_bytes(int N, int rows) {
+  const size_t nch = ((size_t)N + kRotChunk - 1) / kRotChunk;
+  const size_t rr = (size_t)(rows > 0 ? rows : 1);
+  return nch * 8 + (size_t)N * 16 + 2 * nch * rr * 8 + 256;
+}
+
 void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
-                           double* rotw) {
+                           void* scratch, bool mixed) {
   const int nch = (e.N + kRotChunk - 1) / kRotChunk;
+  const size_t rr = (size_t)(rows > 0 ? rows : 1);
+  RotScratch w;
+  unsigned char* p = (unsigned char*)scratch;
+  w.A = (double*)p;
+  p += ((size_t)nch * 8 + 15) & ~(size_t)15;
+  w.rotf = (float4*)p;
+  p += (size_t)e.N * 16;
+  w.Bw = (double*)p;
+  w.Xw = w.Bw + (size_t)nch * rr;
+  if (rows <= 0 || nch == 0) return;
+  k_rot_prep<<<1, 1024, 0, st>>>(e, w);
+  SVDUP_COUNT_LAUNCH();
   dim3 g((rows + 127) / 128, nch);
-  k_rot_compose<<<g, 128, 0, st>>>(e, X, ldx, rows, rotw);
+  if (mixed) k_rot_compose<true><<<g, 128, 0, st>>>(e, X, ldx, rows, w);
+  else k_rot_compose<false><<<g, 128, 0, st>>>(e, X, ldx, rows, w);
   SVDUP_COUNT_LAUNCH();
-  k_rot_carry<<<(rows + 127) / 128, 128, 0, st>>>(e, rows, nch, rotw);
+  if (mixed) k_rot_carry<true><<<(rows + 127) / 128, 128, 0, st>>>(e, rows, w);
+  else k_rot_carry<false><<<(rows + 127) / 128, 128, 0, st>>>(e, rows, w);
   SVDUP_COUNT_LAUNCH();
-  k_rot_apply<<<g, 128, 0, st>>>(e, X, ldx, rows, rotw);
+  if (mixed) k_rot_apply<true><<<g, 128, 0, st>>>(e, X, ldx, rows, w);
+  else k_rot_apply<false><<<g, 128, 0, st>>>(e, X, ldx, rows, w);
   SVDUP_COUNT_LAUNCH();
 }
 

@@ -870,13 +870,40 @@ __global__ void k_secular(const double* __restrict__ dc, const double* __restric
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
+  if (far && blockIdx.x == 0) {
+    // Block 0 (scheduled first, so it runs beside the others) solves the extreme root,
+    // whose bracket reaches far past the poles, with direct sums over the whole block.
+    __shared__ double red[4 * 32];
+    const BlockSums bs = {dc, z2c, k, red};
+    int o;
+    double t;
+    const int j = k - 1;
+    const int bad = secular_root(bs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
+    if (threadIdx.x == 0) {
+      if (bad) latch(status, SVDUP_ENOCONV);
+      if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
+      orgc[j] = o;
+      tauc[j] = t;
+      if (rho > 0.0) {
+        org[j] = o;
+        tau[j] = t;
+        dorg[j] = dk[o];
+      } else {
+        org[0] = k - 1 - o;
+        tau[0] = -t;
+        dorg[0] = dk[k - 1 - o];
+      }
+    }
+    return;
+  }
+  const int off = far ? 1 : 0;  // block 0 is busy with the extreme root
+  const int warps = ((gridDim.x - off) * blockDim.x) >> 5;
   const DirectSums direct = {dc, z2c, k};
-  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < k; j += warps) {
+  for (int j = ((blockIdx.x - off) * blockDim.x + threadIdx.x) >> 5; j < k; j += warps) {
     int o;
     double t;
     int bad;
-    if (far && j == k - 1) continue;  // k_secular_last
+    if (far && j == k - 1) continue;  // done by block 0
     if (far) {
       const int b = j / kSqLeaf;
       const FarSums fs = {dc, z2c, sqn[2 * b], sqn[2 * b + 1], sqb[2 * b], sqb[2 * b + 1],
@@ -904,51 +931,6 @@ __global__ void k_secular(const double* __restrict__ dc, const double* __restric
   }
 }
 
-// The extreme root alone, its sums spread over a whole block.
-__global__ void __launch_bounds__(512) k_secular_last(
-    const double* __restrict__ dc, const double* __restrict__ z2c, const int* __restrict__ kp,
-    const double* __restrict__ rhop, const double* __restrict__ dk, int* orgc, double* tauc,
-    int* org, double* tau, double* dorg, int* status, int maxit) {
-  __shared__ double red[4 * 32];
-  __shared__ double s_zn2;
-  const int k = kp[0];
-  if (k < kSqMinK) return;
-  const double rho = rhop[0];
-  const double R = fabs(rho);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double a = 0.0;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) a += z2c[i];
-  a = warp_sum(a);
-  if (lane == 0) red[w] = a;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q];
-    s_zn2 = t;
-  }
-  __syncthreads();
-  const BlockSums bs = {dc, z2c, k, red};
-  int o;
-  double t;
-  const int j = k - 1;
-  const int bad = secular_root(bs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
-  if (threadIdx.x == 0) {
-    if (bad) latch(status, SVDUP_ENOCONV);
-    if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
-    orgc[j] = o;
-    tauc[j] = t;
-    if (rho > 0.0) {
-      org[j] = o;
-      tau[j] = t;
-      dorg[j] = dk[o];
-    } else {
-      org[0] = k - 1 - o;
-      tau[0] = -t;
-      dorg[0] = dk[k - 1 - o];
-    }
-  }
-}
-
 static int secular_blocks(int N) {
   int warps = N;                   // one warp per root
   int blocks = (warps * 32 + 255) / 256;
@@ -966,15 +948,10 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
     SVDUP_COUNT_LAUNCH();
     sqv = e.sqv;
   }
-  k_secular<<<secular_blocks(e.N), 256, 0, st>>>(e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc,
-                                                e.org, e.tau, e.dorg, status, maxit, e.sqb,
-                                                e.sqn, sqv);
+  k_secular<<<secular_blocks(e.N) + (sqv ? 1 : 0), 256, 0, st>>>(
+      e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org, e.tau, e.dorg, status, maxit, e.sqb,
+      e.sqn, sqv);
   SVDUP_COUNT_LAUNCH();
-  if (sqv) {
-    k_secular_last<<<1, 512, 0, st>>>(e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org,
-                                      e.tau, e.dorg, status, maxit);
-    SVDUP_COUNT_LAUNCH();
-  }
 }
 
 // The stand-alone secular entry point: d strictly ascending, z nonzero; the problem
@@ -1148,9 +1125,13 @@ __global__ void k_defl_copy(Eig e, const double* __restrict__ ysorted, double* o
   }
 }
 
-void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final) {
-  k_norms<<<secular_blocks(e.N), 256, 0, st>>>(e, ysorted, out_final);
-  SVDUP_COUNT_LAUNCH();
+void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final, bool pairs) {
+  if (pairs) {
+    launch_norms_df(st, e, ysorted, out_final, secular_blocks(e.N));
+  } else {
+    k_norms<<<secular_blocks(e.N), 256, 0, st>>>(e, ysorted, out_final);
+    SVDUP_COUNT_LAUNCH();
+  }
   if (ysorted) {
     k_defl_copy<<<(e.N + 255) / 256, 256, 0, st>>>(e, ysorted, out_final);
     SVDUP_COUNT_LAUNCH();
@@ -1277,13 +1258,14 @@ __global__ void __launch_bounds__(1024) k_gather_rotate(Eig e, const double* __r
     for (int s = threadIdx.x; s < e.N; s += blockDim.x) ysorted[s] = v[s];
 }
 
-void launch_apply_qt(cudaStream_t st, Eig e, const double* xphys, double* work, double* out_final) {
+void launch_apply_qt(cudaStream_t st, Eig e, const double* xphys, double* work, double* out_final,
+                     bool pairs) {
   size_t sm = vec_smem(e.N);
   cudaFuncSetAttribute(k_gather_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_gather_rotate<<<1, 1024, sm, st>>>(e, xphys, work, sm > 0 ? 1 : 0);
   SVDUP_COUNT_LAUNCH();
-  // k_norms recomputes inv (identical values); only the product is wanted here.
-  launch_norms(st, e, work, out_final);
+  // the norms are recomputed (identical values in FP64); only the product is wanted here
+  launch_norms(st, e, work, out_final, pairs);
 }
 
 __global__ void k_apply_q_core(Eig e, const double* __restrict__ xfinal, double* vsorted) {
@@ -1318,9 +1300,14 @@ __global__ void __launch_bounds__(1024) k_unrotate_scatter(Eig e, double* vsorte
   for (int s = threadIdx.x; s < e.N; s += blockDim.x) yphys[e.perm[s]] = v[s];
 }
 
-void launch_apply_q(cudaStream_t st, Eig e, const double* xfinal, double* work, double* yphys) {
-  k_apply_q_core<<<secular_blocks(e.N), 256, 0, st>>>(e, xfinal, work);
-  SVDUP_COUNT_LAUNCH();
+void launch_apply_q(cudaStream_t st, Eig e, const double* xfinal, double* work, double* yphys,
+                    bool pairs) {
+  if (pairs) {
+    launch_apply_q_core_df(st, e, xfinal, work, secular_blocks(e.N));
+  } else {
+    k_apply_q_core<<<secular_blocks(e.N), 256, 0, st>>>(e, xfinal, work);
+    SVDUP_COUNT_LAUNCH();
+  }
   size_t sm = vec_smem(e.N);
   cudaFuncSetAttribute(k_unrotate_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_unrotate_scatter<<<1, 1024, sm, st>>>(e, work, yphys, sm > 0 ? 1 : 0);
