@@ -98,6 +98,7 @@ struct Eig {
   // origin and half width, its near pole range, and the far sums at its nodes
   double* sqb;
   int* sqn;
+  int* sqf;  // the boxed roots first .. last
   double* sqv;
   // double-float copies for the pair-arithmetic sums (svdup_dfsum.cu): scales fsc[4]
   // (exponents), tau, zhat, y and root weights as (hi, lo) FP32 pairs

@@ -9,6 +9,8 @@
 //   probe that pairs left and right vectors), and Shat = sqrt(D_n) (STEP 8).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "svdup_internal.cuh"
 
 namespace svdup {
@@ -211,15 +213,18 @@ void launch_fill_generic(cudaStream_t st, Eig e, const double* d, const double* 
 //     z~_i^2 = sum_{t=i0..i} z_t^2   and   d~_i = sum z_t^2 d_t / z~_i^2
 // (each Givens step is a z^2-weighted mean), so the sequential test reduces to
 //     |d_i - d~_{i-1}| |z_i| z~_{i-1} <= tol (z~_{i-1}^2 + z_i^2).
-// One warp walks the survivors on shared-memory copies with just these two running
-// sums, 32 pairs per step, to find where runs start and end; only pairs that pass with
-// the original values (a bitmask found in parallel) can start a run.  The rotation records (position pair,
+// Only pairs that pass with the original values (a bitmask found in parallel) can start
+// a run, so the maximal chains of such pairs are walked in parallel by the block's
+// warps, on shared-memory copies with just these two running sums, 32 pairs per step;
+// the rare run that reaches into the next chain is resumed in order afterwards, so the
+// boundaries are those of the sequential walk.  The rotation records (position pair,
 // cos, sin) and the merged values are then formed in parallel from segmented prefix
 // sums of z^2 and z^2 d over the runs.  This is the Bunch-Nielsen-Sorensen deflation
 // in exact arithmetic; only the rounding of the merged values differs from applying
 // the rotations one at a time.
 // ---------------------------------------------------------------------------
 constexpr int kDeflateThreads = 1024;
+constexpr int kMaxOverrun = 128;  // chains entered by the previous chain's run, listed
 
 // Dynamic shared memory of k_deflate: two bitmasks, plus the survivors' d, z and
 // positions when they fit.
@@ -291,6 +296,9 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
   __shared__ int scnt[kDeflateThreads];
   __shared__ double sW[kDeflateThreads], sM[kDeflateThreads];
   __shared__ double s_tol, s_zn, s_dsc, s_zsc;
+  __shared__ int s_nov;
+  __shared__ int s_ovh[kMaxOverrun];
+  __shared__ double s_ovW[kMaxOverrun], s_ovM[kMaxOverrun];
   const int N = e.N;
   const double rho = e.rhop[0];
   int tid = threadIdx.x, nt = blockDim.x;
@@ -379,27 +387,37 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
     brk[i] = m ? 0 : 1;
   }
   __syncthreads();
-  // Run boundaries by one warp walking the survivors 32 pairs at a time.  From position
-  // pos with carrier (W, M), lane l tests pair (pos + l - 1, pos + l) against the
-  // carrier that exists if every earlier lane merged (W, M plus the lanes' exclusive
-  // prefix sums of z^2 and z^2 d): exactly the sequential carrier up to the first lane
-  // that fails.  Earlier lanes merge; the failing position starts a new run, and the
-  // walk resumes at the next pair that passes with the original values (only such a
-  // pair can start a merge).
+  // Run boundaries, as the sequential walk finds them.  Runs start only at pairs that pass
+  // with the original values (set bits of cmask); a chain is a maximal sequence of such
+  // pairs.  A run may continue past its chain's end through poles whose pairs fail alone
+  // but pass with the run's carrier, up to the pole before the next chain's first pair.
+  // Pass 1: warp w walks the chains whose first pair lies in bitmask words w, w + 32, ...
+  // from a fresh carrier, exactly as the sequential walk enters them, unless the previous
+  // chain's last run reached the next chain's first pole ("overran"); such chains are
+  // listed with the carrier.  Pass 2: one warp resumes the sequential walk at each listed
+  // chain, in order, with the listed carrier, cascading while runs keep overrunning.
+  // A warp steps 32 pairs at a time: from position pos with carrier (W, M), lane l tests
+  // pair (pos + l - 1, pos + l) against the carrier that exists if every earlier lane
+  // merged (W, M plus the lanes' exclusive prefix sums of z^2 and z^2 d): exactly the
+  // sequential carrier up to the first lane that fails.  Earlier lanes merge; a failing
+  // pole starts a new run with the next pair if that pair passes alone.
   const int cpt = (nk + nt - 1) / nt;
   const int c0 = min(nk, tid * cpt), c1 = min(nk, c0 + cpt);
   for (int i = tid; i < nk; i += nt) brk[i] = 1;
+  if (tid == 0) s_nov = 0;
   __syncthreads();
-  if (tid < 32) {
-    const int lane = tid;
+  {
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const int nw = (nk + 31) >> 5;
-    auto next_cand = [&](int from) -> int {  // first set bit of cmask at or after from
+    auto bit = [&](int i) -> bool { return i < nk && ((cmask[i >> 5] >> (i & 31)) & 1u); };
+    // first position >= from whose bit equals want (nk if none), by the whole warp
+    auto next_bit = [&](int from, bool want) -> int {
       if (from >= nk) return nk;
       for (int w0 = from >> 5; w0 < nw; w0 += 32) {
         const int w = w0 + lane;
         unsigned m = 0u;
         if (w < nw) {
-          m = cmask[w];
+          m = want ? cmask[w] : ~cmask[w];
           if (w == (from >> 5)) m &= 0xffffffffu << (from & 31);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
@@ -411,38 +429,99 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
       }
       return nk;
     };
-    int pos = next_cand(1);
-    bool have = false;
-    double W = 0.0, M = 0.0;
-    while (pos < nk) {
-      if (!have) {
-        const double zj = kz[pos - 1];
-        W = zj * zj;
-        M = W * kd[pos - 1];
-      }
-      const int i = pos + lane;
-      double zi = 0.0, di = 0.0;
-      if (i < nk) { zi = kz[i]; di = kd[i]; }
-      const double z2 = zi * zi, dz = z2 * di;
-      double iz2 = z2, idz = dz;  // inclusive prefix over the lanes
+    // Walks the chain with first pair h up to pole lim (the pole before the next chain's
+    // first pair, or nk - 1); returns 1 if the last run merged pole lim and a chain
+    // follows, with the carrier in (W, M).
+    auto walk = [&](int h, int lim, bool have, double& W, double& M) -> int {
+      int pos = h;
+      while (true) {
+        if (!have) {
+          const double zj = kz[pos - 1];
+          W = zj * zj;
+          M = W * kd[pos - 1];
+        }
+        const int i = pos + lane;
+        const int nin = min(32, lim - pos + 1);
+        double zi = 0.0, di = 0.0;
+        if (lane < nin) { zi = kz[i]; di = kd[i]; }
+        const double z2 = zi * zi, dz = z2 * di;
+        double iz2 = z2, idz = dz;  // inclusive prefix over the lanes
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const double a2 = __shfl_up_sync(0xffffffffu, iz2, o);
-        const double ad = __shfl_up_sync(0xffffffffu, idz, o);
-        if (lane >= o) { iz2 += a2; idz += ad; }
+        for (int o = 1; o < 32; o <<= 1) {
+          const double a2 = __shfl_up_sync(0xffffffffu, iz2, o);
+          const double ad = __shfl_up_sync(0xffffffffu, idz, o);
+          if (lane >= o) { iz2 += a2; idz += ad; }
+        }
+        const bool ok = lane < nin && merges(di, zi, W + (iz2 - z2), M + (idz - dz), tol2);
+        const unsigned fail = __ballot_sync(0xffffffffu, !ok);
+        const int nm = fail ? __ffs(fail) - 1 : 32;  // lanes that merge
+        if (lane < nm) brk[i] = 0;
+        if (nm == nin) {  // every pole of the window merged
+          W += __shfl_sync(0xffffffffu, iz2, nm - 1);
+          M += __shfl_sync(0xffffffffu, idz, nm - 1);
+          have = true;
+          pos += nm;
+          if (pos > lim) return lim + 1 < nk ? 1 : 0;
+        } else {  // pole pos + nm failed: a new run only if its pair with the next passes
+          have = false;
+          pos += nm + 1;
+          if (pos > lim || !bit(pos)) return 0;
+        }
       }
-      const bool ok = i < nk && merges(di, zi, W + (iz2 - z2), M + (idz - dz), tol2);
-      const unsigned fail = __ballot_sync(0xffffffffu, !ok);
-      const int nm = fail ? __ffs(fail) - 1 : 32;  // lanes that merge
-      if (lane < nm) brk[i] = 0;
-      if (nm == 32) {
-        W += __shfl_sync(0xffffffffu, iz2, 31);
-        M += __shfl_sync(0xffffffffu, idz, 31);
-        have = true;
-        pos += 32;
+    };
+    for (int w = warp; w < nw; w += nwarps) {
+      const unsigned m = cmask[w];
+      const unsigned prev = (w > 0) ? (cmask[w - 1] >> 31) : 0u;
+      unsigned heads = m & ~((m << 1) | prev);  // first pair of each chain
+      while (heads) {
+        const int h = (w << 5) + __ffs(heads) - 1;
+        heads &= heads - 1;
+        const int nh = next_bit(next_bit(h, false), true);  // the next chain's first pair
+        double W = 0.0, M = 0.0;
+        if (walk(h, nh - 1, false, W, M) && lane == 0) {
+          const int q = atomicAdd(&s_nov, 1);
+          if (q < kMaxOverrun) { s_ovh[q] = nh; s_ovW[q] = W; s_ovM[q] = M; }
+        }
+      }
+    }
+    __syncthreads();
+    if (warp == 0 && s_nov > 0) {
+      const int nov = s_nov;
+      if (nov > kMaxOverrun) {  // too many to list: the whole walk again, sequentially
+        for (int i = lane; i < nk; i += 32) brk[i] = 1;
+        __syncwarp();
+        int h = next_bit(1, true);
+        bool have = false;
+        double W = 0.0, M = 0.0;
+        while (h < nk) {
+          const int nh = next_bit(next_bit(h, false), true);
+          have = walk(h, nh - 1, have, W, M) != 0;
+          h = nh;
+        }
       } else {
-        have = false;
-        pos = next_cand(pos + nm + 1);
+        if (lane == 0)  // ascending chain order (a short list)
+          for (int x = 1; x < nov; x++)
+            for (int y = x; y > 0 && s_ovh[y - 1] > s_ovh[y]; y--) {
+              const int th = s_ovh[y]; s_ovh[y] = s_ovh[y - 1]; s_ovh[y - 1] = th;
+              const double tw = s_ovW[y]; s_ovW[y] = s_ovW[y - 1]; s_ovW[y - 1] = tw;
+              const double tm = s_ovM[y]; s_ovM[y] = s_ovM[y - 1]; s_ovM[y - 1] = tm;
+            }
+        __syncwarp();
+        int done = 0;  // chains before this position hold their final boundaries
+        for (int x = 0; x < nov; x++) {
+          int h = s_ovh[x];
+          if (h <= done) continue;  // listed by a chain that a resumed walk redid
+          double W = s_ovW[x], M = s_ovM[x];
+          while (true) {  // resume the sequential walk at chain h
+            const int nh = next_bit(next_bit(h, false), true);
+            for (int i = h + lane; i < nh; i += 32) brk[i] = 1;
+            __syncwarp();
+            const int more = walk(h, nh - 1, true, W, M);
+            done = nh;
+            if (!more) break;
+            h = nh;
+          }
+        }
       }
     }
   }
@@ -612,28 +691,74 @@ __device__ __forceinline__ int lower_bound_d(const double* a, int n, double v) {
   return lo;
 }
 
-// Boxes: sqb[2b] = d_{64b} (the coordinate origin), sqb[2b+1] = r; sqn[2b], sqn[2b+1] =
-// the near pole range [n0, n1).
+// Roots whose bracket is wider than the rest of their box -- the isolated largest
+// poles, such as the large eigenvalues earlier updates have added, among the poles of
+// a solve -- would stretch their box over the spectrum (and every pole into its near
+// field).  From each end, while one bracket gap is more than half the span of the next
+// kSqLeaf roots, every root up to that gap is solved alone by one block with direct
+// sums (at most kSqMaxWide per end), as is the last root (beyond all poles).  The boxes
+// of kSqLeaf roots cover roots first .. last; k_sq_boxes stores the layout in sqf.
+constexpr int kSqMaxWide = 16;
+
+__device__ void sq_layout(const double* __restrict__ dc, int k, int* first, int* last) {
+  int f = 0, l = k - 2;
+  if (k >= kSqMinK) {
+    while (f < kSqMaxWide) {
+      const double span = dc[f + kSqLeaf] - dc[f];
+      int g = f;
+      double gmax = -1.0;
+      for (int j = f; j < f + kSqLeaf; j++) {
+        const double gap = dc[j + 1] - dc[j];
+        if (gap > gmax) { gmax = gap; g = j; }
+      }
+      if (!(gmax > 0.5 * span) || g + 1 > kSqMaxWide) break;
+      f = g + 1;
+    }
+    while (k - 2 - l < kSqMaxWide) {
+      const double span = dc[l + 1] - dc[l + 1 - kSqLeaf];
+      int g = l;
+      double gmax = -1.0;
+      for (int j = l; j > l - kSqLeaf; j--) {
+        const double gap = dc[j + 1] - dc[j];
+        if (gap > gmax) { gmax = gap; g = j; }
+      }
+      if (!(gmax > 0.5 * span) || k - 1 - g > kSqMaxWide) break;
+      l = g - 1;
+    }
+  }
+  *first = f;
+  *last = l;
+}
+
+__device__ __forceinline__ int sq_boxes(int first, int last) {
+  return (last - first + 1 + kSqLeaf - 1) / kSqLeaf;
+}
+
+// Boxes: sqb[2b] = d_{j0} (the coordinate origin, j0 = first + b kSqLeaf), sqb[2b+1] = r;
+// sqn[2b], sqn[2b+1] = the near pole range [n0, n1): the box's roots lie in
+// [d_{j0}, d_{j1}], every pole outside [n0, n1) is at least 2r beyond that interval, and
+// the near range reaches at least one box width past each end.
 __global__ void k_sq_boxes(const double* __restrict__ dc, const int* __restrict__ kp, double* sqb,
-                           int* sqn) {
+                           int* sqn, int* sqf) {
   const int k = kp[0];
   if (k < kSqMinK) return;
-  const int nb = (k - 1 + kSqLeaf - 1) / kSqLeaf;
-  const int nleaf = (k + kSqLeaf - 1) / kSqLeaf;
+  int first, last;
+  sq_layout(dc, k, &first, &last);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sqf[0] = first;
+    sqf[1] = last;
+  }
+  const int nb = sq_boxes(first, last);
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-    const int j0 = b * kSqLeaf, j1 = min(j0 + kSqLeaf, k - 1);
+    const int j0 = first + b * kSqLeaf, j1 = min(j0 + kSqLeaf, last + 1);
     const double lo = dc[j0], hi = dc[j1];
     const double r = 0.5 * (hi - lo);
     const int t_lo = lower_bound_d(dc, k, lo - 2.0 * r);     // first pole >= c - 3r
     const int t_hi = lower_bound_d(dc, k, hi + 2.0 * r);     // first pole >= c + 3r
-    int a_lo = min(b - 1, t_lo / kSqLeaf);
-    a_lo = max(a_lo, 0);
-    int a_hi = max(b + 1, t_hi / kSqLeaf);                   // leaf of the first pole past it
-    a_hi = min(a_hi, nleaf - 1);
     sqb[2 * b] = lo;
     sqb[2 * b + 1] = r;
-    sqn[2 * b] = a_lo * kSqLeaf;
-    sqn[2 * b + 1] = min(k, (a_hi + 1) * kSqLeaf);
+    sqn[2 * b] = max(0, min(j0 - kSqLeaf, t_lo));
+    sqn[2 * b + 1] = min(k, max(j1 + kSqLeaf, t_hi));
   }
 }
 
@@ -641,10 +766,10 @@ __global__ void k_sq_boxes(const double* __restrict__ dc, const int* __restrict_
 // psi_L', psi_R, psi_R'.  One warp per (box, node).
 __global__ void k_sq_nodes(const double* __restrict__ dc, const double* __restrict__ z2c,
                            const int* __restrict__ kp, const double* __restrict__ sqb,
-                           const int* __restrict__ sqn, double* sqv) {
+                           const int* __restrict__ sqn, const int* __restrict__ sqf, double* sqv) {
   const int k = kp[0];
   if (k < kSqMinK) return;
-  const int nb = (k - 1 + kSqLeaf - 1) / kSqLeaf;
+  const int nb = sq_boxes(sqf[0], sqf[1]);
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nb * kSqP; w += warps) {
@@ -845,12 +970,31 @@ __device__ int secular_root(const Sums& sums, const double* __restrict__ dc,
 
 // Writes roots in both orientations: (orgc, tauc) for rho > 0 form, (org, tau, dorg)
 // for the problem as given (rho < 0: root j' of the reflected problem is root k-1-j').
-__global__ void k_secular(const double* __restrict__ dc, const double* __restrict__ z2c,
-                          const int* __restrict__ kp, const double* __restrict__ rhop,
-                          const double* __restrict__ dk, int* orgc, double* tauc, int* org,
-                          double* tau, double* dorg, int* status, int maxit,
-                          const double* __restrict__ sqb, const int* __restrict__ sqn,
-                          const double* __restrict__ sqv) {
+__device__ __forceinline__ void store_root(int j, int o, double t, int k, double rho,
+                                           const double* __restrict__ dk, int* orgc,
+                                           double* tauc, int* org, double* tau, double* dorg) {
+  orgc[j] = o;
+  tauc[j] = t;
+  if (rho > 0.0) {
+    org[j] = o;
+    tau[j] = t;
+    dorg[j] = dk[o];
+  } else {
+    const int jj = k - 1 - j, oo = k - 1 - o;
+    org[jj] = oo;
+    tau[jj] = -t;
+    dorg[jj] = dk[oo];
+  }
+}
+
+constexpr int kSecularThreads = 1024;
+constexpr int kSecularSpecial = 1 + 2 * kSqMaxWide;  // the last root and the wide roots
+
+__global__ void __launch_bounds__(kSecularThreads) k_secular(
+    const double* __restrict__ dc, const double* __restrict__ z2c, const int* __restrict__ kp,
+    const double* __restrict__ rhop, const double* __restrict__ dk, int* orgc, double* tauc,
+    int* org, double* tau, double* dorg, int* status, int maxit, const double* __restrict__ sqb,
+    const int* __restrict__ sqn, const int* __restrict__ sqf, const double* __restrict__ sqv) {
   __shared__ double s_zn2;
   __shared__ double s_x[kSqP], s_w[kSqP];
   const int k = kp[0];
@@ -870,42 +1014,41 @@ __global__ void k_secular(const double* __restrict__ dc, const double* __restric
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  if (far && blockIdx.x == 0) {
-    // Block 0 (scheduled first, so it runs beside the others) solves the extreme root,
-    // whose bracket reaches far past the poles, with direct sums over the whole block.
+  const int first = far ? sqf[0] : 0, last = far ? sqf[1] : k - 2;
+  if (far && blockIdx.x < kSecularSpecial) {
+    // The first blocks (scheduled first, each alone on its SM: one block of
+    // kSecularThreads per SM) solve the last root, whose bracket reaches far past the
+    // poles, and the wide roots, with direct sums over the whole block.
+    const int s = blockIdx.x;
+    int j = -1;
+    if (s == 0) j = k - 1;
+    else if (s <= kSqMaxWide) j = (s - 1 < first) ? s - 1 : -1;
+    else j = (last + s - kSqMaxWide <= k - 2) ? last + s - kSqMaxWide : -1;
+    if (j < 0) return;
     __shared__ double red[4 * 32];
     const BlockSums bs = {dc, z2c, k, red};
     int o;
     double t;
-    const int j = k - 1;
     const int bad = secular_root(bs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
     if (threadIdx.x == 0) {
       if (bad) latch(status, SVDUP_ENOCONV);
       if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
-      orgc[j] = o;
-      tauc[j] = t;
-      if (rho > 0.0) {
-        org[j] = o;
-        tau[j] = t;
-        dorg[j] = dk[o];
-      } else {
-        org[0] = k - 1 - o;
-        tau[0] = -t;
-        dorg[0] = dk[k - 1 - o];
-      }
+      store_root(j, o, t, k, rho, dk, orgc, tauc, org, tau, dorg);
     }
     return;
   }
-  const int off = far ? 1 : 0;  // block 0 is busy with the extreme root
-  const int warps = ((gridDim.x - off) * blockDim.x) >> 5;
+  const int off = far ? kSecularSpecial : 0;
+  // roots interleaved over the blocks (root j to block j mod G): neighbouring roots, whose
+  // work is alike, spread over the SMs
+  const int G = gridDim.x - off, bm = blockIdx.x - off, wl = threadIdx.x >> 5;
   const DirectSums direct = {dc, z2c, k};
-  for (int j = ((blockIdx.x - off) * blockDim.x + threadIdx.x) >> 5; j < k; j += warps) {
+  for (int j = wl * G + bm; j < k; j += G * (blockDim.x >> 5)) {
     int o;
     double t;
     int bad;
-    if (far && j == k - 1) continue;  // done by block 0
+    if (far && (j < first || j > last)) continue;  // done by blocks 0-2
     if (far) {
-      const int b = j / kSqLeaf;
+      const int b = (j - first) / kSqLeaf;
       const FarSums fs = {dc, z2c, sqn[2 * b], sqn[2 * b + 1], sqb[2 * b], sqb[2 * b + 1],
                           sqv + (size_t)4 * b * kSqP, s_x, s_w};
       bad = secular_root(fs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
@@ -915,20 +1058,23 @@ __global__ void k_secular(const double* __restrict__ dc, const double* __restric
     if (lane == 0) {
       if (bad) latch(status, SVDUP_ENOCONV);
       if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
-      orgc[j] = o;
-      tauc[j] = t;
-      if (rho > 0.0) {
-        org[j] = o;
-        tau[j] = t;
-        dorg[j] = dk[o];
-      } else {
-        int jj = k - 1 - j, oo = k - 1 - o;
-        org[jj] = oo;
-        tau[jj] = -t;
-        dorg[jj] = dk[oo];
-      }
+      store_root(j, o, t, k, rho, dk, orgc, tauc, org, tau, dorg);
     }
   }
+}
+
+// Streaming multiprocessors of the current device (queried once per device).
+static int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 152;
+  }
+  return cached[dev];
 }
 
 static int secular_blocks(int N) {
@@ -941,16 +1087,19 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
   const double* sqv = nullptr;
   if (e.sqv && e.N >= kSqMinK) {  // far-field set-up (the kernels skip small k themselves)
     const int nb = (e.N + kSqLeaf - 1) / kSqLeaf;
-    k_sq_boxes<<<(nb + 127) / 128, 128, 0, st>>>(e.dc, e.kp, e.sqb, e.sqn);
+    k_sq_boxes<<<(nb + 127) / 128, 128, 0, st>>>(e.dc, e.kp, e.sqb, e.sqn, e.sqf);
     SVDUP_COUNT_LAUNCH();
     const int nw = nb * kSqP;
-    k_sq_nodes<<<(nw * 32 + 255) / 256, 256, 0, st>>>(e.dc, e.z2c, e.kp, e.sqb, e.sqn, e.sqv);
+    k_sq_nodes<<<(nw * 32 + 255) / 256, 256, 0, st>>>(e.dc, e.z2c, e.kp, e.sqb, e.sqn, e.sqf,
+                                                      e.sqv);
     SVDUP_COUNT_LAUNCH();
     sqv = e.sqv;
   }
-  k_secular<<<secular_blocks(e.N) + (sqv ? 1 : 0), 256, 0, st>>>(
+  // a warp per root, at most one block per SM (the roots are interleaved over them)
+  const int blocks = std::min((e.N + kSecularThreads / 32 - 1) / (kSecularThreads / 32), sm_count());
+  k_secular<<<blocks + (sqv ? kSecularSpecial : 0), kSecularThreads, 0, st>>>(
       e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org, e.tau, e.dorg, status, maxit, e.sqb,
-      e.sqn, sqv);
+      e.sqn, e.sqf, sqv);
   SVDUP_COUNT_LAUNCH();
 }
 
