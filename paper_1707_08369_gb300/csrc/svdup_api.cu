@@ -164,10 +164,9 @@ FmmPlan make_plan(Arena& ar, int N, int rows, double eps, int leaf, bool mixed) 
   const size_t rrows = (size_t)(rows > 0 ? rows : 1);
   if (mixed) rows = 1;
   f.s = leaf;
-  f.Lmax = (N + f.s - 1) / f.s;
-  if (f.Lmax < 1) f.Lmax = 1;
+  f.Lmax = (N + f.s - 1) / f.s + 1;  // one more for the leaf offset (k_fmm_boxes)
   size_t L = (size_t)f.Lmax;
-  f.L = ar.take<int>(2);
+  f.L = ar.take<int>(4);
   f.sbox_c = ar.take<double>(L);
   f.sbox_r = ar.take<double>(L);
   f.tbox_c = ar.take<double>(L + 1);
@@ -193,6 +192,7 @@ MixPlan make_mix(Arena& ar, int rows, const FmmPlan& f) {
   mp.rows = rows;
   mp.rt = (rows + 127) / 128;
   mp.s = f.s;
+  mp.fL = f.L;
   mp.Lmax = f.Lmax;
   mp.kx = f.Lmax * f.s / 64;
   mp.kphi = (f.Lmax * kMixP + 63) / 64;
@@ -208,6 +208,7 @@ MixPlan make_mix(Arena& ar, int rows, const FmmPlan& f) {
   mp.nnear = ar.take<int>(L + 1);
   mp.near = ar.take<int>((L + 1) * L);
   mp.noff = ar.take<int>(L + 2);
+  mp.order = ar.take<int>(L + 1);
   return mp;
 }
 
@@ -371,13 +372,15 @@ void queue_product_mixed(svdup_ctx* h, Eig e, FmmPlan f, MixPlan mp, int rows, d
   int dense = use_dense(h, e.N, mode) ? 1 : 0;
   mp.rows = rows;
   mp.rt = (rows + 127) / 128;
-  stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rot, true);
-  launch_mix_gather(h->stream, e, X, ldx, rows, mp, om);
-  stage_end(h);
+  // the set-up (leaves, near lists, operator tiles) depends on the solve alone; it
+  // comes first because the gather places X's columns by the leaf offset it finds
   stage_begin(h, SVDUP_STAGE_SETUP);
   launch_fmm_setup(h->stream, e, f, 0);
   launch_mix_setup(h->stream, e, f, mp, dense);
+  stage_end(h);
+  stage_begin(h, SVDUP_STAGE_GATHER);
+  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rot, true);
+  launch_mix_gather(h->stream, e, X, ldx, rows, mp, om);
   stage_end(h);
   if (!dense) {
     stage_begin(h, SVDUP_STAGE_P2M);

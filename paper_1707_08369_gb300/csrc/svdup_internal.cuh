@@ -120,14 +120,16 @@ struct OutMap {
 };
 
 // FMM (flat Chebyshev far field + direct near field) plan for one product.
-// Source leaf a holds poles [a s, a s + s).  Target leaf b < Ls holds the roots of the
-// same index range except the extreme root (the largest for rho > 0, the smallest for
-// rho < 0, which can lie far outside the poles); target leaf Ls holds that root alone.
+// Source leaf a holds the sorted poles [a s - P, a s + s - P) (leaf K position g is pole
+// g - P; the offset P starts a leaf at an isolated group of largest poles, see
+// k_fmm_boxes).  Target leaf b < Lt - 1 holds the roots [b s - Pt, b s + s - Pt) that lie
+// between poles; the last target leaf holds the extreme root (the largest for rho > 0,
+// the smallest for rho < 0, which can lie far outside the poles) alone.
 struct FmmPlan {
   int p;     // expansion order
   int s;     // leaf size
-  int Lmax;  // upper bound on the number of source leaves (ceil(N / s)); targets Lmax + 1
-  int* L;    // device: [0] source leaves Ls, [1] target leaves Lt
+  int Lmax;  // upper bound on the number of source leaves (ceil(N / s) + 1); targets Lmax + 1
+  int* L;    // device: source leaves Ls, target leaves Lt, leaf offsets P (poles), Pt (roots)
   double* sbox_c;
   double* sbox_r;
   double* tbox_c;
@@ -168,6 +170,8 @@ struct MixPlan {
   int* nnear;           // per target leaf: near source leaves (dense: every leaf)
   int* near;            // near[b * Lmax + i]
   int* noff;            // exclusive prefix sum of nnear
+  int* order;           // target leaves by descending nnear (the output stage's job order)
+  const int* fL;        // the plan's leaf counts and offsets (FmmPlan::L)
 };
 
 constexpr int kMixP = 16;

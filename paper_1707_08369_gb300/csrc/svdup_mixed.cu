@@ -279,9 +279,9 @@ __global__ void __launch_bounds__(256) k_mix_gather(Eig e, const double* __restr
   __shared__ long long scol[kKB];
   const int rt = blockIdx.x, kt = blockIdx.y;
   const int k = e.kp[0];
-  if (threadIdx.x < kKB) {
-    int t = kt * kKB + threadIdx.x;
-    scol[threadIdx.x] = t < k ? (long long)e.perm[e.idx[t]] * ldx : -1;
+  if (threadIdx.x < kKB) {  // K position kt 64 + c holds sorted pole kt 64 + c - P
+    const int t = kt * kKB + threadIdx.x - mp.fL[2];
+    scol[threadIdx.x] = (t >= 0 && t < k) ? (long long)e.perm[e.idx[t]] * ldx : -1;
   }
   __syncthreads();
   unsigned char* tile = mp.Xp + ((size_t)rt * mp.kx + kt) * kTileA;
@@ -336,6 +336,17 @@ __global__ void k_mix_near(FmmPlan f, MixPlan mp, int dense) {
       acc += mp.nnear[b];
     }
     mp.noff[Lt] = acc;
+  }
+  // Output jobs by descending near count (ties by leaf): the longest CTAs start first
+  // instead of trailing the grid.
+  for (int b = threadIdx.x; b < Lt; b += blockDim.x) {
+    const int nb = mp.nnear[b];
+    int rank = 0;
+    for (int c = 0; c < Lt; c++) {
+      const int nc = mp.nnear[c];
+      rank += (nc > nb || (nc == nb && c < b)) ? 1 : 0;
+    }
+    mp.order[rank] = b;
   }
 }
 
@@ -405,6 +416,7 @@ __global__ void k_mix_pack_C(Eig e, FmmPlan f, MixPlan mp) {
   const int s = mp.s, hs = s / kKB;
   const int a = mp.near[(long long)b * mp.Lmax + i];
   const int j0 = f.tj0[b], j1 = f.tj1[b];
+  const int P = f.L[2];  // source leaf a holds poles [a s - P, a s + s - P)
   unsigned char* tile = mp.Cp + ((size_t)(mp.noff[b] + i) * hs + h) * tile_C_bytes(s);
   const uint32_t plane = (uint32_t)s * kKB * 2;
   for (int it = threadIdx.x; it < s * (kKB / 8); it += blockDim.x) {
@@ -415,8 +427,8 @@ __global__ void k_mix_pack_C(Eig e, FmmPlan f, MixPlan mp) {
       const double dO = e.dorg[j], tj = e.tau[j], inv = e.inv[j];
 #pragma unroll
       for (int c = 0; c < 8; c++) {
-        int t = a * s + h * kKB + ch * 8 + c;
-        v[c] = t < k ? e.zhat[t] * inv * rcp64((e.dk[t] - dO) - tj) : 0.0;
+        const int t = a * s + h * kKB + ch * 8 + c - P;
+        v[c] = (t >= 0 && t < k) ? e.zhat[t] * inv * rcp64((e.dk[t] - dO) - tj) : 0.0;
       }
     } else {
 #pragma unroll
@@ -578,6 +590,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
   J.k = e.kp[0];
   J.Ls = f.L[0];
   J.Lt = f.L[1];
+  if (STAGE == MS_OUT) {  // heaviest target leaves first
+    if ((int)blockIdx.y >= J.Lt) return;
+    J.job = mp.order[blockIdx.y];
+  }
   // inactive jobs leave before any barrier or tensor-memory use (uniform per CTA)
   if (STAGE == MS_P2M && 4 * J.job >= J.Ls) return;
   if (STAGE == MS_M2L && J.job * (kTM / kMixP) >= J.Lt) return;

@@ -312,30 +312,67 @@ __device__ __forceinline__ double box_coord(double off, double r) {
   return fmin(1.0, fmax(-1.0, off / r));
 }
 
-// Leaves and boxes.  Sources: leaf a = poles [a s, a s + s).  Targets: see FmmPlan.
-// Dense mode: one source leaf with every pole, one target leaf with every root.
+// Leaves and boxes.  The largest poles of a solve may stand far above the rest (the
+// large eigenvalues that earlier updates added); a leaf holding them and ordinary poles
+// would reach over the whole spectrum and be near every target.  So the partition is
+// shifted to start a leaf at that group: with g the first pole above a gap wider than
+// half the span of the top s + 1 poles (at most kMaxTop poles above it; g = k when
+// there is none), source leaf a holds the sorted poles [a s - P, a s + s - P) with
+// P = (-g) mod s, and target leaf b < Lt - 1 the roots [b s - Pt, b s + s - Pt) that lie
+// between poles, with Pt = (-gt) mod s for gt the root in the gap (g - 1 when rho > 0,
+// g when rho < 0), so that the root in the gap and the roots above it share a leaf.  The
+// last target leaf holds the root beyond all poles.  Dense mode: one source leaf with
+// every pole, one target leaf with every root.
+constexpr int kMaxTop = 16;
+
+__device__ int top_group(const double* __restrict__ dk, int k, int s) {
+  if (k < 2 * s + 2) return k;
+  const double span = dk[k - 1] - dk[k - 1 - s];
+  double gmax = -1.0;
+  int g = k;
+  for (int j = k - 2; j >= k - 1 - s; j--) {
+    const double gap = dk[j + 1] - dk[j];
+    if (gap > gmax) { gmax = gap; g = j + 1; }
+  }
+  return (gmax > 0.5 * span && k - g <= kMaxTop) ? g : k;
+}
+
 __global__ void k_fmm_boxes(Eig e, FmmPlan f, int dense) {
   const int k = e.kp[0];
   const double rho = e.rhop[0];
-  int Ls, Lt;
+  const int rlo = rho > 0.0 ? 0 : 1, rhi = rho > 0.0 ? k - 1 : k;  // roots between poles
+  int Ls, Lt, P = 0, Pt = 0;
   if (k == 0) { Ls = 0; Lt = 0; }
   else if (dense) { Ls = 1; Lt = 1; }
-  else { Ls = (k + f.s - 1) / f.s; Lt = Ls + 1; }
-  if (blockIdx.x == 0 && threadIdx.x == 0) { f.L[0] = Ls; f.L[1] = Lt; }
+  else {
+    const int g = top_group(e.dk, k, f.s);
+    if (g < k) {
+      const int gt = rho > 0.0 ? g - 1 : g;
+      P = (f.s - g % f.s) % f.s;
+      Pt = (f.s - gt % f.s) % f.s;
+    }
+    Ls = (k + P + f.s - 1) / f.s;
+    Lt = (rhi > rlo ? (rhi - 1 + Pt) / f.s + 1 : 1) + 1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    f.L[0] = Ls;
+    f.L[1] = Lt;
+    f.L[2] = P;
+    f.L[3] = Pt;
+  }
   const int s = dense ? max(k, 1) : f.s;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < Lt; a += gridDim.x * blockDim.x) {
     if (a < Ls) {
-      int t0 = a * s, t1 = min(k, t0 + s) - 1;
-      double lo = e.dk[t0], hi = e.dk[t1];
+      const int t0 = max(0, a * s - P), t1 = min(k, a * s + s - P) - 1;
+      const double lo = e.dk[t0], hi = e.dk[t1];
       f.sbox_c[a] = 0.5 * (lo + hi);
       f.sbox_r[a] = box_radius(lo, hi);
     }
     int j0, j1;
     if (dense) { j0 = 0; j1 = k; }
-    else if (a < Ls) {
-      int lo = rho > 0.0 ? 0 : 1, hi = rho > 0.0 ? k - 1 : k;
-      j0 = max(a * s, lo);
-      j1 = min(a * s + s, hi);
+    else if (a < Lt - 1) {
+      j0 = max(a * s - Pt, rlo);
+      j1 = min(a * s + s - Pt, rhi);
       if (j1 < j0) j1 = j0;
     } else {
       j0 = rho > 0.0 ? k - 1 : 0;
@@ -354,7 +391,7 @@ __global__ void k_fmm_boxes(Eig e, FmmPlan f, int dense) {
   }
 }
 
-// Near list of target leaf b: the source leaves b-1..b+1 (for b < Ls) and every source
+// Near list of target leaf b: the source leaves b-1..b+1 (for b < Lt - 1) and every source
 // leaf a not admissible with b, i.e. with |c_a - c_b| - r_a - r_b < max(r_a, r_b).
 // Everything else is far field.
 __global__ void k_fmm_near(Eig e, FmmPlan f, int dense) {
@@ -366,7 +403,7 @@ __global__ void k_fmm_near(Eig e, FmmPlan f, int dense) {
     const bool has = f.tj1[b] > f.tj0[b];
     const double cb = f.tbox_c[b], rb = f.tbox_r[b];
     for (int a = 0; a < Ls; a++) {
-      bool nr = (b < Ls && a >= b - 1 && a <= b + 1);
+      bool nr = (b < Lt - 1 && a >= b - 1 && a <= b + 1);
       if (!nr && has) {
         double ca = f.sbox_c[a], ra = f.sbox_r[a];
         double gap = fabs(ca - cb) - ra - rb;
@@ -424,14 +461,14 @@ __device__ void cheb_tables(int p, double* st, double* sw) {
 __global__ void k_fmm_S(Eig e, FmmPlan f) {
   __shared__ double st[32], sw[32];
   cheb_tables(f.p, st, sw);
-  const int k = e.kp[0], L = f.L[0], p = f.p, s = f.s;
+  const int k = e.kp[0], L = f.L[0], p = f.p, s = f.s, P = f.L[2];
   const long long total = (long long)L * s;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
        x += (long long)gridDim.x * blockDim.x) {
     const int a = (int)(x / s), tl = (int)(x - (long long)a * s);
-    const int t = a * s + tl;
+    const int t = a * s + tl - P;
     double* col = f.S + (size_t)a * s * p + tl;
-    if (t < k) {
+    if (t >= 0 && t < k) {
       double u[32];
       lagrange_all(p, box_coord(e.dk[t] - f.sbox_c[a], f.sbox_r[a]), st, sw, u);
       const double zt = e.zhat[t];
@@ -524,6 +561,7 @@ __global__ void __launch_bounds__(128) k_gemm_f64(Eig e, FmmPlan f, int rows,
   const int Ls = f.L[0], Lt = f.L[1];
   const int p = f.p;
   const int s = dense ? max(k, 1) : f.s;
+  const int P = dense ? 0 : f.L[2];  // K positions g are poles g - P (leaf offset)
   const int leaf = blockIdx.y;
   if (leaf >= (STAGE == ST_P2M ? Ls : Lt)) return;
   const int r0 = blockIdx.x * BM;
@@ -547,27 +585,28 @@ __global__ void __launch_bounds__(128) k_gemm_f64(Eig e, FmmPlan f, int rows,
   else nseg = dense ? 2 : 1 + f.nnear[leaf];
   for (int sg = 0; sg < nseg; sg++) {
     int g0, g1;
-    if (STAGE == ST_P2M) { g0 = leaf * f.s; g1 = min(k, g0 + f.s); }
+    if (STAGE == ST_P2M) { g0 = leaf * f.s; g1 = min(k + P, g0 + f.s); }
     else if (STAGE == ST_M2L) { g0 = 0; g1 = Ls * p; }
     else if (dense) { g0 = 0; g1 = (sg == 0) ? 0 : k; }
     else if (sg == 0) { g0 = 0; g1 = p; }
     else {
       int a = f.near[(long long)leaf * f.Lmax + sg - 1];
       g0 = a * f.s;
-      g1 = min(k, g0 + f.s);
+      g1 = min(k + P, g0 + f.s);
     }
+    const bool poles = STAGE == ST_P2M || (STAGE == ST_OUT && sg > 0);
     for (int kb = g0; kb < g1; kb += BK) {
       // A tile: BK columns x BM rows
       for (int x = tid; x < BK * BM; x += 128) {
         int kk = x / BM, r = x - kk * BM;
         int g = kb + kk;
         double v = 0.0;
-        if (g < g1 && r0 + r < rows) {
+        if (g < g1 && r0 + r < rows && !(poles && g < P)) {
           const double* col;
-          if (STAGE == ST_P2M) col = Xs + (long long)g * ldxs;
+          if (STAGE == ST_P2M) col = Xs + (long long)(g - P) * ldxs;
           else if (STAGE == ST_M2L) col = f.Phi + (long long)g * f.ldphi;
           else col = (sg == 0) ? f.Psi + (long long)(leaf * p + g) * f.ldphi
-                               : Xs + (long long)g * ldxs;
+                               : Xs + (long long)(g - P) * ldxs;
           v = col[r0 + r];
         }
         As[kk][r] = v;
@@ -585,10 +624,10 @@ __global__ void __launch_bounds__(128) k_gemm_f64(Eig e, FmmPlan f, int rows,
             v = f.T[(long long)g + (long long)(leaf * p + cc) * ((long long)f.Lmax * p)];
           } else if (sg == 0) {
             v = f.Lop[(long long)leaf * f.s * p + (long long)cc * p + g];
-          } else {
-            int j = j0 + cc;
-            double del = (e.dk[g] - e.dorg[j]) - e.tau[j];
-            v = e.zhat[g] * e.inv[j] * rcp64(del);
+          } else if (g >= P) {
+            const int j = j0 + cc, t = g - P;
+            double del = (e.dk[t] - e.dorg[j]) - e.tau[j];
+            v = e.zhat[t] * e.inv[j] * rcp64(del);
           }
         }
         Bs[kk][c] = v;
@@ -643,7 +682,7 @@ __global__ void k_flop_count(Eig e, FmmPlan f, int rows, int dense, double* acc)
     acc[2] += 2.0 * R * (double)k * (double)k;
     return;
   }
-  const int Ls = f.L[0], Lt = f.L[1], p = f.p, s = f.s;
+  const int Ls = f.L[0], Lt = f.L[1], p = f.p, s = f.s, P = f.L[2];
   double p2m = 2.0 * R * (double)k * p, m2l = 0.0, out = 0.0;
   for (int b = 0; b < Lt; b++) {
     int nb = f.tj1[b] - f.tj0[b];
@@ -651,7 +690,7 @@ __global__ void k_flop_count(Eig e, FmmPlan f, int rows, int dense, double* acc)
     int near_src = 0;
     for (int i = 0; i < f.nnear[b]; i++) {
       int a = f.near[(long long)b * f.Lmax + i];
-      near_src += min(k, a * s + s) - a * s;
+      near_src += min(k, a * s + s - P) - max(0, a * s - P);
     }
     m2l += 2.0 * R * (double)p * p * (double)(Ls - f.nnear[b]);
     out += 2.0 * R * (double)nb * (double)(p + near_src);

@@ -852,36 +852,61 @@ struct FarSums {
   }
 };
 
-// All poles summed by a whole block (the extreme root, whose bracket reaches far past
-// the poles, when the far-field form serves the others).  Every thread calls it.
-struct BlockSums {
+// The sums of one root by a whole block, for a root iterated by warp 0 alone (the
+// block's other warps only help evaluate): warp 0 posts (o, tau, jsplit) and meets the
+// helpers at named barrier 1; every warp adds its share of the poles into part[4][32];
+// at barrier 2 warp 0 collects them.  The helpers leave when warp 0 posts cmd = 0.
+struct LedSums {
   const double* dc;
   const double* z2c;
   int k;
-  double* red;  // shared, 4 x 32
-  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
+  double* part;  // shared, 4 x 32
+  double* s_tau;
+  int* s_o;
+  int* s_js;
+  int* s_cmd;
+  __device__ static void bar(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"((int)blockDim.x) : "memory");
+  }
+  __device__ void partial(int o, double tau, int jsplit) const {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const double dO = dc[o];
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-      double del = (dc[i] - dO) - tau;
-      double rc = rcp64(del);
-      double t = z2c[i] * rc;
-      double dt = t * rc;
+      const double del = (dc[i] - dO) - tau;
+      const double rc = rcp64(del);
+      const double t = z2c[i] * rc;
+      const double dt = t * rc;
       if (i <= jsplit) { v[0] += t; v[1] += dt; }
       else { v[2] += t; v[3] += dt; }
     }
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       v[q] = warp_sum(v[q]);
-      if (lane == 0) red[q * 32 + w] = v[q];
+      if ((threadIdx.x & 31) == 0) part[q * 32 + w] = v[q];
     }
-    __syncthreads();
+  }
+  // warp 0 only
+  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
+    if (lane == 0) { *s_o = o; *s_tau = tau; *s_js = jsplit; *s_cmd = 1; }
+    bar(1);
+    partial(o, tau, jsplit);
+    bar(2);
+    const int nw = blockDim.x >> 5;
+    double v[4];
 #pragma unroll
-    for (int q = 0; q < 4; q++) v[q] = warp_sum(lane < nw ? red[q * 32 + lane] : 0.0);
-    __syncthreads();
+    for (int q = 0; q < 4; q++) v[q] = warp_sum(lane < nw ? part[q * 32 + lane] : 0.0);
     SecSums s = {v[0], v[1], v[2], v[3], v[2] - v[0]};
     return s;
+  }
+  // warps 1 ..
+  __device__ void help() const {
+    while (true) {
+      bar(1);
+      if (*s_cmd == 0) return;
+      partial(*s_o, *s_tau, *s_js);
+      bar(2);
+    }
   }
 };
 
@@ -1025,15 +1050,24 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
     else if (s <= kSqMaxWide) j = (s - 1 < first) ? s - 1 : -1;
     else j = (last + s - kSqMaxWide <= k - 2) ? last + s - kSqMaxWide : -1;
     if (j < 0) return;
-    __shared__ double red[4 * 32];
-    const BlockSums bs = {dc, z2c, k, red};
-    int o;
-    double t;
-    const int bad = secular_root(bs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
-    if (threadIdx.x == 0) {
-      if (bad) latch(status, SVDUP_ENOCONV);
-      if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
-      store_root(j, o, t, k, rho, dk, orgc, tauc, org, tau, dorg);
+    // warp 0 iterates, the whole block evaluates the sums
+    __shared__ double part[4 * 32];
+    __shared__ double s_tau;
+    __shared__ int s_o, s_js, s_cmd;
+    const LedSums ls = {dc, z2c, k, part, &s_tau, &s_o, &s_js, &s_cmd};
+    if (threadIdx.x < 32) {
+      int o;
+      double t;
+      const int bad = secular_root(ls, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
+      if (lane == 0) s_cmd = 0;
+      LedSums::bar(1);  // releases the helpers
+      if (lane == 0) {
+        if (bad) latch(status, SVDUP_ENOCONV);
+        if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
+        store_root(j, o, t, k, rho, dk, orgc, tauc, org, tau, dorg);
+      }
+    } else {
+      ls.help();
     }
     return;
   }
