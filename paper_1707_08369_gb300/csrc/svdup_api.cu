@@ -66,6 +66,9 @@ struct svdup_ctx {
   // product-path choices (set by svdup_autotune; defaults below): index 0 FP64, 1 mixed
   int dense_max[2];   // N <= dense_max: dense Cauchy product (no far field)
   int leaf128_min[2]; // N >= leaf128_min: leaves of 128 poles, else 64
+  // the right-hand problem of an update runs on `side`, beside the left-hand one
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_mid, ev_join;
 };
 
 namespace {
@@ -251,13 +254,15 @@ int set_device(svdup_ctx* h) {
 }
 
 // The per-update workspace.
+// Update workspace.  The left-hand (U) and right-hand (V) problems own their scratch
+// (ysort, the product's plan, W and Xs) so that they can run side by side.
 struct UpdateWs {
-  double *p, *q, *ab, *z2p, *z4p, *ysort, *zsec2, *zsec4, *ones, *g1, *g, *yv, *h1, *h, *sign,
-      *work;
+  double *p, *q, *ab, *z2p, *z4p, *ysortL, *ysortR, *zsec2, *zsec4, *ones, *g1, *g, *yv, *h1,
+      *h, *sign, *work;
   Eig E1, E2, E3, E4;
-  double *Xs, *W;
-  FmmPlan F;
-  MixPlan M;
+  double *XsL, *XsR, *WL, *WR;
+  FmmPlan FL, FR;
+  MixPlan ML, MR;
 };
 
 UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed) {
@@ -267,7 +272,8 @@ UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed
   u.ab = ar.take<double>(2);
   u.z2p = ar.take<double>(m);
   u.z4p = ar.take<double>(n);
-  u.ysort = ar.take<double>(n);
+  u.ysortL = ar.take<double>(m);
+  u.ysortR = ar.take<double>(n);
   u.zsec2 = ar.take<double>(m);
   u.zsec4 = ar.take<double>(n);
   u.ones = ar.take<double>(m);
@@ -282,11 +288,18 @@ UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed
   u.E2 = make_eig(ar, m);
   u.E3 = make_eig(ar, n);
   u.E4 = make_eig(ar, n);
-  u.Xs = mixed ? nullptr : ar.take<double>((size_t)n * n);
-  u.W = ar.take<double>((size_t)n * n);
-  u.F = make_plan(ar, n, n, eps, leaf, mixed);
-  if (mixed) u.M = make_mix(ar, n, u.F);
-  else memset(&u.M, 0, sizeof(u.M));
+  u.XsL = mixed ? nullptr : ar.take<double>((size_t)m * m);
+  u.XsR = mixed ? nullptr : ar.take<double>((size_t)n * n);
+  u.WL = ar.take<double>((size_t)m * m);
+  u.WR = ar.take<double>((size_t)n * n);
+  u.FL = make_plan(ar, m, m, eps, leaf, mixed);
+  u.FR = make_plan(ar, n, n, eps, leaf, mixed);
+  memset(&u.ML, 0, sizeof(u.ML));
+  memset(&u.MR, 0, sizeof(u.MR));
+  if (mixed) {
+    u.ML = make_mix(ar, m, u.FL);
+    u.MR = make_mix(ar, n, u.FR);
+  }
   return u;
 }
 
@@ -332,42 +345,43 @@ void stage_end(svdup_ctx* h) {
 // (fused with a transposed product when the next solve needs its z).
 // pairs: Loewner's zhat in double-float arithmetic (svdup_dfsum.cu), for solves whose
 // zhat feeds vectors only (never the z of another solve) in the mixed mode
-void queue_solve(svdup_ctx* h, Eig e, bool pairs = false) {
-  launch_deflate(h->stream, e, h->status);
-  launch_secular(h->stream, e, h->status, h->maxit);
-  launch_merge(h->stream, e);
-  if (pairs) launch_loewner_df(h->stream, e);
-  else launch_loewner(h->stream, e);
+void queue_solve(svdup_ctx* h, cudaStream_t st, Eig e, bool pairs = false) {
+  launch_deflate(st, e, h->status);
+  launch_secular(st, e, h->status, h->maxit);
+  launch_merge(st, e);
+  if (pairs) launch_loewner_df(st, e);
+  else launch_loewner(st, e);
 }
 
 // Y[:, out(q)] = (X Q)[:, q] for the solve e (X rows x N, modified in place by the
-// deflation rotations).  Xs is a rows x N scratch.
-void queue_product(svdup_ctx* h, Eig e, FmmPlan f, int rows, double* X, long long ldx,
+// deflation rotations).  Xs is a rows x N scratch.  The stage timers record on the
+// handle's stream: with timing on, every product runs there (st == h->stream).
+void queue_product(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, double* X, long long ldx,
                    double* Xs, OutMap om, int mode) {
   int dense = use_dense(h, e.N, mode) ? 1 : 0;
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rot, false);
-  launch_gather_columns(h->stream, e, X, ldx, rows, Xs, rows, om);
+  launch_rotate_columns(st, e, X, ldx, rows, f.rot, false);
+  launch_gather_columns(st, e, X, ldx, rows, Xs, rows, om);
   stage_end(h);
   stage_begin(h, SVDUP_STAGE_SETUP);
-  launch_fmm_setup(h->stream, e, f, dense);
+  launch_fmm_setup(st, e, f, dense);
   stage_end(h);
   if (!dense) {
     stage_begin(h, SVDUP_STAGE_P2M);
-    launch_product_f64_stage(h->stream, 0, e, f, rows, Xs, rows, om, dense);
+    launch_product_f64_stage(st, 0, e, f, rows, Xs, rows, om, dense);
     stage_end(h);
     stage_begin(h, SVDUP_STAGE_M2L);
-    launch_product_f64_stage(h->stream, 1, e, f, rows, Xs, rows, om, dense);
+    launch_product_f64_stage(st, 1, e, f, rows, Xs, rows, om, dense);
     stage_end(h);
   }
   stage_begin(h, SVDUP_STAGE_OUT);
-  launch_product_f64_stage(h->stream, 2, e, f, rows, Xs, rows, om, dense);
+  launch_product_f64_stage(st, 2, e, f, rows, Xs, rows, om, dense);
   stage_end(h);
-  if (h->timing) launch_flop_count(h->stream, e, f, rows, dense, h->flops_dev);
+  if (h->timing) launch_flop_count(st, e, f, rows, dense, h->flops_dev);
 }
 
 // The same product in split BF16 on the tensor cores (svdup_mixed.cu).
-void queue_product_mixed(svdup_ctx* h, Eig e, FmmPlan f, MixPlan mp, int rows, double* X,
+void queue_product_mixed(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, double* X,
                          long long ldx, OutMap om, int mode) {
   int dense = use_dense(h, e.N, mode) ? 1 : 0;
   mp.rows = rows;
@@ -375,27 +389,27 @@ void queue_product_mixed(svdup_ctx* h, Eig e, FmmPlan f, MixPlan mp, int rows, d
   // the set-up (leaves, near lists, operator tiles) depends on the solve alone; it
   // comes first because the gather places X's columns by the leaf offset it finds
   stage_begin(h, SVDUP_STAGE_SETUP);
-  launch_fmm_setup(h->stream, e, f, 0);
-  launch_mix_setup(h->stream, e, f, mp, dense);
+  launch_fmm_setup(st, e, f, 0);
+  launch_mix_setup(st, e, f, mp, dense);
   stage_end(h);
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(h->stream, e, X, ldx, rows, f.rot, true);
-  launch_mix_gather(h->stream, e, X, ldx, rows, mp, om);
+  launch_rotate_columns(st, e, X, ldx, rows, f.rot, true);
+  launch_mix_gather(st, e, X, ldx, rows, mp, om);
   stage_end(h);
   if (!dense) {
     stage_begin(h, SVDUP_STAGE_P2M);
-    launch_mix_stage(h->stream, 0, e, f, mp, om, dense, h->status);
+    launch_mix_stage(st, 0, e, f, mp, om, dense, h->status);
     stage_end(h);
     stage_begin(h, SVDUP_STAGE_M2L);
-    launch_mix_stage(h->stream, 1, e, f, mp, om, dense, h->status);
+    launch_mix_stage(st, 1, e, f, mp, om, dense, h->status);
     stage_end(h);
   }
   stage_begin(h, SVDUP_STAGE_OUT);
-  launch_mix_stage(h->stream, 2, e, f, mp, om, dense, h->status);
+  launch_mix_stage(st, 2, e, f, mp, om, dense, h->status);
   stage_end(h);
   if (h->timing) {
-    launch_flop_count(h->stream, e, f, rows, dense, h->flops_dev);
-    launch_mix_flop_count(h->stream, e, f, mp, dense, h->flops_dev + 3);
+    launch_flop_count(st, e, f, rows, dense, h->flops_dev);
+    launch_mix_flop_count(st, e, f, mp, dense, h->flops_dev + 3);
   }
 }
 
@@ -403,12 +417,45 @@ void queue_product_mixed(svdup_ctx* h, Eig e, FmmPlan f, MixPlan mp, int rows, d
 // Batches: lane contexts share the parent's status word and counters but own a
 // stream and a workspace.
 // ---------------------------------------------------------------------------
+// The side stream and the three events of the two-stream update.
+int make_side(svdup_ctx* h) {
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->side = nullptr;
+    return SVDUP_ECUDA;
+  }
+  if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(h->side);
+    h->side = nullptr;
+    return SVDUP_ECUDA;
+  }
+  return SVDUP_OK;
+}
+
+void free_side(svdup_ctx* h) {
+  if (!h->side) return;
+  cudaStreamSynchronize(h->side);
+  cudaEventDestroy(h->ev_fork);
+  cudaEventDestroy(h->ev_mid);
+  cudaEventDestroy(h->ev_join);
+  cudaStreamDestroy(h->side);
+  h->side = nullptr;
+}
+
 svdup_ctx* lane_create(const svdup_ctx* parent) {
   svdup_ctx* l = (svdup_ctx*)calloc(1, sizeof(svdup_ctx));
   if (!l) return nullptr;
   l->device = parent->device;
   if (cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
+    free(l);
+    return nullptr;
+  }
+  if (make_side(l) != SVDUP_OK) {
+    cudaStreamDestroy(l->stream);
     free(l);
     return nullptr;
   }
@@ -426,6 +473,7 @@ svdup_ctx* lane_create(const svdup_ctx* parent) {
 void lane_destroy(svdup_ctx* l) {
   if (!l) return;
   cudaStreamSynchronize(l->stream);
+  free_side(l);
   if (l->ws) cudaFree(l->ws);
   cudaStreamDestroy(l->stream);
   free(l->recs);
@@ -612,8 +660,10 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
     free(h);
     return SVDUP_ENOMEM;
   }
-  if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess) {
+  if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess ||
+      make_side(h) != SVDUP_OK) {
     cudaFree(h->status);
+    cudaFree(h->flops_dev);
     free(h);
     return SVDUP_ECUDA;
   }
@@ -625,6 +675,7 @@ int svdup_destroy(svdup_t h) {
   if (!h) return SVDUP_EINVAL;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  free_side(h);
   if (h->ws) cudaFree(h->ws);
   cudaFree(h->status);
   cudaFree(h->flops_dev);
@@ -746,50 +797,69 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   stage_begin(h, SVDUP_STAGE_GEMV);
   launch_gemv_pq(st, m, n, U, ldu, V, ldv, a, b, u.p, u.q, u.ab);
   stage_end(h);
+  // The left-hand problem (E1, E2, U) runs on the handle's stream, the right-hand one
+  // (E3, E4, V) on the side stream; they meet once, where the sign pairing hands the
+  // left vectors' sums to the right.  With stage timing on, both run on one stream.
+  const bool side = !h->timing && h->side;
+  cudaStream_t sR = side ? h->side : st;
+  if (side) {
+    if (cudaEventRecord(h->ev_fork, st) != cudaSuccess ||
+        cudaStreamWaitEvent(sR, h->ev_fork, 0) != cudaSuccess)
+      return SVDUP_ECUDA;
+  }
   stage_begin(h, SVDUP_STAGE_SOLVE);
-  // STEPs 2, 4: first left solve; its transposed product gives the second left z
-  launch_fill_left(st, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
-  queue_solve(h, u.E1);
-  launch_apply_qt(st, u.E1, u.z2p, u.ysort, u.zsec2);
+  // STEPs 3, 6: first right solve; STEP 7: second right solve
+  launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
+  queue_solve(h, sR, u.E3);
+  launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4);
+  launch_fill_second(sR, u.E4, u.E3.lam, u.zsec4);
+  queue_solve(h, sR, u.E4, mixed);
+  launch_norms(sR, u.E4, nullptr, nullptr, mixed);
+  // STEPs 2, 4: first left solve; its transposed product gives the second left z;
   // STEP 5: second left solve
+  launch_fill_left(st, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
+  queue_solve(h, st, u.E1);
+  launch_apply_qt(st, u.E1, u.z2p, u.ysortL, u.zsec2);
   launch_fill_second(st, u.E2, u.E1.lam, u.zsec2);
-  queue_solve(h, u.E2, mixed);
+  queue_solve(h, st, u.E2, mixed);
   launch_norms(st, u.E2, nullptr, nullptr, mixed);
-  // STEPs 3, 6: first right solve
-  launch_fill_right(st, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
-  queue_solve(h, u.E3);
-  launch_apply_qt(st, u.E3, u.z4p, u.ysort, u.zsec4);
-  // STEP 7: second right solve
-  launch_fill_second(st, u.E4, u.E3.lam, u.zsec4);
-  queue_solve(h, u.E4, mixed);
-  launch_norms(st, u.E4, nullptr, nullptr, mixed);
   stage_end(h);
-  // sign pairing of right vectors with left vectors (before S is overwritten)
+  // sign pairing of right vectors with left vectors (before S is overwritten); in the
+  // mixed mode its sums run on FP32 pairs (only the signs are used)
   stage_begin(h, SVDUP_STAGE_SIGN);
   launch_fill_ones(st, m, u.ones);
-  // in the mixed mode the sign sums run on FP32 pairs (only the signs are used)
   launch_apply_q(st, u.E2, u.ones, u.work, u.g1, mixed);
   launch_apply_q(st, u.E1, u.g1, u.work, u.g, mixed);
   launch_sign_combine(st, m, n, S, u.p, u.q, u.g, u.yv);
-  launch_apply_qt(st, u.E3, u.yv, u.ysort, u.h1, mixed);
-  launch_apply_qt(st, u.E4, u.h1, u.ysort, u.h, mixed);
-  launch_sign_finish(st, m, n, u.h, u.sign);
+  if (side) {
+    if (cudaEventRecord(h->ev_mid, st) != cudaSuccess ||
+        cudaStreamWaitEvent(sR, h->ev_mid, 0) != cudaSuccess)
+      return SVDUP_ECUDA;
+  }
+  launch_apply_qt(sR, u.E3, u.yv, u.ysortR, u.h1, mixed);
+  launch_apply_qt(sR, u.E4, u.h1, u.ysortR, u.h, mixed);
+  launch_sign_finish(sR, m, n, u.h, u.sign);
   stage_end(h);
   // products: U -> W -> U (descending), V -> W -> V (descending, signed)
-  OutMap om1 = {u.W, (long long)m, m, 0, nullptr};
+  OutMap om1 = {u.WL, (long long)m, m, 0, nullptr};
   OutMap om2 = {U, (long long)ldu, m, 1, nullptr};
-  OutMap om3 = {u.W, (long long)n, n, 0, nullptr};
+  OutMap om3 = {u.WR, (long long)n, n, 0, nullptr};
   OutMap om4 = {V, (long long)ldv, n, 1, u.sign};
   if (mixed) {
-    queue_product_mixed(h, u.E1, u.F, u.M, m, U, ldu, om1, mode);
-    queue_product_mixed(h, u.E2, u.F, u.M, m, u.W, m, om2, mode);
-    queue_product_mixed(h, u.E3, u.F, u.M, n, V, ldv, om3, mode);
-    queue_product_mixed(h, u.E4, u.F, u.M, n, u.W, n, om4, mode);
+    queue_product_mixed(h, st, u.E1, u.FL, u.ML, m, U, ldu, om1, mode);
+    queue_product_mixed(h, st, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
+    queue_product_mixed(h, sR, u.E3, u.FR, u.MR, n, V, ldv, om3, mode);
+    queue_product_mixed(h, sR, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
   } else {
-    queue_product(h, u.E1, u.F, m, U, ldu, u.Xs, om1, mode);
-    queue_product(h, u.E2, u.F, m, u.W, m, u.Xs, om2, mode);
-    queue_product(h, u.E3, u.F, n, V, ldv, u.Xs, om3, mode);
-    queue_product(h, u.E4, u.F, n, u.W, n, u.Xs, om4, mode);
+    queue_product(h, st, u.E1, u.FL, m, U, ldu, u.XsL, om1, mode);
+    queue_product(h, st, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
+    queue_product(h, sR, u.E3, u.FR, n, V, ldv, u.XsR, om3, mode);
+    queue_product(h, sR, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
+  }
+  if (side) {
+    if (cudaEventRecord(h->ev_join, sR) != cudaSuccess ||
+        cudaStreamWaitEvent(st, h->ev_join, 0) != cudaSuccess)
+      return SVDUP_ECUDA;
   }
   // STEP 8
   launch_sqrt_desc(st, m, u.E2.lam, S, h->status);
@@ -865,7 +935,7 @@ int svdup_rank_one_eig(svdup_t h, int N, const double* d, const double* z, doubl
   if (cudaMemcpyAsync(rhod, &rho, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return SVDUP_ECUDA;
   launch_fill_generic(st, e, d, z, rhod, h->status);
-  queue_solve(h, e);
+  queue_solve(h, st, e);
   launch_norms(st, e, nullptr, nullptr);
   cudaMemcpyAsync(k, e.kp, sizeof(int), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(idx, e.idx, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
@@ -935,11 +1005,11 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
       cudaSuccess)
     return SVDUP_ECUDA;
   launch_fill_generic(st, e, d, z, rhod, h->status);
-  queue_solve(h, e, mixed);
+  queue_solve(h, st, e, mixed);
   launch_norms(st, e, nullptr, nullptr, mixed);
   OutMap om = {Y, (long long)ldy, N, 0, nullptr};
-  if (mixed) queue_product_mixed(h, e, f, mp, rows, Xw, rows, om, mode);
-  else queue_product(h, e, f, rows, Xw, rows, Xs, om, mode);
+  if (mixed) queue_product_mixed(h, st, e, f, mp, rows, Xw, rows, om, mode);
+  else queue_product(h, st, e, f, rows, Xw, rows, Xs, om, mode);
   cudaMemcpyAsync(lam, e.lam, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
   return check_launch();
 }

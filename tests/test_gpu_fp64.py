@@ -326,3 +326,21 @@ def test_long_deflation_chain(sv, hnd, orc, mode_name):
     G_g = Y_g[:, clus] @ Y_g[:, clus].T
     G_o = Y_o[:, clus] @ Y_o[:, clus].T
     assert np.abs(G_g - G_o).max() <= 10 * tol
+
+
+@pytest.mark.parametrize("mode_name", ["FP64", "MIXED_BF16X3"])
+def test_two_streams_match_one_stream(sv, hnd, mode_name):
+    """The left- and right-hand problems run on two streams; with stage timing on they
+    run on one.  Same kernels on the same data: the results are bit-identical."""
+    mode = getattr(sv, mode_name)
+    U, S, V, a, b = wl.loguniform_sq(1536, seed=wl.BASE_SEED + 91)
+    outs = []
+    for timing in (False, True):
+        hnd.timing(timing)
+        try:
+            Un, Sn, Vn = _run_update(sv, hnd, U, S, V, a, b, eps=1e-12, mode=mode)
+        finally:
+            hnd.timing(False)
+        outs.append((Un, Sn, Vn))
+    for x, y in zip(outs[0], outs[1]):
+        assert np.array_equal(x, y)
