@@ -177,6 +177,9 @@ struct MixPlan {
 constexpr int kMixP = 16;
 constexpr size_t kMixTileA = 3 * 128 * 64 * 2;  // A tile bytes (3 planes)
 
+// Streaming multiprocessors of the current device (cached per device; svdup_solve.cu).
+int device_sm_count();
+
 // Host-side launchers (defined in svdup_solve.cu / svdup_product.cu / svdup_mixed.cu).  Each queues
 // its kernels on `st` and adds to the launch counter.
 void launch_gemv_pq(cudaStream_t st, int m, int n, const double* U, long long ldu, const double* V,

@@ -33,6 +33,8 @@
 // SVDUP_ETIMEOUT and lets the CTA finish.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "svdup_internal.cuh"
@@ -578,6 +580,31 @@ constexpr int kEpiWarps = 8;
 constexpr int kUmmaThreads = (kEpiWarps + 2) * 32;
 constexpr uint32_t kTmemCols = 512;
 
+// Work items: (row tile rt, job).  Jobs per row tile: P2M one per 4 source leaves, M2L
+// one per 128 local-expansion columns (8 target leaves), OUT one per target leaf (in
+// descending near count).  Items run row-tile major, so the CTAs running at one time
+// share a few row tiles of X: the X tiles that neighbouring target leaves both read
+// stay in L2 between their uses.
+template <int STAGE>
+__device__ __forceinline__ int stage_jobs(const Job& J) {
+  if (STAGE == MS_P2M) return (J.Ls + 3) / 4;
+  if (STAGE == MS_M2L) return (J.Lt + kTM / kMixP - 1) / (kTM / kMixP);
+  return J.Lt;
+}
+
+template <int STAGE>
+__device__ __forceinline__ void set_item(Job& J, int x, int njobs, const FmmPlan& f,
+                                         const MixPlan& mp, int dense) {
+  J.rt = x / njobs;
+  const int jo = x - J.rt * njobs;
+  J.job = (STAGE == MS_OUT) ? mp.order[jo] : jo;
+  J.ntiles = job_tiles<STAGE>(J, f, mp, dense);
+}
+
+// Persistent: one CTA per SM loops over the work items (x = blockIdx.x, += gridDim.x).
+// The producer and MMA warps run ahead into the next item while the epilogue warps
+// finish the previous one; every role counts the K tiles it has handled (g) across
+// items, which fixes the ring slot (g & 1) and the barrier phase (g >> 1) & 1.
 template <int STAGE, int W>
 __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixPlan mp, OutMap om,
                                                           int dense, int* status) {
@@ -585,20 +612,11 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
   constexpr int NCH = QW / 16;     // 16-column chunks per epilogue warp
   extern __shared__ unsigned char smem_raw[];
   Job J;
-  J.rt = blockIdx.x;
-  J.job = blockIdx.y;
   J.k = e.kp[0];
   J.Ls = f.L[0];
   J.Lt = f.L[1];
-  if (STAGE == MS_OUT) {  // heaviest target leaves first
-    if ((int)blockIdx.y >= J.Lt) return;
-    J.job = mp.order[blockIdx.y];
-  }
-  // inactive jobs leave before any barrier or tensor-memory use (uniform per CTA)
-  if (STAGE == MS_P2M && 4 * J.job >= J.Ls) return;
-  if (STAGE == MS_M2L && J.job * (kTM / kMixP) >= J.Lt) return;
-  if (STAGE == MS_OUT && J.job >= J.Lt) return;
-  J.ntiles = job_tiles<STAGE>(J, f, mp, dense);
+  const int njobs = stage_jobs<STAGE>(J);
+  const int nitems = mp.rt * njobs;
 
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_base = smem_u32(sm);
@@ -611,6 +629,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
   auto bar_tfull = [&](int i) { return bar0 + 8u * (uint32_t)(4 + i); };
   auto bar_tempty = [&](int i) { return bar0 + 8u * (uint32_t)(6 + i); };
   const uint32_t bar_done = bar0 + 8u * 8u;
+  if ((int)blockIdx.x >= nitems) return;  // uniform per CTA, before any barrier or TMEM use
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kEpiWarps + 1) {
@@ -635,95 +654,106 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
 
   if (warp == kEpiWarps) {
     if (lane == 0) {  // producer: bulk copies into the shared-memory ring
-      for (int i = 0; i < J.ntiles; i++) {
-        const int st = i & 1;
-        const uint32_t u = (uint32_t)(i >> 1);
-        if (i >= 2 && !mbar_wait(bar_empty(st), (u & 1u) ^ 1u, abort_flag)) {
-          *abort_flag = 1;
-          latch(status, SVDUP_ETIMEOUT);
-          break;
+      uint32_t g = 0;
+      bool alive = true;
+      for (int x = blockIdx.x; x < nitems && alive; x += gridDim.x) {
+        set_item<STAGE>(J, x, njobs, f, mp, dense);
+        for (int i = 0; i < J.ntiles; i++, g++) {
+          const int st = g & 1;
+          if (g >= 2 && !mbar_wait(bar_empty(st), ((g >> 1) & 1u) ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            latch(status, SVDUP_ETIMEOUT);
+            alive = false;
+            break;
+          }
+          KTile t = ktile<STAGE>(i, J, f, mp, dense);
+          const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kTileA;
+          mbar_expect_tx(bar_full(st), t.abytes + t.bbytes);
+          bulk_g2s(sa, t.a, t.abytes, bar_full(st));
+          bulk_g2s(sb, t.b, t.bbytes, bar_full(st));
         }
-        KTile t = ktile<STAGE>(i, J, f, mp, dense);
-        const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kTileA;
-        mbar_expect_tx(bar_full(st), t.abytes + t.bbytes);
-        bulk_g2s(sa, t.a, t.abytes, bar_full(st));
-        bulk_g2s(sb, t.b, t.bbytes, bar_full(st));
       }
     }
   } else if (warp == kEpiWarps + 1) {
     if (lane == 0) {  // MMA issuer
-      for (int i = 0; i < J.ntiles; i++) {
-        const int st = i & 1;
-        const uint32_t u = (uint32_t)(i >> 1);
-        if (!mbar_wait(bar_full(st), u & 1u, abort_flag) ||
-            (i >= 2 && !mbar_wait(bar_tempty(st), (u & 1u) ^ 1u, abort_flag))) {
-          *abort_flag = 1;
-          latch(status, SVDUP_ETIMEOUT);
-          break;
-        }
-        tc_fence_after();
-        KTile t = ktile<STAGE>(i, J, f, mp, dense);
-        const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kTileA;
-        const uint32_t dA = tmem + (uint32_t)st * 256u + (uint32_t)t.col;
-        const uint32_t dB = dA + 128u;
-        const uint32_t idesc = idesc_bf16(kTM, t.n);
-        const uint32_t sbo = (uint32_t)t.kb * 16;
-        for (int ks = 0; ks < t.kb / 16; ks++) {
-#pragma unroll
-          for (int q = 0; q < 6; q++) {
-            uint64_t ad = sdesc(sa + kPairA[q] * t.aplane + ks * 256, 128, sbo);
-            uint64_t bd = sdesc(sb + kPairB[q] * t.bplane + ks * 256, 128, sbo);
-            if (q == 0) umma_bf16(dA, ad, bd, idesc, ks > 0 ? 1u : 0u);
-            else umma_bf16(dB, ad, bd, idesc, (ks > 0 || q > 1) ? 1u : 0u);
+      uint32_t g = 0;
+      bool alive = true;
+      for (int x = blockIdx.x; x < nitems && alive; x += gridDim.x) {
+        set_item<STAGE>(J, x, njobs, f, mp, dense);
+        for (int i = 0; i < J.ntiles; i++, g++) {
+          const int st = g & 1;
+          const uint32_t ph = (g >> 1) & 1u;
+          if (!mbar_wait(bar_full(st), ph, abort_flag) ||
+              (g >= 2 && !mbar_wait(bar_tempty(st), ph ^ 1u, abort_flag))) {
+            *abort_flag = 1;
+            latch(status, SVDUP_ETIMEOUT);
+            alive = false;
+            break;
           }
+          tc_fence_after();
+          KTile t = ktile<STAGE>(i, J, f, mp, dense);
+          const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kTileA;
+          const uint32_t dA = tmem + (uint32_t)st * 256u + (uint32_t)t.col;
+          const uint32_t dB = dA + 128u;
+          const uint32_t idesc = idesc_bf16(kTM, t.n);
+          const uint32_t sbo = (uint32_t)t.kb * 16;
+          for (int ks = 0; ks < t.kb / 16; ks++) {
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+              uint64_t ad = sdesc(sa + kPairA[q] * t.aplane + ks * 256, 128, sbo);
+              uint64_t bd = sdesc(sb + kPairB[q] * t.bplane + ks * 256, 128, sbo);
+              if (q == 0) umma_bf16(dA, ad, bd, idesc, ks > 0 ? 1u : 0u);
+              else umma_bf16(dB, ad, bd, idesc, (ks > 0 || q > 1) ? 1u : 0u);
+            }
+          }
+          umma_commit(bar_empty(st));  // frees the ring stage once these MMAs have read it
+          umma_commit(bar_tfull(st));  // hands the accumulators to the epilogue
         }
-        umma_commit(bar_empty(st));  // frees the ring stage once these MMAs have read it
-        umma_commit(bar_tfull(st));  // hands the accumulators to the epilogue
       }
       // every MMA this thread issued has completed before tensor memory is released
       umma_commit(bar_done);
       if (!mbar_wait_timed(bar_done, 0)) latch(status, SVDUP_ETIMEOUT);
     }
   } else {
-    // epilogue: drain every K tile into (hi, lo) pairs, then write the output
+    // epilogue: drain every K tile into (hi, lo) pairs, then write the item's output
     const int quad = warp & 3, qc = warp >> 2;
     const int r = quad * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-    float hi[QW], lo[QW];
-#pragma unroll
-    for (int c = 0; c < QW; c++) { hi[c] = 0.0f; lo[c] = 0.0f; }
+    uint32_t g = 0;
     bool ok = true;
-    for (int i = 0; i < J.ntiles && ok; i++) {
-      const int st = i & 1;
-      if (!mbar_wait(bar_tfull(st), (uint32_t)(i >> 1) & 1u, abort_flag)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      KTile t = ktile<STAGE>(i, J, f, mp, dense);
+    for (int x = blockIdx.x; x < nitems && ok; x += gridDim.x) {
+      set_item<STAGE>(J, x, njobs, f, mp, dense);
+      float hi[QW], lo[QW];
 #pragma unroll
-      for (int ch = 0; ch < NCH; ch++) {
-        const int col = qc * QW + ch * 16;
-        if (col >= t.col && col < t.col + t.n) {
+      for (int c = 0; c < QW; c++) { hi[c] = 0.0f; lo[c] = 0.0f; }
+      for (int i = 0; i < J.ntiles; i++, g++) {
+        const int st = g & 1;
+        if (!mbar_wait(bar_tfull(st), (g >> 1) & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        KTile t = ktile<STAGE>(i, J, f, mp, dense);
 #pragma unroll
-          for (int part = 0; part < 2; part++) {  // hi.hi region, then the cross region
-            float v[16];
-            tmem_ld16(lane_base + (uint32_t)st * 256u + (uint32_t)part * 128u + (uint32_t)col, v);
+        for (int ch = 0; ch < NCH; ch++) {
+          const int col = qc * QW + ch * 16;
+          if (col >= t.col && col < t.col + t.n) {
 #pragma unroll
-            for (int c = 0; c < 16; c++) {
-              if (part == 0) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], v[c]);
-              else lo[ch * 16 + c] += v[c];  // cross terms: 2^-8 of hi.hi and below
+            for (int part = 0; part < 2; part++) {  // hi.hi region, then the cross region
+              float v[16];
+              tmem_ld16(lane_base + (uint32_t)st * 256u + (uint32_t)part * 128u + (uint32_t)col, v);
+#pragma unroll
+              for (int c = 0; c < 16; c++) {
+                if (part == 0) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], v[c]);
+                else lo[ch * 16 + c] += v[c];  // cross terms: 2^-8 of hi.hi and below
+              }
             }
           }
         }
+        tc_fence_before();
+        mbar_arrive(bar_tempty(st));
       }
-      tc_fence_before();
-      mbar_arrive(bar_tempty(st));
-    }
-    if (!ok) {
-      *abort_flag = 1;
-      latch(status, SVDUP_ETIMEOUT);
-    } else if (!*abort_flag) {
+      if (!ok || *abort_flag) break;
       if (STAGE == MS_P2M) {
         // half qc = leaves 4 job + 2 qc + {0, 1}: columns 32 qc .. of the Phi tile
         unsigned char* tile = mp.Phip + ((size_t)J.rt * mp.kphi + J.job) * kTileA;
@@ -746,31 +776,29 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
             store_split8_ff(tile, kPlanePsi, cl_off(r, 8, kMixP), hi + u * 16 + 8, lo + u * 16 + 8);
           }
         }
-      }
-    }
-    if (STAGE == MS_OUT) {
-      // The operands carry 24 significant bits, so the output is rounded to FP32 (hi + lo)
-      // and widened exactly; the column scale is a sign (+-1), applied as one.  The tile
-      // is staged column-major in the (now idle) ring, then written as whole output
-      // columns: 128 consecutive rows per column, one warp per column.
-      float* stile = (float*)sm;  // [W][128]
-#pragma unroll
-      for (int c = 0; c < QW; c++) stile[(qc * QW + c) * kTM + r] = hi[c] + lo[c];
-      asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
-      if (ok && !*abort_flag) {
+      } else {
+        // The operands carry 24 significant bits, so the output is rounded to FP32
+        // (hi + lo) and widened exactly; the column scale is a sign (+-1), applied as
+        // one.  Each store of a warp covers 32 consecutive rows of one column.
         const int j0 = f.tj0[J.job], nb = f.tj1[J.job] - j0;
-        const long long row0 = (long long)J.rt * kTM;
-        for (int cc = warp; cc < nb; cc += kEpiWarps) {
-          const int q = e.rank_root[j0 + cc];
-          const bool flip = om.colscale && om.colscale[q] < 0.0;
-          double* ycol = om.Y + out_col_m(om, q) * om.ldy + row0;
-          for (int rr = lane; rr < kTM; rr += 32)
-            if (row0 + rr < mp.rows) {
-              const float v = stile[cc * kTM + rr];
-              ycol[rr] = widen_f32(flip ? -v : v);
+        const long long row = (long long)J.rt * kTM + r;
+        if (row < mp.rows) {
+#pragma unroll
+          for (int c = 0; c < QW; c++) {
+            const int cc = qc * QW + c;
+            if (cc < nb) {
+              const int q = e.rank_root[j0 + cc];
+              const bool flip = om.colscale && om.colscale[q] < 0.0;
+              const float v = hi[c] + lo[c];
+              om.Y[out_col_m(om, q) * om.ldy + row] = widen_f32(flip ? -v : v);
             }
+          }
         }
       }
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      latch(status, SVDUP_ETIMEOUT);
     }
   }
   tc_fence_before();
@@ -782,10 +810,11 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
 }
 
 template <int STAGE, int W>
-void launch_umma(cudaStream_t st, dim3 grid, Eig e, FmmPlan f, MixPlan mp, OutMap om, int dense,
-                 int* status) {
+void launch_umma(cudaStream_t st, int items_max, Eig e, FmmPlan f, MixPlan mp, OutMap om,
+                 int dense, int* status) {
   cudaFuncSetAttribute(k_umma<STAGE, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kSmemBytes);
+  const int grid = std::max(1, std::min(items_max, device_sm_count()));  // persistent
   k_umma<STAGE, W><<<grid, kUmmaThreads, kSmemBytes, st>>>(e, f, mp, om, dense, status);
   SVDUP_COUNT_LAUNCH();
 }
@@ -843,14 +872,14 @@ void launch_mix_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, MixPlan mp, 
                       int dense, int* status) {
   if (stage == 0) {
     if (dense) return;
-    launch_umma<MS_P2M, 64>(st, dim3(mp.rt, mp.kphi), e, f, mp, om, dense, status);
+    launch_umma<MS_P2M, 64>(st, mp.rt * mp.kphi, e, f, mp, om, dense, status);
   } else if (stage == 1) {
     if (dense) return;
-    launch_umma<MS_M2L, 128>(st, dim3(mp.rt, mp.ntT), e, f, mp, om, dense, status);
+    launch_umma<MS_M2L, 128>(st, mp.rt * mp.ntT, e, f, mp, om, dense, status);
   } else if (mp.s == 64) {
-    launch_umma<MS_OUT, 64>(st, dim3(mp.rt, mp.Lmax + 1), e, f, mp, om, dense, status);
+    launch_umma<MS_OUT, 64>(st, mp.rt * (mp.Lmax + 1), e, f, mp, om, dense, status);
   } else {
-    launch_umma<MS_OUT, 128>(st, dim3(mp.rt, mp.Lmax + 1), e, f, mp, om, dense, status);
+    launch_umma<MS_OUT, 128>(st, mp.rt * (mp.Lmax + 1), e, f, mp, om, dense, status);
   }
 }
 

@@ -1098,7 +1098,7 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
 }
 
 // Streaming multiprocessors of the current device (queried once per device).
-static int sm_count() {
+int device_sm_count() {
   static int cached[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1130,7 +1130,8 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
     sqv = e.sqv;
   }
   // a warp per root, at most one block per SM (the roots are interleaved over them)
-  const int blocks = std::min((e.N + kSecularThreads / 32 - 1) / (kSecularThreads / 32), sm_count());
+  const int blocks =
+      std::min((e.N + kSecularThreads / 32 - 1) / (kSecularThreads / 32), device_sm_count());
   k_secular<<<blocks + (sqv ? kSecularSpecial : 0), kSecularThreads, 0, st>>>(
       e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org, e.tau, e.dorg, status, maxit, e.sqb,
       e.sqn, e.sqf, sqv);
@@ -1235,9 +1236,22 @@ void launch_merge(cudaStream_t st, Eig e) {
 // a problem whose exact eigenvalues are the computed roots, and stay orthogonal.
 // Each pole j != i is paired with an adjacent root so every factor lies in (0, 1):
 //   j < i: (mu_j - d_i)/(d_j - d_i),  j > i: (mu_{j-1} - d_i)/(d_j - d_i),
-// and the remaining root mu_{k-1} contributes (mu_{k-1} - d_i)/R.
-// One warp per index i; differences mu_j - d_i come from the offsets.
+// and the remaining root mu_{k-1} contributes (mu_{k-1} - d_i)/R.  The numerator and
+// denominator products are kept apart, each as a mantissa and a power of two (renormalised
+// after every factor by the bit fields), so no factor takes a reciprocal: five FP64
+// operations per factor.  One warp per index i; differences mu_j - d_i come from the
+// offsets.
 // ---------------------------------------------------------------------------
+// Exponent bookkeeping for long FP64 products: x = m 2^e with m in [1, 2) after
+// renorm (bit fields only; a zero stays zero).
+__device__ __forceinline__ void renorm64(double& m, int& e) {
+  const long long b = __double_as_longlong(m);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return;
+  m = __longlong_as_double((b & ~(0x7ffll << 52)) | (1023ll << 52));
+  e += ex - 1023;
+}
+
 __global__ void k_loewner(Eig e) {
   const int k = e.kp[0];
   const double rho = e.rhop[0];
@@ -1247,16 +1261,28 @@ __global__ void k_loewner(Eig e) {
   const double* dc = e.dc;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < k; i += warps) {
     const double di = dc[i];
-    double pr = 1.0;
+    double pn = 1.0, pd = 1.0;
+    int en = 0, ed = 0;
     for (int j = lane; j < k; j += 32) {
       if (j == i) continue;
-      int jr = (j < i) ? j : j - 1;
-      double num = (dc[e.orgc[jr]] - di) + e.tauc[jr];
-      double den = dc[j] - di;
-      pr *= num * rcp64(den);
+      const int jr = (j < i) ? j : j - 1;
+      pn *= (dc[e.orgc[jr]] - di) + e.tauc[jr];
+      pd *= dc[j] - di;
+      renorm64(pn, en);
+      renorm64(pd, ed);
     }
-    pr = warp_prod(pr);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      pn *= __shfl_xor_sync(0xffffffffu, pn, o);
+      pd *= __shfl_xor_sync(0xffffffffu, pd, o);
+      en += __shfl_xor_sync(0xffffffffu, en, o);
+      ed += __shfl_xor_sync(0xffffffffu, ed, o);
+      renorm64(pn, en);
+      renorm64(pd, ed);
+    }
     if (lane == 0) {
+      const int sx = en - ed, h = sx / 2;
+      double pr = (pn / pd) * ldexp(1.0, h) * ldexp(1.0, sx - h);
       pr *= ((dc[e.orgc[k - 1]] - di) + e.tauc[k - 1]) / R;
       double mag = sqrt(fmax(pr, 0.0));
       int io = (rho > 0.0) ? i : (k - 1 - i);
