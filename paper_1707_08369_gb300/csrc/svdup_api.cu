@@ -119,6 +119,12 @@ Eig make_eig(Arena& ar, int N) {
   e.rank_root = ar.take<int>(n);
   e.rank_defl = ar.take<int>(n);
   e.tol = ar.take<double>(1);
+  e.dmask = ar.take<unsigned>((n + 31) / 32 + 1);
+  e.dint = ar.take<int>(4);
+  e.dflt = ar.take<double>(4);
+  e.ovh = ar.take<int>(kMaxOverrunList);
+  e.ovW = ar.take<double>(kMaxOverrunList);
+  e.ovM = ar.take<double>(kMaxOverrunList);
   const size_t nbox = (n + 63) / 64;
   e.sqb = ar.take<double>(2 * nbox);
   e.sqn = ar.take<int>(2 * nbox);

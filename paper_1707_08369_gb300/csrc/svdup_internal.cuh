@@ -58,6 +58,8 @@ __device__ __forceinline__ double warp_max(double v) {
 // in device memory.  N is known on the host; k (the non-deflated count) lives on the
 // device so that nothing waits on the host between stages.
 // ---------------------------------------------------------------------------
+constexpr int kMaxOverrunList = 256;  // deflation: listed chain overruns (svdup_solve.cu)
+
 struct Eig {
   int N;
   double* rhop;  // rho (1 value, device: it depends on device-computed norms)
@@ -94,6 +96,14 @@ struct Eig {
   int* rank_root;  // root j -> final index
   int* rank_defl;  // sorted position s (deflated) -> final index, else -1
   double* tol;     // deflation tolerance (1 value)
+  // deflation scratch: candidate bitmask (N / 32 words), survivor count and listed
+  // overruns (dint), scaled tolerance and scalings (dflt), the overrun list
+  unsigned* dmask;
+  int* dint;
+  double* dflt;
+  int* ovh;
+  double* ovW;
+  double* ovM;
   // far-field secular evaluation (null: direct sums only): per box of 64 roots its
   // origin and half width, its near pole range, and the far sums at its nodes
   double* sqb;

@@ -224,19 +224,7 @@ void launch_fill_generic(cudaStream_t st, Eig e, const double* d, const double* 
 // the rotations one at a time.
 // ---------------------------------------------------------------------------
 constexpr int kDeflateThreads = 1024;
-constexpr int kMaxOverrun = 128;  // chains entered by the previous chain's run, listed
-
-// Dynamic shared memory of k_deflate: two bitmasks, plus the survivors' d, z and
-// positions when they fit.
-static size_t deflate_smem(int N, int* in_smem) {
-  size_t words = (size_t)(N + 31) / 32;
-  size_t masks = words * sizeof(unsigned);
-  size_t arrays = (size_t)N * (2 * sizeof(double) + sizeof(int) + 1);
-  size_t total = ((masks + 15) & ~(size_t)15) + arrays;
-  if (total <= 192 * 1024) { *in_smem = 1; return total; }
-  *in_smem = 0;
-  return masks;
-}
+constexpr int kMaxOverrun = kMaxOverrunList;  // chains entered by the previous chain's run
 
 // Block-wide exclusive prefix sum of one int per thread (Hillis-Steele over scnt);
 // returns the exclusive prefix and writes the total to *total.
@@ -290,15 +278,100 @@ __device__ __forceinline__ bool merges(double di, double zi, double W, double M,
   return g * g * zi2 <= tol2 * W * s * s;
 }
 
-__global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status, int in_smem) {
-  extern __shared__ double dsm[];
+// The case-(3) walk on the survivors (scaled d and z, the candidate bitmask and the run
+// flags brk, all in global scratch); every member is warp-collective.
+struct DeflWalk {
+  const unsigned* cmask;  // bit i: pair (i-1, i) passes with the original values
+  const double* kd;
+  const double* kz;
+  unsigned char* brk;     // 1: survivor i starts a run
+  int nk;
+  double tol2;
+  __device__ bool bit(int i) const { return i < nk && ((cmask[i >> 5] >> (i & 31)) & 1u); }
+  // first position >= from whose bit equals want (nk if none)
+  __device__ int next_bit(int from, bool want, int lane) const {
+    if (from >= nk) return nk;
+    const int nw = (nk + 31) >> 5;
+    for (int w0 = from >> 5; w0 < nw; w0 += 32) {
+      const int w = w0 + lane;
+      unsigned m = 0u;
+      if (w < nw) {
+        m = want ? cmask[w] : ~cmask[w];
+        if (w == (from >> 5)) m &= 0xffffffffu << (from & 31);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
+      if (bal) {
+        const int src = __ffs(bal) - 1;
+        const unsigned mm = __shfl_sync(0xffffffffu, m, src);
+        return min(nk, ((w0 + src) << 5) + __ffs(mm) - 1);
+      }
+    }
+    return nk;
+  }
+  // Walks the chain with first pair h up to pole lim (the pole before the next chain's
+  // first pair, or nk - 1); returns 1 if the last run merged pole lim and a chain
+  // follows, with the carrier in (W, M).
+  __device__ int walk(int h, int lim, bool have, double& W, double& M, int lane) const {
+    int pos = h;
+    int ppos = -1;  // the window whose values are already loaded (next_z, next_d)
+    double next_z = 0.0, next_d = 0.0;
+    while (true) {
+      if (!have) {
+        const double zj = kz[pos - 1];
+        W = zj * zj;
+        M = W * kd[pos - 1];
+      }
+      const int i = pos + lane;
+      const int nin = min(32, lim - pos + 1);
+      double zi = 0.0, di = 0.0;
+      if (ppos == pos) {
+        zi = next_z;
+        di = next_d;
+      } else if (lane < nin) {
+        zi = kz[i];
+        di = kd[i];
+      }
+      // the next window, if the whole of this one merges, loads while this one is tested
+      ppos = pos + 32;
+      next_z = 0.0;
+      next_d = 0.0;
+      if (ppos + lane <= lim) {
+        next_z = kz[ppos + lane];
+        next_d = kd[ppos + lane];
+      }
+      const double z2 = zi * zi, dz = z2 * di;
+      double iz2 = z2, idz = dz;  // inclusive prefix over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double a2 = __shfl_up_sync(0xffffffffu, iz2, o);
+        const double ad = __shfl_up_sync(0xffffffffu, idz, o);
+        if (lane >= o) { iz2 += a2; idz += ad; }
+      }
+      const bool ok = lane < nin && merges(di, zi, W + (iz2 - z2), M + (idz - dz), tol2);
+      const unsigned fail = __ballot_sync(0xffffffffu, !ok);
+      const int nm = fail ? __ffs(fail) - 1 : 32;  // lanes that merge
+      if (lane < nm) brk[i] = 0;
+      if (nm == nin) {  // every pole of the window merged
+        W += __shfl_sync(0xffffffffu, iz2, nm - 1);
+        M += __shfl_sync(0xffffffffu, idz, nm - 1);
+        have = true;
+        pos += nm;
+        if (pos > lim) return lim + 1 < nk ? 1 : 0;
+      } else {  // pole pos + nm failed: a new run only if its pair with the next passes
+        have = false;
+        pos += nm + 1;
+        if (pos > lim || !bit(pos)) return 0;
+      }
+    }
+  }
+};
+
+// Deflation, part 1 (one block): tolerance and scalings, case (1), the survivors'
+// scaled d and z and sorted positions, the case-(3) candidate bitmask.
+__global__ void __launch_bounds__(kDeflateThreads) k_deflate_pre(Eig e, int* status) {
   __shared__ double sred[3][32];
   __shared__ int scnt[kDeflateThreads];
-  __shared__ double sW[kDeflateThreads], sM[kDeflateThreads];
   __shared__ double s_tol, s_zn, s_dsc, s_zsc;
-  __shared__ int s_nov;
-  __shared__ int s_ovh[kMaxOverrun];
-  __shared__ double s_ovW[kMaxOverrun], s_ovM[kMaxOverrun];
   const int N = e.N;
   const double rho = e.rhop[0];
   int tid = threadIdx.x, nt = blockDim.x;
@@ -335,26 +408,13 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
   }
   __syncthreads();
   const double tol = s_tol, zn = s_zn, dsc = s_dsc, zsc = s_zsc;
-  const double idsc = 1.0 / dsc, izsc = 1.0 / zsc;  // exact: powers of two
   const double tolS = tol * dsc, tol2 = tolS * tolS;
   const int nwords = (N + 31) >> 5;
-  unsigned* cmask = (unsigned*)dsm;   // pair (i-1, i) passes with the original values
-  double* kd;                         // survivors' d * dsc
-  double* kz;                         // survivors' z * zsc
-  int* kpos;                          // survivors' sorted positions
-  unsigned char* brk;                 // 1: survivor i starts a run (pair (i-1, i) not merged)
-  if (in_smem) {
-    char* base = (char*)dsm + (((size_t)nwords * sizeof(unsigned) + 15) & ~(size_t)15);
-    kd = (double*)base;
-    kz = kd + N;
-    kpos = (int*)(kz + N);
-    brk = (unsigned char*)(kpos + N);
-  } else {  // global scratch that the compaction below overwrites anyway
-    kd = e.dk;
-    kz = e.zk;
-    kpos = e.idx;
-    brk = (unsigned char*)e.didx;
-  }
+  unsigned* cmask = e.dmask;
+  double* kd = e.dk;  // survivors' d * dsc (scratch: the compaction rewrites dk, zk, idx)
+  double* kz = e.zk;  // survivors' z * zsc
+  int* kpos = e.idx;  // survivors' sorted positions
+  unsigned char* brk = (unsigned char*)e.didx;
   for (int w = tid; w < nwords; w += nt) cmask[w] = 0u;
   // case (1) on my contiguous chunk [b0, b1), then the survivors' positions in order
   const int chunk = (N + nt - 1) / nt;
@@ -375,157 +435,139 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
     pos++;
   }
   __syncthreads();
-  // case (3) pre-test with the original values; it also seeds the run boundaries
+  // case (3) pre-test with the original values: the candidate pairs
   for (int i = tid; i < nk; i += nt) {
-    bool m = false;
     if (i > 0) {
       const double zj = kz[i - 1];
       const double W = zj * zj;
-      m = merges(kd[i], kz[i], W, W * kd[i - 1], tol2);
-      if (m) atomicOr(&cmask[i >> 5], 1u << (i & 31));
+      if (merges(kd[i], kz[i], W, W * kd[i - 1], tol2)) atomicOr(&cmask[i >> 5], 1u << (i & 31));
     }
-    brk[i] = m ? 0 : 1;
+    brk[i] = 1;
   }
-  __syncthreads();
-  // Run boundaries, as the sequential walk finds them.  Runs start only at pairs that pass
-  // with the original values (set bits of cmask); a chain is a maximal sequence of such
-  // pairs.  A run may continue past its chain's end through poles whose pairs fail alone
-  // but pass with the run's carrier, up to the pole before the next chain's first pair.
-  // Pass 1: warp w walks the chains whose first pair lies in bitmask words w, w + 32, ...
-  // from a fresh carrier, exactly as the sequential walk enters them, unless the previous
-  // chain's last run reached the next chain's first pole ("overran"); such chains are
-  // listed with the carrier.  Pass 2: one warp resumes the sequential walk at each listed
-  // chain, in order, with the listed carrier, cascading while runs keep overrunning.
-  // A warp steps 32 pairs at a time: from position pos with carrier (W, M), lane l tests
-  // pair (pos + l - 1, pos + l) against the carrier that exists if every earlier lane
-  // merged (W, M plus the lanes' exclusive prefix sums of z^2 and z^2 d): exactly the
-  // sequential carrier up to the first lane that fails.  Earlier lanes merge; a failing
-  // pole starts a new run with the next pair if that pair passes alone.
-  const int cpt = (nk + nt - 1) / nt;
-  const int c0 = min(nk, tid * cpt), c1 = min(nk, c0 + cpt);
-  for (int i = tid; i < nk; i += nt) brk[i] = 1;
-  if (tid == 0) s_nov = 0;
-  __syncthreads();
-  {
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-    const int nw = (nk + 31) >> 5;
-    auto bit = [&](int i) -> bool { return i < nk && ((cmask[i >> 5] >> (i & 31)) & 1u); };
-    // first position >= from whose bit equals want (nk if none), by the whole warp
-    auto next_bit = [&](int from, bool want) -> int {
-      if (from >= nk) return nk;
-      for (int w0 = from >> 5; w0 < nw; w0 += 32) {
-        const int w = w0 + lane;
-        unsigned m = 0u;
-        if (w < nw) {
-          m = want ? cmask[w] : ~cmask[w];
-          if (w == (from >> 5)) m &= 0xffffffffu << (from & 31);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
-        if (bal) {
-          const int src = __ffs(bal) - 1;
-          const unsigned mm = __shfl_sync(0xffffffffu, m, src);
-          return min(nk, ((w0 + src) << 5) + __ffs(mm) - 1);
-        }
+  if (tid == 0) {
+    e.dint[0] = nk;
+    e.dint[1] = 0;  // listed overruns
+    e.dflt[0] = tol2;
+    e.dflt[1] = dsc;
+    e.dflt[2] = zsc;
+  }
+}
+
+// Deflation, part 2 (many blocks): run boundaries, as the sequential walk finds them.
+// Runs start only at pairs that pass with the original values (set bits of the
+// bitmask); a chain is a maximal sequence of such pairs.  A run may continue past its
+// chain's end through poles whose pairs fail alone but pass with the run's carrier, up
+// to the pole before the next chain's first pair.  Global warp w walks the chains whose
+// first pair lies in bitmask words w, w + W, ... from a fresh carrier, exactly as the
+// sequential walk enters them, unless the previous chain's last run reached the next
+// chain's first pole ("overran"); such chains are listed with the carrier for part 3.
+// A warp steps 32 pairs at a time: from position pos with carrier (W, M), lane l tests
+// pair (pos + l - 1, pos + l) against the carrier that exists if every earlier lane
+// merged (W, M plus the lanes' exclusive prefix sums of z^2 and z^2 d): exactly the
+// sequential carrier up to the first lane that fails.  Earlier lanes merge; a failing
+// pole starts a new run with the next pair if that pair passes alone.
+__global__ void __launch_bounds__(256) k_deflate_walk(Eig e) {
+  const int nk = e.dint[0];
+  const DeflWalk dw = {e.dmask, e.dk, e.zk, (unsigned char*)e.didx, nk, e.dflt[0]};
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int nw = (nk + 31) >> 5;
+  for (int w = gw; w < nw; w += nwarps) {
+    const unsigned m = dw.cmask[w];
+    const unsigned prev = (w > 0) ? (dw.cmask[w - 1] >> 31) : 0u;
+    unsigned heads = m & ~((m << 1) | prev);  // first pair of each chain
+    while (heads) {
+      const int h = (w << 5) + __ffs(heads) - 1;
+      heads &= heads - 1;
+      const int nh = dw.next_bit(dw.next_bit(h, false, lane), true, lane);  // next chain
+      double W = 0.0, M = 0.0;
+      if (dw.walk(h, nh - 1, false, W, M, lane) && lane == 0) {
+        const int q = atomicAdd(&e.dint[1], 1);
+        if (q < kMaxOverrun) { e.ovh[q] = nh; e.ovW[q] = W; e.ovM[q] = M; }
       }
-      return nk;
-    };
-    // Walks the chain with first pair h up to pole lim (the pole before the next chain's
-    // first pair, or nk - 1); returns 1 if the last run merged pole lim and a chain
-    // follows, with the carrier in (W, M).
-    auto walk = [&](int h, int lim, bool have, double& W, double& M) -> int {
-      int pos = h;
-      while (true) {
-        if (!have) {
-          const double zj = kz[pos - 1];
-          W = zj * zj;
-          M = W * kd[pos - 1];
-        }
-        const int i = pos + lane;
-        const int nin = min(32, lim - pos + 1);
-        double zi = 0.0, di = 0.0;
-        if (lane < nin) { zi = kz[i]; di = kd[i]; }
-        const double z2 = zi * zi, dz = z2 * di;
-        double iz2 = z2, idz = dz;  // inclusive prefix over the lanes
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const double a2 = __shfl_up_sync(0xffffffffu, iz2, o);
-          const double ad = __shfl_up_sync(0xffffffffu, idz, o);
-          if (lane >= o) { iz2 += a2; idz += ad; }
-        }
-        const bool ok = lane < nin && merges(di, zi, W + (iz2 - z2), M + (idz - dz), tol2);
-        const unsigned fail = __ballot_sync(0xffffffffu, !ok);
-        const int nm = fail ? __ffs(fail) - 1 : 32;  // lanes that merge
-        if (lane < nm) brk[i] = 0;
-        if (nm == nin) {  // every pole of the window merged
-          W += __shfl_sync(0xffffffffu, iz2, nm - 1);
-          M += __shfl_sync(0xffffffffu, idz, nm - 1);
-          have = true;
-          pos += nm;
-          if (pos > lim) return lim + 1 < nk ? 1 : 0;
-        } else {  // pole pos + nm failed: a new run only if its pair with the next passes
-          have = false;
-          pos += nm + 1;
-          if (pos > lim || !bit(pos)) return 0;
-        }
-      }
-    };
-    for (int w = warp; w < nw; w += nwarps) {
-      const unsigned m = cmask[w];
-      const unsigned prev = (w > 0) ? (cmask[w - 1] >> 31) : 0u;
-      unsigned heads = m & ~((m << 1) | prev);  // first pair of each chain
-      while (heads) {
-        const int h = (w << 5) + __ffs(heads) - 1;
-        heads &= heads - 1;
-        const int nh = next_bit(next_bit(h, false), true);  // the next chain's first pair
-        double W = 0.0, M = 0.0;
-        if (walk(h, nh - 1, false, W, M) && lane == 0) {
-          const int q = atomicAdd(&s_nov, 1);
-          if (q < kMaxOverrun) { s_ovh[q] = nh; s_ovW[q] = W; s_ovM[q] = M; }
-        }
-      }
+    }
+  }
+}
+
+// Deflation, part 3 (one block): the listed overruns resumed in order (one warp,
+// cascading while runs keep overrunning; beyond kMaxOverrun listed, the whole walk again,
+// sequentially), then the rotation records, the merged values and the compaction.
+__global__ void __launch_bounds__(kDeflateThreads) k_deflate_post(Eig e, int in_smem) {
+  extern __shared__ double dsm[];
+  __shared__ int scnt[kDeflateThreads];
+  __shared__ double sW[kDeflateThreads], sM[kDeflateThreads];
+  const int N = e.N;
+  const double rho = e.rhop[0];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nk = e.dint[0];
+  const double dsc = e.dflt[1], zsc = e.dflt[2];
+  const double idsc = 1.0 / dsc, izsc = 1.0 / zsc;  // exact: powers of two
+  const double* kd = e.dk;
+  const double* kz = e.zk;
+  const int* kpos = e.idx;
+  unsigned char* brk = (unsigned char*)e.didx;
+  if (in_smem) {  // the sequential resumes and the records read these many times
+    double* skd = dsm;
+    double* skz = dsm + N;
+    unsigned char* sbrk = (unsigned char*)(dsm + 2 * (size_t)N);
+    for (int i = tid; i < nk; i += nt) {
+      skd[i] = kd[i];
+      skz[i] = kz[i];
+      sbrk[i] = brk[i];
     }
     __syncthreads();
-    if (warp == 0 && s_nov > 0) {
-      const int nov = s_nov;
-      if (nov > kMaxOverrun) {  // too many to list: the whole walk again, sequentially
-        for (int i = lane; i < nk; i += 32) brk[i] = 1;
-        __syncwarp();
-        int h = next_bit(1, true);
-        bool have = false;
-        double W = 0.0, M = 0.0;
-        while (h < nk) {
-          const int nh = next_bit(next_bit(h, false), true);
-          have = walk(h, nh - 1, have, W, M) != 0;
-          h = nh;
-        }
-      } else {
-        if (lane == 0)  // ascending chain order (a short list)
-          for (int x = 1; x < nov; x++)
-            for (int y = x; y > 0 && s_ovh[y - 1] > s_ovh[y]; y--) {
-              const int th = s_ovh[y]; s_ovh[y] = s_ovh[y - 1]; s_ovh[y - 1] = th;
-              const double tw = s_ovW[y]; s_ovW[y] = s_ovW[y - 1]; s_ovW[y - 1] = tw;
-              const double tm = s_ovM[y]; s_ovM[y] = s_ovM[y - 1]; s_ovM[y - 1] = tm;
-            }
-        __syncwarp();
-        int done = 0;  // chains before this position hold their final boundaries
-        for (int x = 0; x < nov; x++) {
-          int h = s_ovh[x];
-          if (h <= done) continue;  // listed by a chain that a resumed walk redid
-          double W = s_ovW[x], M = s_ovM[x];
-          while (true) {  // resume the sequential walk at chain h
-            const int nh = next_bit(next_bit(h, false), true);
-            for (int i = h + lane; i < nh; i += 32) brk[i] = 1;
-            __syncwarp();
-            const int more = walk(h, nh - 1, true, W, M);
-            done = nh;
-            if (!more) break;
-            h = nh;
+    kd = skd;
+    kz = skz;
+    brk = sbrk;
+  }
+  const int nov = e.dint[1];
+  if (tid < 32 && nov > 0) {
+    const int lane = tid;
+    const DeflWalk dw = {e.dmask, kd, kz, brk, nk, e.dflt[0]};
+    if (nov > kMaxOverrun) {
+      for (int i = lane; i < nk; i += 32) brk[i] = 1;
+      __syncwarp();
+      int h = dw.next_bit(1, true, lane);
+      bool have = false;
+      double W = 0.0, M = 0.0;
+      while (h < nk) {
+        const int nh = dw.next_bit(dw.next_bit(h, false, lane), true, lane);
+        have = dw.walk(h, nh - 1, have, W, M, lane) != 0;
+        h = nh;
+      }
+    } else {
+      if (lane == 0)  // ascending chain order (a short list)
+        for (int x = 1; x < nov; x++)
+          for (int y = x; y > 0 && e.ovh[y - 1] > e.ovh[y]; y--) {
+            const int th = e.ovh[y]; e.ovh[y] = e.ovh[y - 1]; e.ovh[y - 1] = th;
+            const double tw = e.ovW[y]; e.ovW[y] = e.ovW[y - 1]; e.ovW[y - 1] = tw;
+            const double tm = e.ovM[y]; e.ovM[y] = e.ovM[y - 1]; e.ovM[y - 1] = tm;
           }
+      __syncwarp();
+      int done = 0;  // chains before this position hold their final boundaries
+      for (int x = 0; x < nov; x++) {
+        int h = e.ovh[x];
+        if (h <= done) continue;  // listed by a chain that a resumed walk redid
+        double W = e.ovW[x], M = e.ovM[x];
+        while (true) {  // resume the sequential walk at chain h
+          const int nh = dw.next_bit(dw.next_bit(h, false, lane), true, lane);
+          for (int i = h + lane; i < nh; i += 32) brk[i] = 1;
+          __syncwarp();
+          const int more = dw.walk(h, nh - 1, true, W, M, lane);
+          done = nh;
+          if (!more) break;
+          h = nh;
         }
       }
     }
   }
   __syncthreads();
+  const int cpt = (nk + nt - 1) / nt;
+  const int c0 = min(nk, tid * cpt), c1 = min(nk, c0 + cpt);
+  const int chunk = (N + nt - 1) / nt;
+  const int b0 = min(N, tid * chunk), b1 = min(N, b0 + chunk);
+  int cnt, pos;
   // rotation records and merged values from the runs (segmented sums again)
   {
     double lW = 0.0, lM = 0.0;
@@ -604,11 +646,17 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate(Eig e, int* status,
 }
 
 void launch_deflate(cudaStream_t st, Eig e, int* status) {
-  int in_smem = 0;
-  size_t smem = deflate_smem(e.N, &in_smem);
-  // static (about 21 KB) plus dynamic shared memory may pass the 48 KB default
-  cudaFuncSetAttribute(k_deflate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_deflate<<<1, kDeflateThreads, smem, st>>>(e, status, in_smem);
+  k_deflate_pre<<<1, kDeflateThreads, 0, st>>>(e, status);
+  SVDUP_COUNT_LAUNCH();
+  const int nwords = (e.N + 31) / 32;
+  k_deflate_walk<<<std::max(1, (nwords + 7) / 8), 256, 0, st>>>(e);  // a warp per bitmask word
+  SVDUP_COUNT_LAUNCH();
+  // the survivors' d, z and run flags in shared memory when they fit (static: 20 KB)
+  const size_t smem = (size_t)e.N * (2 * sizeof(double) + 1) + 16;
+  const int in_smem = smem <= 200 * 1024 ? 1 : 0;
+  cudaFuncSetAttribute(k_deflate_post, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       in_smem ? (int)smem : 0);
+  k_deflate_post<<<1, kDeflateThreads, in_smem ? smem : 0, st>>>(e, in_smem);
   SVDUP_COUNT_LAUNCH();
 }
 
