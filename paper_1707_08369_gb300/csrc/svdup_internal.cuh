@@ -108,7 +108,8 @@ struct Eig {
   // origin and half width, its near pole range, and the far sums at its nodes
   double* sqb;
   int* sqn;
-  int* sqf;  // the boxed roots first .. last
+  int* sqf;  // the boxed roots first .. last, the pair-form scales E, Z
+  float2* z2f;  // z^2 2^-Z as pairs (the far-field form)
   double* sqv;
   // double-float copies for the pair-arithmetic sums (svdup_dfsum.cu): scales fsc[4]
   // (exponents), tau, zhat, y and root weights as (hi, lo) FP32 pairs

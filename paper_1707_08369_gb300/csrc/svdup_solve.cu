@@ -11,6 +11,7 @@
 
 #include <algorithm>
 
+#include "svdup_df.cuh"
 #include "svdup_internal.cuh"
 
 namespace svdup {
@@ -703,6 +704,7 @@ struct DirectSums {
   const double* dc;
   const double* z2c;
   int k;
+  static constexpr double wtol = kU;
   __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
     return secular_sums(dc, z2c, k, o, tau, jsplit, lane);
   }
@@ -728,7 +730,30 @@ struct DirectSums {
 // ---------------------------------------------------------------------------
 constexpr int kSqLeaf = 64;
 constexpr int kSqP = 26;
-constexpr int kSqMinK = 1024;  // smaller problems use the direct sums only
+constexpr int kSqMinK = 2048;  // smaller problems use the direct FP64 sums only
+
+// Far-field form in FP32 pairs.  For k >= kSqMinK the FP64 evaluation of w itself carries
+// a rounding bound of about k u (1 + R sum |t|) >= 2^-42 (1 + R sum |t|) (the attainable
+// accuracy the secular tests use); the pair arithmetic (about 2^-44 per term, see
+// svdup_df.cuh) stays inside it, so the far-field form sums in pairs and stops at
+// |w| <= kSecTolPairs (1 + R sum |t|).  Each root's origin pole, whose offset can be
+// arbitrarily small, is summed in FP64.  Poles and offsets are scaled by 2^-E, z^2 by 2^-Z
+// (powers of two from k_sq_prep), which keeps every other term inside the FP32 range.
+constexpr double kSecTolPairs = 0x1p-42;
+
+// x 2^s for a pair, in FP64, applied in two halves (each inside the FP64 range).
+__device__ __forceinline__ double pair_scaled(Df a, int s) {
+  const int h = s / 2;
+  return df_to_f64(a, 0) * pow2d(max(-1022, min(1023, h))) * pow2d(max(-1022, min(1023, s - h)));
+}
+
+// z^2 / delta and z^2 / delta^2 in pairs for delta = dd - tau (dd = d_i - d_o exact in
+// FP64; ntau = -tau 2^-E; z2 = z^2 2^-Z): results scaled by 2^(E - Z) and 2^(2E - Z).
+__device__ __forceinline__ void pair_term(double dd, Df ntau, Df z2, int E, Df& t, Df& dt) {
+  const Df r = df_rcp(df_add(df_from_f64(dd, E), ntau));
+  t = df_mul(z2, r);
+  dt = df_mul(t, r);
+}
 
 __device__ __forceinline__ int lower_bound_d(const double* a, int n, double v) {
   int lo = 0, hi = n;
@@ -812,12 +837,46 @@ __global__ void k_sq_boxes(const double* __restrict__ dc, const int* __restrict_
 
 // Far sums at the Chebyshev nodes of each box: sqv[(4 b + q) kSqP + beta] for q = psi_L,
 // psi_L', psi_R, psi_R'.  One warp per (box, node).
-__global__ void k_sq_nodes(const double* __restrict__ dc, const double* __restrict__ z2c,
+// Scales of the pair form (one block): sqf[2] = E with |d|, |tau| < 2^E for every
+// non-extreme root, sqf[3] = Z with z^2 <= 2^Z; z2f = z^2 2^-Z as pairs.
+__global__ void __launch_bounds__(1024) k_sq_prep(const double* __restrict__ dc,
+                                                  const double* __restrict__ z2c,
+                                                  const int* __restrict__ kp, int* sqf,
+                                                  float2* z2f) {
+  __shared__ int sz;
+  const int k = kp[0];
+  if (k < kSqMinK) return;
+  if (threadIdx.x == 0) sz = -1100;
+  __syncthreads();
+  int mz = -1100;
+  for (int t = threadIdx.x; t < k; t += blockDim.x) mz = max(mz, exp2_of(z2c[t]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mz = max(mz, __shfl_xor_sync(0xffffffffu, mz, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&sz, mz);
+  __syncthreads();
+  const int Z = sz <= -1000 ? 0 : sz;
+  // the roots' offsets stay within twice the pole range: one more bit
+  const int E = max(exp2_of(dc[0]), exp2_of(dc[k - 1])) + 2;
+  if (threadIdx.x == 0) {
+    sqf[2] = E;
+    sqf[3] = Z;
+  }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) {
+    const Df v = df_from_f64(z2c[t], Z);
+    z2f[t] = make_float2(v.hi, v.lo);
+  }
+}
+
+// Far sums at the Chebyshev nodes of each box: sqv[(4 b + q) kSqP + beta] for q = psi_L,
+// psi_L', psi_R', psi_R', in pairs (every pole is at least 2r from the node).  One warp
+// per (box, node).
+__global__ void k_sq_nodes(const double* __restrict__ dc, const float2* __restrict__ z2f,
                            const int* __restrict__ kp, const double* __restrict__ sqb,
                            const int* __restrict__ sqn, const int* __restrict__ sqf, double* sqv) {
   const int k = kp[0];
   if (k < kSqMinK) return;
   const int nb = sq_boxes(sqf[0], sqf[1]);
+  const int E = sqf[2], Z = sqf[3];
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nb * kSqP; w += warps) {
@@ -825,31 +884,32 @@ __global__ void k_sq_nodes(const double* __restrict__ dc, const double* __restri
     const double base = sqb[2 * b], r = sqb[2 * b + 1];
     const int n0 = sqn[2 * b], n1 = sqn[2 * b + 1];
     const double yo = r * (1.0 + cospi((2.0 * beta + 1.0) / (2.0 * kSqP)));
-    double pL = 0.0, dL = 0.0, pR = 0.0, dR = 0.0;
+    const Df nyo = df_neg(df_from_f64(yo, E));
+    Df pL = {0.f, 0.f}, dL = {0.f, 0.f}, pR = {0.f, 0.f}, dR = {0.f, 0.f};
     for (int t = lane; t < n0; t += 32) {
-      double del = (dc[t] - base) - yo;
-      double rc = rcp64(del);
-      double tt = z2c[t] * rc;
-      pL += tt;
-      dL = fma(tt, rc, dL);
+      Df tt, dt;
+      const float2 z = z2f[t];
+      pair_term(dc[t] - base, nyo, Df{z.x, z.y}, E, tt, dt);
+      pL = df_add(pL, tt);
+      dL = df_add(dL, dt);
     }
     for (int t = n1 + lane; t < k; t += 32) {
-      double del = (dc[t] - base) - yo;
-      double rc = rcp64(del);
-      double tt = z2c[t] * rc;
-      pR += tt;
-      dR = fma(tt, rc, dR);
+      Df tt, dt;
+      const float2 z = z2f[t];
+      pair_term(dc[t] - base, nyo, Df{z.x, z.y}, E, tt, dt);
+      pR = df_add(pR, tt);
+      dR = df_add(dR, dt);
     }
-    pL = warp_sum(pL);
-    dL = warp_sum(dL);
-    pR = warp_sum(pR);
-    dR = warp_sum(dR);
+    pL = df_warp_sum(pL);
+    dL = df_warp_sum(dL);
+    pR = df_warp_sum(pR);
+    dR = df_warp_sum(dR);
     if (lane == 0) {
       double* v = sqv + (size_t)4 * b * kSqP;
-      v[beta] = pL;
-      v[kSqP + beta] = dL;
-      v[2 * kSqP + beta] = pR;
-      v[3 * kSqP + beta] = dR;
+      v[beta] = pair_scaled(pL, Z - E);
+      v[kSqP + beta] = pair_scaled(dL, Z - 2 * E);
+      v[2 * kSqP + beta] = pair_scaled(pR, Z - E);
+      v[3 * kSqP + beta] = pair_scaled(dR, Z - 2 * E);
     }
   }
 }
@@ -862,6 +922,9 @@ struct FarSums {
   const double* vals;  // 4 x kSqP node values of this box
   const double* sx;    // Chebyshev nodes (shared memory)
   const double* sw;    // barycentric weights (shared memory)
+  const float2* z2f;   // z^2 2^-Z as pairs
+  int E, Z;
+  static constexpr double wtol = kSecTolPairs;
   __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
     SecSums s = {0.0, 0.0, 0.0, 0.0, 0.0};
     const double dO = dc[o];
@@ -883,18 +946,42 @@ struct FarSums {
       s.psiR = c * vals[2 * kSqP + lane];
       s.dpsiR = c * vals[3 * kSqP + lane];
     }
+    // near poles in pairs, the origin pole (offset -tau) in FP64
+    const Df ntau = df_neg(df_from_f64(tau, E));
+    Df pL = {0.f, 0.f}, dL = {0.f, 0.f}, pR = {0.f, 0.f}, dR = {0.f, 0.f};
     for (int i = n0 + lane; i < n1; i += 32) {
-      double del = (dc[i] - dO) - tau;
-      double rc = rcp64(del);
-      double t = z2c[i] * rc;
-      double dt = t * rc;
-      if (i <= jsplit) { s.psiL += t; s.dpsiL += dt; }
+      if (i == o) continue;
+      Df t, dt;
+      const float2 z = z2f[i];
+      pair_term(dc[i] - dO, ntau, Df{z.x, z.y}, E, t, dt);
+      if (i <= jsplit) { pL = df_add(pL, t); dL = df_add(dL, dt); }
+      else { pR = df_add(pR, t); dR = df_add(dR, dt); }
+    }
+    double nL = pair_scaled(df_warp_sum(pL), Z - E), ndL = pair_scaled(df_warp_sum(dL), Z - 2 * E);
+    double nR = pair_scaled(df_warp_sum(pR), Z - E), ndR = pair_scaled(df_warp_sum(dR), Z - 2 * E);
+    if (!isfinite(nL + ndL + nR + ndR)) {  // a term left the FP32 range: this one in FP64
+      nL = ndL = nR = ndR = 0.0;
+      for (int i = n0 + lane; i < n1; i += 32) {
+        if (i == o) continue;
+        const double rc = rcp64((dc[i] - dO) - tau);
+        const double t = z2c[i] * rc, dt = t * rc;
+        if (i <= jsplit) { nL += t; ndL += dt; }
+        else { nR += t; ndR += dt; }
+      }
+      nL = warp_sum(nL);
+      ndL = warp_sum(ndL);
+      nR = warp_sum(nR);
+      ndR = warp_sum(ndR);
+    }
+    s.psiL = warp_sum(s.psiL) + nL;
+    s.dpsiL = warp_sum(s.dpsiL) + ndL;
+    s.psiR = warp_sum(s.psiR) + nR;
+    s.dpsiR = warp_sum(s.dpsiR) + ndR;
+    {
+      const double t = z2c[o] / (-tau), dt = t / (-tau);
+      if (o <= jsplit) { s.psiL += t; s.dpsiL += dt; }
       else { s.psiR += t; s.dpsiR += dt; }
     }
-    s.psiL = warp_sum(s.psiL);
-    s.dpsiL = warp_sum(s.dpsiL);
-    s.psiR = warp_sum(s.psiR);
-    s.dpsiR = warp_sum(s.dpsiR);
     s.asum = s.psiR - s.psiL;
     return s;
   }
@@ -913,25 +1000,29 @@ struct LedSums {
   int* s_o;
   int* s_js;
   int* s_cmd;
+  const float2* z2f;  // the pair form (scales E, Z), as FarSums
+  int E, Z;
+  static constexpr double wtol = kSecTolPairs;
   __device__ static void bar(int id) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"((int)blockDim.x) : "memory");
   }
   __device__ void partial(int o, double tau, int jsplit) const {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    Df v[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const double dO = dc[o];
+    const Df ntau = df_neg(df_from_f64(tau, E));
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-      const double del = (dc[i] - dO) - tau;
-      const double rc = rcp64(del);
-      const double t = z2c[i] * rc;
-      const double dt = t * rc;
-      if (i <= jsplit) { v[0] += t; v[1] += dt; }
-      else { v[2] += t; v[3] += dt; }
+      if (i == o) continue;  // the origin pole: FP64, by warp 0
+      Df t, dt;
+      const float2 z = z2f[i];
+      pair_term(dc[i] - dO, ntau, Df{z.x, z.y}, E, t, dt);
+      if (i <= jsplit) { v[0] = df_add(v[0], t); v[1] = df_add(v[1], dt); }
+      else { v[2] = df_add(v[2], t); v[3] = df_add(v[3], dt); }
     }
     const int w = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      v[q] = warp_sum(v[q]);
-      if ((threadIdx.x & 31) == 0) part[q * 32 + w] = v[q];
+      const Df r = df_warp_sum(v[q]);
+      if ((threadIdx.x & 31) == 0) part[q * 32 + w] = pair_scaled(r, (q & 1) ? Z - 2 * E : Z - E);
     }
   }
   // warp 0 only
@@ -944,6 +1035,21 @@ struct LedSums {
     double v[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) v[q] = warp_sum(lane < nw ? part[q * 32 + lane] : 0.0);
+    if (!isfinite(v[0] + v[1] + v[2] + v[3])) {  // a term left the FP32 range: FP64, warp 0
+      const double dO = dc[o];
+      for (int q = 0; q < 4; q++) v[q] = 0.0;
+      for (int i = lane; i < k; i += 32) {
+        if (i == o) continue;
+        const double rc = rcp64((dc[i] - dO) - tau);
+        const double t = z2c[i] * rc, dt = t * rc;
+        if (i <= jsplit) { v[0] += t; v[1] += dt; }
+        else { v[2] += t; v[3] += dt; }
+      }
+      for (int q = 0; q < 4; q++) v[q] = warp_sum(v[q]);
+    }
+    const double t = z2c[o] / (-tau), dt = t / (-tau);  // the origin pole
+    if (o <= jsplit) { v[0] += t; v[1] += dt; }
+    else { v[2] += t; v[3] += dt; }
     SecSums s = {v[0], v[1], v[2], v[3], v[2] - v[0]};
     return s;
   }
@@ -992,7 +1098,11 @@ __device__ int secular_root(const Sums& sums, const double* __restrict__ dc,
     if (w < 0.0) lo = tau; else hi = tau;
   }
   for (int it = 0; it < maxit; it++) {
-    if (w == 0.0 || fabs(w) <= kU * (1.0 + R * sm.asum)) { *o_out = o; *tau_out = tau; return 0; }
+    if (w == 0.0 || fabs(w) <= Sums::wtol * (1.0 + R * sm.asum)) {
+      *o_out = o;
+      *tau_out = tau;
+      return 0;
+    }
     double eta;
     bool ok = true;
     if (!last) {
@@ -1067,7 +1177,8 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
     const double* __restrict__ dc, const double* __restrict__ z2c, const int* __restrict__ kp,
     const double* __restrict__ rhop, const double* __restrict__ dk, int* orgc, double* tauc,
     int* org, double* tau, double* dorg, int* status, int maxit, const double* __restrict__ sqb,
-    const int* __restrict__ sqn, const int* __restrict__ sqf, const double* __restrict__ sqv) {
+    const int* __restrict__ sqn, const int* __restrict__ sqf, const double* __restrict__ sqv,
+    const float2* __restrict__ z2f) {
   __shared__ double s_zn2;
   __shared__ double s_x[kSqP], s_w[kSqP];
   const int k = kp[0];
@@ -1102,7 +1213,9 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
     __shared__ double part[4 * 32];
     __shared__ double s_tau;
     __shared__ int s_o, s_js, s_cmd;
-    const LedSums ls = {dc, z2c, k, part, &s_tau, &s_o, &s_js, &s_cmd};
+    // the last root's offset reaches R ||z||^2 past the largest pole: its own scale
+    const int E = max(sqf[2], exp2_of(R * s_zn2) + 2);
+    const LedSums ls = {dc, z2c, k, part, &s_tau, &s_o, &s_js, &s_cmd, z2f, E, sqf[3]};
     if (threadIdx.x < 32) {
       int o;
       double t;
@@ -1131,8 +1244,9 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
     if (far && (j < first || j > last)) continue;  // done by blocks 0-2
     if (far) {
       const int b = (j - first) / kSqLeaf;
-      const FarSums fs = {dc, z2c, sqn[2 * b], sqn[2 * b + 1], sqb[2 * b], sqb[2 * b + 1],
-                          sqv + (size_t)4 * b * kSqP, s_x, s_w};
+      const FarSums fs = {dc,      z2c,      sqn[2 * b], sqn[2 * b + 1], sqb[2 * b],
+                          sqb[2 * b + 1], sqv + (size_t)4 * b * kSqP, s_x, s_w, z2f,
+                          sqf[2],  sqf[3]};
       bad = secular_root(fs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
     } else {
       bad = secular_root(direct, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
@@ -1169,10 +1283,12 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
   const double* sqv = nullptr;
   if (e.sqv && e.N >= kSqMinK) {  // far-field set-up (the kernels skip small k themselves)
     const int nb = (e.N + kSqLeaf - 1) / kSqLeaf;
+    k_sq_prep<<<1, 1024, 0, st>>>(e.dc, e.z2c, e.kp, e.sqf, e.z2f);
+    SVDUP_COUNT_LAUNCH();
     k_sq_boxes<<<(nb + 127) / 128, 128, 0, st>>>(e.dc, e.kp, e.sqb, e.sqn, e.sqf);
     SVDUP_COUNT_LAUNCH();
     const int nw = nb * kSqP;
-    k_sq_nodes<<<(nw * 32 + 255) / 256, 256, 0, st>>>(e.dc, e.z2c, e.kp, e.sqb, e.sqn, e.sqf,
+    k_sq_nodes<<<(nw * 32 + 255) / 256, 256, 0, st>>>(e.dc, e.z2f, e.kp, e.sqb, e.sqn, e.sqf,
                                                       e.sqv);
     SVDUP_COUNT_LAUNCH();
     sqv = e.sqv;
@@ -1182,7 +1298,7 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
       std::min((e.N + kSecularThreads / 32 - 1) / (kSecularThreads / 32), device_sm_count());
   k_secular<<<blocks + (sqv ? kSecularSpecial : 0), kSecularThreads, 0, st>>>(
       e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org, e.tau, e.dorg, status, maxit, e.sqb,
-      e.sqn, e.sqf, sqv);
+      e.sqn, e.sqf, sqv, e.z2f);
   SVDUP_COUNT_LAUNCH();
 }
 
