@@ -23,14 +23,25 @@ void note_launch(const char* file, int line);
 
 constexpr double kU = 1.1102230246251565e-16;  // 2^-53, unit roundoff of IEEE double
 
-// 1/x for IEEE double by Newton-Raphson on the reciprocal: an FP32 seed from the
-// hardware reciprocal (__frcp_rn) refined by two FP64 Newton steps r <- r + r(1 - x r),
-// each doubling the number of correct bits (2^-23 -> 2^-46 -> below 2^-53).  Outside
-// the FP32 normal range the seed is unusable and CUDA's division is used instead.
+// 1/x for IEEE double by Newton-Raphson on the reciprocal.  The seed comes from the
+// significand alone, by the bit fields: m in [1, 2) (the top 23 fraction bits as an FP32
+// number), its FP32 reciprocal (rcp.approx, about one ulp), then x's exponent negated and
+// its sign put back, so no FP64 operation and no range limit is spent on the seed.  Two
+// FP64 Newton steps r <- r + r (1 - x r) take it from 2^-22 to 2^-44 to below 2^-53.
+// Zeros, subnormals, the largest binades (whose reciprocals are subnormal), infinities and
+// NaNs take CUDA's division.  On this GPU every FP64 warp instruction costs the same
+// whatever its active lanes; the seed keeps four of them per reciprocal.
 __device__ __forceinline__ double rcp64(double x) {
-  double ax = fabs(x);
-  if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
-  double r = (double)__frcp_rn((float)x);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned ex = (unsigned)(b >> 52) & 0x7ffu;
+  if (ex == 0u || ex >= 0x7fdu) return 1.0 / x;
+  const float m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffffu));
+  float rm;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rm) : "f"(m));  // in (0.5, 1]
+  const unsigned um = __float_as_uint(rm);
+  const unsigned long long de = (unsigned long long)((um >> 23) & 0xffu) + 1919ull - ex;
+  double r = __longlong_as_double((long long)((b & 0x8000000000000000ull) | (de << 52) |
+                                              ((unsigned long long)(um & 0x7fffffu) << 29)));
   double e = fma(-x, r, 1.0);
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);

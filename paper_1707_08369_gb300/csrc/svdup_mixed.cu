@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <stdint.h>
 
+#include "svdup_df.cuh"
 #include "svdup_internal.cuh"
 
 namespace svdup {
@@ -83,16 +84,20 @@ __device__ __forceinline__ void split3f(float x, uint16_t& h, uint16_t& m, uint1
   l = __bfloat16_as_ushort(bl);
 }
 
-__device__ __forceinline__ void split3d(double x, uint16_t& h, uint16_t& m, uint16_t& l) {
-  __nv_bfloat16 bh = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(bh);
-  __nv_bfloat16 bm = __double2bfloat16(r);
-  r = r - (double)__bfloat162float(bm);
-  __nv_bfloat16 bl = __double2bfloat16(r);
-  h = __bfloat16_as_ushort(bh);
-  m = __bfloat16_as_ushort(bm);
-  l = __bfloat16_as_ushort(bl);
+// FP64 -> FP32 rounded to nearest (ties away from zero) by the bit fields: the top 24
+// significant bits plus the next one as a carry, which the exponent field absorbs when
+// it overflows the fraction.  Values below the FP32 normal range become signed zeros.
+__device__ __forceinline__ float narrow_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex <= 896) return __uint_as_float(sign);
+  if (ex >= 1151) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  const unsigned u = (unsigned)((mag >> 29) - (896ull << 23)) + (unsigned)((b >> 28) & 1ull);
+  return __uint_as_float(sign | u);
 }
+
 
 __device__ __forceinline__ uint4 pack8(const uint16_t* v) {
   uint4 o;
@@ -112,6 +117,41 @@ __device__ __forceinline__ void store_split8(unsigned char* tile, uint32_t plane
   *(uint4*)(tile + 2 * plane + off) = pack8(l);
 }
 
+// Three BF16 terms of the double-float value hi + lo (24 significant bits).
+__device__ __forceinline__ void split3ff(float hi, float lo, uint16_t& h, uint16_t& m,
+                                         uint16_t& l) {
+  __nv_bfloat16 bh = __float2bfloat16_rn(hi);
+  float r = (hi - __bfloat162float(bh)) + lo;
+  __nv_bfloat16 bm = __float2bfloat16_rn(r);
+  r = r - __bfloat162float(bm);
+  __nv_bfloat16 bl = __float2bfloat16_rn(r);
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+
+__device__ __forceinline__ void store_split8_ff(unsigned char* tile, uint32_t plane, uint32_t off,
+                                                const float* hi, const float* lo) {
+  uint16_t h[8], m[8], l[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) split3ff(hi[c], lo[c], h[c], m[c], l[c]);
+  store_split8(tile, plane, off, h, m, l);
+}
+
+// An FP64 value reaches its three BF16 terms through an FP32 pair (bit fields, no FP64
+// operation): the pair carries 47 bits, the split keeps the top 24.
+__device__ __forceinline__ void store_split8_d(unsigned char* tile, uint32_t plane, uint32_t off,
+                                               const double* v) {
+  float hi[8], lo[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    const Df p = df_from_f64(v[c], 0);
+    hi[c] = p.hi;
+    lo[c] = p.lo;
+  }
+  store_split8_ff(tile, plane, off, hi, lo);
+}
+
 __device__ __forceinline__ void store_split8_f(unsigned char* tile, uint32_t plane, uint32_t off,
                                                const float* v) {
   uint16_t h[8], m[8], l[8];
@@ -120,13 +160,6 @@ __device__ __forceinline__ void store_split8_f(unsigned char* tile, uint32_t pla
   store_split8(tile, plane, off, h, m, l);
 }
 
-__device__ __forceinline__ void store_split8_d(unsigned char* tile, uint32_t plane, uint32_t off,
-                                               const double* v) {
-  uint16_t h[8], m[8], l[8];
-#pragma unroll
-  for (int c = 0; c < 8; c++) split3d(v[c], h[c], m[c], l[c]);
-  store_split8(tile, plane, off, h, m, l);
-}
 
 // ---------------------------------------------------------------------------
 // PTX wrappers: mbarrier, bulk copy, tcgen05
@@ -294,7 +327,7 @@ __global__ void __launch_bounds__(256) k_mix_gather(Eig e, const double* __restr
 #pragma unroll
     for (int c = 0; c < 8; c++) {
       long long col = scol[ch * 8 + c];
-      v[c] = (col >= 0 && row < rows) ? (float)X[row + col] : 0.0f;
+      v[c] = (col >= 0 && row < rows) ? narrow_rn(X[row + col]) : 0.0f;
     }
     store_split8_f(tile, kPlaneA, cl_off(r, ch * 8, kKB), v);
   }
@@ -548,26 +581,6 @@ __device__ __forceinline__ double widen_f32(float x) {
   return __longlong_as_double((long long)d);
 }
 
-// Three BF16 terms of the double-float value hi + lo (24 significant bits).
-__device__ __forceinline__ void split3ff(float hi, float lo, uint16_t& h, uint16_t& m,
-                                         uint16_t& l) {
-  __nv_bfloat16 bh = __float2bfloat16_rn(hi);
-  float r = (hi - __bfloat162float(bh)) + lo;
-  __nv_bfloat16 bm = __float2bfloat16_rn(r);
-  r = r - __bfloat162float(bm);
-  __nv_bfloat16 bl = __float2bfloat16_rn(r);
-  h = __bfloat16_as_ushort(bh);
-  m = __bfloat16_as_ushort(bm);
-  l = __bfloat16_as_ushort(bl);
-}
-
-__device__ __forceinline__ void store_split8_ff(unsigned char* tile, uint32_t plane, uint32_t off,
-                                                const float* hi, const float* lo) {
-  uint16_t h[8], m[8], l[8];
-#pragma unroll
-  for (int c = 0; c < 8; c++) split3ff(hi[c], lo[c], h[c], m[c], l[c]);
-  store_split8(tile, plane, off, h, m, l);
-}
 
 // Roles: warps 0-7 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) .., i.e.
 // output rows, and the column half w / 4 of the W accumulator columns), warp 8 issues
