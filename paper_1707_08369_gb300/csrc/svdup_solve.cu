@@ -928,23 +928,33 @@ struct FarSums {
   __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
     SecSums s = {0.0, 0.0, 0.0, 0.0, 0.0};
     const double dO = dc[o];
-    // barycentric weights of the far field at the box coordinate of mu
-    const double yh = (((dO - base) + tau) - r) / r;
-    double c = 0.0;
+    // Barycentric weights of the far field at the box coordinate of mu, in pairs (within
+    // the pair form's error budget): c_l = w_l / (y - x_l), normalised by their sum.
+    const double yh = (((dO - base) + tau) - r) * rcp64(r);
+    // node values beyond the pair range (exponent tests only): the FP64 form below
+    const bool big = lane < kSqP && max(max(exp2_of(vals[lane]), exp2_of(vals[kSqP + lane])),
+                                        max(exp2_of(vals[2 * kSqP + lane]),
+                                            exp2_of(vals[3 * kSqP + lane]))) > 120;
+    const bool f64far = __any_sync(0xffffffffu, big);
+    Df c = {0.f, 0.f};
     int hit = 0;
     if (lane < kSqP) {
-      const double df = yh - sx[lane];
-      if (df == 0.0) hit = 1;
-      else c = sw[lane] / df;
+      const Df dfy = df_add(df_from_f64(yh, 0), df_neg(df_from_f64(sx[lane], 0)));
+      if (dfy.hi == 0.0f) hit = 1;
+      else c = df_mul(df_from_f64(sw[lane], 0), df_rcp(dfy));
     }
     const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    if (hm) c = (lane == __ffs(hm) - 1) ? 1.0 : 0.0;  // mu sits exactly on a node
-    else c = c / warp_sum(c);
+    if (hm) {  // mu sits exactly on a node
+      c = (lane == __ffs(hm) - 1) ? Df{1.0f, 0.0f} : Df{0.0f, 0.0f};
+    } else {
+      c = df_mul(c, df_rcp(df_warp_sum(c)));
+    }
+    Df fL = {0.f, 0.f}, fdL = {0.f, 0.f}, fR = {0.f, 0.f}, fdR = {0.f, 0.f};
     if (lane < kSqP) {  // far-left terms are negative, far-right positive
-      s.psiL = c * vals[lane];
-      s.dpsiL = c * vals[kSqP + lane];
-      s.psiR = c * vals[2 * kSqP + lane];
-      s.dpsiR = c * vals[3 * kSqP + lane];
+      fL = df_mul(c, df_from_f64(vals[lane], 0));
+      fdL = df_mul(c, df_from_f64(vals[kSqP + lane], 0));
+      fR = df_mul(c, df_from_f64(vals[2 * kSqP + lane], 0));
+      fdR = df_mul(c, df_from_f64(vals[3 * kSqP + lane], 0));
     }
     // near poles in pairs, the origin pole (offset -tau) in FP64
     const Df ntau = df_neg(df_from_f64(tau, E));
@@ -973,12 +983,31 @@ struct FarSums {
       nR = warp_sum(nR);
       ndR = warp_sum(ndR);
     }
-    s.psiL = warp_sum(s.psiL) + nL;
-    s.dpsiL = warp_sum(s.dpsiL) + ndL;
-    s.psiR = warp_sum(s.psiR) + nR;
-    s.dpsiR = warp_sum(s.dpsiR) + ndR;
+    if (f64far) {
+      double cc = 0.0;
+      int h2 = 0;
+      if (lane < kSqP) {
+        const double d = yh - sx[lane];
+        if (d == 0.0) h2 = 1;
+        else cc = sw[lane] / d;
+      }
+      const unsigned hm2 = __ballot_sync(0xffffffffu, h2);
+      if (hm2) cc = (lane == __ffs(hm2) - 1) ? 1.0 : 0.0;
+      else cc = cc / warp_sum(cc);
+      const bool on = lane < kSqP;
+      s.psiL = warp_sum(on ? cc * vals[lane] : 0.0) + nL;
+      s.dpsiL = warp_sum(on ? cc * vals[kSqP + lane] : 0.0) + ndL;
+      s.psiR = warp_sum(on ? cc * vals[2 * kSqP + lane] : 0.0) + nR;
+      s.dpsiR = warp_sum(on ? cc * vals[3 * kSqP + lane] : 0.0) + ndR;
+    } else {
+      s.psiL = df_to_f64(df_warp_sum(fL), 0) + nL;
+      s.dpsiL = df_to_f64(df_warp_sum(fdL), 0) + ndL;
+      s.psiR = df_to_f64(df_warp_sum(fR), 0) + nR;
+      s.dpsiR = df_to_f64(df_warp_sum(fdR), 0) + ndR;
+    }
     {
-      const double t = z2c[o] / (-tau), dt = t / (-tau);
+      const double ri = -rcp64(tau);
+      const double t = z2c[o] * ri, dt = t * ri;
       if (o <= jsplit) { s.psiL += t; s.dpsiL += dt; }
       else { s.psiR += t; s.dpsiR += dt; }
     }
@@ -1047,7 +1076,8 @@ struct LedSums {
       }
       for (int q = 0; q < 4; q++) v[q] = warp_sum(v[q]);
     }
-    const double t = z2c[o] / (-tau), dt = t / (-tau);  // the origin pole
+    const double ri = -rcp64(tau);  // the origin pole
+    const double t = z2c[o] * ri, dt = t * ri;
     if (o <= jsplit) { v[0] += t; v[1] += dt; }
     else { v[2] += t; v[3] += dt; }
     SecSums s = {v[0], v[1], v[2], v[3], v[2] - v[0]};
