@@ -367,7 +367,7 @@ void queue_product(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, do
                    double* Xs, OutMap om, int mode) {
   int dense = use_dense(h, e.N, mode) ? 1 : 0;
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(st, e, X, ldx, rows, f.rot, false);
+  launch_rotate_columns(st, e, X, ldx, rows, f.rot, false, om);
   launch_gather_columns(st, e, X, ldx, rows, Xs, rows, om);
   stage_end(h);
   stage_begin(h, SVDUP_STAGE_SETUP);
@@ -400,7 +400,7 @@ void queue_product_mixed(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPla
   launch_mix_setup(st, e, f, mp, dense);
   stage_end(h);
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(st, e, X, ldx, rows, f.rot, true);
+  launch_rotate_columns(st, e, X, ldx, rows, f.rot, true, om);
   launch_mix_gather(st, e, X, ldx, rows, mp, om);
   stage_end(h);
   if (!dense) {

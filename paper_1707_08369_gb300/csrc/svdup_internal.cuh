@@ -244,8 +244,9 @@ void launch_fill_random(cudaStream_t st, int rows, int N, double* X, double* d, 
 // scratch: rotate_scratch_bytes(N, rows) bytes, 16-byte aligned; mixed: FP32-accurate
 // arithmetic (see svdup_product.cu)
 size_t rotate_scratch_bytes(int N, int rows);
+// Deflated columns (rotation outputs) go straight to their output column in om.
 void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
-                           void* scratch, bool mixed);
+                           void* scratch, bool mixed, OutMap om);
 void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
                            double* Xs, long long ldxs, OutMap om);
 void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense);

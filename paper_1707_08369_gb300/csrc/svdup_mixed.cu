@@ -84,19 +84,6 @@ __device__ __forceinline__ void split3f(float x, uint16_t& h, uint16_t& m, uint1
   l = __bfloat16_as_ushort(bl);
 }
 
-// FP64 -> FP32 rounded to nearest (ties away from zero) by the bit fields: the top 24
-// significant bits plus the next one as a carry, which the exponent field absorbs when
-// it overflows the fraction.  Values below the FP32 normal range become signed zeros.
-__device__ __forceinline__ float narrow_rn(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int ex = (int)((b >> 52) & 0x7ff);
-  if (ex <= 896) return __uint_as_float(sign);
-  if (ex >= 1151) return __uint_as_float(sign | 0x7f800000u);
-  const unsigned long long mag = b & 0x7fffffffffffffffull;
-  const unsigned u = (unsigned)((mag >> 29) - (896ull << 23)) + (unsigned)((b >> 28) & 1ull);
-  return __uint_as_float(sign | u);
-}
 
 
 __device__ __forceinline__ uint4 pack8(const uint16_t* v) {
@@ -344,6 +331,7 @@ __global__ void k_mix_defl(Eig e, const double* __restrict__ X, long long ldx, i
   const int c = k + blockIdx.x;
   if (c >= e.N) return;
   int s = e.didx[c - k];
+  if (e.defl[s] == 2) return;  // deflated by a rotation: the rotation kernel wrote it
   int q = e.rank_defl[s];
   double sc = om.colscale ? om.colscale[q] : 1.0;
   const double* src = X + (long long)e.perm[s] * ldx;
@@ -566,20 +554,6 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += err;
 }
 
-// Exact FP32 -> FP64 widening through the IEEE-754 bit fields: the exponent is re-biased
-// (1023 - 127 = 896) and the 23 fraction bits move up by 29.  FP32 subnormals (below
-// 1.2e-38) become signed zeros; Inf and NaN keep their class.  Integer work only, so the
-// conversion of an output tile stays off the FP64 pipe.
-__device__ __forceinline__ double widen_f32(float x) {
-  const uint32_t u = __float_as_uint(x);
-  const uint32_t mag = u & 0x7fffffffu;
-  unsigned long long d = (unsigned long long)(u & 0x80000000u) << 32;
-  if (mag >= 0x7f800000u)
-    d |= 0x7ff0000000000000ull | ((unsigned long long)(mag & 0x007fffffu) << 29);
-  else if (mag >= 0x00800000u)
-    d |= ((unsigned long long)mag << 29) + (896ull << 52);
-  return __longlong_as_double((long long)d);
-}
 
 
 // Roles: warps 0-7 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) .., i.e.

@@ -84,18 +84,24 @@ __global__ void __launch_bounds__(1024) k_rot_prep(Eig e, RotScratch w) {
 // The chunk's rotations, staged once per block.
 struct RotChunkSm {
   long long a[kRotChunk], b[kRotChunk];
+  long long ya[kRotChunk];  // output column of the deflated a (the product's OutMap)
   float4 cs[kRotChunk];
-  double c[kRotChunk], s[kRotChunk];
+  double c[kRotChunk], s[kRotChunk], ysc[kRotChunk];
   unsigned char chained[kRotChunk], ends[kRotChunk];
 };
 
 __device__ __forceinline__ int stage_chunk(Eig e, long long ldx, const float4* rotf, int c0,
-                                           int nr, RotChunkSm& sm) {
+                                           int nr, RotChunkSm& sm, const OutMap* om) {
   const int cn = min(kRotChunk, nr - c0);
   for (int i = threadIdx.x; i < cn; i += blockDim.x) {
     const int g = c0 + i;
     sm.a[i] = (long long)e.perm[e.rj[g]] * ldx;
     sm.b[i] = (long long)e.perm[e.ri[g]] * ldx;
+    if (om) {  // the deflated column goes straight to its output column
+      const int q = e.rank_defl[e.rj[g]];
+      sm.ya[i] = (om->out_rev ? (long long)(om->out_n - 1 - q) : (long long)q) * om->ldy;
+      sm.ysc[i] = om->colscale ? om->colscale[q] : 1.0;
+    }
     sm.c[i] = e.rc[g];
     sm.s[i] = e.rs[g];
     sm.cs[i] = rotf[g];
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __rest
   const int nr = e.nrot[0];
   const int ch = blockIdx.y, c0 = ch * kRotChunk;
   if (c0 >= nr) return;
-  const int cn = stage_chunk(e, ldx, w.rotf, c0, nr, sm);
+  const int cn = stage_chunk(e, ldx, w.rotf, c0, nr, sm, nullptr);
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   double B = 0.0, xlast = 0.0;
@@ -134,8 +140,8 @@ __global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __rest
           B = fma(sm.s[i], sm.chained[i] ? B : xa[u], sm.c[i] * xb[u]);
         } else {
           const float4 q = sm.cs[i];
-          const Df uu = sm.chained[i] ? Bf : Df{(float)xa[u], 0.f};
-          Bf = df_add(df_mul(Df{q.z, q.w}, uu), df_mul(Df{q.x, q.y}, Df{(float)xb[u], 0.f}));
+          const Df uu = sm.chained[i] ? Bf : Df{narrow_rn(xa[u]), 0.f};
+          Bf = df_add(df_mul(Df{q.z, q.w}, uu), df_mul(Df{q.x, q.y}, Df{narrow_rn(xb[u]), 0.f}));
         }
         xlast = xb[u];
       }
@@ -177,12 +183,12 @@ __global__ void k_rot_carry(Eig e, int rows, RotScratch w) {
 
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_rot_apply(Eig e, double* X, long long ldx, int rows,
-                                                   RotScratch w) {
+                                                   RotScratch w, OutMap om) {
   __shared__ RotChunkSm sm;
   const int nr = e.nrot[0];
   const int ch = blockIdx.y, c0 = ch * kRotChunk;
   if (c0 >= nr) return;
-  const int cn = stage_chunk(e, ldx, w.rotf, c0, nr, sm);
+  const int cn = stage_chunk(e, ldx, w.rotf, c0, nr, sm, &om);
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const size_t o = (size_t)ch * rows + r;
@@ -211,17 +217,18 @@ __global__ void __launch_bounds__(128) k_rot_apply(Eig e, double* X, long long l
       if (i < cn) {
         if (!MIXED) {
           const double uu = sm.chained[i] ? v : xa[u];
-          X[r + sm.a[i]] = fma(sm.c[i], uu, -sm.s[i] * xb[u]);
+          om.Y[r + sm.ya[i]] = sm.ysc[i] * fma(sm.c[i], uu, -sm.s[i] * xb[u]);
           v = fma(sm.s[i], uu, sm.c[i] * xb[u]);
           if (sm.ends[i]) X[r + sm.b[i]] = v;
         } else {
           const float4 q = sm.cs[i];
-          const Df cc = {q.x, q.y}, ss = {q.z, q.w}, xx = {(float)xb[u], 0.f};
-          const Df uu = sm.chained[i] ? vf : Df{(float)xa[u], 0.f};
+          const Df cc = {q.x, q.y}, ss = {q.z, q.w}, xx = {narrow_rn(xb[u]), 0.f};
+          const Df uu = sm.chained[i] ? vf : Df{narrow_rn(xa[u]), 0.f};
           const Df out = df_add(df_mul(cc, uu), df_mul(Df{-ss.hi, -ss.lo}, xx));
-          X[r + sm.a[i]] = (double)(out.hi + out.lo);
+          const float ov = out.hi + out.lo;
+          om.Y[r + sm.ya[i]] = widen_f32(sm.ysc[i] < 0.0 ? -ov : ov);
           vf = df_add(df_mul(ss, uu), df_mul(cc, xx));
-          if (sm.ends[i]) X[r + sm.b[i]] = (double)(vf.hi + vf.lo);
+          if (sm.ends[i]) X[r + sm.b[i]] = widen_f32(vf.hi + vf.lo);
         }
       }
     }
@@ -235,7 +242,7 @@ size_t rotate_scratch_bytes(int N, int rows) {
 }
 
 void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
-                           void* scratch, bool mixed) {
+                           void* scratch, bool mixed, OutMap om) {
   const int nch = (e.N + kRotChunk - 1) / kRotChunk;
   const size_t rr = (size_t)(rows > 0 ? rows : 1);
   RotScratch w;
@@ -256,8 +263,8 @@ void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int
   if (mixed) k_rot_carry<true><<<(rows + 127) / 128, 128, 0, st>>>(e, rows, w);
   else k_rot_carry<false><<<(rows + 127) / 128, 128, 0, st>>>(e, rows, w);
   SVDUP_COUNT_LAUNCH();
-  if (mixed) k_rot_apply<true><<<g, 128, 0, st>>>(e, X, ldx, rows, w);
-  else k_rot_apply<false><<<g, 128, 0, st>>>(e, X, ldx, rows, w);
+  if (mixed) k_rot_apply<true><<<g, 128, 0, st>>>(e, X, ldx, rows, w, om);
+  else k_rot_apply<false><<<g, 128, 0, st>>>(e, X, ldx, rows, w, om);
   SVDUP_COUNT_LAUNCH();
 }
 
@@ -278,6 +285,7 @@ __global__ void k_gather_columns(Eig e, const double* __restrict__ X, long long 
     for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = src[r];
   } else if (c < e.N) {
     int s = e.didx[c - k];
+    if (e.defl[s] == 2) return;  // written by the rotation kernel
     int q = e.rank_defl[s];
     double sc = om.colscale ? om.colscale[q] : 1.0;
     const double* src = X + (long long)e.perm[s] * ldx;

@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate_post(Eig e, int in_
         const int pj = kpos[i - 1], pi = kpos[i];
         e.ds[pj] = (cs * cs * dprev + sn * sn * di) * idsc;
         e.zs[pj] = 0.0;
-        e.defl[pj] = 1;
+        e.defl[pj] = 2;  // deflated by a rotation: the rotation kernel writes its column
         e.rj[ridx] = pj; e.ri[ridx] = pi; e.rc[ridx] = cs; e.rs[ridx] = sn;
         ridx++;
         W = Wn;
