@@ -48,6 +48,28 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(r, e, r);
 }
 
+// 1/sqrt(x) for a positive normal double, the same way: x = m 2^(e - eo) with m in [1, 4)
+// (e - eo even), an FP32 rsqrt.approx of m, the exponent halved by the bit fields, then
+// two FP64 Newton steps y <- y + y (1 - x y^2) / 2 (2^-22 -> 2^-44 -> rounding).  Other
+// inputs take CUDA's square root and division.
+__device__ __forceinline__ double rsqrt64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0 || ex == 0x7ff || (b >> 63)) return 1.0 / sqrt(x);
+  const int e = ex - 1023, eo = e & 1;
+  const float m = __int_as_float(((127 + eo) << 23) | (int)((b >> 29) & 0x7fffffu));
+  float rm;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rm) : "f"(m));  // in (0.5, 1]
+  const unsigned um = __float_as_uint(rm);
+  const long long de = (long long)((um >> 23) & 0xffu) + 896 - (e - eo) / 2;
+  double y = __longlong_as_double((long long)(((unsigned long long)de << 52) |
+                                              ((unsigned long long)(um & 0x7fffffu) << 29)));
+  double h = fma(-(x * y), y, 1.0);
+  y = fma(0.5 * y, h, y);
+  h = fma(-(x * y), y, 1.0);
+  return fma(0.5 * y, h, y);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

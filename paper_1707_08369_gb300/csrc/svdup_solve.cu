@@ -591,11 +591,11 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate_post(Eig e, int in_
         M = z2 * di;
       } else {
         // rotation merging survivor i-1 (the carrier) into i
-        const double zprev = brk[i - 1] ? kz[i - 1] : sqrt(W);  // signed at a run start
+        const double zprev = brk[i - 1] ? kz[i - 1] : W * rsqrt64(W);  // signed at a run start
         const double Wn = W + z2;
-        const double irn = 1.0 / sqrt(Wn);
+        const double irn = rsqrt64(Wn);
         const double cs = zi * irn, sn = zprev * irn;
-        const double dprev = M / W;
+        const double dprev = M * rcp64(W);
         const int pj = kpos[i - 1], pi = kpos[i];
         e.ds[pj] = (cs * cs * dprev + sn * sn * di) * idsc;
         e.zs[pj] = 0.0;
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate_post(Eig e, int in_
       }
       if (!(i + 1 < nk && !brk[i + 1])) {  // not merged away by the next pair
         const int ps = kpos[i];
-        if (p) { e.ds[ps] = (M / W) * idsc; e.zs[ps] = sqrt(W) * izsc; }
+        if (p) { e.ds[ps] = (M * rcp64(W)) * idsc; e.zs[ps] = (W * rsqrt64(W)) * izsc; }
         else { e.ds[ps] = di * idsc; e.zs[ps] = zi * izsc; }
       }
     }
@@ -1374,10 +1374,13 @@ __device__ __forceinline__ long long ordered_key(double v) {
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 
-__global__ void __launch_bounds__(64) k_merge_count(Eig e) {
+constexpr int kMergeLanes = 8;  // threads per eigenvalue, each counting a strided slice
+
+__global__ void __launch_bounds__(256) k_merge_count(Eig e) {
   __shared__ long long sv[kMergeChunk];
   const int N = e.N, k = e.kp[0], nd = N - k;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = threadIdx.x % kMergeLanes;
+  const int x = (blockIdx.x * blockDim.x + threadIdx.x) / kMergeLanes;
   const bool root = x < k;
   double val = 0.0;
   if (x < N) val = root ? e.dorg[x] + e.tau[x] : e.ds[e.didx[x - k]];
@@ -1391,17 +1394,19 @@ __global__ void __launch_bounds__(64) k_merge_count(Eig e) {
     __syncthreads();
     if (x < N) {
       if (root) {
-        for (int t = 0; t < cn; t++) cnt += (sv[t] <= key);
+        for (int t = q; t < cn; t += kMergeLanes) cnt += (sv[t] <= key);
       } else {
         const int lim = me - c0;  // equal values rank by position in didx
-        for (int t = 0; t < cn; t++) {
+        for (int t = q; t < cn; t += kMergeLanes) {
           const long long w = sv[t];
           cnt += (w < key) || (w == key && t < lim);
         }
       }
     }
   }
-  if (x >= N) return;
+#pragma unroll
+  for (int o = kMergeLanes / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (x >= N || q != 0) return;
   if (root) {
     const int r = x + cnt;
     e.lam[r] = val;
@@ -1419,7 +1424,8 @@ __global__ void __launch_bounds__(64) k_merge_count(Eig e) {
 }
 
 void launch_merge(cudaStream_t st, Eig e) {
-  k_merge_count<<<(e.N + 63) / 64, 64, 0, st>>>(e);
+  const long long threads = (long long)e.N * kMergeLanes;
+  k_merge_count<<<(int)((threads + 255) / 256), 256, 0, st>>>(e);
   SVDUP_COUNT_LAUNCH();
 }
 
