@@ -233,6 +233,23 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def recorded_traffic(n, mode_name):
+    """DRAM bytes per launch of the output-stage kernel from the committed ncu summary
+    (profiles/umma_out_traffic.json), if it was taken on this workload and the kernel
+    source is unchanged since (SHA-256 of csrc/svdup_mixed.cu); else None."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "umma_out_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, "paper_1707_08369_gb300", "csrc", "svdup_mixed.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except Exception:
+        return None
+    if rec.get("source_sha256") != sha or rec.get("n") != n or rec.get("mode") != mode_name:
+        return None
+    return rec.get("bytes_per_launch")
+
+
 def fp64_peak_tflops(sm_mhz):
     """FP64 (DFMA) peak from unit counts and clock: 152 SMs x 2 DFMA per SM per clock
     x 2 flops (1.26 TFLOP/s at 2070 MHz)."""
@@ -556,7 +573,8 @@ def main():
         useful = (dom_fl / max(dom_cnt, 1)) / per_launch_s / 1e12
         roofline = {"kernel": "k_umma<%s>" % stage_names[dom], "bound": "tensor",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "useful_tflops": useful,
+                    "traffic": recorded_traffic(n, args.mode) if dom == "out" else None,
+                    "useful_tflops": useful,
                     "peak_source": "bf16_tflops_sustained of %s MEASURED_PEAKS.json (kernel timed "
                                    "inside a long step); achieved counts the six split BF16 "
                                    "products executed; launch duration from the stage timers of "
