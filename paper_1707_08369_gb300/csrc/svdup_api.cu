@@ -66,9 +66,12 @@ struct svdup_ctx {
   // product-path choices (set by svdup_autotune; defaults below): index 0 FP64, 1 mixed
   int dense_max[2];   // N <= dense_max: dense Cauchy product (no far field)
   int leaf128_min[2]; // N >= leaf128_min: leaves of 128 poles, else 64
-  // the right-hand problem of an update runs on `side`, beside the left-hand one
+  // the right-hand problem of an update runs on `side`, beside the left-hand one; the
+  // products of each side run on prod[0] (U) and prod[1] (V)
   cudaStream_t side;
+  cudaStream_t prod[2];
   cudaEvent_t ev_fork, ev_mid, ev_join;
+  cudaEvent_t ev[6];  // e1 ready, e2 ready, e3 ready, signs ready, U done, V done
 };
 
 namespace {
@@ -426,17 +429,17 @@ void queue_product_mixed(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPla
 // ---------------------------------------------------------------------------
 // The side stream and the three events of the two-stream update.
 int make_side(svdup_ctx* h) {
-  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&h->prod[0], cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&h->prod[1], cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < 6; i++)
+    ok = ok && cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
-    h->side = nullptr;
-    return SVDUP_ECUDA;
-  }
-  if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    cudaStreamDestroy(h->side);
-    h->side = nullptr;
+    h->side = nullptr;  // the update then runs on one stream
     return SVDUP_ECUDA;
   }
   return SVDUP_OK;
@@ -445,9 +448,14 @@ int make_side(svdup_ctx* h) {
 void free_side(svdup_ctx* h) {
   if (!h->side) return;
   cudaStreamSynchronize(h->side);
+  cudaStreamSynchronize(h->prod[0]);
+  cudaStreamSynchronize(h->prod[1]);
   cudaEventDestroy(h->ev_fork);
   cudaEventDestroy(h->ev_mid);
   cudaEventDestroy(h->ev_join);
+  for (int i = 0; i < 6; i++) cudaEventDestroy(h->ev[i]);
+  cudaStreamDestroy(h->prod[0]);
+  cudaStreamDestroy(h->prod[1]);
   cudaStreamDestroy(h->side);
   h->side = nullptr;
 }
@@ -804,21 +812,26 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   stage_begin(h, SVDUP_STAGE_GEMV);
   launch_gemv_pq(st, m, n, U, ldu, V, ldv, a, b, u.p, u.q, u.ab);
   stage_end(h);
-  // The left-hand problem (E1, E2, U) runs on the handle's stream, the right-hand one
-  // (E3, E4, V) on the side stream; they meet once, where the sign pairing hands the
-  // left vectors' sums to the right.  With stage timing on, both run on one stream.
-  const bool side = !h->timing && h->side;
-  cudaStream_t sR = side ? h->side : st;
-  if (side) {
-    if (cudaEventRecord(h->ev_fork, st) != cudaSuccess ||
-        cudaStreamWaitEvent(sR, h->ev_fork, 0) != cudaSuccess)
-      return SVDUP_ECUDA;
-  }
+  // Streams: the left-hand solves (E1, E2) on the handle's stream, the right-hand ones
+  // (E3, E4) on the side stream, the products with U on prod[0] and with V on prod[1].
+  // A side's first product needs only its first solve, so it runs beside the second
+  // solve; the V side's second product waits for the sign pairing, which hands the left
+  // vectors' sums to the right.  With stage timing on, everything runs on one stream.
+  const bool multi = !h->timing && h->side;
+  cudaStream_t sR = multi ? h->side : st;
+  cudaStream_t pU = multi ? h->prod[0] : st;
+  cudaStream_t pV = multi ? h->prod[1] : st;
+  auto hand = [&](cudaEvent_t ev, cudaStream_t from, cudaStream_t to) -> bool {
+    return !multi || (cudaEventRecord(ev, from) == cudaSuccess &&
+                      cudaStreamWaitEvent(to, ev, 0) == cudaSuccess);
+  };
+  if (!hand(h->ev_fork, st, sR)) return SVDUP_ECUDA;
   stage_begin(h, SVDUP_STAGE_SOLVE);
   // STEPs 3, 6: first right solve; STEP 7: second right solve
   launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
   queue_solve(h, sR, u.E3);
   launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4);
+  if (!hand(h->ev[2], sR, pV)) return SVDUP_ECUDA;  // E3 ready: V's first product
   launch_fill_second(sR, u.E4, u.E3.lam, u.zsec4);
   queue_solve(h, sR, u.E4, mixed);
   launch_norms(sR, u.E4, nullptr, nullptr, mixed);
@@ -827,25 +840,10 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   launch_fill_left(st, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
   queue_solve(h, st, u.E1);
   launch_apply_qt(st, u.E1, u.z2p, u.ysortL, u.zsec2);
+  if (!hand(h->ev[0], st, pU)) return SVDUP_ECUDA;  // E1 ready: U's first product
   launch_fill_second(st, u.E2, u.E1.lam, u.zsec2);
   queue_solve(h, st, u.E2, mixed);
   launch_norms(st, u.E2, nullptr, nullptr, mixed);
-  stage_end(h);
-  // sign pairing of right vectors with left vectors (before S is overwritten); in the
-  // mixed mode its sums run on FP32 pairs (only the signs are used)
-  stage_begin(h, SVDUP_STAGE_SIGN);
-  launch_fill_ones(st, m, u.ones);
-  launch_apply_q(st, u.E2, u.ones, u.work, u.g1, mixed);
-  launch_apply_q(st, u.E1, u.g1, u.work, u.g, mixed);
-  launch_sign_combine(st, m, n, S, u.p, u.q, u.g, u.yv);
-  if (side) {
-    if (cudaEventRecord(h->ev_mid, st) != cudaSuccess ||
-        cudaStreamWaitEvent(sR, h->ev_mid, 0) != cudaSuccess)
-      return SVDUP_ECUDA;
-  }
-  launch_apply_qt(sR, u.E3, u.yv, u.ysortR, u.h1, mixed);
-  launch_apply_qt(sR, u.E4, u.h1, u.ysortR, u.h, mixed);
-  launch_sign_finish(sR, m, n, u.h, u.sign);
   stage_end(h);
   // products: U -> W -> U (descending), V -> W -> V (descending, signed)
   OutMap om1 = {u.WL, (long long)m, m, 0, nullptr};
@@ -853,21 +851,37 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   OutMap om3 = {u.WR, (long long)n, n, 0, nullptr};
   OutMap om4 = {V, (long long)ldv, n, 1, u.sign};
   if (mixed) {
-    queue_product_mixed(h, st, u.E1, u.FL, u.ML, m, U, ldu, om1, mode);
-    queue_product_mixed(h, st, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
-    queue_product_mixed(h, sR, u.E3, u.FR, u.MR, n, V, ldv, om3, mode);
-    queue_product_mixed(h, sR, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
+    queue_product_mixed(h, pU, u.E1, u.FL, u.ML, m, U, ldu, om1, mode);
+    queue_product_mixed(h, pV, u.E3, u.FR, u.MR, n, V, ldv, om3, mode);
   } else {
-    queue_product(h, st, u.E1, u.FL, m, U, ldu, u.XsL, om1, mode);
-    queue_product(h, st, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
-    queue_product(h, sR, u.E3, u.FR, n, V, ldv, u.XsR, om3, mode);
-    queue_product(h, sR, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
+    queue_product(h, pU, u.E1, u.FL, m, U, ldu, u.XsL, om1, mode);
+    queue_product(h, pV, u.E3, u.FR, n, V, ldv, u.XsR, om3, mode);
   }
-  if (side) {
-    if (cudaEventRecord(h->ev_join, sR) != cudaSuccess ||
-        cudaStreamWaitEvent(st, h->ev_join, 0) != cudaSuccess)
-      return SVDUP_ECUDA;
+  if (!hand(h->ev[1], st, pU)) return SVDUP_ECUDA;  // E2 ready: U's second product
+  // sign pairing of right vectors with left vectors (before S is overwritten); in the
+  // mixed mode its sums run on FP32 pairs (only the signs are used)
+  stage_begin(h, SVDUP_STAGE_SIGN);
+  launch_fill_ones(st, m, u.ones);
+  launch_apply_q(st, u.E2, u.ones, u.work, u.g1, mixed);
+  launch_apply_q(st, u.E1, u.g1, u.work, u.g, mixed);
+  launch_sign_combine(st, m, n, S, u.p, u.q, u.g, u.yv);
+  if (!hand(h->ev_mid, st, sR)) return SVDUP_ECUDA;
+  // (the stored norms of E3 and E4 stay: V's products read them, possibly meanwhile)
+  launch_apply_qt(sR, u.E3, u.yv, u.ysortR, u.h1, mixed, true);
+  launch_apply_qt(sR, u.E4, u.h1, u.ysortR, u.h, mixed, true);
+  launch_sign_finish(sR, m, n, u.h, u.sign);
+  stage_end(h);
+  if (!hand(h->ev[3], sR, pV)) return SVDUP_ECUDA;  // E4 and the signs: V's second product
+  if (mixed) {
+    queue_product_mixed(h, pU, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
+    queue_product_mixed(h, pV, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
+  } else {
+    queue_product(h, pU, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
+    queue_product(h, pV, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
   }
+  // join before STEP 8 (it overwrites S, which the right-hand fill and the signs read)
+  if (!hand(h->ev[4], pU, st) || !hand(h->ev[5], pV, st) || !hand(h->ev_join, sR, st))
+    return SVDUP_ECUDA;
   // STEP 8
   launch_sqrt_desc(st, m, u.E2.lam, S, h->status);
   return check_launch();

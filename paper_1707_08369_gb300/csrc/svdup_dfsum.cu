@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(1024) k_df_prep(Eig e, const double* __restric
 
 // Column norms (and Q^T y when ysorted is set): one warp per root j.
 __global__ void __launch_bounds__(256) k_norms_df(Eig e, const double* __restrict__ ysorted,
-                                                  double* out_final) {
+                                                  double* out_final, int keep_inv) {
   const int k = e.kp[0];
   const int E = e.fsc[0], Z = e.fsc[1], Y = e.fsc[2];
   const int lane = threadIdx.x & 31;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) k_norms_df(Eig e, const double* __restric
     }
     if (lane == 0) {
       const double inv = 1.0 / sqrt(S2);
-      e.inv[j] = inv;
+      if (!keep_inv) e.inv[j] = inv;
       if (ysorted) out_final[e.rank_root[j]] = SY * inv;
     }
   }
@@ -253,10 +253,10 @@ void launch_loewner_df(cudaStream_t st, Eig e) {
 }
 
 void launch_norms_df(cudaStream_t st, Eig e, const double* ysorted, double* out_final,
-                     int blocks) {
+                     int blocks, bool keep_inv) {
   k_df_prep<<<1, 1024, 0, st>>>(e, ysorted, nullptr);
   SVDUP_COUNT_LAUNCH();
-  k_norms_df<<<blocks, 256, 0, st>>>(e, ysorted, out_final);
+  k_norms_df<<<blocks, 256, 0, st>>>(e, ysorted, out_final, keep_inv ? 1 : 0);
   SVDUP_COUNT_LAUNCH();
 }
 

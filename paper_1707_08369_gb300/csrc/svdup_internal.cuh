@@ -245,13 +245,16 @@ void launch_loewner(cudaStream_t st, Eig e);
 void launch_loewner_df(cudaStream_t st, Eig e);
 // pairs = true: the sums in double-float arithmetic (svdup_dfsum.cu), for outputs that
 // need FP32 accuracy only (the mixed mode's vectors and signs)
+// keep_inv: the stored 1/||c_j|| stay as they are (the norms are recomputed for the
+// product only), for calls that may run beside a product reading them
 void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final,
-                  bool pairs = false);
+                  bool pairs = false, bool keep_inv = false);
 void launch_apply_qt(cudaStream_t st, Eig e, const double* xphys, double* work, double* out_final,
-                     bool pairs = false);
+                     bool pairs = false, bool keep_inv = false);
 void launch_apply_q(cudaStream_t st, Eig e, const double* xfinal, double* work, double* yphys,
                     bool pairs = false);
-void launch_norms_df(cudaStream_t st, Eig e, const double* ysorted, double* out_final, int blocks);
+void launch_norms_df(cudaStream_t st, Eig e, const double* ysorted, double* out_final, int blocks,
+                     bool keep_inv = false);
 void launch_apply_q_core_df(cudaStream_t st, Eig e, const double* xfinal, double* vsorted,
                             int blocks);
 void launch_sign_combine(cudaStream_t st, int m, int n, const double* S, const double* p,

@@ -1503,7 +1503,7 @@ void launch_loewner(cudaStream_t st, Eig e) {
 // fused with the transposed product out[rank(j)] = (1/||c_j||) sum_t zhat_t y_t / delta_tj
 // when a vector y (sorted, rotated basis) is given.  One warp per root j.
 // ---------------------------------------------------------------------------
-__global__ void k_norms(Eig e, const double* __restrict__ ysorted, double* out_final) {
+__global__ void k_norms(Eig e, const double* __restrict__ ysorted, double* out_final, int keep_inv) {
   const int k = e.kp[0];
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -1520,7 +1520,7 @@ __global__ void k_norms(Eig e, const double* __restrict__ ysorted, double* out_f
     if (ysorted) sy = warp_sum(sy);
     if (lane == 0) {
       double inv = 1.0 / sqrt(s2);
-      e.inv[j] = inv;
+      if (!keep_inv) e.inv[j] = inv;
       if (ysorted) out_final[e.rank_root[j]] = sy * inv;
     }
   }
@@ -1534,11 +1534,12 @@ __global__ void k_defl_copy(Eig e, const double* __restrict__ ysorted, double* o
   }
 }
 
-void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final, bool pairs) {
+void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final, bool pairs,
+                  bool keep_inv) {
   if (pairs) {
-    launch_norms_df(st, e, ysorted, out_final, secular_blocks(e.N));
+    launch_norms_df(st, e, ysorted, out_final, secular_blocks(e.N), keep_inv);
   } else {
-    k_norms<<<secular_blocks(e.N), 256, 0, st>>>(e, ysorted, out_final);
+    k_norms<<<secular_blocks(e.N), 256, 0, st>>>(e, ysorted, out_final, keep_inv ? 1 : 0);
     SVDUP_COUNT_LAUNCH();
   }
   if (ysorted) {
@@ -1668,13 +1669,13 @@ __global__ void __launch_bounds__(1024) k_gather_rotate(Eig e, const double* __r
 }
 
 void launch_apply_qt(cudaStream_t st, Eig e, const double* xphys, double* work, double* out_final,
-                     bool pairs) {
+                     bool pairs, bool keep_inv) {
   size_t sm = vec_smem(e.N);
   cudaFuncSetAttribute(k_gather_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_gather_rotate<<<1, 1024, sm, st>>>(e, xphys, work, sm > 0 ? 1 : 0);
   SVDUP_COUNT_LAUNCH();
   // the norms are recomputed (identical values in FP64); only the product is wanted here
-  launch_norms(st, e, work, out_final, pairs);
+  launch_norms(st, e, work, out_final, pairs, keep_inv);
 }
 
 __global__ void k_apply_q_core(Eig e, const double* __restrict__ xfinal, double* vsorted) {
