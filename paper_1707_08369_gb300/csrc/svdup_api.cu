@@ -122,6 +122,13 @@ Eig make_eig(Arena& ar, int N) {
   e.rank_root = ar.take<int>(n);
   e.rank_defl = ar.take<int>(n);
   e.tol = ar.take<double>(1);
+  e.sd = ar.take<double>(n);
+  e.sz = ar.take<double>(n);
+  e.spos = ar.take<int>(n);
+  e.sbrk = ar.take<unsigned char>(n);
+  e.srix = ar.take<int>(n);
+  e.skix = ar.take<int>(n);
+  e.srs = ar.take<int>(n);
   e.dmask = ar.take<unsigned>((n + 31) / 32 + 1);
   e.dint = ar.take<int>(4);
   e.dflt = ar.take<double>(4);

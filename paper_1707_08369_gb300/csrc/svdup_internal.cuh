@@ -91,7 +91,7 @@ __device__ __forceinline__ double warp_max(double v) {
 // in device memory.  N is known on the host; k (the non-deflated count) lives on the
 // device so that nothing waits on the host between stages.
 // ---------------------------------------------------------------------------
-constexpr int kMaxOverrunList = 256;  // deflation: listed chain overruns (svdup_solve.cu)
+constexpr int kMaxOverrunList = 256;  // deflation: walking ranges (svdup_solve.cu)
 
 struct Eig {
   int N;
@@ -129,8 +129,17 @@ struct Eig {
   int* rank_root;  // root j -> final index
   int* rank_defl;  // sorted position s (deflated) -> final index, else -1
   double* tol;     // deflation tolerance (1 value)
-  // deflation scratch: candidate bitmask (N / 32 words), survivor count and listed
-  // overruns (dint), scaled tolerance and scalings (dflt), the overrun list
+  // deflation scratch: the survivors of case (1) (scaled d and z, sorted positions, run
+  // flags, rotation index, kept index, run start), the candidate bitmask (N / 32 + 1
+  // words), the survivor count (dint), scaled tolerance and scalings (dflt), and per
+  // walking range the run it carried into the next range (head, carrier)
+  double* sd;
+  double* sz;
+  int* spos;
+  unsigned char* sbrk;
+  int* srix;
+  int* skix;
+  int* srs;
   unsigned* dmask;
   int* dint;
   double* dflt;

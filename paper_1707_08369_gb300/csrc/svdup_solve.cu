@@ -207,65 +207,44 @@ void launch_fill_generic(cudaStream_t st, Eig e, const double* d, const double* 
 //           removed when the dropped coupling |(d_s - d_j) c s| <= tol.
 //  (The paper's case (2), |abar| = 1, is the special case of (1) where z is a unit
 //  coordinate vector.)  tol = 8 u max(max|d|, |rho| ||z||^2).
-// One block.  Reductions, case (1) and the compaction of its survivors run in
-// parallel.  Case (3) on consecutive survivors (i-1, i): a rotation merges pole i-1
-// into pole i, and the next pair (i, i+1) sees the merged values.  Along a run of
-// merges starting at i0 the carrier after i holds
+// Case (3) runs on consecutive survivors of case (1) (i-1, i): a rotation merges
+// survivor i-1 into i, and the next pair (i, i+1) sees the merged values.  Along a run
+// of merges starting at i0 the carrier after i holds
 //     z~_i^2 = sum_{t=i0..i} z_t^2   and   d~_i = sum z_t^2 d_t / z~_i^2
 // (each Givens step is a z^2-weighted mean), so the sequential test reduces to
 //     |d_i - d~_{i-1}| |z_i| z~_{i-1} <= tol (z~_{i-1}^2 + z_i^2).
-// Only pairs that pass with the original values (a bitmask found in parallel) can start
-// a run, so the maximal chains of such pairs are walked in parallel by the block's
-// warps, on shared-memory copies with just these two running sums, 32 pairs per step;
-// the rare run that reaches into the next chain is resumed in order afterwards, so the
-// boundaries are those of the sequential walk.  The rotation records (position pair,
-// cos, sin) and the merged values are then formed in parallel from segmented prefix
-// sums of z^2 and z^2 d over the runs.  This is the Bunch-Nielsen-Sorensen deflation
-// in exact arithmetic; only the rounding of the merged values differs from applying
-// the rotations one at a time.
+// Five launches.  An FP64 instruction costs as much as about 60 FP32 ones on this GPU,
+// so per-pole FP64 work runs on many SMs and the single-block steps do integer work:
+//  pre   (one block)  reductions, tol, case (1), the survivors' positions;
+//  bits  (many)       scaled survivors and the candidate bitmask: the pairs that pass
+//                     with the original values, the only places a run can start;
+//  walk  (many)       the run boundaries: warp w walks the chains (maximal sequences
+//                     of candidate pairs) whose first pair lies in its range of
+//                     survivors, in order, as the sequential walk does;
+//  fix   (one block)  a run that the previous range's walk carried into a range's
+//                     first chain is resumed there, until the resumed walk starts a
+//                     run where the range's own walk started one; then the rotation
+//                     and kept indices and the compaction;
+//  rec   (many)       the rotation records and merged values, from segmented sums of
+//                     z^2 and z^2 d over the runs.
+// The run boundaries are those of the sequential walk (in this arithmetic); only the
+// rounding of the merged values differs from applying the rotations one at a time.
 // ---------------------------------------------------------------------------
 constexpr int kDeflateThreads = 1024;
-constexpr int kMaxOverrun = kMaxOverrunList;  // chains entered by the previous chain's run
+constexpr int kDeflRecThreads = 256;
+constexpr int kDeflRange = 128;  // survivors per walking warp (at least; see defl_range)
 
-// Block-wide exclusive prefix sum of one int per thread (Hillis-Steele over scnt);
-// returns the exclusive prefix and writes the total to *total.
-__device__ int block_excl_scan(int v, int* scnt, int* total) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  scnt[tid] = v;
-  __syncthreads();
-  for (int off = 1; off < nt; off <<= 1) {
-    int u = tid >= off ? scnt[tid - off] : 0;
-    __syncthreads();
-    scnt[tid] += u;
-    __syncthreads();
-  }
-  int incl = scnt[tid];
-  *total = scnt[nt - 1];
-  __syncthreads();
-  return incl - v;
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// Segmented inclusive scan over the threads' chunks of (flag, W, M): a chunk with
-// flag set starts a new run at or after its start.  Returns the (W, M) of the run
-// through the element just before the calling thread's chunk.
-__device__ void run_carry(int lflag, double lW, double lM, int* sflag, double* sW, double* sM,
-                          double* cW, double* cM) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  sflag[tid] = lflag;
-  sW[tid] = lW;
-  sM[tid] = lM;
-  __syncthreads();
-  for (int off = 1; off < nt; off <<= 1) {
-    int f2 = 0;
-    double W2 = 0.0, M2 = 0.0;
-    if (tid >= off) { f2 = sflag[tid - off]; W2 = sW[tid - off]; M2 = sM[tid - off]; }
-    __syncthreads();
-    if (tid >= off && !sflag[tid]) { sW[tid] += W2; sM[tid] += M2; sflag[tid] = f2; }
-    __syncthreads();
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
   }
-  *cW = tid > 0 ? sW[tid - 1] : 0.0;
-  *cM = tid > 0 ? sM[tid - 1] : 0.0;
-  __syncthreads();
+  return v;
 }
 
 // The merge test of survivor i against the carrier (W = z~^2, M = W d~) of the run
@@ -279,25 +258,24 @@ __device__ __forceinline__ bool merges(double di, double zi, double W, double M,
   return g * g * zi2 <= tol2 * W * s * s;
 }
 
-// The case-(3) walk on the survivors (scaled d and z, the candidate bitmask and the run
-// flags brk, all in global scratch); every member is warp-collective.
+// The sequential walk over the survivors (scaled d and z, the candidate bitmask, the
+// run-start flags); every member is warp-collective.
 struct DeflWalk {
-  const unsigned* cmask;  // bit i: pair (i-1, i) passes with the original values
   const double* kd;
   const double* kz;
-  unsigned char* brk;     // 1: survivor i starts a run
+  const unsigned* cm;   // bit i: pair (i-1, i) passes with the original values
+  unsigned char* brk;   // 1: survivor i starts a run
   int nk;
   double tol2;
-  __device__ bool bit(int i) const { return i < nk && ((cmask[i >> 5] >> (i & 31)) & 1u); }
-  // first position >= from whose bit equals want (nk if none)
-  __device__ int next_bit(int from, bool want, int lane) const {
-    if (from >= nk) return nk;
+
+  // first i >= from with bit i set (nk if none)
+  __device__ int next_set(int from, int lane) const {
     const int nw = (nk + 31) >> 5;
-    for (int w0 = from >> 5; w0 < nw; w0 += 32) {
+    for (int w0 = from >> 5; w0 < nw && from < nk; w0 += 32) {
       const int w = w0 + lane;
       unsigned m = 0u;
       if (w < nw) {
-        m = want ? cmask[w] : ~cmask[w];
+        m = cm[w];
         if (w == (from >> 5)) m &= 0xffffffffu << (from & 31);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
@@ -309,355 +287,506 @@ struct DeflWalk {
     }
     return nk;
   }
-  // Walks the chain with first pair h up to pole lim (the pole before the next chain's
-  // first pair, or nk - 1); returns 1 if the last run merged pole lim and a chain
-  // follows, with the carrier in (W, M).
-  __device__ int walk(int h, int lim, bool have, double& W, double& M, int lane) const {
-    int pos = h;
-    int ppos = -1;  // the window whose values are already loaded (next_z, next_d)
-    double next_z = 0.0, next_d = 0.0;
+  // first chain head h >= from (bit h set, bit h - 1 clear); nk if none
+  __device__ int first_head(int from, int lane) const {
+    const int nw = (nk + 31) >> 5;
+    for (int w0 = from >> 5; w0 < nw && from < nk; w0 += 32) {
+      const int w = w0 + lane;
+      unsigned hm = 0u;
+      if (w < nw) {
+        const unsigned m = cm[w];
+        const unsigned prev = w > 0 ? cm[w - 1] : 0u;
+        hm = m & ~((m << 1) | (prev >> 31));
+        if (w == (from >> 5)) hm &= 0xffffffffu << (from & 31);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, hm != 0u);
+      if (bal) {
+        const int src = __ffs(bal) - 1;
+        const unsigned mm = __shfl_sync(0xffffffffu, hm, src);
+        return min(nk, ((w0 + src) << 5) + __ffs(mm) - 1);
+      }
+    }
+    return nk;
+  }
+  // resumed walk: the first q in [a, b) whose flag is set (b if none); flags a .. that q
+  // (or b - 1) are set, since those survivors now start runs of one
+  __device__ int restart_span(int a, int b, int lane) const {
+    for (int x0 = a; x0 < b; x0 += 32) {
+      const int x = x0 + lane;
+      const bool was = x < b && brk[x] != 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, was);
+      const int q = bal ? x0 + __ffs(bal) - 1 : b;
+      if (x < b && x < q) brk[x] = 1;
+      if (bal) return q;
+    }
+    return b;
+  }
+
+  // The sequential rule from survivor pos (pos <= lim): a run in progress merges survivor
+  // i when the carrier test passes, else i starts a new run; a run of one at i - 1 can
+  // only grow where bit i is set, so stretches without bits are skipped.  The carrier of
+  // the run through pos - 1 is (W, M), or with fresh the run is survivor pos - 1 alone.
+  // One step tests a window of 32 survivors (pos's aligned window): lane l against the
+  // carrier that exists if every earlier lane merged (the carrier plus the lanes'
+  // exclusive prefix sums of z^2 and z^2 d), which is the sequential carrier up to the
+  // first lane that fails; a failing lane starts a run, and the rest of the window is
+  // tested again from it without reloading.  A run of one gets its carrier by the same
+  // operations as the bitmask (0 + z^2 and z^2 d), so the two agree.
+  // Plain walk (RESUME false): stops at survivor lim; returns lim + 1 when the run merged
+  // lim (its carrier in oW, oM: it continues into the next range), else -1.
+  // RESUME: lim = nk - 1; flags are rewritten, and the walk stops at the first survivor
+  // where it starts a run whose flag was already set (there it agrees with the plain
+  // walk that wrote the flags); returns that survivor, or nk.
+  template <bool RESUME>
+  __device__ int walk(int pos, bool fresh, double W, double M, int lim, int lane, double& oW,
+                      double& oM) const {
+    int pw = -1;  // the window whose values are already loaded (prefetched)
+    double pz = 0.0, pd = 0.0;
+    unsigned pword = 0u;
     while (true) {
-      if (!have) {
-        const double zj = kz[pos - 1];
-        W = zj * zj;
-        M = W * kd[pos - 1];
+      const int w0 = pos & ~31;
+      double zi, di;
+      unsigned word;
+      if (pw == w0) {
+        zi = pz;
+        di = pd;
+        word = pword;
+      } else {
+        const int i = w0 + lane;
+        zi = i < nk ? kz[i] : 0.0;
+        di = i < nk ? kd[i] : 0.0;
+        word = cm[w0 >> 5];
       }
-      const int i = pos + lane;
-      const int nin = min(32, lim - pos + 1);
-      double zi = 0.0, di = 0.0;
-      if (ppos == pos) {
-        zi = next_z;
-        di = next_d;
-      } else if (lane < nin) {
-        zi = kz[i];
-        di = kd[i];
-      }
-      // the next window, if the whole of this one merges, loads while this one is tested
-      ppos = pos + 32;
-      next_z = 0.0;
-      next_d = 0.0;
-      if (ppos + lane <= lim) {
-        next_z = kz[ppos + lane];
-        next_d = kd[ppos + lane];
+      pw = w0 + 32;  // the next window loads while this one is tested
+      if (pw < nk) {
+        const int i = pw + lane;
+        pz = i < nk ? kz[i] : 0.0;
+        pd = i < nk ? kd[i] : 0.0;
+        pword = cm[pw >> 5];
       }
       const double z2 = zi * zi, dz = z2 * di;
-      double iz2 = z2, idz = dz;  // inclusive prefix over the lanes
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const double a2 = __shfl_up_sync(0xffffffffu, iz2, o);
-        const double ad = __shfl_up_sync(0xffffffffu, idz, o);
-        if (lane >= o) { iz2 += a2; idz += ad; }
+      int start = pos - w0;  // lanes >= start are tested
+      int src = start;       // lanes >= src are in the run, after the carrier (Wb, Mb)
+      double Wb = W, Mb = M;
+      if (fresh) {  // the run is survivor pos - 1 alone, which lies in this window
+        src = start - 1;
+        Wb = 0.0;
+        Mb = 0.0;
       }
-      const bool ok = lane < nin && merges(di, zi, W + (iz2 - z2), M + (idz - dz), tol2);
-      const unsigned fail = __ballot_sync(0xffffffffu, !ok);
-      const int nm = fail ? __ffs(fail) - 1 : 32;  // lanes that merge
-      if (lane < nm) brk[i] = 0;
-      if (nm == nin) {  // every pole of the window merged
-        W += __shfl_sync(0xffffffffu, iz2, nm - 1);
-        M += __shfl_sync(0xffffffffu, idz, nm - 1);
-        have = true;
-        pos += nm;
-        if (pos > lim) return lim + 1 < nk ? 1 : 0;
-      } else {  // pole pos + nm failed: a new run only if its pair with the next passes
-        have = false;
-        pos += nm + 1;
-        if (pos > lim || !bit(pos)) return 0;
+      const int last = min(31, lim - w0);
+      while (true) {
+        double v2 = lane >= src ? z2 : 0.0, vd = lane >= src ? dz : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const double a2 = __shfl_up_sync(0xffffffffu, v2, o);
+          const double ad = __shfl_up_sync(0xffffffffu, vd, o);
+          if (lane >= o) { v2 += a2; vd += ad; }
+        }
+        double e2 = __shfl_up_sync(0xffffffffu, v2, 1), ed = __shfl_up_sync(0xffffffffu, vd, 1);
+        if (lane == 0) { e2 = 0.0; ed = 0.0; }
+        const bool act = lane >= start && lane <= last;
+        const bool ok = act && merges(di, zi, Wb + e2, Mb + ed, tol2);
+        const unsigned fail = __ballot_sync(0xffffffffu, act && !ok);
+        const int f = fail ? __ffs(fail) - 1 : last + 1;
+        if (lane >= start && lane < f) brk[w0 + lane] = 0;
+        if (!fail) {  // every tested lane merged
+          const double Wn = Wb + __shfl_sync(0xffffffffu, v2, last);
+          const double Mn = Mb + __shfl_sync(0xffffffffu, vd, last);
+          if (w0 + last >= lim) {
+            if (RESUME) return nk;
+            oW = Wn;
+            oM = Mn;
+            return lim + 1 < nk ? lim + 1 : -1;
+          }
+          W = Wn;
+          M = Mn;
+          fresh = false;
+          pos = w0 + 32;
+          break;
+        }
+        const int p = w0 + f;  // survivor p starts a run
+        if (RESUME) {
+          if (brk[p]) return p;
+          __syncwarp();
+          if (lane == 0) brk[p] = 1;
+        }
+        if (p >= lim) return RESUME ? nk : -1;
+        const unsigned above = f < 31 ? (word >> (f + 1)) : 0u;
+        const int h = above ? p + __ffs(above) : next_set(w0 + 32, lane);  // the next bit
+        if (RESUME && h > p + 1) {
+          const int q = restart_span(p + 1, h, lane);
+          if (q < h) return q;
+        }
+        if (h > lim) return RESUME ? nk : -1;
+        if (h < w0 + 32) {  // a run of one at h - 1 in this window
+          src = h - 1 - w0;
+          start = h - w0;
+          Wb = 0.0;
+          Mb = 0.0;
+          continue;
+        }
+        pos = h;
+        if (h & 31) {
+          fresh = true;
+        } else if (h == w0 + 32) {  // survivor h - 1 is this window's last lane
+          fresh = false;
+          W = __shfl_sync(0xffffffffu, z2, 31);
+          M = __shfl_sync(0xffffffffu, dz, 31);
+        } else {
+          fresh = false;
+          const double zj = kz[h - 1];
+          W = zj * zj;
+          M = W * kd[h - 1];
+        }
+        break;
       }
     }
   }
 };
 
-// Deflation, part 1 (one block): tolerance and scalings, case (1), the survivors'
-// scaled d and z and sorted positions, the case-(3) candidate bitmask.
+// Deflation, part 1 (one block): tolerance and scalings, case (1), the survivors' sorted
+// positions in order.
 __global__ void __launch_bounds__(kDeflateThreads) k_deflate_pre(Eig e, int* status) {
-  __shared__ double sred[3][32];
-  __shared__ int scnt[kDeflateThreads];
-  __shared__ double s_tol, s_zn, s_dsc, s_zsc;
+  __shared__ double sred[32];
+  __shared__ unsigned long long sdm[32], szm[32];
+  __shared__ int swc[32];
+  __shared__ double s_tol, s_zn;
   const int N = e.N;
   const double rho = e.rhop[0];
-  int tid = threadIdx.x, nt = blockDim.x;
-  double zn2 = 0.0, dmax = 0.0, zmax = 0.0;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  double zn2 = 0.0;
+  unsigned long long dm = 0ull, zm = 0ull;  // max |d|, max |z| by their bit patterns
   for (int s = tid; s < N; s += nt) {
-    double z = e.zs[s], d = e.ds[s];
+    const double z = e.zs[s];
     zn2 = fma(z, z, zn2);
-    dmax = fmax(dmax, fabs(d));
-    zmax = fmax(zmax, fabs(z));
+    dm = max(dm, abs_bits(e.ds[s]));
+    zm = max(zm, abs_bits(z));
   }
   zn2 = warp_sum(zn2);
-  dmax = warp_max(dmax);
-  zmax = warp_max(zmax);
-  if ((tid & 31) == 0) { sred[0][tid >> 5] = zn2; sred[1][tid >> 5] = dmax; sred[2][tid >> 5] = zmax; }
+  dm = warp_max_u64(dm);
+  zm = warp_max_u64(zm);
+  if (lane == 0) { sred[wid] = zn2; sdm[wid] = dm; szm[wid] = zm; }
   __syncthreads();
-  if (tid < 32) {
-    int nw = nt >> 5;
-    zn2 = tid < nw ? sred[0][tid] : 0.0;
-    dmax = tid < nw ? sred[1][tid] : 0.0;
-    zmax = tid < nw ? sred[2][tid] : 0.0;
+  if (wid == 0) {
+    const int nw = nt >> 5;
+    zn2 = lane < nw ? sred[lane] : 0.0;
+    dm = lane < nw ? sdm[lane] : 0ull;
+    zm = lane < nw ? szm[lane] : 0ull;
     zn2 = warp_sum(zn2);
-    dmax = warp_max(dmax);
-    zmax = warp_max(zmax);
-    if (tid == 0) {
-      double t = fabs(rho) * zn2;
+    dm = warp_max_u64(dm);
+    zm = warp_max_u64(zm);
+    if (lane == 0) {
+      const double dmax = __longlong_as_double((long long)dm);
+      const double zmax = __longlong_as_double((long long)zm);
+      const double t = fabs(rho) * zn2;
       s_tol = 8.0 * kU * fmax(dmax, t);
       s_zn = sqrt(zn2);
       // exact power-of-two scalings that bring max|d| and max|z| near 1 for the merge test
-      s_dsc = (dmax > 0.0 && isfinite(dmax)) ? ldexp(1.0, -ilogb(dmax)) : 1.0;
-      s_zsc = (zmax > 0.0 && isfinite(zmax)) ? ldexp(1.0, -ilogb(zmax)) : 1.0;
+      const double dsc = (dmax > 0.0 && isfinite(dmax)) ? ldexp(1.0, -ilogb(dmax)) : 1.0;
+      const double zsc = (zmax > 0.0 && isfinite(zmax)) ? ldexp(1.0, -ilogb(zmax)) : 1.0;
+      const double tolS = s_tol * dsc;
       e.tol[0] = s_tol;
+      e.dflt[0] = tolS * tolS;
+      e.dflt[1] = dsc;
+      e.dflt[2] = zsc;
       if (!isfinite(s_tol) || !isfinite(rho)) latch(status, SVDUP_ENONFINITE);
     }
   }
   __syncthreads();
-  const double tol = s_tol, zn = s_zn, dsc = s_dsc, zsc = s_zsc;
-  const double tolS = tol * dsc, tol2 = tolS * tolS;
-  const int nwords = (N + 31) >> 5;
-  unsigned* cmask = e.dmask;
-  double* kd = e.dk;  // survivors' d * dsc (scratch: the compaction rewrites dk, zk, idx)
-  double* kz = e.zk;  // survivors' z * zsc
-  int* kpos = e.idx;  // survivors' sorted positions
-  unsigned char* brk = (unsigned char*)e.didx;
-  for (int w = tid; w < nwords; w += nt) cmask[w] = 0u;
-  // case (1) on my contiguous chunk [b0, b1), then the survivors' positions in order
-  const int chunk = (N + nt - 1) / nt;
-  const int b0 = min(N, tid * chunk), b1 = min(N, b0 + chunk);
-  int cnt = 0;
-  for (int s = b0; s < b1; s++) {
-    int d1 = (rho == 0.0 || fabs(rho) * zn * fabs(e.zs[s]) <= tol) ? 1 : 0;
-    e.defl[s] = d1;
-    cnt += !d1;
+  const double tol = s_tol;
+  const double c1 = fabs(rho) * s_zn;
+  int base = 0;
+  for (int s0 = 0; s0 < N; s0 += nt) {
+    const int s = s0 + tid;
+    bool surv = false;
+    if (s < N) {
+      const int d1 = (rho == 0.0 || c1 * fabs(e.zs[s]) <= tol) ? 1 : 0;
+      e.defl[s] = d1;
+      surv = !d1;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, surv);
+    if (lane == 0) swc[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < (nt >> 5); w++) {
+      const int c = swc[w];
+      off += w < wid ? c : 0;
+      tot += c;
+    }
+    if (surv) e.spos[base + off + __popc(bal & ((1u << lane) - 1u))] = s;
+    base += tot;
+    __syncthreads();
   }
-  int nk;
-  int pos = block_excl_scan(cnt, scnt, &nk);
-  for (int s = b0; s < b1; s++) {
-    if (e.defl[s]) continue;
-    kpos[pos] = s;
-    kd[pos] = e.ds[s] * dsc;
-    kz[pos] = e.zs[s] * zsc;
-    pos++;
+  if (tid == 0) e.dint[0] = base;
+}
+
+// Deflation, part 2 (a thread per survivor): scaled d and z, run flags, candidate bits.
+__global__ void k_deflate_bits(Eig e) {
+  const int nk = e.dint[0];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nwords = (nk + 31) >> 5;
+  if ((i >> 5) > nwords) return;  // warp-uniform
+  const double tol2 = e.dflt[0], dsc = e.dflt[1], zsc = e.dflt[2];
+  bool ok = false;
+  if (i < nk) {
+    const int s = e.spos[i];
+    const double di = e.ds[s] * dsc, zi = e.zs[s] * zsc;
+    e.sd[i] = di;
+    e.sz[i] = zi;
+    e.sbrk[i] = 1;
+    if (i > 0) {
+      const int sp = e.spos[i - 1];
+      const double dj = e.ds[sp] * dsc, zj = e.zs[sp] * zsc;
+      const double W = zj * zj;
+      ok = merges(di, zi, W, W * dj, tol2);
+    }
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, ok);
+  if ((threadIdx.x & 31) == 0) e.dmask[i >> 5] = bal;
+}
+
+// Deflation, part 3 (a warp per range of R survivors): the chains whose first pair lies
+// in the range, walked in order from a run of one at the first chain's first survivor,
+// up to the pole before the next range's first chain.  A run that merged that pole is
+// listed (slot = the range) with its carrier.
+__global__ void __launch_bounds__(32) k_deflate_walk(Eig e, int R) {
+  const int nk = e.dint[0];
+  const int lane = threadIdx.x;
+  const int slot = blockIdx.x;
+  const int r0 = slot * R;
+  int ov = -1;
+  double oW = 0.0, oM = 0.0;
+  if (r0 < nk) {
+    const DeflWalk dw = {e.sd, e.sz, e.dmask, e.sbrk, nk, e.dflt[0]};
+    const int r1 = min(nk, r0 + R);
+    const int h0 = dw.first_head(r0, lane);
+    if (h0 < r1) {
+      const int H = dw.first_head(r1, lane);
+      double W = 0.0, M = 0.0;
+      bool fresh = (h0 & 31) != 0;
+      if (!fresh) {
+        const double zj = e.sz[h0 - 1];
+        W = zj * zj;
+        M = W * e.sd[h0 - 1];
+      }
+      ov = dw.walk<false>(h0, fresh, W, M, H - 1, lane, oW, oM);
+    }
+  }
+  if (lane == 0) {
+    e.ovh[slot] = ov;
+    e.ovW[slot] = oW;
+    e.ovM[slot] = oM;
+  }
+}
+
+// Deflation, part 4 (one block): the listed runs resumed in order (one warp); then the
+// rotation index of every merge, the kept index of every run end, each survivor's run
+// start, the final flags and the kept and deflated position lists.
+__global__ void __launch_bounds__(kDeflateThreads) k_deflate_fix(Eig e, int nslots) {
+  __shared__ int sov[kMaxOverrunList];
+  __shared__ int sc_m[32], sc_e[32], sc_r[32];
+  const int N = e.N;
+  const int nk = e.dint[0];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  unsigned char* brk = e.sbrk;
+  for (int s = tid; s < nslots; s += nt) sov[s] = e.ovh[s];
+  __syncthreads();
+  if (wid == 0) {
+    const DeflWalk dw = {e.sd, e.sz, e.dmask, brk, nk, e.dflt[0]};
+    int done = -1;
+    for (int s = 0; s < nslots; s++) {
+      const int H = sov[s];
+      if (H < 0 || H <= done) continue;  // none, or redone by an earlier resume
+      double oW, oM;
+      done = dw.walk<true>(H, false, e.ovW[s], e.ovM[s], nk - 1, lane, oW, oM);
+    }
   }
   __syncthreads();
-  // case (3) pre-test with the original values: the candidate pairs
-  for (int i = tid; i < nk; i += nt) {
-    if (i > 0) {
-      const double zj = kz[i - 1];
-      const double W = zj * zj;
-      if (merges(kd[i], kz[i], W, W * kd[i - 1], tol2)) atomicOr(&cmask[i >> 5], 1u << (i & 31));
+  const unsigned lt = (1u << lane) - 1u;
+  int base_m = 0, base_e = 0, carry_r = 0;
+  for (int i0 = 0; i0 < nk; i0 += nt) {
+    const int i = i0 + tid;
+    const bool in = i < nk;
+    const bool b = in ? brk[i] != 0 : true;
+    const bool m = in && !b;
+    const bool en = in && (i + 1 >= nk || brk[i + 1] != 0);
+    int rs = (in && b) ? i : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, rs, o);
+      if (lane >= o) rs = max(rs, t);
     }
-    brk[i] = 1;
+    const unsigned bm = __ballot_sync(0xffffffffu, m), be = __ballot_sync(0xffffffffu, en);
+    if (lane == 31) { sc_m[wid] = __popc(bm); sc_e[wid] = __popc(be); sc_r[wid] = rs; }
+    __syncthreads();
+    int om = base_m, oe = base_e, orr = carry_r, tm = 0, te = 0, tr = carry_r;
+    for (int w = 0; w < (nt >> 5); w++) {
+      const int cm_ = sc_m[w], ce = sc_e[w], cr = sc_r[w];
+      if (w < wid) { om += cm_; oe += ce; orr = max(orr, cr); }
+      tm += cm_;
+      te += ce;
+      tr = max(tr, cr);
+    }
+    if (in) {
+      const int ps = e.spos[i];
+      e.srs[i] = max(orr, rs);
+      if (m) e.srix[i] = om + __popc(bm & lt);
+      if (en) {
+        const int kx = oe + __popc(be & lt);
+        e.skix[i] = kx;
+        e.idx[kx] = ps;
+      }
+      e.defl[ps] = en ? 0 : 2;  // 2: deflated by a rotation (the rotation kernel writes its column)
+    }
+    base_m += tm;
+    base_e += te;
+    carry_r = tr;
+    __syncthreads();
+  }
+  int base_d = 0;
+  for (int s0 = 0; s0 < N; s0 += nt) {
+    const int s = s0 + tid;
+    const bool dd = s < N && e.defl[s] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, dd);
+    if (lane == 0) sc_m[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < (nt >> 5); w++) {
+      const int c = sc_m[w];
+      off += w < wid ? c : 0;
+      tot += c;
+    }
+    if (dd) e.didx[base_d + off + __popc(bal & lt)] = s;
+    base_d += tot;
+    __syncthreads();
   }
   if (tid == 0) {
-    e.dint[0] = nk;
-    e.dint[1] = 0;  // listed overruns
-    e.dflt[0] = tol2;
-    e.dflt[1] = dsc;
-    e.dflt[2] = zsc;
+    e.kp[0] = base_e;
+    e.nrot[0] = base_m;
   }
 }
 
-// Deflation, part 2 (many blocks): run boundaries, as the sequential walk finds them.
-// Runs start only at pairs that pass with the original values (set bits of the
-// bitmask); a chain is a maximal sequence of such pairs.  A run may continue past its
-// chain's end through poles whose pairs fail alone but pass with the run's carrier, up
-// to the pole before the next chain's first pair.  Global warp w walks the chains whose
-// first pair lies in bitmask words w, w + W, ... from a fresh carrier, exactly as the
-// sequential walk enters them, unless the previous chain's last run reached the next
-// chain's first pole ("overran"); such chains are listed with the carrier for part 3.
-// A warp steps 32 pairs at a time: from position pos with carrier (W, M), lane l tests
-// pair (pos + l - 1, pos + l) against the carrier that exists if every earlier lane
-// merged (W, M plus the lanes' exclusive prefix sums of z^2 and z^2 d): exactly the
-// sequential carrier up to the first lane that fails.  Earlier lanes merge; a failing
-// pole starts a new run with the next pair if that pair passes alone.
-__global__ void __launch_bounds__(256) k_deflate_walk(Eig e) {
+// Deflation, part 5 (a thread per survivor): the carrier before each survivor from a
+// segmented scan of (z^2, z^2 d) over the block plus the sum over the part of its run
+// before the block; rotation records (position pair, cos, sin), rotated values, merged
+// run ends, the kept set and its rho > 0 orientation for the solver (d -> -d, reversed,
+// when rho < 0).
+__global__ void __launch_bounds__(kDeflRecThreads) k_deflate_rec(Eig e) {
+  __shared__ double sW[kDeflRecThreads], sM[kDeflRecThreads];
+  __shared__ int sF[kDeflRecThreads];
+  __shared__ double rW[kDeflRecThreads / 32], rM[kDeflRecThreads / 32];
   const int nk = e.dint[0];
-  const DeflWalk dw = {e.dmask, e.dk, e.zk, (unsigned char*)e.didx, nk, e.dflt[0]};
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int nw = (nk + 31) >> 5;
-  for (int w = gw; w < nw; w += nwarps) {
-    const unsigned m = dw.cmask[w];
-    const unsigned prev = (w > 0) ? (dw.cmask[w - 1] >> 31) : 0u;
-    unsigned heads = m & ~((m << 1) | prev);  // first pair of each chain
-    while (heads) {
-      const int h = (w << 5) + __ffs(heads) - 1;
-      heads &= heads - 1;
-      const int nh = dw.next_bit(dw.next_bit(h, false, lane), true, lane);  // next chain
-      double W = 0.0, M = 0.0;
-      if (dw.walk(h, nh - 1, false, W, M, lane) && lane == 0) {
-        const int q = atomicAdd(&e.dint[1], 1);
-        if (q < kMaxOverrun) { e.ovh[q] = nh; e.ovW[q] = W; e.ovM[q] = M; }
-      }
-    }
-  }
-}
-
-// Deflation, part 3 (one block): the listed overruns resumed in order (one warp,
-// cascading while runs keep overrunning; beyond kMaxOverrun listed, the whole walk again,
-// sequentially), then the rotation records, the merged values and the compaction.
-__global__ void __launch_bounds__(kDeflateThreads) k_deflate_post(Eig e, int in_smem) {
-  extern __shared__ double dsm[];
-  __shared__ int scnt[kDeflateThreads];
-  __shared__ double sW[kDeflateThreads], sM[kDeflateThreads];
-  const int N = e.N;
-  const double rho = e.rhop[0];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int nk = e.dint[0];
-  const double dsc = e.dflt[1], zsc = e.dflt[2];
+  const int i0 = blockIdx.x * blockDim.x;
+  if (i0 >= nk) return;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x;
+  const int i = i0 + tid;
+  const bool in = i < nk;
+  const double rho = e.rhop[0], dsc = e.dflt[1], zsc = e.dflt[2];
   const double idsc = 1.0 / dsc, izsc = 1.0 / zsc;  // exact: powers of two
-  const double* kd = e.dk;
-  const double* kz = e.zk;
-  const int* kpos = e.idx;
-  unsigned char* brk = (unsigned char*)e.didx;
-  if (in_smem) {  // the sequential resumes and the records read these many times
-    double* skd = dsm;
-    double* skz = dsm + N;
-    unsigned char* sbrk = (unsigned char*)(dsm + 2 * (size_t)N);
-    for (int i = tid; i < nk; i += nt) {
-      skd[i] = kd[i];
-      skz[i] = kz[i];
-      sbrk[i] = brk[i];
+  // the run entering the block: survivors rs .. i0 - 1
+  const int rs = e.srs[i0];
+  double cW = 0.0, cM = 0.0;
+  if (rs < i0) {
+    for (int t = rs + tid; t < i0; t += nt) {
+      const double z = e.sz[t], z2 = z * z;
+      cW += z2;
+      cM = fma(z2, e.sd[t], cM);
     }
+    cW = warp_sum(cW);
+    cM = warp_sum(cM);
+    if (lane == 0) { rW[wid] = cW; rM[wid] = cM; }
     __syncthreads();
-    kd = skd;
-    kz = skz;
-    brk = sbrk;
+    cW = 0.0;
+    cM = 0.0;
+    for (int w = 0; w < (nt >> 5); w++) { cW += rW[w]; cM += rM[w]; }
   }
-  const int nov = e.dint[1];
-  if (tid < 32 && nov > 0) {
-    const int lane = tid;
-    const DeflWalk dw = {e.dmask, kd, kz, brk, nk, e.dflt[0]};
-    if (nov > kMaxOverrun) {
-      for (int i = lane; i < nk; i += 32) brk[i] = 1;
-      __syncwarp();
-      int h = dw.next_bit(1, true, lane);
-      bool have = false;
-      double W = 0.0, M = 0.0;
-      while (h < nk) {
-        const int nh = dw.next_bit(dw.next_bit(h, false, lane), true, lane);
-        have = dw.walk(h, nh - 1, have, W, M, lane) != 0;
-        h = nh;
-      }
-    } else {
-      if (lane == 0)  // ascending chain order (a short list)
-        for (int x = 1; x < nov; x++)
-          for (int y = x; y > 0 && e.ovh[y - 1] > e.ovh[y]; y--) {
-            const int th = e.ovh[y]; e.ovh[y] = e.ovh[y - 1]; e.ovh[y - 1] = th;
-            const double tw = e.ovW[y]; e.ovW[y] = e.ovW[y - 1]; e.ovW[y - 1] = tw;
-            const double tm = e.ovM[y]; e.ovM[y] = e.ovM[y - 1]; e.ovM[y - 1] = tm;
-          }
-      __syncwarp();
-      int done = 0;  // chains before this position hold their final boundaries
-      for (int x = 0; x < nov; x++) {
-        int h = e.ovh[x];
-        if (h <= done) continue;  // listed by a chain that a resumed walk redid
-        double W = e.ovW[x], M = e.ovM[x];
-        while (true) {  // resume the sequential walk at chain h
-          const int nh = dw.next_bit(dw.next_bit(h, false, lane), true, lane);
-          for (int i = h + lane; i < nh; i += 32) brk[i] = 1;
-          __syncwarp();
-          const int more = dw.walk(h, nh - 1, true, W, M, lane);
-          done = nh;
-          if (!more) break;
-          h = nh;
-        }
-      }
-    }
-  }
+  const double zi = in ? e.sz[i] : 0.0, di = in ? e.sd[i] : 0.0;
+  const bool b = in ? e.sbrk[i] != 0 : true;
+  const double z2 = zi * zi;
+  // inclusive segmented scan over the block (flag: a run starts at or after the element)
+  double w = z2, m = z2 * di;
+  int f = b ? 1 : 0;
+  sW[tid] = w;
+  sM[tid] = m;
+  sF[tid] = f;
   __syncthreads();
-  const int cpt = (nk + nt - 1) / nt;
-  const int c0 = min(nk, tid * cpt), c1 = min(nk, c0 + cpt);
-  const int chunk = (N + nt - 1) / nt;
-  const int b0 = min(N, tid * chunk), b1 = min(N, b0 + chunk);
-  int cnt, pos;
-  // rotation records and merged values from the runs (segmented sums again)
-  {
-    double lW = 0.0, lM = 0.0;
-    int lflag = 0, lrot = 0;
-    for (int i = c0; i < c1; i++) {
-      const double z2 = kz[i] * kz[i];
-      if (brk[i]) { lflag = 1; lW = z2; lM = z2 * kd[i]; }
-      else { lW += z2; lM = fma(z2, kd[i], lM); lrot++; }
-    }
-    int nrot;
-    const int rbase = block_excl_scan(lrot, scnt, &nrot);
-    double W, M;
-    run_carry(lflag, lW, lM, scnt, sW, sM, &W, &M);
-    int ridx = rbase;
-    for (int i = c0; i < c1; i++) {
-      const bool p = !brk[i];
-      const double zi = kz[i], di = kd[i], z2 = zi * zi;
-      if (!p) {
-        W = z2;
-        M = z2 * di;
-      } else {
-        // rotation merging survivor i-1 (the carrier) into i
-        const double zprev = brk[i - 1] ? kz[i - 1] : W * rsqrt64(W);  // signed at a run start
-        const double Wn = W + z2;
-        const double irn = rsqrt64(Wn);
-        const double cs = zi * irn, sn = zprev * irn;
-        const double dprev = M * rcp64(W);
-        const int pj = kpos[i - 1], pi = kpos[i];
-        e.ds[pj] = (cs * cs * dprev + sn * sn * di) * idsc;
-        e.zs[pj] = 0.0;
-        e.defl[pj] = 2;  // deflated by a rotation: the rotation kernel writes its column
-        e.rj[ridx] = pj; e.ri[ridx] = pi; e.rc[ridx] = cs; e.rs[ridx] = sn;
-        ridx++;
-        W = Wn;
-        M = fma(z2, di, M);
-      }
-      if (!(i + 1 < nk && !brk[i + 1])) {  // not merged away by the next pair
-        const int ps = kpos[i];
-        if (p) { e.ds[ps] = (M * rcp64(W)) * idsc; e.zs[ps] = (W * rsqrt64(W)) * izsc; }
-        else { e.ds[ps] = di * idsc; e.zs[ps] = zi * izsc; }
-      }
-    }
-    if (tid == 0) e.nrot[0] = nrot;
+  for (int off = 1; off < nt; off <<= 1) {
+    double w2 = 0.0, m2 = 0.0;
+    int f2 = 0;
+    if (tid >= off) { w2 = sW[tid - off]; m2 = sM[tid - off]; f2 = sF[tid - off]; }
+    __syncthreads();
+    if (tid >= off && !f) { w += w2; m += m2; f = f2; }
+    sW[tid] = w;
+    sM[tid] = m;
+    sF[tid] = f;
+    __syncthreads();
   }
-  __syncthreads();
-  // compaction of the kept set
-  cnt = 0;
-  for (int s = b0; s < b1; s++) cnt += !e.defl[s];
-  int kk;
-  pos = block_excl_scan(cnt, scnt, &kk);  // kept entries before my chunk
-  int dpos = b0 - pos;                     // deflated entries before my chunk
-  for (int s = b0; s < b1; s++) {
-    if (!e.defl[s]) {
-      e.idx[pos] = s;
-      e.dk[pos] = e.ds[s];
-      e.zk[pos] = e.zs[s];
-      pos++;
+  if (!f) { w += cW; m += cM; }  // the run began before the block
+  // the carrier through i - 1
+  double Wp = cW, Mp = cM;
+  if (tid > 0) {
+    Wp = sW[tid - 1];
+    Mp = sM[tid - 1];
+    if (!sF[tid - 1]) { Wp += cW; Mp += cM; }
+  }
+  if (!in) return;
+  if (!b) {  // rotation merging survivor i - 1 (the carrier) into i
+    const double zprev = e.sbrk[i - 1] ? e.sz[i - 1] : Wp * rsqrt64(Wp);  // signed at a run start
+    const double Wn = Wp + z2;
+    const double irn = rsqrt64(Wn);
+    const double cs = zi * irn, sn = zprev * irn;
+    const double dprev = Mp * rcp64(Wp);
+    const int pj = e.spos[i - 1], pi = e.spos[i];
+    e.ds[pj] = (cs * cs * dprev + sn * sn * di) * idsc;
+    e.zs[pj] = 0.0;
+    const int r = e.srix[i];
+    e.rj[r] = pj;
+    e.ri[r] = pi;
+    e.rc[r] = cs;
+    e.rs[r] = sn;
+  }
+  if (i + 1 >= nk || e.sbrk[i + 1]) {  // a run end: kept
+    const int ps = e.spos[i];
+    double dv, zv;
+    if (!b) {
+      dv = (m * rcp64(w)) * idsc;
+      zv = (w * rsqrt64(w)) * izsc;
     } else {
-      e.didx[dpos++] = s;
+      dv = di * idsc;
+      zv = zi * izsc;
     }
+    e.ds[ps] = dv;
+    e.zs[ps] = zv;
+    const int kx = e.skix[i];
+    e.dk[kx] = dv;
+    e.zk[kx] = zv;
+    const int kk = e.kp[0];
+    const int t = rho > 0.0 ? kx : kk - 1 - kx;
+    e.dc[t] = rho > 0.0 ? dv : -dv;
+    e.z2c[t] = zv * zv;
   }
-  if (tid == 0) e.kp[0] = kk;
-  __syncthreads();
-  // the rho > 0 orientation for the solver: reflect d -> -d (reversed) when rho < 0
-  for (int t = tid; t < kk; t += nt) {
-    if (rho > 0.0) {
-      e.dc[t] = e.dk[t];
-      double z = e.zk[t];
-      e.z2c[t] = z * z;
-    } else {
-      e.dc[t] = -e.dk[kk - 1 - t];
-      double z = e.zk[kk - 1 - t];
-      e.z2c[t] = z * z;
-    }
-  }
+}
+
+// survivors per walking warp: at least kDeflRange, and few enough ranges for the slots
+static int defl_range(int N) {
+  int R = kDeflRange;
+  while ((N + R - 1) / R > kMaxOverrunList) R *= 2;
+  return R;
 }
 
 void launch_deflate(cudaStream_t st, Eig e, int* status) {
+  const int N = e.N;
   k_deflate_pre<<<1, kDeflateThreads, 0, st>>>(e, status);
   SVDUP_COUNT_LAUNCH();
-  const int nwords = (e.N + 31) / 32;
-  k_deflate_walk<<<std::max(1, (nwords + 7) / 8), 256, 0, st>>>(e);  // a warp per bitmask word
+  k_deflate_bits<<<(N + 32 + 255) / 256, 256, 0, st>>>(e);
   SVDUP_COUNT_LAUNCH();
-  // the survivors' d, z and run flags in shared memory when they fit (static: 20 KB)
-  const size_t smem = (size_t)e.N * (2 * sizeof(double) + 1) + 16;
-  const int in_smem = smem <= 200 * 1024 ? 1 : 0;
-  cudaFuncSetAttribute(k_deflate_post, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       in_smem ? (int)smem : 0);
-  k_deflate_post<<<1, kDeflateThreads, in_smem ? smem : 0, st>>>(e, in_smem);
+  const int R = defl_range(N);
+  const int nslots = std::max(1, (N + R - 1) / R);
+  k_deflate_walk<<<nslots, 32, 0, st>>>(e, R);
+  SVDUP_COUNT_LAUNCH();
+  k_deflate_fix<<<1, kDeflateThreads, 0, st>>>(e, nslots);
+  SVDUP_COUNT_LAUNCH();
+  k_deflate_rec<<<std::max(1, (N + kDeflRecThreads - 1) / kDeflRecThreads), kDeflRecThreads, 0, st>>>(e);
   SVDUP_COUNT_LAUNCH();
 }
 

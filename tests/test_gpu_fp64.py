@@ -98,6 +98,37 @@ def test_rank_one_eig_vs_oracle(sv, hnd, orc, N, sgn, case, seed):
     assert np.all(np.abs(inv - ref["inv_norm"]) <= 1e-10 * np.abs(ref["inv_norm"]))
 
 
+@pytest.mark.parametrize("seed", [0, 1])
+def test_rank_one_eig_long_chains(sv, hnd, orc, seed):
+    """The first eigen-problem of a square n = 8192 update with sigma log-uniform in
+    [1e-4, 1]: poles sigma^2, z Gaussian, rho = ||b||^2 (about n).  Then tol = 8 u rho
+    ||z||^2 is about 6e-8, so the lowest few thousand poles form one chain of candidate
+    pairs holding a run of about 2000 merges, and the walk's ranges hand runs across
+    their boundaries.  The deflated set is compared exactly."""
+    g = wl.rng(wl.BASE_SEED + 90 + seed)
+    n = 8192
+    d = np.sort(wl.loguniform_sigma(n, g)) ** 2
+    z = g.standard_normal(n)
+    b = g.standard_normal(n)
+    rho = float(b @ b)
+    ref = orc.rank_one_compact(d, z, rho)
+    assert n - ref["k"] > 3000  # the workload deflates heavily
+    out = hnd.rank_one_eig(dev(d), dev(z), rho)
+    k = int(out["k"].item())
+    assert k == ref["k"]
+    assert np.array_equal(out["idx"].cpu().numpy()[:k], ref["idx"])
+    # A kept pole that carries a run of L merged poles is their z^2-weighted mean; both
+    # sides sum it in their own order, so they agree to the summation bound L u max|d_t|
+    # over the run (the run's last pole is its largest).
+    idx = ref["idx"]
+    L = np.diff(idx, prepend=-1)
+    dk = out["dk"].cpu().numpy()[:k]
+    assert np.all(np.abs(dk - ref["dk"]) <= 16 * U53 * np.abs(ref["dk"]) + 2 * L * U53 * d[idx])
+    assert L.max() > 1000
+    lam_g = out["lam"].cpu().numpy()
+    assert np.abs(lam_g - ref["lam"]).max() <= 1e-13 * np.abs(ref["lam"]).max()
+
+
 # ------------------------------------------------------------------ Cauchy product
 @pytest.mark.parametrize("rows,N,mode_dense,seed,spread", [(7, 33, True, 0, "u"), (130, 200, True, 1, "u"),
                                                            (96, 700, False, 2, "u"), (257, 1500, False, 3, "g"),
