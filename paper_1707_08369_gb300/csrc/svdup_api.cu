@@ -71,7 +71,7 @@ struct svdup_ctx {
   cudaStream_t side;
   cudaStream_t prod[2];
   cudaEvent_t ev_fork, ev_mid, ev_join;
-  cudaEvent_t ev[6];  // e1 ready, e2 ready, e3 ready, signs ready, U done, V done
+  cudaEvent_t ev[6];  // e1 ready, e2 ready, e3 ready, e4 ready, U done, V done
 };
 
 namespace {
@@ -822,8 +822,10 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   // Streams: the left-hand solves (E1, E2) on the handle's stream, the right-hand ones
   // (E3, E4) on the side stream, the products with U on prod[0] and with V on prod[1].
   // A side's first product needs only its first solve, so it runs beside the second
-  // solve; the V side's second product waits for the sign pairing, which hands the left
-  // vectors' sums to the right.  With stage timing on, everything runs on one stream.
+  // solve, and the second product follows the second solve.  V's second product writes
+  // its columns unsigned; the sign pairing (which hands the left vectors' sums to the
+  // right) runs meanwhile, and its signs are applied to V after the join.  With stage
+  // timing on, everything runs on one stream.
   const bool multi = !h->timing && h->side;
   cudaStream_t sR = multi ? h->side : st;
   cudaStream_t pU = multi ? h->prod[0] : st;
@@ -842,21 +844,22 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   launch_fill_second(sR, u.E4, u.E3.lam, u.zsec4);
   queue_solve(h, sR, u.E4, mixed);
   launch_norms(sR, u.E4, nullptr, nullptr, mixed);
-  // STEPs 2, 4: first left solve; its transposed product gives the second left z;
-  // STEP 5: second left solve
+  if (multi && cudaEventRecord(h->ev[3], sR) != cudaSuccess) return SVDUP_ECUDA;  // E4 ready
+  // STEPs 2, 4: first left solve; its transposed product gives the second left z
   launch_fill_left(st, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
   queue_solve(h, st, u.E1);
   launch_apply_qt(st, u.E1, u.z2p, u.ysortL, u.zsec2);
   if (!hand(h->ev[0], st, pU)) return SVDUP_ECUDA;  // E1 ready: U's first product
+  // STEP 5: second left solve
   launch_fill_second(st, u.E2, u.E1.lam, u.zsec2);
   queue_solve(h, st, u.E2, mixed);
   launch_norms(st, u.E2, nullptr, nullptr, mixed);
   stage_end(h);
-  // products: U -> W -> U (descending), V -> W -> V (descending, signed)
+  // products: U -> W -> U (descending), V -> W -> V (descending; the signs follow)
   OutMap om1 = {u.WL, (long long)m, m, 0, nullptr};
   OutMap om2 = {U, (long long)ldu, m, 1, nullptr};
   OutMap om3 = {u.WR, (long long)n, n, 0, nullptr};
-  OutMap om4 = {V, (long long)ldv, n, 1, u.sign};
+  OutMap om4 = {V, (long long)ldv, n, 1, nullptr};
   if (mixed) {
     queue_product_mixed(h, pU, u.E1, u.FL, u.ML, m, U, ldu, om1, mode);
     queue_product_mixed(h, pV, u.E3, u.FR, u.MR, n, V, ldv, om3, mode);
@@ -864,7 +867,13 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     queue_product(h, pU, u.E1, u.FL, m, U, ldu, u.XsL, om1, mode);
     queue_product(h, pV, u.E3, u.FR, n, V, ldv, u.XsR, om3, mode);
   }
+  // V's second product, after its first (stream order) and E4 (the event above)
+  if (multi && cudaStreamWaitEvent(pV, h->ev[3], 0) != cudaSuccess) return SVDUP_ECUDA;
+  if (mixed) queue_product_mixed(h, pV, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
+  else queue_product(h, pV, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
   if (!hand(h->ev[1], st, pU)) return SVDUP_ECUDA;  // E2 ready: U's second product
+  if (mixed) queue_product_mixed(h, pU, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
+  else queue_product(h, pU, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
   // sign pairing of right vectors with left vectors (before S is overwritten); in the
   // mixed mode its sums run on FP32 pairs (only the signs are used)
   stage_begin(h, SVDUP_STAGE_SIGN);
@@ -878,17 +887,11 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   launch_apply_qt(sR, u.E4, u.h1, u.ysortR, u.h, mixed, true);
   launch_sign_finish(sR, m, n, u.h, u.sign);
   stage_end(h);
-  if (!hand(h->ev[3], sR, pV)) return SVDUP_ECUDA;  // E4 and the signs: V's second product
-  if (mixed) {
-    queue_product_mixed(h, pU, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
-    queue_product_mixed(h, pV, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
-  } else {
-    queue_product(h, pU, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
-    queue_product(h, pV, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
-  }
-  // join before STEP 8 (it overwrites S, which the right-hand fill and the signs read)
+  // join before the signs are applied to V and before STEP 8 (it overwrites S, which
+  // the right-hand fill and the signs read)
   if (!hand(h->ev[4], pU, st) || !hand(h->ev[5], pV, st) || !hand(h->ev_join, sR, st))
     return SVDUP_ECUDA;
+  launch_sign_apply(st, m, n, V, ldv, u.sign);
   // STEP 8
   launch_sqrt_desc(st, m, u.E2.lam, S, h->status);
   return check_launch();

@@ -269,6 +269,7 @@ void launch_apply_q_core_df(cudaStream_t st, Eig e, const double* xfinal, double
 void launch_sign_combine(cudaStream_t st, int m, int n, const double* S, const double* p,
                          const double* q, const double* g, double* y);
 void launch_sign_finish(cudaStream_t st, int m, int n, const double* h, double* sign);
+void launch_sign_apply(cudaStream_t st, int m, int n, double* V, long long ldv, const double* sign);
 void launch_fill_ones(cudaStream_t st, int n, double* w);
 void launch_sqrt_desc(cudaStream_t st, int m, const double* lam, double* S, int* status);
 // synthetic inputs for the autotuner

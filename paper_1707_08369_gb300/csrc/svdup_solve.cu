@@ -1900,6 +1900,21 @@ void launch_sign_finish(cudaStream_t st, int m, int n, const double* h, double* 
   SVDUP_COUNT_LAUNCH();
 }
 
+// The signs applied to V after its second product (written unsigned, so that the
+// product need not wait for the sign pairing): physical column c holds final index
+// n - 1 - c; a block per column of the paired part, the unflipped ones exit at once.
+__global__ void k_sign_apply(int m, int n, double* V, long long ldv, const double* __restrict__ sign) {
+  const int c = blockIdx.x;
+  if (c >= m || !(sign[n - 1 - c] < 0.0)) return;
+  double* col = V + (long long)c * ldv;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) col[r] = -col[r];
+}
+
+void launch_sign_apply(cudaStream_t st, int m, int n, double* V, long long ldv, const double* sign) {
+  k_sign_apply<<<m, 256, 0, st>>>(m, n, V, ldv, sign);
+  SVDUP_COUNT_LAUNCH();
+}
+
 __global__ void k_fill_ones(int n, double* w) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) w[i] = 1.0;
