@@ -68,10 +68,11 @@ struct svdup_ctx {
   int leaf128_min[2]; // N >= leaf128_min: leaves of 128 poles, else 64
   // the right-hand problem of an update runs on `side`, beside the left-hand one; the
   // products of each side run on prod[0] (U) and prod[1] (V)
-  cudaStream_t side;
-  cudaStream_t prod[2];
+  cudaStream_t side;   // the right-hand solves (high priority)
+  cudaStream_t left;   // the left-hand solves (high priority)
+  cudaStream_t prod[2];  // the products with U and with V (low priority)
   cudaEvent_t ev_fork, ev_mid, ev_join;
-  cudaEvent_t ev[6];  // e1 ready, e2 ready, e3 ready, e4 ready, U done, V done
+  cudaEvent_t ev[7];  // e1 ready, e2 ready, e3 ready, e4 ready, U done, V done, left done
 };
 
 namespace {
@@ -436,13 +437,18 @@ void queue_product_mixed(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPla
 // ---------------------------------------------------------------------------
 // The side stream and the three events of the two-stream update.
 int make_side(svdup_ctx* h) {
-  bool ok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess;
-  ok = ok && cudaStreamCreateWithFlags(&h->prod[0], cudaStreamNonBlocking) == cudaSuccess;
-  ok = ok && cudaStreamCreateWithFlags(&h->prod[1], cudaStreamNonBlocking) == cudaSuccess;
+  // The solve chains are latency-bound and on the critical path; the products fill the
+  // GPU around them.  Higher priority lets the solves' blocks go first.
+  int lo = 0, hi = 0;
+  bool ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&h->left, cudaStreamNonBlocking, hi) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&h->prod[0], cudaStreamNonBlocking, lo) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&h->prod[1], cudaStreamNonBlocking, lo) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
-  for (int i = 0; i < 6; i++)
+  for (int i = 0; i < 7; i++)
     ok = ok && cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -455,14 +461,16 @@ int make_side(svdup_ctx* h) {
 void free_side(svdup_ctx* h) {
   if (!h->side) return;
   cudaStreamSynchronize(h->side);
+  cudaStreamSynchronize(h->left);
   cudaStreamSynchronize(h->prod[0]);
   cudaStreamSynchronize(h->prod[1]);
   cudaEventDestroy(h->ev_fork);
   cudaEventDestroy(h->ev_mid);
   cudaEventDestroy(h->ev_join);
-  for (int i = 0; i < 6; i++) cudaEventDestroy(h->ev[i]);
+  for (int i = 0; i < 7; i++) cudaEventDestroy(h->ev[i]);
   cudaStreamDestroy(h->prod[0]);
   cudaStreamDestroy(h->prod[1]);
+  cudaStreamDestroy(h->left);
   cudaStreamDestroy(h->side);
   h->side = nullptr;
 }
@@ -819,8 +827,9 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   stage_begin(h, SVDUP_STAGE_GEMV);
   launch_gemv_pq(st, m, n, U, ldu, V, ldv, a, b, u.p, u.q, u.ab);
   stage_end(h);
-  // Streams: the left-hand solves (E1, E2) on the handle's stream, the right-hand ones
-  // (E3, E4) on the side stream, the products with U on prod[0] and with V on prod[1].
+  // Streams: the left-hand solves (E1, E2) on `left`, the right-hand ones (E3, E4) on
+  // `side`, the products with U on prod[0] and with V on prod[1]; the handle's stream
+  // forks them after STEP 1 and joins them before the signs are applied and STEP 8.
   // A side's first product needs only its first solve, so it runs beside the second
   // solve, and the second product follows the second solve.  V's second product writes
   // its columns unsigned; the sign pairing (which hands the left vectors' sums to the
@@ -828,13 +837,15 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   // timing on, everything runs on one stream.
   const bool multi = !h->timing && h->side;
   cudaStream_t sR = multi ? h->side : st;
+  cudaStream_t sL = multi ? h->left : st;
   cudaStream_t pU = multi ? h->prod[0] : st;
   cudaStream_t pV = multi ? h->prod[1] : st;
   auto hand = [&](cudaEvent_t ev, cudaStream_t from, cudaStream_t to) -> bool {
     return !multi || (cudaEventRecord(ev, from) == cudaSuccess &&
                       cudaStreamWaitEvent(to, ev, 0) == cudaSuccess);
   };
-  if (!hand(h->ev_fork, st, sR)) return SVDUP_ECUDA;
+  if (!hand(h->ev_fork, st, sR) || (multi && cudaStreamWaitEvent(sL, h->ev_fork, 0) != cudaSuccess))
+    return SVDUP_ECUDA;
   stage_begin(h, SVDUP_STAGE_SOLVE);
   // STEPs 3, 6: first right solve; STEP 7: second right solve
   launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
@@ -846,20 +857,20 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   launch_norms(sR, u.E4, nullptr, nullptr, mixed);
   if (multi && cudaEventRecord(h->ev[3], sR) != cudaSuccess) return SVDUP_ECUDA;  // E4 ready
   // STEPs 2, 4: first left solve; its transposed product gives the second left z
-  launch_fill_left(st, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
-  queue_solve(h, st, u.E1);
-  launch_apply_qt(st, u.E1, u.z2p, u.ysortL, u.zsec2);
-  if (!hand(h->ev[0], st, pU)) return SVDUP_ECUDA;  // E1 ready: U's first product
+  launch_fill_left(sL, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
+  queue_solve(h, sL, u.E1);
+  launch_apply_qt(sL, u.E1, u.z2p, u.ysortL, u.zsec2);
+  if (!hand(h->ev[0], sL, pU)) return SVDUP_ECUDA;  // E1 ready: U's first product
   // STEP 5: second left solve
-  launch_fill_second(st, u.E2, u.E1.lam, u.zsec2);
-  queue_solve(h, st, u.E2, mixed);
-  launch_norms(st, u.E2, nullptr, nullptr, mixed);
+  launch_fill_second(sL, u.E2, u.E1.lam, u.zsec2);
+  queue_solve(h, sL, u.E2, mixed);
+  launch_norms(sL, u.E2, nullptr, nullptr, mixed);
   stage_end(h);
   // products: U -> W -> U (descending), V -> W -> V (descending; the signs follow)
-  OutMap om1 = {u.WL, (long long)m, m, 0, nullptr};
-  OutMap om2 = {U, (long long)ldu, m, 1, nullptr};
-  OutMap om3 = {u.WR, (long long)n, n, 0, nullptr};
-  OutMap om4 = {V, (long long)ldv, n, 1, nullptr};
+  OutMap om1 = {u.WL, (long long)m, m, 0};
+  OutMap om2 = {U, (long long)ldu, m, 1};
+  OutMap om3 = {u.WR, (long long)n, n, 0};
+  OutMap om4 = {V, (long long)ldv, n, 1};
   if (mixed) {
     queue_product_mixed(h, pU, u.E1, u.FL, u.ML, m, U, ldu, om1, mode);
     queue_product_mixed(h, pV, u.E3, u.FR, u.MR, n, V, ldv, om3, mode);
@@ -871,17 +882,17 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   if (multi && cudaStreamWaitEvent(pV, h->ev[3], 0) != cudaSuccess) return SVDUP_ECUDA;
   if (mixed) queue_product_mixed(h, pV, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
   else queue_product(h, pV, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
-  if (!hand(h->ev[1], st, pU)) return SVDUP_ECUDA;  // E2 ready: U's second product
+  if (!hand(h->ev[1], sL, pU)) return SVDUP_ECUDA;  // E2 ready: U's second product
   if (mixed) queue_product_mixed(h, pU, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
   else queue_product(h, pU, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
   // sign pairing of right vectors with left vectors (before S is overwritten); in the
   // mixed mode its sums run on FP32 pairs (only the signs are used)
   stage_begin(h, SVDUP_STAGE_SIGN);
-  launch_fill_ones(st, m, u.ones);
-  launch_apply_q(st, u.E2, u.ones, u.work, u.g1, mixed);
-  launch_apply_q(st, u.E1, u.g1, u.work, u.g, mixed);
-  launch_sign_combine(st, m, n, S, u.p, u.q, u.g, u.yv);
-  if (!hand(h->ev_mid, st, sR)) return SVDUP_ECUDA;
+  launch_fill_ones(sL, m, u.ones);
+  launch_apply_q(sL, u.E2, u.ones, u.work, u.g1, mixed);
+  launch_apply_q(sL, u.E1, u.g1, u.work, u.g, mixed);
+  launch_sign_combine(sL, m, n, S, u.p, u.q, u.g, u.yv);
+  if (!hand(h->ev_mid, sL, sR)) return SVDUP_ECUDA;
   // (the stored norms of E3 and E4 stay: V's products read them, possibly meanwhile)
   launch_apply_qt(sR, u.E3, u.yv, u.ysortR, u.h1, mixed, true);
   launch_apply_qt(sR, u.E4, u.h1, u.ysortR, u.h, mixed, true);
@@ -889,7 +900,8 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   stage_end(h);
   // join before the signs are applied to V and before STEP 8 (it overwrites S, which
   // the right-hand fill and the signs read)
-  if (!hand(h->ev[4], pU, st) || !hand(h->ev[5], pV, st) || !hand(h->ev_join, sR, st))
+  if (!hand(h->ev[4], pU, st) || !hand(h->ev[5], pV, st) || !hand(h->ev_join, sR, st) ||
+      !hand(h->ev[6], sL, st))
     return SVDUP_ECUDA;
   launch_sign_apply(st, m, n, V, ldv, u.sign);
   // STEP 8
@@ -1038,7 +1050,7 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
   launch_fill_generic(st, e, d, z, rhod, h->status);
   queue_solve(h, st, e, mixed);
   launch_norms(st, e, nullptr, nullptr, mixed);
-  OutMap om = {Y, (long long)ldy, N, 0, nullptr};
+  OutMap om = {Y, (long long)ldy, N, 0};
   if (mixed) queue_product_mixed(h, st, e, f, mp, rows, Xw, rows, om, mode);
   else queue_product(h, st, e, f, rows, Xw, rows, Xs, om, mode);
   cudaMemcpyAsync(lam, e.lam, N * sizeof(double), cudaMemcpyDeviceToDevice, st);

@@ -163,13 +163,12 @@ struct Eig {
 };
 
 // Column mapping of a product's output: physical column of final index q is
-//   out_rev ? (out_n - 1 - q) : q, and the column is scaled by colscale[q] if set.
+//   out_rev ? (out_n - 1 - q) : q.
 struct OutMap {
   double* Y;
   long long ldy;
   int out_n;
   int out_rev;
-  const double* colscale;  // +-1 signs indexed by final index q, may be null
 };
 
 // FMM (flat Chebyshev far field + direct near field) plan for one product.

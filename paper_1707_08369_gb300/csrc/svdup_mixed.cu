@@ -52,13 +52,14 @@ namespace {
 constexpr int kTM = 128;                      // rows per A tile / MMA M
 constexpr int kKB = 64;                       // K per tile (X, Phi, T, C)
 constexpr uint32_t kTileA = 3 * kTM * kKB * 2;       // 49152
-constexpr uint32_t kPlaneA = kTM * kKB * 2;          // 16384
 constexpr uint32_t kTilePsi = 3 * kTM * kMixP * 2;   // 12288 (128 x 16)
 constexpr uint32_t kPlanePsi = kTM * kMixP * 2;      // 4096
 constexpr uint32_t kTileS = 3 * kMixP * kKB * 2;     // 6144 (16 x 64)
-constexpr uint32_t kPlaneS = kMixP * kKB * 2;        // 2048
-constexpr uint32_t kStageBytes = 2 * kTileA;         // A + B region per ring stage
-constexpr uint32_t kRingBytes = 2 * kStageBytes;     // two stages
+constexpr int kStages = 2;                           // ring stages
+constexpr int kHalvesPerStep = 4 / kStages;          // K halves of a 64-K tile per stage
+constexpr uint32_t kStepMax = kTileA / 2 * kHalvesPerStep;  // A (or B) bytes of one step
+constexpr uint32_t kStageBytes = 2 * kStepMax;       // A + B region per ring stage
+constexpr uint32_t kRingBytes = kStages * kStageBytes;
 constexpr uint32_t kSmemBytes = kRingBytes + 256 + 1024;  // + barriers, + alignment slack
 
 __host__ __device__ constexpr uint32_t tile_L_bytes(int s) { return 3u * s * kMixP * 2; }
@@ -67,6 +68,14 @@ __host__ __device__ constexpr uint32_t tile_C_bytes(int s) { return 3u * s * kKB
 // byte offset of element (r, k) in a canonical K-major plane with K extent KB
 __device__ __forceinline__ uint32_t cl_off(int r, int k, int KB) {
   return (uint32_t)((r >> 3) * (KB * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// A 64-K tile of R rows is stored as its two K halves one after the other, each half
+// three planes (hi, mid, lo) of R x 32 in the canonical layout, half_plane(R) bytes
+// apart, so that one ring stage takes one contiguous half.
+__host__ __device__ constexpr uint32_t half_plane(int R) { return (uint32_t)R * 64u; }
+__device__ __forceinline__ uint32_t t64_off(int r, int k, int R) {
+  return (uint32_t)(k >> 5) * 3u * half_plane(R) + cl_off(r, k & 31, 32);
 }
 
 // ---------------------------------------------------------------------------
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__(256) k_mix_gather(Eig e, const double* __restr
       long long col = scol[ch * 8 + c];
       v[c] = (col >= 0 && row < rows) ? narrow_rn(X[row + col]) : 0.0f;
     }
-    store_split8_f(tile, kPlaneA, cl_off(r, ch * 8, kKB), v);
+    store_split8_f(tile, half_plane(kTM), t64_off(r, ch * 8, kTM), v);
   }
 }
 
@@ -333,10 +342,9 @@ __global__ void k_mix_defl(Eig e, const double* __restrict__ X, long long ldx, i
   int s = e.didx[c - k];
   if (e.defl[s] == 2) return;  // deflated by a rotation: the rotation kernel wrote it
   int q = e.rank_defl[s];
-  double sc = om.colscale ? om.colscale[q] : 1.0;
   const double* src = X + (long long)e.perm[s] * ldx;
   double* dst = om.Y + out_col_m(om, q) * om.ldy;
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = sc * src[r];
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = src[r];
 }
 
 // ---------------------------------------------------------------------------
@@ -387,7 +395,7 @@ __global__ void k_mix_pack_S(Eig e, FmmPlan f, MixPlan mp) {
       int tl = h * kKB + ch * 8 + c;
       v[c] = f.S[(size_t)a * f.s * f.p + (size_t)al * f.s + tl];
     }
-    store_split8_d(tile, kPlaneS, cl_off(al, ch * 8, kKB), v);
+    store_split8_d(tile, half_plane(kMixP), t64_off(al, ch * 8, kMixP), v);
   }
 }
 
@@ -407,7 +415,7 @@ __global__ void k_mix_pack_T(FmmPlan f, MixPlan mp) {
       int row = kt * kKB + ch * 8 + c;
       v[c] = (col < Lt * kMixP && row < Ls * kMixP) ? f.T[row + col * ldT] : 0.0;
     }
-    store_split8_d(tile, kPlaneA, cl_off(n, ch * 8, kKB), v);
+    store_split8_d(tile, half_plane(kTM), t64_off(n, ch * 8, kTM), v);
   }
 }
 
@@ -431,7 +439,17 @@ __global__ void k_mix_pack_L(FmmPlan f, MixPlan mp) {
 // Near-field tile (b, i, h): source leaf a = near[b][i], K half h:
 //   B[jl][kk] = zhat_t inv_j / delta_tj,  t = a s + 64 h + kk,  j = tj0[b] + jl,
 //   delta_tj = (dk_t - d_org(j)) - tau_j   (the offsets of the FP64 root solve),
-// zero for t >= k or j >= tj1[b].
+// zero for t >= k or j >= tj1[b].  One FP64 operation per entry, the pole difference
+// (exact when the poles are close, by Sterbenz's lemma); tau_j is subtracted, and the
+// reciprocal and products formed, on FP32 pairs at a common power-of-two scale (a
+// pair carries about 46 bits, the split keeps 24).  For a pole t outside root j's
+// bracket the subtraction cancels at most a factor 3 (|tau_j| is at most half the
+// bracket); at the bracketing poles it is exact or cancels at most a factor 2.
+__device__ __forceinline__ Df df_scaled_pow2(Df v, int sh) {  // v 2^sh, in two exact steps
+  const float a = pow2f(max(sh, -126)), b = pow2f(min(0, sh + 126));
+  return Df{(v.hi * a) * b, (v.lo * a) * b};
+}
+
 __global__ void k_mix_pack_C(Eig e, FmmPlan f, MixPlan mp) {
   const int b = blockIdx.x, i = blockIdx.y, h = blockIdx.z;
   if (b >= f.L[1] || i >= mp.nnear[b]) return;
@@ -441,23 +459,38 @@ __global__ void k_mix_pack_C(Eig e, FmmPlan f, MixPlan mp) {
   const int j0 = f.tj0[b], j1 = f.tj1[b];
   const int P = f.L[2];  // source leaf a holds poles [a s - P, a s + s - P)
   unsigned char* tile = mp.Cp + ((size_t)(mp.noff[b] + i) * hs + h) * tile_C_bytes(s);
-  const uint32_t plane = (uint32_t)s * kKB * 2;
   for (int it = threadIdx.x; it < s * (kKB / 8); it += blockDim.x) {
     const int jl = it % s, ch = it / s;
     const int j = j0 + jl;
-    double v[8];
+    float hi[8], lo[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) { hi[c] = 0.f; lo[c] = 0.f; }
     if (j < j1) {
       const double dO = e.dorg[j], tj = e.tau[j], inv = e.inv[j];
+      const int eT = exp2_of(tj), eI = exp2_of(inv);
+      const Df ij = df_from_f64(inv, eI);
 #pragma unroll
       for (int c = 0; c < 8; c++) {
         const int t = a * s + h * kKB + ch * 8 + c - P;
-        v[c] = (t >= 0 && t < k) ? e.zhat[t] * inv * rcp64((e.dk[t] - dO) - tj) : 0.0;
+        if (t < 0 || t >= k) continue;
+        const double zt = e.zhat[t];
+        const double d1 = e.dk[t] - dO;
+        const int eD = max(exp2_of(d1), eT), eZ = exp2_of(zt);
+        if (zt == 0.0 || eZ < -1000 || eI < -1000 || eD < -1000) {  // zero or subnormal
+          const double v = zt * inv * rcp64(d1 - tj);
+          const Df p = df_from_f64(v, 0);
+          hi[c] = p.hi;
+          lo[c] = p.lo;
+          continue;
+        }
+        const Df del = df_add(df_from_f64(d1, eD), df_neg(df_from_f64(tj, eD)));
+        const Df v = df_mul(df_mul(df_from_f64(zt, eZ), ij), df_rcp(del));
+        const Df w = df_scaled_pow2(v, eZ + eI - eD);
+        hi[c] = w.hi;
+        lo[c] = w.lo;
       }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; c++) v[c] = 0.0;
     }
-    store_split8_d(tile, plane, cl_off(jl, ch * 8, kKB), v);
+    store_split8_ff(tile, half_plane(s), t64_off(jl, ch * 8, s), hi, lo);
   }
 }
 
@@ -470,9 +503,10 @@ enum { MS_P2M = 0, MS_M2L = 1, MS_OUT = 2 };
 struct KTile {
   const unsigned char* a;
   const unsigned char* b;
-  uint32_t abytes, bbytes;  // copy sizes (three planes)
-  uint32_t aplane, bplane;  // plane strides
-  int kb;                   // K extent (16 or 64)
+  uint32_t astep, bstep;    // bytes per step: a K half of a 64-K tile, or a 16-K tile whole
+  uint32_t aplane, bplane;  // plane strides within a step
+  int kstep;                // K per step (32 or 16)
+  int nsteps;               // steps (ring stages) of the tile: 2 or 1
   int n;                    // MMA N
   int col;                  // accumulator column offset
   int first;                // first K tile of its accumulator
@@ -493,53 +527,55 @@ __device__ __forceinline__ int job_tiles(const Job& J, const FmmPlan& f, const M
   return (dense ? 0 : 1) + mp.nnear[J.job] * hs;
 }
 
+// a 64-K tile of rows R at p, in steps of kHalvesPerStep K halves
+__device__ __forceinline__ void half_steps_a(KTile& t, const unsigned char* p, int R) {
+  t.a = p; t.astep = 3u * half_plane(R) * kHalvesPerStep; t.aplane = half_plane(R);
+}
+__device__ __forceinline__ void half_steps_b(KTile& t, const unsigned char* p, int R) {
+  t.b = p; t.bstep = 3u * half_plane(R) * kHalvesPerStep; t.bplane = half_plane(R);
+}
+
 template <int STAGE>
 __device__ __forceinline__ KTile ktile(int i, const Job& J, const FmmPlan& f, const MixPlan& mp,
                                        int dense) {
   KTile t;
   const int hs = mp.s / kKB;
+  t.kstep = kKB / 2 * kHalvesPerStep;
+  t.nsteps = 2 / kHalvesPerStep;
   if (STAGE == MS_P2M) {
     const int a = 4 * J.job + i / hs, h = i % hs;
-    t.a = mp.Xp + ((size_t)J.rt * mp.kx + (size_t)a * hs + h) * kTileA;
-    t.b = mp.Sp + ((size_t)a * hs + h) * kTileS;
-    t.abytes = kTileA; t.aplane = kPlaneA;
-    t.bbytes = kTileS; t.bplane = kPlaneS;
-    t.kb = kKB; t.n = kMixP; t.col = (a - 4 * J.job) * kMixP; t.first = (h == 0);
+    half_steps_a(t, mp.Xp + ((size_t)J.rt * mp.kx + (size_t)a * hs + h) * kTileA, kTM);
+    half_steps_b(t, mp.Sp + ((size_t)a * hs + h) * kTileS, kMixP);
+    t.n = kMixP; t.col = (a - 4 * J.job) * kMixP; t.first = (h == 0);
   } else if (STAGE == MS_M2L) {
-    t.a = mp.Phip + ((size_t)J.rt * mp.kphi + i) * kTileA;
-    t.b = mp.Tp + ((size_t)J.job * mp.kphi + i) * kTileA;
-    t.abytes = kTileA; t.aplane = kPlaneA;
-    t.bbytes = kTileA; t.bplane = kPlaneA;
-    t.kb = kKB; t.n = kTM; t.col = 0; t.first = (i == 0);
+    half_steps_a(t, mp.Phip + ((size_t)J.rt * mp.kphi + i) * kTileA, kTM);
+    half_steps_b(t, mp.Tp + ((size_t)J.job * mp.kphi + i) * kTileA, kTM);
+    t.n = kTM; t.col = 0; t.first = (i == 0);
   } else {
     const int s = mp.s;
     const int b = J.job;
     if (!dense && i == 0) {
       t.a = mp.Psip + ((size_t)J.rt * (mp.Lmax + 1) + b) * kTilePsi;
       t.b = mp.Lp + (size_t)b * tile_L_bytes(s);
-      t.abytes = kTilePsi; t.aplane = kPlanePsi;
-      t.bbytes = tile_L_bytes(s); t.bplane = (uint32_t)s * kMixP * 2;
-      t.kb = kMixP; t.n = s; t.col = 0; t.first = 1;
+      t.astep = kTilePsi; t.aplane = kPlanePsi;
+      t.bstep = tile_L_bytes(s); t.bplane = (uint32_t)s * kMixP * 2;
+      t.kstep = kMixP; t.nsteps = 1; t.n = s; t.col = 0; t.first = 1;
     } else {
       const int q = i - (dense ? 0 : 1);
       const int ni = q / hs, h = q % hs;
       const int a = mp.near[(long long)b * mp.Lmax + ni];
-      t.a = mp.Xp + ((size_t)J.rt * mp.kx + (size_t)a * hs + h) * kTileA;
-      t.b = mp.Cp + ((size_t)(mp.noff[b] + ni) * hs + h) * tile_C_bytes(s);
-      t.abytes = kTileA; t.aplane = kPlaneA;
-      t.bbytes = tile_C_bytes(s); t.bplane = (uint32_t)s * kKB * 2;
-      t.kb = kKB; t.n = s; t.col = 0;
+      half_steps_a(t, mp.Xp + ((size_t)J.rt * mp.kx + (size_t)a * hs + h) * kTileA, kTM);
+      half_steps_b(t, mp.Cp + ((size_t)(mp.noff[b] + ni) * hs + h) * tile_C_bytes(s), s);
+      t.n = s; t.col = 0;
       t.first = dense && q == 0;  // with the far field, tile 0 (Psi L) opened the sum
     }
   }
   return t;
 }
 
-// The six partial products of the 3-term split: (A plane, B plane).  Product 0
-// (hi.hi) accumulates in its own tensor-memory region; the five cross products, smaller
-// by 2^-8 or more, share a second region.
-__constant__ int kPairA[6] = {0, 0, 1, 0, 2, 1};
-__constant__ int kPairB[6] = {0, 1, 0, 2, 0, 1};
+// The six partial products of the 3-term split, (A plane, B plane): (hi, hi) accumulates
+// in its own tensor-memory region; (hi, mid) (mid, hi) (hi, lo) (lo, hi) (mid, mid),
+// smaller by 2^-8 or more, share a second region.
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -559,13 +595,18 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 // Roles: warps 0-7 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) .., i.e.
 // output rows, and the column half w / 4 of the W accumulator columns), warp 8 issues
 // the bulk copies, warp 9 owns tensor memory and issues the MMAs.
-// Tensor memory (512 columns): two regions (K tiles alternate), each holding the hi.hi
-// accumulator in columns [0, W) and the cross-product accumulator in [128, 128 + W).
-// Every K tile is drained into double-float registers while the next one is multiplied,
-// so FP32 rounding in tensor memory covers at most one K tile (64 or 16 products).
-constexpr int kEpiWarps = 8;
+// Tensor memory (512 columns): three hi.hi accumulators that K tiles take in turn, and
+// one accumulator for the five cross products of the whole item.  Every K tile's hi.hi
+// sum is drained into double-float registers while the next ones are multiplied, so FP32
+// rounding of the leading products covers at most one K tile (64 or 16 products); the
+// cross products, 2^-8 of them and below, accumulate in FP32 over the item and are
+// drained once.  With three hi.hi regions the MMAs run up to three K tiles ahead of the
+// drains, which covers the epilogue's output stores at the end of an item.
+constexpr int kEpiWarps = 16;  // four per quarter of the TMEM lanes (rows), each a quarter of the columns
 constexpr int kUmmaThreads = (kEpiWarps + 2) * 32;
 constexpr uint32_t kTmemCols = 512;
+constexpr int kHiRegions = 3;          // hi.hi accumulators, columns [128 r, 128 r + 128)
+constexpr uint32_t kCrossCol = 384;    // the cross-product accumulator, columns [384, 512)
 
 // Work items: (row tile rt, job).  Jobs per row tile: P2M one per 4 source leaves, M2L
 // one per 128 local-expansion columns (8 target leaves), OUT one per target leaf (in
@@ -590,12 +631,13 @@ __device__ __forceinline__ void set_item(Job& J, int x, int njobs, const FmmPlan
 
 // Persistent: one CTA per SM loops over the work items (x = blockIdx.x, += gridDim.x).
 // The producer and MMA warps run ahead into the next item while the epilogue warps
-// finish the previous one; every role counts the K tiles it has handled (g) across
-// items, which fixes the ring slot (g & 1) and the barrier phase (g >> 1) & 1.
+// finish the previous one; every role counts what it has handled across items (ring
+// steps, K tiles, items), which fixes the slot or region (count mod their number) and
+// the barrier phase (count / their number, mod 2).
 template <int STAGE, int W>
 __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixPlan mp, OutMap om,
                                                           int dense, int* status) {
-  constexpr int QW = W / 2;        // columns per epilogue warp
+  constexpr int QW = W / (kEpiWarps / 4);  // columns per epilogue warp
   constexpr int NCH = QW / 16;     // 16-column chunks per epilogue warp
   extern __shared__ unsigned char smem_raw[];
   Job J;
@@ -607,15 +649,19 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
 
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_base = smem_u32(sm);
-  uint64_t* bars = (uint64_t*)(sm + kRingBytes);  // full[2] empty[2] tfull[2] tempty[2] done
+  // barriers: full[S] empty[S] (ring), tfull[3] tempty[3] (hi.hi regions), xfull xempty
+  // (cross region), done
+  uint64_t* bars = (uint64_t*)(sm + kRingBytes);
   const uint32_t bar0 = smem_u32(bars);
   volatile uint32_t* tmem_slot = (volatile uint32_t*)(sm + kRingBytes + 128);
   volatile int* abort_flag = (volatile int*)(sm + kRingBytes + 192);
   auto bar_full = [&](int i) { return bar0 + 8u * (uint32_t)i; };
-  auto bar_empty = [&](int i) { return bar0 + 8u * (uint32_t)(2 + i); };
-  auto bar_tfull = [&](int i) { return bar0 + 8u * (uint32_t)(4 + i); };
-  auto bar_tempty = [&](int i) { return bar0 + 8u * (uint32_t)(6 + i); };
-  const uint32_t bar_done = bar0 + 8u * 8u;
+  auto bar_empty = [&](int i) { return bar0 + 8u * (uint32_t)(kStages + i); };
+  auto bar_tfull = [&](int i) { return bar0 + 8u * (uint32_t)(2 * kStages + i); };
+  auto bar_tempty = [&](int i) { return bar0 + 8u * (uint32_t)(2 * kStages + 3 + i); };
+  const uint32_t bar_xfull = bar0 + 8u * (uint32_t)(2 * kStages + 6);
+  const uint32_t bar_xempty = bar0 + 8u * (uint32_t)(2 * kStages + 7);
+  const uint32_t bar_done = bar0 + 8u * (uint32_t)(2 * kStages + 8);
   if ((int)blockIdx.x >= nitems) return;  // uniform per CTA, before any barrier or TMEM use
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -624,12 +670,16 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
     tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < kStages; i++) {
       mbar_init(bar_full(i), 1);
       mbar_init(bar_empty(i), 1);
+    }
+    for (int i = 0; i < kHiRegions; i++) {
       mbar_init(bar_tfull(i), 1);
       mbar_init(bar_tempty(i), kEpiWarps * 32);
     }
+    mbar_init(bar_xfull, 1);
+    mbar_init(bar_xempty, kEpiWarps * 32);
     mbar_init(bar_done, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -640,82 +690,123 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
   const uint32_t tmem = *tmem_slot;
 
   if (warp == kEpiWarps) {
-    if (lane == 0) {  // producer: bulk copies into the shared-memory ring
-      uint32_t g = 0;
+    if (lane == 0) {  // producer: bulk copies into the shared-memory ring, a step per stage
+      uint32_t g = 0;  // steps issued
       bool alive = true;
       for (int x = blockIdx.x; x < nitems && alive; x += gridDim.x) {
         set_item<STAGE>(J, x, njobs, f, mp, dense);
-        for (int i = 0; i < J.ntiles; i++, g++) {
-          const int st = g & 1;
-          if (g >= 2 && !mbar_wait(bar_empty(st), ((g >> 1) & 1u) ^ 1u, abort_flag)) {
-            *abort_flag = 1;
-            latch(status, SVDUP_ETIMEOUT);
-            alive = false;
-            break;
-          }
+        for (int i = 0; i < J.ntiles && alive; i++) {
           KTile t = ktile<STAGE>(i, J, f, mp, dense);
-          const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kTileA;
-          mbar_expect_tx(bar_full(st), t.abytes + t.bbytes);
-          bulk_g2s(sa, t.a, t.abytes, bar_full(st));
-          bulk_g2s(sb, t.b, t.bbytes, bar_full(st));
+          for (int q = 0; q < t.nsteps; q++, g++) {
+            const int st = (int)(g % kStages);
+            if (g >= (uint32_t)kStages &&
+                !mbar_wait(bar_empty(st), ((g / kStages) & 1u) ^ 1u, abort_flag)) {
+              *abort_flag = 1;
+              latch(status, SVDUP_ETIMEOUT);
+              alive = false;
+              break;
+            }
+            const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kStepMax;
+            mbar_expect_tx(bar_full(st), t.astep + t.bstep);
+            bulk_g2s(sa, t.a + (size_t)q * t.astep, t.astep, bar_full(st));
+            bulk_g2s(sb, t.b + (size_t)q * t.bstep, t.bstep, bar_full(st));
+          }
         }
       }
     }
   } else if (warp == kEpiWarps + 1) {
     if (lane == 0) {  // MMA issuer
-      uint32_t g = 0;
+      uint32_t g = 0;   // K tiles (hi.hi regions rotate per K tile)
+      uint32_t gs = 0;  // ring steps
+      uint32_t y = 0;   // items (the cross region is drained once per item)
       bool alive = true;
-      for (int x = blockIdx.x; x < nitems && alive; x += gridDim.x) {
+      for (int x = blockIdx.x; x < nitems && alive; x += gridDim.x, y++) {
         set_item<STAGE>(J, x, njobs, f, mp, dense);
-        for (int i = 0; i < J.ntiles; i++, g++) {
-          const int st = g & 1;
-          const uint32_t ph = (g >> 1) & 1u;
-          if (!mbar_wait(bar_full(st), ph, abort_flag) ||
-              (g >= 2 && !mbar_wait(bar_tempty(st), ph ^ 1u, abort_flag))) {
+        if (y >= 1 && !mbar_wait(bar_xempty, (y - 1) & 1u, abort_flag)) {
+          *abort_flag = 1;
+          latch(status, SVDUP_ETIMEOUT);
+          break;
+        }
+        for (int i = 0; i < J.ntiles && alive; i++, g++) {
+          const int rg = (int)(g % kHiRegions);
+          if (g >= (uint32_t)kHiRegions &&
+              !mbar_wait(bar_tempty(rg), ((g / kHiRegions) & 1u) ^ 1u, abort_flag)) {
             *abort_flag = 1;
             latch(status, SVDUP_ETIMEOUT);
             alive = false;
             break;
           }
-          tc_fence_after();
           KTile t = ktile<STAGE>(i, J, f, mp, dense);
-          const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kTileA;
-          const uint32_t dA = tmem + (uint32_t)st * 256u + (uint32_t)t.col;
-          const uint32_t dB = dA + 128u;
+          const uint32_t dA = tmem + (uint32_t)rg * 128u + (uint32_t)t.col;
+          const uint32_t dX = tmem + kCrossCol + (uint32_t)t.col;
           const uint32_t idesc = idesc_bf16(kTM, t.n);
-          const uint32_t sbo = (uint32_t)t.kb * 16;
-          for (int ks = 0; ks < t.kb / 16; ks++) {
-#pragma unroll
-            for (int q = 0; q < 6; q++) {
-              uint64_t ad = sdesc(sa + kPairA[q] * t.aplane + ks * 256, 128, sbo);
-              uint64_t bd = sdesc(sb + kPairB[q] * t.bplane + ks * 256, 128, sbo);
-              if (q == 0) umma_bf16(dA, ad, bd, idesc, ks > 0 ? 1u : 0u);
-              else umma_bf16(dB, ad, bd, idesc, (ks > 0 || q > 1) ? 1u : 0u);
+          const uint32_t sbo = (uint32_t)min(t.kstep, 32) * 16;  // a K half holds 32
+          for (int q = 0; q < t.nsteps; q++, gs++) {
+            const int st = (int)(gs % kStages);
+            if (!mbar_wait(bar_full(st), (gs / kStages) & 1u, abort_flag)) {
+              *abort_flag = 1;
+              latch(status, SVDUP_ETIMEOUT);
+              alive = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kStepMax;
+            // Descriptors differ only in their start-address field (bytes >> 4, below
+            // 2^14 for any shared-memory address), so planes and K steps are additions.
+            const uint64_t a0 = sdesc(sa, 128, sbo), b0 = sdesc(sb, 128, sbo);
+            const uint64_t ap = t.aplane >> 4, bp = t.bplane >> 4;
+            for (int ks = 0; ks < t.kstep / 16; ks++) {
+              const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
+              const uint32_t xacc = (t.first && q == 0 && ks == 0) ? 0u : 1u;
+              // K step ks: half ks / 2 (three planes further on), core matrices 2 (ks % 2)
+              const uint64_t ko = (uint64_t)((ks >> 1) * 3) * ap + (uint64_t)((ks & 1) * 16);
+              const uint64_t kob = (uint64_t)((ks >> 1) * 3) * bp + (uint64_t)((ks & 1) * 16);
+              const uint64_t ka = a0 + ko, kb = b0 + kob;
+              // (A plane, B plane): hi.hi alone, then (hi, mid) (mid, hi) (hi, lo) (lo, hi) (mid, mid)
+              umma_bf16(dA, ka, kb, idesc, acc);
+              umma_bf16(dX, ka, kb + bp, idesc, xacc);
+              umma_bf16(dX, ka + ap, kb, idesc, 1u);
+              umma_bf16(dX, ka, kb + 2 * bp, idesc, 1u);
+              umma_bf16(dX, ka + 2 * ap, kb, idesc, 1u);
+              umma_bf16(dX, ka + ap, kb + bp, idesc, 1u);
+            }
+            umma_commit(bar_empty(st));  // frees the ring stage once these MMAs have read it
           }
-          umma_commit(bar_empty(st));  // frees the ring stage once these MMAs have read it
-          umma_commit(bar_tfull(st));  // hands the accumulators to the epilogue
+          if (!alive) break;
+          umma_commit(bar_tfull(rg));  // hands the hi.hi accumulator to the epilogue
         }
+        if (!alive) break;
+        umma_commit(bar_xfull);  // the item's cross products are complete
       }
       // every MMA this thread issued has completed before tensor memory is released
       umma_commit(bar_done);
       if (!mbar_wait_timed(bar_done, 0)) latch(status, SVDUP_ETIMEOUT);
     }
   } else {
-    // epilogue: drain every K tile into (hi, lo) pairs, then write the item's output
+    // epilogue: drain every K tile's hi.hi products into (hi, lo) pairs and the item's
+    // cross products once, then write the item's output
     const int quad = warp & 3, qc = warp >> 2;
     const int r = quad * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-    uint32_t g = 0;
+    uint32_t g = 0, y = 0;
     bool ok = true;
-    for (int x = blockIdx.x; x < nitems && ok; x += gridDim.x) {
+    for (int x = blockIdx.x; x < nitems && ok; x += gridDim.x, y++) {
       set_item<STAGE>(J, x, njobs, f, mp, dense);
+      // the output columns of this warp's 64 (or 32) accumulator columns, one or two per
+      // lane, loaded now (their latency hides behind the drains), shuffled at the end
+      int cm0 = -1, cm1 = -1;
+      if (STAGE == MS_OUT) {
+        const int j0 = f.tj0[J.job], nb = f.tj1[J.job] - j0;
+        const int c0 = qc * QW + lane;
+        if (c0 < nb) cm0 = (int)out_col_m(om, e.rank_root[j0 + c0]);
+        if (QW > 32 && c0 + 32 < nb) cm1 = (int)out_col_m(om, e.rank_root[j0 + c0 + 32]);
+      }
       float hi[QW], lo[QW];
 #pragma unroll
       for (int c = 0; c < QW; c++) { hi[c] = 0.0f; lo[c] = 0.0f; }
       for (int i = 0; i < J.ntiles; i++, g++) {
-        const int st = g & 1;
-        if (!mbar_wait(bar_tfull(st), (g >> 1) & 1u, abort_flag)) {
+        const int rg = (int)(g % kHiRegions);
+        if (!mbar_wait(bar_tfull(rg), (g / kHiRegions) & 1u, abort_flag)) {
           ok = false;
           break;
         }
@@ -725,24 +816,32 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
         for (int ch = 0; ch < NCH; ch++) {
           const int col = qc * QW + ch * 16;
           if (col >= t.col && col < t.col + t.n) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)rg * 128u + (uint32_t)col, v);
 #pragma unroll
-            for (int part = 0; part < 2; part++) {  // hi.hi region, then the cross region
-              float v[16];
-              tmem_ld16(lane_base + (uint32_t)st * 256u + (uint32_t)part * 128u + (uint32_t)col, v);
-#pragma unroll
-              for (int c = 0; c < 16; c++) {
-                if (part == 0) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], v[c]);
-                else lo[ch * 16 + c] += v[c];  // cross terms: 2^-8 of hi.hi and below
-              }
-            }
+            for (int c = 0; c < 16; c++) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], v[c]);
           }
         }
         tc_fence_before();
-        mbar_arrive(bar_tempty(st));
+        mbar_arrive(bar_tempty(rg));
       }
+      if (!ok || !mbar_wait(bar_xfull, y & 1u, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int ch = 0; ch < NCH; ch++) {  // cross terms: 2^-8 of hi.hi and below
+        float v[16];
+        tmem_ld16(lane_base + kCrossCol + (uint32_t)(qc * QW + ch * 16), v);
+#pragma unroll
+        for (int c = 0; c < 16; c++) lo[ch * 16 + c] += v[c];
+      }
+      tc_fence_before();
+      mbar_arrive(bar_xempty);
       if (!ok || *abort_flag) break;
       if (STAGE == MS_P2M) {
-        // half qc = leaves 4 job + 2 qc + {0, 1}: columns 32 qc .. of the Phi tile
+        // column group qc = leaves 4 job + (QW / 16) qc + u: columns QW qc .. of the Phi tile
         unsigned char* tile = mp.Phip + ((size_t)J.rt * mp.kphi + J.job) * kTileA;
 #pragma unroll
         for (int u = 0; u < QW / kMixP; u++) {
@@ -752,7 +851,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
         }
 #pragma unroll
         for (int c8 = 0; c8 < QW; c8 += 8)
-          store_split8_ff(tile, kPlaneA, cl_off(r, qc * QW + c8, kKB), hi + c8, lo + c8);
+          store_split8_ff(tile, half_plane(kTM), t64_off(r, qc * QW + c8, kTM), hi + c8, lo + c8);
       } else if (STAGE == MS_M2L) {
 #pragma unroll
         for (int u = 0; u < QW / kMixP; u++) {
@@ -765,21 +864,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
         }
       } else {
         // The operands carry 24 significant bits, so the output is rounded to FP32
-        // (hi + lo) and widened exactly; the column scale is a sign (+-1), applied as
-        // one.  Each store of a warp covers 32 consecutive rows of one column.
-        const int j0 = f.tj0[J.job], nb = f.tj1[J.job] - j0;
+        // (hi + lo) and widened exactly.  Each store of a warp covers 32 consecutive
+        // rows of one column.
         const long long row = (long long)J.rt * kTM + r;
-        if (row < mp.rows) {
 #pragma unroll
-          for (int c = 0; c < QW; c++) {
-            const int cc = qc * QW + c;
-            if (cc < nb) {
-              const int q = e.rank_root[j0 + cc];
-              const bool flip = om.colscale && om.colscale[q] < 0.0;
-              const float v = hi[c] + lo[c];
-              om.Y[out_col_m(om, q) * om.ldy + row] = widen_f32(flip ? -v : v);
-            }
-          }
+        for (int c = 0; c < QW; c++) {
+          const int oc = __shfl_sync(0xffffffffu, c < 32 ? cm0 : cm1, c & 31);
+          if (oc >= 0 && row < mp.rows) om.Y[(long long)oc * om.ldy + row] = widen_f32(hi[c] + lo[c]);
         }
       }
     }

@@ -86,7 +86,7 @@ struct RotChunkSm {
   long long a[kRotChunk], b[kRotChunk];
   long long ya[kRotChunk];  // output column of the deflated a (the product's OutMap)
   float4 cs[kRotChunk];
-  double c[kRotChunk], s[kRotChunk], ysc[kRotChunk];
+  double c[kRotChunk], s[kRotChunk];
   unsigned char chained[kRotChunk], ends[kRotChunk];
 };
 
@@ -100,7 +100,6 @@ __device__ __forceinline__ int stage_chunk(Eig e, long long ldx, const float4* r
     if (om) {  // the deflated column goes straight to its output column
       const int q = e.rank_defl[e.rj[g]];
       sm.ya[i] = (om->out_rev ? (long long)(om->out_n - 1 - q) : (long long)q) * om->ldy;
-      sm.ysc[i] = om->colscale ? om->colscale[q] : 1.0;
     }
     sm.c[i] = e.rc[g];
     sm.s[i] = e.rs[g];
@@ -110,6 +109,20 @@ __device__ __forceinline__ int stage_chunk(Eig e, long long ldx, const float4* r
   }
   __syncthreads();
   return cn;
+}
+
+// A batch of the chunk's original column values (xb for every rotation, xa where a run
+// starts) for row r; i >= cn loads nothing.  xlast replaces the chunk's last b when set.
+__device__ __forceinline__ void rot_load(const double* __restrict__ X, const RotChunkSm& sm,
+                                         long long r, int i0, int cn, bool use_last,
+                                         double xlast, double (&xb)[kRotBatch],
+                                         double (&xa)[kRotBatch]) {
+#pragma unroll
+  for (int u = 0; u < kRotBatch; u++) {
+    const int i = i0 + u;
+    xb[u] = i < cn ? ((use_last && i == cn - 1) ? xlast : X[r + sm.b[i]]) : 0.0;
+    xa[u] = (i < cn && !sm.chained[i]) ? X[r + sm.a[i]] : 0.0;
+  }
 }
 
 template <bool MIXED>
@@ -124,14 +137,11 @@ __global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __rest
   if (r >= rows) return;
   double B = 0.0, xlast = 0.0;
   Df Bf = {0.f, 0.f};
+  // (no prefetch of the next batch here: this kernel is bound by its arithmetic issue
+  // rate, and the extra registers would cost occupancy)
   for (int i0 = 0; i0 < cn; i0 += kRotBatch) {
     double xb[kRotBatch], xa[kRotBatch];
-#pragma unroll
-    for (int u = 0; u < kRotBatch; u++) {  // a batch of independent loads in flight
-      const int i = i0 + u;
-      xb[u] = i < cn ? X[r + sm.b[i]] : 0.0;
-      xa[u] = (i < cn && !sm.chained[i]) ? X[r + sm.a[i]] : 0.0;
-    }
+    rot_load(X, sm, r, i0, cn, false, 0.0, xb, xa);
 #pragma unroll
     for (int u = 0; u < kRotBatch; u++) {
       const int i = i0 + u;
@@ -200,37 +210,43 @@ __global__ void __launch_bounds__(128) k_rot_apply(Eig e, double* X, long long l
     *reinterpret_cast<double*>(&t) = v;
     vf = Df{t.x, t.y};
   }
+  // Loads run a batch ahead of the arithmetic.  Within a chunk, column b_i is written
+  // only at rotation i (a run's end, and no later rotation reads it) and a run-start
+  // column a_i is never written (its output goes to Y), so no value loaded early has
+  // been written yet; the chunk's last b comes from compose (the next chunk may write it).
+  double xb[kRotBatch], xa[kRotBatch], nb[kRotBatch], na[kRotBatch];
+  rot_load(X, sm, r, 0, cn, true, xlast, xb, xa);
   for (int i0 = 0; i0 < cn; i0 += kRotBatch) {
-    // Loads of a batch first: within a chunk, column b_i is written only at rotation i
-    // (a run's end) or i + 1 (as the next a), and a run-start column a_i by rotation i
-    // alone, so no value loaded here has been written yet.
-    double xb[kRotBatch], xa[kRotBatch];
-#pragma unroll
-    for (int u = 0; u < kRotBatch; u++) {
-      const int i = i0 + u;
-      xb[u] = i < cn ? ((i == cn - 1) ? xlast : X[r + sm.b[i]]) : 0.0;
-      xa[u] = (i < cn && !sm.chained[i]) ? X[r + sm.a[i]] : 0.0;
-    }
+    if (i0 + kRotBatch < cn) rot_load(X, sm, r, i0 + kRotBatch, cn, true, xlast, nb, na);
 #pragma unroll
     for (int u = 0; u < kRotBatch; u++) {
       const int i = i0 + u;
       if (i < cn) {
         if (!MIXED) {
           const double uu = sm.chained[i] ? v : xa[u];
-          om.Y[r + sm.ya[i]] = sm.ysc[i] * fma(sm.c[i], uu, -sm.s[i] * xb[u]);
+          om.Y[r + sm.ya[i]] = fma(sm.c[i], uu, -sm.s[i] * xb[u]);
           v = fma(sm.s[i], uu, sm.c[i] * xb[u]);
           if (sm.ends[i]) X[r + sm.b[i]] = v;
         } else {
+          // the carrier stays a pair (runs are long); the deflated output is a rotation
+          // of two unit-scale values and needs FP32 accuracy only
           const float4 q = sm.cs[i];
-          const Df cc = {q.x, q.y}, ss = {q.z, q.w}, xx = {narrow_rn(xb[u]), 0.f};
+          const Df cc = {q.x, q.y}, ss = {q.z, q.w};
+          const float xx = narrow_rn(xb[u]);
           const Df uu = sm.chained[i] ? vf : Df{narrow_rn(xa[u]), 0.f};
-          const Df out = df_add(df_mul(cc, uu), df_mul(Df{-ss.hi, -ss.lo}, xx));
-          const float ov = out.hi + out.lo;
-          om.Y[r + sm.ya[i]] = widen_f32(sm.ysc[i] < 0.0 ? -ov : ov);
-          vf = df_add(df_mul(ss, uu), df_mul(cc, xx));
+          float t = fmaf(cc.lo, uu.hi, -ss.lo * xx);
+          t = fmaf(cc.hi, uu.lo, t);
+          t = fmaf(-ss.hi, xx, t);
+          om.Y[r + sm.ya[i]] = widen_f32(fmaf(cc.hi, uu.hi, t));
+          vf = df_add(df_mul(ss, uu), df_mul(cc, Df{xx, 0.f}));
           if (sm.ends[i]) X[r + sm.b[i]] = widen_f32(vf.hi + vf.lo);
         }
       }
+    }
+#pragma unroll
+    for (int u = 0; u < kRotBatch; u++) {
+      xb[u] = nb[u];
+      xa[u] = na[u];
     }
   }
 }
@@ -287,10 +303,9 @@ __global__ void k_gather_columns(Eig e, const double* __restrict__ X, long long 
     int s = e.didx[c - k];
     if (e.defl[s] == 2) return;  // written by the rotation kernel
     int q = e.rank_defl[s];
-    double sc = om.colscale ? om.colscale[q] : 1.0;
     const double* src = X + (long long)e.perm[s] * ldx;
     double* dst = om.Y + out_col(om, q) * om.ldy;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = sc * src[r];
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = src[r];
   }
 }
 
@@ -662,19 +677,13 @@ __global__ void __launch_bounds__(128) k_gemm_f64(Eig e, FmmPlan f, int rows,
     int cc = c0 + tx * 4 + j;
     if (cc >= ncols) continue;
     double* col;
-    double sc = 1.0;
     if (STAGE == ST_P2M) col = f.Phi + (long long)(leaf * p + cc) * f.ldphi;
     else if (STAGE == ST_M2L) col = f.Psi + (long long)(leaf * p + cc) * f.ldphi;
-    else {
-      int jj = j0 + cc;
-      int q = e.rank_root[jj];
-      if (om.colscale) sc = om.colscale[q];
-      col = om.Y + out_col(om, q) * om.ldy;
-    }
+    else col = om.Y + out_col(om, e.rank_root[j0 + cc]) * om.ldy;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
       int r = r0 + ty * 4 + i;
-      if (r < rows) col[r] = sc * acc[i][j];
+      if (r < rows) col[r] = acc[i][j];
     }
   }
 }
