@@ -72,7 +72,9 @@ struct svdup_ctx {
   cudaStream_t left;   // the left-hand solves (high priority)
   cudaStream_t prod[2];  // the products with U and with V (low priority)
   cudaEvent_t ev_fork, ev_mid, ev_join;
-  cudaEvent_t ev[7];  // e1 ready, e2 ready, e3 ready, e4 ready, U done, V done, left done
+  // e1 ready, e2 ready, e3 ready, e4 ready, U done, V done, left done, e1 deflated,
+  // e1 merged, e3 deflated, e3 merged, e2 deflated, e2 leaves, e4 deflated, e4 leaves
+  cudaEvent_t ev[15];
 };
 
 namespace {
@@ -200,13 +202,26 @@ FmmPlan make_plan(Arena& ar, int N, int rows, double eps, int leaf, bool mixed) 
   f.T = ar.take<double>(L * f.p * (L + 1) * f.p);
   f.Lop = ar.take<double>((L + 1) * f.s * f.p);
   f.ldphi = rows > 0 ? rows : 1;
-  f.Phi = ar.take<double>((size_t)f.ldphi * L * f.p);
-  f.Psi = ar.take<double>((size_t)f.ldphi * (L + 1) * f.p);
-  f.rot = ar.take<unsigned char>(rotate_scratch_bytes(N, (int)rrows));
+  if (rows > 0) {  // operand scratch (a shared plan takes its partner's)
+    f.Phi = ar.take<double>((size_t)f.ldphi * L * f.p);
+    f.Psi = ar.take<double>((size_t)f.ldphi * (L + 1) * f.p);
+    f.rot = ar.take<unsigned char>(rotate_scratch_bytes(N, (int)rrows));
+  }
   return f;
 }
 
 // Split-tile buffers of the mixed product for up to `rows` rows and N columns (plan f).
+// A second plan for the same rows: its own leaves and operators (set up while the first
+// product still runs), the operand scratch (Phi, Psi, rotation scratch) shared.
+FmmPlan make_plan_shared(Arena& ar, int N, double eps, int leaf, bool mixed, const FmmPlan& sh) {
+  FmmPlan f = make_plan(ar, N, 0, eps, leaf, mixed);
+  f.ldphi = sh.ldphi;
+  f.Phi = sh.Phi;
+  f.Psi = sh.Psi;
+  f.rot = sh.rot;
+  return f;
+}
+
 MixPlan make_mix(Arena& ar, int rows, const FmmPlan& f) {
   MixPlan mp;
   memset(&mp, 0, sizeof(mp));
@@ -222,6 +237,22 @@ MixPlan make_mix(Arena& ar, int rows, const FmmPlan& f) {
   mp.Xp = ar.take<unsigned char>((size_t)mp.rt * mp.kx * kMixTileA);
   mp.Phip = ar.take<unsigned char>((size_t)mp.rt * mp.kphi * kMixTileA);
   mp.Psip = ar.take<unsigned char>((size_t)mp.rt * (L + 1) * (3 * 128 * kMixP * 2));
+  mp.Sp = ar.take<unsigned char>(L * hs * (3 * kMixP * 64 * 2));
+  mp.Tp = ar.take<unsigned char>((size_t)mp.ntT * mp.kphi * kMixTileA);
+  mp.Lp = ar.take<unsigned char>((L + 1) * (3 * (size_t)f.s * kMixP * 2));
+  mp.Cp = ar.take<unsigned char>((L + 1) * L * hs * (3 * (size_t)f.s * 64 * 2));
+  mp.nnear = ar.take<int>(L + 1);
+  mp.near = ar.take<int>((L + 1) * L);
+  mp.noff = ar.take<int>(L + 2);
+  mp.order = ar.take<int>(L + 1);
+  return mp;
+}
+
+// The second product's mixed plan: own operator tiles and lists, shared split operands.
+MixPlan make_mix_shared(Arena& ar, const FmmPlan& f, const MixPlan& sh) {
+  MixPlan mp = sh;
+  mp.fL = f.L;
+  const size_t hs = (size_t)f.s / 64, L = (size_t)f.Lmax;
   mp.Sp = ar.take<unsigned char>(L * hs * (3 * kMixP * 64 * 2));
   mp.Tp = ar.take<unsigned char>((size_t)mp.ntT * mp.kphi * kMixTileA);
   mp.Lp = ar.take<unsigned char>((L + 1) * (3 * (size_t)f.s * kMixP * 2));
@@ -279,8 +310,8 @@ struct UpdateWs {
       *h, *sign, *work;
   Eig E1, E2, E3, E4;
   double *XsL, *XsR, *WL, *WR;
-  FmmPlan FL, FR;
-  MixPlan ML, MR;
+  FmmPlan FL, FR, FL2, FR2;  // the second products' plans (mixed: own operators)
+  MixPlan ML, MR, ML2, MR2;
 };
 
 UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed) {
@@ -314,9 +345,17 @@ UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed
   u.FR = make_plan(ar, n, n, eps, leaf, mixed);
   memset(&u.ML, 0, sizeof(u.ML));
   memset(&u.MR, 0, sizeof(u.MR));
+  u.FL2 = u.FL;
+  u.FR2 = u.FR;
+  u.ML2 = u.ML;
+  u.MR2 = u.MR;
   if (mixed) {
     u.ML = make_mix(ar, m, u.FL);
     u.MR = make_mix(ar, n, u.FR);
+    u.FL2 = make_plan_shared(ar, m, eps, leaf, mixed, u.FL);
+    u.FR2 = make_plan_shared(ar, n, eps, leaf, mixed, u.FR);
+    u.ML2 = make_mix_shared(ar, u.FL2, u.ML);
+    u.MR2 = make_mix_shared(ar, u.FR2, u.MR);
   }
   return u;
 }
@@ -363,10 +402,15 @@ void stage_end(svdup_ctx* h) {
 // (fused with a transposed product when the next solve needs its z).
 // pairs: Loewner's zhat in double-float arithmetic (svdup_dfsum.cu), for solves whose
 // zhat feeds vectors only (never the z of another solve) in the mixed mode
-void queue_solve(svdup_ctx* h, cudaStream_t st, Eig e, bool pairs = false) {
+// Optional events mark the deflation (enough for the first half of the rotations) and
+// the merge (the final order, enough for the rest of a product's column work).
+void queue_solve(svdup_ctx* h, cudaStream_t st, Eig e, bool pairs = false,
+                 cudaEvent_t ev_defl = nullptr, cudaEvent_t ev_merge = nullptr) {
   launch_deflate(st, e, h->status);
+  if (ev_defl) cudaEventRecord(ev_defl, st);
   launch_secular(st, e, h->status, h->maxit);
   launch_merge(st, e);
+  if (ev_merge) cudaEventRecord(ev_merge, st);
   if (pairs) launch_loewner_df(st, e);
   else launch_loewner(st, e);
 }
@@ -398,22 +442,56 @@ void queue_product(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, do
   if (h->timing) launch_flop_count(st, e, f, rows, dense, h->flops_dev);
 }
 
-// The same product in split BF16 on the tensor cores (svdup_mixed.cu).
-void queue_product_mixed(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, double* X,
-                         long long ldx, OutMap om, int mode) {
-  int dense = use_dense(h, e.N, mode) ? 1 : 0;
+// The same product in split BF16 on the tensor cores (svdup_mixed.cu), in four phases
+// that an update spreads over its streams as their inputs become ready:
+//   prepare  the first half of the rotation scan           (deflation)
+//   xside    [leaves], the rotations' replay, the split X   (roots and final order)
+//   ops      [leaves], near lists, operator tiles           (zhat and column norms)
+//   mma      the three tensor-core stages
+// The gather places X's columns by the leaf offset that the leaves step finds, so the
+// leaves come with whichever of xside and ops runs first.
+MixPlan mix_rows(MixPlan mp, int rows) {
   mp.rows = rows;
   mp.rt = (rows + 127) / 128;
-  // the set-up (leaves, near lists, operator tiles) depends on the solve alone; it
-  // comes first because the gather places X's columns by the leaf offset it finds
-  stage_begin(h, SVDUP_STAGE_SETUP);
-  launch_fmm_setup(st, e, f, 0);
-  launch_mix_setup(st, e, f, mp, dense);
-  stage_end(h);
+  return mp;
+}
+
+void mix_prepare(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, const double* X,
+                 long long ldx) {
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_columns(st, e, X, ldx, rows, f.rot, true, om);
+  launch_rotate_prepare(st, e, X, ldx, rows, f.rot, true);
+  stage_end(h);
+}
+
+void mix_xside(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, double* X,
+               long long ldx, OutMap om, bool leaves) {
+  mp = mix_rows(mp, rows);
+  if (leaves) {
+    stage_begin(h, SVDUP_STAGE_SETUP);
+    launch_fmm_boxes(st, e, f, 0);
+    stage_end(h);
+  }
+  stage_begin(h, SVDUP_STAGE_GATHER);
+  launch_rotate_apply(st, e, X, ldx, rows, f.rot, true, om);
   launch_mix_gather(st, e, X, ldx, rows, mp, om);
   stage_end(h);
+}
+
+void mix_ops(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, int mode,
+             bool leaves) {
+  const int dense = use_dense(h, e.N, mode) ? 1 : 0;
+  mp = mix_rows(mp, rows);
+  stage_begin(h, SVDUP_STAGE_SETUP);
+  if (leaves) launch_fmm_boxes(st, e, f, 0);
+  launch_fmm_ops(st, e, f, 0);
+  launch_mix_setup(st, e, f, mp, dense);
+  stage_end(h);
+}
+
+void mix_mma(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, OutMap om,
+             int mode) {
+  const int dense = use_dense(h, e.N, mode) ? 1 : 0;
+  mp = mix_rows(mp, rows);
   if (!dense) {
     stage_begin(h, SVDUP_STAGE_P2M);
     launch_mix_stage(st, 0, e, f, mp, om, dense, h->status);
@@ -427,8 +505,17 @@ void queue_product_mixed(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPla
   stage_end(h);
   if (h->timing) {
     launch_flop_count(st, e, f, rows, dense, h->flops_dev);
-    launch_mix_flop_count(st, e, f, mp, dense, h->flops_dev + 3);
+    launch_mix_flop_count(st, e, f, mix_rows(mp, rows), dense, h->flops_dev + 3);
   }
+}
+
+// All four phases on one stream.
+void queue_product_mixed(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows,
+                         double* X, long long ldx, OutMap om, int mode) {
+  mix_prepare(h, st, e, f, rows, X, ldx);
+  mix_xside(h, st, e, f, mp, rows, X, ldx, om, true);
+  mix_ops(h, st, e, f, mp, rows, mode, false);
+  mix_mma(h, st, e, f, mp, rows, om, mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,7 +535,7 @@ int make_side(svdup_ctx* h) {
   ok = ok && cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
-  for (int i = 0; i < 7; i++)
+  for (int i = 0; i < 15; i++)
     ok = ok && cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -467,7 +554,7 @@ void free_side(svdup_ctx* h) {
   cudaEventDestroy(h->ev_fork);
   cudaEventDestroy(h->ev_mid);
   cudaEventDestroy(h->ev_join);
-  for (int i = 0; i < 7; i++) cudaEventDestroy(h->ev[i]);
+  for (int i = 0; i < 15; i++) cudaEventDestroy(h->ev[i]);
   cudaStreamDestroy(h->prod[0]);
   cudaStreamDestroy(h->prod[1]);
   cudaStreamDestroy(h->left);
@@ -846,45 +933,108 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   };
   if (!hand(h->ev_fork, st, sR) || (multi && cudaStreamWaitEvent(sL, h->ev_fork, 0) != cudaSuccess))
     return SVDUP_ECUDA;
-  stage_begin(h, SVDUP_STAGE_SOLVE);
-  // STEPs 3, 6: first right solve; STEP 7: second right solve
-  launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
-  queue_solve(h, sR, u.E3);
-  launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4);
-  if (!hand(h->ev[2], sR, pV)) return SVDUP_ECUDA;  // E3 ready: V's first product
-  launch_fill_second(sR, u.E4, u.E3.lam, u.zsec4);
-  queue_solve(h, sR, u.E4, mixed);
-  launch_norms(sR, u.E4, nullptr, nullptr, mixed);
-  if (multi && cudaEventRecord(h->ev[3], sR) != cudaSuccess) return SVDUP_ECUDA;  // E4 ready
-  // STEPs 2, 4: first left solve; its transposed product gives the second left z
-  launch_fill_left(sL, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
-  queue_solve(h, sL, u.E1);
-  launch_apply_qt(sL, u.E1, u.z2p, u.ysortL, u.zsec2);
-  if (!hand(h->ev[0], sL, pU)) return SVDUP_ECUDA;  // E1 ready: U's first product
-  // STEP 5: second left solve
-  launch_fill_second(sL, u.E2, u.E1.lam, u.zsec2);
-  queue_solve(h, sL, u.E2, mixed);
-  launch_norms(sL, u.E2, nullptr, nullptr, mixed);
-  stage_end(h);
-  // products: U -> W -> U (descending), V -> W -> V (descending; the signs follow)
   OutMap om1 = {u.WL, (long long)m, m, 0};
   OutMap om2 = {U, (long long)ldu, m, 1};
   OutMap om3 = {u.WR, (long long)n, n, 0};
   OutMap om4 = {V, (long long)ldv, n, 1};
-  if (mixed) {
-    queue_product_mixed(h, pU, u.E1, u.FL, u.ML, m, U, ldu, om1, mode);
-    queue_product_mixed(h, pV, u.E3, u.FR, u.MR, n, V, ldv, om3, mode);
+  if (mixed && multi) {
+    // Each product's column work starts as soon as its solve has deflated (the scan's
+    // first half) and merged (the replay, the split X), beside the rest of the solve;
+    // the second products' leaves and operators are set up on the solve streams while
+    // the first products still run.
+    auto wait = [&](cudaStream_t s_, cudaEvent_t ev) {
+      return cudaStreamWaitEvent(s_, ev, 0) == cudaSuccess;
+    };
+    // STEPs 3, 6: first right solve; STEP 7: second right solve
+    launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
+    queue_solve(h, sR, u.E3, false, h->ev[9], h->ev[10]);
+    launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4);
+    if (cudaEventRecord(h->ev[2], sR) != cudaSuccess) return SVDUP_ECUDA;  // E3 ready
+    launch_fill_second(sR, u.E4, u.E3.lam, u.zsec4);
+    queue_solve(h, sR, u.E4, mixed, h->ev[13]);
+    launch_fmm_boxes(sR, u.E4, u.FR2, 0);  // V2's leaves (the roots suffice)
+    if (cudaEventRecord(h->ev[14], sR) != cudaSuccess) return SVDUP_ECUDA;
+    launch_norms(sR, u.E4, nullptr, nullptr, mixed);
+    mix_ops(h, sR, u.E4, u.FR2, u.MR2, n, mode, false);
+    if (cudaEventRecord(h->ev[3], sR) != cudaSuccess) return SVDUP_ECUDA;  // E4, V2's operators
+    // STEPs 2, 4: first left solve; its transposed product gives the second left z
+    launch_fill_left(sL, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
+    queue_solve(h, sL, u.E1, false, h->ev[7], h->ev[8]);
+    launch_apply_qt(sL, u.E1, u.z2p, u.ysortL, u.zsec2);
+    if (cudaEventRecord(h->ev[0], sL) != cudaSuccess) return SVDUP_ECUDA;  // E1 ready
+    // STEP 5: second left solve
+    launch_fill_second(sL, u.E2, u.E1.lam, u.zsec2);
+    queue_solve(h, sL, u.E2, mixed, h->ev[11]);
+    launch_fmm_boxes(sL, u.E2, u.FL2, 0);  // U2's leaves (the roots suffice)
+    if (cudaEventRecord(h->ev[12], sL) != cudaSuccess) return SVDUP_ECUDA;
+    launch_norms(sL, u.E2, nullptr, nullptr, mixed);
+    mix_ops(h, sL, u.E2, u.FL2, u.ML2, m, mode, false);
+    if (cudaEventRecord(h->ev[1], sL) != cudaSuccess) return SVDUP_ECUDA;  // E2, U2's operators
+    // products: U -> W -> U (descending), V -> W -> V (descending; the signs follow)
+    if (!wait(pU, h->ev[7])) return SVDUP_ECUDA;
+    mix_prepare(h, pU, u.E1, u.FL, m, U, ldu);
+    if (!wait(pU, h->ev[8])) return SVDUP_ECUDA;
+    mix_xside(h, pU, u.E1, u.FL, u.ML, m, U, ldu, om1, true);
+    if (!wait(pU, h->ev[0])) return SVDUP_ECUDA;
+    mix_ops(h, pU, u.E1, u.FL, u.ML, m, mode, false);
+    mix_mma(h, pU, u.E1, u.FL, u.ML, m, om1, mode);
+    if (!wait(pV, h->ev[9])) return SVDUP_ECUDA;
+    mix_prepare(h, pV, u.E3, u.FR, n, V, ldv);
+    if (!wait(pV, h->ev[10])) return SVDUP_ECUDA;
+    mix_xside(h, pV, u.E3, u.FR, u.MR, n, V, ldv, om3, true);
+    if (!wait(pV, h->ev[2])) return SVDUP_ECUDA;
+    mix_ops(h, pV, u.E3, u.FR, u.MR, n, mode, false);
+    mix_mma(h, pV, u.E3, u.FR, u.MR, n, om3, mode);
+    // the second products: X is the first product's output (stream order)
+    if (!wait(pV, h->ev[13])) return SVDUP_ECUDA;
+    mix_prepare(h, pV, u.E4, u.FR2, n, u.WR, n);
+    if (!wait(pV, h->ev[14])) return SVDUP_ECUDA;
+    mix_xside(h, pV, u.E4, u.FR2, u.MR2, n, u.WR, n, om4, false);
+    if (!wait(pV, h->ev[3])) return SVDUP_ECUDA;
+    mix_mma(h, pV, u.E4, u.FR2, u.MR2, n, om4, mode);
+    if (!wait(pU, h->ev[11])) return SVDUP_ECUDA;
+    mix_prepare(h, pU, u.E2, u.FL2, m, u.WL, m);
+    if (!wait(pU, h->ev[12])) return SVDUP_ECUDA;
+    mix_xside(h, pU, u.E2, u.FL2, u.ML2, m, u.WL, m, om2, false);
+    if (!wait(pU, h->ev[1])) return SVDUP_ECUDA;
+    mix_mma(h, pU, u.E2, u.FL2, u.ML2, m, om2, mode);
   } else {
-    queue_product(h, pU, u.E1, u.FL, m, U, ldu, u.XsL, om1, mode);
-    queue_product(h, pV, u.E3, u.FR, n, V, ldv, u.XsR, om3, mode);
+    stage_begin(h, SVDUP_STAGE_SOLVE);
+    // STEPs 3, 6: first right solve; STEP 7: second right solve
+    launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
+    queue_solve(h, sR, u.E3);
+    launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4);
+    if (!hand(h->ev[2], sR, pV)) return SVDUP_ECUDA;  // E3 ready: V's first product
+    launch_fill_second(sR, u.E4, u.E3.lam, u.zsec4);
+    queue_solve(h, sR, u.E4, mixed);
+    launch_norms(sR, u.E4, nullptr, nullptr, mixed);
+    if (multi && cudaEventRecord(h->ev[3], sR) != cudaSuccess) return SVDUP_ECUDA;  // E4 ready
+    // STEPs 2, 4: first left solve; its transposed product gives the second left z
+    launch_fill_left(sL, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
+    queue_solve(h, sL, u.E1);
+    launch_apply_qt(sL, u.E1, u.z2p, u.ysortL, u.zsec2);
+    if (!hand(h->ev[0], sL, pU)) return SVDUP_ECUDA;  // E1 ready: U's first product
+    // STEP 5: second left solve
+    launch_fill_second(sL, u.E2, u.E1.lam, u.zsec2);
+    queue_solve(h, sL, u.E2, mixed);
+    launch_norms(sL, u.E2, nullptr, nullptr, mixed);
+    stage_end(h);
+    // products: U -> W -> U (descending), V -> W -> V (descending; the signs follow)
+    if (mixed) {
+      queue_product_mixed(h, pU, u.E1, u.FL, u.ML, m, U, ldu, om1, mode);
+      queue_product_mixed(h, pV, u.E3, u.FR, u.MR, n, V, ldv, om3, mode);
+    } else {
+      queue_product(h, pU, u.E1, u.FL, m, U, ldu, u.XsL, om1, mode);
+      queue_product(h, pV, u.E3, u.FR, n, V, ldv, u.XsR, om3, mode);
+    }
+    // V's second product, after its first (stream order) and E4 (the event above)
+    if (multi && cudaStreamWaitEvent(pV, h->ev[3], 0) != cudaSuccess) return SVDUP_ECUDA;
+    if (mixed) queue_product_mixed(h, pV, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
+    else queue_product(h, pV, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
+    if (!hand(h->ev[1], sL, pU)) return SVDUP_ECUDA;  // E2 ready: U's second product
+    if (mixed) queue_product_mixed(h, pU, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
+    else queue_product(h, pU, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
   }
-  // V's second product, after its first (stream order) and E4 (the event above)
-  if (multi && cudaStreamWaitEvent(pV, h->ev[3], 0) != cudaSuccess) return SVDUP_ECUDA;
-  if (mixed) queue_product_mixed(h, pV, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
-  else queue_product(h, pV, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
-  if (!hand(h->ev[1], sL, pU)) return SVDUP_ECUDA;  // E2 ready: U's second product
-  if (mixed) queue_product_mixed(h, pU, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
-  else queue_product(h, pU, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
   // sign pairing of right vectors with left vectors (before S is overwritten); in the
   // mixed mode its sums run on FP32 pairs (only the signs are used)
   stage_begin(h, SVDUP_STAGE_SIGN);

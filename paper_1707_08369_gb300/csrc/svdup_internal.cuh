@@ -279,10 +279,16 @@ void launch_fill_random(cudaStream_t st, int rows, int N, double* X, double* d, 
 // arithmetic (see svdup_product.cu)
 size_t rotate_scratch_bytes(int N, int rows);
 // Deflated columns (rotation outputs) go straight to their output column in om.
+void launch_rotate_prepare(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
+                           void* scratch, bool mixed);
+void launch_rotate_apply(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
+                         void* scratch, bool mixed, OutMap om);
 void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
                            void* scratch, bool mixed, OutMap om);
 void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
                            double* Xs, long long ldxs, OutMap om);
+void launch_fmm_boxes(cudaStream_t st, Eig e, FmmPlan f, int dense);
+void launch_fmm_ops(cudaStream_t st, Eig e, FmmPlan f, int dense);
 void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense);
 // adds the useful flops of one product's P2M, M2L and output stages to acc[0..2]
 void launch_flop_count(cudaStream_t st, Eig e, FmmPlan f, int rows, int dense, double* acc);

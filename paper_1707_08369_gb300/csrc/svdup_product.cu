@@ -257,8 +257,7 @@ size_t rotate_scratch_bytes(int N, int rows) {
   return nch * 8 + (size_t)N * 16 + 2 * nch * rr * 8 + 256;
 }
 
-void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
-                           void* scratch, bool mixed, OutMap om) {
+static RotScratch rot_scratch(Eig e, int rows, void* scratch) {
   const int nch = (e.N + kRotChunk - 1) / kRotChunk;
   const size_t rr = (size_t)(rows > 0 ? rows : 1);
   RotScratch w;
@@ -269,7 +268,15 @@ void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int
   p += (size_t)e.N * 16;
   w.Bw = (double*)p;
   w.Xw = w.Bw + (size_t)nch * rr;
+  return w;
+}
+
+// The scan's first half (chunk factors, offsets, carries): needs the deflation only.
+void launch_rotate_prepare(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
+                           void* scratch, bool mixed) {
+  const int nch = (e.N + kRotChunk - 1) / kRotChunk;
   if (rows <= 0 || nch == 0) return;
+  const RotScratch w = rot_scratch(e, rows, scratch);
   k_rot_prep<<<1, 1024, 0, st>>>(e, w);
   SVDUP_COUNT_LAUNCH();
   dim3 g((rows + 127) / 128, nch);
@@ -279,9 +286,25 @@ void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int
   if (mixed) k_rot_carry<true><<<(rows + 127) / 128, 128, 0, st>>>(e, rows, w);
   else k_rot_carry<false><<<(rows + 127) / 128, 128, 0, st>>>(e, rows, w);
   SVDUP_COUNT_LAUNCH();
+}
+
+// The replay: deflated columns go to their output columns, which needs the final order
+// of the eigenvalues (after the roots and their merge with the deflated values).
+void launch_rotate_apply(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
+                         void* scratch, bool mixed, OutMap om) {
+  const int nch = (e.N + kRotChunk - 1) / kRotChunk;
+  if (rows <= 0 || nch == 0) return;
+  const RotScratch w = rot_scratch(e, rows, scratch);
+  dim3 g((rows + 127) / 128, nch);
   if (mixed) k_rot_apply<true><<<g, 128, 0, st>>>(e, X, ldx, rows, w, om);
   else k_rot_apply<false><<<g, 128, 0, st>>>(e, X, ldx, rows, w, om);
   SVDUP_COUNT_LAUNCH();
+}
+
+void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
+                           void* scratch, bool mixed, OutMap om) {
+  launch_rotate_prepare(st, e, X, ldx, rows, scratch, mixed);
+  launch_rotate_apply(st, e, X, ldx, rows, scratch, mixed, om);
 }
 
 __device__ __forceinline__ long long out_col(const OutMap& om, int q) {
@@ -547,9 +570,15 @@ __global__ void k_fmm_L(Eig e, FmmPlan f) {
   }
 }
 
-void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense) {
+// Leaves and their boxes: the poles (and the leaf offset at an isolated top group) and the
+// roots; no zhat or norms.
+void launch_fmm_boxes(cudaStream_t st, Eig e, FmmPlan f, int dense) {
   k_fmm_boxes<<<(f.Lmax + 128) / 128, 128, 0, st>>>(e, f, dense);
   SVDUP_COUNT_LAUNCH();
+}
+
+// Near lists and the far-field operators (S carries zhat, L the column norms).
+void launch_fmm_ops(cudaStream_t st, Eig e, FmmPlan f, int dense) {
   k_fmm_near<<<(f.Lmax + 128) / 128, 128, 0, st>>>(e, f, dense);
   SVDUP_COUNT_LAUNCH();
   if (dense) return;
@@ -563,6 +592,11 @@ void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense) {
   int tb = (int)((nt + 255) / 256);
   k_fmm_T<<<tb, 256, 0, st>>>(f);
   SVDUP_COUNT_LAUNCH();
+}
+
+void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense) {
+  launch_fmm_boxes(st, e, f, dense);
+  launch_fmm_ops(st, e, f, dense);
 }
 
 // ---------------------------------------------------------------------------
