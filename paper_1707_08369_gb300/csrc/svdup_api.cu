@@ -136,8 +136,9 @@ Eig make_eig(Arena& ar, int N) {
   e.dint = ar.take<int>(4);
   e.dflt = ar.take<double>(4);
   e.ovh = ar.take<int>(kMaxOverrunList);
-  e.ovW = ar.take<double>(kMaxOverrunList);
-  e.ovM = ar.take<double>(kMaxOverrunList);
+  e.ovW = ar.take<float2>(kMaxOverrunList);
+  e.ovM = ar.take<float2>(kMaxOverrunList);
+  e.ovR = ar.take<double>(kMaxOverrunList);
   const size_t nbox = (n + 63) / 64;
   e.sqb = ar.take<double>(2 * nbox);
   e.sqn = ar.take<int>(2 * nbox);

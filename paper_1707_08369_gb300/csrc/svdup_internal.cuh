@@ -131,8 +131,8 @@ struct Eig {
   double* tol;     // deflation tolerance (1 value)
   // deflation scratch: the survivors of case (1) (scaled d and z, sorted positions, run
   // flags, rotation index, kept index, run start), the candidate bitmask (N / 32 + 1
-  // words), the survivor count (dint), scaled tolerance and scalings (dflt), and per
-  // walking range the run it carried into the next range (head, carrier)
+  // words), the survivor count (dint), scaled tolerance, scalings and 1 / tol (dflt), and
+  // per walking range the run it carried into the next range (head, carrier)
   double* sd;
   double* sz;
   int* spos;
@@ -144,8 +144,9 @@ struct Eig {
   int* dint;
   double* dflt;
   int* ovh;
-  double* ovW;
-  double* ovM;
+  float2* ovW;  // the carried run: sum z^2 and sum z^2 (d - ref) / tol as FP32 pairs,
+  float2* ovM;
+  double* ovR;  // and its first pole ref
   // far-field secular evaluation (null: direct sums only): per box of 64 roots its
   // origin and half width, its near pole range, and the far sums at its nodes
   double* sqb;

@@ -266,7 +266,7 @@ struct DeflWalk {
   const unsigned* cm;   // bit i: pair (i-1, i) passes with the original values
   unsigned char* brk;   // 1: survivor i starts a run
   int nk;
-  double tol2;
+  double itol;          // 1 / tol (tol in the scaled units of kd)
 
   // first i >= from with bit i set (nk if none)
   __device__ int next_set(int from, int lane) const {
@@ -322,80 +322,133 @@ struct DeflWalk {
     return b;
   }
 
+  // The merge test in the units of a run, on FP32 pairs (svdup_df.cuh): d is measured
+  // from the run's first pole (ref) in multiples of tol, dh_i = (d_i - ref) / tol (one
+  // FP64 subtraction, exact for close poles, and one product), W = sum z^2 and
+  // M = sum z^2 dh over the run so far; survivor i merges when
+  //   (dh_i W - M)^2 z_i^2 <= W (W + z_i^2)^2        (merges(), with tol = 1).
+  // Both sides are homogeneous of degree 6 in z, so W, M and z_i^2 are first scaled by
+  // the power of two that brings W + z_i^2 into [1, 2).  Then nothing overflows
+  // (|dh| < 2^52), and the right side stays above 2^-90 unless the carrier is that much
+  // lighter than z_i^2; there the test is taken in FP64.  The measured differences
+  // stay small along a run, so the pairs' 2^-46 leave the decisions those of exact
+  // arithmetic but for margins below about 2^-40.
+  __device__ bool merge_df(Df W, Df M, Df z2, Df dh, double dhd) const {
+    const Df s = df_add(W, z2);
+    const float sc = pow2f(127 - ((__float_as_int(s.hi) >> 23) & 0xff));
+    const Df Ws = {W.hi * sc, W.lo * sc}, Ms = {M.hi * sc, M.lo * sc};
+    const Df z2s = {z2.hi * sc, z2.lo * sc}, ss = {s.hi * sc, s.lo * sc};
+    const Df g = df_add(df_mul(dh, Ws), df_neg(Ms));
+    const Df lhs = df_mul(df_sqr(g), z2s);
+    const Df rhs = df_mul(Ws, df_sqr(ss));
+    if (!(rhs.hi >= 0x1p-90f)) {
+      const double Wd = df_to_f64(W, 0), Md = df_to_f64(M, 0), z2d = df_to_f64(z2, 0);
+      const double gd = fma(dhd, Wd, -Md), sd = Wd + z2d;
+      return gd * gd * z2d <= Wd * sd * sd;
+    }
+    return df_add(rhs, df_neg(lhs)).hi >= 0.0f;
+  }
+
   // The sequential rule from survivor pos (pos <= lim): a run in progress merges survivor
-  // i when the carrier test passes, else i starts a new run; a run of one at i - 1 can
-  // only grow where bit i is set, so stretches without bits are skipped.  The carrier of
-  // the run through pos - 1 is (W, M), or with fresh the run is survivor pos - 1 alone.
+  // i when the test passes against its carrier, else i starts a new run; a run of one
+  // at i - 1 can grow only where bit i is set (and the test passes), so stretches without
+  // bits are skipped.  The carrier of the run through pos - 1 is (W, M) with first pole
+  // ref, or with fresh the run is survivor pos - 1 alone.  A run of one at p has the
+  // carrier (z_p^2, 0) and ref = d_p whichever way the walk reaches it, so the rule is a
+  // function of the state alone.
   // One step tests a window of 32 survivors (pos's aligned window): lane l against the
   // carrier that exists if every earlier lane merged (the carrier plus the lanes'
-  // exclusive prefix sums of z^2 and z^2 d), which is the sequential carrier up to the
+  // exclusive prefix sums of z^2 and z^2 dh), which is the sequential carrier up to the
   // first lane that fails; a failing lane starts a run, and the rest of the window is
-  // tested again from it without reloading.  A run of one gets its carrier by the same
-  // operations as the bitmask (0 + z^2 and z^2 d), so the two agree.
+  // tested again from it without reloading.
   // Plain walk (RESUME false): stops at survivor lim; returns lim + 1 when the run merged
-  // lim (its carrier in oW, oM: it continues into the next range), else -1.
+  // lim (its carrier in oW, oM, oref: it continues into the next range), else -1.
   // RESUME: lim = nk - 1; flags are rewritten, and the walk stops at the first survivor
   // where it starts a run whose flag was already set (there it agrees with the plain
   // walk that wrote the flags); returns that survivor, or nk.
   template <bool RESUME>
-  __device__ int walk(int pos, bool fresh, double W, double M, int lim, int lane, double& oW,
-                      double& oM) const {
-    int pw = -1;  // the window whose values are already loaded (prefetched)
-    double pz = 0.0, pd = 0.0;
-    unsigned pword = 0u;
+  __device__ int walk(int pos, bool fresh, Df W, Df M, double ref, int lim, int lane, Df& oW,
+                      Df& oM, double& oref) const {
+    // the next two windows load while this one is tested (a long run takes them in turn)
+    int pw1 = -1, pw2 = -1;
+    double pz1 = 0.0, pd1 = 0.0, pz2 = 0.0, pd2 = 0.0;
+    unsigned pword1 = 0u, pword2 = 0u;
+    const Df zero = {0.0f, 0.0f};
     while (true) {
       const int w0 = pos & ~31;
       double zi, di;
       unsigned word;
-      if (pw == w0) {
-        zi = pz;
-        di = pd;
-        word = pword;
+      if (pw1 == w0) {
+        zi = pz1;
+        di = pd1;
+        word = pword1;
+        pw1 = pw2;
+        pz1 = pz2;
+        pd1 = pd2;
+        pword1 = pword2;
       } else {
         const int i = w0 + lane;
         zi = i < nk ? kz[i] : 0.0;
         di = i < nk ? kd[i] : 0.0;
         word = cm[w0 >> 5];
+        pw1 = w0 + 32;
+        if (pw1 < nk) {
+          const int j = pw1 + lane;
+          pz1 = j < nk ? kz[j] : 0.0;
+          pd1 = j < nk ? kd[j] : 0.0;
+          pword1 = cm[pw1 >> 5];
+        }
       }
-      pw = w0 + 32;  // the next window loads while this one is tested
-      if (pw < nk) {
-        const int i = pw + lane;
-        pz = i < nk ? kz[i] : 0.0;
-        pd = i < nk ? kd[i] : 0.0;
-        pword = cm[pw >> 5];
+      pw2 = w0 + 64;
+      if (pw2 < nk) {
+        const int j = pw2 + lane;
+        pz2 = j < nk ? kz[j] : 0.0;
+        pd2 = j < nk ? kd[j] : 0.0;
+        pword2 = cm[pw2 >> 5];
       }
-      const double z2 = zi * zi, dz = z2 * di;
+      const Df z2 = df_sqr(df_from_f64(zi, 0));
       int start = pos - w0;  // lanes >= start are tested
       int src = start;       // lanes >= src are in the run, after the carrier (Wb, Mb)
-      double Wb = W, Mb = M;
+      Df Wb = W, Mb = M;
       if (fresh) {  // the run is survivor pos - 1 alone, which lies in this window
         src = start - 1;
-        Wb = 0.0;
-        Mb = 0.0;
+        ref = __shfl_sync(0xffffffffu, di, src);
+        Wb = zero;
+        Mb = zero;
       }
+      double dhd = (di - ref) * itol;
+      Df dh = df_from_f64(dhd, 0);
+      Df dz = df_mul(z2, dh);
       const int last = min(31, lim - w0);
       while (true) {
-        double v2 = lane >= src ? z2 : 0.0, vd = lane >= src ? dz : 0.0;
+        Df v2 = lane >= src ? z2 : zero, vd = lane >= src ? dz : zero;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const double a2 = __shfl_up_sync(0xffffffffu, v2, o);
-          const double ad = __shfl_up_sync(0xffffffffu, vd, o);
-          if (lane >= o) { v2 += a2; vd += ad; }
+          const Df a2 = {__shfl_up_sync(0xffffffffu, v2.hi, o), __shfl_up_sync(0xffffffffu, v2.lo, o)};
+          const Df ad = {__shfl_up_sync(0xffffffffu, vd.hi, o), __shfl_up_sync(0xffffffffu, vd.lo, o)};
+          if (lane >= o) {
+            v2 = df_add(v2, a2);
+            vd = df_add(vd, ad);
+          }
         }
-        double e2 = __shfl_up_sync(0xffffffffu, v2, 1), ed = __shfl_up_sync(0xffffffffu, vd, 1);
-        if (lane == 0) { e2 = 0.0; ed = 0.0; }
+        Df e2 = {__shfl_up_sync(0xffffffffu, v2.hi, 1), __shfl_up_sync(0xffffffffu, v2.lo, 1)};
+        Df ed = {__shfl_up_sync(0xffffffffu, vd.hi, 1), __shfl_up_sync(0xffffffffu, vd.lo, 1)};
+        if (lane == 0) { e2 = zero; ed = zero; }
         const bool act = lane >= start && lane <= last;
-        const bool ok = act && merges(di, zi, Wb + e2, Mb + ed, tol2);
+        const bool ok = act && merge_df(df_add(Wb, e2), df_add(Mb, ed), z2, dh, dhd);
         const unsigned fail = __ballot_sync(0xffffffffu, act && !ok);
         const int f = fail ? __ffs(fail) - 1 : last + 1;
         if (lane >= start && lane < f) brk[w0 + lane] = 0;
         if (!fail) {  // every tested lane merged
-          const double Wn = Wb + __shfl_sync(0xffffffffu, v2, last);
-          const double Mn = Mb + __shfl_sync(0xffffffffu, vd, last);
+          const Df Wn = df_add(Wb, Df{__shfl_sync(0xffffffffu, v2.hi, last),
+                                      __shfl_sync(0xffffffffu, v2.lo, last)});
+          const Df Mn = df_add(Mb, Df{__shfl_sync(0xffffffffu, vd.hi, last),
+                                      __shfl_sync(0xffffffffu, vd.lo, last)});
           if (w0 + last >= lim) {
             if (RESUME) return nk;
             oW = Wn;
             oM = Mn;
+            oref = ref;
             return lim + 1 < nk ? lim + 1 : -1;
           }
           W = Wn;
@@ -418,25 +471,29 @@ struct DeflWalk {
           if (q < h) return q;
         }
         if (h > lim) return RESUME ? nk : -1;
-        if (h < w0 + 32) {  // a run of one at h - 1 in this window
+        if (h < w0 + 32) {  // a run of one at h - 1 in this window: measure from it
           src = h - 1 - w0;
           start = h - w0;
-          Wb = 0.0;
-          Mb = 0.0;
+          Wb = zero;
+          Mb = zero;
+          ref = __shfl_sync(0xffffffffu, di, src);
+          dhd = (di - ref) * itol;
+          dh = df_from_f64(dhd, 0);
+          dz = df_mul(z2, dh);
           continue;
         }
         pos = h;
+        M = zero;
         if (h & 31) {
           fresh = true;
         } else if (h == w0 + 32) {  // survivor h - 1 is this window's last lane
           fresh = false;
-          W = __shfl_sync(0xffffffffu, z2, 31);
-          M = __shfl_sync(0xffffffffu, dz, 31);
+          W = Df{__shfl_sync(0xffffffffu, z2.hi, 31), __shfl_sync(0xffffffffu, z2.lo, 31)};
+          ref = __shfl_sync(0xffffffffu, di, 31);
         } else {
           fresh = false;
-          const double zj = kz[h - 1];
-          W = zj * zj;
-          M = W * kd[h - 1];
+          W = df_sqr(df_from_f64(kz[h - 1], 0));
+          ref = kd[h - 1];
         }
         break;
       }
@@ -489,6 +546,7 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate_pre(Eig e, int* sta
       e.dflt[0] = tolS * tolS;
       e.dflt[1] = dsc;
       e.dflt[2] = zsc;
+      e.dflt[3] = tolS > 0.0 ? 1.0 / tolS : 0.0;
       if (!isfinite(s_tol) || !isfinite(rho)) latch(status, SVDUP_ENONFINITE);
     }
   }
@@ -555,27 +613,29 @@ __global__ void __launch_bounds__(32) k_deflate_walk(Eig e, int R) {
   const int slot = blockIdx.x;
   const int r0 = slot * R;
   int ov = -1;
-  double oW = 0.0, oM = 0.0;
+  Df oW = {0.0f, 0.0f}, oM = {0.0f, 0.0f};
+  double oref = 0.0;
   if (r0 < nk) {
-    const DeflWalk dw = {e.sd, e.sz, e.dmask, e.sbrk, nk, e.dflt[0]};
+    const DeflWalk dw = {e.sd, e.sz, e.dmask, e.sbrk, nk, e.dflt[3]};
     const int r1 = min(nk, r0 + R);
     const int h0 = dw.first_head(r0, lane);
     if (h0 < r1) {
       const int H = dw.first_head(r1, lane);
-      double W = 0.0, M = 0.0;
+      Df W = {0.0f, 0.0f};
+      double ref = 0.0;
       bool fresh = (h0 & 31) != 0;
-      if (!fresh) {
-        const double zj = e.sz[h0 - 1];
-        W = zj * zj;
-        M = W * e.sd[h0 - 1];
+      if (!fresh) {  // a run of one at h0 - 1, in the previous window
+        W = df_sqr(df_from_f64(e.sz[h0 - 1], 0));
+        ref = e.sd[h0 - 1];
       }
-      ov = dw.walk<false>(h0, fresh, W, M, H - 1, lane, oW, oM);
+      ov = dw.walk<false>(h0, fresh, W, Df{0.0f, 0.0f}, ref, H - 1, lane, oW, oM, oref);
     }
   }
   if (lane == 0) {
     e.ovh[slot] = ov;
-    e.ovW[slot] = oW;
-    e.ovM[slot] = oM;
+    e.ovW[slot] = make_float2(oW.hi, oW.lo);
+    e.ovM[slot] = make_float2(oM.hi, oM.lo);
+    e.ovR[slot] = oref;
   }
 }
 
@@ -592,13 +652,16 @@ __global__ void __launch_bounds__(kDeflateThreads) k_deflate_fix(Eig e, int nslo
   for (int s = tid; s < nslots; s += nt) sov[s] = e.ovh[s];
   __syncthreads();
   if (wid == 0) {
-    const DeflWalk dw = {e.sd, e.sz, e.dmask, brk, nk, e.dflt[0]};
+    const DeflWalk dw = {e.sd, e.sz, e.dmask, brk, nk, e.dflt[3]};
     int done = -1;
     for (int s = 0; s < nslots; s++) {
       const int H = sov[s];
       if (H < 0 || H <= done) continue;  // none, or redone by an earlier resume
-      double oW, oM;
-      done = dw.walk<true>(H, false, e.ovW[s], e.ovM[s], nk - 1, lane, oW, oM);
+      Df oW, oM;
+      double oref;
+      const float2 w = e.ovW[s], mm = e.ovM[s];
+      done = dw.walk<true>(H, false, Df{w.x, w.y}, Df{mm.x, mm.y}, e.ovR[s], nk - 1, lane, oW, oM,
+                           oref);
     }
   }
   __syncthreads();
