@@ -311,6 +311,7 @@ struct UpdateWs {
       *h, *sign, *work;
   Eig E1, E2, E3, E4;
   double *XsL, *XsR, *WL, *WR;
+  float *WLf, *WRf;  // the mixed form's intermediates (FP32-accurate by construction)
   FmmPlan FL, FR, FL2, FR2;  // the second products' plans (mixed: own operators)
   MixPlan ML, MR, ML2, MR2;
 };
@@ -340,8 +341,10 @@ UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed
   u.E4 = make_eig(ar, n);
   u.XsL = mixed ? nullptr : ar.take<double>((size_t)m * m);
   u.XsR = mixed ? nullptr : ar.take<double>((size_t)n * n);
-  u.WL = ar.take<double>((size_t)m * m);
-  u.WR = ar.take<double>((size_t)n * n);
+  u.WL = mixed ? nullptr : ar.take<double>((size_t)m * m);
+  u.WR = mixed ? nullptr : ar.take<double>((size_t)n * n);
+  u.WLf = mixed ? ar.take<float>((size_t)m * m) : nullptr;
+  u.WRf = mixed ? ar.take<float>((size_t)n * n) : nullptr;
   u.FL = make_plan(ar, m, m, eps, leaf, mixed);
   u.FR = make_plan(ar, n, n, eps, leaf, mixed);
   memset(&u.ML, 0, sizeof(u.ML));
@@ -457,15 +460,16 @@ MixPlan mix_rows(MixPlan mp, int rows) {
   return mp;
 }
 
-void mix_prepare(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, const double* X,
-                 long long ldx) {
+// X is FP64, or the FP32 intermediate when xf32.
+void mix_prepare(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, const void* X,
+                 bool xf32, long long ldx) {
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_prepare(st, e, X, ldx, rows, f.rot, true);
+  launch_rotate_prepare(st, e, X, ldx, rows, f.rot, true, xf32);
   stage_end(h);
 }
 
-void mix_xside(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, double* X,
-               long long ldx, OutMap om, bool leaves) {
+void mix_xside(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, void* X,
+               bool xf32, long long ldx, OutMap om, bool leaves) {
   mp = mix_rows(mp, rows);
   if (leaves) {
     stage_begin(h, SVDUP_STAGE_SETUP);
@@ -473,8 +477,8 @@ void mix_xside(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int 
     stage_end(h);
   }
   stage_begin(h, SVDUP_STAGE_GATHER);
-  launch_rotate_apply(st, e, X, ldx, rows, f.rot, true, om);
-  launch_mix_gather(st, e, X, ldx, rows, mp, om);
+  launch_rotate_apply(st, e, X, ldx, rows, f.rot, true, om, xf32);
+  launch_mix_gather(st, e, X, xf32, ldx, rows, mp, om);
   stage_end(h);
 }
 
@@ -512,9 +516,9 @@ void mix_mma(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int ro
 
 // All four phases on one stream.
 void queue_product_mixed(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows,
-                         double* X, long long ldx, OutMap om, int mode) {
-  mix_prepare(h, st, e, f, rows, X, ldx);
-  mix_xside(h, st, e, f, mp, rows, X, ldx, om, true);
+                         void* X, bool xf32, long long ldx, OutMap om, int mode) {
+  mix_prepare(h, st, e, f, rows, X, xf32, ldx);
+  mix_xside(h, st, e, f, mp, rows, X, xf32, ldx, om, true);
   mix_ops(h, st, e, f, mp, rows, mode, false);
   mix_mma(h, st, e, f, mp, rows, om, mode);
 }
@@ -934,9 +938,9 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   };
   if (!hand(h->ev_fork, st, sR) || (multi && cudaStreamWaitEvent(sL, h->ev_fork, 0) != cudaSuccess))
     return SVDUP_ECUDA;
-  OutMap om1 = {u.WL, (long long)m, m, 0};
+  OutMap om1 = {u.WL, (long long)m, m, 0, u.WLf};
   OutMap om2 = {U, (long long)ldu, m, 1};
-  OutMap om3 = {u.WR, (long long)n, n, 0};
+  OutMap om3 = {u.WR, (long long)n, n, 0, u.WRf};
   OutMap om4 = {V, (long long)ldv, n, 1};
   if (mixed && multi) {
     // Each product's column work starts as soon as its solve has deflated (the scan's
@@ -973,30 +977,30 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     if (cudaEventRecord(h->ev[1], sL) != cudaSuccess) return SVDUP_ECUDA;  // E2, U2's operators
     // products: U -> W -> U (descending), V -> W -> V (descending; the signs follow)
     if (!wait(pU, h->ev[7])) return SVDUP_ECUDA;
-    mix_prepare(h, pU, u.E1, u.FL, m, U, ldu);
+    mix_prepare(h, pU, u.E1, u.FL, m, U, false, ldu);
     if (!wait(pU, h->ev[8])) return SVDUP_ECUDA;
-    mix_xside(h, pU, u.E1, u.FL, u.ML, m, U, ldu, om1, true);
+    mix_xside(h, pU, u.E1, u.FL, u.ML, m, U, false, ldu, om1, true);
     if (!wait(pU, h->ev[0])) return SVDUP_ECUDA;
     mix_ops(h, pU, u.E1, u.FL, u.ML, m, mode, false);
     mix_mma(h, pU, u.E1, u.FL, u.ML, m, om1, mode);
     if (!wait(pV, h->ev[9])) return SVDUP_ECUDA;
-    mix_prepare(h, pV, u.E3, u.FR, n, V, ldv);
+    mix_prepare(h, pV, u.E3, u.FR, n, V, false, ldv);
     if (!wait(pV, h->ev[10])) return SVDUP_ECUDA;
-    mix_xside(h, pV, u.E3, u.FR, u.MR, n, V, ldv, om3, true);
+    mix_xside(h, pV, u.E3, u.FR, u.MR, n, V, false, ldv, om3, true);
     if (!wait(pV, h->ev[2])) return SVDUP_ECUDA;
     mix_ops(h, pV, u.E3, u.FR, u.MR, n, mode, false);
     mix_mma(h, pV, u.E3, u.FR, u.MR, n, om3, mode);
     // the second products: X is the first product's output (stream order)
     if (!wait(pV, h->ev[13])) return SVDUP_ECUDA;
-    mix_prepare(h, pV, u.E4, u.FR2, n, u.WR, n);
+    mix_prepare(h, pV, u.E4, u.FR2, n, u.WRf, true, n);
     if (!wait(pV, h->ev[14])) return SVDUP_ECUDA;
-    mix_xside(h, pV, u.E4, u.FR2, u.MR2, n, u.WR, n, om4, false);
+    mix_xside(h, pV, u.E4, u.FR2, u.MR2, n, u.WRf, true, n, om4, false);
     if (!wait(pV, h->ev[3])) return SVDUP_ECUDA;
     mix_mma(h, pV, u.E4, u.FR2, u.MR2, n, om4, mode);
     if (!wait(pU, h->ev[11])) return SVDUP_ECUDA;
-    mix_prepare(h, pU, u.E2, u.FL2, m, u.WL, m);
+    mix_prepare(h, pU, u.E2, u.FL2, m, u.WLf, true, m);
     if (!wait(pU, h->ev[12])) return SVDUP_ECUDA;
-    mix_xside(h, pU, u.E2, u.FL2, u.ML2, m, u.WL, m, om2, false);
+    mix_xside(h, pU, u.E2, u.FL2, u.ML2, m, u.WLf, true, m, om2, false);
     if (!wait(pU, h->ev[1])) return SVDUP_ECUDA;
     mix_mma(h, pU, u.E2, u.FL2, u.ML2, m, om2, mode);
   } else {
@@ -1022,18 +1026,18 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     stage_end(h);
     // products: U -> W -> U (descending), V -> W -> V (descending; the signs follow)
     if (mixed) {
-      queue_product_mixed(h, pU, u.E1, u.FL, u.ML, m, U, ldu, om1, mode);
-      queue_product_mixed(h, pV, u.E3, u.FR, u.MR, n, V, ldv, om3, mode);
+      queue_product_mixed(h, pU, u.E1, u.FL, u.ML, m, U, false, ldu, om1, mode);
+      queue_product_mixed(h, pV, u.E3, u.FR, u.MR, n, V, false, ldv, om3, mode);
     } else {
       queue_product(h, pU, u.E1, u.FL, m, U, ldu, u.XsL, om1, mode);
       queue_product(h, pV, u.E3, u.FR, n, V, ldv, u.XsR, om3, mode);
     }
     // V's second product, after its first (stream order) and E4 (the event above)
     if (multi && cudaStreamWaitEvent(pV, h->ev[3], 0) != cudaSuccess) return SVDUP_ECUDA;
-    if (mixed) queue_product_mixed(h, pV, u.E4, u.FR, u.MR, n, u.WR, n, om4, mode);
+    if (mixed) queue_product_mixed(h, pV, u.E4, u.FR, u.MR, n, u.WRf, true, n, om4, mode);
     else queue_product(h, pV, u.E4, u.FR, n, u.WR, n, u.XsR, om4, mode);
     if (!hand(h->ev[1], sL, pU)) return SVDUP_ECUDA;  // E2 ready: U's second product
-    if (mixed) queue_product_mixed(h, pU, u.E2, u.FL, u.ML, m, u.WL, m, om2, mode);
+    if (mixed) queue_product_mixed(h, pU, u.E2, u.FL, u.ML, m, u.WLf, true, m, om2, mode);
     else queue_product(h, pU, u.E2, u.FL, m, u.WL, m, u.XsL, om2, mode);
   }
   // sign pairing of right vectors with left vectors (before S is overwritten); in the
@@ -1202,7 +1206,7 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
   queue_solve(h, st, e, mixed);
   launch_norms(st, e, nullptr, nullptr, mixed);
   OutMap om = {Y, (long long)ldy, N, 0};
-  if (mixed) queue_product_mixed(h, st, e, f, mp, rows, Xw, rows, om, mode);
+  if (mixed) queue_product_mixed(h, st, e, f, mp, rows, Xw, false, rows, om, mode);
   else queue_product(h, st, e, f, rows, Xw, rows, Xs, om, mode);
   cudaMemcpyAsync(lam, e.lam, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
   return check_launch();

@@ -164,12 +164,14 @@ struct Eig {
 };
 
 // Column mapping of a product's output: physical column of final index q is
-//   out_rev ? (out_n - 1 - q) : q.
+//   out_rev ? (out_n - 1 - q) : q.  Yf, when set, replaces Y by an FP32 matrix (the
+// mixed form's intermediate W; only its kernels write it).
 struct OutMap {
   double* Y;
   long long ldy;
   int out_n;
   int out_rev;
+  float* Yf;
 };
 
 // FMM (flat Chebyshev far field + direct near field) plan for one product.
@@ -280,10 +282,10 @@ void launch_fill_random(cudaStream_t st, int rows, int N, double* X, double* d, 
 // arithmetic (see svdup_product.cu)
 size_t rotate_scratch_bytes(int N, int rows);
 // Deflated columns (rotation outputs) go straight to their output column in om.
-void launch_rotate_prepare(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
-                           void* scratch, bool mixed);
-void launch_rotate_apply(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
-                         void* scratch, bool mixed, OutMap om);
+void launch_rotate_prepare(cudaStream_t st, Eig e, const void* X, long long ldx, int rows,
+                           void* scratch, bool mixed, bool xf32);
+void launch_rotate_apply(cudaStream_t st, Eig e, void* X, long long ldx, int rows,
+                         void* scratch, bool mixed, OutMap om, bool xf32);
 void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
                            void* scratch, bool mixed, OutMap om);
 void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
@@ -298,7 +300,7 @@ void launch_product_f64_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, int 
                               const double* Xs, long long ldxs, OutMap om, int dense);
 
 // mixed-precision product (svdup_mixed.cu)
-void launch_mix_gather(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
+void launch_mix_gather(cudaStream_t st, Eig e, const void* X, bool xf32, long long ldx, int rows,
                        MixPlan mp, OutMap om);
 void launch_mix_setup(cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int dense);
 // stage 0 = P2M, 1 = M2L, 2 = L2P + near field (dense: the whole product)

@@ -305,7 +305,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 // X -> split A tiles.  Tile (rt, kt): rows rt*128.., sorted columns t = kt*64 + c
 // (column perm[idx[t]] of X for t < k, zero beyond; zero rows beyond `rows`).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mix_gather(Eig e, const double* __restrict__ X,
+__device__ __forceinline__ float as_f32(double x) { return narrow_rn(x); }
+__device__ __forceinline__ float as_f32(float x) { return x; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mix_gather(Eig e, const T* __restrict__ X,
                                                     long long ldx, int rows, MixPlan mp) {
   __shared__ long long scol[kKB];
   const int rt = blockIdx.x, kt = blockIdx.y;
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(256) k_mix_gather(Eig e, const double* __restr
 #pragma unroll
     for (int c = 0; c < 8; c++) {
       long long col = scol[ch * 8 + c];
-      v[c] = (col >= 0 && row < rows) ? narrow_rn(X[row + col]) : 0.0f;
+      v[c] = (col >= 0 && row < rows) ? as_f32(X[row + col]) : 0.0f;
     }
     store_split8_f(tile, half_plane(kTM), t64_off(r, ch * 8, kTM), v);
   }
@@ -334,7 +338,8 @@ __device__ __forceinline__ long long out_col_m(const OutMap& om, int q) {
 }
 
 // Deflated columns are eigenvectors already: straight to their output column.
-__global__ void k_mix_defl(Eig e, const double* __restrict__ X, long long ldx, int rows,
+template <typename T>
+__global__ void k_mix_defl(Eig e, const T* __restrict__ X, long long ldx, int rows,
                            OutMap om) {
   const int k = e.kp[0];
   const int c = k + blockIdx.x;
@@ -342,9 +347,13 @@ __global__ void k_mix_defl(Eig e, const double* __restrict__ X, long long ldx, i
   int s = e.didx[c - k];
   if (e.defl[s] == 2) return;  // deflated by a rotation: the rotation kernel wrote it
   int q = e.rank_defl[s];
-  const double* src = X + (long long)e.perm[s] * ldx;
-  double* dst = om.Y + out_col_m(om, q) * om.ldy;
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) dst[r] = src[r];
+  const T* src = X + (long long)e.perm[s] * ldx;
+  const long long o = out_col_m(om, q) * om.ldy;
+  if (om.Yf) {
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) om.Yf[o + r] = as_f32(src[r]);
+  } else {
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) om.Y[o + r] = (double)src[r];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -870,7 +879,11 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
 #pragma unroll
         for (int c = 0; c < QW; c++) {
           const int oc = __shfl_sync(0xffffffffu, c < 32 ? cm0 : cm1, c & 31);
-          if (oc >= 0 && row < mp.rows) om.Y[(long long)oc * om.ldy + row] = widen_f32(hi[c] + lo[c]);
+          if (oc >= 0 && row < mp.rows) {
+            const float v = hi[c] + lo[c];
+            if (om.Yf) om.Yf[(long long)oc * om.ldy + row] = v;  // the FP32 intermediate
+            else om.Y[(long long)oc * om.ldy + row] = widen_f32(v);
+          }
         }
       }
     }
@@ -921,12 +934,18 @@ __global__ void k_mix_flops(Eig e, FmmPlan f, MixPlan mp, int dense, double* acc
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_mix_gather(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
+void launch_mix_gather(cudaStream_t st, Eig e, const void* X, bool xf32, long long ldx, int rows,
                        MixPlan mp, OutMap om) {
   dim3 g(mp.rt, mp.kx);
-  k_mix_gather<<<g, 256, 0, st>>>(e, X, ldx, rows, mp);
-  SVDUP_COUNT_LAUNCH();
-  k_mix_defl<<<e.N, 256, 0, st>>>(e, X, ldx, rows, om);
+  if (xf32) {
+    k_mix_gather<float><<<g, 256, 0, st>>>(e, (const float*)X, ldx, rows, mp);
+    SVDUP_COUNT_LAUNCH();
+    k_mix_defl<float><<<e.N, 256, 0, st>>>(e, (const float*)X, ldx, rows, om);
+  } else {
+    k_mix_gather<double><<<g, 256, 0, st>>>(e, (const double*)X, ldx, rows, mp);
+    SVDUP_COUNT_LAUNCH();
+    k_mix_defl<double><<<e.N, 256, 0, st>>>(e, (const double*)X, ldx, rows, om);
+  }
   SVDUP_COUNT_LAUNCH();
 }
 

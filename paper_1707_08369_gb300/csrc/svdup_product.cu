@@ -111,22 +111,29 @@ __device__ __forceinline__ int stage_chunk(Eig e, long long ldx, const float4* r
   return cn;
 }
 
+// Columns of X are FP64, or FP32 for an intermediate of the mixed form (the first
+// product's output, FP32-accurate by construction).
+__device__ __forceinline__ float to_f32(double x) { return narrow_rn(x); }
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ void store_from_f32(double* p, float v) { *p = widen_f32(v); }
+__device__ __forceinline__ void store_from_f32(float* p, float v) { *p = v; }
+
 // A batch of the chunk's original column values (xb for every rotation, xa where a run
 // starts) for row r; i >= cn loads nothing.  xlast replaces the chunk's last b when set.
-__device__ __forceinline__ void rot_load(const double* __restrict__ X, const RotChunkSm& sm,
+template <typename T>
+__device__ __forceinline__ void rot_load(const T* __restrict__ X, const RotChunkSm& sm,
                                          long long r, int i0, int cn, bool use_last,
-                                         double xlast, double (&xb)[kRotBatch],
-                                         double (&xa)[kRotBatch]) {
+                                         double xlast, T (&xb)[kRotBatch], T (&xa)[kRotBatch]) {
 #pragma unroll
   for (int u = 0; u < kRotBatch; u++) {
     const int i = i0 + u;
-    xb[u] = i < cn ? ((use_last && i == cn - 1) ? xlast : X[r + sm.b[i]]) : 0.0;
-    xa[u] = (i < cn && !sm.chained[i]) ? X[r + sm.a[i]] : 0.0;
+    xb[u] = i < cn ? ((use_last && i == cn - 1) ? (T)xlast : X[r + sm.b[i]]) : (T)0;
+    xa[u] = (i < cn && !sm.chained[i]) ? X[r + sm.a[i]] : (T)0;
   }
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __restrict__ X,
+template <bool MIXED, typename T>
+__global__ void __launch_bounds__(128) k_rot_compose(Eig e, const T* __restrict__ X,
                                                      long long ldx, int rows, RotScratch w) {
   __shared__ RotChunkSm sm;
   const int nr = e.nrot[0];
@@ -140,8 +147,8 @@ __global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __rest
   // (no prefetch of the next batch here: this kernel is bound by its arithmetic issue
   // rate, and the extra registers would cost occupancy)
   for (int i0 = 0; i0 < cn; i0 += kRotBatch) {
-    double xb[kRotBatch], xa[kRotBatch];
-    rot_load(X, sm, r, i0, cn, false, 0.0, xb, xa);
+    T xb[kRotBatch], xa[kRotBatch];
+    rot_load<T>(X, sm, r, i0, cn, false, 0.0, xb, xa);
 #pragma unroll
     for (int u = 0; u < kRotBatch; u++) {
       const int i = i0 + u;
@@ -150,10 +157,10 @@ __global__ void __launch_bounds__(128) k_rot_compose(Eig e, const double* __rest
           B = fma(sm.s[i], sm.chained[i] ? B : xa[u], sm.c[i] * xb[u]);
         } else {
           const float4 q = sm.cs[i];
-          const Df uu = sm.chained[i] ? Bf : Df{narrow_rn(xa[u]), 0.f};
-          Bf = df_add(df_mul(Df{q.z, q.w}, uu), df_mul(Df{q.x, q.y}, Df{narrow_rn(xb[u]), 0.f}));
+          const Df uu = sm.chained[i] ? Bf : Df{to_f32(xa[u]), 0.f};
+          Bf = df_add(df_mul(Df{q.z, q.w}, uu), df_mul(Df{q.x, q.y}, Df{to_f32(xb[u]), 0.f}));
         }
-        xlast = xb[u];
+        xlast = (double)xb[u];
       }
     }
   }
@@ -191,8 +198,8 @@ __global__ void k_rot_carry(Eig e, int rows, RotScratch w) {
   }
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(128) k_rot_apply(Eig e, double* X, long long ldx, int rows,
+template <bool MIXED, typename T>
+__global__ void __launch_bounds__(128) k_rot_apply(Eig e, T* X, long long ldx, int rows,
                                                    RotScratch w, OutMap om) {
   __shared__ RotChunkSm sm;
   const int nr = e.nrot[0];
@@ -214,32 +221,34 @@ __global__ void __launch_bounds__(128) k_rot_apply(Eig e, double* X, long long l
   // only at rotation i (a run's end, and no later rotation reads it) and a run-start
   // column a_i is never written (its output goes to Y), so no value loaded early has
   // been written yet; the chunk's last b comes from compose (the next chunk may write it).
-  double xb[kRotBatch], xa[kRotBatch], nb[kRotBatch], na[kRotBatch];
-  rot_load(X, sm, r, 0, cn, true, xlast, xb, xa);
+  T xb[kRotBatch], xa[kRotBatch], nb[kRotBatch], na[kRotBatch];
+  rot_load<T>(X, sm, r, 0, cn, true, xlast, xb, xa);
   for (int i0 = 0; i0 < cn; i0 += kRotBatch) {
-    if (i0 + kRotBatch < cn) rot_load(X, sm, r, i0 + kRotBatch, cn, true, xlast, nb, na);
+    if (i0 + kRotBatch < cn) rot_load<T>(X, sm, r, i0 + kRotBatch, cn, true, xlast, nb, na);
 #pragma unroll
     for (int u = 0; u < kRotBatch; u++) {
       const int i = i0 + u;
       if (i < cn) {
         if (!MIXED) {
-          const double uu = sm.chained[i] ? v : xa[u];
-          om.Y[r + sm.ya[i]] = fma(sm.c[i], uu, -sm.s[i] * xb[u]);
-          v = fma(sm.s[i], uu, sm.c[i] * xb[u]);
-          if (sm.ends[i]) X[r + sm.b[i]] = v;
+          const double uu = sm.chained[i] ? v : (double)xa[u];
+          om.Y[r + sm.ya[i]] = fma(sm.c[i], uu, -sm.s[i] * (double)xb[u]);
+          v = fma(sm.s[i], uu, sm.c[i] * (double)xb[u]);
+          if (sm.ends[i]) X[r + sm.b[i]] = (T)v;
         } else {
           // the carrier stays a pair (runs are long); the deflated output is a rotation
           // of two unit-scale values and needs FP32 accuracy only
           const float4 q = sm.cs[i];
           const Df cc = {q.x, q.y}, ss = {q.z, q.w};
-          const float xx = narrow_rn(xb[u]);
-          const Df uu = sm.chained[i] ? vf : Df{narrow_rn(xa[u]), 0.f};
+          const float xx = to_f32(xb[u]);
+          const Df uu = sm.chained[i] ? vf : Df{to_f32(xa[u]), 0.f};
           float t = fmaf(cc.lo, uu.hi, -ss.lo * xx);
           t = fmaf(cc.hi, uu.lo, t);
           t = fmaf(-ss.hi, xx, t);
-          om.Y[r + sm.ya[i]] = widen_f32(fmaf(cc.hi, uu.hi, t));
+          const float ov = fmaf(cc.hi, uu.hi, t);
+          if (om.Yf) om.Yf[r + sm.ya[i]] = ov;
+          else om.Y[r + sm.ya[i]] = widen_f32(ov);
           vf = df_add(df_mul(ss, uu), df_mul(cc, Df{xx, 0.f}));
-          if (sm.ends[i]) X[r + sm.b[i]] = widen_f32(vf.hi + vf.lo);
+          if (sm.ends[i]) store_from_f32(&X[r + sm.b[i]], vf.hi + vf.lo);
         }
       }
     }
@@ -272,16 +281,18 @@ static RotScratch rot_scratch(Eig e, int rows, void* scratch) {
 }
 
 // The scan's first half (chunk factors, offsets, carries): needs the deflation only.
-void launch_rotate_prepare(cudaStream_t st, Eig e, const double* X, long long ldx, int rows,
-                           void* scratch, bool mixed) {
+// X is FP64, or FP32 when xf32 (mixed only).
+void launch_rotate_prepare(cudaStream_t st, Eig e, const void* X, long long ldx, int rows,
+                           void* scratch, bool mixed, bool xf32) {
   const int nch = (e.N + kRotChunk - 1) / kRotChunk;
   if (rows <= 0 || nch == 0) return;
   const RotScratch w = rot_scratch(e, rows, scratch);
   k_rot_prep<<<1, 1024, 0, st>>>(e, w);
   SVDUP_COUNT_LAUNCH();
   dim3 g((rows + 127) / 128, nch);
-  if (mixed) k_rot_compose<true><<<g, 128, 0, st>>>(e, X, ldx, rows, w);
-  else k_rot_compose<false><<<g, 128, 0, st>>>(e, X, ldx, rows, w);
+  if (mixed && xf32) k_rot_compose<true, float><<<g, 128, 0, st>>>(e, (const float*)X, ldx, rows, w);
+  else if (mixed) k_rot_compose<true, double><<<g, 128, 0, st>>>(e, (const double*)X, ldx, rows, w);
+  else k_rot_compose<false, double><<<g, 128, 0, st>>>(e, (const double*)X, ldx, rows, w);
   SVDUP_COUNT_LAUNCH();
   if (mixed) k_rot_carry<true><<<(rows + 127) / 128, 128, 0, st>>>(e, rows, w);
   else k_rot_carry<false><<<(rows + 127) / 128, 128, 0, st>>>(e, rows, w);
@@ -290,21 +301,22 @@ void launch_rotate_prepare(cudaStream_t st, Eig e, const double* X, long long ld
 
 // The replay: deflated columns go to their output columns, which needs the final order
 // of the eigenvalues (after the roots and their merge with the deflated values).
-void launch_rotate_apply(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
-                         void* scratch, bool mixed, OutMap om) {
+void launch_rotate_apply(cudaStream_t st, Eig e, void* X, long long ldx, int rows,
+                         void* scratch, bool mixed, OutMap om, bool xf32) {
   const int nch = (e.N + kRotChunk - 1) / kRotChunk;
   if (rows <= 0 || nch == 0) return;
   const RotScratch w = rot_scratch(e, rows, scratch);
   dim3 g((rows + 127) / 128, nch);
-  if (mixed) k_rot_apply<true><<<g, 128, 0, st>>>(e, X, ldx, rows, w, om);
-  else k_rot_apply<false><<<g, 128, 0, st>>>(e, X, ldx, rows, w, om);
+  if (mixed && xf32) k_rot_apply<true, float><<<g, 128, 0, st>>>(e, (float*)X, ldx, rows, w, om);
+  else if (mixed) k_rot_apply<true, double><<<g, 128, 0, st>>>(e, (double*)X, ldx, rows, w, om);
+  else k_rot_apply<false, double><<<g, 128, 0, st>>>(e, (double*)X, ldx, rows, w, om);
   SVDUP_COUNT_LAUNCH();
 }
 
 void launch_rotate_columns(cudaStream_t st, Eig e, double* X, long long ldx, int rows,
                            void* scratch, bool mixed, OutMap om) {
-  launch_rotate_prepare(st, e, X, ldx, rows, scratch, mixed);
-  launch_rotate_apply(st, e, X, ldx, rows, scratch, mixed, om);
+  launch_rotate_prepare(st, e, X, ldx, rows, scratch, mixed, false);
+  launch_rotate_apply(st, e, X, ldx, rows, scratch, mixed, om, false);
 }
 
 __device__ __forceinline__ long long out_col(const OutMap& om, int q) {
