@@ -307,6 +307,8 @@ int set_device(svdup_ctx* h) {
 // Update workspace.  The left-hand (U) and right-hand (V) problems own their scratch
 // (ysort, the product's plan, W and Xs) so that they can run side by side.
 struct UpdateWs {
+  float2* abf;  // a, b as scaled FP32 pairs (STEP 1)
+  int* abe;     // their scales
   double *p, *q, *ab, *z2p, *z4p, *ysortL, *ysortR, *zsec2, *zsec4, *ones, *g1, *g, *yv, *h1,
       *h, *sign, *work;
   Eig E1, E2, E3, E4;
@@ -321,6 +323,8 @@ UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed
   u.p = ar.take<double>(m);
   u.q = ar.take<double>(n);
   u.ab = ar.take<double>(2);
+  u.abf = ar.take<float2>((size_t)m + n);
+  u.abe = ar.take<int>(2);
   u.z2p = ar.take<double>(m);
   u.z4p = ar.take<double>(n);
   u.ysortL = ar.take<double>(m);
@@ -917,7 +921,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
 
   // STEP 1 (rewritten): p = U^T a, q = V^T b, alpha, beta
   stage_begin(h, SVDUP_STAGE_GEMV);
-  launch_gemv_pq(st, m, n, U, ldu, V, ldv, a, b, u.p, u.q, u.ab);
+  launch_gemv_pq(st, m, n, U, ldu, V, ldv, a, b, u.p, u.q, u.ab, u.abf, u.abe);
   stage_end(h);
   // Streams: the left-hand solves (E1, E2) on `left`, the right-hand ones (E3, E4) on
   // `side`, the products with U on prod[0] and with V on prod[1]; the handle's stream

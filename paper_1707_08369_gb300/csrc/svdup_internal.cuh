@@ -239,7 +239,7 @@ int device_sm_count();
 // its kernels on `st` and adds to the launch counter.
 void launch_gemv_pq(cudaStream_t st, int m, int n, const double* U, long long ldu, const double* V,
                     long long ldv, const double* a, const double* b, double* p, double* q,
-                    double* ab);
+                    double* ab, float2* abf, int* abe);
 void launch_fill_left(cudaStream_t st, Eig e, int m, const double* S, const double* p,
                       const double* q, const double* ab, double* z2p, double* rho2, int* status);
 void launch_fill_right(cudaStream_t st, Eig e, int m, int n, const double* S, const double* p,

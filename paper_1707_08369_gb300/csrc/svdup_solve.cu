@@ -23,48 +23,125 @@ extern long long g_launch_count;
 // then, inside RankOneUpdate STEP 1, abar = U^T a1.  With U, V orthogonal (App. A)
 // U^T btilde = S (V^T b) and V^T atilde = S^T (U^T a), so every z vector follows from
 // p = U^T a and q = V^T b: one pass over U and one over V.
-// One block per column: blocks [0, m) do columns of U, [m, m+n) columns of V, the
-// last block computes alpha = a^T a and beta = b^T b.
+// The pass is bound by reading U and V (8 (m^2 + n^2) bytes), so the dot products run
+// on FP32 pairs (svdup_df.cuh) rather than on the FP64 pipe, which would take twice the
+// time of the reads: every entry of U (|u| <= 1) and of a 2^-Ea is truncated to a pair
+// (47 bits), their product formed exactly but for the lo.lo term, and the sum kept as a
+// pair.  Each term carries about 2^-46 relative error, so the result's error is about
+// 2^-46 sum |u_r a_r|, the size of an FP64 dot product's typical rounding (sqrt(m) u).
+// k_gemv_prep (one block): Ea, Eb (exponents of max|a|, max|b|), the pairs of
+// a 2^-Ea and b 2^-Eb, and alpha = a^T a, beta = b^T b in FP64.
+// k_gemv_pq: one block per column, [0, m) of U and [m, m + n) of V.
 // ---------------------------------------------------------------------------
-__global__ void k_gemv_pq(int m, int n, const double* __restrict__ U, long long ldu,
-                          const double* __restrict__ V, long long ldv, const double* __restrict__ a,
-                          const double* __restrict__ b, double* p, double* q, double* ab) {
+__global__ void __launch_bounds__(1024) k_gemv_prep(int m, int n, const double* __restrict__ a,
+                                                    const double* __restrict__ b, float2* abf,
+                                                    int* abe, double* ab) {
   __shared__ double red[2][32];
-  int c = blockIdx.x;
+  __shared__ int sx[2];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nt = blockDim.x;
+  if (tid < 2) sx[tid] = -1100;
+  __syncthreads();
   double s0 = 0.0, s1 = 0.0;
-  if (c < m) {
-    const double* col = U + (long long)c * ldu;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) s0 = fma(col[r], a[r], s0);
-  } else if (c < m + n) {
-    const double* col = V + (long long)(c - m) * ldv;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) s0 = fma(col[r], b[r], s0);
-  } else {
-    for (int r = threadIdx.x; r < m; r += blockDim.x) s0 = fma(a[r], a[r], s0);
-    for (int r = threadIdx.x; r < n; r += blockDim.x) s1 = fma(b[r], b[r], s1);
+  int ea = -1100, eb = -1100;
+  for (int r = tid; r < m; r += nt) {
+    const double x = a[r];
+    s0 = fma(x, x, s0);
+    ea = max(ea, exp2_of(x));
+  }
+  for (int r = tid; r < n; r += nt) {
+    const double x = b[r];
+    s1 = fma(x, x, s1);
+    eb = max(eb, exp2_of(x));
   }
   s0 = warp_sum(s0);
   s1 = warp_sum(s1);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { red[0][w] = s0; red[1][w] = s1; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
+    eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+  }
+  if (lane == 0) {
+    red[0][w] = s0;
+    red[1][w] = s1;
+    atomicMax(&sx[0], ea);
+    atomicMax(&sx[1], eb);
+  }
   __syncthreads();
   if (w == 0) {
-    int nw = blockDim.x >> 5;
-    s0 = l < nw ? red[0][l] : 0.0;
-    s1 = l < nw ? red[1][l] : 0.0;
+    const int nw = nt >> 5;
+    s0 = lane < nw ? red[0][lane] : 0.0;
+    s1 = lane < nw ? red[1][lane] : 0.0;
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
+    if (lane == 0) {
+      ab[0] = s0;
+      ab[1] = s1;
+    }
+  }
+  const int Ea = sx[0] < -1000 ? 0 : sx[0], Eb = sx[1] < -1000 ? 0 : sx[1];
+  if (tid == 0) {
+    abe[0] = Ea;
+    abe[1] = Eb;
+  }
+  for (int r = tid; r < m; r += nt) {
+    const Df v = df_from_f64(a[r], Ea);
+    abf[r] = make_float2(v.hi, v.lo);
+  }
+  for (int r = tid; r < n; r += nt) {
+    const Df v = df_from_f64(b[r], Eb);
+    abf[m + r] = make_float2(v.hi, v.lo);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gemv_pq(int m, int n, const double* __restrict__ U,
+                                                 long long ldu, const double* __restrict__ V,
+                                                 long long ldv, const float2* __restrict__ abf,
+                                                 const int* __restrict__ abe, double* p, double* q) {
+  __shared__ float2 red[8];
+  const int c = blockIdx.x;
+  const bool left = c < m;
+  const double* col = left ? U + (long long)c * ldu : V + (long long)(c - m) * ldv;
+  const float2* vec = left ? abf : abf + m;
+  const int len = left ? m : n;
+  // four rows per thread and step, their loads issued together (the pass is bound by
+  // the loads in flight), summed into two chains
+  Df acc = {0.0f, 0.0f}, acc2 = {0.0f, 0.0f};
+  const int bd = blockDim.x;
+  int r = threadIdx.x;
+  for (; r + 3 * bd < len; r += 4 * bd) {
+    const double u0 = col[r], u1 = col[r + bd], u2 = col[r + 2 * bd], u3 = col[r + 3 * bd];
+    const float2 v0 = vec[r], v1 = vec[r + bd], v2 = vec[r + 2 * bd], v3 = vec[r + 3 * bd];
+    acc = df_add(acc, df_mul(df_from_f64(u0, 0), Df{v0.x, v0.y}));
+    acc2 = df_add(acc2, df_mul(df_from_f64(u1, 0), Df{v1.x, v1.y}));
+    acc = df_add(acc, df_mul(df_from_f64(u2, 0), Df{v2.x, v2.y}));
+    acc2 = df_add(acc2, df_mul(df_from_f64(u3, 0), Df{v3.x, v3.y}));
+  }
+  for (; r < len; r += bd) {
+    const float2 v = vec[r];
+    acc = df_add(acc, df_mul(df_from_f64(col[r], 0), Df{v.x, v.y}));
+  }
+  acc = df_warp_sum(df_add(acc, acc2));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = make_float2(acc.hi, acc.lo);
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    const float2 t = l < nw ? red[l] : make_float2(0.0f, 0.0f);
+    acc = df_warp_sum(Df{t.x, t.y});
     if (l == 0) {
-      if (c < m) p[c] = s0;
-      else if (c < m + n) q[c - m] = s0;
-      else { ab[0] = s0; ab[1] = s1; }
+      const double r = df_to_f64(acc, left ? abe[0] : abe[1]);
+      if (left) p[c] = r;
+      else q[c - m] = r;
     }
   }
 }
 
 void launch_gemv_pq(cudaStream_t st, int m, int n, const double* U, long long ldu, const double* V,
                     long long ldv, const double* a, const double* b, double* p, double* q,
-                    double* ab) {
-  k_gemv_pq<<<m + n + 1, 256, 0, st>>>(m, n, U, ldu, V, ldv, a, b, p, q, ab);
+                    double* ab, float2* abf, int* abe) {
+  k_gemv_prep<<<1, 1024, 0, st>>>(m, n, a, b, abf, abe, ab);
+  SVDUP_COUNT_LAUNCH();
+  k_gemv_pq<<<m + n, 256, 0, st>>>(m, n, U, ldu, V, ldv, abf, abe, p, q);
   SVDUP_COUNT_LAUNCH();
 }
 
@@ -1965,16 +2042,28 @@ void launch_sign_finish(cudaStream_t st, int m, int n, const double* h, double* 
 
 // The signs applied to V after its second product (written unsigned, so that the
 // product need not wait for the sign pairing): physical column c holds final index
-// n - 1 - c; a block per column of the paired part, the unflipped ones exit at once.
+// n - 1 - c.  Blocks of 1024 rows of one column of the paired part, four rows per thread
+// with their loads issued together; blocks of unflipped columns exit at once.
 __global__ void k_sign_apply(int m, int n, double* V, long long ldv, const double* __restrict__ sign) {
   const int c = blockIdx.x;
   if (c >= m || !(sign[n - 1 - c] < 0.0)) return;
   double* col = V + (long long)c * ldv;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) col[r] = -col[r];
+  const int r0 = blockIdx.y * 1024 + threadIdx.x;
+  double v[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int r = r0 + q * 256;
+    v[q] = r < n ? col[r] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int r = r0 + q * 256;
+    if (r < n) col[r] = -v[q];
+  }
 }
 
 void launch_sign_apply(cudaStream_t st, int m, int n, double* V, long long ldv, const double* sign) {
-  k_sign_apply<<<m, 256, 0, st>>>(m, n, V, ldv, sign);
+  k_sign_apply<<<dim3(m, (n + 1023) / 1024), 256, 0, st>>>(m, n, V, ldv, sign);
   SVDUP_COUNT_LAUNCH();
 }
 
