@@ -26,7 +26,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "svdup_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# A prebuilt variant of the library may be named in SVDUP_ORACLE_LIB: the
+# planted-mistake tests compile altered copies of svdup_oracle.c and run the pins
+# against each of them in a child process.
+_VARIANT = os.environ.get("SVDUP_ORACLE_LIB")
+_LIB_PATH = _VARIANT or os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 OK, EINVAL, ENOMEM, ENOCONV = 0, 1, 2, 3
@@ -34,6 +38,8 @@ OK, EINVAL, ENOMEM, ENOCONV = 0, 1, 2, 3
 
 def build(force: bool = False) -> str:
     """Compile svdup_oracle.c into oracle/liboracle.so with gcc (-fopenmp)."""
+    if _VARIANT:
+        return _LIB_PATH
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",

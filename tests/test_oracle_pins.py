@@ -199,6 +199,71 @@ def test_deflation_near_equal_poles(orc):
     assert np.abs(lam - np.linalg.eigvalsh(M)).max() <= 1e-13
 
 
+def test_deflation_unequal_weights(orc):
+    """Sec. 3.1 case (3) with unequal weights: when z_i << z_j the rotation
+    angle is small, so poles 1e-10 apart still deflate (|gap c s| <= tol).  The
+    rotated poles then differ visibly from the originals, and a mix-up of the two
+    rotated values moves an eigenvalue by about the gap."""
+    g = np.random.default_rng(8)
+    d = np.sort(g.uniform(0, 1, 30))
+    d[11] = d[10] + 1e-10
+    z = g.standard_normal(30)
+    z[10] = 1e-7
+    for rho in (0.8, -0.6):
+        c = orc.rank_one_compact(d, z, rho)
+        assert c["k"] == 29                      # the pair deflated to one pole
+        lam, Q = orc.rank_one_eig(d, z, rho)
+        M = np.diag(d) + rho * np.outer(z, z)
+        w = np.linalg.eigvalsh(M)
+        assert np.abs(lam - w).max() <= 1e-13
+        assert np.abs(M @ Q - Q * lam).max() <= 1e-13
+        assert np.abs(Q.T @ Q - np.eye(30)).max() <= 1e-13
+
+
+@pytest.mark.parametrize("seed,k,sgn,spread", [(30, 50, 1, "uniform"), (31, 64, -1, "uniform"),
+                                               (32, 40, 1, "graded")])
+def test_rank_one_compact_fields(orc, seed, k, sgn, spread):
+    """The compact eigen-system that the element-wise GPU comparisons use:
+    (i) no deflation for generic data, idx the identity and dk the sorted poles;
+    (ii) mu_j = dk[org_j] + tau_j are the eigenvalues (LAPACK), the origin is
+    the nearer end of root j's interlacing bracket (Sec. 3.1) and tau points into it;
+    (iii) the Loewner vector equals z to rounding, since the roots are exact to
+    rounding (Sec. 3.2: rho zhat_i^2 prod_{j!=i}(d_j - d_i) = prod_j (mu_j - d_i));
+    (iv) zhat_i/(d_i - mu_j) * inv_norm_j are unit columns and LAPACK's vectors."""
+    g = np.random.default_rng(seed)
+    d = np.sort(g.uniform(0, 1, k)) if spread == "uniform" else np.sort(10.0 ** (-4 * g.uniform(0, 1, k)))
+    z = g.standard_normal(k)
+    rho = sgn * g.uniform(0.5, 2.0)
+    perm = g.permutation(k)
+    c = orc.rank_one_compact(d[perm], z[perm], rho)
+    assert c["k"] == k
+    assert np.array_equal(c["idx"], np.arange(k)) and np.array_equal(c["dk"], d)
+    zs = z                                          # z in sorted order
+    mu = c["dk"][c["org"]] + c["tau"]
+    M = np.diag(d) + rho * np.outer(zs, zs)
+    w, E = np.linalg.eigh(M)
+    assert np.abs(mu - w).max() <= 32 * k * U53 * np.abs(w).max()
+    assert np.array_equal(c["lam"], np.sort(mu))
+    j = np.arange(k)
+    if sgn > 0:
+        lo_pole, hi_pole = j, j + 1                 # root j in (d_j, d_{j+1})
+    else:
+        lo_pole, hi_pole = j - 1, j                 # root j in (d_{j-1}, d_j)
+    org = c["org"]
+    assert np.all((org == lo_pole) | (org == hi_pole))
+    assert np.all(c["tau"][org == lo_pole] > 0) and np.all(c["tau"][org == hi_pole] < 0)
+    inner = (lo_pole >= 0) & (hi_pole < k)
+    gap = d[np.minimum(hi_pole, k - 1)] - d[np.maximum(lo_pole, 0)]
+    assert np.all(np.abs(c["tau"][inner]) <= 0.5 * gap[inner] * (1 + 4 * U53))
+    assert np.all(np.abs(c["zhat"] - zs) <= 4 * k * U53 * np.abs(zs))
+    C = c["zhat"][:, None] / ((d[:, None] - d[org][None, :]) - c["tau"][None, :]) * c["inv_norm"][None, :]
+    assert np.abs((C * C).sum(axis=0) - 1.0).max() <= 4 * k * U53
+    if spread == "uniform":                         # separated roots: unique up to sign
+        s = np.sign(np.sum(E * C, axis=0))
+        assert np.abs(E * s - C).max() <= 1e-9
+    assert np.abs(M @ C - C * mu).max() <= 64 * U53 * np.abs(M).max() * k
+
+
 # ---------------------------------------------------------------- the full update (Alg. 6.1)
 def _check_svd(orc, U, S, V, a, b, rtol=1e-12, graded=False):
     """Alg. 6.1 works with Ahat Ahat^T and Ahat^T Ahat (App. A), so the computed
