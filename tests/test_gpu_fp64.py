@@ -255,6 +255,86 @@ def test_chained_updates(sv, hnd, orc):
     assert np.abs(tS.cpu().numpy() - So).max() <= 1e-11 * So[0]
 
 
+# ------------------------------------------------------------------ degenerate updates
+def _mode_bar(sv, mode_name):
+    """(mode, reconstruction slack over the oracle's, orthogonality bound, vector bound)"""
+    if mode_name == "FP64":
+        return sv.FP64, 1e-10, 1e-10, 1e-10
+    return sv.MIXED_BF16X3, 1e-6, 1e-5, 1e-5
+
+
+@pytest.mark.parametrize("mode_name", ["FP64", "MIXED_BF16X3"])
+@pytest.mark.parametrize("zero", ["a", "b"])
+def test_update_zero_direction(sv, hnd, orc, mode_name, zero):
+    """a = 0 or b = 0 leaves A unchanged.  Alg. 6.1 still applies both of its rank-one
+    eigen-updates: the positive one (rho_1) and the negative one (rho_2 = -1/rho_1)
+    cancel exactly, since rho_1 Q_21^2 + rho_2 Q_22^2 = 0 (STEPs 2-5).  The values come
+    back to sigma within the FP64 bar, and the vectors still give a valid SVD."""
+    mode, slack, orth_bar, _ = _mode_bar(sv, mode_name)
+    A, a, b = wl.small_gaussian(40, 56, seed=21)
+    U, S, Vh = np.linalg.svd(A)
+    V = Vh.T
+    if zero == "a":
+        a = np.zeros_like(a)
+    else:
+        b = np.zeros_like(b)
+    Uo, So, Vo = orc.svd_update(U, S, V, a, b)
+    Un, Sn, Vn = _run_update(sv, hnd, U, S, V, a, b, mode=mode)
+    assert np.abs(Sn - So).max() <= 1e-12 * So[0]
+    assert np.abs(Sn - S).max() <= 1e-12 * S[0]
+    Ah, nrm, recon, orthU, orthV = _invariants(U, S, V, a, b, Un, Sn, Vn)
+    recon_o = _invariants(U, S, V, a, b, Uo, So, Vo)[2]
+    assert recon <= recon_o + slack and orthU <= orth_bar and orthV <= orth_bar
+
+
+@pytest.mark.parametrize("mode_name", ["FP64", "MIXED_BF16X3"])
+def test_update_rank_deficient(sv, hnd, orc, mode_name):
+    """A of rank 4 with a repeated value (sigma = 5, 3, 3, 1, 0, 0; 6 x 9): exactly equal
+    poles on the left and a null block of 5 zero poles on the right deflate (Sec. 3.1
+    cases (1) and (3)); A + a b^T has rank 5, so its last singular value is 0."""
+    mode, slack, orth_bar, _ = _mode_bar(sv, mode_name)
+    g = wl.rng(31)
+    m, n = 6, 9
+    U = wl.haar(m, g)
+    V = wl.haar(n, g)
+    S = np.array([5.0, 3.0, 3.0, 1.0, 0.0, 0.0])
+    a = g.standard_normal(m)
+    b = g.standard_normal(n)
+    Uo, So, Vo = orc.svd_update(U, S, V, a, b)
+    Un, Sn, Vn = _run_update(sv, hnd, U, S, V, a, b, mode=mode)
+    assert np.abs(Sn - So).max() <= 1e-12 * So[0]
+    Ah, nrm, recon, orthU, orthV = _invariants(U, S, V, a, b, Un, Sn, Vn)
+    assert np.abs(Sn - np.linalg.svd(Ah, compute_uv=False)).max() <= 1e-12 * So[0]
+    recon_o = _invariants(U, S, V, a, b, Uo, So, Vo)[2]
+    assert recon <= recon_o + slack and orthU <= orth_bar and orthV <= orth_bar
+    assert np.linalg.norm(Ah @ Vn[:, m:]) <= max(1e-10, slack) * nrm  # null space
+
+
+@pytest.mark.parametrize("mode_name", ["FP64", "MIXED_BF16X3"])
+def test_update_along_singular_pair(sv, hnd, orc, mode_name):
+    """a = c u_j, b = v_j: A + a b^T = U (Sigma + c e_j e_j^T) V^T.  z is a coordinate
+    vector (the paper's case (2) of Sec. 3.1, a special case of (1)), every other
+    component deflates, and the result is sigma_j -> sigma_j + c with U and V kept
+    (c is a third of the gap above sigma_j, so the order does not change)."""
+    mode, slack, orth_bar, vec_bar = _mode_bar(sv, mode_name)
+    U, S, V, _, _ = wl.loguniform_sq(64, seed=wl.BASE_SEED + 41)
+    j = 5
+    c = 0.3 * (S[j - 1] - S[j])
+    a = c * U[:, j]
+    b = V[:, j].copy()
+    expect = S.copy()
+    expect[j] += c
+    Uo, So, Vo = orc.svd_update(U, S, V, a, b)
+    Un, Sn, Vn = _run_update(sv, hnd, U, S, V, a, b, mode=mode)
+    assert np.abs(Sn - So).max() <= 1e-12 * So[0]
+    assert np.abs(Sn - expect).max() <= 1e-12 * S[0]
+    assert np.abs(np.abs(Un) - np.abs(U)).max() <= vec_bar
+    assert np.abs(np.abs(Vn) - np.abs(V)).max() <= vec_bar
+    Ah, nrm, recon, orthU, orthV = _invariants(U, S, V, a, b, Un, Sn, Vn)
+    recon_o = _invariants(U, S, V, a, b, Uo, So, Vo)[2]
+    assert recon <= recon_o + slack and orthU <= orth_bar and orthV <= orth_bar
+
+
 # ------------------------------------------------------------------ errors, no fault
 def test_invalid_arguments(sv, hnd):
     U = devF(np.eye(4)); S = dev(np.ones(4)); V = devF(np.eye(4)); a = dev(np.ones(4))
