@@ -45,10 +45,11 @@ extern "C" {
 /* ---- update modes (svdup_update's mode argument) -------------------------- */
 #define SVDUP_FP64 0          /* every step in FP64 */
 #define SVDUP_MIXED_BF16X3 1  /* products in 3-term BF16 split, FP32 accumulation */
-#define SVDUP_MIXED_FP16X2 2  /* products in 2-term scaled FP16 split, FP32 accumulation */
+#define SVDUP_MIXED_FP16X2 2  /* reserved: 2-term scaled FP16 split; not built, SVDUP_EINVAL */
 #define SVDUP_MODE_MASK 0xff
 #define SVDUP_DENSE 0x100     /* flag: force the dense Cauchy product (no far field) */
-#define SVDUP_REFINE 0x200    /* flag (mixed modes): one orthogonalising refinement step */
+#define SVDUP_REFINE 0x200    /* reserved flag: an orthogonalising refinement step of the
+                                 mixed modes; not built, any mode with it: SVDUP_EINVAL */
 
 typedef struct svdup_ctx* svdup_t;
 
@@ -107,7 +108,8 @@ int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, do
  *   a  m, b n           the rank-one term a b^T (read only).
  *   eps                 accuracy of the Cauchy products, 0 < eps < 1; the
  *                       expansion order is p = ceil(log5(1/eps)) (App. D STEP 1).
- *   mode                SVDUP_FP64 / SVDUP_MIXED_* plus optional flags.
+ *   mode                SVDUP_FP64 or SVDUP_MIXED_BF16X3, optionally | SVDUP_DENSE;
+ *                       any other value returns SVDUP_EINVAL.
  * The signs of Vhat's columns are chosen so that u_j^T Ahat v_j >= 0.
  * Requires 1 <= m <= n.  U, V are assumed orthogonal (as the paper does, App. A).
  */

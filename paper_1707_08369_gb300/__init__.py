@@ -18,8 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsvdup.so")
 
 OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE, ECUDA, EORDER, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6, 7
-FP64, MIXED_BF16X3, MIXED_FP16X2 = 0, 1, 2
-DENSE, REFINE = 0x100, 0x200
+FP64, MIXED_BF16X3, MIXED_FP16X2 = 0, 1, 2  # MIXED_FP16X2: reserved, rejected (EINVAL)
+DENSE, REFINE = 0x100, 0x200                 # REFINE: reserved, rejected (EINVAL)
 
 _lib = None
 
