@@ -68,8 +68,9 @@ int svdup_sync(svdup_t h);
 /* Text of a return code (static storage). */
 const char* svdup_error_string(int code);
 
-/* Number of distinct kernels this library launched on the handle's stream since
- * create (a launch counter, for accounting). */
+/* Number of kernels this library has launched in this process, over all handles,
+ * servers and threads (a launch counter, for accounting; take differences).  A batch
+ * graph's kernels count once per svdup_batch_launch.  h is not used. */
 long long svdup_launch_count(svdup_t h);
 
 /* ---- stage timers ------------------------------------------------------ */

@@ -6,32 +6,39 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "svdup_internal.cuh"
 
 namespace svdup {
 
-long long g_launch_count = 0;
+// Kernels launched by this process (all handles and threads; the serving engine's
+// scheduler thread launches beside the caller's).  Launches made while this thread
+// records a batch graph are counted when the graph is launched, not here.
+std::atomic<long long> g_launch_count{0};
+static thread_local bool t_recording = false;
 
 static int debug_mode() {
-  static int v = -1;
-  if (v < 0) {
+  static const int v = [] {
     const char* e = getenv("SVDUP_DEBUG");
-    v = (e && e[0] && e[0] != '0') ? 1 : 0;
-  }
+    return (e && e[0] && e[0] != '0') ? 1 : 0;
+  }();
   return v;
 }
 
-static cudaError_t g_debug_err = cudaSuccess;  // first failure seen in debug mode
+static std::atomic<int> g_debug_err{cudaSuccess};  // first failure seen in debug mode
 
 void note_launch(const char* file, int line) {
-  ++g_launch_count;
+  if (t_recording) return;  // a captured launch: no device synchronisation either
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
   if (!debug_mode()) return;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     fprintf(stderr, "svdup: kernel launched at %s:%d failed: %s\n", file, line,
             cudaGetErrorString(e));
-    if (g_debug_err == cudaSuccess) g_debug_err = e;
+    int none = cudaSuccess;
+    g_debug_err.compare_exchange_strong(none, (int)e);
   }
 }
 
@@ -292,9 +299,9 @@ int ensure_ws(svdup_ctx* h, size_t bytes) {
 
 int check_launch() {
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && g_debug_err != cudaSuccess) {  // consumed by note_launch
-    e = g_debug_err;
-    g_debug_err = cudaSuccess;
+  if (e == cudaSuccess) {  // a failure that note_launch consumed in debug mode
+    const int d = g_debug_err.exchange(cudaSuccess);
+    if (d != cudaSuccess) e = (cudaError_t)d;
   }
   return e == cudaSuccess ? SVDUP_OK : SVDUP_ECUDA;
 }
@@ -899,7 +906,7 @@ const char* svdup_error_string(int code) {
 
 long long svdup_launch_count(svdup_t h) {
   (void)h;
-  return g_launch_count;
+  return g_launch_count.load(std::memory_order_relaxed);
 }
 
 int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double* V, int ldv,
@@ -1224,19 +1231,19 @@ int svdup_batch_create(svdup_t h, int count, const svdup_problem* probs, double 
   if (rc) return rc;
   // Record the batch into a graph: capture on the batch's own origin stream (the
   // handle's stream may be the legacy default stream, which cannot be captured).
-  const long long k0 = g_launch_count;
   if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
     cudaGetLastError();
     batch_free(b);
     return SVDUP_ECUDA;
   }
+  t_recording = true;  // recorded, not launched: counted per graph launch
   rc = batch_queue(b);
+  t_recording = false;
   cudaGraph_t g = nullptr;
   cudaError_t ce = cudaStreamEndCapture(b->origin, &g);
   b->graph = g;
   if (rc == SVDUP_OK && ce != cudaSuccess) rc = SVDUP_ECUDA;
   if (rc == SVDUP_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = SVDUP_ECUDA;
-  g_launch_count = k0;  // recorded, not launched
   b->kernels = 0;
   if (rc == SVDUP_OK) {
     size_t nn = 0;
@@ -1267,7 +1274,7 @@ int svdup_batch_launch(svdup_batch_t b) {
     cudaGetLastError();
     return SVDUP_ECUDA;
   }
-  g_launch_count += b->kernels;
+  g_launch_count.fetch_add(b->kernels, std::memory_order_relaxed);
   return SVDUP_OK;
 }
 

@@ -16,8 +16,10 @@ __device__ __forceinline__ void latch(int* status, int code) {
 }
 
 // Launch accounting: every kernel launch calls note_launch (via SVDUP_COUNT_LAUNCH),
-// which counts it and, when the environment sets SVDUP_DEBUG, waits for the device and
-// reports the launch site of the first failing kernel on stderr.
+// which counts it (one atomic counter for the process) and, when the environment sets
+// SVDUP_DEBUG, waits for the device and reports the launch site of the first failing
+// kernel on stderr.  Launches recorded into a batch graph are counted when the graph
+// is launched.
 void note_launch(const char* file, int line);
 #define SVDUP_COUNT_LAUNCH() ::svdup::note_launch(__FILE__, __LINE__)
 

@@ -42,7 +42,6 @@
 
 namespace svdup {
 
-extern long long g_launch_count;
 
 namespace {
 

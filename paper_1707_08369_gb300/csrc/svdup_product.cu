@@ -26,7 +26,6 @@
 
 namespace svdup {
 
-extern long long g_launch_count;
 
 // ---------------------------------------------------------------------------
 // Deflation rotations applied to the columns of X (in place): X <- X G_1^T ... G_r^T,

@@ -16,7 +16,6 @@
 
 namespace svdup {
 
-extern long long g_launch_count;
 
 // ---------------------------------------------------------------------------
 // Alg. 6.1 STEP 1.  The paper forms btilde = U S V^T b and atilde = V S^T U^T a and

@@ -20,7 +20,6 @@
 #include "svdup_internal.cuh"
 
 namespace svdup {
-extern long long g_launch_count;
 }  // namespace svdup
 
 using namespace svdup;
