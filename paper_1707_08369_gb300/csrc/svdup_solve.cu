@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "svdup_df.cuh"
 #include "svdup_internal.cuh"
@@ -1557,18 +1558,21 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
   }
 }
 
-// Streaming multiprocessors of the current device (queried once per device).
+// Streaming multiprocessors of the current device (queried once per device; threads
+// that race on the first query store the same value).
 int device_sm_count() {
-  static int cached[64] = {0};
+  static std::atomic<int> cached[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return 152;
-  if (cached[dev] == 0) {
+  int c = cached[dev].load(std::memory_order_relaxed);
+  if (c == 0) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    cached[dev] = n > 0 ? n : 152;
+    c = n > 0 ? n : 152;
+    cached[dev].store(c, std::memory_order_relaxed);
   }
-  return cached[dev];
+  return c;
 }
 
 static int secular_blocks(int N) {
