@@ -42,7 +42,6 @@
 
 namespace svdup {
 
-
 namespace {
 
 // ---------------------------------------------------------------------------
