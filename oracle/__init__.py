@@ -13,7 +13,10 @@ Functions and the passages they follow:
   rank_one_eig      RankOneUpdate STEPs 2-5 (Sec. 6.2) with deflation (Sec. 3.1)
   rank_one_compact  the same, returned as (k, idx, poles, org, tau, zhat, 1/||c_j||)
   rank_one_update   RankOneUpdate STEPs 1-7 with a dense product (Sec. 6.2)
+  rank_one_apply    Q X for a thin X (the products of Alg. 6.1 STEPs 5 and 7 on a few vectors)
   svd_update        Alg. 6.1 STEPs 1-8, descending order, paired signs
+  svd_update_sampled  Alg. 6.1 with every singular value but only sampled columns of the
+                    vectors, for sizes whose dense products are out of reach
   jacobi_svd        independent one-sided Jacobi SVD (Hestenes)
 """
 from __future__ import annotations
@@ -63,6 +66,7 @@ def _load():
         lib.oracle_rank_one_compact.argtypes = [I, P, P, D, P, P, P, P, P, P, P, P]
         lib.oracle_rank_one_update_z.argtypes = [I, I, P, I, P, P, D, P, P, I, I, P]
         lib.oracle_rank_one_update.argtypes = [I, I, P, I, P, P, D, P, P, I]
+        lib.oracle_rank_one_apply.argtypes = [I, P, P, D, I, P, P, P]
         lib.oracle_svd_update.argtypes = [I, I, P, I, P, P, I, P, P, P, P, P]
         lib.oracle_jacobi_svd.argtypes = [I, I, P, I, P, P, P]
         lib.oracle_num_threads.restype = I
@@ -178,6 +182,21 @@ def rank_one_update(X, d, a1, rho):
     return lam, Y
 
 
+def rank_one_apply(d, z, rho, X):
+    """Q X for the eigenvectors Q of diag(d) + rho z z^T (column c: the c-th smallest
+    eigenvalue) and a thin X (N x s).  Returns (lam ascending, Y = Q X)."""
+    d = _vec(d); z = _vec(z)
+    N = d.size
+    X = _mat(np.asarray(X, dtype=np.float64).reshape(N, -1))
+    s = X.shape[1]
+    lam = np.zeros(N)
+    Y = np.zeros((N, s), order="F")
+    st = _load().oracle_rank_one_apply(N, _p(d), _p(z), float(rho), s, _p(X), _p(Y), _p(lam))
+    if st not in (OK, ENOCONV):
+        raise RuntimeError("oracle_rank_one_apply failed: %d" % st)
+    return lam, Y
+
+
 def svd_update(U, S, V, a, b):
     """Alg. 6.1: SVD of U diag(S) V^T + a b^T.  Returns (Un, Sn, Vn), Sn descending."""
     U = _mat(U); V = _mat(V)
@@ -188,6 +207,59 @@ def svd_update(U, S, V, a, b):
     if st not in (OK, ENOCONV):
         raise RuntimeError("oracle_svd_update failed: %d" % st)
     return Un, Sn, Vn
+
+
+def svd_update_sampled(U, S, V, a, b, cols):
+    """Alg. 6.1 at sizes whose dense products are out of reach: every singular value
+    of Ahat = U diag(S) V^T + a b^T (descending), and only the columns `cols` (indices
+    into the descending order, each < m) of Uhat and Vhat.  Returns (Sn, Un_cols, Vn_cols).
+
+    The arithmetic is that of svd_update with STEP 1 read through the input SVD (the
+    Sec. 6.2 direction U^T a1 expressed by p = U^T a and q = V^T b, since U^T btilde =
+    S q[:m] and V^T atilde = [S p; 0]); the second solve of each side takes z = Q^T z'
+    from the first.  Column j of Uhat is U Q1 Q2 e_(m-1-j) and of Vhat V Q3 Q4 e_(n-1-j)
+    (the solves are ascending), and v_j is negated where u_j^T Ahat v_j < 0, as in
+    svd_update."""
+    U = np.asarray(U, dtype=np.float64); V = np.asarray(V, dtype=np.float64)
+    S = _vec(S); a = _vec(a); b = _vec(b)
+    m, n = U.shape[0], V.shape[0]
+    cols = np.asarray(cols, dtype=np.int64).ravel()
+    if cols.size and (cols.min() < 0 or cols.max() >= m):
+        raise ValueError("sampled columns must lie in [0, m)")
+    # STEP 1
+    p = gemv_t(U, a)
+    q = gemv_t(V, b)
+    alpha, beta = float(a @ a), float(b @ b)
+    # STEPs 2 and 3: [a btilde] Qu = [a1 b1], [b atilde] Qv = [a2 b2], in the basis
+    r1, r2, Qu = schur2(beta)
+    r3, r4, Qv = schur2(alpha)
+    sq = S * q[:m]
+    sp = np.concatenate([S * p, np.zeros(n - m)])
+    z1 = Qu[0, 0] * p + Qu[1, 0] * sq
+    z2p = Qu[0, 1] * p + Qu[1, 1] * sq
+    z3 = Qv[0, 0] * q + Qv[1, 0] * sp
+    z4p = Qv[0, 1] * q + Qv[1, 1] * sp
+    Du = S * S
+    Dv = np.concatenate([S * S, np.zeros(n - m)])
+
+    def side(X, D, za, zb_prime, ra, rb, N):
+        lam1, zrow = rank_one_update_z(zb_prime[None, :], D, za, ra)   # z of the second solve
+        E = np.zeros((N, cols.size))
+        E[N - 1 - cols, np.arange(cols.size)] = 1.0
+        lam2, Q2E = rank_one_apply(lam1, zrow[0], rb, E)
+        _, W = rank_one_apply(D, za, ra, Q2E)
+        return lam2, X @ W
+
+    lam_u, Un = side(U, Du, z1, z2p, r1, r2, m)                  # STEPs 4, 5
+    _, Vn = side(V, Dv, z3, z4p, r3, r4, n)                      # STEPs 6, 7
+    Sn = np.sqrt(np.maximum(lam_u, 0.0))[::-1].copy()            # STEP 8
+    # pair the signs: u_j^T Ahat v_j >= 0, Ahat v = U (S (V^T v)[:m]) + a (b^T v)
+    for c in range(cols.size):
+        v = Vn[:, c]
+        t = Un[:, c] @ (U @ (S * (V.T @ v)[:m]) + a * (b @ v))
+        if t < 0.0:
+            Vn[:, c] = -v
+    return Sn, Un, Vn
 
 
 def jacobi_svd(A):

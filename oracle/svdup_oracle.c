@@ -21,6 +21,8 @@
  *                          computed roots by the characteristic-polynomial identity
  *                          (Loewner) so that the columns are the exact eigenvectors of
  *                          the problem whose exact eigenvalues are the computed roots.
+ *   oracle_rank_one_apply  Q X for a thin X: the products of Alg. 6.1 STEPs 5 and 7 on
+ *                          a few sampled vectors (full-size checks column by column).
  *   oracle_rank_one_update RankOneUpdate STEPs 1-7 with the dense product X*Q in place
  *                          of the FMM of STEP 6 (the dense product is the quantity the
  *                          FMM approximates).
@@ -471,6 +473,47 @@ int oracle_rank_one_update_z(int rows, int N, const double* X, int ldx, const do
     }
     eigsys_free(&e);
     return st;
+}
+
+/* Y = Q X: the eigenvector matrix Q of diag(d) + rho z z^T (Sec. 3.2; column c belongs
+ * to the c-th smallest eigenvalue, rows follow the order of d) applied to a thin X
+ * (N x s, column-major, leading dimension N), one column of Q at a time.  This is the
+ * product of Alg. 6.1 STEPs 5 and 7 evaluated for a few sampled vectors, so that sizes
+ * whose full product is out of reach can still be checked column by column.  lam (N)
+ * receives the eigenvalues, ascending. */
+int oracle_rank_one_apply(int N, const double* d, const double* z, double rho, int s,
+                          const double* X, double* Y, double* lam)
+{
+    if (N <= 0 || s < 0) return ORC_EINVAL;
+    eigsys e;
+    int st = eigsys_build(N, d, z, rho, &e);
+    if (st == ORC_ENOMEM) return st;
+    for (int q = 0; q < N; q++) lam[q] = e.lam[q];
+    int fail = 0;
+    #pragma omp parallel
+    {
+        double* work = (double*)malloc(sizeof(double) * N);
+        double* qv = (double*)malloc(sizeof(double) * N);
+        if (!work || !qv) {
+            #pragma omp atomic write
+            fail = 1;
+        }
+        #pragma omp for schedule(dynamic, 1)
+        for (int t = 0; t < s; t++) {
+            if (!work || !qv) continue;
+            const double* x = X + (size_t)t * N;
+            double* y = Y + (size_t)t * N;
+            for (int r = 0; r < N; r++) y[r] = 0.0;
+            for (int c = 0; c < N; c++) {
+                if (x[c] == 0.0) continue;
+                eigsys_column(&e, c, qv, work);
+                for (int r = 0; r < N; r++) y[r] += qv[r] * x[c];
+            }
+        }
+        free(work); free(qv);
+    }
+    eigsys_free(&e);
+    return fail ? ORC_ENOMEM : st;
 }
 
 /* RankOneUpdate (Sec. 6.2), STEPs 1-7, literally: abar = X^T a1 (STEP 1), then the

@@ -81,6 +81,9 @@ MUTANTS = [
      "for (int i = 0; i < m; i++) beta += b[i] * b[i];"),
     ("step3_transposed_Q", "Alg. 6.1 STEP 3: [b atilde] Q = [a2 b2]",
      "a2[i] = qv[2] * b[i] + qv[3] * at[i];", "a2[i] = qv[3] * b[i] + qv[2] * at[i];"),
+    ("apply_index", "Alg. 6.1 STEPs 5, 7: Q X summed over the columns of Q",
+     "for (int r = 0; r < N; r++) y[r] += qv[r] * x[c];",
+     "for (int r = 0; r < N; r++) y[r] += qv[r] * x[r];"),
     ("jacobi_rotation", "one-sided Jacobi: an orthogonal plane rotation",
      "wp[i] = c * x - s * y; wq[i] = s * x + c * y;",
      "wp[i] = c * x - s * y; wq[i] = s * x - c * y;"),

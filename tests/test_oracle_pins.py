@@ -384,6 +384,55 @@ def test_svd_duplicated_sigma(orc):
     _check_svd(orc, U, S, V, a, b)
 
 
+@pytest.mark.parametrize("m,n,seed", [(48, 48, 60), (50, 90, 61)])
+def test_svd_update_sampled_columns(orc, m, n, seed):
+    """The sampled form of Alg. 6.1 (every singular value, a few columns of the
+    vectors, for sizes whose dense products are out of reach): its values are LAPACK's
+    for the explicit Ahat, each sampled pair is a unit singular pair with the paired
+    sign (Ahat v_j = sigma_j u_j, Ahat^T u_j = sigma_j v_j), and it agrees with the dense
+    form column by column."""
+    g = wl.rng(seed)
+    U = wl.haar(m, g)
+    V = wl.haar(n, g)
+    S = np.sort(g.uniform(0.1, 3.0, m))[::-1]
+    a = g.standard_normal(m)
+    b = g.standard_normal(n)
+    cols = np.array([0, 1, m // 2, m - 2, m - 1])
+    Sn, Un, Vn = orc.svd_update_sampled(U, S, V, a, b, cols)
+    Ah = U @ np.diag(S) @ V[:, :m].T + np.outer(a, b)
+    ref = np.linalg.svd(Ah, compute_uv=False)
+    assert np.abs(Sn - ref).max() <= 1e-14 * ref[0]
+    for c, j in enumerate(cols):
+        u, v = Un[:, c], Vn[:, c]
+        assert abs(u @ u - 1.0) <= 64 * U53 and abs(v @ v - 1.0) <= 64 * U53
+        assert np.linalg.norm(Ah @ v - Sn[j] * u) <= 1e-14 * ref[0]
+        assert np.linalg.norm(Ah.T @ u - Sn[j] * v) <= 1e-14 * ref[0]
+    Uo, So, Vo = orc.svd_update(U, S, V, a, b)
+    assert np.abs(Un - Uo[:, cols]).max() <= 1e-13
+    assert np.abs(Vn - Vo[:, cols]).max() <= 1e-13
+
+
+def test_rank_one_apply_is_the_eigenvector_product(orc):
+    """Q X column by column (the sampled products): on unit vectors it returns LAPACK's
+    eigenvectors up to sign, and it is linear in X."""
+    g = np.random.default_rng(62)
+    N = 40
+    d = np.sort(g.uniform(0.0, 1.0, N))
+    z = g.standard_normal(N)
+    rho = 0.9
+    E = np.eye(N)[:, [0, 7, 39]]
+    lam, QE = orc.rank_one_apply(d, z, rho, E)
+    w, W = np.linalg.eigh(np.diag(d) + rho * np.outer(z, z))
+    assert np.abs(lam - w).max() <= 64 * N * U53 * np.abs(w).max()
+    ref = W[:, [0, 7, 39]]
+    sgn = np.sign(np.sum(ref * QE, axis=0))
+    assert np.abs(ref * sgn - QE).max() <= 1e-12
+    X = g.standard_normal((N, 3))
+    _, Y = orc.rank_one_apply(d, z, rho, X)
+    _, Y2 = orc.rank_one_apply(d, z, rho, 2.0 * X[:, :1] - X[:, 1:2])
+    assert np.abs(Y2[:, 0] - (2.0 * Y[:, 0] - Y[:, 1])).max() <= 1e-13
+
+
 def test_jacobi_svd_vs_lapack(orc):
     g = np.random.default_rng(4)
     for m, n in [(1, 1), (3, 7), (20, 20), (31, 45)]:
