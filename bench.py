@@ -78,32 +78,55 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 25 ms from before the
+    warm-up until after the timed region.  Each sample carries nvidia-smi's own
+    timestamp (the time of arrival where that does not parse); stop() summarises the
+    samples that fall inside the host wall-clock window of the timed region."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, gpu: int):
+    def __init__(self, gpu: int, interval_ms: int = 25):
         self.gpu = gpu
+        self.interval_ms = interval_ms
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
 
-    def start(self):
+    def start(self, wait_s: float = 3.0):
+        """Start sampling; wait (at most wait_s) for the first sample."""
+        self.lines = []
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits",
+                                          "-lms", str(self.interval_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + wait_s
+        while not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    @staticmethod
+    def _stamp(text, arrival):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except Exception:
+            return arrival
+
+    def stop(self, window=None):
+        """Summary of the samples taken in `window` = (t0, t1), host wall-clock seconds
+        (all samples when window is None).  Where none fell inside, the samples within
+        250 ms of it are used and in_window is false."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -111,22 +134,39 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        try:
+            return self._summary(window)
+        except Exception as e:  # the record is evidence, never a reason to lose the line
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock record unreadable: %s" % e]}
+
+    def _summary(self, window):
+        samples = []
+        for arrival, ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1])); smax.append(float(f[2]))
+                sm, smax = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": float(max(smax)) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            reasons = {nm for nm, v in zip(self.NAMES, f[6:10]) if v.lower() == "active"}
+            samples.append((self._stamp(f[0], arrival), sm, smax, reasons))
+        chosen, in_window = samples, None
+        if window is not None:
+            t0, t1 = window
+            chosen = [x for x in samples if t0 <= x[0] <= t1]
+            in_window = bool(chosen)
+            if not chosen:
+                chosen = [x for x in samples if t0 - 0.25 <= x[0] <= t1 + 0.25]
+        out = {"sm_mhz": float(np.median([x[1] for x in chosen])) if chosen else None,
+               "sm_max_mhz": float(max(x[2] for x in chosen)) if chosen else None,
+               "reasons": sorted(set().union(*[x[3] for x in chosen])) if chosen else [],
+               "samples": len(chosen)}
+        if window is not None:
+            out["in_window"] = in_window
+            out["window_ms"] = round((window[1] - window[0]) * 1e3, 3)
+            out["interval_ms"] = self.interval_ms
+        return out
 
 
 def cpu_cores():
@@ -265,6 +305,8 @@ def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, w
     `stage_steps` further updates after the timed region."""
     import torch
     with torch.cuda.stream(stream):
+        if clocks is not None:
+            clocks.start()  # running, with a first sample, before the warm-up
         for i in range(warmup):
             h.update(tU, tS, tV, ta[i], tb[i], eps=eps, mode=mode, check=False)
         rc = h.sync()
@@ -272,20 +314,20 @@ def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, w
             raise SystemExit("warm-up update failed: %s" % sv.error_string(rc))
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         launches0 = h.launch_count()
-        if clocks is not None:
-            clocks.start()
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
+        t_wall0 = time.time()
         ev[0].record(stream)
         for i in range(steps):
             j = warmup + i
             h.update(tU, tS, tV, ta[j], tb[j], eps=eps, mode=mode, check=False)
             ev[i + 1].record(stream)
         torch.cuda.synchronize(dev)
+        t_wall1 = time.time()
         if ws > 1:
             torch.distributed.barrier()
-        clk = clocks.stop() if clocks is not None else None
+        clk = clocks.stop((t_wall0, t_wall1)) if clocks is not None else None
         launches = h.launch_count() - launches0
         rc = h.sync()
         if rc != 0:

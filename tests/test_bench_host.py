@@ -61,20 +61,28 @@ class _Stopped:
         return 0
 
 
-def _summary(lines):
+def _summary(rows, window=None):
+    """rows: (seconds after t=1000, the fields after the timestamp)."""
+    import datetime
     c = bench.ClockSampler(0)
     c.proc = _Stopped()
-    c.lines = list(lines)
-    return c.stop()
+    c.lines = []
+    for t, rest in rows:
+        stamp = datetime.datetime.fromtimestamp(1000.0 + t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        c.lines.append((0.0, stamp + ", " + rest))
+    return c.stop(None if window is None else (1000.0 + window[0], 1000.0 + window[1]))
+
+
+IDLE = "Not Active, Not Active, Not Active, Not Active"
 
 
 def test_clock_summary_takes_median_and_reasons():
     out = _summary([
-        "0, 2070, 2070, 812.3, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
-        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
-        "0, 2055, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
-        "malformed line",
-        "0, [N/A], 2070, 0, 0x0, Active, Not Active, Not Active, Not Active",
+        (0.00, "0, 2070, 2070, 812.3, 0x0000000000000000, " + IDLE),
+        (0.03, "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active"),
+        (0.06, "0, 2055, 2070, 1200.0, 0x0000000000000000, " + IDLE),
+        (0.07, "malformed line"),
+        (0.08, "0, [N/A], 2070, 0, 0x0, Active, Not Active, Not Active, Not Active"),
     ])
     assert out == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
                    "samples": 3}
@@ -82,16 +90,56 @@ def test_clock_summary_takes_median_and_reasons():
 
 def test_clock_summary_names_every_slowdown():
     out = _summary([
-        "0, 1500, 2070, 1400.0, 0x48, Active, Active, Not Active, Not Active",
-        "0, 1600, 2070, 1400.0, 0x20, Not Active, Not Active, Active, Not Active",
+        (0.0, "0, 1500, 2070, 1400.0, 0x48, Active, Active, Not Active, Not Active"),
+        (0.1, "0, 1600, 2070, 1400.0, 0x20, Not Active, Not Active, Active, Not Active"),
     ])
     assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
     assert out["sm_mhz"] == 1550.0 and out["samples"] == 2
 
 
+def test_clock_summary_keeps_the_timed_window():
+    rows = [(0.00, "0, 1200, 2070, 300.0, 0x1, " + IDLE),       # idle, before the region
+            (0.50, "0, 2070, 2070, 1300.0, 0x0, " + IDLE),
+            (0.55, "0, 2040, 2070, 1350.0, 0x0, " + IDLE),
+            (0.60, "0, 2070, 2070, 1380.0, 0x0, " + IDLE),
+            (1.50, "0, 1100, 2070, 200.0, 0x1, Active, Not Active, Not Active, Not Active")]
+    out = _summary(rows, window=(0.45, 0.65))
+    assert out["samples"] == 3 and out["in_window"] is True and out["sm_mhz"] == 2070.0
+    assert out["reasons"] == [] and abs(out["window_ms"] - 200.0) < 1e-6
+    near = _summary(rows, window=(0.70, 0.72))      # no sample inside: the nearest 250 ms
+    assert near["in_window"] is False and near["samples"] == 3
+
+
 def test_clock_summary_without_nvidia_smi():
     c = bench.ClockSampler(0)
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_clock_sampler_reads_a_running_tool(tmp_path, monkeypatch):
+    """The sampler as bench.py runs it, against a stand-in nvidia-smi on PATH that
+    prints a timestamped sample every 10 ms."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!" + sys.executable + "\n"
+        "import datetime, sys, time\n"
+        "while True:\n"
+        "    t = datetime.datetime.now().strftime('%Y/%m/%d %H:%M:%S.%f')[:-3]\n"
+        "    print(t + ', 0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active',"
+        " flush=True)\n"
+        "    time.sleep(0.01)\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    import time
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.lines, "no first sample before the timed region"
+    t0 = time.time()
+    time.sleep(0.2)
+    t1 = time.time()
+    time.sleep(0.05)
+    out = c.stop((t0, t1))
+    assert out["in_window"] is True and out["samples"] >= 5
+    assert out["sm_mhz"] == 2070.0 and out["reasons"] == []
 
 
 def test_recorded_traffic_belongs_to_its_source(tmp_path, monkeypatch):
