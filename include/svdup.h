@@ -113,6 +113,9 @@ int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, do
  *                       any other value returns SVDUP_EINVAL.
  * The signs of Vhat's columns are chosen so that u_j^T Ahat v_j >= 0.
  * Requires 1 <= m <= n.  U, V are assumed orthogonal (as the paper does, App. A).
+ * Sizes: element offsets are 64-bit and the workspace grows with m and n
+ * (svdup_update_workspace reports it); parity with the FP64 oracle has been shown up
+ * to m = n = 8192 and 2048 x 4096.
  */
 int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double* V, int ldv,
                  const double* a, const double* b, double eps, int mode);
