@@ -1,5 +1,6 @@
 """The C ABI library builds for sm_103a, loads, and exports every entry point that
-include/*.h declares (no GPU needed: nothing is called)."""
+include/*.h declares; without the library or without a GPU, the product path fails
+loudly (no GPU needed: no compute call is made)."""
 import ctypes
 import glob
 import os
@@ -40,3 +41,39 @@ def test_error_strings_without_gpu():
     assert sv.error_string(sv.OK) == "ok"
     assert "converge" in sv.error_string(sv.ENOCONV)
     assert sv.error_string(12345) == "unknown error"
+
+
+def _child(code):
+    import subprocess
+    import sys
+    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                          timeout=300)
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No CPU path exists: the binding raises when libsvdup.so is absent."""
+    r = _child("import paper_1707_08369_gb300 as sv\n"
+               "try:\n"
+               "    sv.load('/nonexistent/libsvdup.so')\n"
+               "except RuntimeError as e:\n"
+               "    print('raised:', e)\n")
+    assert r.returncode == 0, r.stderr
+    assert "raised: libsvdup.so not built" in r.stdout
+
+
+def test_handle_without_a_gpu_is_an_error():
+    """Without a CUDA device, creating a handle returns SVDUP_ECUDA: the library has no
+    host fallback to quietly run instead."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1707_08369_gb300 import build
+    build.build()
+    r = _child("import ctypes\n"
+               "import paper_1707_08369_gb300 as sv\n"
+               "lib = sv.load()\n"
+               "h = ctypes.c_void_p()\n"
+               "print('code', lib.svdup_create(ctypes.byref(h), 0, None, 0), h.value)\n")
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "code %d None" % 5, r.stdout  # SVDUP_ECUDA, no handle
