@@ -107,8 +107,12 @@ int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, do
  *   V  n x n (ldv >= n), in: V, out: Vhat; Vhat[:, :m] pairs with Uhat and Shat,
  *                       Vhat[:, m:] is an orthonormal basis of the null space.
  *   a  m, b n           the rank-one term a b^T (read only).
- *   eps                 accuracy of the Cauchy products, 0 < eps < 1; the
- *                       expansion order is p = ceil(log5(1/eps)) (App. D STEP 1).
+ *   eps                 target accuracy of the Cauchy products, 0 < eps < 1; the
+ *                       expansion order is p = ceil(log5(1/eps)) (App. D STEP 1) in
+ *                       FP64 mode (16 in the mixed modes).  The far field's error for
+ *                       the closest admissible leaf pair (a gap of one leaf radius)
+ *                       is 4 (2 + sqrt 3)^-p of that pair's largest kernel entry:
+ *                       about 200 eps at eps = 1e-12.
  *   mode                SVDUP_FP64 or SVDUP_MIXED_BF16X3, optionally | SVDUP_DENSE;
  *                       any other value returns SVDUP_EINVAL.
  * The signs of Vhat's columns are chosen so that u_j^T Ahat v_j >= 0.
