@@ -77,3 +77,33 @@ def test_handle_without_a_gpu_is_an_error():
                "print('code', lib.svdup_create(ctypes.byref(h), 0, None, 0), h.value)\n")
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == "code %d None" % 5, r.stdout  # SVDUP_ECUDA, no handle
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/svdup.h compiles as C11 without warnings, and a C program links
+    against libsvdup.so and calls it (without a GPU the call reports SVDUP_ECUDA)."""
+    import shutil
+    import subprocess
+    import pytest
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_1707_08369_gb300 import build
+    lib = build.build()
+    src = tmp_path / "use.c"
+    src.write_text('#include "svdup.h"\n#include <stdio.h>\n'
+                   "int main(void) {\n"
+                   "  svdup_t h = 0;\n"
+                   "  int rc = svdup_create(&h, 0, NULL, 0u);\n"
+                   '  printf("%d %s\\n", rc, svdup_error_string(rc));\n'
+                   "  if (rc == SVDUP_OK) svdup_destroy(h);\n"
+                   "  return 0;\n}\n")
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(lib)
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I" + os.path.join(ROOT, "include"), str(src), "-L" + libdir, "-lsvdup",
+                        "-Wl,-rpath," + libdir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    code = int(out.stdout.split()[0])
+    assert code in (0, 5), out.stdout  # OK with a GPU, SVDUP_ECUDA without
