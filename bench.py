@@ -9,11 +9,13 @@ result (chained updates, Alg. 6.1), inputs resident in HBM.  U and V are 512 MiB
 each, larger than L2, so no flush is needed between steps.
 
 One JSON line on stdout (rank 0).  `value` is whole-job updates/s (device-timed with
-CUDA events on the library's stream); `fp64` is the plain FP64 form on the same inputs;
-`e2e` is the same metric through the host-buffer entry point (copies inside the timed
-region); `roofline` is for the dominant kernel (timed live with the library's stage
-timers, which bracket exactly that kernel's launches); `cpu_baseline` is the CPU oracle
-on a bounded, extrapolated sample of the same update.
+CUDA events on the library's stream); `fp64` is the plain FP64 form on the same inputs,
+with its own timed region, roofline, clock record and end-to-end figure; `e2e` is the
+same metric through the host-buffer entry point (copies inside the timed region);
+`roofline` is for the dominant product kernel, whose launches are timed by event pairs
+on their own stream inside the timed region, against App. D's algorithmic operation
+count; `cpu_baseline` is the CPU oracle on a bounded, extrapolated sample of the same
+update.
 
 --impl reference times the CPU oracle (the reference arm of this comparison) instead.
 Under torchrun every rank runs an independent replica (no collective in the data path).
@@ -50,12 +52,12 @@ def bench_config(args, ws):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--mode", default="bf16x3", choices=list(MODES))
-    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -88,7 +90,7 @@ class ClockSampler:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, gpu: int, interval_ms: int = 25):
+    def __init__(self, gpu: int, interval_ms: int = 10):
         self.gpu = gpu
         self.interval_ms = interval_ms
         self.proc = None
@@ -296,13 +298,57 @@ def fp64_peak_tflops(sm_mhz):
     return 152 * 2 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
 
 
+STAGE_KERNELS = {"p2m": "P2M", "m2l": "M2L", "out": "OUT"}
+
+
+def roofline_of(kernels, mode, clk, peaks, peak_src, n, mode_name):
+    """Roofline of the dominant product kernel, from its own event timers over the timed
+    region: achieved = the algorithmic flops of its launches (App. D's operation count,
+    14 N p multiply-adds per right-hand side for the whole FMM, of which STEPs 9-10 fall
+    to the output stage) / their summed duration.  The executed flops (the six split BF16
+    partial products, padding included) and the useful flops of the flat partition are
+    reported beside it."""
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    ms, cnt, useful, executed, alg = kernels[dom]
+    cnt = max(int(cnt), 1)
+    per_launch_s = ms / cnt / 1e3
+    per = lambda fl: fl / cnt / per_launch_s / 1e12
+    if mode == 0:
+        peak = fp64_peak_tflops(clk.get("sm_mhz") if clk else None)
+        r = {"kernel": "k_gemm_f64<%s>" % STAGE_KERNELS[dom], "bound": "alu",
+             "achieved": per(alg), "peak": peak, "unit": "TFLOP/s", "frac": per(alg) / peak,
+             "traffic": None, "useful_tflops": per(useful), "useful_frac": per(useful) / peak,
+             "peak_source": "FP64 pipe from unit counts and the sampled SM clock "
+                            "(152 SMs x 2 DFMA/clk x 2 flops), not a measured figure"}
+    else:
+        peak = float(peaks["bf16_tflops_sustained"])
+        r = {"kernel": "k_umma<%s>" % STAGE_KERNELS[dom], "bound": "tensor",
+             "achieved": per(alg), "peak": peak, "unit": "TFLOP/s", "frac": per(alg) / peak,
+             "traffic": recorded_traffic(n, mode_name) if dom == "out" else None,
+             "executed_tflops": per(executed), "executed_frac": per(executed) / peak,
+             "useful_tflops": per(useful),
+             "peak_source": "bf16_tflops_sustained, %s (kernel timed inside a long step)" % (
+                 "of MEASURED_PEAKS.json" if peak_src == "measured" else
+                 "fallback figure (MEASURED_PEAKS.json absent)")}
+    r.update({"launches": cnt, "ms_per_launch": ms / cnt,
+              "alg_flops_per_launch": alg / cnt,
+              "work": "algorithmic flops: App. D's 14 N p multiply-adds per row for N points at "
+                      "order p, split 2:5:7 over P2M, M2L, OUT; N = the product's non-deflated "
+                      "size, 2 flops per multiply-add; launch durations from event pairs on the "
+                      "kernel's own stream inside the timed region"})
+    return r
+
+
 def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, ws, dev, clocks=None,
                   stage_steps=1):
     """W untimed then K timed chained updates on the handle's stream; returns per-update
     latencies (ms), the total (ms), the launch count, the stage timers and how many
-    updates they cover.  The timed updates run as in use (the left- and right-hand
-    problems on two streams); the stage timers need one stream, so they come from
-    `stage_steps` further updates after the timed region."""
+    updates they cover, the clock record, and the product kernels' own timers over the
+    timed region.  The timed updates run as in use (the left- and right-hand problems on
+    their streams), with the kernel timers on: an event pair around each product-stage
+    kernel on the stream it runs on, which leaves the schedule as it is.  The per-stage
+    breakdown needs one stream, so it comes from `stage_steps` further updates after the
+    timed region."""
     import torch
     with torch.cuda.stream(stream):
         if clocks is not None:
@@ -312,6 +358,7 @@ def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, w
         rc = h.sync()
         if rc != 0:
             raise SystemExit("warm-up update failed: %s" % sv.error_string(rc))
+        h.timing(sv.TIMING_KERNELS)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         launches0 = h.launch_count()
         if ws > 1:
@@ -332,6 +379,10 @@ def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, w
         rc = h.sync()
         if rc != 0:
             raise SystemExit("timed update failed: %s" % sv.error_string(rc))
+        kernels = h.timing_read()
+        alg = h.timing_read_alg()
+        kernels = {k: v + (alg[k],) for k, v in kernels.items() if k in ("p2m", "m2l", "out")}
+        h.timing(False)
         stages = None
         if stage_steps > 0:
             h.timing(True)
@@ -347,7 +398,7 @@ def timed_updates(sv, h, stream, tU, tS, tV, ta, tb, mode, eps, warmup, steps, w
     total_ms = float(ev[0].elapsed_time(ev[-1]))
     if ws > 1:
         total_ms = max_over_ranks(total_ms, dev)
-    return lat, total_ms, launches, (stages, stage_steps), clk
+    return lat, total_ms, launches, (stages, stage_steps), clk, kernels
 
 
 def max_over_ranks(ms, device):
@@ -564,23 +615,65 @@ def main():
     h = sv.Handle(local, stream=stream)
     tU, tS, tV = upload()
     clocks = ClockSampler(local)
-    lat, total_ms, launches, (stages, stage_n), clk = timed_updates(
+    lat, total_ms, launches, (stages, stage_n), clk, kern = timed_updates(
         sv, h, stream, tU, tS, tV, ta, tb, mode, args.eps, args.warmup, args.steps, ws, dev, clocks)
     value = replica_rate(args.steps, total_ms, ws)
+    peaks, peak_src = load_peaks()
+    roofline = roofline_of(kern, mode, clk, peaks, peak_src, n, args.mode)
+    stage_ms = {k: round(v[0] / stage_n, 3) for k, v in stages.items()}
 
-    # the plain FP64 form on the same GPU, same workload (the comparison the metric names)
+    def e2e_form(m_, steps_):
+        """The same metric end to end through the host-buffer entry point: every step
+        copies U, S, V, a, b from pinned host memory to the device and the results back
+        (host wall clock around the call, which waits for completion)."""
+        pU = torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
+        pV = torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
+        pS = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        pa = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        pb = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        pUf = pU.T  # column-major views of the pinned buffers
+        pVf = pV.T
+        pUf[...] = tU.cpu().numpy()
+        pVf[...] = tV.cpu().numpy()
+        pS[...] = tS.cpu().numpy()
+        times = []
+        for i in range(steps_ + 1):  # the first call is an untimed warm-up
+            pa[...] = ab[i % len(ab)][0]
+            pb[...] = ab[i % len(ab)][1]
+            t0 = time.perf_counter()
+            h.update_host(pUf, pS, pVf, pa, pb, eps=args.eps, mode=m_)
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        t = float(np.mean(times))
+        if ws > 1:
+            t = max_over_ranks(t, dev)
+        return {"value": ws / t, "unit": "updates/s", "steps": steps_,
+                "h2d_bytes_per_step": 8 * (2 * n * n + 3 * n),
+                "d2h_bytes_per_step": 8 * (2 * n * n + n)}
+
+    # the plain FP64 form on the same GPU, same workload (the comparison the metric names):
+    # its own timed region, clock record, roofline and end-to-end figure
     fp64 = None
     if mode != 0 and not args.no_fp64:
         del tU, tV
         tU, tS, tV = upload()
-        k64 = max(3, args.fp64_steps)
-        lat64, tot64, _, _, _ = timed_updates(
-            sv, h, stream, tU, tS, tV, ta, tb, 0, args.eps, min(args.warmup, 3),
-            min(k64, steps_total - min(args.warmup, 3)), ws, dev, stage_steps=0)
+        w64 = min(args.warmup, 3)
+        k64 = min(max(3, args.fp64_steps), steps_total - w64)
+        clocks64 = ClockSampler(local, interval_ms=25)
+        lat64, tot64, _, _, clk64, kern64 = timed_updates(
+            sv, h, stream, tU, tS, tV, ta, tb, 0, args.eps, w64, k64, ws, dev, clocks64,
+            stage_steps=0)
         k64 = len(lat64)
         v64 = ws * k64 / (tot64 / 1e3)
-        fp64 = {"value": v64, "unit": "updates/s", "steps": k64, "ms_per_step": tot64 / k64,
-                "p99_ms": float(np.percentile(lat64, 99)), "mixed_over_fp64": value / v64}
+        fp64 = {"value": v64, "unit": "updates/s", "steps": k64, "warmup": w64,
+                "ms_per_step": tot64 / k64,
+                "latency_ms": {"p50": float(np.percentile(lat64, 50)),
+                               "p99": float(np.percentile(lat64, 99))},
+                "mixed_over_fp64": value / v64,
+                "roofline": roofline_of(kern64, 0, clk64, peaks, peak_src, n, "fp64"),
+                "clocks": clk64}
+        if not args.no_e2e and args.e2e_steps > 0:
+            fp64["e2e"] = e2e_form(0, args.e2e_steps)
         del tU, tV
         tU, tS, tV = upload()
 
@@ -594,60 +687,10 @@ def main():
         serving = serving_form(sv, dev, mode, args.eps, args.serve_seconds, 2000.0, 16, 8,
                                170708369 + 4)
 
-    # dominant product stage -> roofline (stage timers bracket exactly that kernel's launch)
-    peaks, peak_src = load_peaks()
-    prod = {k: v for k, v in stages.items() if k in ("p2m", "m2l", "out")}
-    dom = max(prod, key=lambda k: prod[k][0])
-    dom_ms, dom_cnt, dom_fl, dom_mma = prod[dom]
-    per_launch_s = (dom_ms / max(dom_cnt, 1)) / 1e3
-    stage_names = {"p2m": "P2M", "m2l": "M2L", "out": "OUT"}
-    if mode == 0:
-        peak = fp64_peak_tflops(clk.get("sm_mhz") if clk else None)
-        achieved = (dom_fl / max(dom_cnt, 1)) / per_launch_s / 1e12
-        roofline = {"kernel": "k_gemm_f64<%s>" % stage_names[dom], "bound": "alu",
-                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None,
-                    "peak_source": "FP64 pipe from unit counts and the sampled SM clock "
-                                   "(152 SMs x 2 DFMA/clk x 2 flops)"}
-    else:
-        peak = float(peaks["bf16_tflops_sustained"])
-        achieved = (dom_mma / max(dom_cnt, 1)) / per_launch_s / 1e12
-        useful = (dom_fl / max(dom_cnt, 1)) / per_launch_s / 1e12
-        roofline = {"kernel": "k_umma<%s>" % stage_names[dom], "bound": "tensor",
-                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": recorded_traffic(n, args.mode) if dom == "out" else None,
-                    "useful_tflops": useful,
-                    "peak_source": "bf16_tflops_sustained of %s MEASURED_PEAKS.json (kernel timed "
-                                   "inside a long step); achieved counts the six split BF16 "
-                                   "products executed; launch duration from the stage timers of "
-                                   "an update run right after the timed region on one stream" % peak_src}
-    stage_ms = {k: round(v[0] / stage_n, 3) for k, v in stages.items()}
-
     # end-to-end through the host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
-        pU = torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
-        pV = torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy()
-        pS = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-        pa = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-        pb = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-        pUf = pU.T  # column-major views of the pinned buffers
-        pVf = pV.T
-        pUf[...] = tU.cpu().numpy()
-        pVf[...] = tV.cpu().numpy()
-        pS[...] = tS.cpu().numpy()
-        times = []
-        for i in range(args.e2e_steps + 1):  # the first call is an untimed warm-up
-            pa[...] = ab[i % len(ab)][0]
-            pb[...] = ab[i % len(ab)][1]
-            t0 = time.perf_counter()
-            h.update_host(pUf, pS, pVf, pa, pb, eps=args.eps, mode=mode)
-            if i > 0:
-                times.append(time.perf_counter() - t0)
-        h2d = 8 * (2 * n * n + 3 * n)
-        d2h = 8 * (2 * n * n + n)
-        e2e = {"value": ws / float(np.mean(times)), "unit": "updates/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+        e2e = e2e_form(mode, args.e2e_steps)
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -85,8 +85,20 @@ long long svdup_launch_count(svdup_t h);
 #define SVDUP_STAGE_OUT 7     /* L2P + near field (or the dense product) */
 #define SVDUP_NSTAGE 8
 
-/* Enable (1) or disable (0) the stage timers; enabling clears the totals.  Timing
- * adds two event records per stage and does not change results. */
+/* Timer modes (svdup_timing's enable argument):
+ *  SVDUP_TIMING_STAGES   every stage above is timed; the update then runs all its work
+ *                        on the handle's stream, in dependency order, so that the stage
+ *                        intervals do not overlap.
+ *  SVDUP_TIMING_KERNELS  only the three product-stage kernels (P2M, M2L, OUT) are timed,
+ *                        each by an event pair on the stream it is launched on; the
+ *                        update keeps its multi-stream schedule, so the times are those
+ *                        of the kernels as they run beside the solves. */
+#define SVDUP_TIMING_STAGES 1
+#define SVDUP_TIMING_KERNELS 2
+
+/* Set the timer mode (0 disables); setting it clears the totals.  Timing adds two
+ * event records per timed interval and one small counting kernel per product, and
+ * does not change results.  Any other value returns SVDUP_EINVAL. */
 int svdup_timing(svdup_t h, int enable);
 
 /* Wait for the stream and return, per stage, the summed device time in ms, the
@@ -98,6 +110,15 @@ int svdup_timing(svdup_t h, int enable);
 int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, double* mma_flops,
                       int nstage);
 
+/* The algorithmic flops of the product stages since timing was enabled: App. D's
+ * operation count of the FMM, 14 N p multiply-adds per right-hand side for N points
+ * at expansion order p (leaves of 2p points), split as STEPs 5-6 (2 N p) to P2M,
+ * STEPs 7-8 (5 N p) to M2L and STEPs 9-10 (7 N p) to OUT, with 2 flops per
+ * multiply-add and N the non-deflated size of each product; 2 rows N^2 for the dense
+ * product (in OUT).  Stages other than the three product stages read 0.  This is the
+ * method's own work, not what the kernels execute (svdup_timing_read). */
+int svdup_timing_read_alg(svdup_t h, double* alg_flops, int nstage);
+
 /*
  * The full rank-one SVD update, Alg. 6.1 STEPs 1-8, in place (device pointers):
  *   U  m x m (ldu >= m), in: U, out: Uhat, columns ordered as Shat.
@@ -107,12 +128,14 @@ int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, do
  *   V  n x n (ldv >= n), in: V, out: Vhat; Vhat[:, :m] pairs with Uhat and Shat,
  *                       Vhat[:, m:] is an orthonormal basis of the null space.
  *   a  m, b n           the rank-one term a b^T (read only).
- *   eps                 target accuracy of the Cauchy products, 0 < eps < 1; the
- *                       expansion order is p = ceil(log5(1/eps)) (App. D STEP 1) in
- *                       FP64 mode (16 in the mixed modes).  The far field's error for
- *                       the closest admissible leaf pair (a gap of one leaf radius)
- *                       is 4 (2 + sqrt 3)^-p of that pair's largest kernel entry:
- *                       about 200 eps at eps = 1e-12.
+ *   eps                 target accuracy of the Cauchy products, 0 < eps < 1.  In FP64
+ *                       mode the expansion order p is chosen so that the far field's
+ *                       error for the closest admissible leaf pair (a gap of one leaf
+ *                       radius), 4 (2 + sqrt 3)^-p of that pair's largest kernel entry,
+ *                       is at most eps: p = ceil(log(4/eps) / log(2 + sqrt 3)), 23 at
+ *                       eps = 1e-12, clamped to [4, 32].  (App. D STEP 1's
+ *                       p = log5(1/eps) is the rate of the paper's interaction lists,
+ *                       whose leaves are two radii apart.)  The mixed modes use p = 16.
  *   mode                SVDUP_FP64 or SVDUP_MIXED_BF16X3, optionally | SVDUP_DENSE;
  *                       any other value returns SVDUP_EINVAL.
  * The signs of Vhat's columns are chosen so that u_j^T Ahat v_j >= 0.

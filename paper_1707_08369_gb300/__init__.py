@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libsvdup.so")
 OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE, ECUDA, EORDER, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6, 7
 FP64, MIXED_BF16X3, MIXED_FP16X2 = 0, 1, 2  # MIXED_FP16X2: reserved, rejected (EINVAL)
 DENSE, REFINE = 0x100, 0x200                 # REFINE: reserved, rejected (EINVAL)
+TIMING_STAGES, TIMING_KERNELS = 1, 2      # svdup_timing modes
 
 _lib = None
 
@@ -48,6 +49,7 @@ def load(path: str = LIB_PATH):
     lib.svdup_launch_count.restype = ctypes.c_longlong
     lib.svdup_timing.argtypes = [P, I]
     lib.svdup_timing_read.argtypes = [P, P, P, P, P, I]
+    lib.svdup_timing_read_alg.argtypes = [P, P, I]
     lib.svdup_update.argtypes = [P, I, I, P, I, P, P, I, P, P, D, I]
     lib.svdup_update_host.argtypes = [P, I, I, P, I, P, P, I, P, P, D, I]
     lib.svdup_rank_one_eig.argtypes = [P, I, P, P, D, P, P, P, P, P, P, P, P]
@@ -162,8 +164,18 @@ class Handle:
 
     STAGES = ("gemv", "solve", "sign", "gather", "setup", "p2m", "m2l", "out")
 
-    def timing(self, enable: bool = True):
-        _check(load().svdup_timing(self._h, 1 if enable else 0), "svdup_timing")
+    def timing(self, enable=True):
+        """Timer mode: True / TIMING_STAGES (every stage, one stream), TIMING_KERNELS (the
+        product-stage kernels on their own streams, schedule unchanged), False / 0 off."""
+        mode = TIMING_STAGES if enable is True else int(enable)
+        _check(load().svdup_timing(self._h, mode), "svdup_timing")
+
+    def timing_read_alg(self):
+        """{stage: algorithmic flops (App. D's operation count)} since timing was enabled."""
+        n = len(self.STAGES)
+        fl = (ctypes.c_double * n)()
+        _check(load().svdup_timing_read_alg(self._h, fl, n), "svdup_timing_read_alg")
+        return {s: fl[i] for i, s in enumerate(self.STAGES)}
 
     def timing_read(self):
         """{stage: (ms, intervals, useful flops, executed tensor-core flops)} since

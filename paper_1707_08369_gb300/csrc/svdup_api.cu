@@ -68,8 +68,9 @@ struct svdup_ctx {
   long long cnt[SVDUP_NSTAGE];
   int open_stage;
   cudaEvent_t open_ev;
-  double* flops_dev;  // 6 accumulators, device: useful flops of P2M, M2L, OUT, then the
-                      // executed tensor-core flops of the same stages (mixed modes)
+  double* flops_dev;  // kFlopSlots accumulators, device: useful flops of P2M, M2L, OUT,
+                      // the executed tensor-core flops of the same stages (mixed modes),
+                      // then their algorithmic flops (App. D's operation count)
   // product-path choices (set by svdup_autotune; defaults below): index 0 FP64, 1 mixed
   int dense_max[2];   // N <= dense_max: dense Cauchy product (no far field)
   int leaf128_min[2]; // N >= leaf128_min: leaves of 128 poles, else 64
@@ -160,12 +161,17 @@ Eig make_eig(Arena& ar, int N) {
   return e;
 }
 
-// Expansion order from the accuracy (App. D STEP 1: p = log5(1/eps)), and the leaf
-// size: about 2p points per leaf in the paper (STEP 2); here leaves are wider so the
-// near field stays a few leaves across on graded spectra (relative leaf widths shrink
-// with more leaves) while the far field is a handful of large contractions.
+// Expansion order from the accuracy.  App. D STEP 1 takes p = log5(1/eps), the
+// convergence rate of two-sided Chebyshev interpolation of 1/(x - y) between leaves two
+// radii apart (the paper's interaction lists).  The flat partition here admits leaf
+// pairs one radius apart, where the error is 4 (2 + sqrt 3)^-p of the pair's largest
+// kernel entry (the Bernstein-ellipse rate for a singularity two radii from the leaf
+// centre), so p is chosen from that rate.  Leaf size: about 2p points per leaf in the
+// paper (STEP 2); here leaves are wider so the near field stays a few leaves across on
+// graded spectra (relative leaf widths shrink with more leaves) while the far field is
+// a handful of large contractions.
 int expansion_order(double eps) {
-  int p = (int)ceil(log(1.0 / eps) / log(5.0));
+  int p = (int)ceil(log(4.0 / eps) / log(2.0 + sqrt(3.0)));
   if (p < 4) p = 4;
   if (p > 32) p = 32;
   return p;
@@ -394,17 +400,27 @@ cudaEvent_t take_event(svdup_ctx* h) {
   return e;
 }
 
-void stage_begin(svdup_ctx* h, int stage) {
-  if (!h->timing) return;
-  h->open_stage = stage;
-  h->open_ev = take_event(h);
-  cudaEventRecord(h->open_ev, h->stream);
+// With timing == SVDUP_TIMING_STAGES every stage is timed and the update runs on one
+// stream; with SVDUP_TIMING_KERNELS only the three product-stage kernels are, each on
+// the stream it is launched on, and the update keeps its multi-stream schedule.  The
+// host queues a stage's begin, launch and end back to back, so one open slot suffices.
+bool stage_timed(const svdup_ctx* h, int stage) {
+  if (h->timing == SVDUP_TIMING_STAGES) return true;
+  return h->timing == SVDUP_TIMING_KERNELS &&
+         (stage == SVDUP_STAGE_P2M || stage == SVDUP_STAGE_M2L || stage == SVDUP_STAGE_OUT);
 }
 
-void stage_end(svdup_ctx* h) {
+void stage_begin(svdup_ctx* h, int stage, cudaStream_t st) {
+  if (!stage_timed(h, stage)) return;
+  h->open_stage = stage;
+  h->open_ev = take_event(h);
+  cudaEventRecord(h->open_ev, st);
+}
+
+void stage_end(svdup_ctx* h, cudaStream_t st) {
   if (!h->timing || h->open_stage < 0) return;
   cudaEvent_t b = take_event(h);
-  cudaEventRecord(b, h->stream);
+  cudaEventRecord(b, st);
   if (h->nrec + 1 > h->caprec) {
     h->caprec = h->caprec ? 2 * h->caprec : 256;
     h->recs = (TimerRec*)realloc(h->recs, h->caprec * sizeof(TimerRec));
@@ -436,24 +452,24 @@ void queue_solve(svdup_ctx* h, cudaStream_t st, Eig e, bool pairs = false,
 void queue_product(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, double* X, long long ldx,
                    double* Xs, OutMap om, int mode) {
   int dense = use_dense(h, e.N, mode) ? 1 : 0;
-  stage_begin(h, SVDUP_STAGE_GATHER);
+  stage_begin(h, SVDUP_STAGE_GATHER, st);
   launch_rotate_columns(st, e, X, ldx, rows, f.rot, false, om);
   launch_gather_columns(st, e, X, ldx, rows, Xs, rows, om);
-  stage_end(h);
-  stage_begin(h, SVDUP_STAGE_SETUP);
+  stage_end(h, st);
+  stage_begin(h, SVDUP_STAGE_SETUP, st);
   launch_fmm_setup(st, e, f, dense);
-  stage_end(h);
+  stage_end(h, st);
   if (!dense) {
-    stage_begin(h, SVDUP_STAGE_P2M);
+    stage_begin(h, SVDUP_STAGE_P2M, st);
     launch_product_f64_stage(st, 0, e, f, rows, Xs, rows, om, dense);
-    stage_end(h);
-    stage_begin(h, SVDUP_STAGE_M2L);
+    stage_end(h, st);
+    stage_begin(h, SVDUP_STAGE_M2L, st);
     launch_product_f64_stage(st, 1, e, f, rows, Xs, rows, om, dense);
-    stage_end(h);
+    stage_end(h, st);
   }
-  stage_begin(h, SVDUP_STAGE_OUT);
+  stage_begin(h, SVDUP_STAGE_OUT, st);
   launch_product_f64_stage(st, 2, e, f, rows, Xs, rows, om, dense);
-  stage_end(h);
+  stage_end(h, st);
   if (h->timing) launch_flop_count(st, e, f, rows, dense, h->flops_dev);
 }
 
@@ -474,34 +490,34 @@ MixPlan mix_rows(MixPlan mp, int rows) {
 // X is FP64, or the FP32 intermediate when xf32.
 void mix_prepare(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, const void* X,
                  bool xf32, long long ldx) {
-  stage_begin(h, SVDUP_STAGE_GATHER);
+  stage_begin(h, SVDUP_STAGE_GATHER, st);
   launch_rotate_prepare(st, e, X, ldx, rows, f.rot, true, xf32);
-  stage_end(h);
+  stage_end(h, st);
 }
 
 void mix_xside(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, void* X,
                bool xf32, long long ldx, OutMap om, bool leaves) {
   mp = mix_rows(mp, rows);
   if (leaves) {
-    stage_begin(h, SVDUP_STAGE_SETUP);
+    stage_begin(h, SVDUP_STAGE_SETUP, st);
     launch_fmm_boxes(st, e, f, 0);
-    stage_end(h);
+    stage_end(h, st);
   }
-  stage_begin(h, SVDUP_STAGE_GATHER);
+  stage_begin(h, SVDUP_STAGE_GATHER, st);
   launch_rotate_apply(st, e, X, ldx, rows, f.rot, true, om, xf32);
   launch_mix_gather(st, e, X, xf32, ldx, rows, mp, om);
-  stage_end(h);
+  stage_end(h, st);
 }
 
 void mix_ops(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, int mode,
              bool leaves) {
   const int dense = use_dense(h, e.N, mode) ? 1 : 0;
   mp = mix_rows(mp, rows);
-  stage_begin(h, SVDUP_STAGE_SETUP);
+  stage_begin(h, SVDUP_STAGE_SETUP, st);
   if (leaves) launch_fmm_boxes(st, e, f, 0);
   launch_fmm_ops(st, e, f, 0);
   launch_mix_setup(st, e, f, mp, dense);
-  stage_end(h);
+  stage_end(h, st);
 }
 
 void mix_mma(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int rows, OutMap om,
@@ -509,16 +525,16 @@ void mix_mma(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int ro
   const int dense = use_dense(h, e.N, mode) ? 1 : 0;
   mp = mix_rows(mp, rows);
   if (!dense) {
-    stage_begin(h, SVDUP_STAGE_P2M);
+    stage_begin(h, SVDUP_STAGE_P2M, st);
     launch_mix_stage(st, 0, e, f, mp, om, dense, h->status);
-    stage_end(h);
-    stage_begin(h, SVDUP_STAGE_M2L);
+    stage_end(h, st);
+    stage_begin(h, SVDUP_STAGE_M2L, st);
     launch_mix_stage(st, 1, e, f, mp, om, dense, h->status);
-    stage_end(h);
+    stage_end(h, st);
   }
-  stage_begin(h, SVDUP_STAGE_OUT);
+  stage_begin(h, SVDUP_STAGE_OUT, st);
   launch_mix_stage(st, 2, e, f, mp, om, dense, h->status);
-  stage_end(h);
+  stage_end(h, st);
   if (h->timing) {
     launch_flop_count(st, e, f, rows, dense, h->flops_dev);
     launch_mix_flop_count(st, e, f, mix_rows(mp, rows), dense, h->flops_dev + 3);
@@ -787,8 +803,8 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
     free(h);
     return SVDUP_ENOMEM;
   }
-  if (cudaMalloc(&h->flops_dev, 6 * sizeof(double)) != cudaSuccess ||
-      cudaMemsetAsync(h->flops_dev, 0, 6 * sizeof(double), h->stream) != cudaSuccess) {
+  if (cudaMalloc(&h->flops_dev, kFlopSlots * sizeof(double)) != cudaSuccess ||
+      cudaMemsetAsync(h->flops_dev, 0, kFlopSlots * sizeof(double), h->stream) != cudaSuccess) {
     cudaFree(h->status);
     free(h);
     return SVDUP_ENOMEM;
@@ -824,7 +840,7 @@ int svdup_destroy(svdup_t h) {
 }
 
 int svdup_timing(svdup_t h, int enable) {
-  if (!h) return SVDUP_EINVAL;
+  if (!h || enable < 0 || enable > SVDUP_TIMING_KERNELS) return SVDUP_EINVAL;
   if (set_device(h)) return SVDUP_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
   // recycle outstanding records
@@ -837,9 +853,9 @@ int svdup_timing(svdup_t h, int enable) {
   }
   h->nrec = 0;
   for (int s = 0; s < SVDUP_NSTAGE; s++) { h->ms[s] = 0.0; h->cnt[s] = 0; }
-  h->timing = enable ? 1 : 0;
+  h->timing = enable;
   h->open_stage = -1;
-  if (cudaMemsetAsync(h->flops_dev, 0, 6 * sizeof(double), h->stream) != cudaSuccess)
+  if (cudaMemsetAsync(h->flops_dev, 0, kFlopSlots * sizeof(double), h->stream) != cudaSuccess)
     return SVDUP_ECUDA;
   return SVDUP_OK;
 }
@@ -848,8 +864,8 @@ int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, do
                       int nstage) {
   if (!h || nstage < 0 || nstage > SVDUP_NSTAGE) return SVDUP_EINVAL;
   if (set_device(h)) return SVDUP_ECUDA;
-  double fl[6] = {0, 0, 0, 0, 0, 0};
-  if (cudaMemcpyAsync(fl, h->flops_dev, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
+  double fl[kFlopSlots] = {};
+  if (cudaMemcpyAsync(fl, h->flops_dev, kFlopSlots * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
       cudaSuccess)
     return SVDUP_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
@@ -871,6 +887,21 @@ int svdup_timing_read(svdup_t h, double* ms, long long* count, double* flops, do
     int slot = s == SVDUP_STAGE_P2M ? 0 : s == SVDUP_STAGE_M2L ? 1 : s == SVDUP_STAGE_OUT ? 2 : -1;
     if (flops) flops[s] = slot >= 0 ? fl[slot] : 0.0;
     if (mma_flops) mma_flops[s] = slot >= 0 ? fl[3 + slot] : 0.0;
+  }
+  return SVDUP_OK;
+}
+
+int svdup_timing_read_alg(svdup_t h, double* alg_flops, int nstage) {
+  if (!h || nstage < 0 || nstage > SVDUP_NSTAGE) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  double fl[kFlopSlots] = {};
+  if (cudaMemcpyAsync(fl, h->flops_dev, kFlopSlots * sizeof(double), cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess)
+    return SVDUP_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SVDUP_ECUDA;
+  for (int s = 0; s < nstage; s++) {
+    int slot = s == SVDUP_STAGE_P2M ? 0 : s == SVDUP_STAGE_M2L ? 1 : s == SVDUP_STAGE_OUT ? 2 : -1;
+    if (alg_flops) alg_flops[s] = slot >= 0 ? fl[6 + slot] : 0.0;
   }
   return SVDUP_OK;
 }
@@ -927,9 +958,9 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   cudaStream_t st = h->stream;
 
   // STEP 1 (rewritten): p = U^T a, q = V^T b, alpha, beta
-  stage_begin(h, SVDUP_STAGE_GEMV);
+  stage_begin(h, SVDUP_STAGE_GEMV, h->stream);
   launch_gemv_pq(st, m, n, U, ldu, V, ldv, a, b, u.p, u.q, u.ab, u.abf, u.abe);
-  stage_end(h);
+  stage_end(h, h->stream);
   // Streams: the left-hand solves (E1, E2) on `left`, the right-hand ones (E3, E4) on
   // `side`, the products with U on prod[0] and with V on prod[1]; the handle's stream
   // forks them after STEP 1 and joins them before the signs are applied and STEP 8.
@@ -938,7 +969,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   // its columns unsigned; the sign pairing (which hands the left vectors' sums to the
   // right) runs meanwhile, and its signs are applied to V after the join.  With stage
   // timing on, everything runs on one stream.
-  const bool multi = !h->timing && h->side;
+  const bool multi = h->timing != SVDUP_TIMING_STAGES && h->side;
   cudaStream_t sR = multi ? h->side : st;
   cudaStream_t sL = multi ? h->left : st;
   cudaStream_t pU = multi ? h->prod[0] : st;
@@ -1015,7 +1046,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     if (!wait(pU, h->ev[1])) return SVDUP_ECUDA;
     mix_mma(h, pU, u.E2, u.FL2, u.ML2, m, om2, mode);
   } else {
-    stage_begin(h, SVDUP_STAGE_SOLVE);
+    stage_begin(h, SVDUP_STAGE_SOLVE, h->stream);
     // STEPs 3, 6: first right solve; STEP 7: second right solve
     launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
     queue_solve(h, sR, u.E3);
@@ -1034,7 +1065,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     launch_fill_second(sL, u.E2, u.E1.lam, u.zsec2);
     queue_solve(h, sL, u.E2, mixed);
     launch_norms(sL, u.E2, nullptr, nullptr, mixed);
-    stage_end(h);
+    stage_end(h, h->stream);
     // products: U -> W -> U (descending), V -> W -> V (descending; the signs follow)
     if (mixed) {
       queue_product_mixed(h, pU, u.E1, u.FL, u.ML, m, U, false, ldu, om1, mode);
@@ -1053,7 +1084,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   }
   // sign pairing of right vectors with left vectors (before S is overwritten); in the
   // mixed mode its sums run on FP32 pairs (only the signs are used)
-  stage_begin(h, SVDUP_STAGE_SIGN);
+  stage_begin(h, SVDUP_STAGE_SIGN, h->stream);
   launch_fill_ones(sL, m, u.ones);
   launch_apply_q(sL, u.E2, u.ones, u.work, u.g1, mixed);
   launch_apply_q(sL, u.E1, u.g1, u.work, u.g, mixed);
@@ -1063,7 +1094,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   launch_apply_qt(sR, u.E3, u.yv, u.ysortR, u.h1, mixed, true);
   launch_apply_qt(sR, u.E4, u.h1, u.ysortR, u.h, mixed, true);
   launch_sign_finish(sR, m, n, u.h, u.sign);
-  stage_end(h);
+  stage_end(h, h->stream);
   // join before the signs are applied to V and before STEP 8 (it overwrites S, which
   // the right-hand fill and the signs read)
   if (!hand(h->ev[4], pU, st) || !hand(h->ev[5], pV, st) || !hand(h->ev_join, sR, st) ||

@@ -295,7 +295,11 @@ void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ld
 void launch_fmm_boxes(cudaStream_t st, Eig e, FmmPlan f, int dense);
 void launch_fmm_ops(cudaStream_t st, Eig e, FmmPlan f, int dense);
 void launch_fmm_setup(cudaStream_t st, Eig e, FmmPlan f, int dense);
-// adds the useful flops of one product's P2M, M2L and output stages to acc[0..2]
+// Flop accumulators of a handle's timers: useful flops of P2M, M2L, OUT (0..2), executed
+// tensor-core flops (3..5), algorithmic flops (6..8).
+constexpr int kFlopSlots = 9;
+// adds the useful flops of one product's P2M, M2L and output stages to acc[0..2] and
+// their algorithmic flops to acc[6..8]
 void launch_flop_count(cudaStream_t st, Eig e, FmmPlan f, int rows, int dense, double* acc);
 // stage 0 = P2M, 1 = M2L, 2 = L2P + near field (dense: the whole product)
 void launch_product_f64_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, int rows,

@@ -742,6 +742,7 @@ __global__ void k_flop_count(Eig e, FmmPlan f, int rows, int dense, double* acc)
   const double R = (double)rows;
   if (dense) {
     acc[2] += 2.0 * R * (double)k * (double)k;
+    acc[8] += 2.0 * R * (double)k * (double)k;
     return;
   }
   const int Ls = f.L[0], Lt = f.L[1], p = f.p, s = f.s, P = f.L[2];
@@ -760,6 +761,14 @@ __global__ void k_flop_count(Eig e, FmmPlan f, int rows, int dense, double* acc)
   acc[0] += p2m;
   acc[1] += m2l;
   acc[2] += out;
+  // App. D's operation count for N = k points with leaves of s = 2p: STEPs 5-6 (the
+  // far-field expansions and their bottom-up shifts) 2 N p multiply-adds, STEPs 7-8 (the
+  // local expansions and translations) 5 N p, STEPs 9-10 (evaluation and the near field)
+  // 7 N p; 14 N p in all, for each of the `rows` right-hand sides.
+  const double np = R * (double)k * p;
+  acc[6] += 4.0 * np;
+  acc[7] += 10.0 * np;
+  acc[8] += 14.0 * np;
 }
 
 void launch_flop_count(cudaStream_t st, Eig e, FmmPlan f, int rows, int dense, double* acc) {

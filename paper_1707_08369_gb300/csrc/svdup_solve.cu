@@ -1605,9 +1605,11 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
 }
 
 // The stand-alone secular entry point: d strictly ascending, z nonzero; the problem
-// is brought to the rho > 0 orientation first.
+// is brought to the rho > 0 orientation first.  A NaN or infinity in d or z latches
+// SVDUP_ENONFINITE.
 __global__ void k_secular_prep(int k, const double* __restrict__ d, const double* __restrict__ z,
-                               const double* rhop, double* dc, double* z2c, double* dk, int* kp) {
+                               const double* rhop, double* dc, double* z2c, double* dk, int* kp,
+                               int* status) {
   const double rho = rhop[0];
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) kp[0] = k;
@@ -1620,11 +1622,13 @@ __global__ void k_secular_prep(int k, const double* __restrict__ d, const double
     dc[t] = -d[k - 1 - t];
     z2c[t] = z[k - 1 - t] * z[k - 1 - t];
   }
+  if (!isfinite(d[t]) || !isfinite(z[t])) latch(status, SVDUP_ENONFINITE);
 }
 
 void launch_secular_direct(cudaStream_t st, Eig e, int k, const double* d, const double* z,
                            int* status, int maxit) {
-  k_secular_prep<<<(k + 255) / 256, 256, 0, st>>>(k, d, z, e.rhop, e.dc, e.z2c, e.dk, e.kp);
+  k_secular_prep<<<(k + 255) / 256, 256, 0, st>>>(k, d, z, e.rhop, e.dc, e.z2c, e.dk, e.kp,
+                                                  status);
   SVDUP_COUNT_LAUNCH();
   launch_secular(st, e, status, maxit);
 }

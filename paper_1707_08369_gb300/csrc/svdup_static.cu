@@ -19,9 +19,6 @@
 
 #include "svdup_internal.cuh"
 
-namespace svdup {
-}  // namespace svdup
-
 using namespace svdup;
 
 namespace {
@@ -65,9 +62,10 @@ int scratch_on_current_device(double** out) {
 
 // rho, k and the rho > 0 orientation of the problem (the solver's input form): for
 // rho < 0 the poles are reflected, d -> -d in reversed order.
+// A NaN or infinity in d or z latches SVDUP_ENONFINITE in the caller's info word.
 __global__ void k_static_prep(int k, const double* __restrict__ d, const double* __restrict__ z,
                               double rho, double* rhop, int* kp, double* dc, double* z2c,
-                              double* dk) {
+                              double* dk, int* status) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) {
     rhop[0] = rho;
@@ -78,6 +76,7 @@ __global__ void k_static_prep(int k, const double* __restrict__ d, const double*
   const int s = rho > 0.0 ? t : k - 1 - t;
   dc[t] = rho > 0.0 ? d[s] : -d[s];
   z2c[t] = z[s] * z[s];
+  if (!isfinite(d[s]) || !isfinite(z[s])) latch(status, SVDUP_ENONFINITE);
 }
 
 }  // namespace
@@ -110,7 +109,8 @@ extern "C" int svdup_secular_static(void* stream, int k, const double* d, const 
     cudaGetLastError();
     return SVDUP_ECUDA;
   }
-  k_static_prep<<<(k + 255) / 256, 256, 0, st>>>(k, d, z, rho, e.rhop, e.kp, e.dc, e.z2c, e.dk);
+  k_static_prep<<<(k + 255) / 256, 256, 0, st>>>(k, d, z, rho, e.rhop, e.kp, e.dc, e.z2c, e.dk,
+                                                 info);
   SVDUP_COUNT_LAUNCH();
   launch_secular(st, e, info, 64);
   cudaError_t err = cudaGetLastError();

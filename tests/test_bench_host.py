@@ -178,3 +178,23 @@ def test_fp64_peak_from_unit_counts():
     # 152 SMs x 2 DFMA per SM per clock x 2 flops at 2070 MHz
     assert abs(bench.fp64_peak_tflops(2070.0) - 1.25856) < 1e-9
     assert bench.fp64_peak_tflops(None) == bench.fp64_peak_tflops(2070.0)
+
+
+def test_roofline_uses_the_algorithmic_count_of_the_dominant_kernel():
+    """frac = App. D's algorithmic flops of the dominant kernel's launches over their
+    summed event time and the peak; the executed and useful figures ride beside it."""
+    # stage: (ms, launches, useful flops, executed flops, algorithmic flops)
+    kern = {"p2m": (0.5, 4, 1e9, 6e9, 4e9), "m2l": (0.25, 4, 2e9, 12e9, 1e10),
+            "out": (2.0, 4, 3e11, 1.8e12, 1.4e10)}
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+    r = bench.roofline_of(kern, 1, {"sm_mhz": 2070.0}, peaks, "fallback", 8192, "bf16x3")
+    assert r["kernel"] == "k_umma<OUT>" and r["bound"] == "tensor" and r["launches"] == 4
+    per_launch_s = 2.0 / 4 / 1e3
+    assert abs(r["achieved"] - 1.4e10 / 4 / per_launch_s / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1700.0) < 1e-12
+    assert abs(r["executed_tflops"] - 1.8e12 / 4 / per_launch_s / 1e12) < 1e-9
+    assert "fallback" in r["peak_source"]
+    r64 = bench.roofline_of(kern, 0, {"sm_mhz": 1035.0}, peaks, "measured", 8192, "fp64")
+    assert r64["kernel"] == "k_gemm_f64<OUT>" and r64["bound"] == "alu"
+    assert abs(r64["peak"] - bench.fp64_peak_tflops(1035.0)) < 1e-12
+    assert abs(r64["frac"] - r64["achieved"] / r64["peak"]) < 1e-12

@@ -147,6 +147,44 @@ def test_cauchy_product_vs_oracle(sv, hnd, orc, rows, N, mode_dense, seed, sprea
     assert np.abs(Y_g - Y_o).max() <= 1e-10
 
 
+def test_far_field_meets_eps_on_the_closest_admissible_pair(sv, orc):
+    """The far field at its worst geometry: a source leaf and a target leaf one radius
+    apart (the closest pair the flat partition admits), with the poles and the roots
+    crowded at the near ends.  X is zero outside the source leaf, so the target leaf's
+    columns are that one far-field interaction alone.  The expansion order for eps must
+    keep its error within eps of the pair's scale, inv_j * sum_t |x_t zhat_t| / dist, for
+    dist the pair's shortest distance (App. D STEP 1's accuracy, with the order taken
+    from the 4 (2 + sqrt 3)^-p rate of this gap; p = log5(1/eps) misses it by about 20x
+    here)."""
+    h = sv.Handle(0)
+    try:
+        h.set_tuning(sv.FP64, 0, 1 << 30)  # far field from the smallest N, leaves of 64
+        t = np.arange(64)
+        d = np.concatenate([2 - 2 * (1 - t / 63) ** 2,      # leaf 0: [0, 2], crowded at 2
+                            np.linspace(2.2, 2.8, 64),       # leaf 1
+                            3 + 2 * (t / 63) ** 2])          # leaf 2: [3, 5], crowded at 3
+        g = np.random.default_rng(11)
+        z = 0.05 * (1 + g.uniform(0, 1, 192)) * np.where(g.uniform(0, 1, 192) < 0.5, -1, 1)
+        rho = 1.0
+        X = g.standard_normal((8, 192))
+        X[:, 64:] = 0.0
+        oc = orc.rank_one_compact(d, z, rho)
+        assert oc["k"] == 192  # nothing deflates
+        mu = oc["dk"][oc["org"]] + oc["tau"]
+        tg = np.arange(128, 191)  # target leaf 2 (roots between its poles)
+        lam_o, Y_o = orc.rank_one_update_z(X, d, z, rho)
+        for eps in (1e-12, 1e-8):
+            lam_g, Y_g = h.cauchy_product(devF(X), dev(d), dev(z), rho, eps=eps, mode=sv.FP64)
+            Y_g = Y_g.cpu().numpy()
+            q = np.abs(X[:, :64] * oc["zhat"][:64]).sum(axis=1)
+            scale = q[:, None] * oc["inv_norm"][tg][None, :] / (mu[128] - d[63])
+            err = np.abs(Y_g[:, tg] - Y_o[:, tg])
+            assert (err <= eps * scale).all(), (eps, (err / scale).max())
+            assert np.abs(Y_g - Y_o).max() <= max(1e-10, 10 * eps)
+    finally:
+        h.close()
+
+
 # ------------------------------------------------------------------ full update
 def _run_update(sv, hnd, U, S, V, a, b, eps=1e-12, mode=0):
     tU, tS, tV = devF(U), dev(S), devF(V)
@@ -355,6 +393,20 @@ def test_nonfinite_input_reports_status(sv, hnd):
     # the handle stays usable
     a[3] = 0.5
     _run_update(sv, hnd, U, S, Vh.T, a, b)
+
+
+def test_secular_nonfinite_input_reports_status(sv, hnd):
+    """A NaN in z of the stand-alone secular entry point is reported from the device
+    (SVDUP_ENONFINITE at the sync), not returned as roots."""
+    g = np.random.default_rng(21)
+    d = np.sort(g.uniform(0, 1, 300))
+    z = g.standard_normal(300)
+    z[100] = np.nan
+    with pytest.raises(sv.SvdupError) as ei:
+        hnd.secular(dev(d), dev(z), 1.5)
+    assert ei.value.code == sv.ENONFINITE
+    z[100] = 0.25
+    hnd.secular(dev(d), dev(z), 1.5)
 
 
 def test_unsorted_singular_values(sv, hnd):

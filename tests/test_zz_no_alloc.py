@@ -6,8 +6,10 @@ CUDA allocator, a latency-critical loop where cudaMalloc would synchronise the
 device): its scratch is a fixed array inside the library.  This file checks, through
 the C ABI, that two calls in a row (a larger problem, then a smaller one, so the second
 runs over the first one's leftover scratch) give the roots of the handle-based
-svdup_secular within the root-accuracy bound the secular tests use, and that sizes
-beyond the array's limit are refused.  It is named to be collected last."""
+svdup_secular within the root-accuracy bound the secular tests use; that a call
+leaves the device's free memory unchanged (the property the entry point exists for);
+that a device error (a NaN in z) reaches the caller's info word; and that sizes beyond
+the array's limit are refused.  It is named to be collected last."""
 import ctypes
 
 import numpy as np
@@ -93,3 +95,42 @@ def test_static_secular_rejects_oversize(sv):
     rc = lib.svdup_secular_static(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), k,
                                   p(buf), p(buf), 1.0, p(ibuf), p(buf), p(ibuf))
     assert rc == sv.EINVAL
+
+
+def test_static_secular_allocates_nothing(sv):
+    """After a first call (which looks up the array's address), a call changes nothing
+    in the device's free memory: every buffer it touches is the caller's or the
+    library's fixed array."""
+    lib = sv.load()
+    d, z, rho = _problem(3000, 1, False, 13)
+    td, tz = torch.from_numpy(d).cuda(), torch.from_numpy(z).cuda()
+    org = torch.empty(d.size, dtype=torch.int32, device="cuda")
+    tau = torch.empty(d.size, dtype=torch.float64, device="cuda")
+    info = torch.empty(1, dtype=torch.int32, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    def call():
+        rc = lib.svdup_secular_static(st, d.size, p(td), p(tz), float(rho), p(org), p(tau), p(info))
+        assert rc == sv.OK, sv.error_string(rc)
+        torch.cuda.synchronize()
+
+    call()
+    free0, _ = torch.cuda.mem_get_info()
+    call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert int(info.item()) == sv.OK
+
+
+def test_static_secular_reports_nonfinite_input(sv):
+    """A NaN in z is found on the device: the call itself succeeds, and the caller's
+    info word holds SVDUP_ENONFINITE once the stream has run."""
+    d, z, rho = _problem(300, 1, False, 14)
+    z[17] = np.nan
+    org, tau, info = _static_call(sv, d, z, rho)
+    assert info == sv.ENONFINITE
+    # a clean call after it starts from a cleared info word
+    d, z, rho = _problem(300, -1, False, 15)
+    org, tau, info = _static_call(sv, d, z, rho)
+    assert info == sv.OK
