@@ -35,8 +35,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-MODES = {"fp64": 0, "bf16x3": 1}
-DTYPES = {"fp64": "f64", "bf16x3": "bf16x3"}  # bf16x3: 3-term BF16 split products, FP32 accumulation
+MODES = {"fp64": 0, "bf16x3": 1, "fp16x2": 2}
+# bf16x3: 3-term BF16 split products; fp16x2: 2-term FP16 split at a power-of-two scale per
+# tile; both with FP32 accumulation and FP64 roots
+DTYPES = {"fp64": "f64", "bf16x3": "bf16x3", "fp16x2": "fp16x2"}
 METRIC = "rank-1 SVD updates/s at n=8192 (mixed vs FP64, same GPU) + p99 latency"
 
 
@@ -59,6 +61,8 @@ def parse():
     ap.add_argument("--mode", default="bf16x3", choices=list(MODES))
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-alt", action="store_true",
+                    help="skip the other split form's sub-line (fp16x2 beside bf16x3 and back)")
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-cols", type=int, default=64)
@@ -416,17 +420,18 @@ def replica_rate(units_per_rank, ms, ws):
     return ws * units_per_rank / (ms / 1e3)
 
 
-def accuracy_report(sv, h, stream, upload, ta, tb, eps, mode, dev):
-    """One update from the same inputs in the FP64 form and in `mode`; the mixed form's
-    errors against the FP64 form, and invariants of each output measured with random
-    probes x (n x 4, FP64 on the device): ||U^T U x - x||, ||V^T V x - x|| and the
-    reconstruction ||Ahat Vhat x - Uhat Shat x|| / (sigma_max ||x||) with
-    Ahat = U S V^T + a b^T applied factor by factor."""
+def accuracy_report(sv, h, stream, upload, ta, tb, eps, modes, dev):
+    """One update from the same inputs in the FP64 form and in each mode of `modes`;
+    each mixed form's errors against the FP64 form, and invariants of each output
+    measured with random probes x (n x 4, FP64 on the device): ||U^T U x - x||,
+    ||V^T V x - x|| and the reconstruction ||Ahat Vhat x - Uhat Shat x|| / (sigma_max ||x||)
+    with Ahat = U S V^T + a b^T applied factor by factor."""
     import torch
     outs = {}
+    names = {v: k for k, v in MODES.items()}
     with torch.cuda.stream(stream):
         U0, S0, V0 = upload()
-        for m in sorted({0, mode}):
+        for m in sorted({0, *modes}):
             tU, tS, tV = upload()
             h.update(tU, tS, tV, ta[0], tb[0], eps=eps, mode=m, check=True)
             outs[m] = (tU, tS, tV)
@@ -435,11 +440,11 @@ def accuracy_report(sv, h, stream, upload, ta, tb, eps, mode, dev):
         gen.manual_seed(170708369)
         n, m_ = V0.shape[0], U0.shape[0]
         x = torch.randn(m_, 4, dtype=torch.float64, device=dev, generator=gen)
+        y = torch.randn(n, 4, dtype=torch.float64, device=dev, generator=gen)
         rep = {}
         for mm, (Un, Sn, Vn) in outs.items():
             Vm = Vn[:, :m_]
             ortU = float(torch.linalg.norm(Un.t() @ (Un @ x) - x) / torch.linalg.norm(x))
-            y = torch.randn(n, 4, dtype=torch.float64, device=dev, generator=gen)
             ortV = float(torch.linalg.norm(Vn.t() @ (Vn @ y) - y) / torch.linalg.norm(y))
             w = Vm @ x
             lhs = U0 @ (S0[:, None] * (V0[:, :m_].t() @ w)) + ta[0][:, None] * (tb[0][None, :] @ w)
@@ -447,14 +452,15 @@ def accuracy_report(sv, h, stream, upload, ta, tb, eps, mode, dev):
             rep[mm] = {"orth_U": ortU, "orth_V": ortV, "recon": rec}
         res = {"probe": "4 Gaussian probe vectors; norms are 2-norms of the probe block",
                "fp64": rep[0]}
-        if mode != 0:
-            U64, S64, V64 = outs[0]
-            Um, Sm, Vm2 = outs[mode]
-            res["mixed"] = rep[mode]
-            res["mixed_vs_fp64"] = {
+        U64, S64, V64 = outs[0]
+        for mm in modes:
+            if mm == 0:
+                continue
+            Um, Sm, Vm2 = outs[mm]
+            res[names[mm]] = dict(rep[mm], vs_fp64={
                 "sigma_max_rel": float((Sm - S64).abs().max() / S64[0]),
                 "U_max_abs": float((Um - U64).abs().max()),
-                "V_max_abs": float((Vm2[:, :m_] - V64[:, :m_]).abs().max())}
+                "V_max_abs": float((Vm2[:, :m_] - V64[:, :m_]).abs().max())})
     del outs
     return res
 
@@ -677,8 +683,32 @@ def main():
         del tU, tV
         tU, tS, tV = upload()
 
+    # the other split form on the same GPU and workload: its own timed region
+    alt = None
+    alt_name = {"bf16x3": "fp16x2", "fp16x2": "bf16x3"}.get(args.mode)
+    if alt_name and not args.no_alt:
+        del tU, tV
+        tU, tS, tV = upload()
+        w2 = min(args.warmup, 3)
+        k2 = min(args.steps, steps_total - w2)
+        lat2, tot2, _, _, clk2, kern2 = timed_updates(
+            sv, h, stream, tU, tS, tV, ta, tb, MODES[alt_name], args.eps, w2, k2, ws, dev,
+            ClockSampler(local), stage_steps=0)
+        v2 = ws * len(lat2) / (tot2 / 1e3)
+        alt = {"mode": alt_name, "value": v2, "unit": "updates/s", "steps": len(lat2),
+               "warmup": w2, "ms_per_step": tot2 / len(lat2),
+               "latency_ms": {"p50": float(np.percentile(lat2, 50)),
+                              "p99": float(np.percentile(lat2, 99))},
+               "roofline": roofline_of(kern2, MODES[alt_name], clk2, peaks, peak_src, n, alt_name),
+               "clocks": clk2}
+        if fp64:
+            alt["over_fp64"] = v2 / fp64["value"]
+        del tU, tV
+        tU, tS, tV = upload()
+
+    acc_modes = [mode] + ([MODES[alt_name]] if alt else [])
     accuracy = None if args.no_accuracy else accuracy_report(
-        sv, h, stream, upload, ta, tb, args.eps, mode, dev)
+        sv, h, stream, upload, ta, tb, args.eps, acc_modes, dev)
     batched = None
     if not args.no_batched and ws == 1:
         batched = batched_form(sv, dev, mode, args.eps, args.batch_count, 5, 2, 16)
@@ -709,6 +739,7 @@ def main():
                 "config": bench_config(args, ws),
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                 "fp64": fp64,
+                (alt_name or "alt"): alt,
                 "accuracy": accuracy,
                 "batched": batched,
                 "serving": serving,

@@ -45,7 +45,8 @@ extern "C" {
 /* ---- update modes (svdup_update's mode argument) -------------------------- */
 #define SVDUP_FP64 0          /* every step in FP64 */
 #define SVDUP_MIXED_BF16X3 1  /* products in 3-term BF16 split, FP32 accumulation */
-#define SVDUP_MIXED_FP16X2 2  /* reserved: 2-term scaled FP16 split; not built, SVDUP_EINVAL */
+#define SVDUP_MIXED_FP16X2 2  /* products in 2-term FP16 split, one power-of-two scale per
+                                 tile, FP32 accumulation (about 2^-22 per operand) */
 #define SVDUP_MODE_MASK 0xff
 #define SVDUP_DENSE 0x100     /* flag: force the dense Cauchy product (no far field) */
 #define SVDUP_REFINE 0x200    /* reserved flag: an orthogonalising refinement step of the
@@ -136,7 +137,8 @@ int svdup_timing_read_alg(svdup_t h, double* alg_flops, int nstage);
  *                       eps = 1e-12, clamped to [4, 32].  (App. D STEP 1's
  *                       p = log5(1/eps) is the rate of the paper's interaction lists,
  *                       whose leaves are two radii apart.)  The mixed modes use p = 16.
- *   mode                SVDUP_FP64 or SVDUP_MIXED_BF16X3, optionally | SVDUP_DENSE;
+ *   mode                SVDUP_FP64, SVDUP_MIXED_BF16X3 or SVDUP_MIXED_FP16X2, optionally
+ *                       | SVDUP_DENSE;
  *                       any other value returns SVDUP_EINVAL.
  * The signs of Vhat's columns are chosen so that u_j^T Ahat v_j >= 0.
  * Requires 1 <= m <= n.  U, V are assumed orthogonal (as the paper does, App. A).

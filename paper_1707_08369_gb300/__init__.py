@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsvdup.so")
 
 OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE, ECUDA, EORDER, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6, 7
-FP64, MIXED_BF16X3, MIXED_FP16X2 = 0, 1, 2  # MIXED_FP16X2: reserved, rejected (EINVAL)
+FP64, MIXED_BF16X3, MIXED_FP16X2 = 0, 1, 2  # update modes (split BF16 x3, scaled FP16 x2)
 DENSE, REFINE = 0x100, 0x200                 # REFINE: reserved, rejected (EINVAL)
 TIMING_STAGES, TIMING_KERNELS = 1, 2      # svdup_timing modes
 

@@ -259,6 +259,13 @@ MixPlan make_mix(Arena& ar, int rows, const FmmPlan& f) {
   mp.near = ar.take<int>((L + 1) * L);
   mp.noff = ar.take<int>(L + 2);
   mp.order = ar.take<int>(L + 1);
+  mp.scX = ar.take<signed char>((size_t)mp.rt * mp.kx);
+  mp.scPhi = ar.take<signed char>((size_t)mp.rt * mp.kphi);
+  mp.scPsi = ar.take<signed char>((size_t)mp.rt * (L + 1));
+  mp.scS = ar.take<signed char>(L * hs);
+  mp.scT = ar.take<signed char>((size_t)mp.ntT * mp.kphi);
+  mp.scL = ar.take<signed char>(L + 1);
+  mp.scC = ar.take<signed char>((L + 1) * L * hs);
   return mp;
 }
 
@@ -275,14 +282,23 @@ MixPlan make_mix_shared(Arena& ar, const FmmPlan& f, const MixPlan& sh) {
   mp.near = ar.take<int>((L + 1) * L);
   mp.noff = ar.take<int>(L + 2);
   mp.order = ar.take<int>(L + 1);
+  mp.scS = ar.take<signed char>(L * hs);
+  mp.scT = ar.take<signed char>((size_t)mp.ntT * mp.kphi);
+  mp.scL = ar.take<signed char>(L + 1);
+  mp.scC = ar.take<signed char>((L + 1) * L * hs);
   return mp;
 }
 
-bool is_mixed(int mode) { return (mode & SVDUP_MODE_MASK) == SVDUP_MIXED_BF16X3; }
+bool is_mixed(int mode) {
+  const int prec = mode & SVDUP_MODE_MASK;
+  return prec == SVDUP_MIXED_BF16X3 || prec == SVDUP_MIXED_FP16X2;
+}
+
+bool is_fp16(int mode) { return (mode & SVDUP_MODE_MASK) == SVDUP_MIXED_FP16X2; }
 
 bool mode_ok(int mode) {
   int prec = mode & SVDUP_MODE_MASK;
-  if (prec != SVDUP_FP64 && prec != SVDUP_MIXED_BF16X3) return false;
+  if (prec != SVDUP_FP64 && prec != SVDUP_MIXED_BF16X3 && prec != SVDUP_MIXED_FP16X2) return false;
   return (mode & ~(SVDUP_MODE_MASK | SVDUP_DENSE)) == 0;
 }
 
@@ -331,7 +347,8 @@ struct UpdateWs {
   MixPlan ML, MR, ML2, MR2;
 };
 
-UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed) {
+UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed,
+                       bool fp16 = false) {
   UpdateWs u;
   u.p = ar.take<double>(m);
   u.q = ar.take<double>(n);
@@ -377,6 +394,7 @@ UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed
     u.FR2 = make_plan_shared(ar, n, eps, leaf, mixed, u.FR);
     u.ML2 = make_mix_shared(ar, u.FL2, u.ML);
     u.MR2 = make_mix_shared(ar, u.FR2, u.MR);
+    u.ML.fp16 = u.MR.fp16 = u.ML2.fp16 = u.MR2.fp16 = fp16 ? 1 : 0;
   }
   return u;
 }
@@ -954,7 +972,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   int rc = ensure_ws(h, meas.off);
   if (rc) return rc;
   Arena ar = {h->ws, 0};
-  UpdateWs u = layout_update(ar, m, n, eps, leaf, mixed);
+  UpdateWs u = layout_update(ar, m, n, eps, leaf, mixed, is_fp16(mode));
   cudaStream_t st = h->stream;
 
   // STEP 1 (rewritten): p = U^T a, q = V^T b, alpha, beta
@@ -1224,7 +1242,10 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
     *Xw = ar.take<double>((size_t)rows * N);
     *Xs = mixed ? nullptr : ar.take<double>((size_t)rows * N);
     *f = make_plan(ar, N, rows, eps, leaf_size(h, N, mode), mixed);
-    if (mixed) *mp = make_mix(ar, rows, *f);
+    if (mixed) {
+      *mp = make_mix(ar, rows, *f);
+      mp->fp16 = is_fp16(mode) ? 1 : 0;
+    }
   };
   Eig e;
   double *Xw, *Xs, *rhod;

@@ -229,6 +229,12 @@ struct MixPlan {
   int* noff;            // exclusive prefix sum of nnear
   int* order;           // target leaves by descending nnear (the output stage's job order)
   const int* fL;        // the plan's leaf counts and offsets (FmmPlan::L)
+  // FP16 2-term split (SVDUP_MIXED_FP16X2): every tile holds two FP16 planes (hi, lo) of
+  // its values times 2^sc, sc one power of two per tile, in the same geometry as the
+  // three BF16 planes (the third plane unused); the scales, one byte per tile, parallel
+  // the tile arrays.
+  int fp16;
+  signed char *scX, *scPhi, *scPsi, *scS, *scT, *scL, *scC;
 };
 
 constexpr int kMixP = 16;

@@ -32,6 +32,7 @@
 // on an mbarrier gives up after about one second of global time, latches
 // SVDUP_ETIMEOUT and lets the CTA finish.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -154,6 +155,87 @@ __device__ __forceinline__ void store_split8_f(unsigned char* tile, uint32_t pla
   store_split8(tile, plane, off, h, m, l);
 }
 
+
+// ---------------------------------------------------------------------------
+// FP16 2-term split (SVDUP_MIXED_FP16X2): a tile's values v are stored as
+// v 2^sc = hi + lo, two FP16 numbers (round to nearest; the first remainder is exact in
+// FP32), with one power of two 2^sc per tile that puts the tile's largest magnitude in
+// [2^14, 2^15).  hi + lo carries 22 significant bits down to 2^-3 of that magnitude and
+// an absolute error below 2^-39 of it beyond.  Values are collected as FP32 in shared
+// memory (row r, K position k at r * KB + k), then the block finds the scale and writes
+// the two planes.
+// ---------------------------------------------------------------------------
+constexpr int kScMax = 100;  // scales are clamped to [-100, 100] (one signed byte)
+
+__device__ __forceinline__ void split2h(float x, uint16_t& h, uint16_t& l) {
+  const __half bh = __float2half_rn(x);
+  const float r = x - __half2float(bh);
+  h = __half_as_ushort(bh);
+  l = __half_as_ushort(__float2half_rn(r));
+}
+
+// Largest |v| over the block (every thread passes its partial maximum).
+__device__ float block_max(float v) {
+  __shared__ float wmax[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) wmax[w] = v;
+  __syncthreads();
+  float m = 0.0f;
+  for (int i = 0; i < nw; i++) m = fmaxf(m, wmax[i]);
+  return m;
+}
+
+// The scale of a tile whose largest magnitude is m (0 for an empty or non-finite tile).
+__device__ __forceinline__ int fp16_scale(float m) {
+  if (!(m > 0.0f) || !isfinite(m)) return 0;
+  const int e = ((__float_as_int(m) >> 23) & 0xff) - 127;  // m in [2^e, 2^(e+1))
+  return max(-kScMax, min(kScMax, 14 - e));
+}
+
+// Tile layouts: a 64-K tile (two K halves of three planes each, t64_off) or a 16-K tile
+// (three planes of R x 16, cl_off).
+enum { TL_K64 = 0, TL_K16 = 1 };
+
+// Splits the R x KB FP32 values in shared memory `v` into the FP16 planes of `tile` and
+// stores the tile's scale; every thread of the block calls it.
+__device__ void finish_tile16(unsigned char* tile, const float* v, int R, int KB, int layout,
+                              signed char* sc_out) {
+  float m = 0.0f;
+  for (int i = threadIdx.x; i < R * KB; i += blockDim.x) m = fmaxf(m, fabsf(v[i]));
+  const int sc = fp16_scale(block_max(m));
+  const float f = pow2f(sc);
+  if (threadIdx.x == 0) *sc_out = (signed char)sc;
+  const uint32_t plane = layout == TL_K64 ? half_plane(R) : (uint32_t)R * KB * 2;
+  for (int it = threadIdx.x; it < R * (KB / 8); it += blockDim.x) {
+    const int r = it % R, k8 = (it / R) * 8;
+    uint16_t h[8], l[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) split2h(v[r * KB + k8 + c] * f, h[c], l[c]);
+    const uint32_t off = layout == TL_K64 ? t64_off(r, k8, R) : cl_off(r, k8, KB);
+    *(uint4*)(tile + off) = pack8(h);
+    *(uint4*)(tile + plane + off) = pack8(l);
+  }
+}
+
+// The same for a tile whose FP32 values the tensor-core epilogue left in the tile's own
+// memory, row-major (P2M's Phi, M2L's Psi): read into shared memory first.
+__global__ void __launch_bounds__(256) k_split16_inplace(unsigned char* base, size_t tile_bytes,
+                                                        int R, int KB, int layout,
+                                                        signed char* scales, int tiles_per_row,
+                                                        const int* fL, int which) {
+  extern __shared__ float sv16[];
+  // only the tiles the stage wrote: P2M, K tiles below ceil(Ls / 4); M2L, leaves below Lt
+  const int row_tile_pos = blockIdx.x % tiles_per_row;
+  const int lim = which == 0 ? (fL[0] + 3) / 4 : fL[1];
+  if (row_tile_pos >= lim) return;
+  unsigned char* tile = base + (size_t)blockIdx.x * tile_bytes;
+  const float* src = (const float*)tile;
+  for (int i = threadIdx.x; i < R * KB; i += blockDim.x) sv16[i] = src[i];
+  __syncthreads();
+  finish_tile16(tile, sv16, R, KB, layout, scales + blockIdx.x);
+}
 
 // ---------------------------------------------------------------------------
 // PTX wrappers: mbarrier, bulk copy, tcgen05
@@ -309,6 +391,7 @@ __device__ __forceinline__ float as_f32(float x) { return x; }
 template <typename T>
 __global__ void __launch_bounds__(256) k_mix_gather(Eig e, const T* __restrict__ X,
                                                     long long ldx, int rows, MixPlan mp) {
+  extern __shared__ float stage16[];  // FP16 mode: the tile's values (kTM x kKB)
   __shared__ long long scol[kKB];
   const int rt = blockIdx.x, kt = blockIdx.y;
   const int k = e.kp[0];
@@ -327,7 +410,16 @@ __global__ void __launch_bounds__(256) k_mix_gather(Eig e, const T* __restrict__
       long long col = scol[ch * 8 + c];
       v[c] = (col >= 0 && row < rows) ? as_f32(X[row + col]) : 0.0f;
     }
-    store_split8_f(tile, half_plane(kTM), t64_off(r, ch * 8, kTM), v);
+    if (mp.fp16) {
+#pragma unroll
+      for (int c = 0; c < 8; c++) stage16[r * kKB + ch * 8 + c] = v[c];
+    } else {
+      store_split8_f(tile, half_plane(kTM), t64_off(r, ch * 8, kTM), v);
+    }
+  }
+  if (mp.fp16) {
+    __syncthreads();
+    finish_tile16(tile, stage16, kTM, kKB, TL_K64, mp.scX + (size_t)rt * mp.kx + kt);
   }
 }
 
@@ -390,6 +482,7 @@ __global__ void k_mix_near(FmmPlan f, MixPlan mp, int dense) {
 
 // S tile (a, h): B[alpha][kk] = S_a(tl = 64 h + kk, alpha) (16 x 64).
 __global__ void k_mix_pack_S(Eig e, FmmPlan f, MixPlan mp) {
+  extern __shared__ float stage16[];
   const int hs = mp.s / kKB;
   const int a = blockIdx.x / hs, h = blockIdx.x % hs;
   if (a >= f.L[0]) return;
@@ -402,13 +495,23 @@ __global__ void k_mix_pack_S(Eig e, FmmPlan f, MixPlan mp) {
       int tl = h * kKB + ch * 8 + c;
       v[c] = f.S[(size_t)a * f.s * f.p + (size_t)al * f.s + tl];
     }
-    store_split8_d(tile, half_plane(kMixP), t64_off(al, ch * 8, kMixP), v);
+    if (mp.fp16) {
+#pragma unroll
+      for (int c = 0; c < 8; c++) stage16[al * kKB + ch * 8 + c] = narrow_rn(v[c]);
+    } else {
+      store_split8_d(tile, half_plane(kMixP), t64_off(al, ch * 8, kMixP), v);
+    }
+  }
+  if (mp.fp16) {
+    __syncthreads();
+    finish_tile16(tile, stage16, kMixP, kKB, TL_K64, mp.scS + blockIdx.x);
   }
 }
 
 // T tile (nt, kt): B[n][kk] = T(row = 64 kt + kk, col = 128 nt + n), zero outside
 // (Ls P) x (Lt P).
 __global__ void k_mix_pack_T(FmmPlan f, MixPlan mp) {
+  extern __shared__ float stage16[];
   const int nt = blockIdx.x, kt = blockIdx.y;
   const int Ls = f.L[0], Lt = f.L[1];
   const long long ldT = (long long)f.Lmax * f.p;
@@ -422,12 +525,22 @@ __global__ void k_mix_pack_T(FmmPlan f, MixPlan mp) {
       int row = kt * kKB + ch * 8 + c;
       v[c] = (col < Lt * kMixP && row < Ls * kMixP) ? f.T[row + col * ldT] : 0.0;
     }
-    store_split8_d(tile, half_plane(kTM), t64_off(n, ch * 8, kTM), v);
+    if (mp.fp16) {
+#pragma unroll
+      for (int c = 0; c < 8; c++) stage16[n * kKB + ch * 8 + c] = narrow_rn(v[c]);
+    } else {
+      store_split8_d(tile, half_plane(kTM), t64_off(n, ch * 8, kTM), v);
+    }
+  }
+  if (mp.fp16) {
+    __syncthreads();
+    finish_tile16(tile, stage16, kTM, kKB, TL_K64, mp.scT + (size_t)nt * mp.kphi + kt);
   }
 }
 
 // L tile b: B[jl][beta] = L_b(beta, jl) (s x 16).
 __global__ void k_mix_pack_L(FmmPlan f, MixPlan mp) {
+  extern __shared__ float stage16[];
   const int b = blockIdx.x;
   if (b >= f.L[1]) return;
   const int s = mp.s;
@@ -439,7 +552,16 @@ __global__ void k_mix_pack_L(FmmPlan f, MixPlan mp) {
 #pragma unroll
     for (int c = 0; c < 8; c++)
       v[c] = f.Lop[(size_t)b * f.s * f.p + (size_t)jl * f.p + ch * 8 + c];
-    store_split8_d(tile, plane, cl_off(jl, ch * 8, kMixP), v);
+    if (mp.fp16) {
+#pragma unroll
+      for (int c = 0; c < 8; c++) stage16[jl * kMixP + ch * 8 + c] = narrow_rn(v[c]);
+    } else {
+      store_split8_d(tile, plane, cl_off(jl, ch * 8, kMixP), v);
+    }
+  }
+  if (mp.fp16) {
+    __syncthreads();
+    finish_tile16(tile, stage16, s, kMixP, TL_K16, mp.scL + b);
   }
 }
 
@@ -458,6 +580,7 @@ __device__ __forceinline__ Df df_scaled_pow2(Df v, int sh) {  // v 2^sh, in two 
 }
 
 __global__ void k_mix_pack_C(Eig e, FmmPlan f, MixPlan mp) {
+  extern __shared__ float stage16[];
   const int b = blockIdx.x, i = blockIdx.y, h = blockIdx.z;
   if (b >= f.L[1] || i >= mp.nnear[b]) return;
   const int k = e.kp[0];
@@ -497,7 +620,16 @@ __global__ void k_mix_pack_C(Eig e, FmmPlan f, MixPlan mp) {
         lo[c] = w.lo;
       }
     }
-    store_split8_ff(tile, half_plane(s), t64_off(jl, ch * 8, s), hi, lo);
+    if (mp.fp16) {
+#pragma unroll
+      for (int c = 0; c < 8; c++) stage16[jl * kKB + ch * 8 + c] = hi[c] + lo[c];
+    } else {
+      store_split8_ff(tile, half_plane(s), t64_off(jl, ch * 8, s), hi, lo);
+    }
+  }
+  if (mp.fp16) {
+    __syncthreads();
+    finish_tile16(tile, stage16, s, kKB, TL_K64, mp.scC + ((size_t)(mp.noff[b] + i) * hs + h));
   }
 }
 
@@ -578,6 +710,38 @@ __device__ __forceinline__ KTile ktile(int i, const Job& J, const FmmPlan& f, co
     }
   }
   return t;
+}
+
+// FP16 mode: the sum of the two operand tiles' scales of K tile i (the drain multiplies
+// the tile's accumulator by 2^-scale).
+template <int STAGE>
+__device__ __forceinline__ int tile_scale(int i, const Job& J, const FmmPlan& f, const MixPlan& mp,
+                                          int dense) {
+  const int hs = mp.s / kKB;
+  if (STAGE == MS_P2M) {
+    const int a = 4 * J.job + i / hs, h = i % hs;
+    return mp.scX[(size_t)J.rt * mp.kx + (size_t)a * hs + h] + mp.scS[(size_t)a * hs + h];
+  }
+  if (STAGE == MS_M2L)
+    return mp.scPhi[(size_t)J.rt * mp.kphi + i] + mp.scT[(size_t)J.job * mp.kphi + i];
+  const int b = J.job;
+  if (!dense && i == 0) return mp.scPsi[(size_t)J.rt * (mp.Lmax + 1) + b] + mp.scL[b];
+  const int q = i - (dense ? 0 : 1);
+  const int ni = q / hs, h = q % hs;
+  const int a = mp.near[(long long)b * mp.Lmax + ni];
+  return mp.scX[(size_t)J.rt * mp.kx + (size_t)a * hs + h] + mp.scC[(size_t)(mp.noff[b] + ni) * hs + h];
+}
+
+// 2^-sc in two steps (sc up to 2 kScMax in magnitude), exact unless the result is
+// subnormal.
+__device__ __forceinline__ float unscale(float v, int sc) {
+  const int s1 = sc / 2;
+  return (v * pow2f(-s1)) * pow2f(s1 - sc);
+}
+
+// Instruction descriptor, kind::f16 with FP16 operands (A and B type fields 0).
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // The six partial products of the 3-term split, (A plane, B plane): (hi, hi) accumulates
@@ -746,7 +910,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
           KTile t = ktile<STAGE>(i, J, f, mp, dense);
           const uint32_t dA = tmem + (uint32_t)rg * 128u + (uint32_t)t.col;
           const uint32_t dX = tmem + kCrossCol + (uint32_t)t.col;
-          const uint32_t idesc = idesc_bf16(kTM, t.n);
+          const uint32_t idesc = mp.fp16 ? idesc_f16(kTM, t.n) : idesc_bf16(kTM, t.n);
           const uint32_t sbo = (uint32_t)min(t.kstep, 32) * 16;  // a K half holds 32
           for (int q = 0; q < t.nsteps; q++, gs++) {
             const int st = (int)(gs % kStages);
@@ -769,13 +933,22 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
               const uint64_t ko = (uint64_t)((ks >> 1) * 3) * ap + (uint64_t)((ks & 1) * 16);
               const uint64_t kob = (uint64_t)((ks >> 1) * 3) * bp + (uint64_t)((ks & 1) * 16);
               const uint64_t ka = a0 + ko, kb = b0 + kob;
-              // (A plane, B plane): hi.hi alone, then (hi, mid) (mid, hi) (hi, lo) (lo, hi) (mid, mid)
-              umma_bf16(dA, ka, kb, idesc, acc);
-              umma_bf16(dX, ka, kb + bp, idesc, xacc);
-              umma_bf16(dX, ka + ap, kb, idesc, 1u);
-              umma_bf16(dX, ka, kb + 2 * bp, idesc, 1u);
-              umma_bf16(dX, ka + 2 * ap, kb, idesc, 1u);
-              umma_bf16(dX, ka + ap, kb + bp, idesc, 1u);
+              if (mp.fp16) {
+                // FP16 2-term split: (hi, hi) (hi, lo) (lo, hi) together in the K tile's
+                // accumulator (the tiles' scales differ, so every K tile is drained)
+                umma_bf16(dA, ka, kb, idesc, acc);
+                umma_bf16(dA, ka, kb + bp, idesc, 1u);
+                umma_bf16(dA, ka + ap, kb, idesc, 1u);
+              } else {
+                // (A plane, B plane): hi.hi alone, then (hi, mid) (mid, hi) (hi, lo) (lo, hi)
+                // (mid, mid)
+                umma_bf16(dA, ka, kb, idesc, acc);
+                umma_bf16(dX, ka, kb + bp, idesc, xacc);
+                umma_bf16(dX, ka + ap, kb, idesc, 1u);
+                umma_bf16(dX, ka, kb + 2 * bp, idesc, 1u);
+                umma_bf16(dX, ka + 2 * ap, kb, idesc, 1u);
+                umma_bf16(dX, ka + ap, kb + bp, idesc, 1u);
+              }
             }
             umma_commit(bar_empty(st));  // frees the ring stage once these MMAs have read it
           }
@@ -819,12 +992,17 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
         }
         tc_fence_after();
         KTile t = ktile<STAGE>(i, J, f, mp, dense);
+        const int tsc = mp.fp16 ? tile_scale<STAGE>(i, J, f, mp, dense) : 0;
 #pragma unroll
         for (int ch = 0; ch < NCH; ch++) {
           const int col = qc * QW + ch * 16;
           if (col >= t.col && col < t.col + t.n) {
             float v[16];
             tmem_ld16(lane_base + (uint32_t)rg * 128u + (uint32_t)col, v);
+            if (mp.fp16) {
+#pragma unroll
+              for (int c = 0; c < 16; c++) v[c] = unscale(v[c], tsc);
+            }
 #pragma unroll
             for (int c = 0; c < 16; c++) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], v[c]);
           }
@@ -837,12 +1015,14 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
         break;
       }
       tc_fence_after();
+      if (!mp.fp16) {
 #pragma unroll
-      for (int ch = 0; ch < NCH; ch++) {  // cross terms: 2^-8 of hi.hi and below
-        float v[16];
-        tmem_ld16(lane_base + kCrossCol + (uint32_t)(qc * QW + ch * 16), v);
+        for (int ch = 0; ch < NCH; ch++) {  // cross terms: 2^-8 of hi.hi and below
+          float v[16];
+          tmem_ld16(lane_base + kCrossCol + (uint32_t)(qc * QW + ch * 16), v);
 #pragma unroll
-        for (int c = 0; c < 16; c++) lo[ch * 16 + c] += v[c];
+          for (int c = 0; c < 16; c++) lo[ch * 16 + c] += v[c];
+        }
       }
       tc_fence_before();
       mbar_arrive(bar_xempty);
@@ -856,17 +1036,30 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
 #pragma unroll
             for (int c = 0; c < kMixP; c++) { hi[u * kMixP + c] = 0.0f; lo[u * kMixP + c] = 0.0f; }
         }
+        if (mp.fp16) {  // FP32 values, row-major in the tile; k_split16_inplace splits them
+          float* out = (float*)tile + (size_t)r * kKB + qc * QW;
 #pragma unroll
-        for (int c8 = 0; c8 < QW; c8 += 8)
-          store_split8_ff(tile, half_plane(kTM), t64_off(r, qc * QW + c8, kTM), hi + c8, lo + c8);
+          for (int c = 0; c < QW; c++) out[c] = hi[c] + lo[c];
+        } else {
+#pragma unroll
+          for (int c8 = 0; c8 < QW; c8 += 8)
+            store_split8_ff(tile, half_plane(kTM), t64_off(r, qc * QW + c8, kTM), hi + c8, lo + c8);
+        }
       } else if (STAGE == MS_M2L) {
 #pragma unroll
         for (int u = 0; u < QW / kMixP; u++) {
           const int b = J.job * (kTM / kMixP) + qc * (QW / kMixP) + u;
           if (b < J.Lt) {
             unsigned char* tile = mp.Psip + ((size_t)J.rt * (mp.Lmax + 1) + b) * kTilePsi;
-            store_split8_ff(tile, kPlanePsi, cl_off(r, 0, kMixP), hi + u * 16, lo + u * 16);
-            store_split8_ff(tile, kPlanePsi, cl_off(r, 8, kMixP), hi + u * 16 + 8, lo + u * 16 + 8);
+            if (mp.fp16) {
+              float* out = (float*)tile + (size_t)r * kMixP;
+#pragma unroll
+              for (int c = 0; c < kMixP; c++) out[c] = hi[u * 16 + c] + lo[u * 16 + c];
+            } else {
+              store_split8_ff(tile, kPlanePsi, cl_off(r, 0, kMixP), hi + u * 16, lo + u * 16);
+              store_split8_ff(tile, kPlanePsi, cl_off(r, 8, kMixP), hi + u * 16 + 8,
+                              lo + u * 16 + 8);
+            }
           }
         }
       } else {
@@ -908,20 +1101,22 @@ void launch_umma(cudaStream_t st, int items_max, Eig e, FmmPlan f, MixPlan mp, O
   SVDUP_COUNT_LAUNCH();
 }
 
-// Executed tensor-core flops: 2 M N K per split product, six split products.
+// Executed tensor-core flops: 2 M N K per split product, six split products (three in
+// the FP16 mode).
 __global__ void k_mix_flops(Eig e, FmmPlan f, MixPlan mp, int dense, double* acc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double parts = mp.fp16 ? 3.0 : 6.0;
   const double M = (double)mp.rt * kTM, s = (double)mp.s;
   const int Ls = f.L[0], Lt = f.L[1];
   if (Ls == 0) return;
   double p2m = 0.0, m2l = 0.0, out = 0.0;
   if (!dense) {
-    p2m = 6.0 * 2.0 * M * kMixP * (double)Ls * s;
-    m2l = 6.0 * 2.0 * M * (double)((Lt * kMixP + kTM - 1) / kTM) * kTM * (double)((Ls + 3) / 4) *
-          kKB;
+    p2m = parts * 2.0 * M * kMixP * (double)Ls * s;
+    m2l = parts * 2.0 * M * (double)((Lt * kMixP + kTM - 1) / kTM) * kTM *
+          (double)((Ls + 3) / 4) * kKB;
   }
   for (int b = 0; b < Lt; b++)
-    out += 6.0 * 2.0 * M * s * ((dense ? 0.0 : (double)kMixP) + (double)mp.nnear[b] * s);
+    out += parts * 2.0 * M * s * ((dense ? 0.0 : (double)kMixP) + (double)mp.nnear[b] * s);
   acc[0] += p2m;
   acc[1] += m2l;
   acc[2] += out;
@@ -935,12 +1130,13 @@ __global__ void k_mix_flops(Eig e, FmmPlan f, MixPlan mp, int dense, double* acc
 void launch_mix_gather(cudaStream_t st, Eig e, const void* X, bool xf32, long long ldx, int rows,
                        MixPlan mp, OutMap om) {
   dim3 g(mp.rt, mp.kx);
+  const size_t sm16 = mp.fp16 ? (size_t)kTM * kKB * sizeof(float) : 0;
   if (xf32) {
-    k_mix_gather<float><<<g, 256, 0, st>>>(e, (const float*)X, ldx, rows, mp);
+    k_mix_gather<float><<<g, 256, sm16, st>>>(e, (const float*)X, ldx, rows, mp);
     SVDUP_COUNT_LAUNCH();
     k_mix_defl<float><<<e.N, 256, 0, st>>>(e, (const float*)X, ldx, rows, om);
   } else {
-    k_mix_gather<double><<<g, 256, 0, st>>>(e, (const double*)X, ldx, rows, mp);
+    k_mix_gather<double><<<g, 256, sm16, st>>>(e, (const double*)X, ldx, rows, mp);
     SVDUP_COUNT_LAUNCH();
     k_mix_defl<double><<<e.N, 256, 0, st>>>(e, (const double*)X, ldx, rows, om);
   }
@@ -951,15 +1147,17 @@ void launch_mix_setup(cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int dense) 
   k_mix_near<<<1, 256, 0, st>>>(f, mp, dense);
   SVDUP_COUNT_LAUNCH();
   const int hs = mp.s / kKB;
+  // FP16 mode: each block collects its tile's FP32 values in shared memory
+  const size_t f4 = mp.fp16 ? sizeof(float) : 0;
   if (!dense) {
-    k_mix_pack_S<<<mp.Lmax * hs, 128, 0, st>>>(e, f, mp);
+    k_mix_pack_S<<<mp.Lmax * hs, 128, f4 * kMixP * kKB, st>>>(e, f, mp);
     SVDUP_COUNT_LAUNCH();
-    k_mix_pack_T<<<dim3(mp.ntT, mp.kphi), 256, 0, st>>>(f, mp);
+    k_mix_pack_T<<<dim3(mp.ntT, mp.kphi), 256, f4 * kTM * kKB, st>>>(f, mp);
     SVDUP_COUNT_LAUNCH();
-    k_mix_pack_L<<<mp.Lmax + 1, 256, 0, st>>>(f, mp);
+    k_mix_pack_L<<<mp.Lmax + 1, 256, f4 * mp.s * kMixP, st>>>(f, mp);
     SVDUP_COUNT_LAUNCH();
   }
-  k_mix_pack_C<<<dim3(mp.Lmax + 1, mp.Lmax, hs), 256, 0, st>>>(e, f, mp);
+  k_mix_pack_C<<<dim3(mp.Lmax + 1, mp.Lmax, hs), 256, f4 * mp.s * kKB, st>>>(e, f, mp);
   SVDUP_COUNT_LAUNCH();
 }
 
@@ -968,9 +1166,19 @@ void launch_mix_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, MixPlan mp, 
   if (stage == 0) {
     if (dense) return;
     launch_umma<MS_P2M, 64>(st, mp.rt * mp.kphi, e, f, mp, om, dense, status);
+    if (mp.fp16) {  // Phi: FP32 values to FP16 planes
+      k_split16_inplace<<<mp.rt * mp.kphi, 256, kTM * kKB * sizeof(float), st>>>(
+          mp.Phip, kTileA, kTM, kKB, TL_K64, mp.scPhi, mp.kphi, mp.fL, 0);
+      SVDUP_COUNT_LAUNCH();
+    }
   } else if (stage == 1) {
     if (dense) return;
     launch_umma<MS_M2L, 128>(st, mp.rt * mp.ntT, e, f, mp, om, dense, status);
+    if (mp.fp16) {  // Psi: FP32 values to FP16 planes
+      k_split16_inplace<<<mp.rt * (mp.Lmax + 1), 256, kTM * kMixP * sizeof(float), st>>>(
+          mp.Psip, kTilePsi, kTM, kMixP, TL_K16, mp.scPsi, mp.Lmax + 1, mp.fL, 1);
+      SVDUP_COUNT_LAUNCH();
+    }
   } else if (mp.s == 64) {
     launch_umma<MS_OUT, 64>(st, mp.rt * (mp.Lmax + 1), e, f, mp, om, dense, status);
   } else {

@@ -1498,16 +1498,16 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int first = far ? sqf[0] : 0, last = far ? sqf[1] : k - 2;
-  if (far && blockIdx.x < kSecularSpecial) {
-    // The first blocks (scheduled first, each alone on its SM: one block of
-    // kSecularThreads per SM) solve the last root, whose bracket reaches far past the
-    // poles, and the wide roots, with direct sums over the whole block.
+  // The special roots: the last root, whose bracket reaches far past the poles, and the
+  // wide roots below `first` and above `last`.  Block s < nspec solves special root s
+  // with direct sums over the whole block (one block of kSecularThreads per SM); the
+  // other blocks share the regular roots, so no regular root waits behind a special
+  // one and no SM is left with nothing to do.
+  const int nwl = far ? first : 0, nwr = far ? k - 2 - last : 0;
+  const int nspec = far ? 1 + nwl + nwr : 0;
+  if (blockIdx.x < nspec) {
     const int s = blockIdx.x;
-    int j = -1;
-    if (s == 0) j = k - 1;
-    else if (s <= kSqMaxWide) j = (s - 1 < first) ? s - 1 : -1;
-    else j = (last + s - kSqMaxWide <= k - 2) ? last + s - kSqMaxWide : -1;
-    if (j < 0) return;
+    const int j = (s == 0) ? k - 1 : (s <= nwl ? s - 1 : last + (s - nwl));
     // warp 0 iterates, the whole block evaluates the sums
     __shared__ double part[4 * 32];
     __shared__ double s_tau;
@@ -1531,7 +1531,7 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
     }
     return;
   }
-  const int off = far ? kSecularSpecial : 0;
+  const int off = nspec;
   // roots interleaved over the blocks (root j to block j mod G): neighbouring roots, whose
   // work is alike, spread over the SMs
   const int G = gridDim.x - off, bm = blockIdx.x - off, wl = threadIdx.x >> 5;
@@ -1595,10 +1595,13 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
     SVDUP_COUNT_LAUNCH();
     sqv = e.sqv;
   }
-  // a warp per root, at most one block per SM (the roots are interleaved over them)
-  const int blocks =
-      std::min((e.N + kSecularThreads / 32 - 1) / (kSecularThreads / 32), device_sm_count());
-  k_secular<<<blocks + (sqv ? kSecularSpecial : 0), kSecularThreads, 0, st>>>(
+  // a warp per root, one block per SM (the roots are interleaved over them); with the
+  // far-field form, one block per SM in all, the first ones taking the special roots
+  // (at most kSecularSpecial of them)
+  const int sms = device_sm_count();
+  const int blocks = sqv ? std::max(sms, kSecularSpecial + 1)
+                         : std::min((e.N + kSecularThreads / 32 - 1) / (kSecularThreads / 32), sms);
+  k_secular<<<blocks, kSecularThreads, 0, st>>>(
       e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org, e.tau, e.dorg, status, maxit, e.sqb,
       e.sqn, e.sqf, sqv, e.z2f);
   SVDUP_COUNT_LAUNCH();
