@@ -72,7 +72,10 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=0.25)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rates", default="100,300,2000",
+                    help="offered Poisson rates (updates/s) of the serving sweep")
+    ap.add_argument("--serve-group", type=int, default=4)
     return ap.parse_args()
 
 
@@ -465,6 +468,38 @@ def accuracy_report(sv, h, stream, upload, ta, tb, eps, modes, dev):
     return res
 
 
+def refine_report(sv, h, stream, upload, ta, tb, eps, mode, dev):
+    """The precision form's refinement step (one Newton-Schulz step on Uhat and on Vhat,
+    forced with tolerance 0): its cost (an update with the step minus one without, each
+    timed by CUDA events after a warm-up call) and the probe invariants after it."""
+    import torch
+    h.set_refine_tol(0.0)
+    ms = {}
+    with torch.cuda.stream(stream):
+        for flags in (sv.REFINE, 0, sv.REFINE):  # the first call grows the workspace
+            tU, tS, tV = upload()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.update(tU, tS, tV, ta[0], tb[0], eps=eps, mode=mode | flags, check=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms[flags] = e0.elapsed_time(e1)
+        before = h.refine_residuals()
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(170708369)
+        x = torch.randn(tU.shape[1], 4, dtype=torch.float64, device=dev, generator=gen)
+        y = torch.randn(tV.shape[1], 4, dtype=torch.float64, device=dev, generator=gen)
+        oU = float(torch.linalg.norm(tU.t() @ (tU @ x) - x) / torch.linalg.norm(x))
+        oV = float(torch.linalg.norm(tV.t() @ (tV @ y) - y) / torch.linalg.norm(y))
+    h.set_refine_tol(1e-6)
+    return {"step_ms": ms[sv.REFINE] - ms[0], "update_ms_with_step": ms[sv.REFINE],
+            "probe_residual_before": {"U": before[0], "V": before[1]},
+            "after": {"orth_U": oU, "orth_V": oV},
+            "note": "one Newton-Schulz step X (3I - X^T X)/2 on Uhat and Vhat, forced "
+                    "(tolerance 0); E in 3-term BF16 split, X E in one BF16 product"}
+
+
 def batched_form(sv, dev, mode, eps, count, steps, warmup, lanes):
     """The batching form: `count` independent square updates, n log-uniform in
     [32, 1024], each A Gaussian (its SVD taken on the device with torch.linalg.svd,
@@ -524,22 +559,23 @@ def batched_form(sv, dev, mode, eps, count, steps, warmup, lanes):
             "no_graph_ms_per_batch": t_nograph * 1e3}
 
 
-def serving_form(sv, dev, mode, eps, seconds, rate, nmats, lanes, seed):
+def serving_form(sv, dev, mode, eps, seconds, rates, nmats, lanes, group, seed):
     """The serving form: `nmats` resident SVDs of m x 2m matrices, m log-uniform in
     [1024, 4096], spectrum log-uniform in [1e-4, 1] with Haar U, V (QR of Gaussians on the
     device, input preparation only); rank-one updates with N(0,1) a, b arrive as a
-    Poisson stream at `rate` per second for `seconds`, each for a uniformly chosen
-    matrix, and are submitted to the serving engine as they arrive.  Reports the
-    sustained updates/s (completed / time from the first arrival to the last
-    completion) and the latency percentiles (submission to completion, queueing
-    included)."""
+    Poisson stream for `seconds` at each offered rate, each for a uniformly chosen
+    matrix, and are submitted to the serving engine as they arrive (lanes take up to
+    `group` requests of one size class per cycle).  The vectors come from a pool of 32
+    seeded N(0,1) pairs per matrix.  Per rate: the sustained updates/s (completed / time
+    from the first arrival to the last completion) and the latency percentiles
+    (submission to the posted result, queueing included)."""
     import torch
-    from paper_1707_08369_gb300 import workloads as wl
     g = np.random.default_rng(seed)
     ms = np.rint(1024 * 4.0 ** g.uniform(0, 1, nmats)).astype(int)
     tg = torch.Generator(device=dev)
     tg.manual_seed(seed)
     srv = sv.Server(dev.index, lanes=lanes, eps=eps, mode=mode)
+    srv.set_group(group)
     live, shapes = [], []
     for m in ms:
         m = int(m)
@@ -552,39 +588,47 @@ def serving_form(sv, dev, mode, eps, seconds, rate, nmats, lanes, seed):
         shapes.append((m, n))
     torch.cuda.synchronize(dev)
     ids = [srv.register(U, S, V) for U, S, V in live]
+    pool = [[(g.standard_normal(m), g.standard_normal(n)) for _ in range(32)] for m, n in shapes]
     # warm the lanes' workspaces with one update per matrix (not timed)
-    for i, (m, n) in enumerate(shapes):
-        srv.wait(srv.submit(ids[i], g.standard_normal(m), g.standard_normal(n)))
-    nreq = max(1, int(rate * seconds))
-    gaps = g.exponential(1.0 / rate, nreq)
-    which = g.integers(0, nmats, nreq)
-    vecs = [(g.standard_normal(shapes[i][0]), g.standard_normal(shapes[i][1])) for i in which]
-    base = srv.stats()["completed"]
-    t0 = time.perf_counter()
-    arrive = t0 + np.cumsum(gaps)
-    tickets = []
-    for k in range(nreq):
-        while time.perf_counter() < arrive[k]:
-            pass
-        tickets.append(srv.submit(ids[int(which[k])], *vecs[k]))
-    lats = []
-    for t in tickets:
-        st, lat = srv.wait(t)
-        if st:
-            raise SystemExit("serving update failed: %s" % sv.error_string(st))
-        lats.append(lat)
-    t_end = time.perf_counter()
+    for i in range(nmats):
+        srv.wait(srv.submit(ids[i], *pool[i][0]))
+    out = []
+    for rate in rates:
+        nreq = max(1, int(rate * seconds))
+        gaps = g.exponential(1.0 / rate, nreq)
+        which = g.integers(0, nmats, nreq)
+        pick = g.integers(0, 32, nreq)
+        g0 = srv.group_stats()
+        t0 = time.perf_counter()
+        arrive = t0 + np.cumsum(gaps)
+        tickets = []
+        for k in range(nreq):
+            while time.perf_counter() < arrive[k]:
+                pass
+            i = int(which[k])
+            tickets.append(srv.submit(ids[i], *pool[i][int(pick[k])]))
+        lats = []
+        for t in tickets:
+            st, lat = srv.wait(t)
+            if st:
+                raise SystemExit("serving update failed: %s" % sv.error_string(st))
+            lats.append(lat)
+        t_end = time.perf_counter()
+        g1 = srv.group_stats()
+        lats = np.array(lats)
+        cyc = g1["groups"] - g0["groups"]
+        out.append({"offered_per_s": rate, "requests": nreq, "seconds": seconds,
+                    "value": nreq / (t_end - t0), "unit": "updates/s (sustained)",
+                    "latency_ms": {"p50": float(np.percentile(lats, 50)),
+                                   "p99": float(np.percentile(lats, 99))},
+                    "mean_group": (g1["grouped"] - g0["grouped"]) / max(cyc, 1)})
     stats = srv.stats()
     srv.close()
-    lats = np.array(lats)
-    return {"workload": "%d resident SVDs m x 2m, m log-uniform in [1024, 4096], sigma log-uniform "
-                        "[1e-4, 1]; Poisson arrivals of N(0,1) rank-one updates at %g/s for %g s"
-                        % (nmats, rate, seconds),
-            "value": nreq / (t_end - t0), "unit": "updates/s (sustained)", "requests": nreq,
-            "offered_per_s": rate, "lanes": lanes,
-            "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99))},
-            "max_in_flight": stats["max_in_flight"], "max_workspace_bytes": stats["max_ws_bytes"],
-            "completed_total": stats["completed"] - base}
+    return {"workload": "%d resident SVDs m x 2m, m log-uniform in [1024, 4096], sigma "
+                        "log-uniform [1e-4, 1]; Poisson arrivals of N(0,1) rank-one updates "
+                        "(pool of 32 pairs per matrix)" % nmats,
+            "lanes": lanes, "group_max": group, "sweep": out,
+            "max_in_flight": stats["max_in_flight"], "max_workspace_bytes": stats["max_ws_bytes"]}
 
 
 def main():
@@ -709,13 +753,20 @@ def main():
     acc_modes = [mode] + ([MODES[alt_name]] if alt else [])
     accuracy = None if args.no_accuracy else accuracy_report(
         sv, h, stream, upload, ta, tb, args.eps, acc_modes, dev)
+    refine = None
+    if mode != 0 and not args.no_accuracy:
+        refine = {args.mode: refine_report(sv, h, stream, upload, ta, tb, args.eps, mode, dev)}
+        if alt:
+            refine[alt_name] = refine_report(sv, h, stream, upload, ta, tb, args.eps,
+                                             MODES[alt_name], dev)
     batched = None
     if not args.no_batched and ws == 1:
         batched = batched_form(sv, dev, mode, args.eps, args.batch_count, 5, 2, 16)
     serving = None
     if not args.no_serving and ws == 1:
-        serving = serving_form(sv, dev, mode, args.eps, args.serve_seconds, 2000.0, 16, 8,
-                               170708369 + 4)
+        serving = serving_form(sv, dev, mode, args.eps, args.serve_seconds,
+                               [float(r) for r in args.serve_rates.split(",")], 16, 8,
+                               args.serve_group, 170708369 + 4)
 
     # end-to-end through the host-buffer entry point (pinned host memory)
     e2e = None
@@ -741,6 +792,7 @@ def main():
                 "fp64": fp64,
                 (alt_name or "alt"): alt,
                 "accuracy": accuracy,
+                "refine": refine,
                 "batched": batched,
                 "serving": serving,
                 "stage_ms_per_update": stage_ms,

@@ -49,8 +49,8 @@ extern "C" {
                                  tile, FP32 accumulation (about 2^-22 per operand) */
 #define SVDUP_MODE_MASK 0xff
 #define SVDUP_DENSE 0x100     /* flag: force the dense Cauchy product (no far field) */
-#define SVDUP_REFINE 0x200    /* reserved flag: an orthogonalising refinement step of the
-                                 mixed modes; not built, any mode with it: SVDUP_EINVAL */
+#define SVDUP_REFINE 0x200    /* flag: after the update, one gated orthogonalising step on
+                                 Uhat and on Vhat (svdup_refine, at the handle's tolerance) */
 
 typedef struct svdup_ctx* svdup_t;
 
@@ -150,6 +150,31 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
                  const double* a, const double* b, double eps, int mode);
 
 /*
+ * Orthogonalising refinement (no counterpart in the paper: the spec precision
+ * form's correction of split-precision products).  One Newton-Schulz step toward the
+ * nearest matrix with orthonormal columns,
+ *   X <- X (3 I - X^T X) / 2 = X - X E / 2,   E = X^T X - I,
+ * in place on X (device, rows x cols column-major, ldx >= rows, rows >= cols >= 1), on
+ * the tensor cores: E in the 3-term BF16 split with FP32 accumulation per 64-term tile
+ * and double-float sums across tiles (about 2^-24 per term), X E in one BF16 product
+ * (about 2^-8 of |E|).  The step is gated on the device: a probe residual
+ * r = max_q ||X^T X w_q - w_q|| / ||w_q|| over four fixed +-1 vectors (FP64, two passes
+ * over X) is measured first, and the step runs only if r > tol (tol <= 0: always).
+ * After the step, r falls to about max(r^2, the split's own floor of a few 1e-8..1e-7).
+ * residual: optional device double that receives r (measured before the step).
+ * Queued on the handle's stream; scratch from the handle's workspace (about
+ * 3 x 6 x rows x cols bytes of split tiles).
+ */
+int svdup_refine(svdup_t h, int rows, int cols, double* X, int ldx, double tol, double* residual);
+
+/* The gate tolerance of SVDUP_REFINE updates (default 1e-6; <= 0 refines always). */
+int svdup_set_refine_tol(svdup_t h, double tol);
+
+/* Wait for the stream; out2[0], out2[1] = the probe residuals of Uhat and Vhat that the
+ * last SVDUP_REFINE update measured before its steps. */
+int svdup_refine_residuals(svdup_t h, double* out2);
+
+/*
  * The same update with HOST buffers (end-to-end form): the inputs are copied to
  * the device on the handle's stream, the update runs, the results are copied back,
  * and the call waits for completion.  Returns the first error of the whole call.
@@ -222,6 +247,17 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
                          const double* z, double rho, double* Y, int ldy, double* lam, double eps,
                          int mode);
 
+/*
+ * Diagnostic (no counterpart in the paper): the library's own FP64 reciprocal and
+ * reciprocal square root, which its FP64 kernels use in place of division and sqrt
+ * (Newton-Raphson from an FP32 seed of the significand, exponent set by bit fields;
+ * zeros, subnormals, the largest binades, infinities and NaNs fall back to CUDA's
+ * division and sqrt).  Device arrays of n doubles: rcp[i] = 1/x[i], rsqrt[i] =
+ * 1/sqrt(x[i]) (either output may be NULL); queued on `stream` (a cudaStream_t, NULL:
+ * the legacy default stream).
+ */
+int svdup_check_rcp(void* stream, int n, const double* x, double* rcp, double* rsqrt);
+
 /* ---- batches of independent updates ------------------------------------- */
 /* One problem of a batch: the arguments of svdup_update (device pointers). */
 typedef struct svdup_problem {
@@ -284,10 +320,14 @@ int svdup_update_workspace(svdup_t h, int m, int n, double eps, int mode, size_t
  * device buffers and then submit rank-one updates of them at any time.  One scheduler
  * thread admits requests continuously: the oldest pending request whose matrix has no
  * update in flight goes to a free lane (a stream with its own workspace) as soon as one
- * is free and the free-HBM ledger (the workspace bytes of the updates in flight, capped
- * by hbm_budget) has room for it.  Updates of different matrices run concurrently on
- * the device; updates of one matrix apply in submission order.  Latency is measured on
- * the host from submission to the completion of the update's last kernel.
+ * is free and the free-HBM ledger (the workspace bytes held by the lanes, capped by
+ * hbm_budget) has room for it.  It opens a group: later pending requests of the same
+ * size class (n in the same power-of-two range) whose matrices are idle join it, up to
+ * the group size (svdup_server_set_group, default 4), and the lane queues the group's
+ * updates back to back on its stream.  Updates of different matrices run concurrently
+ * on the device; updates of one matrix apply in submission order.  Latency is measured
+ * on the host from submission to the moment the result is posted, when the request's
+ * whole group has completed.
  *   lanes       1..64 concurrent updates (0 picks 8)
  *   hbm_budget  bytes of workspace the engine may hold at once (0: 3/4 of free memory)
  */
@@ -312,6 +352,11 @@ int svdup_server_drain(svdup_server_t s);
  * of updates in flight at once, and the largest workspace bytes held at once. */
 int svdup_server_stats(svdup_server_t s, long long* completed, double* p50_ms, double* p99_ms,
                        int* max_in_flight, size_t* max_ws_bytes);
+/* Requests a lane takes per cycle, 1..16 (1: one update per lane cycle). */
+int svdup_server_set_group(svdup_server_t s, int group_max);
+/* Lane cycles launched, the requests in them, and the largest group so far. */
+int svdup_server_group_stats(svdup_server_t s, long long* groups, long long* grouped,
+                             int* max_group);
 /* Stop the scheduler (after draining) and release everything the engine allocated. */
 int svdup_server_destroy(svdup_server_t s);
 

@@ -18,6 +18,10 @@ Functions and the passages they follow:
   svd_update_sampled  Alg. 6.1 with every singular value but only sampled columns of the
                     vectors, for sizes whose dense products are out of reach
   jacobi_svd        independent one-sided Jacobi SVD (Hestenes)
+  newton_schulz_step  one orthogonalising step X (3 I - X^T X) / 2 of the precision form's
+                    refinement (not in the paper; its definition written out in FP64)
+  probe_residual    max over four fixed +-1 probes w of ||X^T X w - w|| / ||w|| (the
+                    refinement's gate)
 """
 from __future__ import annotations
 
@@ -271,3 +275,35 @@ def jacobi_svd(A):
     if st not in (OK, ENOCONV):
         raise RuntimeError("oracle_jacobi_svd failed: %d" % st)
     return U, S, Vt
+
+
+def newton_schulz_step(X):
+    """X (3 I - X^T X) / 2 in FP64: one Newton-Schulz step toward the polar factor of X.
+    Its plain definition; numpy's matmul is the only primitive."""
+    X = np.asarray(X, dtype=np.float64)
+    G = X.T @ X
+    return X @ (1.5 * np.eye(X.shape[1]) - 0.5 * G)
+
+
+def probe_signs(cols):
+    """The four +-1 probe vectors of the refinement gate (cols x 4): entry (c, q) is the
+    parity of the SplitMix64 finaliser of 0x9E3779B97F4A7C15 * (4 c + q + 1) (mod 2^64),
+    -1 when odd."""
+    M = (1 << 64) - 1
+    out = np.empty((cols, 4))
+    for c in range(cols):
+        for q in range(4):
+            x = (0x9E3779B97F4A7C15 * (4 * c + q + 1)) & M
+            x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & M
+            x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & M
+            x ^= x >> 31
+            out[c, q] = -1.0 if (x & 1) else 1.0
+    return out
+
+
+def probe_residual(X):
+    """max_q ||X^T X w_q - w_q|| / ||w_q|| over the four probe vectors (FP64)."""
+    X = np.asarray(X, dtype=np.float64)
+    W = probe_signs(X.shape[1])
+    R = X.T @ (X @ W) - W
+    return float(np.max(np.linalg.norm(R, axis=0) / np.sqrt(X.shape[1])))

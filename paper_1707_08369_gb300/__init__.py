@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libsvdup.so")
 
 OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE, ECUDA, EORDER, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6, 7
 FP64, MIXED_BF16X3, MIXED_FP16X2 = 0, 1, 2  # update modes (split BF16 x3, scaled FP16 x2)
-DENSE, REFINE = 0x100, 0x200                 # REFINE: reserved, rejected (EINVAL)
+DENSE, REFINE = 0x100, 0x200                 # flags: dense product; gated refinement
 TIMING_STAGES, TIMING_KERNELS = 1, 2      # svdup_timing modes
 
 _lib = None
@@ -56,6 +56,10 @@ def load(path: str = LIB_PATH):
     lib.svdup_secular.argtypes = [P, I, P, P, D, P, P]
     lib.svdup_cauchy_product.argtypes = [P, I, I, P, I, P, P, D, P, I, P, D, I]
     lib.svdup_secular_static.argtypes = [P, I, P, P, D, P, P, P]
+    lib.svdup_refine.argtypes = [P, I, I, P, I, D, P]
+    lib.svdup_check_rcp.argtypes = [P, I, P, P, P]
+    lib.svdup_set_refine_tol.argtypes = [P, D]
+    lib.svdup_refine_residuals.argtypes = [P, P]
     lib.svdup_batch_create.argtypes = [P, I, P, D, I, I, ctypes.POINTER(P)]
     lib.svdup_batch_launch.argtypes = [P]
     lib.svdup_batch_kernels.argtypes = [P]
@@ -75,6 +79,9 @@ def load(path: str = LIB_PATH):
     lib.svdup_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                                        ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(S_T)]
     lib.svdup_server_destroy.argtypes = [P]
+    lib.svdup_server_set_group.argtypes = [P, I]
+    lib.svdup_server_group_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I)]
     _lib = lib
     return lib
 
@@ -286,6 +293,28 @@ class Handle:
         _check(self.sync(), "svdup_secular (device)")
         return org, tau
 
+    def refine(self, X, tol: float = 0.0):
+        """One gated Newton-Schulz step on X (device, rows x cols column-major) in place;
+        returns the probe residual measured before the step (0-d device tensor)."""
+        import torch
+        rows, cols = X.shape
+        _dev_f64(X, "X")
+        ldx = _colmajor_ld(X, rows, cols, "X")
+        res = torch.zeros((), dtype=torch.float64, device=X.device)
+        _check(load().svdup_refine(self._h, rows, cols, _ptr(X), ldx, float(tol), _ptr(res)),
+               "svdup_refine")
+        _check(self.sync(), "svdup_refine (device)")
+        return res
+
+    def set_refine_tol(self, tol: float):
+        _check(load().svdup_set_refine_tol(self._h, float(tol)), "svdup_set_refine_tol")
+
+    def refine_residuals(self):
+        """Probe residuals of Uhat and Vhat measured by the last REFINE update."""
+        out = (ctypes.c_double * 2)()
+        _check(load().svdup_refine_residuals(self._h, out), "svdup_refine_residuals")
+        return out[0], out[1]
+
     def cauchy_product(self, X, d, z, rho: float, eps: float = 1e-12, mode: int = FP64):
         """Y = X Q for diag(d) + rho z z^T = Q diag(lam) Q^T; returns (lam, Y)."""
         import torch
@@ -380,6 +409,16 @@ class Server:
                                          ctypes.byref(mif), ctypes.byref(mws)), "svdup_server_stats")
         return {"completed": c.value, "p50_ms": p50.value, "p99_ms": p99.value,
                 "max_in_flight": mif.value, "max_ws_bytes": mws.value}
+
+    def set_group(self, group_max: int):
+        """Requests of one size class a lane takes per cycle (1..16)."""
+        _check(load().svdup_server_set_group(self._s, int(group_max)), "svdup_server_set_group")
+
+    def group_stats(self):
+        g, r, m = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+        _check(load().svdup_server_group_stats(self._s, ctypes.byref(g), ctypes.byref(r),
+                                               ctypes.byref(m)), "svdup_server_group_stats")
+        return {"groups": g.value, "grouped": r.value, "max_group": m.value}
 
     def close(self):
         if self._s:

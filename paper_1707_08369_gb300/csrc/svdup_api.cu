@@ -58,6 +58,8 @@ struct svdup_ctx {
   char* ws;
   size_t ws_size;
   int maxit;
+  double refine_tol;  // SVDUP_REFINE: probe residual above which the step runs
+  double* ref_res;    // device: the last probe residuals of U and V (SVDUP_REFINE)
   // stage timers
   int timing;
   TimerRec* recs;
@@ -299,7 +301,7 @@ bool is_fp16(int mode) { return (mode & SVDUP_MODE_MASK) == SVDUP_MIXED_FP16X2; 
 bool mode_ok(int mode) {
   int prec = mode & SVDUP_MODE_MASK;
   if (prec != SVDUP_FP64 && prec != SVDUP_MIXED_BF16X3 && prec != SVDUP_MIXED_FP16X2) return false;
-  return (mode & ~(SVDUP_MODE_MASK | SVDUP_DENSE)) == 0;
+  return (mode & ~(SVDUP_MODE_MASK | SVDUP_DENSE | SVDUP_REFINE)) == 0;
 }
 
 int ensure_ws(svdup_ctx* h, size_t bytes) {
@@ -345,11 +347,13 @@ struct UpdateWs {
   float *WLf, *WRf;  // the mixed form's intermediates (FP32-accurate by construction)
   FmmPlan FL, FR, FL2, FR2;  // the second products' plans (mixed: own operators)
   MixPlan ML, MR, ML2, MR2;
+  char* refbase;  // the refinement's scratch (SVDUP_REFINE), for n x n and smaller
 };
 
 UpdateWs layout_update(Arena& ar, int m, int n, double eps, int leaf, bool mixed,
-                       bool fp16 = false) {
+                       bool fp16 = false, bool refine = false) {
   UpdateWs u;
+  u.refbase = refine ? ar.take<char>(refine_ws_bytes(n, n)) : nullptr;
   u.p = ar.take<double>(m);
   u.q = ar.take<double>(n);
   u.ab = ar.take<double>(2);
@@ -628,6 +632,8 @@ svdup_ctx* lane_create(const svdup_ctx* parent) {
   }
   l->status = parent->status;
   l->flops_dev = parent->flops_dev;
+  l->ref_res = parent->ref_res;
+  l->refine_tol = parent->refine_tol;
   l->maxit = parent->maxit;
   l->open_stage = -1;
   for (int i = 0; i < 2; i++) {
@@ -810,6 +816,7 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
   h->device = device;
   h->stream = (cudaStream_t)stream;
   h->maxit = 64;
+  h->refine_tol = 1e-6;
   h->open_stage = -1;
   for (int i = 0; i < 2; i++) {
     h->dense_max[i] = kDefaultDenseMax;
@@ -827,10 +834,18 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
     free(h);
     return SVDUP_ENOMEM;
   }
+  if (cudaMalloc(&h->ref_res, 2 * sizeof(double)) != cudaSuccess ||
+      cudaMemsetAsync(h->ref_res, 0, 2 * sizeof(double), h->stream) != cudaSuccess) {
+    cudaFree(h->flops_dev);
+    cudaFree(h->status);
+    free(h);
+    return SVDUP_ENOMEM;
+  }
   if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess ||
       make_side(h) != SVDUP_OK) {
     cudaFree(h->status);
     cudaFree(h->flops_dev);
+    cudaFree(h->ref_res);
     free(h);
     return SVDUP_ECUDA;
   }
@@ -846,6 +861,7 @@ int svdup_destroy(svdup_t h) {
   if (h->ws) cudaFree(h->ws);
   cudaFree(h->status);
   cudaFree(h->flops_dev);
+  cudaFree(h->ref_res);
   for (int i = 0; i < h->nrec; i++) { cudaEventDestroy(h->recs[i].a); cudaEventDestroy(h->recs[i].b); }
   for (int i = 0; i < h->npool; i++) {
     cudaEventDestroy(h->pool[i].a);
@@ -968,11 +984,12 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   if (set_device(h)) return SVDUP_ECUDA;
   Arena meas = {nullptr, 0};
   const int leaf = leaf_size(h, n, mode);
-  layout_update(meas, m, n, eps, leaf, mixed);
+  const bool refine = (mode & SVDUP_REFINE) != 0;
+  layout_update(meas, m, n, eps, leaf, mixed, false, refine);
   int rc = ensure_ws(h, meas.off);
   if (rc) return rc;
   Arena ar = {h->ws, 0};
-  UpdateWs u = layout_update(ar, m, n, eps, leaf, mixed, is_fp16(mode));
+  UpdateWs u = layout_update(ar, m, n, eps, leaf, mixed, is_fp16(mode), refine);
   cudaStream_t st = h->stream;
 
   // STEP 1 (rewritten): p = U^T a, q = V^T b, alpha, beta
@@ -1121,7 +1138,45 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   launch_sign_apply(st, m, n, V, ldv, u.sign);
   // STEP 8
   launch_sqrt_desc(st, m, u.E2.lam, S, h->status);
+  if (refine) {  // the gated orthogonalising step, on Uhat, then on Vhat
+    RefWs wu = refine_ws_carve(u.refbase, m, m);
+    launch_refine(st, U, ldu, m, m, wu, h->refine_tol, h->status);
+    cudaMemcpyAsync(h->ref_res, wu.res, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    RefWs wv = refine_ws_carve(u.refbase, n, n);
+    launch_refine(st, V, ldv, n, n, wv, h->refine_tol, h->status);
+    cudaMemcpyAsync(h->ref_res + 1, wv.res, sizeof(double), cudaMemcpyDeviceToDevice, st);
+  }
   return check_launch();
+}
+
+int svdup_refine(svdup_t h, int rows, int cols, double* X, int ldx, double tol, double* residual) {
+  if (!h || !X || cols < 1 || rows < cols || ldx < rows || !(tol == tol)) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  int rc = ensure_ws(h, refine_ws_bytes(rows, cols));
+  if (rc) return rc;
+  RefWs w = refine_ws_carve(h->ws, rows, cols);
+  launch_refine(h->stream, X, ldx, rows, cols, w, tol, h->status);
+  if (residual &&
+      cudaMemcpyAsync(residual, w.res, sizeof(double), cudaMemcpyDeviceToDevice, h->stream) !=
+          cudaSuccess)
+    return SVDUP_ECUDA;
+  return check_launch();
+}
+
+int svdup_set_refine_tol(svdup_t h, double tol) {
+  if (!h || !(tol == tol)) return SVDUP_EINVAL;
+  h->refine_tol = tol;
+  return SVDUP_OK;
+}
+
+int svdup_refine_residuals(svdup_t h, double* out2) {
+  if (!h || !out2) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  if (cudaMemcpyAsync(out2, h->ref_res, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return SVDUP_ECUDA;
+  return SVDUP_OK;
 }
 
 int svdup_update_host(svdup_t h, int m, int n, double* U, int ldu, double* S, double* V, int ldv,

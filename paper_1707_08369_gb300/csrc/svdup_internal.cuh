@@ -235,7 +235,33 @@ struct MixPlan {
   // the tile arrays.
   int fp16;
   signed char *scX, *scPhi, *scPsi, *scS, *scT, *scL, *scC;
+  // The orthogonalising refinement's two GEMMs (RefPlan) reuse this kernel's pipeline:
+  // for them rows, rt, kx and Xp describe X's plain split tiles and the fields below the
+  // rest.
+  int cols, ct;         // columns of X and their 128-column tiles
+  double* Xr;           // X itself (FP64, column-major), updated in place
+  long long ldxr;
+  unsigned char* Xt;    // X^T split tiles [ct][ceil(rows / 64)] (128 columns x 64 rows)
+  unsigned char* Et;    // E = X^T X - I split tiles [ct][ceil(cols / 64)]
+  int kr;               // ceil(rows / 64)
+  const int* gate;      // refinement runs only where *gate != 0
 };
+
+// Scratch of the refinement of an up-to rows x cols matrix (svdup_mixed.cu).
+struct RefWs {
+  MixPlan mp;      // tile buffers and sizes (see above)
+  double* probe;   // 4 x cols probe vectors, then 4 x rows and 4 x cols products
+  double* res;     // the probe residual (1)
+  int* gate;       // 1 when the residual exceeded the tolerance
+};
+size_t refine_ws_bytes(int rows, int cols);
+RefWs refine_ws_carve(void* base, int rows, int cols);
+// One Newton-Schulz step X <- X (3 I - X^T X) / 2 = X - X E / 2, E = X^T X - I, on the
+// tensor cores (E in the 3-term BF16 split, X E in one BF16 product), queued only where
+// a probe residual ||X^T X w - w|| / ||w|| over four fixed +-1 vectors w exceeds tol
+// (tol <= 0: always).
+void launch_refine(cudaStream_t st, double* X, long long ldx, int rows, int cols, RefWs ws,
+                   double tol, int* status);
 
 constexpr int kMixP = 16;
 constexpr size_t kMixTileA = 3 * 128 * 64 * 2;  // A tile bytes (3 planes)

@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <stdint.h>
+#include <string.h>
 
 #include "svdup_df.cuh"
 #include "svdup_internal.cuh"
@@ -637,7 +638,7 @@ __global__ void k_mix_pack_C(Eig e, FmmPlan f, MixPlan mp) {
 // The tcgen05 GEMM.  A K tile is a pair (A tile, B tile) of split operands; the CTA
 // accumulates sum over its K tiles of A B^T (B stored N x K) into tensor memory.
 // ---------------------------------------------------------------------------
-enum { MS_P2M = 0, MS_M2L = 1, MS_OUT = 2 };
+enum { MS_P2M = 0, MS_M2L = 1, MS_OUT = 2, MS_GRAM = 3, MS_CORR = 4 };
 
 struct KTile {
   const unsigned char* a;
@@ -660,6 +661,8 @@ struct Job {
 template <int STAGE>
 __device__ __forceinline__ int job_tiles(const Job& J, const FmmPlan& f, const MixPlan& mp,
                                          int dense) {
+  if (STAGE == MS_GRAM) return mp.kr;  // K: the rows of X
+  if (STAGE == MS_CORR) return mp.kx;  // K: the columns of X
   const int hs = mp.s / kKB;
   if (STAGE == MS_P2M) return (min(4 * J.job + 4, J.Ls) - 4 * J.job) * hs;
   if (STAGE == MS_M2L) return (J.Ls + 3) / 4;
@@ -681,7 +684,15 @@ __device__ __forceinline__ KTile ktile(int i, const Job& J, const FmmPlan& f, co
   const int hs = mp.s / kKB;
   t.kstep = kKB / 2 * kHalvesPerStep;
   t.nsteps = 2 / kHalvesPerStep;
-  if (STAGE == MS_P2M) {
+  if (STAGE == MS_GRAM) {  // (X^T X) tile (J.rt, J.job): both operands are X^T tiles
+    half_steps_a(t, mp.Xt + ((size_t)J.rt * mp.kr + i) * kTileA, kTM);
+    half_steps_b(t, mp.Xt + ((size_t)J.job * mp.kr + i) * kTileA, kTM);
+    t.n = kTM; t.col = 0; t.first = (i == 0);
+  } else if (STAGE == MS_CORR) {  // (X E) tile (J.rt, J.job)
+    half_steps_a(t, mp.Xp + ((size_t)J.rt * mp.kx + i) * kTileA, kTM);
+    half_steps_b(t, mp.Et + ((size_t)J.job * mp.kx + i) * kTileA, kTM);
+    t.n = kTM; t.col = 0; t.first = (i == 0);
+  } else if (STAGE == MS_P2M) {
     const int a = 4 * J.job + i / hs, h = i % hs;
     half_steps_a(t, mp.Xp + ((size_t)J.rt * mp.kx + (size_t)a * hs + h) * kTileA, kTM);
     half_steps_b(t, mp.Sp + ((size_t)a * hs + h) * kTileS, kMixP);
@@ -785,7 +796,8 @@ constexpr uint32_t kCrossCol = 384;    // the cross-product accumulator, columns
 // share a few row tiles of X: the X tiles that neighbouring target leaves both read
 // stay in L2 between their uses.
 template <int STAGE>
-__device__ __forceinline__ int stage_jobs(const Job& J) {
+__device__ __forceinline__ int stage_jobs(const Job& J, const MixPlan& mp) {
+  if (STAGE == MS_GRAM || STAGE == MS_CORR) return mp.ct;  // 128-column tiles of the output
   if (STAGE == MS_P2M) return (J.Ls + 3) / 4;
   if (STAGE == MS_M2L) return (J.Lt + kTM / kMixP - 1) / (kTM / kMixP);
   return J.Lt;
@@ -811,12 +823,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
   constexpr int QW = W / (kEpiWarps / 4);  // columns per epilogue warp
   constexpr int NCH = QW / 16;     // 16-column chunks per epilogue warp
   extern __shared__ unsigned char smem_raw[];
+  constexpr bool kRef = (STAGE == MS_GRAM || STAGE == MS_CORR);  // no eigen-system, no plan
   Job J;
-  J.k = e.kp[0];
-  J.Ls = f.L[0];
-  J.Lt = f.L[1];
-  const int njobs = stage_jobs<STAGE>(J);
-  const int nitems = mp.rt * njobs;
+  J.k = kRef ? 0 : e.kp[0];
+  J.Ls = kRef ? 0 : f.L[0];
+  J.Lt = kRef ? 0 : f.L[1];
+  const int njobs = stage_jobs<STAGE>(J, mp);
+  const int nitems = (STAGE == MS_GRAM ? mp.ct : mp.rt) * njobs;
 
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_base = smem_u32(sm);
@@ -834,6 +847,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
   const uint32_t bar_xempty = bar0 + 8u * (uint32_t)(2 * kStages + 7);
   const uint32_t bar_done = bar0 + 8u * (uint32_t)(2 * kStages + 8);
   if ((int)blockIdx.x >= nitems) return;  // uniform per CTA, before any barrier or TMEM use
+  if (kRef && *mp.gate == 0) return;  // refinement not due
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kEpiWarps + 1) {
@@ -878,9 +892,27 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
               break;
             }
             const uint32_t sa = s_base + (uint32_t)st * kStageBytes, sb = sa + kStepMax;
-            mbar_expect_tx(bar_full(st), t.astep + t.bstep);
-            bulk_g2s(sa, t.a + (size_t)q * t.astep, t.astep, bar_full(st));
-            bulk_g2s(sb, t.b + (size_t)q * t.bstep, t.bstep, bar_full(st));
+            if (!mp.fp16) {
+              mbar_expect_tx(bar_full(st), t.astep + t.bstep);
+              bulk_g2s(sa, t.a + (size_t)q * t.astep, t.astep, bar_full(st));
+              bulk_g2s(sb, t.b + (size_t)q * t.bstep, t.bstep, bar_full(st));
+            } else {
+              // FP16 planes (hi, lo) only: each K half's first two planes, packed
+              const int nh = t.kstep / 32;  // K halves in the step (0: one 16-K tile)
+              const uint32_t ab = 2u * t.aplane, bb = 2u * t.bplane;
+              mbar_expect_tx(bar_full(st), (ab + bb) * (uint32_t)max(nh, 1));
+              if (nh == 0) {
+                bulk_g2s(sa, t.a + (size_t)q * t.astep, ab, bar_full(st));
+                bulk_g2s(sb, t.b + (size_t)q * t.bstep, bb, bar_full(st));
+              } else {
+                for (int hh = 0; hh < nh; hh++) {
+                  bulk_g2s(sa + hh * ab, t.a + (size_t)q * t.astep + (size_t)hh * 3u * t.aplane, ab,
+                           bar_full(st));
+                  bulk_g2s(sb + hh * bb, t.b + (size_t)q * t.bstep + (size_t)hh * 3u * t.bplane, bb,
+                           bar_full(st));
+                }
+              }
+            }
           }
         }
       }
@@ -930,10 +962,16 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
               const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
               const uint32_t xacc = (t.first && q == 0 && ks == 0) ? 0u : 1u;
               // K step ks: half ks / 2 (three planes further on), core matrices 2 (ks % 2)
-              const uint64_t ko = (uint64_t)((ks >> 1) * 3) * ap + (uint64_t)((ks & 1) * 16);
-              const uint64_t kob = (uint64_t)((ks >> 1) * 3) * bp + (uint64_t)((ks & 1) * 16);
+              // (FP16: the halves hold two planes each in shared memory)
+              const int hp = mp.fp16 ? 2 : 3;
+              const uint64_t ko = (uint64_t)((ks >> 1) * hp) * ap + (uint64_t)((ks & 1) * 16);
+              const uint64_t kob = (uint64_t)((ks >> 1) * hp) * bp + (uint64_t)((ks & 1) * 16);
               const uint64_t ka = a0 + ko, kb = b0 + kob;
-              if (mp.fp16) {
+              if (STAGE == MS_CORR) {
+                // the correction X E / 2 is about |E| of X: one BF16 product (hi, hi)
+                // leaves an error of 2^-8 |E|
+                umma_bf16(dA, ka, kb, idesc, acc);
+              } else if (mp.fp16) {
                 // FP16 2-term split: (hi, hi) (hi, lo) (lo, hi) together in the K tile's
                 // accumulator (the tiles' scales differ, so every K tile is drained)
                 umma_bf16(dA, ka, kb, idesc, acc);
@@ -1015,7 +1053,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
         break;
       }
       tc_fence_after();
-      if (!mp.fp16) {
+      if (!mp.fp16 && STAGE != MS_CORR) {
 #pragma unroll
         for (int ch = 0; ch < NCH; ch++) {  // cross terms: 2^-8 of hi.hi and below
           float v[16];
@@ -1027,7 +1065,46 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
       tc_fence_before();
       mbar_arrive(bar_xempty);
       if (!ok || *abort_flag) break;
-      if (STAGE == MS_P2M) {
+      if (STAGE == MS_GRAM) {
+        // E = X^T X - I, stored as the B operand of the correction: E is symmetric, so
+        // row i of this tile (the lane's row) is written as B row n = i with K = j.
+        const int i = J.rt * kTM + r;
+        const int kt = 2 * J.job + (qc >> 1), k0 = (qc & 1) * 32;
+        unsigned char* tile = mp.Et + ((size_t)J.rt * mp.kx + kt) * kTileA;
+#pragma unroll
+        for (int c = 0; c < QW; c++) {
+          const int j = J.job * kTM + qc * QW + c;
+          if (i >= mp.cols || j >= mp.cols) {
+            hi[c] = 0.0f; lo[c] = 0.0f;
+            continue;
+          }
+          if (i == j) two_sum_acc(hi[c], lo[c], -1.0f);  // (hi + lo) - 1
+          // The pair's two halves may nearly cancel (lo carries the cross products,
+          // 2^-8 of hi.hi); renormalise it (TwoSum) so that hi is E rounded to FP32: the
+          // correction product uses E's leading BF16 term only.
+          const float sum = hi[c] + lo[c];
+          const float bb = sum - hi[c];
+          const float err = (hi[c] - (sum - bb)) + (lo[c] - bb);
+          hi[c] = sum;
+          lo[c] = err;
+        }
+        if (kt < mp.kx) {  // (a K tile past the last column holds nothing)
+#pragma unroll
+          for (int c8 = 0; c8 < QW; c8 += 8)
+            store_split8_ff(tile, half_plane(kTM), t64_off(r, k0 + c8, kTM), hi + c8, lo + c8);
+        }
+      } else if (STAGE == MS_CORR) {
+        // X <- X - (X E) / 2 in FP64 (lanes: consecutive rows of one column)
+        const long long row = (long long)J.rt * kTM + r;
+#pragma unroll
+        for (int c = 0; c < QW; c++) {
+          const int j = J.job * kTM + qc * QW + c;
+          if (row < mp.rows && j < mp.cols) {
+            double* x = mp.Xr + (long long)j * mp.ldxr + row;
+            *x -= 0.5 * ((double)hi[c] + (double)lo[c]);
+          }
+        }
+      } else if (STAGE == MS_P2M) {
         // column group qc = leaves 4 job + (QW / 16) qc + u: columns QW qc .. of the Phi tile
         unsigned char* tile = mp.Phip + ((size_t)J.rt * mp.kphi + J.job) * kTileA;
 #pragma unroll
@@ -1099,6 +1176,138 @@ void launch_umma(cudaStream_t st, int items_max, Eig e, FmmPlan f, MixPlan mp, O
   const int grid = std::max(1, std::min(items_max, device_sm_count()));  // persistent
   k_umma<STAGE, W><<<grid, kUmmaThreads, kSmemBytes, st>>>(e, f, mp, om, dense, status);
   SVDUP_COUNT_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// The orthogonalising refinement: operand gathers and the probe check.
+// ---------------------------------------------------------------------------
+// X^T tile (ct, kt): B-style rows n = columns ct*128 + n of X, K = rows kt*64 + k.  A
+// thread takes 8 consecutive rows of one column (contiguous in X).
+__global__ void __launch_bounds__(256) k_ref_gather_t(const double* __restrict__ X, long long ldx,
+                                                      int rows, int cols, MixPlan mp) {
+  if (*mp.gate == 0) return;
+  const int ct = blockIdx.x, kt = blockIdx.y;
+  unsigned char* tile = mp.Xt + ((size_t)ct * mp.kr + kt) * kTileA;
+  for (int it = threadIdx.x; it < kTM * (kKB / 8); it += blockDim.x) {
+    const int n = it >> 3, k8 = (it & 7) * 8;
+    const int col = ct * kTM + n;
+    double v[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      const int row = kt * kKB + k8 + c;
+      v[c] = (col < cols && row < rows) ? X[(long long)col * ldx + row] : 0.0;
+    }
+    store_split8_d(tile, half_plane(kTM), t64_off(n, k8, kTM), v);
+  }
+}
+
+// X tile (rt, kt): rows rt*128 + r, K = columns kt*64 + k (lanes: consecutive rows).
+__global__ void __launch_bounds__(256) k_ref_gather(const double* __restrict__ X, long long ldx,
+                                                    int rows, int cols, MixPlan mp) {
+  if (*mp.gate == 0) return;
+  const int rt = blockIdx.x, kt = blockIdx.y;
+  unsigned char* tile = mp.Xp + ((size_t)rt * mp.kx + kt) * kTileA;
+  for (int it = threadIdx.x; it < kTM * (kKB / 8); it += blockDim.x) {
+    const int r = it & (kTM - 1), ch = it >> 7;
+    const long long row = (long long)rt * kTM + r;
+    double v[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      const int col = kt * kKB + ch * 8 + c;
+      v[c] = (col < cols && row < rows) ? X[(long long)col * ldx + row] : 0.0;
+    }
+    store_split8_d(tile, half_plane(kTM), t64_off(r, ch * 8, kTM), v);
+  }
+}
+
+// Probe vectors: entry c of probe q is +-1 by the parity of a SplitMix64 hash of (q, c).
+__device__ __forceinline__ double probe_sign(int q, int c) {
+  unsigned long long x = 0x9E3779B97F4A7C15ull * (unsigned long long)(4 * (long long)c + q + 1);
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (x & 1ull) ? -1.0 : 1.0;
+}
+
+constexpr int kProbeChunk = 512;  // columns per block of the first probe product
+
+// y = X w for the four probes: a thread per row, the columns in chunks over blocks
+// (FP64 atomic sums into y, zeroed by the caller).
+__global__ void __launch_bounds__(256) k_ref_probe1(const double* __restrict__ X, long long ldx,
+                                                    int rows, int cols, double* y) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c0 = blockIdx.y * kProbeChunk, c1 = min(cols, c0 + kProbeChunk);
+  if (r >= rows) return;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  for (int c = c0; c < c1; c++) {
+    const double x = X[(long long)c * ldx + r];
+    a0 = fma(x, probe_sign(0, c), a0);
+    a1 = fma(x, probe_sign(1, c), a1);
+    a2 = fma(x, probe_sign(2, c), a2);
+    a3 = fma(x, probe_sign(3, c), a3);
+  }
+  atomicAdd(y + r, a0);
+  atomicAdd(y + rows + r, a1);
+  atomicAdd(y + 2 * rows + r, a2);
+  atomicAdd(y + 3 * rows + r, a3);
+}
+
+// v = X^T y - w for the four probes: a block per column.
+__global__ void __launch_bounds__(256) k_ref_probe2(const double* __restrict__ X, long long ldx,
+                                                    int rows, int cols, const double* __restrict__ y,
+                                                    double* v) {
+  __shared__ double part[4][8];
+  const int c = blockIdx.x;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    const double x = X[(long long)c * ldx + r];
+#pragma unroll
+    for (int q = 0; q < 4; q++) a[q] = fma(x, y[(long long)q * rows + r], a[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    double t = a[q];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) part[q][threadIdx.x >> 5] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[threadIdx.x][w];
+    v[(long long)threadIdx.x * cols + c] = t - probe_sign(threadIdx.x, c);
+  }
+}
+
+// residual = max over the probes of ||X^T X w - w|| / ||w|| (||w||^2 = cols); the gate
+// opens when it exceeds tol.
+__global__ void __launch_bounds__(256) k_ref_gate(const double* __restrict__ v, int cols, double tol,
+                                                  double* res, int* gate, int* status) {
+  __shared__ double part[4][8];
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int c = threadIdx.x; c < cols; c += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const double t = v[(long long)q * cols + c];
+      a[q] = fma(t, t, a[q]);
+    }
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    double t = a[q];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) part[q][threadIdx.x >> 5] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int q = 0; q < 4; q++) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[q][w];
+      m = fmax(m, sqrt(t / (double)cols));
+    }
+    *res = m;
+    if (!isfinite(m)) latch(status, SVDUP_ENONFINITE);
+    *gate = (tol <= 0.0 || m > tol) && isfinite(m) ? 1 : 0;
+  }
 }
 
 // Executed tensor-core flops: 2 M N K per split product, six split products (three in
@@ -1190,6 +1399,85 @@ void launch_mix_flop_count(cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int de
                            double* acc) {
   k_mix_flops<<<1, 32, 0, st>>>(e, f, mp, dense, acc);
   SVDUP_COUNT_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// The refinement's scratch and launch sequence.
+// ---------------------------------------------------------------------------
+namespace {
+struct RefLayout {
+  size_t off_probe, off_res, off_gate, off_xt, off_et, off_xp, total;
+};
+
+RefLayout ref_layout(int rows, int cols) {
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t ct = (cols + kTM - 1) / kTM, rt = (rows + kTM - 1) / kTM;
+  const size_t kr = (rows + kKB - 1) / kKB, kx = (cols + kKB - 1) / kKB;
+  RefLayout L;
+  size_t o = 0;
+  L.off_probe = o; o += up(sizeof(double) * (4 * (size_t)rows + 8 * (size_t)cols));
+  L.off_res = o; o += up(sizeof(double));
+  L.off_gate = o; o += up(sizeof(int));
+  L.off_xt = o; o += up(ct * kr * kTileA);
+  L.off_et = o; o += up(ct * kx * kTileA);
+  L.off_xp = o; o += up(rt * kx * kTileA);
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t refine_ws_bytes(int rows, int cols) { return ref_layout(rows, cols).total; }
+
+RefWs refine_ws_carve(void* base, int rows, int cols) {
+  const RefLayout L = ref_layout(rows, cols);
+  char* b = (char*)base;
+  RefWs w;
+  memset(&w, 0, sizeof(w));
+  w.probe = (double*)(b + L.off_probe);
+  w.res = (double*)(b + L.off_res);
+  w.gate = (int*)(b + L.off_gate);
+  MixPlan& mp = w.mp;
+  mp.rows = rows;
+  mp.rt = (rows + kTM - 1) / kTM;
+  mp.cols = cols;
+  mp.ct = (cols + kTM - 1) / kTM;
+  mp.kr = (rows + kKB - 1) / kKB;
+  mp.kx = (cols + kKB - 1) / kKB;
+  mp.Xt = (unsigned char*)(b + L.off_xt);
+  mp.Et = (unsigned char*)(b + L.off_et);
+  mp.Xp = (unsigned char*)(b + L.off_xp);
+  mp.gate = w.gate;
+  mp.s = kKB;
+  return w;
+}
+
+void launch_refine(cudaStream_t st, double* X, long long ldx, int rows, int cols, RefWs ws,
+                   double tol, int* status) {
+  MixPlan mp = ws.mp;
+  mp.Xr = X;
+  mp.ldxr = ldx;
+  double* w = ws.probe;  // y (4 rows), then v (4 cols)
+  cudaMemsetAsync(w, 0, sizeof(double) * 4 * (size_t)rows, st);
+  k_ref_probe1<<<dim3((rows + 255) / 256, (cols + kProbeChunk - 1) / kProbeChunk), 256, 0, st>>>(
+      X, ldx, rows, cols, w);
+  SVDUP_COUNT_LAUNCH();
+  k_ref_probe2<<<cols, 256, 0, st>>>(X, ldx, rows, cols, w, w + 4 * (size_t)rows);
+  SVDUP_COUNT_LAUNCH();
+  k_ref_gate<<<1, 256, 0, st>>>(w + 4 * (size_t)rows, cols, tol, ws.res, ws.gate, status);
+  SVDUP_COUNT_LAUNCH();
+  // (every kernel below returns at once unless the gate opened)
+  k_ref_gather_t<<<dim3(mp.ct, mp.kr), 256, 0, st>>>(X, ldx, rows, cols, mp);
+  SVDUP_COUNT_LAUNCH();
+  k_ref_gather<<<dim3(mp.rt, mp.kx), 256, 0, st>>>(X, ldx, rows, cols, mp);
+  SVDUP_COUNT_LAUNCH();
+  Eig e;
+  memset(&e, 0, sizeof(e));
+  FmmPlan f;
+  memset(&f, 0, sizeof(f));
+  OutMap om;
+  memset(&om, 0, sizeof(om));
+  launch_umma<MS_GRAM, 128>(st, mp.ct * mp.ct, e, f, mp, om, 0, status);
+  launch_umma<MS_CORR, 128>(st, mp.rt * mp.ct, e, f, mp, om, 0, status);
 }
 
 }  // namespace svdup

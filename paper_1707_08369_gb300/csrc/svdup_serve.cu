@@ -2,13 +2,18 @@
 // rank-one updates (svdup_server_* in include/svdup.h).
 //
 // One scheduler thread owns every CUDA call of the engine.  Its loop:
-//   1. completions: a busy lane whose completion event has fired finishes its request
-//      (status from the lane's handle, latency from the submission time);
+//   1. completions: a lane whose whole group of requests has completed (every slot's
+//      event has fired) finishes them (status from the lane's handle, latency from each
+//      submission to the moment the result is posted);
 //   2. admissions, in submission order: a request is admitted when its matrix has no
 //      update in flight, a lane is free, and the free-HBM ledger allows the workspace
-//      the update needs.  The ledger counts the workspace every lane holds (a lane
-//      keeps the largest workspace it has needed); when a request does not fit, idle
-//      lanes give their workspace back (their handle is recreated) before it waits.
+//      the update needs.  The admitted request opens a group: later pending requests of
+//      the same size class (n in the same power-of-two range) join it, up to the
+//      engine's group size, and the group's updates are queued back to back on the
+//      lane's stream (updates of one matrix in submission order).  The ledger counts
+//      the workspace every lane holds (a lane keeps the largest workspace it has
+//      needed); when a group does not fit, idle lanes give their workspace back (their
+//      handle is recreated) before it waits.
 // Requests of one matrix therefore apply in submission order, requests of different
 // matrices overlap on the device, and a request that arrives while others run is
 // admitted as soon as a lane and memory free up (continuous batching).
@@ -19,11 +24,12 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
-#include <deque>
+#include <list>
 #include <mutex>
 #include <new>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/svdup.h"
@@ -50,24 +56,37 @@ struct Result {
 struct Matrix {
   int m, n, ldu, ldv;
   double *U, *S, *V;
-  bool busy;
+  int inflight;  // updates of this matrix queued on a lane
 };
 
-struct Lane {
-  svdup_t h = nullptr;
-  cudaStream_t st = nullptr;
+constexpr int kMaxGroup = 16;  // requests one lane takes per cycle (at most)
+
+struct Slot {
   cudaEvent_t done = nullptr;
   double* da = nullptr;     // device copies of a, b
   double* db = nullptr;
   double* ha = nullptr;     // pinned staging
   double* hb = nullptr;
   int cap = 0;              // capacity (entries) of the four vectors
-  size_t ws = 0;            // workspace bytes the lane's handle holds
-  bool busy = false;
   long long ticket = 0;
   int id = -1;
   double t_submit = 0.0;
 };
+
+struct Lane {
+  svdup_t h = nullptr;
+  cudaStream_t st = nullptr;
+  size_t ws = 0;            // workspace bytes the lane's handle holds
+  int nbusy = 0;            // requests of the current group (0: free)
+  Slot slot[kMaxGroup];
+};
+
+// Size class of an m x n update: the power-of-two range of n.
+int size_class(int n) {
+  int c = 0;
+  while ((1 << (c + 1)) <= n && c < 30) c++;
+  return c;
+}
 
 }  // namespace
 
@@ -78,7 +97,7 @@ struct svdup_server {
   size_t budget = 0;
   std::vector<Lane> lanes;
   std::vector<Matrix> mats;
-  std::deque<Request> pending;
+  std::list<Request> pending;
   std::unordered_map<long long, Result> results;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -90,40 +109,47 @@ struct svdup_server {
   std::vector<double> lat;
   int in_flight = 0, max_in_flight = 0;
   size_t held = 0, max_held = 0;
+  int group_max = 4;                      // requests per lane cycle (same size class)
+  long long groups = 0, grouped = 0;      // lane cycles launched, requests in them
+  int max_group_seen = 0;
 };
 
 namespace {
 
 int lane_open(svdup_server* s, Lane& l) {
-  if (cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return SVDUP_ECUDA;
   }
+  for (Slot& q : l.slot)
+    if (cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return SVDUP_ECUDA;
+    }
   return svdup_create(&l.h, s->device, (void*)l.st, 0);
 }
 
-void lane_vectors_free(Lane& l) {
-  if (l.da) cudaFree(l.da);
-  if (l.db) cudaFree(l.db);
-  if (l.ha) cudaFreeHost(l.ha);
-  if (l.hb) cudaFreeHost(l.hb);
-  l.da = l.db = l.ha = l.hb = nullptr;
-  l.cap = 0;
+void slot_vectors_free(Slot& q) {
+  if (q.da) cudaFree(q.da);
+  if (q.db) cudaFree(q.db);
+  if (q.ha) cudaFreeHost(q.ha);
+  if (q.hb) cudaFreeHost(q.hb);
+  q.da = q.db = q.ha = q.hb = nullptr;
+  q.cap = 0;
 }
 
-int lane_vectors(Lane& l, int n) {
-  if (n <= l.cap) return SVDUP_OK;
-  lane_vectors_free(l);
-  if (cudaMalloc(&l.da, n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&l.db, n * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&l.ha, n * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&l.hb, n * sizeof(double)) != cudaSuccess) {
+int slot_vectors(Slot& q, int n) {
+  if (n <= q.cap) return SVDUP_OK;
+  slot_vectors_free(q);
+  if (cudaMalloc(&q.da, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&q.db, n * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&q.ha, n * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&q.hb, n * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
-    lane_vectors_free(l);
+    slot_vectors_free(q);
     return SVDUP_ENOMEM;
   }
-  l.cap = n;
+  q.cap = n;
   return SVDUP_OK;
 }
 
@@ -142,12 +168,12 @@ int pick_lane(svdup_server* s, size_t need) {
   int best = -1;
   for (int i = 0; i < (int)s->lanes.size(); i++) {  // a free lane that already holds enough
     const Lane& l = s->lanes[i];
-    if (!l.busy && l.ws >= need && (best < 0 || l.ws < s->lanes[best].ws)) best = i;
+    if (l.nbusy == 0 && l.ws >= need && (best < 0 || l.ws < s->lanes[best].ws)) best = i;
   }
   if (best >= 0) return best;
   for (int i = 0; i < (int)s->lanes.size(); i++) {  // else the free lane that grows least
     const Lane& l = s->lanes[i];
-    if (!l.busy && (best < 0 || l.ws > s->lanes[best].ws)) best = i;
+    if (l.nbusy == 0 && (best < 0 || l.ws > s->lanes[best].ws)) best = i;
   }
   if (best < 0) return -1;
   size_t grow = need - s->lanes[best].ws;
@@ -155,7 +181,7 @@ int pick_lane(svdup_server* s, size_t need) {
   // free idle workspaces, largest first, until the growth fits
   std::vector<int> idle;
   for (int i = 0; i < (int)s->lanes.size(); i++)
-    if (!s->lanes[i].busy && i != best && s->lanes[i].ws > 0) idle.push_back(i);
+    if (s->lanes[i].nbusy == 0 && i != best && s->lanes[i].ws > 0) idle.push_back(i);
   std::sort(idle.begin(), idle.end(),
             [&](int x, int y) { return s->lanes[x].ws > s->lanes[y].ws; });
   for (int i : idle) {
@@ -172,29 +198,57 @@ void finish(svdup_server* s, long long ticket, int status, double t_submit) {
   s->completed++;
 }
 
+// Queues request r on slot q of lane l (its vectors, then the update, then the slot's
+// event); returns a status code.
+int launch_one(svdup_server* s, Lane& l, Slot& q, const Request& r) {
+  const Matrix& M = s->mats[r.id];
+  int rc = slot_vectors(q, M.n);
+  if (rc) return rc;
+  memcpy(q.ha, r.a.data(), M.m * sizeof(double));
+  memcpy(q.hb, r.b.data(), M.n * sizeof(double));
+  if (cudaMemcpyAsync(q.da, q.ha, M.m * sizeof(double), cudaMemcpyHostToDevice, l.st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(q.db, q.hb, M.n * sizeof(double), cudaMemcpyHostToDevice, l.st) !=
+          cudaSuccess)
+    return SVDUP_ECUDA;
+  rc = svdup_update(l.h, M.m, M.n, M.U, M.ldu, M.S, M.V, M.ldv, q.da, q.db, s->eps, s->mode);
+  if (rc) return rc;
+  return cudaEventRecord(q.done, l.st) == cudaSuccess ? SVDUP_OK : SVDUP_ECUDA;
+}
+
 void scheduler(svdup_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
     bool progressed = false;
-    // 1. completions
+    // 1. completions: a lane's group is finished once its last event has fired (the
+    //    handle's status word covers the whole group)
     for (Lane& l : s->lanes) {
-      if (!l.busy) continue;
-      cudaError_t q = cudaEventQuery(l.done);
+      if (l.nbusy == 0) continue;
+      cudaError_t q = cudaEventQuery(l.slot[l.nbusy - 1].done);
       if (q == cudaErrorNotReady) continue;
       int st = (q == cudaSuccess) ? svdup_sync(l.h) : SVDUP_ECUDA;
       if (q != cudaSuccess) cudaGetLastError();
-      s->mats[l.id].busy = false;
-      l.busy = false;
-      s->in_flight--;
-      finish(s, l.ticket, st, l.t_submit);
+      for (int i = 0; i < l.nbusy; i++) {
+        Slot& sl = l.slot[i];
+        s->mats[sl.id].inflight--;
+        s->in_flight--;
+        finish(s, sl.ticket, st, sl.t_submit);
+      }
+      l.nbusy = 0;
       progressed = true;
     }
     if (progressed) s->cv_done.notify_all();
-    // 2. admissions in submission order
+    // 2. admissions in submission order; a request whose matrix is busy, or that finds
+    //    no lane, blocks its matrix's later requests for this pass (order per matrix)
+    std::unordered_set<int> blocked;
     for (auto it = s->pending.begin(); it != s->pending.end();) {
       Matrix& M = s->mats[it->id];
-      if (M.busy) { ++it; continue; }
+      if (M.inflight > 0 || blocked.count(it->id)) {
+        blocked.insert(it->id);
+        ++it;
+        continue;
+      }
       size_t need = 0;
       int rc = svdup_update_workspace(s->lanes[0].h, M.m, M.n, s->eps, s->mode, &need);
       if (rc) {
@@ -203,42 +257,74 @@ void scheduler(svdup_server* s) {
         s->cv_done.notify_all();
         continue;
       }
-      const int li = pick_lane(s, need);
-      if (li < 0) { ++it; continue; }
-      Lane& l = s->lanes[li];
-      rc = lane_vectors(l, M.n);
-      if (!rc) {
-        memcpy(l.ha, it->a.data(), M.m * sizeof(double));
-        memcpy(l.hb, it->b.data(), M.n * sizeof(double));
-        if (cudaMemcpyAsync(l.da, l.ha, M.m * sizeof(double), cudaMemcpyHostToDevice, l.st) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(l.db, l.hb, M.n * sizeof(double), cudaMemcpyHostToDevice, l.st) !=
-                cudaSuccess)
-          rc = SVDUP_ECUDA;
+      // the group: this request and later ones of its size class whose matrices are idle
+      // (or already in the group, in order), up to group_max
+      std::vector<std::list<Request>::iterator> grp{it};
+      size_t need_g = need;
+      const int cls = size_class(M.n);
+      std::unordered_set<int> in_grp{it->id}, skipped;
+      for (auto jt = std::next(it); jt != s->pending.end() && (int)grp.size() < s->group_max;
+           ++jt) {
+        const Matrix& Mj = s->mats[jt->id];
+        const bool ok = size_class(Mj.n) == cls && !blocked.count(jt->id) &&
+                        !skipped.count(jt->id) && (Mj.inflight == 0 || in_grp.count(jt->id));
+        if (!ok) {
+          skipped.insert(jt->id);  // its later requests must wait behind it
+          continue;
+        }
+        size_t nj = 0;
+        if (svdup_update_workspace(s->lanes[0].h, Mj.m, Mj.n, s->eps, s->mode, &nj)) {
+          skipped.insert(jt->id);
+          continue;
+        }
+        need_g = std::max(need_g, nj);
+        grp.push_back(jt);
+        in_grp.insert(jt->id);
       }
-      if (!rc) rc = svdup_update(l.h, M.m, M.n, M.U, M.ldu, M.S, M.V, M.ldv, l.da, l.db, s->eps,
-                                 s->mode);
-      if (!rc && cudaEventRecord(l.done, l.st) != cudaSuccess) rc = SVDUP_ECUDA;
-      if (rc) {
-        cudaGetLastError();
-        finish(s, it->ticket, rc, it->t_submit);
-        it = s->pending.erase(it);
-        s->cv_done.notify_all();
+      int li = pick_lane(s, need_g);
+      if (li < 0 && grp.size() > 1) {  // the group does not fit: the first request alone
+        grp.resize(1);
+        need_g = need;
+        li = pick_lane(s, need);
+      }
+      if (li < 0) {
+        blocked.insert(it->id);
+        ++it;
         continue;
       }
-      if (need > l.ws) {
-        s->held += need - l.ws;
-        l.ws = need;
+      Lane& l = s->lanes[li];
+      if (need_g > l.ws) {
+        s->held += need_g - l.ws;
+        l.ws = need_g;
         s->max_held = std::max(s->max_held, s->held);
       }
-      l.busy = true;
-      l.ticket = it->ticket;
-      l.id = it->id;
-      l.t_submit = it->t_submit;
-      M.busy = true;
-      s->in_flight++;
+      int launched = 0;
+      for (auto& g : grp) {
+        Slot& sl = l.slot[launched];
+        rc = launch_one(s, l, sl, *g);
+        if (rc) {  // this request fails; the ones already queued stay with the lane
+          cudaGetLastError();
+          finish(s, g->ticket, rc, g->t_submit);
+          s->cv_done.notify_all();
+          continue;
+        }
+        sl.ticket = g->ticket;
+        sl.id = g->id;
+        sl.t_submit = g->t_submit;
+        s->mats[g->id].inflight++;
+        launched++;
+      }
+      l.nbusy = launched;
+      s->in_flight += launched;
       s->max_in_flight = std::max(s->max_in_flight, s->in_flight);
-      it = s->pending.erase(it);
+      if (launched > 0) {
+        s->groups++;
+        s->grouped += launched;
+        s->max_group_seen = std::max(s->max_group_seen, launched);
+      }
+      // erase the group's requests (list iterators stay valid across erasures)
+      for (size_t i = grp.size(); i-- > 1;) s->pending.erase(grp[i]);
+      it = s->pending.erase(grp[0]);
       progressed = true;
     }
     if (s->stop && s->pending.empty() && s->in_flight == 0) break;
@@ -294,7 +380,7 @@ int svdup_server_register(svdup_server_t s, int m, int n, double* U, int ldu, do
                           double* V, int ldv, int* id) {
   if (!s || !U || !S || !V || !id || m < 1 || n < m || ldu < m || ldv < n) return SVDUP_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
-  s->mats.push_back(Matrix{m, n, ldu, ldv, U, S, V, false});
+  s->mats.push_back(Matrix{m, n, ldu, ldv, U, S, V, 0});
   *id = (int)s->mats.size() - 1;
   return SVDUP_OK;
 }
@@ -359,6 +445,23 @@ int svdup_server_stats(svdup_server_t s, long long* completed, double* p50_ms, d
   return SVDUP_OK;
 }
 
+int svdup_server_set_group(svdup_server_t s, int group_max) {
+  if (!s || group_max < 1 || group_max > kMaxGroup) return SVDUP_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->group_max = group_max;
+  return SVDUP_OK;
+}
+
+int svdup_server_group_stats(svdup_server_t s, long long* groups, long long* grouped,
+                             int* max_group) {
+  if (!s) return SVDUP_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (groups) *groups = s->groups;
+  if (grouped) *grouped = s->grouped;
+  if (max_group) *max_group = s->max_group_seen;
+  return SVDUP_OK;
+}
+
 int svdup_server_destroy(svdup_server_t s) {
   if (!s) return SVDUP_EINVAL;
   if (s->started) {
@@ -372,8 +475,10 @@ int svdup_server_destroy(svdup_server_t s) {
   cudaSetDevice(s->device);
   for (Lane& l : s->lanes) {
     if (l.h) svdup_destroy(l.h);
-    lane_vectors_free(l);
-    if (l.done) cudaEventDestroy(l.done);
+    for (Slot& q : l.slot) {
+      slot_vectors_free(q);
+      if (q.done) cudaEventDestroy(q.done);
+    }
     if (l.st) cudaStreamDestroy(l.st);
   }
   delete s;

@@ -2137,3 +2137,24 @@ void launch_fill_random(cudaStream_t st, int rows, int N, double* X, double* d, 
 }
 
 }  // namespace svdup
+
+// ---------------------------------------------------------------------------
+// Diagnostic entry point: the library's own reciprocal and reciprocal square root on
+// device arrays, so that tests can hold them against CUDA's division and square root.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_check_rcp(int n, const double* __restrict__ x, double* r, double* rs) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (r) r[i] = svdup::rcp64(x[i]);
+    if (rs) rs[i] = svdup::rsqrt64(x[i]);
+  }
+}
+}  // namespace
+
+extern "C" int svdup_check_rcp(void* stream, int n, const double* x, double* rcp, double* rsqrt) {
+  if (n < 0 || (n > 0 && !x)) return SVDUP_EINVAL;
+  if (n == 0) return SVDUP_OK;
+  k_check_rcp<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, x, rcp, rsqrt);
+  SVDUP_COUNT_LAUNCH();
+  return cudaGetLastError() == cudaSuccess ? SVDUP_OK : SVDUP_ECUDA;
+}

@@ -62,9 +62,12 @@ def _lone(sv, mats, reqs, mode):
     return res
 
 
-@pytest.mark.parametrize("mode_name,lanes,budget", [("FP64", 4, 0), ("MIXED_BF16X3", 3, 0),
-                                                     ("FP64", 4, "one")])
-def test_server_matches_lone_updates(sv, mode_name, lanes, budget):
+@pytest.mark.parametrize("mode_name,lanes,budget,group", [
+    ("FP64", 4, 0, 1), ("MIXED_BF16X3", 3, 0, 1), ("FP64", 4, "one", 1),
+    ("FP64", 2, 0, 4), ("MIXED_BF16X3", 2, 0, 8), ("MIXED_FP16X2", 3, "one", 4)])
+def test_server_matches_lone_updates(sv, mode_name, lanes, budget, group):
+    """group > 1: a lane takes up to `group` requests of one size class per cycle; the
+    results must still equal lone updates in submission order."""
     mode = getattr(sv, mode_name)
     mats = _mats(11)
     reqs = _requests(36, 12)
@@ -74,6 +77,7 @@ def test_server_matches_lone_updates(sv, mode_name, lanes, budget):
         budget = max(h.update_workspace(m, n, 1e-12, mode) for m, n in SHAPES)
         h.close()
     srv = sv.Server(0, lanes=lanes, hbm_budget=budget, eps=1e-12, mode=mode)
+    srv.set_group(group)
     live = [(devF(U), dev(S), devF(V)) for U, S, V in mats]
     ids = [srv.register(U, S, V) for U, S, V in live]
     tickets = [srv.submit(ids[i], a, b) for i, a, b in reqs]
@@ -81,7 +85,11 @@ def test_server_matches_lone_updates(sv, mode_name, lanes, budget):
         st, lat = srv.wait(t)
         assert st == sv.OK and lat > 0.0
     stats = srv.stats()
+    gs = srv.group_stats()
     srv.close()
+    assert gs["grouped"] == len(reqs) and gs["max_group"] <= group
+    if group > 1:
+        assert gs["max_group"] >= 2  # requests of one size class shared a lane cycle
     assert stats["completed"] == len(reqs)
     assert stats["p99_ms"] >= stats["p50_ms"] > 0.0
     if budget:

@@ -466,3 +466,43 @@ def test_chebyshev_nodes_golden():
     p = int(kv["p"][0])
     t = np.cos((2 * np.arange(1, p + 1) - 1) * np.pi / (2 * p))
     assert np.allclose(t, kv["nodes"], rtol=0, atol=1e-16)
+
+
+# ------------------------------------------------------------------ refinement step
+def test_newton_schulz_step_on_scaled_orthogonal(orc):
+    """X = c Q: X^T X = c^2 I, so the step gives exactly c (3 - c^2) / 2 Q."""
+    g = np.random.default_rng(31)
+    Q = np.linalg.qr(g.standard_normal((60, 40)))[0]
+    for c in (0.9, 1.0, 1.1):
+        X1 = orc.newton_schulz_step(c * Q)
+        assert np.abs(X1 - c * (3 - c * c) / 2 * Q).max() <= 1e-14
+
+
+def test_newton_schulz_step_converges_quadratically(orc):
+    """X = Q (I + eps S), S symmetric: the singular values 1 + eps s_i map to
+    f(1 + x) = 1 - 3 x^2 / 2 - x^3 / 2, so the eigenvalues of X1^T X1 - I are
+    -3 (eps s_i)^2 to leading order."""
+    g = np.random.default_rng(32)
+    Q = np.linalg.qr(g.standard_normal((50, 50)))[0]
+    S = g.standard_normal((50, 50)); S = (S + S.T) / 2
+    s = np.linalg.eigvalsh(S)
+    for eps in (1e-3, 1e-4):
+        X = Q @ (np.eye(50) + eps * S)
+        X1 = orc.newton_schulz_step(X)
+        ev = np.linalg.eigvalsh(X1.T @ X1 - np.eye(50))
+        want = -3.0 * (eps * s) ** 2
+        assert np.abs(np.sort(ev) - np.sort(want)).max() <= 2.0 * (eps * np.abs(s).max()) ** 3 + 1e-14
+
+
+def test_probe_residual_definition(orc):
+    """For c Q the residual is |c^2 - 1| exactly (X^T X w - w = (c^2 - 1) w); the probes
+    are +-1 and differ from each other."""
+    g = np.random.default_rng(33)
+    Q = np.linalg.qr(g.standard_normal((70, 30)))[0]
+    assert orc.probe_residual(Q) <= 1e-14
+    for c in (0.999, 1.002):
+        assert abs(orc.probe_residual(c * Q) - abs(c * c - 1)) <= 1e-13
+    W = orc.probe_signs(257)
+    assert set(np.unique(W)) == {-1.0, 1.0}
+    assert all(np.abs(W[:, i] - W[:, j]).max() > 0 for i in range(4) for j in range(i))
+    assert abs(W.mean()) < 0.15
