@@ -258,6 +258,20 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
  */
 int svdup_check_rcp(void* stream, int n, const double* x, double* rcp, double* rsqrt);
 
+/*
+ * Failure test of the tensor-core pipeline (no counterpart in the paper).  Queues the
+ * mixed (SVDUP_MIXED_BF16X3) Cauchy product of svdup_cauchy_product, same arguments,
+ * with two test settings for that call only: the drains never hand a tensor-memory
+ * region back to the MMA issuer, and every pipeline wait gives up after 1 ms instead of
+ * one second.  The MMA issuer's wait therefore runs out; each CTA waits for the MMAs and
+ * bulk copies it issued, frees its tensor memory and exits, and SVDUP_ETIMEOUT is
+ * latched: the next svdup_sync returns it, Y holds no result, and the handle and the
+ * CUDA context stay usable.  Returns the argument and launch status like
+ * svdup_cauchy_product.
+ */
+int svdup_check_timeout(svdup_t h, int rows, int N, const double* X, int ldx, const double* d,
+                        const double* z, double rho, double* Y, int ldy, double* lam);
+
 /* ---- batches of independent updates ------------------------------------- */
 /* One problem of a batch: the arguments of svdup_update (device pointers). */
 typedef struct svdup_problem {

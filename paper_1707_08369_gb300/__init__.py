@@ -58,6 +58,7 @@ def load(path: str = LIB_PATH):
     lib.svdup_secular_static.argtypes = [P, I, P, P, D, P, P, P]
     lib.svdup_refine.argtypes = [P, I, I, P, I, D, P]
     lib.svdup_check_rcp.argtypes = [P, I, P, P, P]
+    lib.svdup_check_timeout.argtypes = [P, I, I, P, I, P, P, D, P, I, P]
     lib.svdup_set_refine_tol.argtypes = [P, D]
     lib.svdup_refine_residuals.argtypes = [P, P]
     lib.svdup_batch_create.argtypes = [P, I, P, D, I, I, ctypes.POINTER(P)]

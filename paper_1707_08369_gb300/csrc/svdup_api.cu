@@ -59,6 +59,8 @@ struct svdup_ctx {
   size_t ws_size;
   int maxit;
   double refine_tol;  // SVDUP_REFINE: probe residual above which the step runs
+  int test_stall;     // svdup_check_timeout: the tensor-core drains hold their regions
+  unsigned long long test_wait_ns;  // and the pipeline waits give up after this long
   double* ref_res;    // device: the last probe residuals of U and V (SVDUP_REFINE)
   // stage timers
   int timing;
@@ -546,6 +548,8 @@ void mix_mma(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, MixPlan mp, int ro
              int mode) {
   const int dense = use_dense(h, e.N, mode) ? 1 : 0;
   mp = mix_rows(mp, rows);
+  mp.stall = h->test_stall;
+  mp.wait_ns = h->test_wait_ns;
   if (!dense) {
     stage_begin(h, SVDUP_STAGE_P2M, st);
     launch_mix_stage(st, 0, e, f, mp, om, dense, h->status);
@@ -1161,6 +1165,18 @@ int svdup_refine(svdup_t h, int rows, int cols, double* X, int ldx, double tol, 
           cudaSuccess)
     return SVDUP_ECUDA;
   return check_launch();
+}
+
+int svdup_check_timeout(svdup_t h, int rows, int N, const double* X, int ldx, const double* d,
+                        const double* z, double rho, double* Y, int ldy, double* lam) {
+  if (!h) return SVDUP_EINVAL;
+  h->test_stall = 1;
+  h->test_wait_ns = 1000000ull;  // 1 ms
+  const int rc = svdup_cauchy_product(h, rows, N, X, ldx, d, z, rho, Y, ldy, lam, 1e-12,
+                                      SVDUP_MIXED_BF16X3);
+  h->test_stall = 0;
+  h->test_wait_ns = 0;
+  return rc;
 }
 
 int svdup_set_refine_tol(svdup_t h, double tol) {

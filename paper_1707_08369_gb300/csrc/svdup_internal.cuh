@@ -245,6 +245,11 @@ struct MixPlan {
   unsigned char* Et;    // E = X^T X - I split tiles [ct][ceil(cols / 64)]
   int kr;               // ceil(rows / 64)
   const int* gate;      // refinement runs only where *gate != 0
+  // Pipeline waits give up after wait_ns of global time (0: one second).  stall != 0
+  // is the failure test's switch: the drains then never hand a tensor-memory region
+  // back, so the MMA issuer's wait runs out and the kernel reports SVDUP_ETIMEOUT.
+  unsigned long long wait_ns;
+  int stall;
 };
 
 // Scratch of the refinement of an up-to rows x cols matrix (svdup_mixed.cu).

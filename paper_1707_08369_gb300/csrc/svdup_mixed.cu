@@ -278,8 +278,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // one second
 
 // Waits for the phase of `bar` with the given parity to complete.  Gives up (returns
-// false) after kWaitLimitNs or once another role of the CTA has raised *abort.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// false) after `limit` ns of global time or once another role of the CTA has raised
+// *abort.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint64_t limit) {
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -287,21 +288,21 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
       if (*abort) return false;
       uint64_t t = global_ns();
       if (t0 == 0) t0 = t;
-      else if (t - t0 > kWaitLimitNs) return false;
+      else if (t - t0 > limit) return false;
     }
   }
 }
 
-// The same wait bounded by time only (used for the final drain of issued MMAs, which
-// must complete even after another role gave up).
-__device__ bool mbar_wait_timed(uint32_t bar, uint32_t parity) {
+// The same wait bounded by time only (used for the final drains of issued MMAs and
+// bulk copies, which must complete even after another role gave up).
+__device__ bool mbar_wait_timed(uint32_t bar, uint32_t parity, uint64_t limit) {
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u) {
       uint64_t t = global_ns();
       if (t0 == 0) t0 = t;
-      else if (t - t0 > kWaitLimitNs) return false;
+      else if (t - t0 > limit) return false;
     }
   }
 }
@@ -848,6 +849,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
   const uint32_t bar_done = bar0 + 8u * (uint32_t)(2 * kStages + 8);
   if ((int)blockIdx.x >= nitems) return;  // uniform per CTA, before any barrier or TMEM use
   if (kRef && *mp.gate == 0) return;  // refinement not due
+  const uint64_t wlim = mp.wait_ns ? (uint64_t)mp.wait_ns : kWaitLimitNs;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kEpiWarps + 1) {
@@ -885,7 +887,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
           for (int q = 0; q < t.nsteps; q++, g++) {
             const int st = (int)(g % kStages);
             if (g >= (uint32_t)kStages &&
-                !mbar_wait(bar_empty(st), ((g / kStages) & 1u) ^ 1u, abort_flag)) {
+                !mbar_wait(bar_empty(st), ((g / kStages) & 1u) ^ 1u, abort_flag, wlim)) {
               *abort_flag = 1;
               latch(status, SVDUP_ETIMEOUT);
               alive = false;
@@ -916,6 +918,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
           }
         }
       }
+      // Every bulk copy issued has landed before the CTA may exit: wait on the last use
+      // of each ring stage (at once in a normal run, where the MMA issuer consumed them;
+      // after an abort, the copies still in flight).
+      const uint32_t g0 = g >= (uint32_t)kStages ? g - (uint32_t)kStages : 0u;
+      for (uint32_t s2 = g0; s2 < g; s2++)
+        if (!mbar_wait_timed(bar_full((int)(s2 % kStages)), (s2 / kStages) & 1u, wlim))
+          latch(status, SVDUP_ETIMEOUT);
     }
   } else if (warp == kEpiWarps + 1) {
     if (lane == 0) {  // MMA issuer
@@ -925,7 +934,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
       bool alive = true;
       for (int x = blockIdx.x; x < nitems && alive; x += gridDim.x, y++) {
         set_item<STAGE>(J, x, njobs, f, mp, dense);
-        if (y >= 1 && !mbar_wait(bar_xempty, (y - 1) & 1u, abort_flag)) {
+        if (y >= 1 && !mbar_wait(bar_xempty, (y - 1) & 1u, abort_flag, wlim)) {
           *abort_flag = 1;
           latch(status, SVDUP_ETIMEOUT);
           break;
@@ -933,7 +942,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
         for (int i = 0; i < J.ntiles && alive; i++, g++) {
           const int rg = (int)(g % kHiRegions);
           if (g >= (uint32_t)kHiRegions &&
-              !mbar_wait(bar_tempty(rg), ((g / kHiRegions) & 1u) ^ 1u, abort_flag)) {
+              !mbar_wait(bar_tempty(rg), ((g / kHiRegions) & 1u) ^ 1u, abort_flag, wlim)) {
             *abort_flag = 1;
             latch(status, SVDUP_ETIMEOUT);
             alive = false;
@@ -946,7 +955,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
           const uint32_t sbo = (uint32_t)min(t.kstep, 32) * 16;  // a K half holds 32
           for (int q = 0; q < t.nsteps; q++, gs++) {
             const int st = (int)(gs % kStages);
-            if (!mbar_wait(bar_full(st), (gs / kStages) & 1u, abort_flag)) {
+            if (!mbar_wait(bar_full(st), (gs / kStages) & 1u, abort_flag, wlim)) {
               *abort_flag = 1;
               latch(status, SVDUP_ETIMEOUT);
               alive = false;
@@ -998,7 +1007,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
       }
       // every MMA this thread issued has completed before tensor memory is released
       umma_commit(bar_done);
-      if (!mbar_wait_timed(bar_done, 0)) latch(status, SVDUP_ETIMEOUT);
+      if (!mbar_wait_timed(bar_done, 0, wlim)) latch(status, SVDUP_ETIMEOUT);
     }
   } else {
     // epilogue: drain every K tile's hi.hi products into (hi, lo) pairs and the item's
@@ -1024,7 +1033,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
       for (int c = 0; c < QW; c++) { hi[c] = 0.0f; lo[c] = 0.0f; }
       for (int i = 0; i < J.ntiles; i++, g++) {
         const int rg = (int)(g % kHiRegions);
-        if (!mbar_wait(bar_tfull(rg), (g / kHiRegions) & 1u, abort_flag)) {
+        if (!mbar_wait(bar_tfull(rg), (g / kHiRegions) & 1u, abort_flag, wlim)) {
           ok = false;
           break;
         }
@@ -1046,9 +1055,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
           }
         }
         tc_fence_before();
-        mbar_arrive(bar_tempty(rg));
+        if (!mp.stall) mbar_arrive(bar_tempty(rg));
       }
-      if (!ok || !mbar_wait(bar_xfull, y & 1u, abort_flag)) {
+      if (!ok || !mbar_wait(bar_xfull, y & 1u, abort_flag, wlim)) {
         ok = false;
         break;
       }
