@@ -184,6 +184,7 @@ int expansion_order(double eps) {
 // Defaults of the product-path choices (svdup_autotune measures and replaces them).
 constexpr int kDefaultDenseMax = 512;
 constexpr int kDefaultLeaf128Min = 2049;
+constexpr int kDefaultLeaf128MinTree = 1 << 30;
 
 int mode_index(int mode) { return (mode & SVDUP_MODE_MASK) == SVDUP_FP64 ? 0 : 1; }
 
@@ -217,12 +218,31 @@ FmmPlan make_plan(Arena& ar, int N, int rows, double eps, int leaf, bool mixed) 
   f.nnear = ar.take<int>(L + 1);
   f.near = ar.take<int>((L + 1) * L);
   f.S = ar.take<double>(L * f.s * f.p);
-  f.T = ar.take<double>(L * f.p * (L + 1) * f.p);
   f.Lop = ar.take<double>((L + 1) * f.s * f.p);
   f.ldphi = rows > 0 ? rows : 1;
+  // FP64: the hierarchy of App. D (svdup_tree.cu); mixed: the flat translation matrix
+  f.tree = mixed ? 0 : 1;
+  size_t nbox = L;  // expansion column blocks
+  if (f.tree) {
+    f.Hmax = tree_levels(f.Lmax);
+    const size_t tot = (size_t)tree_off(f.Lmax, f.Hmax);
+    f.H = ar.take<int>(1);
+    f.hsc = ar.take<double>(tot);
+    f.hsr = ar.take<double>(tot);
+    f.htc = ar.take<double>(tot);
+    f.htr = ar.take<double>(tot);
+    f.hte = ar.take<int>(tot);
+    f.hnl = ar.take<int>(tot);
+    f.hl = ar.take<int>(tot * (L + 1));
+    f.M2M = ar.take<double>(tot * f.p * f.p);
+    f.L2L = ar.take<double>(tot * f.p * f.p);
+    nbox = tot;
+  } else {
+    f.T = ar.take<double>(L * f.p * (L + 1) * f.p);
+  }
   if (rows > 0) {  // operand scratch (a shared plan takes its partner's)
-    f.Phi = ar.take<double>((size_t)f.ldphi * L * f.p);
-    f.Psi = ar.take<double>((size_t)f.ldphi * (L + 1) * f.p);
+    f.Phi = ar.take<double>((size_t)f.ldphi * nbox * f.p);
+    f.Psi = ar.take<double>((size_t)f.ldphi * (nbox + 1) * f.p);
     f.rot = ar.take<unsigned char>(rotate_scratch_bytes(N, (int)rrows));
   }
   return f;
@@ -482,19 +502,24 @@ void queue_product(svdup_ctx* h, cudaStream_t st, Eig e, FmmPlan f, int rows, do
   stage_end(h, st);
   stage_begin(h, SVDUP_STAGE_SETUP, st);
   launch_fmm_setup(st, e, f, dense);
+  if (!dense && f.tree) launch_tree_setup(st, e, f);
   stage_end(h, st);
   if (!dense) {
     stage_begin(h, SVDUP_STAGE_P2M, st);
     launch_product_f64_stage(st, 0, e, f, rows, Xs, rows, om, dense);
     stage_end(h, st);
     stage_begin(h, SVDUP_STAGE_M2L, st);
-    launch_product_f64_stage(st, 1, e, f, rows, Xs, rows, om, dense);
+    if (f.tree) launch_tree_translate(st, e, f, rows);
+    else launch_product_f64_stage(st, 1, e, f, rows, Xs, rows, om, dense);
     stage_end(h, st);
   }
   stage_begin(h, SVDUP_STAGE_OUT, st);
   launch_product_f64_stage(st, 2, e, f, rows, Xs, rows, om, dense);
   stage_end(h, st);
-  if (h->timing) launch_flop_count(st, e, f, rows, dense, h->flops_dev);
+  if (h->timing) {
+    launch_flop_count(st, e, f, rows, dense, h->flops_dev);
+    if (!dense && f.tree) launch_tree_flops(st, f, rows, h->flops_dev);
+  }
 }
 
 // The same product in split BF16 on the tensor cores (svdup_mixed.cu), in four phases
@@ -826,6 +851,7 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
     h->dense_max[i] = kDefaultDenseMax;
     h->leaf128_min[i] = kDefaultLeaf128Min;
   }
+  h->leaf128_min[0] = kDefaultLeaf128MinTree;  // FP64: the hierarchy keeps leaves small
   const char* mi = getenv("SVDUP_SECULAR_MAXIT");
   if (mi) h->maxit = atoi(mi);
   if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess) {

@@ -198,11 +198,89 @@ struct FmmPlan {
   double* S;      // P2M operators, [leaf][alpha][t] (s x p col-major): zhat_t u_alpha(x_t)
   double* T;      // M2L operator, (Lmax p) x ((Lmax+1) p) col-major, zero where not admissible
   double* Lop;    // L2P operators, [leaf][jl][beta] (p x s col-major): u_beta(y_j) inv_j
-  double* Phi;    // rows x (Lmax p) far-field expansions
-  double* Psi;    // rows x ((Lmax+1) p) local expansions
+  double* Phi;    // rows x (Lmax p) far-field expansions (FP64 tree: every level's boxes)
+  double* Psi;    // rows x ((Lmax+1) p) local expansions (FP64 tree: every level's boxes)
   long long ldphi;
   void* rot;      // scratch of the deflation rotations (rotate_scratch_bytes(N, rows))
+  // The hierarchy of App. D (FP64 mode, tree != 0): level h = 0 are the leaves, box i of
+  // level h covers leaves [i 2^h, (i + 1) 2^h), tree_nb(Lmax, h) boxes at most; level h's
+  // boxes start at tree_off(Lmax, h) in every per-box array and in Phi / Psi (columns
+  // p tree_off + p i), so level 0 keeps the flat layout.
+  int tree;
+  int Hmax;       // levels allocated
+  int* H;         // device: levels in use
+  double *hsc, *hsr, *htc, *htr;  // source / target box centres and radii, every level
+  int* hte;       // target box holds no root (1)
+  int* hnl;       // per target box: interaction-list length
+  int* hl;        // interaction lists: hl[(tree_off(h) + j) * (Lmax + 1) + i]
+  double* M2M;    // per source box below the top: p x p, child coefficients -> parent's
+  double* L2L;    // per target box below the top: p x p, parent's local -> this box's
 };
+
+// ---------------------------------------------------------------------------
+// Chebyshev far-field helpers shared by the FMM set-up kernels (svdup_product.cu,
+// svdup_tree.cu).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cheb_node(int alpha, int p) {
+  return cospi((2.0 * alpha + 1.0) / (2.0 * p));  // alpha = 0..p-1  (App. D Eq. Define_ti)
+}
+
+// Half-width of a box [lo, hi]; a (near-)single-point box gets a small positive width
+// relative to its position so that points map to finite coordinates near 0.
+__device__ __forceinline__ double box_radius(double lo, double hi) {
+  double r = 0.5 * (hi - lo);
+  double floor_r = 1e-6 * fmax(fabs(lo), fabs(hi));
+  return fmax(fmax(r, floor_r), 1e-300);
+}
+
+// Box coordinate in [-1, 1] (clamped: rounding can put a point a few ulps outside).
+__device__ __forceinline__ double box_coord(double off, double r) {
+  return fmin(1.0, fmax(-1.0, off / r));
+}
+
+// All p Lagrange basis values at x (App. D Eq. Define_uj) in the barycentric form on
+// the first-kind Chebyshev nodes: u_alpha(x) = [w_alpha / (x - t_alpha)] / sum_beta
+// [w_beta / (x - t_beta)], w_beta = (-1)^beta sin((2 beta + 1) pi / (2p)); a node hit
+// exactly gives the unit vector.  Nodes and weights come from shared memory.
+__device__ inline void lagrange_all(int p, double x, const double* st, const double* sw, double* out) {
+  int hit = -1;
+  double den = 0.0;
+  for (int b = 0; b < p; b++) {
+    const double df = x - st[b];
+    if (df == 0.0) hit = b;
+    const double c = df == 0.0 ? 0.0 : sw[b] / df;
+    out[b] = c;
+    den += c;
+  }
+  if (hit >= 0) {
+    for (int b = 0; b < p; b++) out[b] = b == hit ? 1.0 : 0.0;
+  } else {
+    const double inv = 1.0 / den;
+    for (int b = 0; b < p; b++) out[b] *= inv;
+  }
+}
+
+__device__ inline void cheb_tables(int p, double* st, double* sw) {
+  for (int b = threadIdx.x; b < p; b += blockDim.x) {
+    const double th = (2.0 * b + 1.0) / (2.0 * p);
+    st[b] = cospi(th);
+    sw[b] = (b & 1 ? -1.0 : 1.0) * sinpi(th);
+  }
+  __syncthreads();
+}
+
+// Boxes of level h (over Lmax + 1 leaves) and the offset of level h in the per-box arrays.
+__host__ __device__ inline int tree_nb(int Lmax, int h) { return ((Lmax + 1) + (1 << h) - 1) >> h; }
+__host__ __device__ inline int tree_off(int Lmax, int h) {
+  int o = 0;
+  for (int i = 0; i < h; i++) o += tree_nb(Lmax, i);
+  return o;
+}
+__host__ inline int tree_levels(int Lmax) {
+  int h = 1;
+  while (tree_nb(Lmax, h - 1) > 2) h++;
+  return h;
+}
 
 // Mixed-precision (split BF16) form of the product on the tensor cores.  Every operand
 // of the three contractions is stored pre-tiled in HBM as three BF16 planes
@@ -341,6 +419,13 @@ void launch_flop_count(cudaStream_t st, Eig e, FmmPlan f, int rows, int dense, d
 // stage 0 = P2M, 1 = M2L, 2 = L2P + near field (dense: the whole product)
 void launch_product_f64_stage(cudaStream_t st, int stage, Eig e, FmmPlan f, int rows,
                               const double* Xs, long long ldxs, OutMap om, int dense);
+// FP64 hierarchy (svdup_tree.cu): boxes, interaction lists and shift operators of every
+// level (after launch_fmm_ops), and the translations: upward shifts of the far-field
+// expansions, the per-level translations into local expansions, downward shifts.
+void launch_tree_setup(cudaStream_t st, Eig e, FmmPlan f);
+void launch_tree_translate(cudaStream_t st, Eig e, FmmPlan f, int rows);
+// useful flops of the hierarchy's translations, added to acc[1]
+void launch_tree_flops(cudaStream_t st, FmmPlan f, int rows, double* acc);
 
 // mixed-precision product (svdup_mixed.cu)
 void launch_mix_gather(cudaStream_t st, Eig e, const void* X, bool xf32, long long ldx, int rows,

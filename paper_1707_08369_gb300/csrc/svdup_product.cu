@@ -352,23 +352,6 @@ void launch_gather_columns(cudaStream_t st, Eig e, const double* X, long long ld
 // ---------------------------------------------------------------------------
 // FMM set-up: leaves, boxes, near ranges, and the operator matrices.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double cheb_node(int alpha, int p) {
-  return cospi((2.0 * alpha + 1.0) / (2.0 * p));  // alpha = 0..p-1  (App. D Eq. Define_ti)
-}
-
-// Half-width of a box [lo, hi]; a (near-)single-point box gets a small positive width
-// relative to its position so that points map to finite coordinates near 0.
-__device__ __forceinline__ double box_radius(double lo, double hi) {
-  double r = 0.5 * (hi - lo);
-  double floor_r = 1e-6 * fmax(fabs(lo), fabs(hi));
-  return fmax(fmax(r, floor_r), 1e-300);
-}
-
-// Box coordinate in [-1, 1] (clamped: rounding can put a point a few ulps outside).
-__device__ __forceinline__ double box_coord(double off, double r) {
-  return fmin(1.0, fmax(-1.0, off / r));
-}
-
 // Leaves and boxes.  The largest poles of a solve may stand far above the rest (the
 // large eigenvalues that earlier updates added); a leaf holding them and ordinary poles
 // would reach over the whole spectrum and be near every target.  So the partition is
@@ -482,37 +465,6 @@ __device__ __forceinline__ bool is_near(const FmmPlan& f, int b, int a) {
   return false;
 }
 
-// All p Lagrange basis values at x (App. D Eq. Define_uj) in the barycentric form on
-// the first-kind Chebyshev nodes: u_alpha(x) = [w_alpha / (x - t_alpha)] / sum_beta
-// [w_beta / (x - t_beta)], w_beta = (-1)^beta sin((2 beta + 1) pi / (2p)); a node hit
-// exactly gives the unit vector.  Nodes and weights come from shared memory.
-__device__ void lagrange_all(int p, double x, const double* st, const double* sw, double* out) {
-  int hit = -1;
-  double den = 0.0;
-  for (int b = 0; b < p; b++) {
-    const double df = x - st[b];
-    if (df == 0.0) hit = b;
-    const double c = df == 0.0 ? 0.0 : sw[b] / df;
-    out[b] = c;
-    den += c;
-  }
-  if (hit >= 0) {
-    for (int b = 0; b < p; b++) out[b] = b == hit ? 1.0 : 0.0;
-  } else {
-    const double inv = 1.0 / den;
-    for (int b = 0; b < p; b++) out[b] *= inv;
-  }
-}
-
-__device__ void cheb_tables(int p, double* st, double* sw) {
-  for (int b = threadIdx.x; b < p; b += blockDim.x) {
-    const double th = (2.0 * b + 1.0) / (2.0 * p);
-    st[b] = cospi(th);
-    sw[b] = (b & 1 ? -1.0 : 1.0) * sinpi(th);
-  }
-  __syncthreads();
-}
-
 // P2M operator of source leaf a: S[a][alpha][tl] = zhat_t u_alpha((d_t - c_a) / r_a)
 // (App. D STEP 5 with the far-field variable mapped to [-1, 1]); one thread per pole.
 __global__ void k_fmm_S(Eig e, FmmPlan f) {
@@ -599,6 +551,7 @@ void launch_fmm_ops(cudaStream_t st, Eig e, FmmPlan f, int dense) {
   SVDUP_COUNT_LAUNCH();
   k_fmm_L<<<blocks, 128, 0, st>>>(e, f);
   SVDUP_COUNT_LAUNCH();
+  if (f.tree) return;  // the hierarchy forms its translations in its GEMMs
   long long nt = (long long)f.Lmax * f.p * (long long)(f.Lmax + 1) * f.p;
   int tb = (int)((nt + 255) / 256);
   k_fmm_T<<<tb, 256, 0, st>>>(f);
@@ -755,7 +708,7 @@ __global__ void k_flop_count(Eig e, FmmPlan f, int rows, int dense, double* acc)
       int a = f.near[(long long)b * f.Lmax + i];
       near_src += min(k, a * s + s - P) - max(0, a * s - P);
     }
-    m2l += 2.0 * R * (double)p * p * (double)(Ls - f.nnear[b]);
+    if (!f.tree) m2l += 2.0 * R * (double)p * p * (double)(Ls - f.nnear[b]);
     out += 2.0 * R * (double)nb * (double)(p + near_src);
   }
   acc[0] += p2m;
