@@ -1060,7 +1060,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     // STEPs 3, 6: first right solve; STEP 7: second right solve
     launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
     queue_solve(h, sR, u.E3, false, h->ev[9], h->ev[10]);
-    launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4);
+    launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4, mixed);
     if (cudaEventRecord(h->ev[2], sR) != cudaSuccess) return SVDUP_ECUDA;  // E3 ready
     launch_fill_second(sR, u.E4, u.E3.lam, u.zsec4);
     queue_solve(h, sR, u.E4, mixed, h->ev[13]);
@@ -1072,7 +1072,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     // STEPs 2, 4: first left solve; its transposed product gives the second left z
     launch_fill_left(sL, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
     queue_solve(h, sL, u.E1, false, h->ev[7], h->ev[8]);
-    launch_apply_qt(sL, u.E1, u.z2p, u.ysortL, u.zsec2);
+    launch_apply_qt(sL, u.E1, u.z2p, u.ysortL, u.zsec2, mixed);
     if (cudaEventRecord(h->ev[0], sL) != cudaSuccess) return SVDUP_ECUDA;  // E1 ready
     // STEP 5: second left solve
     launch_fill_second(sL, u.E2, u.E1.lam, u.zsec2);
@@ -1115,7 +1115,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     // STEPs 3, 6: first right solve; STEP 7: second right solve
     launch_fill_right(sR, u.E3, m, n, S, u.p, u.q, u.ab, u.z4p, u.E4.rhop, h->status);
     queue_solve(h, sR, u.E3);
-    launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4);
+    launch_apply_qt(sR, u.E3, u.z4p, u.ysortR, u.zsec4, mixed);
     if (!hand(h->ev[2], sR, pV)) return SVDUP_ECUDA;  // E3 ready: V's first product
     launch_fill_second(sR, u.E4, u.E3.lam, u.zsec4);
     queue_solve(h, sR, u.E4, mixed);
@@ -1124,7 +1124,7 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
     // STEPs 2, 4: first left solve; its transposed product gives the second left z
     launch_fill_left(sL, u.E1, m, S, u.p, u.q, u.ab, u.z2p, u.E2.rhop, h->status);
     queue_solve(h, sL, u.E1);
-    launch_apply_qt(sL, u.E1, u.z2p, u.ysortL, u.zsec2);
+    launch_apply_qt(sL, u.E1, u.z2p, u.ysortL, u.zsec2, mixed);
     if (!hand(h->ev[0], sL, pU)) return SVDUP_ECUDA;  // E1 ready: U's first product
     // STEP 5: second left solve
     launch_fill_second(sL, u.E2, u.E1.lam, u.zsec2);

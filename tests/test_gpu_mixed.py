@@ -130,16 +130,20 @@ def test_mixed_update_fmm_loguniform(sv, hnd, orc, mode_name):
     assert orthU <= 10 * rtol and orthV <= 10 * rtol, (orthU, orthV)
 
 
-def test_mixed_matches_fp64_eigenvalues_bitwise(sv, hnd):
-    """The mixed forms change only the products: the eigenvalues (FP64 roots) are
-    bit-identical to the FP64 form's."""
+def test_mixed_matches_fp64_eigenvalues(sv, hnd):
+    """The mixed forms keep the secular roots in FP64; the z of each side's second solve
+    comes from double-float sums (about 2^-45 per term) instead of FP64 ones, so their
+    singular values agree with the FP64 form's to far below the 1e-12 S_1 bar (1e-14 S_1
+    here), and the two mixed forms with each other bitwise (the products do not feed
+    the roots)."""
     U, S, V, a, b = wl.loguniform_sq(700, seed=wl.BASE_SEED + 5)
     outs = []
     for mode in (sv.FP64, sv.MIXED_BF16X3, sv.MIXED_FP16X2):
         tU, tS, tV = devF(U), dev(S), devF(V)
         hnd.update(tU, tS, tV, dev(a), dev(b), eps=1e-12, mode=mode)
         outs.append(tS.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert np.abs(outs[1] - outs[0]).max() <= 1e-14 * outs[0][0]
+    assert np.array_equal(outs[1], outs[2])
 
 
 def test_mixed_rejects_unsupported_modes(sv, hnd):
