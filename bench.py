@@ -322,7 +322,9 @@ def roofline_of(kernels, mode, clk, peaks, peak_src, n, mode_name):
     per = lambda fl: fl / cnt / per_launch_s / 1e12
     if mode == 0:
         peak = fp64_peak_tflops(clk.get("sm_mhz") if clk else None)
-        r = {"kernel": "k_gemm_f64<%s>" % STAGE_KERNELS[dom], "bound": "alu",
+        # (FP64: the translation stage is the hierarchy's shifts and translations)
+        kname = "k_tree_gemm<UP/M2L/DOWN>" if dom == "m2l" else "k_gemm_f64<%s>" % STAGE_KERNELS[dom]
+        r = {"kernel": kname, "bound": "alu",
              "achieved": per(alg), "peak": peak, "unit": "TFLOP/s", "frac": per(alg) / peak,
              "traffic": None, "useful_tflops": per(useful), "useful_frac": per(useful) / peak,
              "peak_source": "FP64 pipe from unit counts and the sampled SM clock "
