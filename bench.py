@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-lanes", type=int, default=16)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rates", default="100,300,2000",
@@ -763,7 +764,7 @@ def main():
                                              MODES[alt_name], dev)
     batched = None
     if not args.no_batched and ws == 1:
-        batched = batched_form(sv, dev, mode, args.eps, args.batch_count, 5, 2, 16)
+        batched = batched_form(sv, dev, mode, args.eps, args.batch_count, 5, 2, args.batch_lanes)
     serving = None
     if not args.no_serving and ws == 1:
         serving = serving_form(sv, dev, mode, args.eps, args.serve_seconds,
