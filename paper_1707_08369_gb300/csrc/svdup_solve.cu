@@ -1598,10 +1598,14 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
   // a warp per root, one block per SM (the roots are interleaved over them); with the
   // far-field form, one block per SM in all, the first ones taking the special roots
   // (at most kSecularSpecial of them)
+  // Without the far field (k < kSqMinK), blocks of 8 warps: a small solve then takes a
+  // few SMs' worth of registers instead of whole SMs, which lets many small problems
+  // (a batch's lanes) solve side by side.
   const int sms = device_sm_count();
+  const int threads = sqv ? kSecularThreads : 256;
   const int blocks = sqv ? std::max(sms, kSecularSpecial + 1)
-                         : std::min((e.N + kSecularThreads / 32 - 1) / (kSecularThreads / 32), sms);
-  k_secular<<<blocks, kSecularThreads, 0, st>>>(
+                         : std::min((e.N + threads / 32 - 1) / (threads / 32), 4 * sms);
+  k_secular<<<blocks, threads, 0, st>>>(
       e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org, e.tau, e.dorg, status, maxit, e.sqb,
       e.sqn, e.sqf, sqv, e.z2f);
   SVDUP_COUNT_LAUNCH();

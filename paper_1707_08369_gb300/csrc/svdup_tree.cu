@@ -148,12 +148,13 @@ __global__ void k_tree_shifts(FmmPlan f) {
 // translations their geometry, sit in shared memory.  The translation entries
 // 1 / (xbar - ybar) are formed in the GEMM (rcp64: four FP64 operations).
 // ---------------------------------------------------------------------------
-constexpr int TM = 64, TN = 32, TK = 16;
+constexpr int TM = 64, TK = 16;  // output tile TM x 8 MJ (MJ = 3 for p <= 24, else 4)
 constexpr int kMaxSeg = 512;  // input boxes of one output box (lists longer are cut in parts)
 enum { TR_UP = 0, TR_M2L = 1, TR_DOWN = 2 };
 
-template <int KIND>
+template <int KIND, int MJ>
 __global__ void __launch_bounds__(128) k_tree_gemm(FmmPlan f, int rows, int hin) {
+  constexpr int TN = 8 * MJ;
   __shared__ double As[TK][TM];
   __shared__ double Bs[TK][TN + 1];
   __shared__ double tn[32];
@@ -181,11 +182,11 @@ __global__ void __launch_bounds__(128) k_tree_gemm(FmmPlan f, int rows, int hin)
   const double rj = KIND == TR_M2L ? f.htr[oo] : 0.0;
   const double* Abase = KIND == TR_DOWN ? f.Psi : f.Phi;
   const int r0 = blockIdx.x * TM;
-  double acc[4][4];
+  double acc[4][MJ];
 #pragma unroll
   for (int i = 0; i < 4; i++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+    for (int j = 0; j < MJ; j++) acc[i][j] = 0.0;
   for (int s0 = 0; s0 < nseg; s0 += kMaxSeg) {  // input boxes in chunks of kMaxSeg
   const int ns = min(kMaxSeg, nseg - s0);
   __syncthreads();  // the previous chunk's boxes consumed
@@ -225,23 +226,23 @@ __global__ void __launch_bounds__(128) k_tree_gemm(FmmPlan f, int rows, int hin)
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < TK; kk++) {
-      double a[4], bb[4];
+      double a[4], bb[MJ];
 #pragma unroll
       for (int i = 0; i < 4; i++) a[i] = As[kk][ty * 4 + i];
 #pragma unroll
-      for (int j = 0; j < 4; j++) bb[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < MJ; j++) bb[j] = Bs[kk][tx * MJ + j];
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        for (int j = 0; j < MJ; j++) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
     }
     __syncthreads();
   }
   }
   double* Out = (KIND == TR_UP ? f.Phi : f.Psi) + (long long)oo * p * f.ldphi;
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    const int cc = tx * 4 + j;
+  for (int j = 0; j < MJ; j++) {
+    const int cc = tx * MJ + j;
     if (cc >= p) continue;
     double* col = Out + (long long)cc * f.ldphi;
 #pragma unroll
@@ -283,20 +284,26 @@ void launch_tree_setup(cudaStream_t st, Eig e, FmmPlan f) {
   SVDUP_COUNT_LAUNCH();
 }
 
-void launch_tree_translate(cudaStream_t st, Eig e, FmmPlan f, int rows) {
-  (void)e;
+template <int MJ>
+void tree_translate(cudaStream_t st, FmmPlan f, int rows) {
   const int rt = (rows + TM - 1) / TM;
   for (int h = 0; h + 1 < f.Hmax; h++) {  // upward: level h into level h + 1
-    k_tree_gemm<TR_UP><<<dim3(rt, tree_nb(f.Lmax, h + 1)), 128, 0, st>>>(f, rows, h);
+    k_tree_gemm<TR_UP, MJ><<<dim3(rt, tree_nb(f.Lmax, h + 1)), 128, 0, st>>>(f, rows, h);
     SVDUP_COUNT_LAUNCH();
   }
   // the translations of every level at once (they are independent)
-  k_tree_gemm<TR_M2L><<<dim3(rt, tree_off(f.Lmax, f.Hmax)), 128, 0, st>>>(f, rows, 0);
+  k_tree_gemm<TR_M2L, MJ><<<dim3(rt, tree_off(f.Lmax, f.Hmax)), 128, 0, st>>>(f, rows, 0);
   SVDUP_COUNT_LAUNCH();
   for (int h = f.Hmax - 2; h >= 0; h--) {  // downward: level h + 1 into level h
-    k_tree_gemm<TR_DOWN><<<dim3(rt, tree_nb(f.Lmax, h)), 128, 0, st>>>(f, rows, h);
+    k_tree_gemm<TR_DOWN, MJ><<<dim3(rt, tree_nb(f.Lmax, h)), 128, 0, st>>>(f, rows, h);
     SVDUP_COUNT_LAUNCH();
   }
+}
+
+void launch_tree_translate(cudaStream_t st, Eig e, FmmPlan f, int rows) {
+  (void)e;
+  if (f.p <= 24) tree_translate<3>(st, f, rows);
+  else tree_translate<4>(st, f, rows);
 }
 
 void launch_tree_flops(cudaStream_t st, FmmPlan f, int rows, double* acc) {
