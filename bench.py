@@ -527,6 +527,7 @@ def batched_form(sv, dev, mode, eps, count, steps, warmup, lanes):
     h = sv.Handle(dev.index)
     t0 = time.perf_counter()
     tuned = h.autotune(mode, nmax=1024)
+    tile128 = h.tile_tuning(mode)
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     bt = h.batch_plan(items, eps=eps, mode=mode, lanes=lanes)
@@ -558,7 +559,8 @@ def batched_form(sv, dev, mode, eps, count, steps, warmup, lanes):
                         "(SVD by torch.linalg.svd on the device as input), N(0,1) a, b" % count,
             "value": count / (ms / 1e3), "unit": "updates/s", "ms_per_batch": ms, "steps": steps,
             "lanes": lanes, "graph_kernels": kernels, "plan_s": t_plan,
-            "autotune": {"dense_max": tuned[0], "leaf128_min": tuned[1], "seconds": t_tune},
+            "autotune": {"dense_max": tuned[0], "leaf128_min": tuned[1],
+                         "dense_tile128_min": tile128, "seconds": t_tune},
             "no_graph_ms_per_batch": t_nograph * 1e3}
 
 

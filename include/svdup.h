@@ -314,14 +314,19 @@ int svdup_update_batched(svdup_t h, int count, const svdup_problem* probs, doubl
  * Autotuning of the product path for `mode` (no counterpart in the paper).  For
  * N = 256, 512, ... up to nmax it times the Cauchy product (rows = N, synthetic poles
  * and vectors generated on the device) with the dense tile product, the far field with
- * leaves of 64 poles, and with leaves of 128, and keeps on the handle the largest N at
- * which the dense product was fastest (dense_max) and the smallest N at which leaves
- * of 128 beat 64 (leaf128_min).  svdup_tuning_get / svdup_tuning_set read and restore
- * these two numbers (to cache them between processes).
+ * leaves of 64 poles, with leaves of 128, and (mixed modes) the dense product with
+ * 128-column instead of 64-column output tiles on the tensor cores, and keeps on the
+ * handle the largest N at which a dense product was fastest (dense_max), the smallest N
+ * at which leaves of 128 beat 64 (leaf128_min) and the smallest N at which the dense
+ * product's 128-column tiles beat 64 (dense_tile128_min).  svdup_tuning_get /
+ * svdup_tuning_set and svdup_tuning_get_tile / svdup_tuning_set_tile read and restore
+ * these numbers (to cache them between processes).
  */
 int svdup_autotune(svdup_t h, int mode, int nmax);
 int svdup_tuning_get(svdup_t h, int mode, int* dense_max, int* leaf128_min);
 int svdup_tuning_set(svdup_t h, int mode, int dense_max, int leaf128_min);
+int svdup_tuning_get_tile(svdup_t h, int mode, int* dense_tile128_min);
+int svdup_tuning_set_tile(svdup_t h, int mode, int dense_tile128_min);
 
 /* Bytes of workspace svdup_update needs on this handle for an m x n problem in `mode`
  * (the handle keeps the largest such workspace it has needed). */

@@ -70,6 +70,8 @@ def load(path: str = LIB_PATH):
     lib.svdup_autotune.argtypes = [P, I, I]
     lib.svdup_tuning_get.argtypes = [P, I, P, P]
     lib.svdup_tuning_set.argtypes = [P, I, I, I]
+    lib.svdup_tuning_get_tile.argtypes = [P, I, P]
+    lib.svdup_tuning_set_tile.argtypes = [P, I, I]
     S_T = ctypes.c_size_t
     lib.svdup_update_workspace.argtypes = [P, I, I, D, I, ctypes.POINTER(S_T)]
     lib.svdup_server_create.argtypes = [I, I, S_T, D, I, ctypes.POINTER(P)]
@@ -255,6 +257,17 @@ class Handle:
         _check(load().svdup_tuning_get(self._h, int(mode), ctypes.byref(a), ctypes.byref(b)),
                "svdup_tuning_get")
         return a.value, b.value
+
+    def tile_tuning(self, mode: int = FP64) -> int:
+        """Smallest N at which the mixed dense product uses 128-column output tiles."""
+        a = ctypes.c_int()
+        _check(load().svdup_tuning_get_tile(self._h, int(mode), ctypes.byref(a)),
+               "svdup_tuning_get_tile")
+        return a.value
+
+    def set_tile_tuning(self, mode: int, dense_tile128_min: int):
+        _check(load().svdup_tuning_set_tile(self._h, int(mode), int(dense_tile128_min)),
+               "svdup_tuning_set_tile")
 
     def set_tuning(self, mode: int, dense_max: int, leaf128_min: int):
         _check(load().svdup_tuning_set(self._h, int(mode), int(dense_max), int(leaf128_min)),

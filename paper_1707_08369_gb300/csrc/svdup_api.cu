@@ -78,6 +78,7 @@ struct svdup_ctx {
   // product-path choices (set by svdup_autotune; defaults below): index 0 FP64, 1 mixed
   int dense_max[2];   // N <= dense_max: dense Cauchy product (no far field)
   int leaf128_min[2]; // N >= leaf128_min: leaves of 128 poles, else 64
+  int dense_w128_min[2];  // dense products with N >= this: 128-column output tiles, else 64
   // the right-hand problem of an update runs on `side`, beside the left-hand one; the
   // products of each side run on prod[0] (U) and prod[1] (V)
   cudaStream_t side;   // the right-hand solves (high priority)
@@ -188,13 +189,17 @@ constexpr int kDefaultLeaf128MinTree = 1 << 30;
 
 int mode_index(int mode) { return (mode & SVDUP_MODE_MASK) == SVDUP_FP64 ? 0 : 1; }
 
-int leaf_size(const svdup_ctx* h, int N, int mode) {
-  return N >= h->leaf128_min[mode_index(mode)] ? 128 : 64;
-}
-
 bool use_dense(const svdup_ctx* h, int N, int mode) {
   if (mode & SVDUP_DENSE) return true;
   return N <= h->dense_max[mode_index(mode)];
+}
+
+// Leaf size, which is also the output tile width of the mixed dense product (the dense
+// product lists every leaf as near): the far field's choice, or the dense one.
+int leaf_size(const svdup_ctx* h, int N, int mode) {
+  const int i = mode_index(mode);
+  if (use_dense(h, N, mode)) return N >= h->dense_w128_min[i] ? 128 : 64;
+  return N >= h->leaf128_min[i] ? 128 : 64;
 }
 
 // mixed: P = 16 nodes (the split products' K granularity; 5^-16 is far below the FP32
@@ -668,6 +673,7 @@ svdup_ctx* lane_create(const svdup_ctx* parent) {
   for (int i = 0; i < 2; i++) {
     l->dense_max[i] = parent->dense_max[i];
     l->leaf128_min[i] = parent->leaf128_min[i];
+    l->dense_w128_min[i] = parent->dense_w128_min[i];
   }
   return l;
 }
@@ -850,6 +856,7 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
   for (int i = 0; i < 2; i++) {
     h->dense_max[i] = kDefaultDenseMax;
     h->leaf128_min[i] = kDefaultLeaf128Min;
+    h->dense_w128_min[i] = kDefaultLeaf128Min;
   }
   h->leaf128_min[0] = kDefaultLeaf128MinTree;  // FP64: the hierarchy keeps leaves small
   const char* mi = getenv("SVDUP_SECULAR_MAXIT");
@@ -1485,6 +1492,7 @@ int svdup_autotune(svdup_t h, int mode, int nmax) {
   if (set_device(h)) return SVDUP_ECUDA;
   const int i = mode_index(mode);
   const int keep_dense = h->dense_max[i], keep_leaf = h->leaf128_min[i];
+  const int keep_w = h->dense_w128_min[i];
   int nlim = 256;
   while (nlim * 2 <= nmax) nlim *= 2;
   const size_t maxN = (size_t)nlim;
@@ -1501,18 +1509,23 @@ int svdup_autotune(svdup_t h, int mode, int nmax) {
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (!rc && (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess))
     rc = SVDUP_ECUDA;
-  int dense_max = 0, leaf128_min = 1 << 30;
+  int dense_max = 0, leaf128_min = 1 << 30, dense_w128_min = 1 << 30;
   bool dense_lost = false;
+  // the mixed dense product has a second tile shape (128-column output tiles)
+  const int ncand = is_mixed(mode) ? 4 : 3;
   for (int N = 256; !rc && N <= nlim; N *= 2) {
     launch_fill_random(h->stream, N, N, X, d, z, 0x5eedULL + (unsigned long long)N);
-    // candidates: 0 dense, 1 far field with 64-pole leaves, 2 with 128-pole leaves
+    // candidates: 0 dense (64-column tiles), 1 far field with 64-pole leaves, 2 with
+    // 128-pole leaves, 3 dense with 128-column tiles (mixed modes)
     float best = 1e30f;
     int best_c = 0;
-    float tc[3] = {0, 0, 0};
-    for (int c = 0; c < 3 && !rc; c++) {
-      h->dense_max[i] = (c == 0) ? N : 0;
+    float tc[4] = {0, 0, 0, 0};
+    for (int c = 0; c < ncand && !rc; c++) {
+      const bool dense = (c == 0 || c == 3);
+      h->dense_max[i] = dense ? N : 0;
       h->leaf128_min[i] = (c == 2) ? 1 : (1 << 30);
-      const int m = mode | (c == 0 ? SVDUP_DENSE : 0);
+      h->dense_w128_min[i] = (c == 3) ? 1 : (1 << 30);
+      const int m = mode | (dense ? SVDUP_DENSE : 0);
       float best_t = 1e30f;
       for (int rep = 0; rep < 3 && !rc; rep++) {  // first run warms the workspace
         cudaEventRecord(t0, h->stream);
@@ -1527,9 +1540,10 @@ int svdup_autotune(svdup_t h, int mode, int nmax) {
       if (best_t < best) { best = best_t; best_c = c; }
     }
     if (rc) break;
-    if (best_c == 0 && !dense_lost) dense_max = N;
+    if ((best_c == 0 || best_c == 3) && !dense_lost) dense_max = N;
     else dense_lost = true;
     if (tc[2] < tc[1] && N < leaf128_min) leaf128_min = N;
+    if (ncand == 4 && tc[3] < tc[0] && N < dense_w128_min) dense_w128_min = N;
   }
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
@@ -1537,10 +1551,24 @@ int svdup_autotune(svdup_t h, int mode, int nmax) {
   if (rc) {
     h->dense_max[i] = keep_dense;
     h->leaf128_min[i] = keep_leaf;
+    h->dense_w128_min[i] = keep_w;
     return rc;
   }
   h->dense_max[i] = dense_max;
   h->leaf128_min[i] = leaf128_min;
+  h->dense_w128_min[i] = dense_w128_min;
+  return SVDUP_OK;
+}
+
+int svdup_tuning_get_tile(svdup_t h, int mode, int* dense_tile128_min) {
+  if (!h || !mode_ok(mode & SVDUP_MODE_MASK) || !dense_tile128_min) return SVDUP_EINVAL;
+  *dense_tile128_min = h->dense_w128_min[mode_index(mode)];
+  return SVDUP_OK;
+}
+
+int svdup_tuning_set_tile(svdup_t h, int mode, int dense_tile128_min) {
+  if (!h || !mode_ok(mode & SVDUP_MODE_MASK) || dense_tile128_min < 1) return SVDUP_EINVAL;
+  h->dense_w128_min[mode_index(mode)] = dense_tile128_min;
   return SVDUP_OK;
 }
 

@@ -152,3 +152,23 @@ def test_mixed_rejects_unsupported_modes(sv, hnd):
         with pytest.raises(sv.SvdupError) as ei:
             hnd.update(U, S, V, a, dev(np.ones(4)), mode=mode)
         assert ei.value.code == sv.EINVAL
+
+
+@pytest.mark.parametrize("mode_name", MODES)
+def test_dense_product_tile_widths_agree(sv, orc, mode_name):
+    """The dense mixed product has two output-tile widths (64 and 128 columns) that the
+    autotuner chooses between; both give the oracle's product within the mode's bound."""
+    g = np.random.default_rng(61)
+    N, rows = 300, 200
+    d = g.uniform(0, 1, N); z = g.standard_normal(N); rho = 1.1
+    X = wl.haar(N, g)[:rows, :N]
+    lam_o, Y_o = orc.rank_one_update_z(X, d, z, rho)
+    h = sv.Handle(0)
+    try:
+        mode = getattr(sv, mode_name)
+        for w128 in (1 << 30, 1):
+            h.set_tile_tuning(mode, w128)
+            _, Y_g = h.cauchy_product(devF(X), dev(d), dev(z), rho, eps=1e-12, mode=mode | sv.DENSE)
+            assert np.abs(Y_g.cpu().numpy() - Y_o).max() <= TOLS[mode_name][0]
+    finally:
+        h.close()
