@@ -967,6 +967,24 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
             // 2^14 for any shared-memory address), so planes and K steps are additions.
             const uint64_t a0 = sdesc(sa, 128, sbo), b0 = sdesc(sb, 128, sbo);
             const uint64_t ap = t.aplane >> 4, bp = t.bplane >> 4;
+            if (mp.fp16 && STAGE != MS_CORR) {
+              // FP16 2-term split: (hi, lo) and (lo, hi) of every K step first, while the
+              // accumulator holds only their own sums, then (hi, hi), all in the K tile's
+              // accumulator (the tiles' scales differ, so every K tile is drained)
+              const int nks = t.kstep / 16;
+              for (int pass = 0; pass < 2; pass++)
+                for (int ks = 0; ks < nks; ks++) {
+                  const uint32_t acc = (q > 0 || pass > 0 || ks > 0) ? 1u : 0u;
+                  const uint64_t ka = a0 + (uint64_t)((ks >> 1) * 2) * ap + (uint64_t)((ks & 1) * 16);
+                  const uint64_t kb = b0 + (uint64_t)((ks >> 1) * 2) * bp + (uint64_t)((ks & 1) * 16);
+                  if (pass == 0) {
+                    umma_bf16(dA, ka, kb + bp, idesc, acc);
+                    umma_bf16(dA, ka + ap, kb, idesc, 1u);
+                  } else {
+                    umma_bf16(dA, ka, kb, idesc, acc);
+                  }
+                }
+            } else
             for (int ks = 0; ks < t.kstep / 16; ks++) {
               const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
               const uint32_t xacc = (t.first && q == 0 && ks == 0) ? 0u : 1u;
@@ -980,12 +998,6 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_umma(Eig e, FmmPlan f, MixP
                 // the correction X E / 2 is about |E| of X: one BF16 product (hi, hi)
                 // leaves an error of 2^-8 |E|
                 umma_bf16(dA, ka, kb, idesc, acc);
-              } else if (mp.fp16) {
-                // FP16 2-term split: (hi, hi) (hi, lo) (lo, hi) together in the K tile's
-                // accumulator (the tiles' scales differ, so every K tile is drained)
-                umma_bf16(dA, ka, kb, idesc, acc);
-                umma_bf16(dA, ka, kb + bp, idesc, 1u);
-                umma_bf16(dA, ka + ap, kb, idesc, 1u);
               } else {
                 // (A plane, B plane): hi.hi alone, then (hi, mid) (mid, hi) (hi, lo) (lo, hi)
                 // (mid, mid)
