@@ -30,7 +30,7 @@ def devF(x):
 
 
 # far field on (leaves of 128: seven K tiles per output item); dense (five leaves of 64):
-# both with more K tiles per CTA than the four accumulators, so the MMA issuer waits for
+# both with more K tiles per CTA than the three K-tile accumulators, so the MMA issuer waits for
 # a region that the stalled drains never release
 @pytest.mark.parametrize("rows,N", [(300, 2600), (130, 300)])
 def test_pipeline_timeout_is_reported_and_recoverable(sv, orc, rows, N):
