@@ -328,6 +328,22 @@ int svdup_tuning_set(svdup_t h, int mode, int dense_max, int leaf128_min);
 int svdup_tuning_get_tile(svdup_t h, int mode, int* dense_tile128_min);
 int svdup_tuning_set_tile(svdup_t h, int mode, int dense_tile128_min);
 
+/*
+ * Far-field form of the solve's own sums (Sec. 3.2's Loewner zhat and the column norms
+ * ||c_j|| with Q^T y, RankOneUpdate STEP 7; summed through App. D's interpolation FMM
+ * instead of directly, O(k p) instead of O(k^2) work), for the eigen-problems of this
+ * handle whose non-deflated size k is at least
+ *   kmin        where the direct sums run in FP64 (SVDUP_FP64, and the first solves of
+ *               the mixed modes, whose zhat forms the second solves' z): default 4096;
+ *   kmin_pairs  where they run in FP32 pairs (the second solves and the norms of the
+ *               mixed modes): default 12288.
+ * The defaults are the measured crossovers on GB300 (FP64 costs as much as about 60
+ * FP32 operations there, so the pair sums stay ahead up to larger k).  Values below 2048
+ * are raised to 2048; INT_MAX keeps the direct sums.  The far-field form agrees with the
+ * FP64 direct sums to about 1e-15 relative.
+ */
+int svdup_set_far_sums(svdup_t h, int kmin, int kmin_pairs);
+
 /* Bytes of workspace svdup_update needs on this handle for an m x n problem in `mode`
  * (the handle keeps the largest such workspace it has needed). */
 int svdup_update_workspace(svdup_t h, int m, int n, double eps, int mode, size_t* bytes);

@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
     lib.svdup_tuning_set.argtypes = [P, I, I, I]
     lib.svdup_tuning_get_tile.argtypes = [P, I, P]
     lib.svdup_tuning_set_tile.argtypes = [P, I, I]
+    lib.svdup_set_far_sums.argtypes = [P, I, I]
     S_T = ctypes.c_size_t
     lib.svdup_update_workspace.argtypes = [P, I, I, D, I, ctypes.POINTER(S_T)]
     lib.svdup_server_create.argtypes = [I, I, S_T, D, I, ctypes.POINTER(P)]
@@ -268,6 +269,10 @@ class Handle:
     def set_tile_tuning(self, mode: int, dense_tile128_min: int):
         _check(load().svdup_tuning_set_tile(self._h, int(mode), int(dense_tile128_min)),
                "svdup_tuning_set_tile")
+
+    def set_far_sums(self, kmin: int, kmin_pairs: int = None):
+        kp = kmin if kmin_pairs is None else kmin_pairs
+        _check(load().svdup_set_far_sums(self._h, int(kmin), int(kp)), "svdup_set_far_sums")
 
     def set_tuning(self, mode: int, dense_max: int, leaf128_min: int):
         _check(load().svdup_tuning_set(self._h, int(mode), int(dense_max), int(leaf128_min)),

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsvdup.so")
 SOURCES = ["svdup_api.cu", "svdup_solve.cu", "svdup_product.cu", "svdup_static.cu", "svdup_mixed.cu", "svdup_serve.cu",
-           "svdup_dfsum.cu", "svdup_tree.cu"]
+           "svdup_dfsum.cu", "svdup_tree.cu", "svdup_vfmm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

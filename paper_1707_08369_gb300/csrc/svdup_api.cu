@@ -78,6 +78,7 @@ struct svdup_ctx {
   // product-path choices (set by svdup_autotune; defaults below): index 0 FP64, 1 mixed
   int dense_max[2];   // N <= dense_max: dense Cauchy product (no far field)
   int leaf128_min[2]; // N >= leaf128_min: leaves of 128 poles, else 64
+  int vf_min, vf_min_pairs;  // Loewner and the norms: the far-field form from these k
   int dense_w128_min[2];  // dense products with N >= this: 128-column output tiles, else 64
   // the right-hand problem of an update runs on `side`, beside the left-hand one; the
   // products of each side run on prod[0] (U) and prod[1] (V)
@@ -163,6 +164,12 @@ Eig make_eig(Arena& ar, int N) {
   e.zf = ar.take<float2>(n);
   e.yf = ar.take<float2>(n);
   e.wf = ar.take<float2>(n);
+  e.vfmin = kVfDefault;
+  e.vfmin_pairs = kVfDefaultPairs;
+  if (N >= kVfMinK) {
+    e.vf = ar.take<double>(vf_doubles(N));
+    e.vfc = ar.take<int>(vf_ints(N));
+  }
   return e;
 }
 
@@ -669,6 +676,8 @@ svdup_ctx* lane_create(const svdup_ctx* parent) {
   l->ref_res = parent->ref_res;
   l->refine_tol = parent->refine_tol;
   l->maxit = parent->maxit;
+  l->vf_min = parent->vf_min;
+  l->vf_min_pairs = parent->vf_min_pairs;
   l->open_stage = -1;
   for (int i = 0; i < 2; i++) {
     l->dense_max[i] = parent->dense_max[i];
@@ -852,6 +861,8 @@ int svdup_create(svdup_t* out, int device, void* stream, unsigned flags) {
   h->stream = (cudaStream_t)stream;
   h->maxit = 64;
   h->refine_tol = 1e-6;
+  h->vf_min = kVfDefault;
+  h->vf_min_pairs = kVfDefaultPairs;
   h->open_stage = -1;
   for (int i = 0; i < 2; i++) {
     h->dense_max[i] = kDefaultDenseMax;
@@ -1027,6 +1038,8 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
   if (rc) return rc;
   Arena ar = {h->ws, 0};
   UpdateWs u = layout_update(ar, m, n, eps, leaf, mixed, is_fp16(mode), refine);
+  u.E1.vfmin = u.E2.vfmin = u.E3.vfmin = u.E4.vfmin = h->vf_min;
+  u.E1.vfmin_pairs = u.E2.vfmin_pairs = u.E3.vfmin_pairs = u.E4.vfmin_pairs = h->vf_min_pairs;
   cudaStream_t st = h->stream;
 
   // STEP 1 (rewritten): p = U^T a, q = V^T b, alpha, beta
@@ -1292,6 +1305,8 @@ int svdup_rank_one_eig(svdup_t h, int N, const double* d, const double* z, doubl
   if (rc) return rc;
   Arena ar = {h->ws, 0};
   Eig e = make_eig(ar, N);
+  e.vfmin = h->vf_min;
+  e.vfmin_pairs = h->vf_min_pairs;
   double* rhod = ar.take<double>(1);
   cudaStream_t st = h->stream;
   if (cudaMemcpyAsync(rhod, &rho, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -1342,6 +1357,8 @@ int svdup_cauchy_product(svdup_t h, int rows, int N, const double* X, int ldx, c
   auto lay = [&](Arena& ar, Eig* e, double** Xw, double** Xs, FmmPlan* f, MixPlan* mp,
                  double** rhod) {
     *e = make_eig(ar, N);
+    e->vfmin = h->vf_min;
+    e->vfmin_pairs = h->vf_min_pairs;
     *rhod = ar.take<double>(1);
     *Xw = ar.take<double>((size_t)rows * N);
     *Xs = mixed ? nullptr : ar.take<double>((size_t)rows * N);
@@ -1569,6 +1586,13 @@ int svdup_tuning_get_tile(svdup_t h, int mode, int* dense_tile128_min) {
 int svdup_tuning_set_tile(svdup_t h, int mode, int dense_tile128_min) {
   if (!h || !mode_ok(mode & SVDUP_MODE_MASK) || dense_tile128_min < 1) return SVDUP_EINVAL;
   h->dense_w128_min[mode_index(mode)] = dense_tile128_min;
+  return SVDUP_OK;
+}
+
+int svdup_set_far_sums(svdup_t h, int kmin, int kmin_pairs) {
+  if (!h || kmin < 1 || kmin_pairs < 1) return SVDUP_EINVAL;
+  h->vf_min = kmin < kVfMinK ? kVfMinK : kmin;
+  h->vf_min_pairs = kmin_pairs < kVfMinK ? kVfMinK : kmin_pairs;
   return SVDUP_OK;
 }
 

@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(1024) k_df_prep(Eig e, const double* __restric
                                                   const double* __restrict__ xfinal) {
   __shared__ int sx[4];
   const int k = e.kp[0];
+  if (!xfinal && e.vf && k >= e.vfmin_pairs) return;  // the norms take the far-field form
   if (threadIdx.x < 4) sx[threadIdx.x] = -1100;
   __syncthreads();
   int mE = -1100, mZ = -1100, mY = -1100, mW = -1100;
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(1024) k_df_prep(Eig e, const double* __restric
 __global__ void __launch_bounds__(256) k_norms_df(Eig e, const double* __restrict__ ysorted,
                                                   double* out_final, int keep_inv) {
   const int k = e.kp[0];
+  if (e.vf && k >= e.vfmin_pairs) return;  // the far-field form (svdup_vfmm.cu)
   const int E = e.fsc[0], Z = e.fsc[1], Y = e.fsc[2];
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(256) k_apply_q_df(Eig e, const double* __restr
 // root's are FP64.
 __global__ void __launch_bounds__(256) k_loewner_df(Eig e) {
   const int k = e.kp[0];
+  if (e.vf && k >= e.vfmin_pairs) return;  // the far-field form (svdup_vfmm.cu)
   const double rho = e.rhop[0];
   const double R = fabs(rho);
   const int lane = threadIdx.x & 31;
@@ -248,6 +251,7 @@ __global__ void __launch_bounds__(256) k_loewner_df(Eig e) {
 }
 
 void launch_loewner_df(cudaStream_t st, Eig e) {
+  launch_vf_loewner(st, e, e.vfmin_pairs);  // the far-field form when k >= vfmin_pairs
   k_loewner_df<<<(e.N + 7) / 8, 256, 0, st>>>(e);  // one warp per pole
   SVDUP_COUNT_LAUNCH();
 }

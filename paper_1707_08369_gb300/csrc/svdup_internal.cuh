@@ -72,6 +72,16 @@ __device__ __forceinline__ double rsqrt64(double x) {
   return fma(0.5 * y, h, y);
 }
 
+// Exponent bookkeeping for long FP64 products: x = m 2^e with m in [1, 2) after
+// renorm (bit fields only; a zero stays zero).
+__device__ __forceinline__ void renorm64(double& m, int& e) {
+  const long long b = __double_as_longlong(m);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return;
+  m = __longlong_as_double((b & ~(0x7ffll << 52)) | (1023ll << 52));
+  e += ex - 1023;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -163,6 +173,14 @@ struct Eig {
   float2* zf;
   float2* yf;
   float2* wf;
+  // the far field of the solve's own sums (svdup_vfmm.cu): per-box geometry, moments,
+  // local values and leaf locals (vf), and the upward pass's arrival counters (vfc)
+  double* vf;
+  int* vfc;
+  // the far-field form replaces the FP64 direct sums for k >= vfmin and the FP32-pair
+  // direct sums for k >= vfmin_pairs (vf is allocated for N >= kVfMinK)
+  int vfmin;
+  int vfmin_pairs;
 };
 
 // Column mapping of a product's output: physical column of final index q is
@@ -276,10 +294,38 @@ __host__ __device__ inline int tree_off(int Lmax, int h) {
   for (int i = 0; i < h; i++) o += tree_nb(Lmax, i);
   return o;
 }
-__host__ inline int tree_levels(int Lmax) {
+__host__ __device__ inline int tree_levels(int Lmax) {
   int h = 1;
   while (tree_nb(Lmax, h - 1) > 2) h++;
   return h;
+}
+
+// The far field of Loewner's zhat and of the column norms (svdup_vfmm.cu): leaves of
+// kVfLeaf consecutive indices (the last takes the remainder), kVfP Chebyshev nodes per
+// box, used when k >= kVfMinK.  Layout of Eig::vf for a problem of size N, with
+// Lmax + 1 = max(1, N / kVfLeaf) leaves at most: geometry (4 per box: source centre and
+// radius, target centre and radius), moments and local values (2 sets of kVfP per box,
+// the local values in kVfParts partial sums), leaf locals (2 sets of kVfP per leaf), each
+// leaf's part of the last root's sums (2), the Chebyshev nodes and barycentric weights;
+// Eig::vfc holds the arrival counters (one per box) and each leaf's near list.
+constexpr int kVfP = 28;
+constexpr int kVfLeaf = 64;
+constexpr int kVfMinK = 2048;
+constexpr int kVfDefault = 4096;        // against the FP64 direct sums (measured crossover)
+constexpr int kVfDefaultPairs = 12288;  // against the FP32-pair direct sums
+constexpr int kVfParts = 4;     // translations of a box split over this many warps
+constexpr int kVfNearMax = 64;  // near leaves listed per leaf (more: every pole is near)
+__host__ __device__ inline int vf_lmax(int N) { return (N / kVfLeaf > 1 ? N / kVfLeaf : 1) - 1; }
+__host__ __device__ inline int vf_tot(int N) {
+  const int L = vf_lmax(N);
+  return tree_off(L, tree_levels(L));
+}
+__host__ __device__ inline size_t vf_doubles(int N) {
+  return 2 * (size_t)kVfP + (size_t)vf_tot(N) * (4 + 2 * kVfP * (1 + kVfParts)) +
+         (size_t)(vf_lmax(N) + 1) * 2 * (kVfP + 1);
+}
+__host__ __device__ inline size_t vf_ints(int N) {
+  return (size_t)vf_tot(N) + (size_t)(vf_lmax(N) + 1) * (kVfNearMax + 1);
 }
 
 // Mixed-precision (split BF16) form of the product on the tensor cores.  Every operand
@@ -371,6 +417,11 @@ void launch_secular_direct(cudaStream_t st, Eig e, int k, const double* d, const
 void launch_merge(cudaStream_t st, Eig e);
 void launch_loewner(cudaStream_t st, Eig e);
 void launch_loewner_df(cudaStream_t st, Eig e);
+// Far-field forms (svdup_vfmm.cu), for k >= kmin (every kernel returns at once below):
+// Loewner's zhat, and the column norms with Q^T y (ysorted may be null).
+void launch_vf_loewner(cudaStream_t st, Eig e, int kmin);
+void launch_vf_norms(cudaStream_t st, Eig e, int kmin, const double* ysorted, double* out_final,
+                     bool keep_inv);
 // pairs = true: the sums in double-float arithmetic (svdup_dfsum.cu), for outputs that
 // need FP32 accuracy only (the mixed mode's vectors and signs)
 // keep_inv: the stored 1/||c_j|| stay as they are (the norms are recomputed for the

@@ -1725,18 +1725,9 @@ void launch_merge(cudaStream_t st, Eig e) {
 // operations per factor.  One warp per index i; differences mu_j - d_i come from the
 // offsets.
 // ---------------------------------------------------------------------------
-// Exponent bookkeeping for long FP64 products: x = m 2^e with m in [1, 2) after
-// renorm (bit fields only; a zero stays zero).
-__device__ __forceinline__ void renorm64(double& m, int& e) {
-  const long long b = __double_as_longlong(m);
-  const int ex = (int)((b >> 52) & 0x7ff);
-  if (ex == 0) return;
-  m = __longlong_as_double((b & ~(0x7ffll << 52)) | (1023ll << 52));
-  e += ex - 1023;
-}
-
 __global__ void k_loewner(Eig e) {
   const int k = e.kp[0];
+  if (e.vf && k >= e.vfmin) return;  // the far-field form (svdup_vfmm.cu)
   const double rho = e.rhop[0];
   const double R = fabs(rho);
   const int lane = threadIdx.x & 31;
@@ -1776,6 +1767,7 @@ __global__ void k_loewner(Eig e) {
 }
 
 void launch_loewner(cudaStream_t st, Eig e) {
+  launch_vf_loewner(st, e, e.vfmin);  // the far-field form when k >= vfmin
   k_loewner<<<secular_blocks(e.N), 256, 0, st>>>(e);
   SVDUP_COUNT_LAUNCH();
 }
@@ -1788,6 +1780,7 @@ void launch_loewner(cudaStream_t st, Eig e) {
 // ---------------------------------------------------------------------------
 __global__ void k_norms(Eig e, const double* __restrict__ ysorted, double* out_final, int keep_inv) {
   const int k = e.kp[0];
+  if (e.vf && k >= e.vfmin) return;  // the far-field form (svdup_vfmm.cu)
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < k; j += warps) {
@@ -1819,6 +1812,8 @@ __global__ void k_defl_copy(Eig e, const double* __restrict__ ysorted, double* o
 
 void launch_norms(cudaStream_t st, Eig e, const double* ysorted, double* out_final, bool pairs,
                   bool keep_inv) {
+  // the far-field form when k >= vfmin (FP64) or vfmin_pairs (FP32 pairs)
+  launch_vf_norms(st, e, pairs ? e.vfmin_pairs : e.vfmin, ysorted, out_final, keep_inv);
   if (pairs) {
     launch_norms_df(st, e, ysorted, out_final, secular_blocks(e.N), keep_inv);
   } else {
