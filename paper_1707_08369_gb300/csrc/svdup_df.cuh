@@ -114,6 +114,38 @@ __device__ __forceinline__ double df_to_f64(Df a, int s) {
   return (widen(a.hi) + widen(a.lo)) * pow2d(s);
 }
 
+// x 2^s in FP64 by the bit fields, for x a normal FP32 number or a zero and a result in
+// the FP64 normal range (ok is cleared otherwise): no FP64 operation.
+__device__ __forceinline__ double widen_scaled(float x, int s, bool& ok) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t mag = u & 0x7fffffffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (mag == 0u) return __longlong_as_double((long long)sign);
+  const int e = (int)(mag >> 23) + 896 + s;  // FP32 bias 127 -> FP64 bias 1023
+  if (mag < 0x00800000u || mag >= 0x7f800000u || e < 1 || e > 2046) {
+    ok = false;
+    return 0.0;
+  }
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)e << 52) | ((unsigned long long)(mag & 0x7fffffu) << 29)));
+}
+
+// A pair times 2^s in FP64: both parts scaled by their exponent fields and added (one
+// FP64 operation; the same value as df_to_f64(a, 0) 2^s whenever no part leaves the
+// normal ranges, which then takes the multiplications).
+__device__ __forceinline__ double df_to_f64_scaled(Df a, int s) {
+  bool ok = true;
+  const double h = widen_scaled(a.hi, s, ok), l = widen_scaled(a.lo, s, ok);
+  if (ok) return h + l;
+  const int q = s / 2;
+  return df_to_f64(a, 0) * pow2d(max(-1022, min(1023, q))) * pow2d(max(-1022, min(1023, s - q)));
+}
+
+// FP64 finiteness by the exponent field (an integer test, no FP64 operation).
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 __device__ __forceinline__ Df df_shfl_xor(Df a, int o) {
   return Df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }

@@ -942,7 +942,11 @@ void launch_deflate(cudaStream_t st, Eig e, int* status) {
 // of the root are modelled by P_L + Q_L / (d_left - mu), those right of it by
 // P_R + Q_R / (d_right - mu), each matching value and slope at the current iterate;
 // the model's root in the bracket is one quadratic.  The bracket is kept from the
-// signs of w and a model step that leaves it is replaced by bisection.
+// signs of w and a model step that leaves it is replaced by bisection.  The quadratic's
+// square root and divisions go through rsqrt64 and rcp64 (a few FP64 operations each
+// instead of correctly rounded sequences): a step needs no last-bit accuracy, and the
+// convergence tests and the bracket decide the root.  Finiteness is tested on the bit
+// fields.
 // ---------------------------------------------------------------------------
 struct SecSums {
   double psiL, dpsiL, psiR, dpsiR, asum;
@@ -1011,10 +1015,7 @@ constexpr int kSqMinK = 2048;  // smaller problems use the direct FP64 sums only
 constexpr double kSecTolPairs = 0x1p-42;
 
 // x 2^s for a pair, in FP64, applied in two halves (each inside the FP64 range).
-__device__ __forceinline__ double pair_scaled(Df a, int s) {
-  const int h = s / 2;
-  return df_to_f64(a, 0) * pow2d(max(-1022, min(1023, h))) * pow2d(max(-1022, min(1023, s - h)));
-}
+__device__ __forceinline__ double pair_scaled(Df a, int s) { return df_to_f64_scaled(a, s); }
 
 // z^2 / delta and z^2 / delta^2 in pairs for delta = dd - tau (dd = d_i - d_o exact in
 // FP64; ntau = -tau 2^-E; z2 = z^2 2^-Z): results scaled by 2^(E - Z) and 2^(2E - Z).
@@ -1036,37 +1037,25 @@ __device__ __forceinline__ int lower_bound_d(const double* a, int n, double v) {
 // Roots whose bracket is wider than the rest of their box -- the isolated largest
 // poles, such as the large eigenvalues earlier updates have added, among the poles of
 // a solve -- would stretch their box over the spectrum (and every pole into its near
-// field).  From each end, while one bracket gap is more than half the span of the next
-// kSqLeaf roots, every root up to that gap is solved alone by one block with direct
-// sums (at most kSqMaxWide per end), as is the last root (beyond all poles).  The boxes
-// of kSqLeaf roots cover roots first .. last; k_sq_boxes stores the layout in sqf.
-constexpr int kSqMaxWide = 16;
+// field).  From each end, while the end box of kSqLeaf roots has more than kSqNearPeel
+// poles within two of its radii, its outermost root is taken out and solved alone by one
+// warp with direct sums (at most kSqMaxWide per end; a chain of updates adds one such
+// pole per update), as is the last root (beyond all poles).  The boxes of kSqLeaf roots
+// cover roots first .. last; k_sq_boxes stores the layout in sqf.
+constexpr int kSqMaxWide = 64;
+constexpr int kSqNearPeel = 6 * kSqLeaf;
 
 __device__ void sq_layout(const double* __restrict__ dc, int k, int* first, int* last) {
   int f = 0, l = k - 2;
   if (k >= kSqMinK) {
-    while (f < kSqMaxWide) {
-      const double span = dc[f + kSqLeaf] - dc[f];
-      int g = f;
-      double gmax = -1.0;
-      for (int j = f; j < f + kSqLeaf; j++) {
-        const double gap = dc[j + 1] - dc[j];
-        if (gap > gmax) { gmax = gap; g = j; }
-      }
-      if (!(gmax > 0.5 * span) || g + 1 > kSqMaxWide) break;
-      f = g + 1;
-    }
-    while (k - 2 - l < kSqMaxWide) {
-      const double span = dc[l + 1] - dc[l + 1 - kSqLeaf];
-      int g = l;
-      double gmax = -1.0;
-      for (int j = l; j > l - kSqLeaf; j--) {
-        const double gap = dc[j + 1] - dc[j];
-        if (gap > gmax) { gmax = gap; g = j; }
-      }
-      if (!(gmax > 0.5 * span) || k - 1 - g > kSqMaxWide) break;
-      l = g - 1;
-    }
+    // the box of roots a .. a + kSqLeaf - 1 spans [d_a, d_{a+kSqLeaf}]; it is too wide
+    // when the poles within two radii of it are more than kSqNearPeel
+    auto wide = [&](int a) {
+      const double lo = dc[a], hi = dc[a + kSqLeaf], r = 0.5 * (hi - lo);
+      return lower_bound_d(dc, k, hi + 2.0 * r) - lower_bound_d(dc, k, lo - 2.0 * r) > kSqNearPeel;
+    };
+    while (f < kSqMaxWide && f + 2 * kSqLeaf <= l && wide(f)) f++;
+    while (k - 2 - l < kSqMaxWide && l - 2 * kSqLeaf >= f && wide(l + 1 - kSqLeaf)) l--;
   }
   *first = f;
   *last = l;
@@ -1183,96 +1172,190 @@ __global__ void k_sq_nodes(const double* __restrict__ dc, const float2* __restri
   }
 }
 
-struct FarSums {
-  const double* dc;
-  const double* z2c;
+// ---------------------------------------------------------------------------
+// Two roots per warp (far-field form).  A root's iteration is scalar FP64 arithmetic
+// (the rational model, its quadratic, the bracket), the same for all lanes of the warp
+// that iterates it; on GB300 an FP64 warp instruction costs the same whatever its active
+// lanes, and this scalar work, not the sums, filled the FP64 pipe.  So each group of
+// kSecG = 16 lanes iterates its own root: the scalar work is shared by two roots, and the
+// sums of each root (its near poles and the far field's 26 nodes) are split over its
+// lanes and reduced within the group (xor shuffles below kSecG stay inside it).  The
+// steps are those of secular_root; the groups iterate in lockstep, a group that has
+// converged keeps its result and idles until the other has.  (Four roots of 8 lanes
+// halve the FP64 instructions again, but leave too few warps per SM to hide the
+// dependent FP64 latency, and a warp waits for the slowest of four roots.)
+// ---------------------------------------------------------------------------
+constexpr int kSecG = 16;                           // lanes per root
+constexpr int kSecRoots = 32 / kSecG;                // roots per warp
+constexpr int kSecNQ = (kSqP + kSecG - 1) / kSecG;  // far-field nodes per lane
+
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = kSecG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ Df group_df_sum(Df a) {
+#pragma unroll
+  for (int o = kSecG / 2; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
+  return a;
+}
+__device__ __forceinline__ int group_max(int v) {
+#pragma unroll
+  for (int o = kSecG / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ bool group_any(bool p, int g) {
+  return ((__ballot_sync(0xffffffffu, p) >> (kSecG * g)) & ((1ull << kSecG) - 1ull)) != 0u;
+}
+__device__ __forceinline__ bool warp_all(bool p) { return __all_sync(0xffffffffu, p); }
+
+// One box's far-field data for the root of this lane's group.
+struct FarBox {
   int n0, n1;
   double base, r;
-  const double* vals;  // 4 x kSqP node values of this box
-  const double* sx;    // Chebyshev nodes (shared memory)
-  const double* sw;    // barycentric weights (shared memory)
-  const float2* z2f;   // z^2 2^-Z as pairs
+  const double* vals;
+};
+
+struct FarSumsG {
+  const double* dc;
+  const double* z2c;
+  const float2* z2f;
+  const double* sx;
+  const double* sw;
   int E, Z;
-  static constexpr double wtol = kSecTolPairs;
-  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
+  // The sums of FarSums for the group's root mu = d_o + tau in box fb; every lane of the
+  // group returns them.  sub: this lane's index in its group, g: the group.
+  __device__ SecSums operator()(const FarBox& fb, int o, double tau, int jsplit, int sub,
+                                int g) const {
     SecSums s = {0.0, 0.0, 0.0, 0.0, 0.0};
     const double dO = dc[o];
-    // Barycentric weights of the far field at the box coordinate of mu, in pairs (within
-    // the pair form's error budget): c_l = w_l / (y - x_l), normalised by their sum.
-    const double yh = (((dO - base) + tau) - r) * rcp64(r);
-    // node values beyond the pair range (exponent tests only): the FP64 form below
-    const bool big = lane < kSqP && max(max(exp2_of(vals[lane]), exp2_of(vals[kSqP + lane])),
-                                        max(exp2_of(vals[2 * kSqP + lane]),
-                                            exp2_of(vals[3 * kSqP + lane]))) > 120;
-    const bool f64far = __any_sync(0xffffffffu, big);
-    Df c = {0.f, 0.f};
-    int hit = 0;
-    if (lane < kSqP) {
-      const Df dfy = df_add(df_from_f64(yh, 0), df_neg(df_from_f64(sx[lane], 0)));
-      if (dfy.hi == 0.0f) hit = 1;
-      else c = df_mul(df_from_f64(sw[lane], 0), df_rcp(dfy));
+    const double* vals = fb.vals;
+    const double yh = (((dO - fb.base) + tau) - fb.r) * rcp64(fb.r);
+    bool big = false;
+    for (int q = sub; q < kSqP; q += kSecG)
+      big |= max(max(exp2_of(vals[q]), exp2_of(vals[kSqP + q])),
+                 max(exp2_of(vals[2 * kSqP + q]), exp2_of(vals[3 * kSqP + q]))) > 120;
+    const bool f64far = group_any(big, g);
+    // barycentric weights of the nodes this lane holds (sub, sub + 8, ...)
+    Df c[kSecNQ];
+    int hq = -1;
+#pragma unroll
+    for (int qi = 0; qi < kSecNQ; qi++) {
+      const int q = sub + kSecG * qi;
+      c[qi] = Df{0.0f, 0.0f};
+      if (q < kSqP) {
+        const Df dfy = df_add(df_from_f64(yh, 0), df_neg(df_from_f64(sx[q], 0)));
+        if (dfy.hi == 0.0f) hq = q;
+        else c[qi] = df_mul(df_from_f64(sw[q], 0), df_rcp(dfy));
+      }
     }
-    const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    if (hm) {  // mu sits exactly on a node
-      c = (lane == __ffs(hm) - 1) ? Df{1.0f, 0.0f} : Df{0.0f, 0.0f};
+    const int hm = group_max(hq);
+    if (hm >= 0) {  // mu sits exactly on a node
+#pragma unroll
+      for (int qi = 0; qi < kSecNQ; qi++)
+        c[qi] = (sub + kSecG * qi == hm) ? Df{1.0f, 0.0f} : Df{0.0f, 0.0f};
     } else {
-      c = df_mul(c, df_rcp(df_warp_sum(c)));
+      Df cs = {0.0f, 0.0f};
+#pragma unroll
+      for (int qi = 0; qi < kSecNQ; qi++) cs = df_add(cs, c[qi]);
+      const Df ic = df_rcp(group_df_sum(cs));
+#pragma unroll
+      for (int qi = 0; qi < kSecNQ; qi++) c[qi] = df_mul(c[qi], ic);
     }
     Df fL = {0.f, 0.f}, fdL = {0.f, 0.f}, fR = {0.f, 0.f}, fdR = {0.f, 0.f};
-    if (lane < kSqP) {  // far-left terms are negative, far-right positive
-      fL = df_mul(c, df_from_f64(vals[lane], 0));
-      fdL = df_mul(c, df_from_f64(vals[kSqP + lane], 0));
-      fR = df_mul(c, df_from_f64(vals[2 * kSqP + lane], 0));
-      fdR = df_mul(c, df_from_f64(vals[3 * kSqP + lane], 0));
+#pragma unroll
+    for (int qi = 0; qi < kSecNQ; qi++) {
+      const int q = sub + kSecG * qi;
+      if (q < kSqP) {
+        fL = df_add(fL, df_mul(c[qi], df_from_f64(vals[q], 0)));
+        fdL = df_add(fdL, df_mul(c[qi], df_from_f64(vals[kSqP + q], 0)));
+        fR = df_add(fR, df_mul(c[qi], df_from_f64(vals[2 * kSqP + q], 0)));
+        fdR = df_add(fdR, df_mul(c[qi], df_from_f64(vals[3 * kSqP + q], 0)));
+      }
     }
     // near poles in pairs, the origin pole (offset -tau) in FP64
+    // (two accumulator sets per lane keep two terms in flight)
     const Df ntau = df_neg(df_from_f64(tau, E));
     Df pL = {0.f, 0.f}, dL = {0.f, 0.f}, pR = {0.f, 0.f}, dR = {0.f, 0.f};
-    for (int i = n0 + lane; i < n1; i += 32) {
-      if (i == o) continue;
-      Df t, dt;
-      const float2 z = z2f[i];
-      pair_term(dc[i] - dO, ntau, Df{z.x, z.y}, E, t, dt);
-      if (i <= jsplit) { pL = df_add(pL, t); dL = df_add(dL, dt); }
-      else { pR = df_add(pR, t); dR = df_add(dR, dt); }
+    Df qL = {0.f, 0.f}, eL = {0.f, 0.f}, qR = {0.f, 0.f}, eR = {0.f, 0.f};
+    for (int i = fb.n0 + sub; i < fb.n1; i += 2 * kSecG) {
+      if (i != o) {
+        Df t, dt;
+        const float2 z = z2f[i];
+        pair_term(dc[i] - dO, ntau, Df{z.x, z.y}, E, t, dt);
+        if (i <= jsplit) { pL = df_add(pL, t); dL = df_add(dL, dt); }
+        else { pR = df_add(pR, t); dR = df_add(dR, dt); }
+      }
+      const int i2 = i + kSecG;
+      if (i2 < fb.n1 && i2 != o) {
+        Df t, dt;
+        const float2 z = z2f[i2];
+        pair_term(dc[i2] - dO, ntau, Df{z.x, z.y}, E, t, dt);
+        if (i2 <= jsplit) { qL = df_add(qL, t); eL = df_add(eL, dt); }
+        else { qR = df_add(qR, t); eR = df_add(eR, dt); }
+      }
     }
-    double nL = pair_scaled(df_warp_sum(pL), Z - E), ndL = pair_scaled(df_warp_sum(dL), Z - 2 * E);
-    double nR = pair_scaled(df_warp_sum(pR), Z - E), ndR = pair_scaled(df_warp_sum(dR), Z - 2 * E);
-    if (!isfinite(nL + ndL + nR + ndR)) {  // a term left the FP32 range: this one in FP64
+    double nL = pair_scaled(group_df_sum(df_add(pL, qL)), Z - E);
+    double ndL = pair_scaled(group_df_sum(df_add(dL, eL)), Z - 2 * E);
+    double nR = pair_scaled(group_df_sum(df_add(pR, qR)), Z - E);
+    double ndR = pair_scaled(group_df_sum(df_add(dR, eR)), Z - 2 * E);
+    if (group_any(!(finite_bits(nL) && finite_bits(ndL) && finite_bits(nR) && finite_bits(ndR)), g)) {
+      // a term left the FP32 range: this root's near sums in FP64
       nL = ndL = nR = ndR = 0.0;
-      for (int i = n0 + lane; i < n1; i += 32) {
+      for (int i = fb.n0 + sub; i < fb.n1; i += kSecG) {
         if (i == o) continue;
         const double rc = rcp64((dc[i] - dO) - tau);
         const double t = z2c[i] * rc, dt = t * rc;
         if (i <= jsplit) { nL += t; ndL += dt; }
         else { nR += t; ndR += dt; }
       }
-      nL = warp_sum(nL);
-      ndL = warp_sum(ndL);
-      nR = warp_sum(nR);
-      ndR = warp_sum(ndR);
+      nL = group_sum(nL);
+      ndL = group_sum(ndL);
+      nR = group_sum(nR);
+      ndR = group_sum(ndR);
     }
     if (f64far) {
-      double cc = 0.0;
-      int h2 = 0;
-      if (lane < kSqP) {
-        const double d = yh - sx[lane];
-        if (d == 0.0) h2 = 1;
-        else cc = sw[lane] / d;
+      double cc[kSecNQ];
+      int h2 = -1;
+#pragma unroll
+      for (int qi = 0; qi < kSecNQ; qi++) {
+        const int q = sub + kSecG * qi;
+        cc[qi] = 0.0;
+        if (q < kSqP) {
+          const double d = yh - sx[q];
+          if (d == 0.0) h2 = q;
+          else cc[qi] = sw[q] / d;
+        }
       }
-      const unsigned hm2 = __ballot_sync(0xffffffffu, h2);
-      if (hm2) cc = (lane == __ffs(hm2) - 1) ? 1.0 : 0.0;
-      else cc = cc / warp_sum(cc);
-      const bool on = lane < kSqP;
-      s.psiL = warp_sum(on ? cc * vals[lane] : 0.0) + nL;
-      s.dpsiL = warp_sum(on ? cc * vals[kSqP + lane] : 0.0) + ndL;
-      s.psiR = warp_sum(on ? cc * vals[2 * kSqP + lane] : 0.0) + nR;
-      s.dpsiR = warp_sum(on ? cc * vals[3 * kSqP + lane] : 0.0) + ndR;
+      const int hm2 = group_max(h2);
+      double csum = 0.0;
+#pragma unroll
+      for (int qi = 0; qi < kSecNQ; qi++) {
+        if (hm2 >= 0) cc[qi] = (sub + kSecG * qi == hm2) ? 1.0 : 0.0;
+        csum += cc[qi];
+      }
+      const double icc = hm2 >= 0 ? 1.0 : 1.0 / group_sum(csum);
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+      for (int qi = 0; qi < kSecNQ; qi++) {
+        const int q = sub + kSecG * qi;
+        if (q < kSqP) {
+          const double w = cc[qi] * icc;
+          a0 += w * vals[q];
+          a1 += w * vals[kSqP + q];
+          a2 += w * vals[2 * kSqP + q];
+          a3 += w * vals[3 * kSqP + q];
+        }
+      }
+      s.psiL = group_sum(a0) + nL;
+      s.dpsiL = group_sum(a1) + ndL;
+      s.psiR = group_sum(a2) + nR;
+      s.dpsiR = group_sum(a3) + ndR;
     } else {
-      s.psiL = df_to_f64(df_warp_sum(fL), 0) + nL;
-      s.dpsiL = df_to_f64(df_warp_sum(fdL), 0) + ndL;
-      s.psiR = df_to_f64(df_warp_sum(fR), 0) + nR;
-      s.dpsiR = df_to_f64(df_warp_sum(fdR), 0) + ndR;
+      s.psiL = df_to_f64_scaled(group_df_sum(fL), 0) + nL;
+      s.dpsiL = df_to_f64_scaled(group_df_sum(fdL), 0) + ndL;
+      s.psiR = df_to_f64_scaled(group_df_sum(fR), 0) + nR;
+      s.dpsiR = df_to_f64_scaled(group_df_sum(fdR), 0) + ndR;
     }
     {
       const double ri = -rcp64(tau);
@@ -1285,81 +1368,112 @@ struct FarSums {
   }
 };
 
-// The sums of one root by a whole block, for a root iterated by warp 0 alone (the
-// block's other warps only help evaluate): warp 0 posts (o, tau, jsplit) and meets the
-// helpers at named barrier 1; every warp adds its share of the poles into part[4][32];
-// at barrier 2 warp 0 collects them.  The helpers leave when warp 0 posts cmd = 0.
-struct LedSums {
+// secular_root's steps for a root j < k - 1 per group (active: the group has a root);
+// returns 0 on convergence.  Every lane of the warp must call it.
+__device__ int secular_root_group(const FarSumsG& sums, const FarBox& fb,
+                                  const double* __restrict__ dc, double R, int j, bool active,
+                                  int maxit, int sub, int g, int* o_out, double* tau_out) {
+  const double wtol = kSecTolPairs;
+  const double gap = dc[j + 1] - dc[j];
+  int o = j;
+  double tau = 0.5 * gap, lo, hi, aL, aR;
+  SecSums sm = sums(fb, o, tau, j, sub, g);
+  double w = 1.0 + R * (sm.psiL + sm.psiR);
+  if (w >= 0.0) {  // root in (d_j, midpoint]
+    o = j; lo = 0.0; hi = tau; aL = 0.0; aR = gap;
+  } else {          // root in (midpoint, d_{j+1}): measure from d_{j+1}
+    o = j + 1; tau = tau - gap; lo = tau; hi = 0.0; aL = -gap; aR = 0.0;
+  }
+  bool done = !active;
+  int out_o = o;
+  double out_t = tau;
+  for (int it = 0; it < maxit; it++) {
+    if (!done && (w == 0.0 || fabs(w) <= wtol * (1.0 + R * sm.asum))) {
+      done = true; out_o = o; out_t = tau;
+    }
+    if (warp_all(done)) break;
+    const double dL = aL - tau, dR = aR - tau;
+    const double QL = sm.dpsiL * dL * dL, PL = sm.psiL - sm.dpsiL * dL;
+    const double QR = sm.dpsiR * dR * dR, PR = sm.psiR - sm.dpsiR * dR;
+    const double c = 1.0 + R * (PL + PR);
+    const double A = c, B = c * (dL + dR) + R * (QL + QR), C = w * dL * dR;
+    const double disc = fmax(B * B - 4.0 * A * C, 0.0);
+    const double sq = disc > 0.0 ? disc * rsqrt64(disc) : 0.0;
+    const double eta = (B > 0.0) ? (2.0 * C) * rcp64(B + sq) : (B - sq) * rcp64(2.0 * A);
+    double tn = tau + eta;
+    if (!finite_bits(tn) || !(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (!done && (tn == tau || fabs(tn - tau) <= 2.0 * kU * fabs(tau))) {
+      done = true; out_o = o; out_t = tn;
+    }
+    if (warp_all(done)) break;
+    const SecSums sn = sums(fb, o, done ? tau : tn, j, sub, g);
+    if (!done) {
+      tau = tn;
+      sm = sn;
+      w = 1.0 + R * (sm.psiL + sm.psiR);
+      if (w < 0.0) lo = tau; else hi = tau;
+      if (!(hi - lo > 2.0 * kU * fmax(fabs(lo), fabs(hi)))) { done = true; out_o = o; out_t = tau; }
+    }
+  }
+  *o_out = done ? out_o : o;
+  *tau_out = done ? out_t : tau;
+  return done ? 0 : 1;
+}
+
+// The sums of one root by one warp over every pole, in pairs as FarSumsG's near field,
+// the origin pole in FP64 (the special roots of the far-field form: the last root and
+// the wide roots).  Two accumulator sets per lane keep two terms in flight.
+struct WarpPairSums {
   const double* dc;
   const double* z2c;
   int k;
-  double* part;  // shared, 4 x 32
-  double* s_tau;
-  int* s_o;
-  int* s_js;
-  int* s_cmd;
-  const float2* z2f;  // the pair form (scales E, Z), as FarSums
+  const float2* z2f;  // the pair form (scales E, Z)
   int E, Z;
   static constexpr double wtol = kSecTolPairs;
-  __device__ static void bar(int id) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"((int)blockDim.x) : "memory");
-  }
-  __device__ void partial(int o, double tau, int jsplit) const {
+  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
     Df v[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    Df u[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const double dO = dc[o];
     const Df ntau = df_neg(df_from_f64(tau, E));
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-      if (i == o) continue;  // the origin pole: FP64, by warp 0
-      Df t, dt;
-      const float2 z = z2f[i];
-      pair_term(dc[i] - dO, ntau, Df{z.x, z.y}, E, t, dt);
-      if (i <= jsplit) { v[0] = df_add(v[0], t); v[1] = df_add(v[1], dt); }
-      else { v[2] = df_add(v[2], t); v[3] = df_add(v[3], dt); }
+    for (int i = lane; i < k; i += 64) {
+      if (i != o) {
+        Df t, dt;
+        const float2 z = z2f[i];
+        pair_term(dc[i] - dO, ntau, Df{z.x, z.y}, E, t, dt);
+        if (i <= jsplit) { v[0] = df_add(v[0], t); v[1] = df_add(v[1], dt); }
+        else { v[2] = df_add(v[2], t); v[3] = df_add(v[3], dt); }
+      }
+      const int i2 = i + 32;
+      if (i2 < k && i2 != o) {
+        Df t, dt;
+        const float2 z = z2f[i2];
+        pair_term(dc[i2] - dO, ntau, Df{z.x, z.y}, E, t, dt);
+        if (i2 <= jsplit) { u[0] = df_add(u[0], t); u[1] = df_add(u[1], dt); }
+        else { u[2] = df_add(u[2], t); u[3] = df_add(u[3], dt); }
+      }
     }
-    const int w = threadIdx.x >> 5;
+    double r[4];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const Df r = df_warp_sum(v[q]);
-      if ((threadIdx.x & 31) == 0) part[q * 32 + w] = pair_scaled(r, (q & 1) ? Z - 2 * E : Z - E);
-    }
-  }
-  // warp 0 only
-  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
-    if (lane == 0) { *s_o = o; *s_tau = tau; *s_js = jsplit; *s_cmd = 1; }
-    bar(1);
-    partial(o, tau, jsplit);
-    bar(2);
-    const int nw = blockDim.x >> 5;
-    double v[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) v[q] = warp_sum(lane < nw ? part[q * 32 + lane] : 0.0);
-    if (!isfinite(v[0] + v[1] + v[2] + v[3])) {  // a term left the FP32 range: FP64, warp 0
-      const double dO = dc[o];
-      for (int q = 0; q < 4; q++) v[q] = 0.0;
+    for (int q = 0; q < 4; q++)
+      r[q] = pair_scaled(df_warp_sum(df_add(v[q], u[q])), (q & 1) ? Z - 2 * E : Z - E);
+    if (!(finite_bits(r[0]) && finite_bits(r[1]) && finite_bits(r[2]) && finite_bits(r[3]))) {
+      // a term left the FP32 range: FP64
+      for (int q = 0; q < 4; q++) r[q] = 0.0;
       for (int i = lane; i < k; i += 32) {
         if (i == o) continue;
         const double rc = rcp64((dc[i] - dO) - tau);
         const double t = z2c[i] * rc, dt = t * rc;
-        if (i <= jsplit) { v[0] += t; v[1] += dt; }
-        else { v[2] += t; v[3] += dt; }
+        if (i <= jsplit) { r[0] += t; r[1] += dt; }
+        else { r[2] += t; r[3] += dt; }
       }
-      for (int q = 0; q < 4; q++) v[q] = warp_sum(v[q]);
+      for (int q = 0; q < 4; q++) r[q] = warp_sum(r[q]);
     }
     const double ri = -rcp64(tau);  // the origin pole
     const double t = z2c[o] * ri, dt = t * ri;
-    if (o <= jsplit) { v[0] += t; v[1] += dt; }
-    else { v[2] += t; v[3] += dt; }
-    SecSums s = {v[0], v[1], v[2], v[3], v[2] - v[0]};
-    return s;
-  }
-  // warps 1 ..
-  __device__ void help() const {
-    while (true) {
-      bar(1);
-      if (*s_cmd == 0) return;
-      partial(*s_o, *s_tau, *s_js);
-      bar(2);
-    }
+    if (o <= jsplit) { r[0] += t; r[1] += dt; }
+    else { r[2] += t; r[3] += dt; }
+    SecSums sm = {r[0], r[1], r[2], r[3], r[2] - r[0]};
+    return sm;
   }
 };
 
@@ -1410,9 +1524,9 @@ __device__ int secular_root(const Sums& sums, const double* __restrict__ dc,
       double QR = sm.dpsiR * dR * dR, PR = sm.psiR - sm.dpsiR * dR;
       double c = 1.0 + R * (PL + PR);
       double A = c, B = c * (dL + dR) + R * (QL + QR), C = w * dL * dR;
-      double disc = fmax(B * B - 4.0 * A * C, 0.0);
-      double sq = sqrt(disc);
-      eta = (B > 0.0) ? (2.0 * C) / (B + sq) : (B - sq) / (2.0 * A);
+      const double disc = fmax(B * B - 4.0 * A * C, 0.0);
+      const double sq = disc > 0.0 ? disc * rsqrt64(disc) : 0.0;
+      eta = (B > 0.0) ? (2.0 * C) * rcp64(B + sq) : (B - sq) * rcp64(2.0 * A);
     } else {
       // all poles lie left of the root: the nearest one (k-1) exactly, the rest modelled
       // at the next pole (k-2) by value and slope
@@ -1426,16 +1540,16 @@ __device__ int secular_root(const Sums& sums, const double* __restrict__ dc,
       double c = 1.0 + R * P1;
       if (c > 0.0) {
         double A = c, B = c * (d1 + d2) + R * (Q1 + Q2), C = w * d1 * d2;
-        double disc = fmax(B * B - 4.0 * A * C, 0.0);
-        double sq = sqrt(disc);
-        eta = (B >= 0.0) ? (B + sq) / (2.0 * A) : (2.0 * C) / (B - sq);
+        const double disc = fmax(B * B - 4.0 * A * C, 0.0);
+        const double sq = disc > 0.0 ? disc * rsqrt64(disc) : 0.0;
+        eta = (B >= 0.0) ? (B + sq) * rcp64(2.0 * A) : (2.0 * C) * rcp64(B - sq);
       } else {
         ok = false;
         eta = 0.0;
       }
     }
     double tn = tau + eta;
-    if (!ok || !isfinite(tn) || !(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (!ok || !finite_bits(tn) || !(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
     if (tn == tau || fabs(tn - tau) <= 2.0 * kU * fabs(tau)) {
       *o_out = o; *tau_out = tn; return 0;
     }
@@ -1469,26 +1583,47 @@ __device__ __forceinline__ void store_root(int j, int o, double t, int k, double
   }
 }
 
-constexpr int kSecularThreads = 1024;
-constexpr int kSecularSpecial = 1 + 2 * kSqMaxWide;  // the last root and the wide roots
+constexpr int kSecularThreads = 512;
+constexpr int kSecStageMax = 12288;  // poles staged in shared memory up to this size (192 KB)
 
-__global__ void __launch_bounds__(kSecularThreads) k_secular(
+template <bool FARF>
+__global__ void __launch_bounds__(FARF ? kSecularThreads : 256) k_secular(
     const double* __restrict__ dc, const double* __restrict__ z2c, const int* __restrict__ kp,
     const double* __restrict__ rhop, const double* __restrict__ dk, int* orgc, double* tauc,
     int* org, double* tau, double* dorg, int* status, int maxit, const double* __restrict__ sqb,
     const int* __restrict__ sqn, const int* __restrict__ sqf, const double* __restrict__ sqv,
-    const float2* __restrict__ z2f) {
+    const float2* __restrict__ z2f, int stage_n) {
   __shared__ double s_zn2;
   __shared__ double s_x[kSqP], s_w[kSqP];
   const int k = kp[0];
   const double rho = rhop[0];
   const double R = fabs(rho);
-  const bool far = sqv != nullptr && k >= kSqMinK;
-  if (threadIdx.x < 32) {
+  const bool far = FARF && sqv != nullptr && k >= kSqMinK;
+  // The far-field form reads the poles and their pair weights once per term of every
+  // iteration, from a few warps per SM: from shared memory (staged here when they fit,
+  // stage_n >= k) instead of L2 that latency is no longer exposed.
+  extern __shared__ double s_stage[];
+  if (far && k <= stage_n) {
+    float2* sz = (float2*)(s_stage + stage_n);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      s_stage[i] = dc[i];
+      sz[i] = z2f[i];
+    }
+    dc = s_stage;
+    z2f = sz;
+  }
+  {  // ||z||^2 by the whole block (a warp alone would run k / 32 dependent FP64 adds)
+    __shared__ double s_part[32];
     double a = 0.0;
-    for (int i = threadIdx.x; i < k; i += 32) a += z2c[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) a += z2c[i];
     a = warp_sum(a);
-    if (threadIdx.x == 0) s_zn2 = a;
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      a = threadIdx.x < (int)(blockDim.x >> 5) ? s_part[threadIdx.x] : 0.0;
+      a = warp_sum(a);
+      if (threadIdx.x == 0) s_zn2 = a;
+    }
   }
   if (threadIdx.x < kSqP) {  // Chebyshev nodes and barycentric weights (first kind)
     const double th = (2.0 * threadIdx.x + 1.0) / (2.0 * kSqP);
@@ -1498,58 +1633,60 @@ __global__ void __launch_bounds__(kSecularThreads) k_secular(
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int first = far ? sqf[0] : 0, last = far ? sqf[1] : k - 2;
-  // The special roots: the last root, whose bracket reaches far past the poles, and the
-  // wide roots below `first` and above `last`.  Block s < nspec solves special root s
-  // with direct sums over the whole block (one block of kSecularThreads per SM); the
-  // other blocks share the regular roots, so no regular root waits behind a special
-  // one and no SM is left with nothing to do.
-  const int nwl = far ? first : 0, nwr = far ? k - 2 - last : 0;
-  const int nspec = far ? 1 + nwl + nwr : 0;
-  if (blockIdx.x < nspec) {
-    const int s = blockIdx.x;
-    const int j = (s == 0) ? k - 1 : (s <= nwl ? s - 1 : last + (s - nwl));
-    // warp 0 iterates, the whole block evaluates the sums
-    __shared__ double part[4 * 32];
-    __shared__ double s_tau;
-    __shared__ int s_o, s_js, s_cmd;
-    // the last root's offset reaches R ||z||^2 past the largest pole: its own scale
-    const int E = max(sqf[2], exp2_of(R * s_zn2) + 2);
-    const LedSums ls = {dc, z2c, k, part, &s_tau, &s_o, &s_js, &s_cmd, z2f, E, sqf[3]};
-    if (threadIdx.x < 32) {
+  const int wl = threadIdx.x >> 5;
+  if (far) {
+    // The special roots -- the last root, whose bracket reaches far past the poles, and
+    // the wide roots below `first` and above `last` -- one warp each with direct sums
+    // over every pole (the warps interleaved over the blocks, so over the SMs); every
+    // other warp takes kSecRoots consecutive boxed roots, a group of kSecG lanes each.
+    const int nwl = first, nwr = k - 2 - last;
+    const int nspec = 1 + nwl + nwr;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int gw = wl * gridDim.x + blockIdx.x;
+    if (gw < nspec) {
+      const int s = gw;
+      const int j = (s == 0) ? k - 1 : (s <= nwl ? s - 1 : last + (s - nwl));
+      // the last root's offset reaches R ||z||^2 past the largest pole: its own scale
+      const int E = max(sqf[2], exp2_of(R * s_zn2) + 2);
+      const WarpPairSums ps = {dc, z2c, k, z2f, E, sqf[3]};
       int o;
       double t;
-      const int bad = secular_root(ls, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
-      if (lane == 0) s_cmd = 0;
-      LedSums::bar(1);  // releases the helpers
+      const int bad = secular_root(ps, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
       if (lane == 0) {
         if (bad) latch(status, SVDUP_ENOCONV);
         if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
         store_root(j, o, t, k, rho, dk, orgc, tauc, org, tau, dorg);
       }
-    } else {
-      ls.help();
+      return;
+    }
+    const FarSumsG fsg = {dc, z2c, z2f, s_x, s_w, sqf[2], sqf[3]};
+    const int g = lane / kSecG, sub = lane % kSecG;
+    for (int q = gw - nspec; first + kSecRoots * q <= last; q += nwarps - nspec) {
+      const int jr = first + kSecRoots * q + g;
+      const bool active = jr <= last;
+      const int j = active ? jr : first;  // an idle group evaluates a valid root
+      const int b = (j - first) / kSqLeaf;
+      const FarBox fb = {sqn[2 * b], sqn[2 * b + 1], sqb[2 * b], sqb[2 * b + 1],
+                         sqv + (size_t)4 * b * kSqP};
+      int o;
+      double t;
+      const int bad = secular_root_group(fsg, fb, dc, R, j, active, maxit, sub, g, &o, &t);
+      if (active && sub == 0) {
+        if (bad) latch(status, SVDUP_ENOCONV);
+        if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
+        store_root(j, o, t, k, rho, dk, orgc, tauc, org, tau, dorg);
+      }
     }
     return;
   }
-  const int off = nspec;
   // roots interleaved over the blocks (root j to block j mod G): neighbouring roots, whose
   // work is alike, spread over the SMs
-  const int G = gridDim.x - off, bm = blockIdx.x - off, wl = threadIdx.x >> 5;
+  const int G = gridDim.x;
   const DirectSums direct = {dc, z2c, k};
-  for (int j = wl * G + bm; j < k; j += G * (blockDim.x >> 5)) {
+  for (int j = wl * G + blockIdx.x; j < k; j += G * (blockDim.x >> 5)) {
     int o;
     double t;
-    int bad;
-    if (far && (j < first || j > last)) continue;  // done by blocks 0-2
-    if (far) {
-      const int b = (j - first) / kSqLeaf;
-      const FarSums fs = {dc,      z2c,      sqn[2 * b], sqn[2 * b + 1], sqb[2 * b],
-                          sqb[2 * b + 1], sqv + (size_t)4 * b * kSqP, s_x, s_w, z2f,
-                          sqf[2],  sqf[3]};
-      bad = secular_root(fs, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
-    } else {
-      bad = secular_root(direct, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
-    }
+    const int bad = secular_root(direct, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
     if (lane == 0) {
       if (bad) latch(status, SVDUP_ENOCONV);
       if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
@@ -1595,19 +1732,22 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
     SVDUP_COUNT_LAUNCH();
     sqv = e.sqv;
   }
-  // a warp per root, one block per SM (the roots are interleaved over them); with the
-  // far-field form, one block per SM in all, the first ones taking the special roots
-  // (at most kSecularSpecial of them)
-  // Without the far field (k < kSqMinK), blocks of 8 warps: a small solve then takes a
-  // few SMs' worth of registers instead of whole SMs, which lets many small problems
-  // (a batch's lanes) solve side by side.
+  // With the far field, one block per SM; its warps take the special roots (one each)
+  // and then kSecRoots boxed roots at a time.  Without it (k < kSqMinK), a warp per root in
+  // blocks of 8 warps: a small solve then takes a few SMs' worth of registers instead of
+  // whole SMs, which lets many small problems (a batch's lanes) solve side by side.
   const int sms = device_sm_count();
   const int threads = sqv ? kSecularThreads : 256;
-  const int blocks = sqv ? std::max(sms, kSecularSpecial + 1)
-                         : std::min((e.N + threads / 32 - 1) / (threads / 32), 4 * sms);
-  k_secular<<<blocks, threads, 0, st>>>(
+  const int blocks = sqv ? sms : std::min((e.N + threads / 32 - 1) / (threads / 32), 4 * sms);
+  // the poles and pair weights staged in shared memory (16 B per pole) when they fit
+  const int stage_n = (sqv && e.N <= kSecStageMax) ? e.N : 0;
+  const size_t smem = (size_t)stage_n * (sizeof(double) + sizeof(float2));
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_secular<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = sqv ? k_secular<true> : k_secular<false>;
+  kern<<<blocks, threads, smem, st>>>(
       e.dc, e.z2c, e.kp, e.rhop, e.dk, e.orgc, e.tauc, e.org, e.tau, e.dorg, status, maxit, e.sqb,
-      e.sqn, e.sqf, sqv, e.z2f);
+      e.sqn, e.sqf, sqv, e.z2f, stage_n);
   SVDUP_COUNT_LAUNCH();
 }
 
