@@ -156,7 +156,7 @@ Eig make_eig(Arena& ar, int N) {
   const size_t nbox = (n + 63) / 64;
   e.sqb = ar.take<double>(2 * nbox);
   e.sqn = ar.take<int>(2 * nbox);
-  e.sqf = ar.take<int>(4);
+  e.sqf = ar.take<int>(8);
   e.z2f = ar.take<float2>(n);
   e.sqv = ar.take<double>(4 * 26 * nbox);
   e.fsc = ar.take<int>(4);

@@ -163,7 +163,7 @@ struct Eig {
   // origin and half width, its near pole range, and the far sums at its nodes
   double* sqb;
   int* sqn;
-  int* sqf;  // the boxed roots first .. last, the pair-form scales E, Z
+  int* sqf;  // the boxed roots first .. last, the pair-form scales E, Z; [4]: the solver's root counter
   float2* z2f;  // z^2 2^-Z as pairs (the far-field form)
   double* sqv;
   // double-float copies for the pair-arithmetic sums (svdup_dfsum.cu): scales fsc[4]

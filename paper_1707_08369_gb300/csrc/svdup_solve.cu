@@ -1078,6 +1078,7 @@ __global__ void k_sq_boxes(const double* __restrict__ dc, const int* __restrict_
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     sqf[0] = first;
     sqf[1] = last;
+    sqf[4] = 0;  // the solver's root counter
   }
   const int nb = sq_boxes(first, last);
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
@@ -1420,60 +1421,82 @@ __device__ int secular_root_group(const FarSumsG& sums, const FarBox& fb,
   return done ? 0 : 1;
 }
 
-// The sums of one root by one warp over every pole, in pairs as FarSumsG's near field,
-// the origin pole in FP64 (the special roots of the far-field form: the last root and
-// the wide roots).  Two accumulator sets per lane keep two terms in flight.
-struct WarpPairSums {
+// The sums of one root by a whole block, for a root iterated by warp 0 alone (the
+// block's other warps only help evaluate): warp 0 posts (o, tau, jsplit) and meets the
+// helpers at named barrier 1; every warp adds its share of the poles into part[4][32];
+// at barrier 2 warp 0 collects them.  The helpers leave when warp 0 posts cmd = 0.
+struct LedSums {
   const double* dc;
   const double* z2c;
   int k;
-  const float2* z2f;  // the pair form (scales E, Z)
+  double* part;  // shared, 4 x 32
+  double* s_tau;
+  int* s_o;
+  int* s_js;
+  int* s_cmd;
+  const float2* z2f;  // the pair form (scales E, Z), as FarSums
   int E, Z;
   static constexpr double wtol = kSecTolPairs;
-  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
+  __device__ static void bar(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"((int)blockDim.x) : "memory");
+  }
+  __device__ void partial(int o, double tau, int jsplit) const {
     Df v[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    Df u[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const double dO = dc[o];
     const Df ntau = df_neg(df_from_f64(tau, E));
-    for (int i = lane; i < k; i += 64) {
-      if (i != o) {
-        Df t, dt;
-        const float2 z = z2f[i];
-        pair_term(dc[i] - dO, ntau, Df{z.x, z.y}, E, t, dt);
-        if (i <= jsplit) { v[0] = df_add(v[0], t); v[1] = df_add(v[1], dt); }
-        else { v[2] = df_add(v[2], t); v[3] = df_add(v[3], dt); }
-      }
-      const int i2 = i + 32;
-      if (i2 < k && i2 != o) {
-        Df t, dt;
-        const float2 z = z2f[i2];
-        pair_term(dc[i2] - dO, ntau, Df{z.x, z.y}, E, t, dt);
-        if (i2 <= jsplit) { u[0] = df_add(u[0], t); u[1] = df_add(u[1], dt); }
-        else { u[2] = df_add(u[2], t); u[3] = df_add(u[3], dt); }
-      }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      if (i == o) continue;  // the origin pole: FP64, by warp 0
+      Df t, dt;
+      const float2 z = z2f[i];
+      pair_term(dc[i] - dO, ntau, Df{z.x, z.y}, E, t, dt);
+      if (i <= jsplit) { v[0] = df_add(v[0], t); v[1] = df_add(v[1], dt); }
+      else { v[2] = df_add(v[2], t); v[3] = df_add(v[3], dt); }
     }
-    double r[4];
+    const int w = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < 4; q++)
-      r[q] = pair_scaled(df_warp_sum(df_add(v[q], u[q])), (q & 1) ? Z - 2 * E : Z - E);
-    if (!(finite_bits(r[0]) && finite_bits(r[1]) && finite_bits(r[2]) && finite_bits(r[3]))) {
-      // a term left the FP32 range: FP64
-      for (int q = 0; q < 4; q++) r[q] = 0.0;
+    for (int q = 0; q < 4; q++) {
+      const Df r = df_warp_sum(v[q]);
+      if ((threadIdx.x & 31) == 0) part[q * 32 + w] = pair_scaled(r, (q & 1) ? Z - 2 * E : Z - E);
+    }
+  }
+  // warp 0 only
+  __device__ SecSums operator()(int o, double tau, int jsplit, int lane) const {
+    if (lane == 0) { *s_o = o; *s_tau = tau; *s_js = jsplit; *s_cmd = 1; }
+    bar(1);
+    partial(o, tau, jsplit);
+    bar(2);
+    const int nw = blockDim.x >> 5;
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = warp_sum(lane < nw ? part[q * 32 + lane] : 0.0);
+    if (!(finite_bits(v[0]) && finite_bits(v[1]) && finite_bits(v[2]) && finite_bits(v[3]))) {
+      // a term left the FP32 range: FP64, warp 0
+      const double dO = dc[o];
+      for (int q = 0; q < 4; q++) v[q] = 0.0;
       for (int i = lane; i < k; i += 32) {
         if (i == o) continue;
         const double rc = rcp64((dc[i] - dO) - tau);
         const double t = z2c[i] * rc, dt = t * rc;
-        if (i <= jsplit) { r[0] += t; r[1] += dt; }
-        else { r[2] += t; r[3] += dt; }
+        if (i <= jsplit) { v[0] += t; v[1] += dt; }
+        else { v[2] += t; v[3] += dt; }
       }
-      for (int q = 0; q < 4; q++) r[q] = warp_sum(r[q]);
+      for (int q = 0; q < 4; q++) v[q] = warp_sum(v[q]);
     }
     const double ri = -rcp64(tau);  // the origin pole
     const double t = z2c[o] * ri, dt = t * ri;
-    if (o <= jsplit) { r[0] += t; r[1] += dt; }
-    else { r[2] += t; r[3] += dt; }
-    SecSums sm = {r[0], r[1], r[2], r[3], r[2] - r[0]};
-    return sm;
+    if (o <= jsplit) { v[0] += t; v[1] += dt; }
+    else { v[2] += t; v[3] += dt; }
+    SecSums s = {v[0], v[1], v[2], v[3], v[2] - v[0]};
+    return s;
+  }
+  // warps 1 ..
+  __device__ void help() const {
+    while (true) {
+      bar(1);
+      if (*s_cmd == 0) return;
+      partial(*s_o, *s_tau, *s_js);
+      bar(2);
+    }
   }
 };
 
@@ -1636,32 +1659,45 @@ __global__ void __launch_bounds__(FARF ? kSecularThreads : 256) k_secular(
   const int wl = threadIdx.x >> 5;
   if (far) {
     // The special roots -- the last root, whose bracket reaches far past the poles, and
-    // the wide roots below `first` and above `last` -- one warp each with direct sums
-    // over every pole (the warps interleaved over the blocks, so over the SMs); every
-    // other warp takes kSecRoots consecutive boxed roots, a group of kSecG lanes each.
+    // the wide roots below `first` and above `last` -- one block each: warp 0 iterates,
+    // the whole block evaluates the direct sums over every pole (LedSums).  Then every
+    // warp takes kSecRoots consecutive boxed roots at a time, a group of kSecG lanes
+    // each, from a counter (sqf[4], zeroed by k_sq_boxes): the blocks that solved a
+    // special root join in when it is done, so the boxed roots never wait for them.
     const int nwl = first, nwr = k - 2 - last;
     const int nspec = 1 + nwl + nwr;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const int gw = wl * gridDim.x + blockIdx.x;
-    if (gw < nspec) {
-      const int s = gw;
+    for (int s = blockIdx.x; s < nspec; s += gridDim.x) {
       const int j = (s == 0) ? k - 1 : (s <= nwl ? s - 1 : last + (s - nwl));
+      __shared__ double part[4 * 32];
+      __shared__ double s_tau;
+      __shared__ int s_o, s_js, s_cmd;
       // the last root's offset reaches R ||z||^2 past the largest pole: its own scale
       const int E = max(sqf[2], exp2_of(R * s_zn2) + 2);
-      const WarpPairSums ps = {dc, z2c, k, z2f, E, sqf[3]};
-      int o;
-      double t;
-      const int bad = secular_root(ps, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
-      if (lane == 0) {
-        if (bad) latch(status, SVDUP_ENOCONV);
-        if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
-        store_root(j, o, t, k, rho, dk, orgc, tauc, org, tau, dorg);
+      const LedSums ls = {dc, z2c, k, part, &s_tau, &s_o, &s_js, &s_cmd, z2f, E, sqf[3]};
+      if (threadIdx.x < 32) {
+        int o;
+        double t;
+        const int bad = secular_root(ls, dc, z2c, k, R, s_zn2, j, lane, maxit, &o, &t);
+        if (lane == 0) s_cmd = 0;
+        LedSums::bar(1);  // releases the helpers
+        if (lane == 0) {
+          if (bad) latch(status, SVDUP_ENOCONV);
+          if (!isfinite(t)) latch(status, SVDUP_ENONFINITE);
+          store_root(j, o, t, k, rho, dk, orgc, tauc, org, tau, dorg);
+        }
+      } else {
+        ls.help();
       }
-      return;
+      __syncthreads();
     }
+    int* next = const_cast<int*>(sqf) + 4;
     const FarSumsG fsg = {dc, z2c, z2f, s_x, s_w, sqf[2], sqf[3]};
     const int g = lane / kSecG, sub = lane % kSecG;
-    for (int q = gw - nspec; first + kSecRoots * q <= last; q += nwarps - nspec) {
+    while (true) {
+      int q = 0;
+      if (lane == 0) q = atomicAdd(next, 1);
+      q = __shfl_sync(0xffffffffu, q, 0);
+      if (first + kSecRoots * q > last) break;
       const int jr = first + kSecRoots * q + g;
       const bool active = jr <= last;
       const int j = active ? jr : first;  // an idle group evaluates a valid root
@@ -1732,8 +1768,8 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
     SVDUP_COUNT_LAUNCH();
     sqv = e.sqv;
   }
-  // With the far field, one block per SM; its warps take the special roots (one each)
-  // and then kSecRoots boxed roots at a time.  Without it (k < kSqMinK), a warp per root in
+  // With the far field, one block per SM: the first blocks take the special roots (one
+  // each), then every warp kSecRoots boxed roots at a time from a counter.  Without it (k < kSqMinK), a warp per root in
   // blocks of 8 warps: a small solve then takes a few SMs' worth of registers instead of
   // whole SMs, which lets many small problems (a batch's lanes) solve side by side.
   const int sms = device_sm_count();
