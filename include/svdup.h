@@ -203,6 +203,18 @@ int svdup_rank_one_eig(svdup_t h, int N, const double* d, const double* z, doubl
                        double* lam);
 
 /*
+ * y = Q x for the eigenvectors Q of diag(d) + rho z z^T (RankOneUpdate STEP 7's product
+ * with one vector, as the sign pairing applies it), device pointers:
+ *   in:  N, d (N poles, any order), z (N), rho != 0, x (N; entry q multiplies the
+ *        eigenvector of the q-th smallest eigenvalue);
+ *   out: y (N, in the order of d), lam (N eigenvalues, ascending).
+ * The same solve and deflation as svdup_rank_one_eig, the sums in FP64 (far-field form
+ * from the handle's svdup_set_far_sums threshold).
+ */
+int svdup_rank_one_apply(svdup_t h, int N, const double* d, const double* z, double rho,
+                         const double* x, double* y, double* lam);
+
+/*
  * Secular roots alone (Sec. 3.1, Eq. GolubEigenvalUpdate), device pointers:
  * d (k, strictly ascending), z (k, nonzero), rho != 0 -> org (k ints), tau (k) with
  * root j = d[org[j]] + tau[j], ascending; org[j] is the pole nearer to root j.

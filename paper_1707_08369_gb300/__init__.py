@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     lib.svdup_tuning_get_tile.argtypes = [P, I, P]
     lib.svdup_tuning_set_tile.argtypes = [P, I, I]
     lib.svdup_set_far_sums.argtypes = [P, I, I]
+    lib.svdup_rank_one_apply.argtypes = [P, I, P, P, D, P, P, P]
     S_T = ctypes.c_size_t
     lib.svdup_update_workspace.argtypes = [P, I, I, D, I, ctypes.POINTER(S_T)]
     lib.svdup_server_create.argtypes = [I, I, S_T, D, I, ctypes.POINTER(P)]
@@ -299,6 +300,19 @@ class Handle:
                                          _ptr(out["lam"])), "svdup_rank_one_eig")
         _check(self.sync(), "svdup_rank_one_eig (device)")
         return out
+
+    def rank_one_apply(self, d, z, rho: float, x):
+        """y = Q x for the eigenvectors Q of diag(d) + rho z z^T (device tensors; x in
+        the order of the ascending eigenvalues, y in the order of d).  Returns (y, lam)."""
+        import torch
+        N = d.numel()
+        _dev_f64(d, "d"); _dev_f64(z, "z", N); _dev_f64(x, "x", N)
+        y = torch.zeros(N, dtype=torch.float64, device=d.device)
+        lam = torch.zeros(N, dtype=torch.float64, device=d.device)
+        _check(load().svdup_rank_one_apply(self._h, N, _ptr(d), _ptr(z), float(rho), _ptr(x),
+                                           _ptr(y), _ptr(lam)), "svdup_rank_one_apply")
+        _check(self.sync(), "svdup_rank_one_apply (device)")
+        return y, lam
 
     def secular(self, d, z, rho: float):
         """Roots of the secular equation for strictly ascending d and nonzero z."""

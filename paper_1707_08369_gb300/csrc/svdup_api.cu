@@ -1325,6 +1325,34 @@ int svdup_rank_one_eig(svdup_t h, int N, const double* d, const double* z, doubl
   return check_launch();
 }
 
+int svdup_rank_one_apply(svdup_t h, int N, const double* d, const double* z, double rho,
+                         const double* x, double* y, double* lam) {
+  if (!h || N < 1 || !d || !z || !x || !y || !lam) return SVDUP_EINVAL;
+  if (!(rho != 0.0) || !isfinite(rho)) return SVDUP_EINVAL;
+  if (set_device(h)) return SVDUP_ECUDA;
+  Arena meas = {nullptr, 0};
+  make_eig(meas, N);
+  meas.take<double>(1);
+  meas.take<double>(N);
+  int rc = ensure_ws(h, meas.off);
+  if (rc) return rc;
+  Arena ar = {h->ws, 0};
+  Eig e = make_eig(ar, N);
+  e.vfmin = h->vf_min;
+  e.vfmin_pairs = h->vf_min_pairs;
+  double* rhod = ar.take<double>(1);
+  double* work = ar.take<double>(N);
+  cudaStream_t st = h->stream;
+  if (cudaMemcpyAsync(rhod, &rho, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SVDUP_ECUDA;
+  launch_fill_generic(st, e, d, z, rhod, h->status);
+  queue_solve(h, st, e);
+  launch_norms(st, e, nullptr, nullptr);
+  launch_apply_q(st, e, x, work, y, false);
+  cudaMemcpyAsync(lam, e.lam, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return check_launch();
+}
+
 int svdup_secular(svdup_t h, int k, const double* d, const double* z, double rho, int* org,
                   double* tau) {
   if (!h || k < 1 || !d || !z || !org || !tau) return SVDUP_EINVAL;

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(1024) k_df_prep(Eig e, const double* __restric
                                                   const double* __restrict__ xfinal) {
   __shared__ int sx[4];
   const int k = e.kp[0];
-  if (!xfinal && e.vf && k >= e.vfmin_pairs) return;  // the norms take the far-field form
+  if (e.vf && k >= e.vfmin_pairs) return;  // the far-field form replaces the pair sums
   if (threadIdx.x < 4) sx[threadIdx.x] = -1100;
   __syncthreads();
   int mE = -1100, mZ = -1100, mY = -1100, mW = -1100;
@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(256) k_apply_q_df(Eig e, const double* __restr
   const int* __restrict__ org = e.org;
   const float2* __restrict__ tf = e.tf;
   const float2* __restrict__ wf = e.wf;
-  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < k; t += warps) {
+  const bool far = e.vf && k >= e.vfmin_pairs;  // the far-field form writes the kept entries
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < (far ? 0 : k); t += warps) {
     const double dt = e.dk[t];
     Df acc = {0.f, 0.f};
     for (int j = lane; j < k; j += 32) {

@@ -422,6 +422,8 @@ void launch_loewner_df(cudaStream_t st, Eig e);
 void launch_vf_loewner(cudaStream_t st, Eig e, int kmin);
 void launch_vf_norms(cudaStream_t st, Eig e, int kmin, const double* ysorted, double* out_final,
                      bool keep_inv);
+// Q x for the sign pairing: vsorted[idx[t]] = zhat_t sum_j x_rank(j) inv_j / (d_t - mu_j).
+void launch_vf_applyq(cudaStream_t st, Eig e, int kmin, const double* xfinal, double* vsorted);
 // pairs = true: the sums in double-float arithmetic (svdup_dfsum.cu), for outputs that
 // need FP32 accuracy only (the mixed mode's vectors and signs)
 // keep_inv: the stored 1/||c_j|| stay as they are (the norms are recomputed for the

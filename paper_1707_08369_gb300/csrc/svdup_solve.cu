@@ -2136,7 +2136,8 @@ __global__ void k_apply_q_core(Eig e, const double* __restrict__ xfinal, double*
   const int k = e.kp[0];
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < k; t += warps) {
+  const bool far = e.vf && k >= e.vfmin;  // the far-field form writes the kept entries
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < (far ? 0 : k); t += warps) {
     const double dt = e.dk[t];
     double acc = 0.0;
     for (int j = lane; j < k; j += 32) {
@@ -2166,6 +2167,9 @@ __global__ void __launch_bounds__(1024) k_unrotate_scatter(Eig e, double* vsorte
 
 void launch_apply_q(cudaStream_t st, Eig e, const double* xfinal, double* work, double* yphys,
                     bool pairs) {
+  // the far-field form when k >= vfmin (FP64) or vfmin_pairs (FP32 pairs); the direct
+  // kernels then copy the deflated entries only
+  launch_vf_applyq(st, e, pairs ? e.vfmin_pairs : e.vfmin, xfinal, work);
   if (pairs) {
     launch_apply_q_core_df(st, e, xfinal, work, secular_blocks(e.N));
   } else {

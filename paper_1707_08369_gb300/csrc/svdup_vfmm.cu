@@ -1,7 +1,7 @@
 // svdup_vfmm.cu -- the far field of the solve's own Cauchy-like sums: Loewner's zhat
-// (Sec. 3.2) and the column norms ||c_j|| with the transposed product Q^T y
-// (RankOneUpdate STEP 7, Eq. CTildeFinalForm1), by App. D's interpolation FMM applied
-// to a single vector.  Summed directly, each is O(k^2) work on the FP64 pipe; here only
+// (Sec. 3.2), the column norms ||c_j|| with the transposed product Q^T y (RankOneUpdate
+// STEP 7, Eq. CTildeFinalForm1) and the product Q x, by App. D's interpolation FMM
+// applied to a single vector.  Summed directly, each is O(k^2) work on the FP64 pipe; here only
 // the near leaves are summed directly and the rest goes through Chebyshev expansions
 // (App. D STEPs 5-9) over a hierarchy of boxes.
 //
@@ -29,7 +29,9 @@
 // Norms: ||c_j||^2 = sum_t zhat_t^2 / (d_t - mu_j)^2 (kernel 1/(s - x)^2, point charges
 // zhat_t^2 at the poles, targets the roots); Q^T y: sum_t zhat_t y_t / (d_t - mu_j)
 // (kernel 1/(s - x)).  The last root, beyond every pole, is summed directly, each leaf
-// adding its own poles' terms.
+// adding its own poles' terms.  Q x (the sign pairing's product): zhat_t sum_j w_j /
+// (d_t - mu_j), w_j = x_j / ||c_j|| (point charges at the roots, targets the poles; the
+// last root's term added directly to every target).
 //
 // Expansions: kVfP = 28 first-kind Chebyshev nodes per box.  A source box's charges are
 // interpolated onto its nodes (STEP 5: the weight of node b is the Lagrange basis u_b
@@ -63,7 +65,7 @@ constexpr int P = kVfP;
 constexpr int kLeafMax = 2 * kVfLeaf;  // a leaf holds fewer indices than this
 constexpr int kMaxLevels = 32;
 
-enum { PROB_LOEWNER = 0, PROB_NORMS = 1 };
+enum { PROB_LOEWNER = 0, PROB_NORMS = 1, PROB_APPLYQ = 2 };
 
 // The device view of Eig::vf / Eig::vfc for the current k.
 struct Vf {
@@ -232,12 +234,18 @@ __global__ void __launch_bounds__(128) k_vf_leaf(Eig e, int kmin, const double* 
       shi = j1 < k ? dc[orgc[j1 - 1]] + tauc[j1 - 1] : dc[k - 1];
       tlo = dc[j0];
       thi = dc[j1 - 1];
-    } else {  // sources: poles; targets: the roots but the last
+    } else if (PROB == PROB_NORMS) {  // sources: poles; targets: the roots but the last
       const int jt = min(j1, k - 1) - 1;
       slo = dc[j0];
       shi = dc[j1 - 1];
       tlo = dc[orgc[j0]] + tauc[j0];
       thi = dc[orgc[jt]] + tauc[jt];
+    } else {  // sources: the roots but the last; targets: poles
+      const int jt = min(j1, k - 1) - 1;
+      slo = dc[orgc[j0]] + tauc[j0];
+      shi = dc[orgc[jt]] + tauc[jt];
+      tlo = dc[j0];
+      thi = dc[j1 - 1];
     }
     sg[0] = 0.5 * (slo + shi);
     sg[1] = 0.5 * (shi - slo);
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(128) k_vf_leaf(Eig e, int kmin, const double* 
         for (int q = 0; q < nc; q++) acc += rows[q][mm];
       __syncthreads();
     }
-  } else {
+  } else if (PROB == PROB_NORMS) {
     const double sgn = rho > 0.0 ? 1.0 : -1.0;
     for (int q = tid; q < nc; q += blockDim.x) {
       const int j = j0 + q;
@@ -284,6 +292,26 @@ __global__ void __launch_bounds__(128) k_vf_leaf(Eig e, int kmin, const double* 
       wq[0][q] = zh * zh;
       wq[1][q] = ysorted ? sgn * zh * ysorted[e.idx[io]] : 0.0;
       point_row((dc[j] - c) * ir, rows[q]);
+    }
+    __syncthreads();
+    if (tid < 2 * P)
+      for (int q = 0; q < nc; q++) acc = fma(wq[sm][q], rows[q][mm], acc);
+  } else {
+    // Q x: charges w_j = x_j / ||c_j|| at the roots (ysorted holds x in the final order),
+    // with the sign that makes the far field sgn * sum_j w_j / (d_t - mu_j) in the
+    // rho > 0 orientation; the last root acts directly on every target
+    const double sgn = rho > 0.0 ? 1.0 : -1.0;
+    for (int q = tid; q < nc; q += blockDim.x) {
+      const int j = j0 + q;
+      wq[1][q] = 0.0;
+      if (j == k - 1) {
+        wq[0][q] = 0.0;
+        point_row(0.0, rows[q]);
+      } else {
+        const int io = rho > 0.0 ? j : k - 1 - j;
+        wq[0][q] = -sgn * e.inv[io] * ysorted[e.rank_root[io]];
+        point_row(((dc[orgc[j]] - c) + tauc[j]) * ir, rows[q]);
+      }
     }
     __syncthreads();
     if (tid < 2 * P)
@@ -391,7 +419,7 @@ __global__ void __launch_bounds__(32) k_vf_m2l(Eig e, int kmin, int nsets) {
       for (int b = 0; b < P; b++) {
         const double q0 = __shfl_sync(0xffffffffu, w0, b);
         const double rr = rcp64(fma(rs, st[b], base));
-        if (PROB == PROB_LOEWNER) {
+        if (PROB != PROB_NORMS) {
           s0 = fma(q0, rr, s0);
         } else {
           s0 = fma(q0, rr * rr, s0);
@@ -399,6 +427,7 @@ __global__ void __launch_bounds__(32) k_vf_m2l(Eig e, int kmin, int nsets) {
         }
       }
       if (PROB == PROB_LOEWNER) a0 += set == 0 ? s0 : -s0;
+      else if (PROB == PROB_APPLYQ) a0 += s0;
       else { a0 += s0; a1 += s1; }
     }
   }
@@ -533,6 +562,20 @@ __device__ __forceinline__ void norms_near(const Eig& e, const double* __restric
   }
 }
 
+// Q x's near terms of target pole x = d_t over roots [a, b): sum_j w_j / (d_t - mu_j)
+// (rho > 0 orientation, offsets from the roots' poles), w_j = x_j / ||c_j||.
+__device__ __forceinline__ double applyq_near(const Eig& e, const double* __restrict__ xfinal,
+                                              int a, int b, int k, double rho, double x,
+                                              int lane) {
+  double acc = 0.0;
+  for (int j = a + lane; j < b; j += 32) {
+    const int io = rho > 0.0 ? j : k - 1 - j;
+    const double w = e.inv[io] * xfinal[e.rank_root[io]];
+    acc = fma(w, rcp64((x - e.dc[e.orgc[j]]) - e.tauc[j]), acc);
+  }
+  return acc;
+}
+
 // Targets (STEP 9 and the near field, STEP 10): one warp per target, kLeafMax blocks per
 // leaf (those past the leaf's targets return).  Loewner writes zhat; the norms write inv
 // (unless keep_inv) and out_final[rank] = (Q^T y)_j when ysorted is given.  Each leaf's
@@ -547,7 +590,7 @@ __global__ void __launch_bounds__(32) k_vf_eval(Eig e, int kmin, const double* _
   const int l = blockIdx.x / kLeafMax, tq = blockIdx.x - l * kLeafMax;
   if (l >= v.nb) return;
   const int j0 = leaf_lo(l), j1 = leaf_hi(v, l);
-  const int tend = PROB == PROB_LOEWNER ? j1 : min(j1, k - 1);
+  const int tend = PROB == PROB_NORMS ? min(j1, k - 1) : j1;
   const int j = j0 + tq;
   if (j >= tend) return;
   __shared__ double st[P], sw[P], loc0[P], loc1[P];
@@ -573,7 +616,27 @@ __global__ void __launch_bounds__(32) k_vf_eval(Eig e, int kmin, const double* _
   const double R = fabs(rho);
   const int io = rho > 0.0 ? j : k - 1 - j;
   const bool all = nn > kVfNearMax;  // every pole near: the direct sums alone
-  if (PROB == PROB_LOEWNER) {
+  if (PROB == PROB_APPLYQ) {
+    const double xi = dc[j];
+    const double sgn = rho > 0.0 ? 1.0 : -1.0;
+    const double far = all ? 0.0 : bary_warp(loc0, (xi - ct) / rt, st, sw, lane);
+    double acc = 0.0;
+    if (all) {
+      acc = applyq_near(e, ysorted, 0, k - 1, k, rho, xi, lane);
+    } else {
+      for (int q = 0; q < nn; q++) {
+        const int L = snear[q];
+        acc += applyq_near(e, ysorted, leaf_lo(L), min(leaf_hi(v, L), k - 1), k, rho, xi, lane);
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const int il = rho > 0.0 ? k - 1 : 0;  // the last root, directly
+      acc += e.inv[il] * ysorted[e.rank_root[il]] *
+             rcp64((xi - dc[orgc[k - 1]]) - tauc[k - 1]);
+      out_final[e.idx[io]] = e.zhat[io] * (far + sgn * acc);
+    }
+  } else if (PROB == PROB_LOEWNER) {
     const double xi = dc[j];
     const double far = all ? 0.0 : bary_warp(loc0, (xi - ct) / rt, st, sw, lane);
     double pn = 1.0, pd = 1.0;
@@ -670,7 +733,7 @@ void vf_run(cudaStream_t st, Eig e, int kmin, const double* ysorted, double* out
             bool keep_inv) {
   if (!e.vf || e.N < kmin) return;
   const int Lmax = vf_lmax(e.N), Hmax = tree_levels(Lmax), tot = vf_tot(e.N);
-  const int nsets = PROB == PROB_LOEWNER ? 1 : (ysorted ? 2 : 1);
+  const int nsets = PROB == PROB_NORMS ? (ysorted ? 2 : 1) : 1;
   cudaMemsetAsync(e.vfc, 0, sizeof(int) * (size_t)tot, st);
   k_vf_leaf<PROB><<<Lmax + 1, 128, 0, st>>>(e, kmin, ysorted);
   SVDUP_COUNT_LAUNCH();
@@ -692,6 +755,10 @@ void launch_vf_loewner(cudaStream_t st, Eig e, int kmin) {
 void launch_vf_norms(cudaStream_t st, Eig e, int kmin, const double* ysorted, double* out_final,
                      bool keep_inv) {
   vf_run<PROB_NORMS>(st, e, kmin, ysorted, out_final, keep_inv);
+}
+
+void launch_vf_applyq(cudaStream_t st, Eig e, int kmin, const double* xfinal, double* vsorted) {
+  vf_run<PROB_APPLYQ>(st, e, kmin, xfinal, vsorted, true);
 }
 
 }  // namespace svdup

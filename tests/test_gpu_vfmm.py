@@ -3,7 +3,7 @@
 through App. D's interpolation FMM (here from a non-deflated size k of 2048 on; the
 library's defaults start it where it overtakes the direct sums).
 
-Three kinds of check, through the C ABI:
+Four kinds of check, through the C ABI:
 - against the oracle (its own bisection roots, direct products and sums), at the
   compact eigen-system tests' bars: the deflated set exactly, zhat within 1e-11
   max|zhat|, 1/||c_j|| within 1e-10 relative.  The norms of roots inside a cluster far
@@ -17,6 +17,9 @@ Three kinds of check, through the C ABI:
   ratios, two roundings each) and 2 k u for 1/||c_j|| (k positive terms), and in RMS
   within 2e-14 (the far field's interpolation error is about 1e-16; the direct sums'
   rounding is a random walk of about sqrt(k) u, 1e-14 at k = 8192);
+- y = Q x, the sign pairing's product, whose far field takes the roots as sources
+  (svdup_rank_one_apply): against the oracle's Q x within 1e-9 of max|y| (the columns of
+  Q carry the roots' differences) and against the direct sums within 1e-12;
 - whole updates (n = 4096, where Q^T y forms the second solves' z) with and without the
   far-field form: FP64, singular values within 1e-13 S_1 and columns whose squared value
   is 1e-3 (relatively) from its neighbours within 1e-9; split BF16 (whose direct sums run
@@ -117,6 +120,29 @@ def test_far_sums_vs_oracle_and_direct(sv, handles, orc, case, N, seed, norms_vs
     assert rz.max() <= 4 * k * U53, rz.max()
     assert ri.max() <= 2 * k * U53, ri.max()
     assert np.sqrt(np.mean(rz ** 2)) <= 2e-14 and np.sqrt(np.mean(ri ** 2)) <= 2e-14
+
+
+@pytest.mark.parametrize("case,N,seed", [("uniform", 4096, 10), ("loguni", 8192, 11),
+                                         ("graded", 3000, 13), ("tight", 5000, 14)])
+def test_apply_q_vs_oracle_and_direct(sv, handles, orc, case, N, seed):
+    """y = Q x (the sign pairing's product) with Q x's far-field form: against the oracle's
+    Q x (its own roots; 1e-9 of max|y|) and against the direct sums on the same roots
+    (1e-12 of max|y|)."""
+    g = wl.rng(wl.BASE_SEED + 320 + seed)
+    d, rho = spectrum(case, N, g)
+    z = g.standard_normal(N)
+    x = g.standard_normal(N)
+    far, direct = handles
+    y1, lam1 = far.rank_one_apply(dev(d), dev(z), rho, dev(x))
+    y2, _ = direct.rank_one_apply(dev(d), dev(z), rho, dev(x))
+    y1, y2 = y1.cpu().numpy(), y2.cpu().numpy()
+    scale = np.abs(y2).max()
+    assert np.abs(y1 - y2).max() <= 1e-12 * scale, np.abs(y1 - y2).max() / scale
+    if case != "tight":
+        lam_o, yo = orc.rank_one_apply(d, z, rho, x)
+        # the largest root (rho ||z||^2 past the poles) within the evaluation bound k u
+        assert np.abs(lam1.cpu().numpy() - lam_o).max() <= 4 * N * U53 * np.abs(lam_o).max()
+        assert np.abs(y1 - yo[:, 0]).max() <= 1e-9 * scale
 
 
 @pytest.mark.parametrize("mode,sbar,vbar", [("FP64", 1e-13, 1e-9), ("MIXED_BF16X3", 1e-12, 1e-5)])
