@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-alt", action="store_true",
                     help="skip the other split form's sub-line (fp16x2 beside bf16x3 and back)")
     ap.add_argument("--eps", type=float, default=1e-12)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-cols", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -179,6 +179,9 @@ int svdup_refine_residuals(svdup_t h, double* out2);
  * the device on the handle's stream, the update runs, the results are copied back,
  * and the call waits for completion.  Returns the first error of the whole call.
  * Host buffers should be pinned for full copy bandwidth (any host memory works).
+ * The device copies (8 (m^2 + n^2 + 2m + n) bytes) stay allocated on the handle
+ * between calls, grown when a larger problem comes, and are freed by svdup_destroy;
+ * U's copy back starts as soon as U is final, beside the rest of the update.
  */
 int svdup_update_host(svdup_t h, int m, int n, double* U, int ldu, double* S, double* V, int ldv,
                       const double* a, const double* b, double eps, int mode);

@@ -62,6 +62,8 @@ struct svdup_ctx {
   int test_stall;     // svdup_check_timeout: the tensor-core drains hold their regions
   unsigned long long test_wait_ns;  // and the pipeline waits give up after this long
   double* ref_res;    // device: the last probe residuals of U and V (SVDUP_REFINE)
+  char* hb;           // svdup_update_host's device copies of U, S, V, a, b (kept)
+  size_t hb_size;
   // stage timers
   int timing;
   TimerRec* recs;
@@ -85,7 +87,7 @@ struct svdup_ctx {
   cudaStream_t side;   // the right-hand solves (high priority)
   cudaStream_t left;   // the left-hand solves (high priority)
   cudaStream_t prod[2];  // the products with U and with V (low priority)
-  cudaEvent_t ev_fork, ev_mid, ev_join;
+  cudaEvent_t ev_fork, ev_mid, ev_join, ev_copy;
   // e1 ready, e2 ready, e3 ready, e4 ready, U done, V done, left done, e1 deflated,
   // e1 merged, e3 deflated, e3 merged, e2 deflated, e2 leaves, e4 deflated, e4 leaves
   cudaEvent_t ev[15];
@@ -630,6 +632,7 @@ int make_side(svdup_ctx* h) {
   ok = ok && cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&h->ev_mid, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; i < 15; i++)
     ok = ok && cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
@@ -649,6 +652,7 @@ void free_side(svdup_ctx* h) {
   cudaEventDestroy(h->ev_fork);
   cudaEventDestroy(h->ev_mid);
   cudaEventDestroy(h->ev_join);
+  cudaEventDestroy(h->ev_copy);
   for (int i = 0; i < 15; i++) cudaEventDestroy(h->ev[i]);
   cudaStreamDestroy(h->prod[0]);
   cudaStreamDestroy(h->prod[1]);
@@ -692,6 +696,7 @@ void lane_destroy(svdup_ctx* l) {
   cudaStreamSynchronize(l->stream);
   free_side(l);
   if (l->ws) cudaFree(l->ws);
+  if (l->hb) cudaFree(l->hb);
   cudaStreamDestroy(l->stream);
   free(l->recs);
   free(l->pool);
@@ -907,6 +912,7 @@ int svdup_destroy(svdup_t h) {
   cudaStreamSynchronize(h->stream);
   free_side(h);
   if (h->ws) cudaFree(h->ws);
+  if (h->hb) cudaFree(h->hb);
   cudaFree(h->status);
   cudaFree(h->flops_dev);
   cudaFree(h->ref_res);
@@ -1246,48 +1252,60 @@ int svdup_update_host(svdup_t h, int m, int n, double* U, int ldu, double* S, do
   if (!h || !U || !S || !V || !a || !b) return SVDUP_EINVAL;
   if (m < 1 || n < m || ldu < m || ldv < n) return SVDUP_EINVAL;
   if (set_device(h)) return SVDUP_ECUDA;
-  double *dU = nullptr, *dS = nullptr, *dV = nullptr, *da = nullptr, *db = nullptr;
-  size_t bu = (size_t)m * m * sizeof(double), bv = (size_t)n * n * sizeof(double);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t bu = (size_t)m * m * sizeof(double), bv = (size_t)n * n * sizeof(double);
+  const size_t need = al(bu) + al(bv) + 2 * al(m * sizeof(double)) + al(n * sizeof(double));
+  if (h->hb_size < need) {  // the device copies stay with the handle between calls
+    cudaStreamSynchronize(h->stream);
+    if (h->hb) cudaFree(h->hb);
+    h->hb = nullptr;
+    h->hb_size = 0;
+    if (cudaMalloc(&h->hb, need) != cudaSuccess) {
+      cudaGetLastError();
+      h->hb = nullptr;
+      return SVDUP_ENOMEM;
+    }
+    h->hb_size = need;
+  }
+  char* q = h->hb;
+  double* dU = (double*)q; q += al(bu);
+  double* dV = (double*)q; q += al(bv);
+  double* dS = (double*)q; q += al(m * sizeof(double));
+  double* da = (double*)q; q += al(m * sizeof(double));
+  double* db = (double*)q;
+  cudaStream_t st = h->stream;
   int rc = SVDUP_OK;
-  if (cudaMalloc(&dU, bu) != cudaSuccess || cudaMalloc(&dS, m * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dV, bv) != cudaSuccess || cudaMalloc(&da, m * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&db, n * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    rc = SVDUP_ENOMEM;
-    goto out;
-  }
   if (cudaMemcpy2DAsync(dU, m * sizeof(double), U, (size_t)ldu * sizeof(double),
-                        m * sizeof(double), m, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
-      cudaMemcpyAsync(dS, S, m * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
-          cudaSuccess ||
+                        m * sizeof(double), m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dS, S, m * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpy2DAsync(dV, n * sizeof(double), V, (size_t)ldv * sizeof(double),
-                        n * sizeof(double), n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
-      cudaMemcpyAsync(da, a, m * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(db, b, n * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
-          cudaSuccess) {
+                        n * sizeof(double), n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(da, a, m * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(db, b, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
     rc = SVDUP_ECUDA;
-    goto out;
   }
-  rc = svdup_update(h, m, n, dU, m, dS, dV, n, da, db, eps, mode);
-  if (rc) goto out;
-  if (cudaMemcpy2DAsync(U, (size_t)ldu * sizeof(double), dU, m * sizeof(double),
-                        m * sizeof(double), m, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-      cudaMemcpyAsync(S, dS, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
-          cudaSuccess ||
-      cudaMemcpy2DAsync(V, (size_t)ldv * sizeof(double), dV, n * sizeof(double),
-                        n * sizeof(double), n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) {
-    rc = SVDUP_ECUDA;
-    goto out;
+  if (!rc) rc = svdup_update(h, m, n, dU, m, dS, dV, n, da, db, eps, mode);
+  if (!rc) {
+    // U is final once its last product has run (ev[4] on its product stream, recorded
+    // at the update's join; nothing after the join writes U unless the refinement
+    // runs): its copy back then overlaps the right side's end and V's copy.  (Splitting
+    // each matrix's copies over two streams per direction measured no faster: the
+    // copies run at the host link's rate either way.)
+    const bool early = h->side && h->timing != SVDUP_TIMING_STAGES && !(mode & SVDUP_REFINE);
+    cudaStream_t su = early ? h->left : st;
+    if (early && cudaStreamWaitEvent(su, h->ev[4], 0) != cudaSuccess) rc = SVDUP_ECUDA;
+    if (!rc && (cudaMemcpy2DAsync(U, (size_t)ldu * sizeof(double), dU, m * sizeof(double),
+                                  m * sizeof(double), m, cudaMemcpyDeviceToHost, su) != cudaSuccess ||
+                cudaMemcpyAsync(S, dS, m * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaMemcpy2DAsync(V, (size_t)ldv * sizeof(double), dV, n * sizeof(double),
+                                  n * sizeof(double), n, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+      rc = SVDUP_ECUDA;
+    if (!rc && early &&
+        (cudaEventRecord(h->ev_copy, su) != cudaSuccess || cudaStreamWaitEvent(st, h->ev_copy, 0) != cudaSuccess))
+      rc = SVDUP_ECUDA;
   }
-  rc = svdup_sync(h);
-out:
-  cudaStreamSynchronize(h->stream);
-  if (dU) cudaFree(dU);
-  if (dS) cudaFree(dS);
-  if (dV) cudaFree(dV);
-  if (da) cudaFree(da);
-  if (db) cudaFree(db);
+  if (!rc) rc = svdup_sync(h);
+  cudaStreamSynchronize(st);
   return rc;
 }
 

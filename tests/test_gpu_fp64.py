@@ -276,6 +276,19 @@ def test_update_host_matches_device(sv, hnd, orc):
     Uh, Sh, Vhh = np.asfortranarray(U.copy()), S.copy(), np.asfortranarray(V.copy())
     hnd.update_host(Uh, Sh, Vhh, a.copy(), b.copy())
     assert np.array_equal(Sh, Sn) and np.array_equal(Uh, Un) and np.array_equal(Vhh, Vn)
+    # again, on the device copies the handle kept, and then on a larger problem (the
+    # copies grow) and a smaller one
+    Uh, Sh, Vhh = np.asfortranarray(U.copy()), S.copy(), np.asfortranarray(V.copy())
+    hnd.update_host(Uh, Sh, Vhh, a.copy(), b.copy())
+    assert np.array_equal(Sh, Sn) and np.array_equal(Uh, Un) and np.array_equal(Vhh, Vn)
+    for (mm, nn, sd) in ((64, 80, 4), (24, 30, 5)):
+        A2, a2, b2 = wl.small_gaussian(mm, nn, seed=sd)
+        U2, S2, V2h = np.linalg.svd(A2)
+        V2 = np.asfortranarray(V2h.T)
+        U2n, S2n, V2n = _run_update(sv, hnd, U2, S2, V2, a2, b2)
+        U2h, S2h, V2hh = np.asfortranarray(U2.copy()), S2.copy(), np.asfortranarray(V2.copy())
+        hnd.update_host(U2h, S2h, V2hh, a2.copy(), b2.copy())
+        assert np.array_equal(S2h, S2n) and np.array_equal(U2h, U2n) and np.array_equal(V2hh, V2n)
 
 
 def test_chained_updates(sv, hnd, orc):
