@@ -934,7 +934,8 @@ void launch_deflate(cudaStream_t st, Eig e, int* status) {
 // Secular equation (Sec. 3.1, Eq. GolubEigenvalUpdate):
 //   w(mu) = 1 + R sum_i z_i^2 / (d_i - mu),  R > 0, d strictly ascending.
 // Root j lies in (d_j, d_{j+1}) (j < k-1) or in (d_{k-1}, d_{k-1} + R ||z||^2].
-// One warp per root; the lanes split the k poles and reduce.  The root is held as
+// One warp per root (two per warp in the far-field form, below); the lanes split the
+// poles and reduce.  The root is held as
 // mu = d_o + tau with o the nearer pole (decided by the sign of w at the bracket
 // midpoint), so every difference d_i - mu = (d_i - d_o) - tau keeps full relative
 // accuracy when the root sits next to a pole.
@@ -1224,8 +1225,10 @@ struct FarSumsG {
   const double* sx;
   const double* sw;
   int E, Z;
-  // The sums of FarSums for the group's root mu = d_o + tau in box fb; every lane of the
-  // group returns them.  sub: this lane's index in its group, g: the group.
+  // The far-field form's split sums for the group's root mu = d_o + tau in box fb (the
+  // poles of the box's near range directly, the rest by barycentric interpolation of the
+  // box's node values); every lane of the group returns them.  sub: this lane's index
+  // in its group, g: the group.
   __device__ SecSums operator()(const FarBox& fb, int o, double tau, int jsplit, int sub,
                                 int g) const {
     SecSums s = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -1434,7 +1437,7 @@ struct LedSums {
   int* s_o;
   int* s_js;
   int* s_cmd;
-  const float2* z2f;  // the pair form (scales E, Z), as FarSums
+  const float2* z2f;  // the pair form (scales E, Z), as FarSumsG
   int E, Z;
   static constexpr double wtol = kSecTolPairs;
   __device__ static void bar(int id) {
@@ -1501,7 +1504,8 @@ struct LedSums {
 };
 
 // One root in the rho > 0 orientation; returns 0 on convergence.  `sums` evaluates the
-// split sums of w at mu = d_o + tau (DirectSums or FarSums).
+// split sums of w at mu = d_o + tau (DirectSums, or LedSums for the far-field form's
+// special roots).
 template <class Sums>
 __device__ int secular_root(const Sums& sums, const double* __restrict__ dc,
                             const double* __restrict__ z2c, int k, double R, double zn2, int j,
@@ -1769,9 +1773,10 @@ void launch_secular(cudaStream_t st, Eig e, int* status, int maxit) {
     sqv = e.sqv;
   }
   // With the far field, one block per SM: the first blocks take the special roots (one
-  // each), then every warp kSecRoots boxed roots at a time from a counter.  Without it (k < kSqMinK), a warp per root in
-  // blocks of 8 warps: a small solve then takes a few SMs' worth of registers instead of
-  // whole SMs, which lets many small problems (a batch's lanes) solve side by side.
+  // each), then every warp kSecRoots boxed roots at a time from a counter.  Without it
+  // (k < kSqMinK), a warp per root in blocks of 8 warps: a small solve then takes a few
+  // SMs' worth of registers instead of whole SMs, which lets many small problems (a
+  // batch's lanes) solve side by side.
   const int sms = device_sm_count();
   const int threads = sqv ? kSecularThreads : 256;
   const int blocks = sqv ? sms : std::min((e.N + threads / 32 - 1) / (threads / 32), 4 * sms);
