@@ -107,3 +107,12 @@ def test_header_is_plain_c(tmp_path):
     assert out.returncode == 0, out.stderr
     code = int(out.stdout.split()[0])
     assert code in (0, 5), out.stdout  # OK with a GPU, SVDUP_ECUDA without
+
+
+def test_binding_declares_every_entry_point():
+    """The ctypes binding gives every declared entry point its argument types (a call
+    through an undeclared one would pass doubles as ints)."""
+    src = open(os.path.join(ROOT, "paper_1707_08369_gb300", "__init__.py")).read()
+    typed = set(re.findall(r"lib\.(svdup_\w+)\.argtypes", src))
+    missing = sorted(_declared() - typed)
+    assert not missing, "no argtypes in the binding for: %s" % ", ".join(missing)
