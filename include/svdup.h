@@ -150,8 +150,8 @@ int svdup_update(svdup_t h, int m, int n, double* U, int ldu, double* S, double*
                  const double* a, const double* b, double eps, int mode);
 
 /*
- * Orthogonalising refinement (no counterpart in the paper: the spec precision
- * form's correction of split-precision products).  One Newton-Schulz step toward the
+ * Orthogonalising refinement (no counterpart in the paper: a correction of the
+ * orthogonality that split-precision products lose).  One Newton-Schulz step toward the
  * nearest matrix with orthonormal columns,
  *   X <- X (3 I - X^T X) / 2 = X - X E / 2,   E = X^T X - I,
  * in place on X (device, rows x cols column-major, ldx >= rows, rows >= cols >= 1), on
